@@ -1,0 +1,244 @@
+"""Seeded synthetic inputs for LRDMC: trial-function systems and walker starts.
+
+This module builds the inputs that both the CUDA library and the CPU oracle
+consume. It holds none of the projection method's arithmetic: it only
+writes down trial functions (nuclei, Slater-type or contracted-Gaussian
+shells, orbital coefficients, Pade Jastrow parameters) and draws the first
+electron positions from a seeded generator.
+
+The paper's own guiding functions (optimised JSD/JAGP with cc-pVDZ or ADZP
+bases, supplement Sec. III) are not reproducible here, so the systems are
+the simple Slater-Jastrow atoms of the workloads this library is measured on:
+
+* ``helium``: 1s Slater orbital exp(-1.6875 r) for each spin, Pade e-e
+  Jastrow r / (2 (1 + r)).
+* ``neon``: a single determinant of 1s/2s/2p Slater-type orbitals with
+  exponents from Slater's rules, Pade e-e and e-n Jastrow factors.
+* ``hydrogen``, ``hydrogenic_ion`` and ``be_bare`` are exactly solvable
+  checks: with the exact orbital the local energy is constant.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+MAX_PRIM = 16
+
+STO = 0
+GTO = 1
+
+
+@dataclass
+class Shell:
+    center: int
+    l: int
+    kind: int = STO
+    n_eff: float = 1.0
+    zeta: float = 1.0
+    alpha: list = field(default_factory=list)
+    coef: list = field(default_factory=list)
+
+
+@dataclass
+class System:
+    name: str
+    nuc_xyz: np.ndarray
+    Z: np.ndarray
+    n_up: int
+    n_dn: int
+    shells: list
+    C: np.ndarray  # [n_ao][n_mo]
+    b_ee: float = 1.0
+    c_par: float = 0.25
+    c_anti: float = 0.5
+    en_b1: np.ndarray = None
+    en_b2: float = 1.0
+    ee_on: bool = True
+    # shell whose radial density seeds the start radius of each orbital
+    orbital_shell: list = None
+    exact_energy: float | None = None
+
+    @property
+    def N(self) -> int:
+        return self.n_up + self.n_dn
+
+    @property
+    def n_nuc(self) -> int:
+        return len(self.Z)
+
+    @property
+    def n_ao(self) -> int:
+        return sum(2 * s.l + 1 for s in self.shells)
+
+    @property
+    def n_mo(self) -> int:
+        return self.C.shape[1]
+
+    def shell_arrays(self):
+        """Flat arrays describing the shells (prim arrays padded to MAX_PRIM)."""
+        ns = len(self.shells)
+        center = np.array([s.center for s in self.shells], dtype=np.int32)
+        l = np.array([s.l for s in self.shells], dtype=np.int32)
+        kind = np.array([s.kind for s in self.shells], dtype=np.int32)
+        nprim = np.array([len(s.alpha) for s in self.shells], dtype=np.int32)
+        neff = np.array([s.n_eff for s in self.shells], dtype=np.float64)
+        zeta = np.array([s.zeta for s in self.shells], dtype=np.float64)
+        alpha = np.zeros((ns, MAX_PRIM))
+        coef = np.zeros((ns, MAX_PRIM))
+        for q, s in enumerate(self.shells):
+            alpha[q, : len(s.alpha)] = s.alpha
+            coef[q, : len(s.coef)] = s.coef
+        return center, l, kind, nprim, neff, zeta, alpha, coef
+
+
+def _atom(Z: float):
+    return np.zeros((1, 3)), np.array([float(Z)])
+
+
+def hydrogen(zeta: float = 1.0) -> System:
+    """H atom, psi = exp(-zeta r); exact for zeta = 1 (E = -0.5)."""
+    return hydrogenic_ion(1, zeta)
+
+
+def hydrogenic_ion(Z: int, zeta: float | None = None) -> System:
+    """One electron around charge Z, psi = exp(-zeta r); exact when zeta = Z."""
+    zeta = float(Z) if zeta is None else zeta
+    xyz, Zs = _atom(Z)
+    return System(
+        name=f"Z{Z}_1e", nuc_xyz=xyz, Z=Zs, n_up=1, n_dn=0,
+        shells=[Shell(0, 0, STO, 1.0, zeta)], C=np.eye(1),
+        c_par=0.0, c_anti=0.0, en_b1=np.zeros(1), orbital_shell=[0],
+        exact_energy=-0.5 * Z * Z if zeta == Z else None,
+    )
+
+
+def helium(zeta: float = 1.6875) -> System:
+    """He, 1s exp(-zeta r) per spin times the e-e Pade factor r / (2 (1 + r))
+    and the e-n factor exp(-(2 - zeta) r / (1 + r)), whose slope completes the
+    nuclear cusp (without it E_L ~ -(2 - zeta)/r near the nucleus and the
+    lattice Hamiltonian, whose kinetic part is bounded, has no ground state)."""
+    xyz, Zs = _atom(2)
+    return System(
+        name="He", nuc_xyz=xyz, Z=Zs, n_up=1, n_dn=1,
+        shells=[Shell(0, 0, STO, 1.0, zeta)], C=np.eye(1),
+        b_ee=1.0, c_par=0.25, c_anti=0.5, en_b1=np.array([2.0 - zeta]), en_b2=1.0,
+        orbital_shell=[0],
+    )
+
+
+def be_bare() -> System:
+    """Be nucleus with four non-interacting electrons in the exact hydrogenic
+    1s = exp(-4 r) and 2s = (1 - 2 r) exp(-2 r) orbitals: E = 2(-8) + 2(-2) = -20
+    for every configuration; the 2s node makes fixed-node sign flips occur."""
+    xyz, Zs = _atom(4)
+    shells = [Shell(0, 0, STO, 1.0, 4.0), Shell(0, 0, STO, 1.0, 2.0), Shell(0, 0, STO, 2.0, 2.0)]
+    C = np.array([[1.0, 0.0], [0.0, 1.0], [0.0, -2.0]])
+    return System(
+        name="Be_bare", nuc_xyz=xyz, Z=Zs, n_up=2, n_dn=2, shells=shells, C=C,
+        c_par=0.0, c_anti=0.0, en_b1=np.zeros(1), ee_on=False,
+        orbital_shell=[0, 2], exact_energy=-20.0,
+    )
+
+
+# Slater's-rule exponents for the closed-shell atoms used here.
+# Ne: 1s (10 - 0.30) / 1 = 9.70; 2s2p (10 - 7*0.35 - 2*0.85) / 2 = 2.925.
+NE_ZETA_1S = 9.70
+NE_ZETA_2SP = 2.925
+
+
+def neon() -> System:
+    """Ne, one determinant per spin of hydrogenic-style orbitals with
+    Slater's-rule exponents: 1s = exp(-z1 r), 2s = (1 + (z2 - z1) r) exp(-z2 r),
+    2p = (x, y, z) exp(-z2 r), z1 = 9.70, z2 = 2.925. Both s orbitals have the
+    slope -z1 at the nucleus, so the e-n factor -(10 - z1) r / (1 + r)
+    completes the nuclear cusp for every configuration; the e-e Pade factor
+    has 1/2 (antiparallel) and 1/4 (parallel), b = 1."""
+    xyz, Zs = _atom(10)
+    z1, z2 = NE_ZETA_1S, NE_ZETA_2SP
+    shells = [
+        Shell(0, 0, STO, 1.0, z1),
+        Shell(0, 0, STO, 1.0, z2),
+        Shell(0, 0, STO, 2.0, z2),
+        Shell(0, 1, STO, 2.0, z2),
+    ]
+    C = np.zeros((6, 5))
+    C[0, 0] = 1.0
+    C[1, 1] = 1.0
+    C[2, 1] = z2 - z1
+    C[3, 2] = C[4, 3] = C[5, 4] = 1.0
+    return System(
+        name="Ne", nuc_xyz=xyz, Z=Zs, n_up=5, n_dn=5, shells=shells, C=C,
+        b_ee=1.0, c_par=0.25, c_anti=0.5, en_b1=np.array([10.0 - z1]), en_b2=1.0,
+        orbital_shell=[0, 2, 3, 3, 3],
+    )
+
+
+def tiny_mixed(seed: int = 7) -> System:
+    """Four-electron check system (2 up, 2 down) on two nuclei with mixed
+    s/p/d Slater shells, one contracted-Gaussian shell and a dense,
+    well-conditioned orbital-coefficient matrix: used for brute-force checks."""
+    rng = np.random.default_rng(seed)
+    xyz = np.array([[0.0, 0.0, 0.0], [0.3, -0.4, 1.1]])
+    Zs = np.array([3.0, 1.0])
+    shells = [
+        Shell(0, 0, STO, 1.0, 2.7),
+        Shell(0, 1, STO, 2.0, 1.3),
+        Shell(1, 0, GTO, alpha=[3.1, 0.62, 0.17], coef=[0.2, 0.5, 0.4]),
+        Shell(0, 2, STO, 3.0, 1.1),
+    ]
+    n_ao = 1 + 3 + 1 + 5
+    C = np.zeros((n_ao, 2))
+    C[:, 0] = rng.normal(0, 0.3, n_ao)
+    C[:, 1] = rng.normal(0, 0.3, n_ao)
+    C[0, 0] += 1.0
+    C[1, 1] += 1.0
+    return System(
+        name="tiny_mixed", nuc_xyz=xyz, Z=Zs, n_up=2, n_dn=2, shells=shells, C=C,
+        b_ee=0.8, c_par=0.25, c_anti=0.5, en_b1=np.array([0.2, 0.1]), en_b2=1.3,
+        orbital_shell=[0, 1],
+    )
+
+
+SYSTEMS = {
+    "H": hydrogen,
+    "He": helium,
+    "Ne": neon,
+    "Be_bare": be_bare,
+    "tiny_mixed": tiny_mixed,
+}
+
+
+def make_system(name: str, **kw) -> System:
+    return SYSTEMS[name](**kw)
+
+
+def initial_positions(system: System, n_walkers: int, seed: int) -> np.ndarray:
+    """Start configurations [W][N][3]: electron i of a spin block occupies
+    orbital i of that block; its distance from the orbital's centre is drawn
+    from the radial density r^(2n) exp(-2 zeta r) of the Slater shell seeding
+    that orbital (a Gamma(2n + 1, 1/(2 zeta)) variate; for a Gaussian shell a
+    Gamma(3, 1/2) variate in bohr), its direction uniformly on the sphere."""
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    N = system.N
+    x = np.empty((n_walkers, N, 3))
+    for i in range(N):
+        m = i if i < system.n_up else i - system.n_up
+        sh = system.shells[system.orbital_shell[m % len(system.orbital_shell)]]
+        if sh.kind == STO:
+            r = rng.gamma(2.0 * sh.n_eff + 1.0, 1.0 / (2.0 * sh.zeta), n_walkers)
+        else:
+            r = rng.gamma(3.0, 0.5, n_walkers)
+        v = rng.normal(size=(n_walkers, 3))
+        v /= np.linalg.norm(v, axis=1, keepdims=True)
+        x[:, i, :] = system.nuc_xyz[sh.center][None, :] + r[:, None] * v
+    return x
+
+
+def random_rotations(n: int, seed: int) -> np.ndarray:
+    """Uniformly random 3x3 rotation matrices [n][9] (row-major, column k is
+    the rotated axis e_k), drawn with SciPy: inputs for single-evaluation
+    checks that bypass the in-kernel rotation draw."""
+    from scipy.spatial.transform import Rotation
+
+    return Rotation.random(n, random_state=seed).as_matrix().reshape(n, 9).copy()
