@@ -1,0 +1,202 @@
+/*
+ * lrdmc.h - C ABI of the GB300 (sm_103a) library for lattice-regularized
+ * diffusion Monte Carlo with the single-grid and the double-grid ("smart")
+ * lattice of Nakano, Maezono and Sorella, "Speeding up the ab initio
+ * diffusion Monte Carlo by a smart lattice regularization", arXiv:1909.01589.
+ *
+ * What the library computes, per walker and per walker-move:
+ *   - the lattice moves of every electron, r_i -> r_i +- h e_k on a randomly
+ *     rotated lattice, with h = a and (double grid) h = a', Eq. 1;
+ *   - p at each bond midpoint from Eq. 3 (this work) or Eq. 2 (previous),
+ *     with r_c and a'/a from S-13 and Eq. 6 / Eq. 7, or from Eq. 4;
+ *   - psi_G(x')/psi_G(x) at every move for a Slater-Jastrow trial function,
+ *     the fixed-node jump rates T = w/(2h^2) max(ratio, 0) and the local
+ *     energy (the LRDMC method the paper builds on, Casula, Filippi and
+ *     Sorella, PRL 95, 100201 (2005));
+ *   - continuous-time projection: waiting time, weight, heat-bath jump and
+ *     Sherman-Morrison update of the inverse Slater matrix, and comb
+ *     reconfiguration of the population at the end of every interval tau.
+ *
+ * Conventions for every entry point:
+ *   - lengths in bohr, energies in hartree, all floating point in IEEE
+ *     double (FP64);
+ *   - configurations are [N][3] row-major, electrons 0..n_up-1 spin up;
+ *   - a rotation is a 3x3 row-major matrix whose column k is the axis e_k;
+ *   - candidate (lattice move) c is ordered electron-major, then grid
+ *     (a before a'), axis (x, y, z), sign (+ before -):
+ *         c = ((i*G + g)*3 + k)*2 + (sign < 0),   P = 6 G N moves;
+ *   - every function returns a status and never aborts; on failure
+ *     lrdmc_last_error() describes the cause;
+ *   - device pointers are plain CUDA device addresses (e.g. from PyTorch),
+ *     owned by the caller; host pointers are ordinary host memory, owned by
+ *     the caller; the library copies what it needs during the call;
+ *   - a stream is borrowed, never destroyed; all work of a system is
+ *     ordered on the stream given to lrdmc_init_walkers.
+ * Random numbers: Philox4x64-10 (Salmon et al., SC'11) keyed by (seed, 0),
+ * counter (walker slot, interval k, iteration m, tag); uniforms are
+ * ((bits >> 12) + 1/2) 2^-52.
+ */
+#ifndef LRDMC_H
+#define LRDMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LRDMC_API __attribute__((visibility("default")))
+#else
+#define LRDMC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LRDMC_MAX_NUC 8
+#define LRDMC_MAX_SHELL 32
+#define LRDMC_MAX_PRIM 8
+#define LRDMC_MAX_AO 64
+#define LRDMC_MAX_SPIN 32 /* electrons per spin */
+
+typedef struct lrdmc_system_s* lrdmc_system_t;
+
+typedef enum {
+  LRDMC_OK = 0,
+  LRDMC_ERR_ARG = 1,       /* invalid argument or size beyond the limits    */
+  LRDMC_ERR_CUDA = 2,      /* a CUDA call failed                            */
+  LRDMC_ERR_SINGULAR = 3,  /* singular Slater matrix or zero update ratio   */
+  LRDMC_ERR_NONFINITE = 4, /* non-finite local energy or rate               */
+  LRDMC_ERR_TIMEOUT = 5,   /* an interval exceeded its iteration limit      */
+  LRDMC_ERR_STATE = 6      /* call out of order (e.g. step before init)     */
+} lrdmc_status;
+
+/* Lattice spacing function, Eq. 1-7 and S-13. */
+typedef enum {
+  LRDMC_SINGLE = 0,           /* single grid, p = 1                          */
+  LRDMC_DOUBLE_THIS_WORK = 1, /* Gaussian p (Eq. 3), r_c from S-13, a'/a Eq. 6 */
+  LRDMC_DOUBLE_PREVIOUS = 2,  /* Pade p (Eq. 2) with r_c = Z/2, a'/a Eq. 4   */
+  LRDMC_DOUBLE_EXPLICIT = 3   /* Gaussian p with the given r_c and a'/a      */
+} lrdmc_spacing_kind;
+
+typedef struct {
+  int kind;             /* lrdmc_spacing_kind                                  */
+  double beta;          /* S-13 prefactor (0.75 in the paper), THIS_WORK only  */
+  double kappa;         /* S-13 f(a) constant (2.5 in the paper), THIS_WORK   */
+  double rc;            /* r_c, EXPLICIT only                                 */
+  double aprime_over_a; /* a'/a, EXPLICIT only                               */
+} lrdmc_spacing_fn;
+
+/* One shell of atomic orbitals: 2l+1 real solid harmonics S (l = 0: 1;
+ * l = 1: x, y, z; l = 2: xy, yz, zx, x^2-y^2, 2z^2-x^2-y^2) times a radial
+ * part, kind 0 (Slater): r^(n_eff-1-l) exp(-zeta r); kind 1 (contracted
+ * Gaussian): sum_p coef[p] exp(-alpha[p] r^2). */
+typedef struct {
+  int center; /* nucleus index                 */
+  int l;      /* 0, 1 or 2                      */
+  int kind;   /* 0 = Slater, 1 = Gaussian       */
+  int n_prim; /* primitives (kind 1)            */
+  double n_eff;
+  double zeta;
+  double alpha[LRDMC_MAX_PRIM];
+  double coef[LRDMC_MAX_PRIM];
+} lrdmc_shell;
+
+/* Pade Jastrow factor J = sum_{i<j} c r_ij/(1 + b_ee r_ij)
+ *   (c = c_par for equal spins, c_anti otherwise)
+ *   - sum_{i,I} en_b1[I] r_iI/(1 + en_b2 r_iI);
+ * ee_on = 0 drops the electron-electron Coulomb repulsion (test systems). */
+typedef struct {
+  double b_ee, c_par, c_anti, en_b2;
+  double en_b1[LRDMC_MAX_NUC];
+  int ee_on;
+} lrdmc_jastrow;
+
+/* Creates a system: nuclei [n_nuc][3] and charges Z [n_nuc], n_up >= n_dn
+ * electrons, shells (AOs numbered shell by shell), MO coefficients C
+ * [n_ao][n_mo] row-major shared by both spins (spin down uses the first
+ * n_dn columns), Jastrow parameters. All inputs are host memory, copied.
+ * Limits: n_nuc <= LRDMC_MAX_NUC, n_shell <= LRDMC_MAX_SHELL,
+ * n_ao <= LRDMC_MAX_AO, n_up <= LRDMC_MAX_SPIN, n_mo >= n_up. No GPU work. */
+LRDMC_API lrdmc_status lrdmc_create_system(int n_nuc, const double* nuc_xyz, const double* Z,
+                                 int n_up, int n_dn, const lrdmc_shell* shells, int n_shells,
+                                 const double* mo_coeff, int n_ao, int n_mo,
+                                 const lrdmc_jastrow* jastrow, lrdmc_system_t* out);
+
+/* Double-grid parameters for spacing a: a'/a and r_c (S-13 with Eq. 6 and
+ * Eq. 7 for THIS_WORK, Eq. 4 with r_c = Z_max/2 for PREVIOUS; for a
+ * polyatomic system from the heaviest atom, as the paper's section on large
+ * systems prescribes). N_core of Eq. 7 uses Slater's-rule densities. Host
+ * computation, no GPU. For SINGLE returns a'/a = 1, r_c = 0. */
+LRDMC_API lrdmc_status lrdmc_spacing_params(lrdmc_system_t sys, double a, const lrdmc_spacing_fn* spacing,
+                                  double* aprime_over_a, double* rc);
+
+/* Device workspace bytes needed by lrdmc_init_walkers for n_walkers and a
+ * trace of trace_capacity intervals. */
+LRDMC_API lrdmc_status lrdmc_workspace_bytes(lrdmc_system_t sys, int n_walkers, int trace_capacity,
+                                   size_t* bytes);
+
+/* Starts a population of n_walkers at configurations x0 [n_walkers][N][3]
+ * (host or device memory; copied). workspace is caller-owned device memory
+ * of at least lrdmc_workspace_bytes(), 256-byte aligned, held by the system
+ * until lrdmc_destroy or the next init. tau is the reconfiguration
+ * interval, e_trial the energy shift of the log-weights, recompute_every the
+ * number of intervals between full recomputations of the inverse Slater
+ * matrices (0 = never). stream is a cudaStream_t (NULL = default stream).
+ * Fails with LRDMC_ERR_SINGULAR if a start configuration has a singular
+ * Slater matrix. */
+LRDMC_API lrdmc_status lrdmc_init_walkers(lrdmc_system_t sys, int n_walkers, const double* x0,
+                                uint64_t seed, double tau, double e_trial, int recompute_every,
+                                int trace_capacity, void* workspace, size_t workspace_bytes,
+                                void* stream);
+
+/* Projects the population through n_steps intervals of length tau with
+ * lattice spacing a and the given spacing function: per walker the
+ * continuous-time loop (waiting time of rate b_x, weight exp(-t (E_L -
+ * e_trial)), heat-bath jump, Sherman-Morrison update, new rotation and
+ * evaluation of all P moves), then comb reconfiguration and one trace entry
+ * per interval. Asynchronous on the stream except for one 4-byte read of
+ * the error word at the end. Fails with LRDMC_ERR_ARG when the trace would
+ * exceed its capacity. */
+LRDMC_API lrdmc_status lrdmc_step(lrdmc_system_t sys, int n_steps, double a, const lrdmc_spacing_fn* spacing);
+
+/* Copies the trace to host arrays (each nullable, length >= max_n): e_k =
+ * weighted mean local energy at the end of interval k, wbar_k = mean weight
+ * exp(-int (E_L - e_trial) dt), mean_jumps_k. *n_written = min(max_n, k). */
+LRDMC_API lrdmc_status lrdmc_get_energy_trace(lrdmc_system_t sys, double* e, double* wbar,
+                                    double* mean_jumps, int max_n, int* n_written);
+
+/* Copies the population to host arrays (each nullable): positions
+ * [W][N][3], E_L [W], b [W] and rates T [W][P] of the cached evaluation,
+ * the pre-reconfiguration log-weights and jump counts [W] of the last
+ * interval and the comb's parent indices [W]. Synchronises the stream. */
+LRDMC_API lrdmc_status lrdmc_get_walkers(lrdmc_system_t sys, double* x, double* el, double* b, double* T,
+                               double* logw_pre, int* jumps_pre, int* parent);
+
+/* Total number of walker-moves (jumps, each with one evaluation of all P
+ * moves) made by lrdmc_step since init. */
+LRDMC_API lrdmc_status lrdmc_moves(lrdmc_system_t sys, long long* moves);
+
+/* One evaluation of all P lattice moves for n_configs independent
+ * configurations (no population state): x [n][N][3] and rotations
+ * rot [n][9] are device inputs; ratio [n][P] (psi_G(x')/psi_G(x)),
+ * T [n][P], b [n] and el [n] are device outputs (each nullable except
+ * none of x, rot). Inverse Slater matrices are computed from x. */
+LRDMC_API lrdmc_status lrdmc_evaluate(lrdmc_system_t sys, int n_configs, const double* x, const double* rot,
+                            double a, const lrdmc_spacing_fn* spacing, double* ratio, double* T,
+                            double* b, double* el, void* stream);
+
+/* Writes / reads the population (positions, inverses, rotations, cached
+ * evaluation, parents, interval counter, trace) to / from a file. */
+LRDMC_API lrdmc_status lrdmc_save(lrdmc_system_t sys, const char* path);
+LRDMC_API lrdmc_status lrdmc_load(lrdmc_system_t sys, const char* path);
+
+/* Last error message of the system (static string if sys is NULL). */
+LRDMC_API const char* lrdmc_last_error(lrdmc_system_t sys);
+
+/* Releases the system (not the caller's workspace or stream). */
+LRDMC_API void lrdmc_destroy(lrdmc_system_t sys);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LRDMC_H */

@@ -1,0 +1,271 @@
+"""Python binding of liblrdmc.so, the GB300 (sm_103a) LRDMC library.
+
+Argument marshalling only: every step of the projection runs in the CUDA
+kernels behind the C ABI of include/lrdmc.h. PyTorch provides the device
+memory (the population workspace, configuration and output buffers) and
+the CUDA stream. There is no CPU fallback: importing the binding fails
+loudly when the compiled library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblrdmc.so")
+
+MAX_NUC = 8
+MAX_SHELL = 32
+MAX_PRIM = 8
+MAX_AO = 64
+MAX_SPIN = 32
+
+OK, ERR_ARG, ERR_CUDA, ERR_SINGULAR, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE = range(7)
+SINGLE, THIS_WORK, PREVIOUS, EXPLICIT = 0, 1, 2, 3
+
+EXPORTED = [
+    "lrdmc_create_system", "lrdmc_spacing_params", "lrdmc_workspace_bytes", "lrdmc_init_walkers",
+    "lrdmc_step", "lrdmc_get_energy_trace", "lrdmc_get_walkers", "lrdmc_moves", "lrdmc_evaluate",
+    "lrdmc_save", "lrdmc_load", "lrdmc_last_error", "lrdmc_destroy",
+]
+
+
+class LrdmcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"lrdmc status {status}: {msg}")
+        self.status = status
+
+
+class _Shell(ct.Structure):
+    _fields_ = [("center", ct.c_int), ("l", ct.c_int), ("kind", ct.c_int), ("n_prim", ct.c_int),
+                ("n_eff", ct.c_double), ("zeta", ct.c_double),
+                ("alpha", ct.c_double * MAX_PRIM), ("coef", ct.c_double * MAX_PRIM)]
+
+
+class _Jastrow(ct.Structure):
+    _fields_ = [("b_ee", ct.c_double), ("c_par", ct.c_double), ("c_anti", ct.c_double),
+                ("en_b2", ct.c_double), ("en_b1", ct.c_double * MAX_NUC), ("ee_on", ct.c_int)]
+
+
+class _Spacing(ct.Structure):
+    _fields_ = [("kind", ct.c_int), ("beta", ct.c_double), ("kappa", ct.c_double),
+                ("rc", ct.c_double), ("aprime_over_a", ct.c_double)]
+
+
+@dataclass(frozen=True)
+class Spacing:
+    """Lattice spacing function: SINGLE, THIS_WORK (Eq. 3, S-13, Eq. 6),
+    PREVIOUS (Eq. 2, Eq. 4) or EXPLICIT (Gaussian p with given r_c, a'/a)."""
+    kind: int = SINGLE
+    beta: float = 0.75
+    kappa: float = 2.5
+    rc: float = 0.0
+    aprime_over_a: float = 0.0
+
+    def c(self):
+        return _Spacing(self.kind, self.beta, self.kappa, self.rc, self.aprime_over_a)
+
+
+_lib = None
+
+
+def load_library():
+    """Load liblrdmc.so (built by ``__graft_entry__.build()``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"the CUDA library {LIB_PATH} is not built; run __graft_entry__.build()")
+    L = ct.CDLL(LIB_PATH)
+    i, d, vp, sz = ct.c_int, ct.c_double, ct.c_void_p, ct.c_size_t
+    L.lrdmc_create_system.restype = i
+    L.lrdmc_create_system.argtypes = [i, vp, vp, i, i, vp, i, vp, i, i, vp, ct.POINTER(vp)]
+    L.lrdmc_spacing_params.restype = i
+    L.lrdmc_spacing_params.argtypes = [vp, d, vp, ct.POINTER(d), ct.POINTER(d)]
+    L.lrdmc_workspace_bytes.restype = i
+    L.lrdmc_workspace_bytes.argtypes = [vp, i, i, ct.POINTER(sz)]
+    L.lrdmc_init_walkers.restype = i
+    L.lrdmc_init_walkers.argtypes = [vp, i, vp, ct.c_uint64, d, d, i, i, vp, sz, vp]
+    L.lrdmc_step.restype = i
+    L.lrdmc_step.argtypes = [vp, i, d, vp]
+    L.lrdmc_get_energy_trace.restype = i
+    L.lrdmc_get_energy_trace.argtypes = [vp, vp, vp, vp, i, ct.POINTER(i)]
+    L.lrdmc_get_walkers.restype = i
+    L.lrdmc_get_walkers.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    L.lrdmc_moves.restype = i
+    L.lrdmc_moves.argtypes = [vp, ct.POINTER(ct.c_longlong)]
+    L.lrdmc_evaluate.restype = i
+    L.lrdmc_evaluate.argtypes = [vp, i, vp, vp, d, vp, vp, vp, vp, vp, vp]
+    L.lrdmc_save.restype = i
+    L.lrdmc_save.argtypes = [vp, ct.c_char_p]
+    L.lrdmc_load.restype = i
+    L.lrdmc_load.argtypes = [vp, ct.c_char_p]
+    L.lrdmc_last_error.restype = ct.c_char_p
+    L.lrdmc_last_error.argtypes = [vp]
+    L.lrdmc_destroy.restype = None
+    L.lrdmc_destroy.argtypes = [vp]
+    _lib = L
+    return L
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(ct.c_void_p) if a is not None else None
+
+
+def _t_ptr(t):
+    return ct.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class LrdmcSystem:
+    """A trial function and, after ``init_walkers``, a walker population."""
+
+    def __init__(self, system):
+        L = load_library()
+        self.sys = system
+        n_shell = len(system.shells)
+        shells = (_Shell * n_shell)()
+        for q, s in enumerate(system.shells):
+            sh = shells[q]
+            sh.center, sh.l, sh.kind, sh.n_prim = s.center, s.l, s.kind, len(s.alpha)
+            sh.n_eff, sh.zeta = s.n_eff, s.zeta
+            for p, (a, c) in enumerate(zip(s.alpha, s.coef)):
+                sh.alpha[p], sh.coef[p] = a, c
+        jas = _Jastrow()
+        jas.b_ee, jas.c_par, jas.c_anti, jas.en_b2 = system.b_ee, system.c_par, system.c_anti, system.en_b2
+        en_b1 = system.en_b1 if system.en_b1 is not None else np.zeros(system.n_nuc)
+        for I in range(system.n_nuc):
+            jas.en_b1[I] = float(en_b1[I])
+        jas.ee_on = int(system.ee_on)
+        xyz = np.ascontiguousarray(system.nuc_xyz, dtype=np.float64)
+        Z = np.ascontiguousarray(system.Z, dtype=np.float64)
+        C = np.ascontiguousarray(system.C, dtype=np.float64)
+        h = ct.c_void_p()
+        st = L.lrdmc_create_system(system.n_nuc, _np_ptr(xyz), _np_ptr(Z), system.n_up, system.n_dn,
+                                   ct.cast(shells, ct.c_void_p), n_shell, _np_ptr(C), C.shape[0],
+                                   C.shape[1], ct.byref(jas), ct.byref(h))
+        if st != OK:
+            raise LrdmcError(st, L.lrdmc_last_error(None).decode())
+        self.h = h
+        self.N = system.N
+        self._ws = None
+        self.W = 0
+        self.stream = None
+        self.lattice_G = None
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            load_library().lrdmc_destroy(self.h)
+            self.h = None
+
+    def _check(self, st):
+        if st != OK:
+            raise LrdmcError(st, load_library().lrdmc_last_error(self.h).decode())
+
+    # ---------------------------------------------------------------- host
+    def spacing_params(self, a, spacing: Spacing):
+        r, rc = ct.c_double(), ct.c_double()
+        sp = spacing.c()
+        self._check(load_library().lrdmc_spacing_params(self.h, a, ct.byref(sp), ct.byref(r), ct.byref(rc)))
+        return r.value, rc.value
+
+    def workspace_bytes(self, n_walkers, trace_capacity):
+        b = ct.c_size_t()
+        self._check(load_library().lrdmc_workspace_bytes(self.h, n_walkers, trace_capacity, ct.byref(b)))
+        return b.value
+
+    # ---------------------------------------------------------------- population
+    def init_walkers(self, x0, seed, tau, e_trial=0.0, recompute_every=10, trace_capacity=4096,
+                     stream=None, device="cuda"):
+        """x0: [W][N][3] float64, a CUDA tensor or a host array (copied)."""
+        import torch
+
+        W = int(x0.shape[0])
+        nbytes = self.workspace_bytes(W, trace_capacity)
+        self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        base = self._ws.data_ptr()
+        ptr = (base + 255) & ~255
+        if stream is None:
+            stream = torch.cuda.current_stream(self._ws.device)
+        self.stream = stream
+        if isinstance(x0, np.ndarray):
+            x0 = np.ascontiguousarray(x0, dtype=np.float64)
+            xp = _np_ptr(x0)
+        else:
+            x0 = x0.contiguous()
+            assert x0.dtype == torch.float64
+            xp = _t_ptr(x0)
+        self._x0_keep = x0
+        st = load_library().lrdmc_init_walkers(self.h, W, xp, int(seed), float(tau), float(e_trial),
+                                               int(recompute_every), int(trace_capacity),
+                                               ct.c_void_p(ptr), nbytes, ct.c_void_p(stream.cuda_stream))
+        self._check(st)
+        self.W = W
+        return self
+
+    def step(self, n_steps, a, spacing: Spacing = Spacing()):
+        sp = spacing.c()
+        self._check(load_library().lrdmc_step(self.h, int(n_steps), float(a), ct.byref(sp)))
+        self.lattice_G = 1 if spacing.kind == SINGLE else 2
+
+    def energy_trace(self, max_n=1 << 20):
+        n = ct.c_int()
+        cap = max_n
+        e, w, j = np.zeros(cap), np.zeros(cap), np.zeros(cap)
+        self._check(load_library().lrdmc_get_energy_trace(self.h, _np_ptr(e), _np_ptr(w), _np_ptr(j), cap,
+                                                          ct.byref(n)))
+        k = n.value
+        return e[:k].copy(), w[:k].copy(), j[:k].copy()
+
+    def walkers(self):
+        W, N = self.W, self.N
+        P = 6 * N * (self.lattice_G or 1)
+        x = np.zeros((W, N, 3))
+        el, b = np.zeros(W), np.zeros(W)
+        T = np.zeros((W, P))
+        logw, jumps, parent = np.zeros(W), np.zeros(W, np.int32), np.zeros(W, np.int32)
+        self._check(load_library().lrdmc_get_walkers(self.h, _np_ptr(x), _np_ptr(el), _np_ptr(b),
+                                                     _np_ptr(T) if self.lattice_G else None,
+                                                     _np_ptr(logw), _np_ptr(jumps), _np_ptr(parent)))
+        return dict(x=x, EL=el, b=b, T=T, logw_pre=logw, jumps_pre=jumps, parent=parent)
+
+    def moves(self):
+        m = ct.c_longlong()
+        self._check(load_library().lrdmc_moves(self.h, ct.byref(m)))
+        return m.value
+
+    def save(self, path):
+        self._check(load_library().lrdmc_save(self.h, path.encode()))
+
+    def load(self, path):
+        self._check(load_library().lrdmc_load(self.h, path.encode()))
+
+    # ---------------------------------------------------------------- stateless
+    def evaluate(self, x, rot, a, spacing: Spacing = Spacing(), stream=None):
+        """One evaluation of every lattice move of n configurations.
+        x: [n][N][3] and rot: [n][9] float64 CUDA tensors. Returns CUDA tensors
+        ratio [n][P], T [n][P], b [n], el [n]."""
+        import torch
+
+        n = int(x.shape[0])
+        G = 1 if spacing.kind == SINGLE else 2
+        P = 6 * self.N * G
+        x = x.contiguous()
+        rot = rot.contiguous()
+        ratio = torch.empty((n, P), dtype=torch.float64, device=x.device)
+        T = torch.empty((n, P), dtype=torch.float64, device=x.device)
+        b = torch.empty(n, dtype=torch.float64, device=x.device)
+        el = torch.empty(n, dtype=torch.float64, device=x.device)
+        if stream is None:
+            stream = torch.cuda.current_stream(x.device)
+        sp = spacing.c()
+        self._check(load_library().lrdmc_evaluate(self.h, n, _t_ptr(x), _t_ptr(rot), float(a), ct.byref(sp),
+                                                  _t_ptr(ratio), _t_ptr(T), _t_ptr(b), _t_ptr(el),
+                                                  ct.c_void_p(stream.cuda_stream)))
+        return ratio, T, b, el
+
+
+def create_system(system) -> LrdmcSystem:
+    return LrdmcSystem(system)

@@ -1,0 +1,639 @@
+// C ABI of the LRDMC library (declared in include/lrdmc.h): argument
+// checks, the host-side double-grid parameters (S-13, Eq. 4, 6, 7), the
+// device workspace layout and the launch sequence of one projection step.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "lrdmc_internal.h"
+
+using namespace lrdmc;
+
+struct lrdmc_system_s {
+  SysDev S;
+  Layout Lo;
+  double Zmax;
+  int iZmax;
+  // population
+  int W = 0;
+  int trace_cap = 0;
+  uint64_t seed = 0;
+  double tau = 0.0, e_trial = 0.0;
+  int recompute_every = 0;
+  cudaStream_t stream = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  double* rec[2] = {nullptr, nullptr};
+  int cur = 0;
+  PopDev P;
+  uint64_t k = 0;
+  bool have_pop = false;
+  bool have_eval = false;
+  LatDev eval_lat;
+  int* err_host = nullptr;  // pinned
+  int* eval_err = nullptr;  // device error word of lrdmc_evaluate
+  std::string last_error;
+};
+
+static const char* g_static_error = "";
+
+static lrdmc_status fail(lrdmc_system_t s, lrdmc_status st, const std::string& msg)
+{
+  if (s) s->last_error = msg;
+  else g_static_error = "invalid system handle";
+  return st;
+}
+
+static lrdmc_status cuda_fail(lrdmc_system_t s, cudaError_t e, const char* where)
+{
+  return fail(s, LRDMC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// ----------------------------------------------------------------------------
+// Double-grid parameters.
+// ----------------------------------------------------------------------------
+
+// S-13: r_c(a, Z) = beta (kappa alpha^-2 + 1) / (alpha^-2 + 1) Z^(-5/7),
+// alpha^-2 = (a Z)^2.
+static double rc_s13(double a, double Z, double beta, double kappa)
+{
+  const double aZ2 = (a * Z) * (a * Z);
+  return beta * (kappa * aZ2 + 1.0) / (aZ2 + 1.0) * pow(Z, -5.0 / 7.0);
+}
+
+// Slater's screening rules for a neutral atom: occupied subshells in
+// Madelung order, grouped as (ns,np) or (nd) or (nf); returns per group the
+// electron count, n* and the exponent (Z - s)/n*.
+struct SlaterGroup {
+  int n, kind, occ;  // kind 0 = s/p group, 2 = d, 3 = f
+  double nstar, zeta;
+};
+
+static std::vector<SlaterGroup> slater_groups(int Z)
+{
+  static const int order_n[] = {1, 2, 2, 3, 3, 4, 3, 4, 5, 4, 5, 6, 4, 5, 6, 7, 5, 6, 7};
+  static const int order_l[] = {0, 0, 1, 0, 1, 0, 2, 1, 0, 2, 1, 0, 3, 2, 1, 0, 3, 2, 1};
+  // group list in Slater's left-to-right order
+  std::vector<SlaterGroup> g;
+  auto rank = [](int n, int kind) {  // position in Slater's ordering
+    return n * 10 + (kind == 0 ? 0 : kind);
+  };
+  int left = Z;
+  for (unsigned f = 0; f < sizeof(order_n) / sizeof(int) && left > 0; ++f) {
+    int cap = 4 * order_l[f] + 2, put = left < cap ? left : cap;
+    int kind = order_l[f] < 2 ? 0 : order_l[f];
+    bool found = false;
+    for (auto& q : g)
+      if (q.n == order_n[f] && q.kind == kind) { q.occ += put; found = true; }
+    if (!found) g.push_back({order_n[f], kind, put, 0.0, 0.0});
+    left -= put;
+  }
+  // sort by Slater's ordering
+  for (size_t i = 0; i < g.size(); ++i)
+    for (size_t j = i + 1; j < g.size(); ++j)
+      if (rank(g[j].n, g[j].kind) < rank(g[i].n, g[i].kind)) std::swap(g[i], g[j]);
+  static const double nstar_of[] = {0, 1.0, 2.0, 3.0, 3.7, 4.0, 4.2, 4.2};
+  for (size_t i = 0; i < g.size(); ++i) {
+    double s = (g[i].occ - 1) * (g[i].n == 1 ? 0.30 : 0.35);
+    for (size_t j = 0; j < g.size(); ++j) {
+      if (j == i) continue;
+      if (g[i].kind == 0) {
+        int dn = g[i].n - g[j].n;
+        if (dn == 1) s += 0.85 * g[j].occ;
+        else if (dn >= 2) s += 1.00 * g[j].occ;
+      } else if (j < i) {
+        s += 1.00 * g[j].occ;
+      }
+    }
+    g[i].nstar = nstar_of[g[i].n];
+    g[i].zeta = (Z - s) / g[i].nstar;
+  }
+  return g;
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] by Newton iteration on P_n.
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w)
+{
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double z = cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// Eq. 7: N_core(r_c) = int 4 pi r^2 rho_eff(r) exp(-r^2/(2 r_c^2)) dr with
+// rho_eff from Slater's effective orbitals (normalised r^(n*-1) e^(-zeta r)).
+// Composite 24-point Gauss-Legendre on 240 panels clustered towards r = 0.
+static double n_core(int Z, double rc)
+{
+  auto g = slater_groups(Z);
+  double zmin = 1e300;
+  for (auto& q : g) zmin = fmin(zmin, q.zeta);
+  std::vector<double> gx, gw;
+  gauss_legendre(24, gx, gw);
+  const double rmax = 90.0 / zmin;
+  const int panels = 240;
+  double total = 0.0;
+  for (int p = 0; p < panels; ++p) {
+    double t0 = (double)p / panels, t1 = (double)(p + 1) / panels;
+    double r0 = rmax * t0 * t0, r1 = rmax * t1 * t1;
+    double half = 0.5 * (r1 - r0), mid = 0.5 * (r1 + r0);
+    for (int i = 0; i < 24; ++i) {
+      double r = mid + half * gx[i];
+      double f = 0.0;
+      for (auto& q : g) {
+        double lognorm = (2.0 * q.nstar + 1.0) * log(2.0 * q.zeta) - lgamma(2.0 * q.nstar + 1.0);
+        f += q.occ * exp(lognorm + 2.0 * q.nstar * log(r) - 2.0 * q.zeta * r);
+      }
+      if (rc > 0.0 && isfinite(rc)) f *= exp(-r * r / (2.0 * rc * rc));
+      total += half * gw[i] * f;
+    }
+  }
+  return total;
+}
+
+static lrdmc_status lattice_from(lrdmc_system_t s, double a, const lrdmc_spacing_fn* sp, LatDev& L)
+{
+  if (!(a > 0.0) || !isfinite(a)) return fail(s, LRDMC_ERR_ARG, "lattice spacing a must be > 0");
+  if (!sp) return fail(s, LRDMC_ERR_ARG, "spacing function is NULL");
+  memset(&L, 0, sizeof(L));
+  L.a = a;
+  L.inv2a2 = 0.5 / (a * a);
+  double ratio = 1.0, rc = 0.0;
+  switch (sp->kind) {
+    case LRDMC_SINGLE:
+      L.G = 1;
+      L.ap = a;
+      L.inv2ap2 = L.inv2a2;
+      return LRDMC_OK;
+    case LRDMC_DOUBLE_THIS_WORK: {
+      if (!(sp->beta > 0.0) || !(sp->kappa > 0.0)) return fail(s, LRDMC_ERR_ARG, "beta and kappa must be > 0");
+      if (s->iZmax < 1 || fabs(s->Zmax - s->iZmax) > 1e-12)
+        return fail(s, LRDMC_ERR_ARG, "THIS_WORK needs an integer Z_max (Slater's rules)");
+      rc = rc_s13(a, s->Zmax, sp->beta, sp->kappa);
+      double nc = n_core(s->iZmax, rc);
+      ratio = sqrt((s->Zmax - nc) / nc);
+      L.pkind = 0;
+      break;
+    }
+    case LRDMC_DOUBLE_PREVIOUS:
+      rc = s->Zmax / 2.0;
+      ratio = sqrt(s->Zmax * s->Zmax / 4.0 + 1.0);
+      L.pkind = 1;
+      break;
+    case LRDMC_DOUBLE_EXPLICIT:
+      if (!(sp->rc > 0.0) || !(sp->aprime_over_a > 0.0)) return fail(s, LRDMC_ERR_ARG, "explicit r_c and a'/a must be > 0");
+      rc = sp->rc;
+      ratio = sp->aprime_over_a;
+      L.pkind = 0;
+      break;
+    default:
+      return fail(s, LRDMC_ERR_ARG, "unknown spacing kind");
+  }
+  if (!isfinite(ratio) || !(ratio > 0.0)) return fail(s, LRDMC_ERR_ARG, "a'/a is not finite and positive");
+  L.G = 2;
+  L.ap = a * ratio;
+  L.inv2ap2 = 0.5 / (L.ap * L.ap);
+  L.rc = rc;
+  L.p_coef = (L.pkind == 0) ? 1.0 / (2.0 * rc * rc) : rc * rc;
+  return LRDMC_OK;
+}
+
+static bool same_lattice(const LatDev& x, const LatDev& y)
+{
+  return x.a == y.a && x.ap == y.ap && x.G == y.G && x.pkind == y.pkind && x.rc == y.rc;
+}
+
+// ----------------------------------------------------------------------------
+// C ABI.
+// ----------------------------------------------------------------------------
+extern "C" {
+
+lrdmc_status lrdmc_create_system(int n_nuc, const double* nuc_xyz, const double* Z, int n_up,
+                                 int n_dn, const lrdmc_shell* shells, int n_shells,
+                                 const double* mo_coeff, int n_ao, int n_mo,
+                                 const lrdmc_jastrow* jas, lrdmc_system_t* out)
+{
+  if (!out) return LRDMC_ERR_ARG;
+  *out = nullptr;
+  if (n_nuc < 1 || n_nuc > kMaxNuc || !nuc_xyz || !Z || !shells || !mo_coeff || !jas) {
+    g_static_error = "create_system: bad nuclei or NULL input";
+    return LRDMC_ERR_ARG;
+  }
+  if (n_up < 1 || n_dn < 0 || n_dn > n_up || n_up > kMaxSpin || n_mo < n_up || n_mo > kMaxMO ||
+      n_ao < 1 || n_ao > kMaxAO || n_shells < 1 || n_shells > kMaxShell) {
+    g_static_error = "create_system: sizes beyond the limits of lrdmc.h";
+    return LRDMC_ERR_ARG;
+  }
+  lrdmc_system_t s = new lrdmc_system_s();
+  SysDev& S = s->S;
+  memset(&S, 0, sizeof(S));
+  S.n_nuc = n_nuc;
+  S.n_up = n_up;
+  S.n_dn = n_dn;
+  S.N = n_up + n_dn;
+  S.n_shell = n_shells;
+  S.n_ao = n_ao;
+  S.n_mo = n_mo;
+  S.ee_on = jas->ee_on ? 1 : 0;
+  double zmax = 0.0;
+  for (int I = 0; I < n_nuc; ++I) {
+    for (int d = 0; d < 3; ++d) S.nuc[I][d] = nuc_xyz[3 * I + d];
+    S.Z[I] = Z[I];
+    S.en_b1[I] = jas->en_b1[I];
+    zmax = fmax(zmax, Z[I]);
+  }
+  for (int I = 0; I < n_nuc; ++I) S.heavy[I] = (Z[I] == zmax) ? 1 : 0;
+  s->Zmax = zmax;
+  s->iZmax = (int)lround(zmax);
+  S.b_ee = jas->b_ee;
+  S.c_par = jas->c_par;
+  S.c_anti = jas->c_anti;
+  S.en_b2 = jas->en_b2;
+  double vnn = 0.0;
+  for (int I = 0; I < n_nuc; ++I)
+    for (int J = I + 1; J < n_nuc; ++J) {
+      double dx = S.nuc[I][0] - S.nuc[J][0], dy = S.nuc[I][1] - S.nuc[J][1], dz = S.nuc[I][2] - S.nuc[J][2];
+      vnn += Z[I] * Z[J] / sqrt(dx * dx + dy * dy + dz * dz);
+    }
+  S.V_nn = vnn;
+  int off = 0;
+  for (int q = 0; q < n_shells; ++q) {
+    const lrdmc_shell& in = shells[q];
+    ShellDev& sh = S.sh[q];
+    if (in.center < 0 || in.center >= n_nuc || in.l < 0 || in.l > 2 || (in.kind != 0 && in.kind != 1) ||
+        (in.kind == 1 && (in.n_prim < 1 || in.n_prim > kMaxPrim)) ||
+        (in.kind == 0 && !(in.zeta > 0.0)) || (in.kind == 0 && in.n_eff - 1.0 - in.l < 0.0)) {
+      delete s;
+      g_static_error = "create_system: invalid shell";
+      return LRDMC_ERR_ARG;
+    }
+    sh.center = in.center;
+    sh.l = in.l;
+    sh.kind = in.kind;
+    sh.n_prim = in.kind == 1 ? in.n_prim : 0;
+    sh.ao_offset = off;
+    sh.m = in.n_eff - 1.0 - in.l;
+    sh.zeta = in.zeta;
+    double mr = nearbyint(sh.m);
+    sh.m_int = (in.kind == 0 && fabs(sh.m - mr) == 0.0 && mr <= 8.0) ? (int)mr : -1;
+    for (int p = 0; p < kMaxPrim; ++p) {
+      sh.alpha[p] = in.alpha[p];
+      sh.coef[p] = in.coef[p];
+    }
+    sh.same_exp = (q > 0 && in.kind == 0 && shells[q - 1].kind == 0 && shells[q - 1].center == in.center &&
+                   shells[q - 1].zeta == in.zeta) ? 1 : 0;
+    off += 2 * in.l + 1;
+  }
+  if (off != n_ao) {
+    delete s;
+    g_static_error = "create_system: n_ao differs from the shells' 2l+1 count";
+    return LRDMC_ERR_ARG;
+  }
+  for (int j = 0; j < n_ao * n_mo; ++j) S.C[j] = mo_coeff[j];
+  s->Lo = make_layout(S);
+  *out = s;
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_spacing_params(lrdmc_system_t s, double a, const lrdmc_spacing_fn* sp,
+                                  double* aprime_over_a, double* rc)
+{
+  if (!s) return fail(s, LRDMC_ERR_ARG, "");
+  LatDev L;
+  lrdmc_status st = lattice_from(s, a, sp, L);
+  if (st != LRDMC_OK) return st;
+  if (aprime_over_a) *aprime_over_a = (L.G == 2) ? L.ap / a : 1.0;
+  if (rc) *rc = L.rc;
+  return LRDMC_OK;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct WsPlan {
+  size_t rec, parent, logw, el, jumps, cum, trace, moves, err, counter, total;
+};
+
+static WsPlan plan_ws(const Layout& Lo, int W, int cap)
+{
+  WsPlan p;
+  size_t o = 0;
+  p.rec = o; o += align256(sizeof(double) * (size_t)W * Lo.rec) * 2;
+  p.parent = o; o += align256(sizeof(int) * (size_t)W);
+  p.logw = o; o += align256(sizeof(double) * (size_t)W);
+  p.el = o; o += align256(sizeof(double) * (size_t)W);
+  p.jumps = o; o += align256(sizeof(int) * (size_t)W);
+  p.cum = o; o += align256(sizeof(double) * (size_t)W);
+  p.trace = o; o += align256(sizeof(double) * 3 * (size_t)cap);
+  p.moves = o; o += 256;
+  p.err = o; o += 256;
+  p.counter = o; o += 256;
+  p.total = o;
+  return p;
+}
+
+lrdmc_status lrdmc_workspace_bytes(lrdmc_system_t s, int n_walkers, int cap, size_t* bytes)
+{
+  if (!s) return fail(s, LRDMC_ERR_ARG, "");
+  if (n_walkers < 1 || cap < 1 || !bytes) return fail(s, LRDMC_ERR_ARG, "workspace_bytes: bad sizes");
+  *bytes = plan_ws(s->Lo, n_walkers, cap).total;
+  return LRDMC_OK;
+}
+
+static lrdmc_status read_error_word(lrdmc_system_t s)
+{
+  cudaError_t e = cudaMemcpyAsync(s->err_host, s->P.err, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "error word read");
+  e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "stream synchronize");
+  int w = *s->err_host;
+  if (w & kErrSingular) return fail(s, LRDMC_ERR_SINGULAR, "singular Slater matrix or zero update ratio");
+  if (w & kErrNonFinite) return fail(s, LRDMC_ERR_NONFINITE, "non-finite local energy or rate");
+  if (w & kErrIters) return fail(s, LRDMC_ERR_TIMEOUT, "an interval exceeded its iteration limit");
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_init_walkers(lrdmc_system_t s, int W, const double* x0, uint64_t seed, double tau,
+                                double e_trial, int recompute_every, int cap, void* workspace,
+                                size_t ws_bytes, void* stream)
+{
+  if (!s) return fail(s, LRDMC_ERR_ARG, "");
+  if (W < 1 || cap < 1 || !x0 || !workspace) return fail(s, LRDMC_ERR_ARG, "init_walkers: bad arguments");
+  if (!(tau > 0.0) || !isfinite(tau) || !isfinite(e_trial) || recompute_every < 0)
+    return fail(s, LRDMC_ERR_ARG, "init_walkers: tau must be > 0, recompute_every >= 0");
+  if (((uintptr_t)workspace & 255) != 0) return fail(s, LRDMC_ERR_ARG, "init_walkers: workspace not 256-byte aligned");
+  WsPlan p = plan_ws(s->Lo, W, cap);
+  if (ws_bytes < p.total) return fail(s, LRDMC_ERR_ARG, "init_walkers: workspace too small");
+  if (!s->err_host) {
+    cudaError_t e = cudaMallocHost((void**)&s->err_host, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(s, e, "pinned error word");
+  }
+  s->W = W;
+  s->trace_cap = cap;
+  s->seed = seed;
+  s->tau = tau;
+  s->e_trial = e_trial;
+  s->recompute_every = recompute_every;
+  s->stream = (cudaStream_t)stream;
+  s->ws = (char*)workspace;
+  s->ws_bytes = ws_bytes;
+  size_t recb = align256(sizeof(double) * (size_t)W * s->Lo.rec);
+  s->rec[0] = (double*)(s->ws + p.rec);
+  s->rec[1] = (double*)(s->ws + p.rec + recb);
+  s->cur = 0;
+  PopDev& P = s->P;
+  P.parent = (int*)(s->ws + p.parent);
+  P.logw = (double*)(s->ws + p.logw);
+  P.el_end = (double*)(s->ws + p.el);
+  P.jumps = (int*)(s->ws + p.jumps);
+  P.cum = (double*)(s->ws + p.cum);
+  P.trace = (double*)(s->ws + p.trace);
+  P.moves = (unsigned long long*)(s->ws + p.moves);
+  P.err = (int*)(s->ws + p.err);
+  P.counter = (int*)(s->ws + p.counter);
+  P.W = W;
+  P.trace_cap = cap;
+  P.seed = seed;
+  P.tau = tau;
+  P.e_trial = e_trial;
+  cudaError_t e = cudaMemsetAsync(s->ws + p.moves, 0, 3 * 256, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "workspace clear");
+  e = cudaMemsetAsync(P.logw, 0, sizeof(double) * W, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P.jumps, 0, sizeof(int) * W, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "workspace clear");
+  // stage x0 (host or device memory) in the second record buffer
+  double* stage = s->rec[1];
+  e = cudaMemcpyAsync(stage, x0, sizeof(double) * (size_t)W * 3 * s->S.N, cudaMemcpyDefault, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "x0 copy");
+  P.rec_src = s->rec[0];
+  P.rec_dst = s->rec[1];
+  e = launch_init(s->S, s->Lo, P, stage, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "k_init launch");
+  s->k = 0;
+  s->have_pop = true;
+  s->have_eval = false;
+  return read_error_word(s);
+}
+
+lrdmc_status lrdmc_step(lrdmc_system_t s, int n_steps, double a, const lrdmc_spacing_fn* sp)
+{
+  if (!s) return fail(s, LRDMC_ERR_ARG, "");
+  if (!s->have_pop) return fail(s, LRDMC_ERR_STATE, "step before init_walkers");
+  if (n_steps < 0) return fail(s, LRDMC_ERR_ARG, "n_steps < 0");
+  if (s->k + (uint64_t)n_steps > (uint64_t)s->trace_cap)
+    return fail(s, LRDMC_ERR_ARG, "step: the trace would exceed trace_capacity");
+  LatDev L;
+  lrdmc_status st = lattice_from(s, a, sp, L);
+  if (st != LRDMC_OK) return st;
+  cudaError_t e;
+  PopDev P = s->P;
+  if (!s->have_eval || !same_lattice(L, s->eval_lat)) {
+    P.rec_src = s->rec[s->cur];
+    P.rec_dst = s->rec[1 - s->cur];
+    e = launch_eval_all(s->S, s->Lo, L, P, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "k_eval_all launch");
+    s->have_eval = true;
+    s->eval_lat = L;
+  }
+  for (int n = 0; n < n_steps; ++n) {
+    const uint64_t k = s->k;
+    const int recompute = (k > 0 && s->recompute_every > 0 && k % (uint64_t)s->recompute_every == 0) ? 1 : 0;
+    P.rec_src = s->rec[s->cur];
+    P.rec_dst = s->rec[1 - s->cur];
+    e = launch_interval(s->S, s->Lo, L, P, k, recompute, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "k_interval launch");
+    e = launch_reconfig(P, k, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "k_reconfig launch");
+    s->cur = 1 - s->cur;
+    s->k++;
+  }
+  return read_error_word(s);
+}
+
+lrdmc_status lrdmc_get_energy_trace(lrdmc_system_t s, double* e_out, double* w_out, double* j_out,
+                                    int max_n, int* n_written)
+{
+  if (!s) return fail(s, LRDMC_ERR_ARG, "");
+  if (!s->have_pop) return fail(s, LRDMC_ERR_STATE, "trace before init_walkers");
+  int n = (int)((uint64_t)max_n < s->k ? (uint64_t)max_n : s->k);
+  if (n < 0) n = 0;
+  double* outs[3] = {e_out, w_out, j_out};
+  for (int r = 0; r < 3; ++r) {
+    if (!outs[r] || n == 0) continue;
+    cudaError_t e = cudaMemcpyAsync(outs[r], s->P.trace + (size_t)r * s->trace_cap, sizeof(double) * n,
+                                    cudaMemcpyDeviceToHost, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "trace copy");
+  }
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "stream synchronize");
+  if (n_written) *n_written = n;
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_get_walkers(lrdmc_system_t s, double* x, double* el, double* b, double* T,
+                               double* logw_pre, int* jumps_pre, int* parent)
+{
+  if (!s) return fail(s, LRDMC_ERR_ARG, "");
+  if (!s->have_pop) return fail(s, LRDMC_ERR_STATE, "get_walkers before init_walkers");
+  const int W = s->W;
+  const Layout& Lo = s->Lo;
+  std::vector<double> rec((size_t)W * Lo.rec);
+  std::vector<int> par(W);
+  cudaError_t e = cudaMemcpyAsync(rec.data(), s->rec[s->cur], sizeof(double) * rec.size(),
+                                  cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(par.data(), s->P.parent, sizeof(int) * W, cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess && logw_pre)
+    e = cudaMemcpyAsync(logw_pre, s->P.logw, sizeof(double) * W, cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess && jumps_pre)
+    e = cudaMemcpyAsync(jumps_pre, s->P.jumps, sizeof(int) * W, cudaMemcpyDeviceToHost, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "walker copy");
+  e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "stream synchronize");
+  const int P = s->have_eval ? s->S.N * 6 * s->eval_lat.G : 0;
+  for (int t = 0; t < W; ++t) {
+    const double* r = &rec[(size_t)par[t] * Lo.rec];
+    if (x) memcpy(&x[(size_t)t * 3 * Lo.N], r + Lo.off_x, sizeof(double) * 3 * Lo.N);
+    if (el) el[t] = r[Lo.off_el];
+    if (b) b[t] = r[Lo.off_b];
+    if (T && P) memcpy(&T[(size_t)t * P], r + Lo.off_T, sizeof(double) * P);
+  }
+  if (parent) memcpy(parent, par.data(), sizeof(int) * W);
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_moves(lrdmc_system_t s, long long* moves)
+{
+  if (!s || !moves) return fail(s, LRDMC_ERR_ARG, "moves: NULL");
+  if (!s->have_pop) return fail(s, LRDMC_ERR_STATE, "moves before init_walkers");
+  unsigned long long m = 0;
+  cudaError_t e = cudaMemcpyAsync(&m, s->P.moves, sizeof(m), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "moves copy");
+  *moves = (long long)m;
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_evaluate(lrdmc_system_t s, int n, const double* x, const double* rot, double a,
+                            const lrdmc_spacing_fn* sp, double* ratio, double* T, double* b,
+                            double* el, void* stream)
+{
+  if (!s) return fail(s, LRDMC_ERR_ARG, "");
+  if (n < 0 || (n > 0 && (!x || !rot))) return fail(s, LRDMC_ERR_ARG, "evaluate: bad arguments");
+  if (n == 0) return LRDMC_OK;
+  LatDev L;
+  lrdmc_status st = lattice_from(s, a, sp, L);
+  if (st != LRDMC_OK) return st;
+  cudaStream_t cs = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (!s->eval_err) e = cudaMalloc((void**)&s->eval_err, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(s, e, "evaluate error word");
+  if (!s->err_host) e = cudaMallocHost((void**)&s->err_host, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(s, e, "pinned error word");
+  e = cudaMemsetAsync(s->eval_err, 0, sizeof(int), cs);
+  if (e == cudaSuccess) e = launch_evaluate(s->S, s->Lo, L, n, x, rot, ratio, T, b, el, s->eval_err, cs);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->err_host, s->eval_err, sizeof(int), cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  if (e != cudaSuccess) return cuda_fail(s, e, "evaluate");
+  int h = *s->err_host;
+  if (h & kErrSingular) return fail(s, LRDMC_ERR_SINGULAR, "evaluate: singular Slater matrix");
+  return LRDMC_OK;
+}
+
+// Checkpoint file: magic, sizes, counters, then the current record buffer,
+// parents, trace and the moves counter.
+static const uint64_t kMagic = 0x4C52444D43303031ull;  // "LRDMC001"
+
+lrdmc_status lrdmc_save(lrdmc_system_t s, const char* path)
+{
+  if (!s || !path) return fail(s, LRDMC_ERR_ARG, "save: NULL");
+  if (!s->have_pop) return fail(s, LRDMC_ERR_STATE, "save before init_walkers");
+  const int W = s->W;
+  std::vector<double> rec((size_t)W * s->Lo.rec), trace(3 * (size_t)s->trace_cap);
+  std::vector<int> par(W);
+  unsigned long long moves = 0;
+  cudaError_t e = cudaMemcpyAsync(rec.data(), s->rec[s->cur], sizeof(double) * rec.size(), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(par.data(), s->P.parent, sizeof(int) * W, cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(trace.data(), s->P.trace, sizeof(double) * trace.size(), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&moves, s->P.moves, sizeof(moves), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "save copy");
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(s, LRDMC_ERR_ARG, std::string("save: cannot open ") + path);
+  int64_t hdr[8] = {(int64_t)kMagic, W, s->Lo.rec, s->trace_cap, (int64_t)s->k, s->have_eval ? 1 : 0, 0, 0};
+  bool ok = fwrite(hdr, sizeof(hdr), 1, f) == 1 && fwrite(&s->eval_lat, sizeof(LatDev), 1, f) == 1 &&
+            fwrite(rec.data(), sizeof(double), rec.size(), f) == rec.size() &&
+            fwrite(par.data(), sizeof(int), W, f) == (size_t)W &&
+            fwrite(trace.data(), sizeof(double), trace.size(), f) == trace.size() &&
+            fwrite(&moves, sizeof(moves), 1, f) == 1;
+  fclose(f);
+  return ok ? LRDMC_OK : fail(s, LRDMC_ERR_ARG, "save: write failed");
+}
+
+lrdmc_status lrdmc_load(lrdmc_system_t s, const char* path)
+{
+  if (!s || !path) return fail(s, LRDMC_ERR_ARG, "load: NULL");
+  if (!s->have_pop) return fail(s, LRDMC_ERR_STATE, "load needs an initialised population of the same size");
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(s, LRDMC_ERR_ARG, std::string("load: cannot open ") + path);
+  int64_t hdr[8];
+  LatDev L;
+  bool ok = fread(hdr, sizeof(hdr), 1, f) == 1 && fread(&L, sizeof(LatDev), 1, f) == 1;
+  if (!ok || hdr[0] != (int64_t)kMagic || hdr[1] != s->W || hdr[2] != s->Lo.rec || hdr[3] != s->trace_cap) {
+    fclose(f);
+    return fail(s, LRDMC_ERR_ARG, "load: file does not match this population");
+  }
+  const int W = s->W;
+  std::vector<double> rec((size_t)W * s->Lo.rec), trace(3 * (size_t)s->trace_cap);
+  std::vector<int> par(W);
+  unsigned long long moves = 0;
+  ok = fread(rec.data(), sizeof(double), rec.size(), f) == rec.size() &&
+       fread(par.data(), sizeof(int), W, f) == (size_t)W &&
+       fread(trace.data(), sizeof(double), trace.size(), f) == trace.size() &&
+       fread(&moves, sizeof(moves), 1, f) == 1;
+  fclose(f);
+  if (!ok) return fail(s, LRDMC_ERR_ARG, "load: truncated file");
+  for (int t = 0; t < W; ++t)
+    if (par[t] < 0 || par[t] >= W) return fail(s, LRDMC_ERR_ARG, "load: corrupt parent index");
+  s->cur = 0;
+  cudaError_t e = cudaMemcpyAsync(s->rec[0], rec.data(), sizeof(double) * rec.size(), cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->P.parent, par.data(), sizeof(int) * W, cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->P.trace, trace.data(), sizeof(double) * trace.size(), cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->P.moves, &moves, sizeof(moves), cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "load copy");
+  s->k = (uint64_t)hdr[4];
+  s->have_eval = hdr[5] != 0;
+  s->eval_lat = L;
+  return LRDMC_OK;
+}
+
+const char* lrdmc_last_error(lrdmc_system_t s) { return s ? s->last_error.c_str() : g_static_error; }
+
+void lrdmc_destroy(lrdmc_system_t s)
+{
+  if (!s) return;
+  if (s->err_host) cudaFreeHost(s->err_host);
+  if (s->eval_err) cudaFree(s->eval_err);
+  delete s;
+}
+
+}  // extern "C"

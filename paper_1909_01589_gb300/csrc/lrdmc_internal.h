@@ -1,0 +1,110 @@
+// Internal interface between the C-ABI host code (lrdmc_api.cu) and the
+// CUDA kernels (lrdmc_kernels.cu). Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lrdmc.h"
+
+namespace lrdmc {
+
+constexpr int kMaxNuc = LRDMC_MAX_NUC;
+constexpr int kMaxShell = LRDMC_MAX_SHELL;
+constexpr int kMaxPrim = LRDMC_MAX_PRIM;
+constexpr int kMaxAO = LRDMC_MAX_AO;
+constexpr int kMaxSpin = LRDMC_MAX_SPIN;
+constexpr int kMaxMO = LRDMC_MAX_SPIN;
+constexpr int kWarpsPerBlock = 4;
+constexpr int kMaxItersPerInterval = 1 << 20;
+
+// Error bits of the device error word.
+constexpr int kErrSingular = 1;
+constexpr int kErrNonFinite = 2;
+constexpr int kErrIters = 4;
+
+// Philox counter tags.
+constexpr uint64_t kTagTimeHB = 0;
+constexpr uint64_t kTagRot = 1;
+constexpr uint64_t kTagComb = 2;
+constexpr uint64_t kSlotGlobal = 0xFFFFFFFFFFFFFFFFull;
+constexpr uint64_t kIntervalInit = 0xFFFFFFFFFFFFFFFFull;
+
+struct ShellDev {
+  int center, l, kind, n_prim;
+  int ao_offset;
+  int m_int;       // Slater power r^m as an integer (>= 0), or -1 for pow()
+  int same_exp;    // 1: same centre and Slater exponent as the previous shell
+  int pad;
+  double m;        // n_eff - 1 - l
+  double zeta;
+  double alpha[kMaxPrim];
+  double coef[kMaxPrim];
+};
+
+// Trial function and Hamiltonian constants, passed by value as a kernel
+// parameter (__grid_constant__); the MO coefficients are staged in shared
+// memory by every block.
+struct SysDev {
+  int n_nuc, n_up, n_dn, N;
+  int n_shell, n_ao, n_mo, ee_on;
+  double nuc[kMaxNuc][3];
+  double Z[kMaxNuc];
+  double en_b1[kMaxNuc];
+  int heavy[kMaxNuc];  // 1 for the nuclei with Z = Z_max (centres of p)
+  double b_ee, c_par, c_anti, en_b2;
+  double V_nn;
+  ShellDev sh[kMaxShell];
+  double C[kMaxAO * kMaxMO];  // [n_ao][n_mo]
+};
+
+struct LatDev {
+  double a, ap;     // spacings a and a'
+  double inv2a2;    // 1 / (2 a^2)
+  double inv2ap2;   // 1 / (2 a'^2)
+  double rc;        // r_c (Gaussian: length, Pade: inverse length)
+  double p_coef;    // Gaussian: 1/(2 r_c^2); Pade: r_c^2
+  int G;            // 1 single grid, 2 double grid
+  int pkind;        // 0 Gaussian (Eq. 3), 1 Pade (Eq. 2)
+};
+
+// Walker record layout (doubles) in the double-buffered population.
+struct Layout {
+  int N, nu, nd, P_max;
+  int off_x, off_au, off_ad, off_R, off_T, off_b, off_el;
+  int rec;  // doubles per record (multiple of 4)
+  int smem_warp;  // doubles of shared memory per warp
+  int smem_block_bytes;
+};
+
+Layout make_layout(const SysDev& S);
+
+struct PopDev {
+  double* rec_src;
+  double* rec_dst;
+  int* parent;
+  double* logw;
+  double* el_end;
+  int* jumps;
+  double* cum;
+  double* trace;  // [3][cap]
+  unsigned long long* moves;
+  int* err;
+  int* counter;
+  int W;
+  int trace_cap;
+  uint64_t seed;
+  double tau, e_trial;
+};
+
+cudaError_t launch_init(const SysDev& S, const Layout& Lo, const PopDev& P, const double* x0,
+                        cudaStream_t st);
+cudaError_t launch_eval_all(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P,
+                            cudaStream_t st);
+cudaError_t launch_interval(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P,
+                            uint64_t k, int recompute, cudaStream_t st);
+cudaError_t launch_reconfig(const PopDev& P, uint64_t k, cudaStream_t st);
+cudaError_t launch_evaluate(const SysDev& S, const Layout& Lo, const LatDev& L, int n,
+                            const double* x, const double* rot, double* ratio, double* T,
+                            double* b, double* el, int* err, cudaStream_t st);
+
+}  // namespace lrdmc

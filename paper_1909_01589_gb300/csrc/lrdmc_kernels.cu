@@ -1,0 +1,891 @@
+// CUDA kernels (sm_103a, FP64) of the LRDMC hot path.
+//
+// One warp owns one walker at a time. Shared memory holds the walker's
+// positions, inverse Slater matrices, lattice rotation, the P jump rates of
+// its cached evaluation and per-electron work vectors; the MO coefficients
+// are staged once per block. The lanes split the P lattice moves of an
+// evaluation, the electrons of the local energy, the orbitals and matrix
+// entries of the Sherman-Morrison update, and the rows of the Gauss-Jordan
+// inverse. Kernels:
+//   k_init      start configurations -> inverses, first rotation
+//   k_eval_all  evaluate every walker (after a change of lattice)
+//   k_interval  one interval tau of continuous-time projection per walker,
+//               walkers fetched dynamically by the warps (ragged jump counts)
+//   k_reconfig  weights, trace entry and comb parents (one block)
+//   k_evaluate  stateless evaluation of given configurations
+// The population is double-buffered: k_interval gathers the record of
+// parent[s] from the source buffer, so reconfiguration needs no copy pass.
+#include <math.h>
+#include <stdint.h>
+
+#include "lrdmc_internal.h"
+
+namespace lrdmc {
+
+#define FULL_MASK 0xffffffffu
+
+// ----------------------------------------------------------------------------
+// Counter-based random numbers: Philox4x64-10 (Salmon, Moraes, Dror, Shaw,
+// SC'11), key (seed, 0), counter (slot, interval, iteration, tag).
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1)
+{
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint64_t hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
+    uint64_t hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
+    uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    k0 += 0x9E3779B97F4A7C15ull;
+    k1 += 0xBB67AE8584CAA73Bull;
+  }
+}
+
+__device__ __forceinline__ double to_u01(uint64_t bits)
+{
+  return ((double)(bits >> 12) + 0.5) * 0x1.0p-52;
+}
+
+__device__ __forceinline__ void draw_uniforms(uint64_t seed, uint64_t slot, uint64_t k, uint64_t m,
+                                              uint64_t tag, double u[4])
+{
+  uint64_t c[4] = {slot, k, m, tag};
+  philox4x64_10(c, seed, 0ull);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) u[j] = to_u01(c[j]);
+}
+
+// Uniformly random rotation (Shoemake's unit quaternion from three uniforms).
+__device__ void rotation_matrix(double u1, double u2, double u3, double* R)
+{
+  double s1 = sqrt(1.0 - u1), s2 = sqrt(u1);
+  double sa, ca, sb, cb;
+  sincospi(2.0 * u2, &sa, &ca);
+  sincospi(2.0 * u3, &sb, &cb);
+  double x = s1 * sa, y = s1 * ca, z = s2 * sb, w = s2 * cb;
+  R[0] = 1.0 - 2.0 * (y * y + z * z); R[1] = 2.0 * (x * y - z * w);       R[2] = 2.0 * (x * z + y * w);
+  R[3] = 2.0 * (x * y + z * w);       R[4] = 1.0 - 2.0 * (x * x + z * z); R[5] = 2.0 * (y * z - x * w);
+  R[6] = 2.0 * (x * z - y * w);       R[7] = 2.0 * (y * z + x * w);       R[8] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+// ----------------------------------------------------------------------------
+// Warp helpers.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+  return v;
+}
+
+// Chunked inclusive scan of T[0..P): chunks of 32 in order, a Hillis-Steele
+// scan inside each chunk plus the running total of the previous chunks.
+// Returns the total (identical in every lane). When pick != nullptr, *pick
+// receives the smallest c with target < C_c (or -1), and *last the largest c
+// with T_c > 0 (or -1).
+__device__ double warp_scan(const double* T, int P, int lane, double target, int* pick, int* last)
+{
+  double carry = 0.0;
+  int p = -1, lp = -1;
+  for (int base = 0; base < P; base += 32) {
+    int c = base + lane;
+    double t = (c < P) ? T[c] : 0.0;
+    double v = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      double y = __shfl_up_sync(FULL_MASK, v, o);
+      if (lane >= o) v += y;
+    }
+    double C = carry + v;
+    if (pick) {
+      unsigned hit = __ballot_sync(FULL_MASK, (c < P) && (target < C));
+      if (p < 0 && hit) p = base + __ffs(hit) - 1;
+      unsigned pos = __ballot_sync(FULL_MASK, (c < P) && (t > 0.0));
+      if (pos) lp = base + 31 - __clz(pos);
+    }
+    carry = __shfl_sync(FULL_MASK, C, 31);
+  }
+  if (pick) { *pick = p; *last = lp; }
+  return carry;
+}
+
+// ----------------------------------------------------------------------------
+// Atomic orbitals: chi = S(d) R(|d|), d = r - R_centre, S a real solid
+// harmonic of degree l, R Slater r^m exp(-zeta r) or a Gaussian contraction.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ double int_pow(double r, int m)
+{
+  double p = 1.0;
+  for (int j = 0; j < m; ++j) p *= r;
+  return p;
+}
+
+// Radial value R, R'/r and R''. e is exp(-zeta r) for Slater shells.
+__device__ __forceinline__ void radial(const ShellDev& sh, double r, double e, double& R, double& R1,
+                                       double& R2, bool der)
+{
+  if (sh.kind == 0) {
+    double pw = (sh.m_int >= 0) ? int_pow(r, sh.m_int) : pow(r, sh.m);
+    R = pw * e;
+    if (der) {
+      double t = sh.m / r - sh.zeta;
+      R1 = t * R / r;
+      R2 = (t * t - sh.m / (r * r)) * R;
+    }
+  } else {
+    double r2 = r * r;
+    R = 0.0; R1 = 0.0; R2 = 0.0;
+    for (int p = 0; p < sh.n_prim; ++p) {
+      double al = sh.alpha[p];
+      double g = sh.coef[p] * exp(-al * r2);
+      R += g;
+      if (der) {
+        R1 += -2.0 * al * g;
+        R2 += (4.0 * al * al * r2 - 2.0 * al) * g;
+      }
+    }
+  }
+}
+
+// Solid harmonics of degree l at d and their gradients.
+__device__ __forceinline__ int solid(int l, const double d[3], double S[5], double gS[5][3], bool der)
+{
+  if (l == 0) {
+    S[0] = 1.0;
+    if (der) { gS[0][0] = gS[0][1] = gS[0][2] = 0.0; }
+    return 1;
+  }
+  if (l == 1) {
+    S[0] = d[0]; S[1] = d[1]; S[2] = d[2];
+    if (der) {
+#pragma unroll
+      for (int f = 0; f < 3; ++f)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gS[f][k] = (f == k) ? 1.0 : 0.0;
+    }
+    return 3;
+  }
+  S[0] = d[0] * d[1];
+  S[1] = d[1] * d[2];
+  S[2] = d[2] * d[0];
+  S[3] = d[0] * d[0] - d[1] * d[1];
+  S[4] = 2.0 * d[2] * d[2] - d[0] * d[0] - d[1] * d[1];
+  if (der) {
+    gS[0][0] = d[1];        gS[0][1] = d[0];        gS[0][2] = 0.0;
+    gS[1][0] = 0.0;         gS[1][1] = d[2];        gS[1][2] = d[1];
+    gS[2][0] = d[2];        gS[2][1] = 0.0;         gS[2][2] = d[0];
+    gS[3][0] = 2.0 * d[0];  gS[3][1] = -2.0 * d[1]; gS[3][2] = 0.0;
+    gS[4][0] = -2.0 * d[0]; gS[4][1] = -2.0 * d[1]; gS[4][2] = 4.0 * d[2];
+  }
+  return 5;
+}
+
+// Sum_mu v[mu] chi_mu(p): the determinant ratio when v is the projected
+// inverse column of the moving electron.
+__device__ double ao_dot(const SysDev& S, const double* v, double px, double py, double pz)
+{
+  double acc = 0.0;
+  int prev_c = -1;
+  double d[3] = {0, 0, 0}, r = 0.0, e = 0.0;
+  for (int q = 0; q < S.n_shell; ++q) {
+    const ShellDev& sh = S.sh[q];
+    if (sh.center != prev_c) {
+      prev_c = sh.center;
+      d[0] = px - S.nuc[prev_c][0];
+      d[1] = py - S.nuc[prev_c][1];
+      d[2] = pz - S.nuc[prev_c][2];
+      r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    }
+    if (sh.kind == 0 && !sh.same_exp) e = exp(-sh.zeta * r);
+    double R, R1, R2, Sv[5], gS[5][3];
+    radial(sh, r, e, R, R1, R2, false);
+    int nf = solid(sh.l, d, Sv, gS, false);
+    double part = 0.0;
+    for (int f = 0; f < nf; ++f) part += v[sh.ao_offset + f] * Sv[f];
+    acc += part * R;
+  }
+  return acc;
+}
+
+// Sum_mu v[mu] chi_mu, grad chi_mu, lap chi_mu at p.
+__device__ void ao_dot_der(const SysDev& S, const double* v, const double* p, double& val,
+                           double g[3], double& lap)
+{
+  val = 0.0; g[0] = g[1] = g[2] = 0.0; lap = 0.0;
+  int prev_c = -1;
+  double d[3] = {0, 0, 0}, r = 0.0, e = 0.0;
+  for (int q = 0; q < S.n_shell; ++q) {
+    const ShellDev& sh = S.sh[q];
+    if (sh.center != prev_c) {
+      prev_c = sh.center;
+      d[0] = p[0] - S.nuc[prev_c][0];
+      d[1] = p[1] - S.nuc[prev_c][1];
+      d[2] = p[2] - S.nuc[prev_c][2];
+      r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    }
+    if (sh.kind == 0 && !sh.same_exp) e = exp(-sh.zeta * r);
+    double R, R1, R2, Sv[5], gS[5][3];
+    radial(sh, r, e, R, R1, R2, true);
+    int nf = solid(sh.l, d, Sv, gS, true);
+    double radlap = R2 + 2.0 * (sh.l + 1) * R1;
+    for (int f = 0; f < nf; ++f) {
+      double c = v[sh.ao_offset + f];
+      val += c * Sv[f] * R;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) g[k] += c * (R * gS[f][k] + Sv[f] * R1 * d[k]);
+      lap += c * Sv[f] * radlap;
+    }
+  }
+}
+
+// chi_mu(p) for all AOs into out[n_ao].
+__device__ void ao_values(const SysDev& S, const double* p, double* out)
+{
+  int prev_c = -1;
+  double d[3] = {0, 0, 0}, r = 0.0, e = 0.0;
+  for (int q = 0; q < S.n_shell; ++q) {
+    const ShellDev& sh = S.sh[q];
+    if (sh.center != prev_c) {
+      prev_c = sh.center;
+      d[0] = p[0] - S.nuc[prev_c][0];
+      d[1] = p[1] - S.nuc[prev_c][1];
+      d[2] = p[2] - S.nuc[prev_c][2];
+      r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    }
+    if (sh.kind == 0 && !sh.same_exp) e = exp(-sh.zeta * r);
+    double R, R1, R2, Sv[5], gS[5][3];
+    radial(sh, r, e, R, R1, R2, false);
+    int nf = solid(sh.l, d, Sv, gS, false);
+    for (int f = 0; f < nf; ++f) out[sh.ao_offset + f] = Sv[f] * R;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Jastrow factor.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ int spin_of(const SysDev& S, int i) { return i < S.n_up ? 0 : 1; }
+
+// sum_{j != i} u_ee(|p - r_j|) + sum_I u_en(|p - R_I|).
+__device__ double jastrow_terms(const SysDev& S, const double* sx, int i, double px, double py,
+                                double pz)
+{
+  double acc = 0.0;
+  const int si = spin_of(S, i);
+  for (int j = 0; j < S.N; ++j) {
+    if (j == i) continue;
+    double dx = px - sx[3 * j], dy = py - sx[3 * j + 1], dz = pz - sx[3 * j + 2];
+    double r = sqrt(dx * dx + dy * dy + dz * dz);
+    double c = (spin_of(S, j) == si) ? S.c_par : S.c_anti;
+    acc += c * r / (1.0 + S.b_ee * r);
+  }
+  for (int I = 0; I < S.n_nuc; ++I) {
+    double dx = px - S.nuc[I][0], dy = py - S.nuc[I][1], dz = pz - S.nuc[I][2];
+    double r = sqrt(dx * dx + dy * dy + dz * dz);
+    acc -= S.en_b1[I] * r / (1.0 + S.en_b2 * r);
+  }
+  return acc;
+}
+
+// p at a point: nearest heavy nucleus, Eq. 3 (Gaussian) or Eq. 2 (Pade).
+__device__ __forceinline__ double p_weight(const SysDev& S, const LatDev& L, double px, double py,
+                                           double pz)
+{
+  double best = INFINITY;
+  for (int I = 0; I < S.n_nuc; ++I) {
+    if (!S.heavy[I]) continue;
+    double dx = px - S.nuc[I][0], dy = py - S.nuc[I][1], dz = pz - S.nuc[I][2];
+    double d2 = dx * dx + dy * dy + dz * dz;
+    best = fmin(best, d2);
+  }
+  if (L.pkind == 0) return exp(-best * L.p_coef);
+  return 1.0 / (1.0 + L.p_coef * best);
+}
+
+// ----------------------------------------------------------------------------
+// Per-warp shared-memory views.
+// ----------------------------------------------------------------------------
+struct WarpMem {
+  double* x;    // [N][3]
+  double* A;    // inverse up [nu][nu] then down [nd][nd]
+  double* R;    // [9]
+  double* T;    // [P_max]
+  double* v;    // [N][n_ao]
+  double* Ssum; // [N]
+  double* scr;  // scratch
+};
+
+__device__ __forceinline__ WarpMem warp_mem(const Layout& Lo, const SysDev& S, double* base)
+{
+  WarpMem m;
+  m.x = base;
+  m.A = m.x + 3 * Lo.N;
+  m.R = m.A + Lo.nu * Lo.nu + Lo.nd * Lo.nd;
+  m.T = m.R + 12;
+  m.v = m.T + Lo.P_max;
+  m.Ssum = m.v + Lo.N * S.n_ao;
+  m.scr = m.Ssum + Lo.N;
+  return m;
+}
+
+// ----------------------------------------------------------------------------
+// Inverse Slater matrix of one spin block by Gauss-Jordan elimination with
+// partial pivoting (warp-cooperative). A[l][m] = phi_m(r_l); the inverse is
+// stored as Ainv[m][l]. Returns false if a pivot is zero.
+// ----------------------------------------------------------------------------
+__device__ bool warp_inverse(const SysDev& S, const double* sC, const double* sx, int spin,
+                             double* Ainv, double* scr, int lane)
+{
+  const int n = spin == 0 ? S.n_up : S.n_dn;
+  if (n == 0) return true;
+  const int off = spin == 0 ? 0 : S.n_up;
+  const int w2 = 2 * n;
+  double* M = scr;                 // [n][2n]
+  double* chi = scr + n * w2;      // [n][n_ao]
+  for (int l = lane; l < n; l += 32) {
+    ao_values(S, &sx[3 * (off + l)], &chi[l * S.n_ao]);
+    for (int m = 0; m < n; ++m) {
+      double a = 0.0;
+      for (int mu = 0; mu < S.n_ao; ++mu) a += sC[mu * S.n_mo + m] * chi[l * S.n_ao + mu];
+      M[l * w2 + m] = a;
+      M[l * w2 + n + m] = (m == l) ? 1.0 : 0.0;
+    }
+  }
+  __syncwarp();
+  bool ok = true;
+  for (int col = 0; col < n; ++col) {
+    // pivot row: largest |M[r][col]| for r >= col, lowest r on ties
+    double best = -1.0;
+    int br = col;
+    for (int r = col + lane; r < n; r += 32) {
+      double a = fabs(M[r * w2 + col]);
+      if (a > best) { best = a; br = r; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double ob = __shfl_xor_sync(FULL_MASK, best, o);
+      int orr = __shfl_xor_sync(FULL_MASK, br, o);
+      if (ob > best || (ob == best && orr < br)) { best = ob; br = orr; }
+    }
+    if (!(best > 0.0)) { ok = false; break; }
+    if (br != col) {
+      for (int j = lane; j < w2; j += 32) {
+        double t = M[col * w2 + j];
+        M[col * w2 + j] = M[br * w2 + j];
+        M[br * w2 + j] = t;
+      }
+      __syncwarp();
+    }
+    double inv = 1.0 / M[col * w2 + col];
+    __syncwarp();
+    for (int j = lane; j < w2; j += 32) M[col * w2 + j] *= inv;
+    __syncwarp();
+    for (int r = lane; r < n; r += 32) {
+      if (r == col) continue;
+      double f = M[r * w2 + col];
+      if (f != 0.0)
+        for (int j = 0; j < w2; ++j) M[r * w2 + j] -= f * M[col * w2 + j];
+    }
+    __syncwarp();
+  }
+  if (ok) {
+    for (int idx = lane; idx < n * n; idx += 32) {
+      int m = idx / n, l = idx % n;
+      Ainv[m * n + l] = M[m * w2 + n + l];
+    }
+  }
+  __syncwarp();
+  return ok;
+}
+
+// ----------------------------------------------------------------------------
+// One evaluation of all P lattice moves out of the walker's configuration
+// (Eq. 1 lattice, fixed-node rates) and of its continuous local energy.
+// On return sT holds T_c, b and el are warp-uniform. ratio_out (global,
+// nullable) receives psi_G(x')/psi_G(x) for every move.
+// ----------------------------------------------------------------------------
+__device__ void warp_eval(const SysDev& S, const double* sC, const LatDev& L, const WarpMem& wm,
+                          int lane, double* ratio_out, double& b, double& el)
+{
+  const int N = S.N, nao = S.n_ao, nu = S.n_up;
+  // projected inverse columns: v[i][mu] = sum_m C[mu][m] Ainv_sigma[m][l_i]
+  for (int idx = lane; idx < N * nao; idx += 32) {
+    int i = idx / nao, mu = idx % nao;
+    int spin = i < nu ? 0 : 1, l = i < nu ? i : i - nu, n = spin ? S.n_dn : nu;
+    const double* A = spin ? wm.A + nu * nu : wm.A;
+    double acc = 0.0;
+    for (int m = 0; m < n; ++m) acc += sC[mu * S.n_mo + m] * A[m * n + l];
+    wm.v[idx] = acc;
+  }
+  __syncwarp();
+  // local energy: lanes over electrons
+  double part = 0.0;
+  for (int i = lane; i < N; i += 32) {
+    const double* ri = &wm.x[3 * i];
+    double val, gD[3], lD;
+    ao_dot_der(S, &wm.v[i * nao], ri, val, gD, lD);
+    double gJ[3] = {0.0, 0.0, 0.0}, lJ = 0.0, Ssum = 0.0, V = 0.0;
+    const int si = spin_of(S, i);
+    for (int j = 0; j < N; ++j) {
+      if (j == i) continue;
+      double d0 = ri[0] - wm.x[3 * j], d1 = ri[1] - wm.x[3 * j + 1], d2 = ri[2] - wm.x[3 * j + 2];
+      double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+      double c = (spin_of(S, j) == si) ? S.c_par : S.c_anti;
+      double inv = 1.0 / (1.0 + S.b_ee * r);
+      double u1 = c * inv * inv;
+      double u2 = -2.0 * S.b_ee * c * inv * inv * inv;
+      double ir = 1.0 / r;
+      gJ[0] += u1 * d0 * ir; gJ[1] += u1 * d1 * ir; gJ[2] += u1 * d2 * ir;
+      lJ += u2 + 2.0 * u1 * ir;
+      Ssum += c * r * inv;
+      if (j > i && S.ee_on) V += ir;
+    }
+    for (int I = 0; I < S.n_nuc; ++I) {
+      double d0 = ri[0] - S.nuc[I][0], d1 = ri[1] - S.nuc[I][1], d2 = ri[2] - S.nuc[I][2];
+      double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+      double b1 = S.en_b1[I];
+      double inv = 1.0 / (1.0 + S.en_b2 * r);
+      double u1 = -b1 * inv * inv;
+      double u2 = 2.0 * S.en_b2 * b1 * inv * inv * inv;
+      double ir = 1.0 / r;
+      gJ[0] += u1 * d0 * ir; gJ[1] += u1 * d1 * ir; gJ[2] += u1 * d2 * ir;
+      lJ += u2 + 2.0 * u1 * ir;
+      Ssum -= b1 * r * inv;
+      V -= S.Z[I] * ir;
+    }
+    wm.Ssum[i] = Ssum;
+    double lap = lD + 2.0 * (gD[0] * gJ[0] + gD[1] * gJ[1] + gD[2] * gJ[2]) + lJ +
+                 gJ[0] * gJ[0] + gJ[1] * gJ[1] + gJ[2] * gJ[2];
+    part += -0.5 * lap + V;
+  }
+  el = warp_sum(part) + S.V_nn;
+  __syncwarp();
+  // the P lattice moves: lanes over candidates
+  const int G = L.G, per_e = 6 * G, P = N * per_e;
+  for (int c = lane; c < P; c += 32) {
+    int i = c / per_e, rem = c - i * per_e, g = rem / 6, k = (rem % 6) >> 1;
+    double sign = (c & 1) ? -1.0 : 1.0;
+    double h = g ? L.ap : L.a;
+    double ex = wm.R[k], ey = wm.R[3 + k], ez = wm.R[6 + k];
+    const double* ri = &wm.x[3 * i];
+    double px = ri[0] + sign * h * ex, py = ri[1] + sign * h * ey, pz = ri[2] + sign * h * ez;
+    double rdet = ao_dot(S, &wm.v[i * nao], px, py, pz);
+    double dJ = jastrow_terms(S, wm.x, i, px, py, pz) - wm.Ssum[i];
+    double rho = rdet * exp(dJ);
+    double w = 1.0;
+    if (G == 2) {
+      double hh = 0.5 * h;
+      double pm = p_weight(S, L, ri[0] + sign * hh * ex, ri[1] + sign * hh * ey, ri[2] + sign * hh * ez);
+      w = g ? 1.0 - pm : pm;
+    }
+    double T = rho > 0.0 ? w * (g ? L.inv2ap2 : L.inv2a2) * rho : 0.0;
+    wm.T[c] = T;
+    if (ratio_out) ratio_out[c] = rho;
+  }
+  __syncwarp();
+  b = warp_scan(wm.T, P, lane, 0.0, nullptr, nullptr);
+}
+
+// ----------------------------------------------------------------------------
+// Sherman-Morrison update for electron i moving to p (warp-cooperative):
+// y_n = sum_m phi_m(p) Ainv[m][n], ratio = y_l,
+// Ainv[m][n] -= Ainv[m][l] (y_n - delta_nl) / ratio.
+// ----------------------------------------------------------------------------
+__device__ bool warp_sm_update(const SysDev& S, const double* sC, const WarpMem& wm, int i,
+                               const double* p, int lane)
+{
+  const int nu = S.n_up;
+  const int spin = i < nu ? 0 : 1, l = i < nu ? i : i - nu, n = spin ? S.n_dn : nu;
+  double* A = spin ? wm.A + nu * nu : wm.A;
+  double* chi = wm.scr;            // [n_ao]
+  double* phi = chi + S.n_ao;      // [n]
+  double* y = phi + n;             // [n]
+  double* col = y + n;             // [n]
+  if (lane == 0) ao_values(S, p, chi);
+  __syncwarp();
+  for (int m = lane; m < n; m += 32) {
+    double a = 0.0;
+    for (int mu = 0; mu < S.n_ao; ++mu) a += sC[mu * S.n_mo + m] * chi[mu];
+    phi[m] = a;
+  }
+  __syncwarp();
+  for (int q = lane; q < n; q += 32) {
+    double a = 0.0;
+    for (int m = 0; m < n; ++m) a += phi[m] * A[m * n + q];
+    y[q] = a;
+    col[q] = A[q * n + l];
+  }
+  __syncwarp();
+  double ratio = y[l];
+  if (ratio == 0.0) return false;
+  double inv = 1.0 / ratio;
+  for (int idx = lane; idx < n * n; idx += 32) {
+    int m = idx / n, q = idx % n;
+    A[idx] -= col[m] * ((y[q] - (q == l ? 1.0 : 0.0)) * inv);
+  }
+  __syncwarp();
+  return true;
+}
+
+// ----------------------------------------------------------------------------
+// Record load / store.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void load_record(const Layout& Lo, const double* rec, const WarpMem& wm,
+                                            int lane, double& b, double& el)
+{
+  for (int j = lane; j < 3 * Lo.N; j += 32) wm.x[j] = rec[Lo.off_x + j];
+  for (int j = lane; j < Lo.nu * Lo.nu + Lo.nd * Lo.nd; j += 32) wm.A[j] = rec[Lo.off_au + j];
+  for (int j = lane; j < 9; j += 32) wm.R[j] = rec[Lo.off_R + j];
+  for (int j = lane; j < Lo.P_max; j += 32) wm.T[j] = rec[Lo.off_T + j];
+  b = rec[Lo.off_b];
+  el = rec[Lo.off_el];
+  __syncwarp();
+}
+
+__device__ __forceinline__ void store_record(const Layout& Lo, double* rec, const WarpMem& wm,
+                                             int lane, double b, double el)
+{
+  __syncwarp();
+  for (int j = lane; j < 3 * Lo.N; j += 32) rec[Lo.off_x + j] = wm.x[j];
+  for (int j = lane; j < Lo.nu * Lo.nu + Lo.nd * Lo.nd; j += 32) rec[Lo.off_au + j] = wm.A[j];
+  for (int j = lane; j < 9; j += 32) rec[Lo.off_R + j] = wm.R[j];
+  for (int j = lane; j < Lo.P_max; j += 32) rec[Lo.off_T + j] = wm.T[j];
+  if (lane == 0) {
+    rec[Lo.off_b] = b;
+    rec[Lo.off_el] = el;
+  }
+}
+
+__device__ __forceinline__ void stage_coefficients(const SysDev& S, double* sC)
+{
+  for (int j = threadIdx.x; j < S.n_ao * S.n_mo; j += blockDim.x) sC[j] = S.C[j];
+  __syncthreads();
+}
+
+// ----------------------------------------------------------------------------
+// Kernels.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+k_init(const __grid_constant__ SysDev S, const Layout Lo, const PopDev P, const double* x0)
+{
+  extern __shared__ double smem[];
+  double* sC = smem;
+  stage_coefficients(S, sC);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int s = blockIdx.x * kWarpsPerBlock + wib;
+  if (s >= P.W) return;
+  WarpMem wm = warp_mem(Lo, S, sC + S.n_ao * S.n_mo + wib * Lo.smem_warp);
+  for (int j = lane; j < 3 * Lo.N; j += 32) wm.x[j] = x0[(size_t)s * 3 * Lo.N + j];
+  for (int j = lane; j < Lo.P_max; j += 32) wm.T[j] = 0.0;
+  __syncwarp();
+  bool ok = warp_inverse(S, sC, wm.x, 0, wm.A, wm.scr, lane);
+  ok = ok && warp_inverse(S, sC, wm.x, 1, wm.A + Lo.nu * Lo.nu, wm.scr, lane);
+  if (!ok && lane == 0) atomicOr(P.err, kErrSingular);
+  if (lane == 0) {
+    double u[4];
+    draw_uniforms(P.seed, (uint64_t)s, kIntervalInit, 0, kTagRot, u);
+    rotation_matrix(u[0], u[1], u[2], wm.R);
+    P.parent[s] = s;
+  }
+  store_record(Lo, P.rec_src + (size_t)s * Lo.rec, wm, lane, NAN, NAN);
+}
+
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+k_eval_all(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, const PopDev P)
+{
+  extern __shared__ double smem[];
+  double* sC = smem;
+  stage_coefficients(S, sC);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int s = blockIdx.x * kWarpsPerBlock + wib;
+  if (s >= P.W) return;
+  WarpMem wm = warp_mem(Lo, S, sC + S.n_ao * S.n_mo + wib * Lo.smem_warp);
+  double* rec = P.rec_src + (size_t)s * Lo.rec;
+  double b, el;
+  load_record(Lo, rec, wm, lane, b, el);
+  warp_eval(S, sC, L, wm, lane, nullptr, b, el);
+  if (!isfinite(el) || !isfinite(b)) {
+    if (lane == 0) atomicOr(P.err, kErrNonFinite);
+  }
+  store_record(Lo, rec, wm, lane, b, el);
+}
+
+// One interval of length tau for every walker slot (continuous-time
+// projection of the cited LRDMC method): wait for an exponential time of
+// rate b_x, decrease log w by (E_L - E_T) times the time spent, and at the
+// end of the wait jump to move c with probability T_c / b_x.
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, const PopDev P,
+           uint64_t k, int recompute)
+{
+  extern __shared__ double smem[];
+  double* sC = smem;
+  stage_coefficients(S, sC);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  WarpMem wm = warp_mem(Lo, S, sC + S.n_ao * S.n_mo + wib * Lo.smem_warp);
+  const int P_moves = S.N * 6 * L.G;
+  for (;;) {
+    int s = 0;
+    if (lane == 0) s = atomicAdd(P.counter, 1);
+    s = __shfl_sync(FULL_MASK, s, 0);
+    if (s >= P.W) break;
+    const int src = P.parent[s];
+    double b, el;
+    load_record(Lo, P.rec_src + (size_t)src * Lo.rec, wm, lane, b, el);
+    if (recompute) {
+      bool ok = warp_inverse(S, sC, wm.x, 0, wm.A, wm.scr, lane);
+      ok = ok && warp_inverse(S, sC, wm.x, 1, wm.A + Lo.nu * Lo.nu, wm.scr, lane);
+      if (!ok && lane == 0) atomicOr(P.err, kErrSingular);
+    }
+    double tau_left = P.tau, logw = 0.0;
+    int jumps = 0;
+    for (uint64_t m = 0;; ++m) {
+      double u[4];
+      draw_uniforms(P.seed, (uint64_t)s, k, m, kTagTimeHB, u);
+      double t = b > 0.0 ? -log(u[0]) / b : INFINITY;
+      if (t >= tau_left) {
+        logw -= tau_left * (el - P.e_trial);
+        break;
+      }
+      logw -= t * (el - P.e_trial);
+      tau_left -= t;
+      // heat bath over the cached rates
+      int pick, last;
+      warp_scan(wm.T, P_moves, lane, u[1] * b, &pick, &last);
+      if (pick < 0) pick = last;
+      if (pick < 0) {  // no allowed move: cannot happen with b > 0
+        if (lane == 0) atomicOr(P.err, kErrNonFinite);
+        break;
+      }
+      const int per_e = 6 * L.G;
+      const int i = pick / per_e, rem = pick - i * per_e, g = rem / 6, kx = (rem % 6) >> 1;
+      const double sign = (pick & 1) ? -1.0 : 1.0, h = g ? L.ap : L.a;
+      double pnew[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) pnew[d] = wm.x[3 * i + d] + sign * h * wm.R[3 * d + kx];
+      if (!warp_sm_update(S, sC, wm, i, pnew, lane)) {
+        if (lane == 0) atomicOr(P.err, kErrSingular);
+        break;
+      }
+      if (lane < 3) wm.x[3 * i + lane] = pnew[lane];
+      double ur[4];
+      draw_uniforms(P.seed, (uint64_t)s, k, m, kTagRot, ur);
+      __syncwarp();
+      if (lane == 0) rotation_matrix(ur[0], ur[1], ur[2], wm.R);
+      __syncwarp();
+      warp_eval(S, sC, L, wm, lane, nullptr, b, el);
+      ++jumps;
+      if (!isfinite(el) || !isfinite(b)) {
+        if (lane == 0) atomicOr(P.err, kErrNonFinite);
+        break;
+      }
+      if (m + 1 >= (uint64_t)kMaxItersPerInterval) {
+        if (lane == 0) atomicOr(P.err, kErrIters);
+        break;
+      }
+    }
+    store_record(Lo, P.rec_dst + (size_t)s * Lo.rec, wm, lane, b, el);
+    if (lane == 0) {
+      P.logw[s] = logw;
+      P.el_end[s] = el;
+      P.jumps[s] = jumps;
+    }
+    __syncwarp();
+  }
+}
+
+// Reconfiguration at the end of interval k (one block of 1024 threads):
+// w_s = exp(log w_s), trace (weighted mean E_L, mean weight, mean jumps),
+// comb parents: slot t takes the smallest s with (t + xi) C_W / W < C_s.
+__global__ void __launch_bounds__(1024) k_reconfig(const PopDev P, uint64_t k)
+{
+  __shared__ double s_run[1024];
+  __shared__ double s_e[32], s_j[32], s_w[32];
+  __shared__ double s_total;
+  const int W = P.W, t = threadIdx.x, nt = blockDim.x;
+  const int chunk = (W + nt - 1) / nt;
+  const int lo = min(W, t * chunk), hi = min(W, lo + chunk);
+  double run = 0.0, swe = 0.0, sj = 0.0;
+  for (int s = lo; s < hi; ++s) {
+    double w = exp(P.logw[s]);
+    run += w;
+    P.cum[s] = run;
+    swe += w * P.el_end[s];
+    sj += (double)P.jumps[s];
+  }
+  // block exclusive scan of the chunk totals
+  s_run[t] = run;
+  __syncthreads();
+  for (int o = 1; o < nt; o <<= 1) {
+    double y = (t >= o) ? s_run[t - o] : 0.0;
+    __syncthreads();
+    s_run[t] += y;
+    __syncthreads();
+  }
+  double offset = (t > 0) ? s_run[t - 1] : 0.0;
+  for (int s = lo; s < hi; ++s) P.cum[s] += offset;
+  if (t == nt - 1) s_total = s_run[nt - 1];
+  // reductions of swe and sj
+  double e = warp_sum(swe), j = warp_sum(sj);
+  if ((t & 31) == 0) { s_e[t >> 5] = e; s_j[t >> 5] = j; }
+  __syncthreads();
+  if (t < 32) {
+    double e2 = (t < (nt >> 5)) ? s_e[t] : 0.0, j2 = (t < (nt >> 5)) ? s_j[t] : 0.0;
+    e2 = warp_sum(e2);
+    j2 = warp_sum(j2);
+    if (t == 0) { s_w[0] = e2; s_w[1] = j2; }
+  }
+  __syncthreads();
+  const double total = s_total;
+  double u[4];
+  draw_uniforms(P.seed, kSlotGlobal, k, 0, kTagComb, u);
+  const double xi = u[0];
+  for (int tt = lo; tt < hi; ++tt) {
+    double target = ((double)tt + xi) * total / (double)W;
+    int a = 0, bnd = W - 1;  // smallest s with target < cum[s], else W-1
+    while (a < bnd) {
+      int mid = (a + bnd) >> 1;
+      if (target < P.cum[mid]) bnd = mid; else a = mid + 1;
+    }
+    P.parent[tt] = a;
+  }
+  if (t == 0) {
+    P.trace[k] = s_w[0] / total;
+    P.trace[P.trace_cap + k] = total / (double)W;
+    P.trace[2 * P.trace_cap + k] = s_w[1] / (double)W;
+    *P.moves += (unsigned long long)(s_w[1] + 0.5);
+    *P.counter = 0;
+  }
+}
+
+// Stateless evaluation of given configurations (one warp per configuration).
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+k_evaluate(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, int n,
+           const double* x, const double* rot, double* ratio, double* T, double* b_out,
+           double* el_out, int* err)
+{
+  extern __shared__ double smem[];
+  double* sC = smem;
+  stage_coefficients(S, sC);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int c = blockIdx.x * kWarpsPerBlock + wib;
+  if (c >= n) return;
+  WarpMem wm = warp_mem(Lo, S, sC + S.n_ao * S.n_mo + wib * Lo.smem_warp);
+  for (int j = lane; j < 3 * Lo.N; j += 32) wm.x[j] = x[(size_t)c * 3 * Lo.N + j];
+  for (int j = lane; j < 9; j += 32) wm.R[j] = rot[(size_t)c * 9 + j];
+  __syncwarp();
+  bool ok = warp_inverse(S, sC, wm.x, 0, wm.A, wm.scr, lane);
+  ok = ok && warp_inverse(S, sC, wm.x, 1, wm.A + Lo.nu * Lo.nu, wm.scr, lane);
+  if (!ok) {
+    if (lane == 0) atomicOr(err, kErrSingular);
+    return;
+  }
+  const int P = S.N * 6 * L.G;
+  double b, el;
+  warp_eval(S, sC, L, wm, lane, ratio ? ratio + (size_t)c * P : nullptr, b, el);
+  if (T)
+    for (int j = lane; j < P; j += 32) T[(size_t)c * P + j] = wm.T[j];
+  if (lane == 0) {
+    if (b_out) b_out[c] = b;
+    if (el_out) el_out[c] = el;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Host launchers.
+// ----------------------------------------------------------------------------
+Layout make_layout(const SysDev& S)
+{
+  Layout Lo;
+  Lo.N = S.N;
+  Lo.nu = S.n_up;
+  Lo.nd = S.n_dn;
+  Lo.P_max = 12 * S.N;
+  Lo.off_x = 0;
+  Lo.off_au = 3 * S.N;
+  Lo.off_ad = Lo.off_au + S.n_up * S.n_up;
+  Lo.off_R = Lo.off_ad + S.n_dn * S.n_dn;
+  Lo.off_T = Lo.off_R + 9;
+  Lo.off_b = Lo.off_T + Lo.P_max;
+  Lo.off_el = Lo.off_b + 1;
+  Lo.rec = (Lo.off_el + 1 + 3) & ~3;
+  const int n = S.n_up;
+  int scr = 2 * n * n + n * S.n_ao;          // Gauss-Jordan + orbital rows
+  int scr_sm = S.n_ao + 3 * n;               // Sherman-Morrison
+  if (scr_sm > scr) scr = scr_sm;
+  Lo.smem_warp = 3 * S.N + S.n_up * S.n_up + S.n_dn * S.n_dn + 12 + Lo.P_max + S.N * S.n_ao + S.N + scr;
+  Lo.smem_warp = (Lo.smem_warp + 1) & ~1;
+  Lo.smem_block_bytes = (int)sizeof(double) * (S.n_ao * S.n_mo + kWarpsPerBlock * Lo.smem_warp);
+  return Lo;
+}
+
+static cudaError_t set_smem(const void* fn, int bytes)
+{
+  if (bytes > 48 * 1024) return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return cudaSuccess;
+}
+
+cudaError_t launch_init(const SysDev& S, const Layout& Lo, const PopDev& P, const double* x0,
+                        cudaStream_t st)
+{
+  cudaError_t e = set_smem((const void*)k_init, Lo.smem_block_bytes);
+  if (e != cudaSuccess) return e;
+  int blocks = (P.W + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  k_init<<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(S, Lo, P, x0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eval_all(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P,
+                            cudaStream_t st)
+{
+  cudaError_t e = set_smem((const void*)k_eval_all, Lo.smem_block_bytes);
+  if (e != cudaSuccess) return e;
+  int blocks = (P.W + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  k_eval_all<<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(S, Lo, L, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_interval(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P,
+                            uint64_t k, int recompute, cudaStream_t st)
+{
+  static int blocks_per_sm = -1, sm_count = 0, cached_smem = -1;
+  cudaError_t e = set_smem((const void*)k_interval, Lo.smem_block_bytes);
+  if (e != cudaSuccess) return e;
+  if (cached_smem != Lo.smem_block_bytes) {
+    int dev;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_interval, kWarpsPerBlock * 32,
+                                                      Lo.smem_block_bytes);
+    if (e != cudaSuccess) return e;
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+    cached_smem = Lo.smem_block_bytes;
+  }
+  int need = (P.W + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  int blocks = blocks_per_sm * sm_count;
+  if (blocks > need) blocks = need;
+  k_interval<<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(S, Lo, L, P, k, recompute);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reconfig(const PopDev& P, uint64_t k, cudaStream_t st)
+{
+  k_reconfig<<<1, 1024, 0, st>>>(P, k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_evaluate(const SysDev& S, const Layout& Lo, const LatDev& L, int n,
+                            const double* x, const double* rot, double* ratio, double* T,
+                            double* b, double* el, int* err, cudaStream_t st)
+{
+  cudaError_t e = set_smem((const void*)k_evaluate, Lo.smem_block_bytes);
+  if (e != cudaSuccess) return e;
+  int blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  k_evaluate<<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(S, Lo, L, n, x, rot, ratio, T,
+                                                                       b, el, err);
+  return cudaGetLastError();
+}
+
+}  // namespace lrdmc

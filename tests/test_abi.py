@@ -1,0 +1,100 @@
+"""CPU checks of the C ABI: the library loads, exports every entry point the
+header declares, validates its arguments and computes the double-grid
+parameters (host logic) like the oracle."""
+import ctypes as ct
+import os
+import re
+
+import numpy as np
+import pytest
+
+import lrdmc_synth as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_1909_01589_gb300 import build
+
+    build.build()
+    import paper_1909_01589_gb300 as p
+
+    p.load_library()
+    return p
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "lrdmc.h")).read()
+    return sorted(set(re.findall(r"LRDMC_API\s+[\w\s\*]+?\b(lrdmc_\w+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(pkg):
+    names = declared_functions()
+    assert len(names) >= 13
+    lib = ct.CDLL(pkg.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(pkg.EXPORTED)
+
+
+def test_create_system_rejects_bad_sizes(pkg):
+    s = S.neon()
+    s.n_up, s.n_dn = 40, 5  # beyond LRDMC_MAX_SPIN
+    with pytest.raises(pkg.LrdmcError) as e:
+        pkg.LrdmcSystem(s)
+    assert e.value.status == pkg.ERR_ARG
+    s = S.neon()
+    s.shells = s.shells[:-1]  # n_ao no longer matches C
+    with pytest.raises(pkg.LrdmcError):
+        pkg.LrdmcSystem(s)
+
+
+def test_step_before_init_is_a_state_error(pkg):
+    g = pkg.LrdmcSystem(S.helium())
+    with pytest.raises(pkg.LrdmcError) as e:
+        g.step(1, 0.2)
+    assert e.value.status == pkg.ERR_STATE
+
+
+@pytest.mark.parametrize("name,Z", [("He", 2), ("Ne", 10)])
+@pytest.mark.parametrize("a", [0.4, 0.2, 0.1, 0.02857142857142857])
+def test_spacing_params_match_oracle(pkg, oracle_mod, name, Z, a):
+    """S-13, Eq. 6 and Eq. 7 in the library (Gauss-Legendre quadrature,
+    its own Slater's-rule code) agree with the oracle (Simpson rule)."""
+    s = S.make_system(name)
+    g = pkg.LrdmcSystem(s)
+    ratio, rc = g.spacing_params(a, pkg.Spacing(pkg.THIS_WORK))
+    assert abs(rc - oracle_mod.rc_this_work(a, Z)) < 1e-15 * max(1, rc)
+    q = oracle_mod.aprime_over_a_this_work(Z, a)
+    assert abs(ratio - q) < 1e-11 * q
+    r2, rc2 = g.spacing_params(a, pkg.Spacing(pkg.PREVIOUS))
+    assert abs(r2 - oracle_mod.aprime_over_a_previous(Z)) < 1e-15 * r2 and rc2 == Z / 2
+    r3, rc3 = g.spacing_params(a, pkg.Spacing(pkg.SINGLE))
+    assert r3 == 1.0
+
+
+@pytest.mark.parametrize("Z", [4, 18, 36, 54])
+def test_spacing_params_heavier_atoms(pkg, oracle_mod, Z):
+    s = S.hydrogenic_ion(Z)
+    g = pkg.LrdmcSystem(s)
+    a = 1.0 / (3.5 * Z)
+    ratio, rc = g.spacing_params(a, pkg.Spacing(pkg.THIS_WORK))
+    q = oracle_mod.aprime_over_a_this_work(Z, a)
+    assert abs(ratio - q) < 1e-9 * q
+
+
+def test_spacing_rejects_bad_arguments(pkg):
+    g = pkg.LrdmcSystem(S.neon())
+    with pytest.raises(pkg.LrdmcError):
+        g.spacing_params(-0.1, pkg.Spacing(pkg.SINGLE))
+    with pytest.raises(pkg.LrdmcError):
+        g.spacing_params(0.1, pkg.Spacing(pkg.EXPLICIT, rc=0.0, aprime_over_a=2.0))
+    with pytest.raises(pkg.LrdmcError):
+        g.spacing_params(0.1, pkg.Spacing(7))
+
+
+def test_workspace_bytes_grow_with_walkers(pkg):
+    g = pkg.LrdmcSystem(S.neon())
+    b1, b2 = g.workspace_bytes(100, 10), g.workspace_bytes(1000, 10)
+    assert b2 > 9 * b1 / 2 and b1 % 256 == 0

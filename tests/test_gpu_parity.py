@@ -1,0 +1,225 @@
+"""GPU-vs-oracle parity of the CUDA path, through the C ABI.
+
+Bar (FP64): lattice-move ratios, rates, total rates and local energies
+within 1e-10 relative (ratios: relative to max(1, |ratio|)); positions,
+log-weights and trace energies within 1e-10; jump counts, comb parents and
+move choices identical, except after a decision the oracle reports within
+1e-9 of a bin edge (then the trajectories may part and the comparison
+stops, counting the event).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import lrdmc_synth as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-10
+EDGE = 1e-9
+THREADS = max(1, min(16, os.cpu_count() or 1))
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1909_01589_gb300 import build
+
+    build.build()
+    import paper_1909_01589_gb300 as p
+
+    p.load_library()
+    return p
+
+
+def spacing_pair(pkg, oracle_mod, system, a, kind, rc=0.5, ratio=1.5):
+    if kind == "single":
+        return pkg.Spacing(pkg.SINGLE), oracle_mod.lattice_for(system, a, oracle_mod.SINGLE)
+    if kind == "this_work":
+        return pkg.Spacing(pkg.THIS_WORK), oracle_mod.lattice_for(system, a, oracle_mod.THIS_WORK)
+    if kind == "previous":
+        return pkg.Spacing(pkg.PREVIOUS), oracle_mod.lattice_for(system, a, oracle_mod.PREVIOUS)
+    return (pkg.Spacing(pkg.EXPLICIT, rc=rc, aprime_over_a=ratio),
+            oracle_mod.lattice_for(system, a, oracle_mod.EXPLICIT, rc=rc, aprime_over_a=ratio))
+
+
+EVAL_CASES = [
+    ("He", "single", 0.2), ("He", "this_work", 0.2), ("Ne", "single", 0.1), ("Ne", "this_work", 0.2),
+    ("Ne", "previous", 0.4), ("tiny_mixed", "explicit", 0.3), ("Be_bare", "explicit", 0.25),
+    ("H", "this_work", 0.3),
+]
+
+
+@pytest.mark.parametrize("name,kind,a", EVAL_CASES)
+def test_evaluate_matches_oracle(pkg, oracle_mod, name, kind, a):
+    """All 6N / 12N ratios, rates, total rate and local energy of 37
+    configurations (nine warps of four, a ragged last block)."""
+    system = S.make_system(name)
+    if name == "H" and kind == "this_work":
+        system = S.hydrogen(0.8)
+    g = pkg.LrdmcSystem(system)
+    o = oracle_mod.OracleSystem(system)
+    n = 37
+    x = S.initial_positions(system, n, 101)
+    R = S.random_rotations(n, 102)
+    sp, lat = spacing_pair(pkg, oracle_mod, system, a, kind)
+    ratio, T, b, el = g.evaluate(torch.tensor(x, device="cuda"), torch.tensor(R, device="cuda"), a, sp)
+    ratio, T, b, el = (t.cpu().numpy() for t in (ratio, T, b, el))
+    for c in range(n):
+        ref = o.lattice_eval(lat, x[c], R[c])
+        assert np.all(np.abs(ratio[c] - ref["ratio"]) <= RTOL * np.maximum(1.0, np.abs(ref["ratio"])))
+        assert np.all(np.abs(T[c] - ref["T"]) <= RTOL * np.max(ref["T"]))
+        assert abs(b[c] - ref["b"]) <= RTOL * ref["b"]
+        assert abs(el[c] - ref["EL"]) <= RTOL * max(1.0, abs(ref["EL"]))
+
+
+def test_evaluate_full_size_sampled(pkg, oracle_mod):
+    """The Ne workload at full size (4096 configurations, double grid with
+    the paper's parameters, a = 0.2): 64 sampled configurations against the
+    oracle one by one, every total rate positive and finite."""
+    system = S.neon()
+    g = pkg.LrdmcSystem(system)
+    o = oracle_mod.OracleSystem(system)
+    n = 4096
+    x = S.initial_positions(system, n, 201)
+    R = S.random_rotations(n, 202)
+    sp, lat = spacing_pair(pkg, oracle_mod, system, 0.2, "this_work")
+    ratio, T, b, el = g.evaluate(torch.tensor(x, device="cuda"), torch.tensor(R, device="cuda"), 0.2, sp)
+    ratio, b, el = ratio.cpu().numpy(), b.cpu().numpy(), el.cpu().numpy()
+    assert np.all(np.isfinite(el)) and np.all(b > 0)
+    for c in np.random.default_rng(3).choice(n, 64, replace=False):
+        ref = o.lattice_eval(lat, x[c], R[c])
+        assert np.all(np.abs(ratio[c] - ref["ratio"]) <= RTOL * np.maximum(1.0, np.abs(ref["ratio"])))
+        assert abs(el[c] - ref["EL"]) <= RTOL * abs(ref["EL"])
+
+
+def _compare_runs(pkg, oracle_mod, system, kind, a, W, n_steps, tau, seed, e_trial, rc_every=3):
+    g = pkg.LrdmcSystem(system)
+    o = oracle_mod.OracleSystem(system)
+    x0 = S.initial_positions(system, W, seed)
+    sp, lat = spacing_pair(pkg, oracle_mod, system, a, kind)
+    g.init_walkers(torch.tensor(x0, device="cuda"), seed=seed, tau=tau, e_trial=e_trial,
+                   recompute_every=rc_every, trace_capacity=n_steps)
+    pop = oracle_mod.OraclePopulation(o, x0, seed=seed, tau=tau, e_trial=e_trial, recompute_every=rc_every)
+    compared = 0
+    for k in range(n_steps):
+        g.step(1, a, sp)
+        pop.step(lat, 1, THREADS)
+        gw, ow = g.walkers(), pop.walkers(lat.G)
+        ok = (np.array_equal(gw["jumps_pre"], ow["jumps_pre"]) and np.array_equal(gw["parent"], ow["parent"])
+              and np.all(np.abs(gw["x"] - ow["x"]) <= RTOL * np.maximum(1.0, np.abs(ow["x"])))
+              and np.all(np.abs(gw["EL"] - ow["EL"]) <= RTOL * np.maximum(1.0, np.abs(ow["EL"])))
+              and np.all(np.abs(gw["logw_pre"] - ow["logw_pre"]) <= RTOL * np.maximum(1.0, np.abs(ow["logw_pre"]))))
+        if not ok:
+            mw, mc = pop.margins()
+            assert min(np.min(mw), mc) < EDGE, f"divergence at interval {k} without a near-edge decision"
+            return compared, True
+        compared += 1
+    ge, gwb, gj = g.energy_trace()
+    oe, owb, oj = pop.trace()
+    assert np.all(np.abs(ge - oe) <= RTOL * np.abs(oe))
+    assert np.all(np.abs(gwb - owb) <= RTOL * owb)
+    assert np.array_equal(gj, oj)
+    assert g.moves() == pop.moves
+    return compared, False
+
+
+@pytest.mark.parametrize("name,kind,a,W,steps,tau,et", [
+    ("He", "single", 0.2, 64, 25, 0.02, -2.9),
+    ("He", "this_work", 0.2, 61, 25, 0.02, -2.9),
+    ("Ne", "this_work", 0.2, 32, 8, 0.02, -128.9),
+    ("Ne", "previous", 0.3, 9, 6, 0.01, -128.9),
+    ("Be_bare", "explicit", 0.2, 16, 10, 0.02, -20.0),
+    ("H", "single", 0.3, 5, 10, 0.05, -0.5),
+])
+def test_projection_matches_oracle(pkg, oracle_mod, name, kind, a, W, steps, tau, et):
+    """Whole intervals: waiting times, heat-bath choices, Sherman-Morrison
+    updates, inverse recomputation, weights and comb reconfiguration."""
+    compared, parted = _compare_runs(pkg, oracle_mod, S.make_system(name), kind, a, W, steps, tau, 11, et)
+    assert compared >= (1 if parted else steps)
+
+
+def test_projection_full_size(pkg, oracle_mod):
+    """The Ne workload at full size (4096 walkers, a = 0.2, the paper's
+    double grid, tau = 0.025) for two intervals, walker by walker."""
+    compared, parted = _compare_runs(pkg, oracle_mod, S.neon(), "this_work", 0.2, 4096, 2, 0.025, 5, -128.9)
+    assert compared >= 1
+
+
+@pytest.mark.parametrize("name,E", [("H", -0.5), ("Be_bare", -20.0)])
+def test_zero_variance_on_gpu(pkg, name, E):
+    system = S.make_system(name)
+    g = pkg.LrdmcSystem(system)
+    g.init_walkers(torch.tensor(S.initial_positions(system, 1000, 4), device="cuda"), seed=4, tau=0.05,
+                   e_trial=E, recompute_every=5, trace_capacity=50)
+    g.step(50, 0.2, pkg.Spacing(pkg.EXPLICIT, rc=0.4, aprime_over_a=1.8))
+    e, w, j = g.energy_trace()
+    assert np.max(np.abs(e - E)) < 1e-10 * abs(E)
+    assert np.max(np.abs(w - 1.0)) < 1e-10 and np.mean(j) > 0.5
+
+
+def test_checkpoint_resume_bitwise(pkg, tmp_path):
+    """save after 3 intervals, run 4 more; load and run the same 4: identical."""
+    system = S.helium()
+    sp = pkg.Spacing(pkg.THIS_WORK)
+    g = pkg.LrdmcSystem(system)
+    g.init_walkers(torch.tensor(S.initial_positions(system, 100, 8), device="cuda"), seed=8, tau=0.02,
+                   e_trial=-2.9, recompute_every=2, trace_capacity=10)
+    g.step(3, 0.2, sp)
+    path = str(tmp_path / "ckpt.bin")
+    g.save(path)
+    g.step(4, 0.2, sp)
+    e1 = g.energy_trace()[0]
+    x1 = g.walkers()["x"]
+    g.load(path)
+    g.step(4, 0.2, sp)
+    assert np.array_equal(g.energy_trace()[0], e1)
+    assert np.array_equal(g.walkers()["x"], x1)
+
+
+def test_deterministic_repeat(pkg):
+    system = S.neon()
+    sp = pkg.Spacing(pkg.THIS_WORK)
+    out = []
+    for _ in range(2):
+        g = pkg.LrdmcSystem(system)
+        g.init_walkers(torch.tensor(S.initial_positions(system, 300, 9), device="cuda"), seed=9, tau=0.02,
+                       e_trial=-128.9, recompute_every=3, trace_capacity=5)
+        g.step(5, 0.2, sp)
+        out.append((g.energy_trace()[0], g.walkers()["x"]))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_errors_are_reported_not_faulted(pkg):
+    system = S.neon()
+    g = pkg.LrdmcSystem(system)
+    x0 = S.initial_positions(system, 8, 10)
+    x0[3, 1] = x0[3, 0]  # two spin-up electrons on one point: singular Slater matrix
+    with pytest.raises(pkg.LrdmcError) as e:
+        g.init_walkers(torch.tensor(x0, device="cuda"), seed=1, tau=0.01, trace_capacity=2)
+    assert e.value.status == pkg.ERR_SINGULAR
+    g2 = pkg.LrdmcSystem(system)
+    g2.init_walkers(torch.tensor(S.initial_positions(system, 8, 11), device="cuda"), seed=1, tau=0.01,
+                    trace_capacity=2)
+    g2.step(2, 0.2)
+    with pytest.raises(pkg.LrdmcError) as e:
+        g2.step(1, 0.2)  # trace capacity exhausted
+    assert e.value.status == pkg.ERR_ARG
+    g2.step(0, 0.2)  # zero steps is a no-op
+
+
+def test_host_buffers_and_single_walker(pkg, oracle_mod):
+    """x0 from host memory, one walker, spin-down block empty (H)."""
+    system = S.hydrogen(0.8)
+    system.en_b1 = np.array([0.2])
+    g = pkg.LrdmcSystem(system)
+    x0 = S.initial_positions(system, 1, 12)
+    g.init_walkers(x0, seed=12, tau=0.05, e_trial=-0.5, recompute_every=1, trace_capacity=20)
+    g.step(20, 0.2, pkg.Spacing(pkg.SINGLE))
+    o = oracle_mod.OracleSystem(system)
+    pop = oracle_mod.OraclePopulation(o, x0, seed=12, tau=0.05, e_trial=-0.5, recompute_every=1)
+    pop.step(oracle_mod.lattice_for(system, 0.2, oracle_mod.SINGLE), 20, 1)
+    assert np.allclose(g.energy_trace()[0], pop.trace()[0], rtol=RTOL, atol=0)
