@@ -190,6 +190,17 @@ LRDMC_API lrdmc_status lrdmc_evaluate(lrdmc_system_t sys, int n_configs, const d
 LRDMC_API lrdmc_status lrdmc_save(lrdmc_system_t sys, const char* path);
 LRDMC_API lrdmc_status lrdmc_load(lrdmc_system_t sys, const char* path);
 
+/* Kernel timing for measurement. With profiling on, lrdmc_step brackets
+ * every launch of its interval kernel and of its reconfiguration kernel
+ * with CUDA events on the system's stream and accumulates their durations
+ * (read after the step's final synchronisation). lrdmc_kernel_times returns
+ * the accumulated milliseconds and launch counts (each nullable) and, if
+ * reset != 0, clears them. Profiling is off after init. */
+LRDMC_API lrdmc_status lrdmc_set_profiling(lrdmc_system_t sys, int on);
+LRDMC_API lrdmc_status lrdmc_kernel_times(lrdmc_system_t sys, double* interval_ms, double* reconfig_ms,
+                                          long long* interval_launches, long long* reconfig_launches,
+                                          int reset);
+
 /* Last error message of the system (static string if sys is NULL). */
 LRDMC_API const char* lrdmc_last_error(lrdmc_system_t sys);
 

@@ -29,7 +29,8 @@ SINGLE, THIS_WORK, PREVIOUS, EXPLICIT = 0, 1, 2, 3
 EXPORTED = [
     "lrdmc_create_system", "lrdmc_spacing_params", "lrdmc_workspace_bytes", "lrdmc_init_walkers",
     "lrdmc_step", "lrdmc_get_energy_trace", "lrdmc_get_walkers", "lrdmc_moves", "lrdmc_evaluate",
-    "lrdmc_save", "lrdmc_load", "lrdmc_last_error", "lrdmc_destroy",
+    "lrdmc_save", "lrdmc_load", "lrdmc_set_profiling", "lrdmc_kernel_times", "lrdmc_last_error",
+    "lrdmc_destroy",
 ]
 
 
@@ -103,6 +104,11 @@ def load_library():
     L.lrdmc_save.argtypes = [vp, ct.c_char_p]
     L.lrdmc_load.restype = i
     L.lrdmc_load.argtypes = [vp, ct.c_char_p]
+    L.lrdmc_set_profiling.restype = i
+    L.lrdmc_set_profiling.argtypes = [vp, i]
+    L.lrdmc_kernel_times.restype = i
+    L.lrdmc_kernel_times.argtypes = [vp, ct.POINTER(d), ct.POINTER(d), ct.POINTER(ct.c_longlong),
+                                     ct.POINTER(ct.c_longlong), i]
     L.lrdmc_last_error.restype = ct.c_char_p
     L.lrdmc_last_error.argtypes = [vp]
     L.lrdmc_destroy.restype = None
@@ -235,6 +241,17 @@ class LrdmcSystem:
         m = ct.c_longlong()
         self._check(load_library().lrdmc_moves(self.h, ct.byref(m)))
         return m.value
+
+    def set_profiling(self, on=True):
+        self._check(load_library().lrdmc_set_profiling(self.h, int(on)))
+
+    def kernel_times(self, reset=False):
+        """Accumulated (interval_ms, reconfig_ms, interval_launches, reconfig_launches)."""
+        a, b = ct.c_double(), ct.c_double()
+        na, nb = ct.c_longlong(), ct.c_longlong()
+        self._check(load_library().lrdmc_kernel_times(self.h, ct.byref(a), ct.byref(b), ct.byref(na),
+                                                      ct.byref(nb), int(reset)))
+        return a.value, b.value, na.value, nb.value
 
     def save(self, path):
         self._check(load_library().lrdmc_save(self.h, path.encode()))

@@ -36,6 +36,11 @@ struct lrdmc_system_s {
   LatDev eval_lat;
   int* err_host = nullptr;  // pinned
   int* eval_err = nullptr;  // device error word of lrdmc_evaluate
+  // kernel timing (lrdmc_set_profiling)
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;  // 4 per step: interval start/stop, reconfig start/stop
+  double t_interval_ms = 0.0, t_reconfig_ms = 0.0;
+  long long n_interval = 0, n_reconfig = 0;
   std::string last_error;
 };
 
@@ -444,6 +449,14 @@ lrdmc_status lrdmc_step(lrdmc_system_t s, int n_steps, double a, const lrdmc_spa
   lrdmc_status st = lattice_from(s, a, sp, L);
   if (st != LRDMC_OK) return st;
   cudaError_t e;
+  if (s->profiling) {
+    while (s->events.size() < 4 * (size_t)n_steps) {
+      cudaEvent_t ev;
+      e = cudaEventCreate(&ev);
+      if (e != cudaSuccess) return cuda_fail(s, e, "profiling event");
+      s->events.push_back(ev);
+    }
+  }
   PopDev P = s->P;
   if (!s->have_eval || !same_lattice(L, s->eval_lat)) {
     P.rec_src = s->rec[s->cur];
@@ -458,14 +471,33 @@ lrdmc_status lrdmc_step(lrdmc_system_t s, int n_steps, double a, const lrdmc_spa
     const int recompute = (k > 0 && s->recompute_every > 0 && k % (uint64_t)s->recompute_every == 0) ? 1 : 0;
     P.rec_src = s->rec[s->cur];
     P.rec_dst = s->rec[1 - s->cur];
+    cudaEvent_t* ev = s->profiling ? &s->events[4 * n] : nullptr;
+    if (ev) cudaEventRecord(ev[0], s->stream);
     e = launch_interval(s->S, s->Lo, L, P, k, recompute, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "k_interval launch");
+    if (ev) {
+      cudaEventRecord(ev[1], s->stream);
+      cudaEventRecord(ev[2], s->stream);
+    }
     e = launch_reconfig(P, k, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "k_reconfig launch");
+    if (ev) cudaEventRecord(ev[3], s->stream);
     s->cur = 1 - s->cur;
     s->k++;
   }
-  return read_error_word(s);
+  lrdmc_status rs = read_error_word(s);
+  if (s->profiling && rs == LRDMC_OK) {
+    for (int n = 0; n < n_steps; ++n) {
+      float a_ms = 0.f, b_ms = 0.f;
+      cudaEventElapsedTime(&a_ms, s->events[4 * n], s->events[4 * n + 1]);
+      cudaEventElapsedTime(&b_ms, s->events[4 * n + 2], s->events[4 * n + 3]);
+      s->t_interval_ms += a_ms;
+      s->t_reconfig_ms += b_ms;
+    }
+    s->n_interval += n_steps;
+    s->n_reconfig += n_steps;
+  }
+  return rs;
 }
 
 lrdmc_status lrdmc_get_energy_trace(lrdmc_system_t s, double* e_out, double* w_out, double* j_out,
@@ -626,6 +658,28 @@ lrdmc_status lrdmc_load(lrdmc_system_t s, const char* path)
   return LRDMC_OK;
 }
 
+lrdmc_status lrdmc_set_profiling(lrdmc_system_t s, int on)
+{
+  if (!s) return fail(s, LRDMC_ERR_ARG, "");
+  s->profiling = on != 0;
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_kernel_times(lrdmc_system_t s, double* interval_ms, double* reconfig_ms,
+                                long long* interval_launches, long long* reconfig_launches, int reset)
+{
+  if (!s) return fail(s, LRDMC_ERR_ARG, "");
+  if (interval_ms) *interval_ms = s->t_interval_ms;
+  if (reconfig_ms) *reconfig_ms = s->t_reconfig_ms;
+  if (interval_launches) *interval_launches = s->n_interval;
+  if (reconfig_launches) *reconfig_launches = s->n_reconfig;
+  if (reset) {
+    s->t_interval_ms = s->t_reconfig_ms = 0.0;
+    s->n_interval = s->n_reconfig = 0;
+  }
+  return LRDMC_OK;
+}
+
 const char* lrdmc_last_error(lrdmc_system_t s) { return s ? s->last_error.c_str() : g_static_error; }
 
 void lrdmc_destroy(lrdmc_system_t s)
@@ -633,6 +687,7 @@ void lrdmc_destroy(lrdmc_system_t s)
   if (!s) return;
   if (s->err_host) cudaFreeHost(s->err_host);
   if (s->eval_err) cudaFree(s->eval_err);
+  for (cudaEvent_t ev : s->events) cudaEventDestroy(ev);
   delete s;
 }
 

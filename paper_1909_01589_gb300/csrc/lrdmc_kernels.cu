@@ -352,8 +352,15 @@ __device__ bool warp_inverse(const SysDev& S, const double* sC, const double* sx
     }
   }
   __syncwarp();
-  bool ok = true;
-  for (int col = 0; col < n; ++col) {
+  // scale of the matrix: a pivot below 1e-13 of it means a numerically
+  // singular Slater matrix (e.g. two equal-spin electrons on one point)
+  double scale = 0.0;
+  for (int idx = lane; idx < n * n; idx += 32) scale = fmax(scale, fabs(M[(idx / n) * w2 + idx % n]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) scale = fmax(scale, __shfl_xor_sync(FULL_MASK, scale, o));
+  const double tiny = 1e-13 * scale;
+  bool ok = scale > 0.0;
+  for (int col = 0; col < n && ok; ++col) {
     // pivot row: largest |M[r][col]| for r >= col, lowest r on ties
     double best = -1.0;
     int br = col;
@@ -367,7 +374,7 @@ __device__ bool warp_inverse(const SysDev& S, const double* sC, const double* sx
       int orr = __shfl_xor_sync(FULL_MASK, br, o);
       if (ob > best || (ob == best && orr < br)) { best = ob; br = orr; }
     }
-    if (!(best > 0.0)) { ok = false; break; }
+    if (!(best > tiny)) { ok = false; break; }
     if (br != col) {
       for (int j = lane; j < w2; j += 32) {
         double t = M[col * w2 + j];
