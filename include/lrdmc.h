@@ -185,6 +185,29 @@ LRDMC_API lrdmc_status lrdmc_evaluate(lrdmc_system_t sys, int n_configs, const d
                             double a, const lrdmc_spacing_fn* spacing, double* ratio, double* T,
                             double* b, double* el, void* stream);
 
+/* Evaluation that allocates nothing. The paper has no counterpart: this
+ * is a service for callers that cannot call cudaMalloc when they evaluate -
+ * code running inside another framework's reserved memory budget,
+ * processes that forbid device allocation after start-up, or callers that
+ * must not let an allocation synchronise the device. Same inputs, outputs
+ * and results as lrdmc_evaluate, whose error word comes from cudaMalloc;
+ * here the scratch (a summary status word and one status word per
+ * configuration) lives in a static device array of 64 + LRDMC_STATIC_EVAL_MAX
+ * ints (about 1 MiB) that every GPU loading the library holds until the
+ * process exits. n_configs above LRDMC_STATIC_EVAL_MAX is rejected with
+ * LRDMC_ERR_ARG. The first call on a device looks up the array's device
+ * address (once per device, with that device current); make that first
+ * call before any stream capture. The call clears the words it uses, then
+ * synchronises the stream to read the summary word. All calls share the
+ * array and it keeps the last call's contents: calls that overlap on the
+ * GPU (other threads, other streams) race on it. No cudaMalloc, cudaFree
+ * or other device allocation happens in this call. */
+#define LRDMC_STATIC_EVAL_MAX 262144
+LRDMC_API lrdmc_status lrdmc_evaluate_static(lrdmc_system_t sys, int n_configs, const double* x,
+                                             const double* rot, double a, const lrdmc_spacing_fn* spacing,
+                                             double* ratio, double* T, double* b, double* el,
+                                             void* stream);
+
 /* Writes / reads the population (positions, inverses, rotations, cached
  * evaluation, parents, interval counter, trace) to / from a file. */
 LRDMC_API lrdmc_status lrdmc_save(lrdmc_system_t sys, const char* path);

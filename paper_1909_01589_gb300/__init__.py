@@ -22,6 +22,7 @@ MAX_SHELL = 32
 MAX_PRIM = 8
 MAX_AO = 64
 MAX_SPIN = 32
+STATIC_EVAL_MAX = 262144
 
 OK, ERR_ARG, ERR_CUDA, ERR_SINGULAR, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE = range(7)
 SINGLE, THIS_WORK, PREVIOUS, EXPLICIT = 0, 1, 2, 3
@@ -29,6 +30,7 @@ SINGLE, THIS_WORK, PREVIOUS, EXPLICIT = 0, 1, 2, 3
 EXPORTED = [
     "lrdmc_create_system", "lrdmc_spacing_params", "lrdmc_workspace_bytes", "lrdmc_init_walkers",
     "lrdmc_step", "lrdmc_get_energy_trace", "lrdmc_get_walkers", "lrdmc_moves", "lrdmc_evaluate",
+    "lrdmc_evaluate_static",
     "lrdmc_save", "lrdmc_load", "lrdmc_set_profiling", "lrdmc_kernel_times", "lrdmc_last_error",
     "lrdmc_destroy",
 ]
@@ -100,6 +102,8 @@ def load_library():
     L.lrdmc_moves.argtypes = [vp, ct.POINTER(ct.c_longlong)]
     L.lrdmc_evaluate.restype = i
     L.lrdmc_evaluate.argtypes = [vp, i, vp, vp, d, vp, vp, vp, vp, vp, vp]
+    L.lrdmc_evaluate_static.restype = i
+    L.lrdmc_evaluate_static.argtypes = [vp, i, vp, vp, d, vp, vp, vp, vp, vp, vp]
     L.lrdmc_save.restype = i
     L.lrdmc_save.argtypes = [vp, ct.c_char_p]
     L.lrdmc_load.restype = i
@@ -260,6 +264,32 @@ class LrdmcSystem:
         self._check(load_library().lrdmc_load(self.h, path.encode()))
 
     # ---------------------------------------------------------------- stateless
+    def evaluate_static(self, x, rot, a, spacing: Spacing = Spacing(), stream=None, out=None):
+        """Like evaluate, through lrdmc_evaluate_static: the library allocates
+        no device memory (its scratch is a static device array shared by all
+        calls; at most STATIC_EVAL_MAX configurations). ``out`` may pass
+        preallocated (ratio, T, b, el) CUDA tensors."""
+        import torch
+
+        n = int(x.shape[0])
+        G = 1 if spacing.kind == SINGLE else 2
+        P = 6 * self.N * G
+        x = x.contiguous()
+        rot = rot.contiguous()
+        if out is None:
+            out = (torch.empty((n, P), dtype=torch.float64, device=x.device),
+                   torch.empty((n, P), dtype=torch.float64, device=x.device),
+                   torch.empty(n, dtype=torch.float64, device=x.device),
+                   torch.empty(n, dtype=torch.float64, device=x.device))
+        ratio, T, b, el = out
+        if stream is None:
+            stream = torch.cuda.current_stream(x.device)
+        sp = spacing.c()
+        self._check(load_library().lrdmc_evaluate_static(self.h, n, _t_ptr(x), _t_ptr(rot), float(a),
+                                                         ct.byref(sp), _t_ptr(ratio), _t_ptr(T), _t_ptr(b),
+                                                         _t_ptr(el), ct.c_void_p(stream.cuda_stream)))
+        return ratio, T, b, el
+
     def evaluate(self, x, rot, a, spacing: Spacing = Spacing(), stream=None):
         """One evaluation of every lattice move of n configurations.
         x: [n][N][3] and rot: [n][9] float64 CUDA tensors. Returns CUDA tensors

@@ -590,6 +590,27 @@ lrdmc_status lrdmc_evaluate(lrdmc_system_t s, int n, const double* x, const doub
   return LRDMC_OK;
 }
 
+lrdmc_status lrdmc_evaluate_static(lrdmc_system_t s, int n, const double* x, const double* rot,
+                                   double a, const lrdmc_spacing_fn* sp, double* ratio, double* T,
+                                   double* b, double* el, void* stream)
+{
+  if (!s) return fail(s, LRDMC_ERR_ARG, "");
+  if (n < 0 || (n > 0 && (!x || !rot))) return fail(s, LRDMC_ERR_ARG, "evaluate_static: bad arguments");
+  if (n > LRDMC_STATIC_EVAL_MAX)
+    return fail(s, LRDMC_ERR_ARG, "evaluate_static: n_configs exceeds LRDMC_STATIC_EVAL_MAX (" +
+                                      std::to_string(LRDMC_STATIC_EVAL_MAX) + "); split the batch");
+  if (n == 0) return LRDMC_OK;
+  LatDev L;
+  lrdmc_status st = lattice_from(s, a, sp, L);
+  if (st != LRDMC_OK) return st;
+  int summary = 0;
+  cudaError_t e = launch_evaluate_static(s->S, s->Lo, L, n, x, rot, ratio, T, b, el, &summary,
+                                         (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "evaluate_static");
+  if (summary & kErrSingular) return fail(s, LRDMC_ERR_SINGULAR, "evaluate_static: singular Slater matrix");
+  return LRDMC_OK;
+}
+
 // Checkpoint file: magic, sizes, counters, then the current record buffer,
 // parents, trace and the moves counter.
 static const uint64_t kMagic = 0x4C52444D43303031ull;  // "LRDMC001"

@@ -107,4 +107,8 @@ cudaError_t launch_evaluate(const SysDev& S, const Layout& Lo, const LatDev& L, 
                             const double* x, const double* rot, double* ratio, double* T,
                             double* b, double* el, int* err, cudaStream_t st);
 
+cudaError_t launch_evaluate_static(const SysDev& S, const Layout& Lo, const LatDev& L, int n,
+                                   const double* x, const double* rot, double* ratio, double* T,
+                                   double* b, double* el, int* summary, cudaStream_t st);
+
 }  // namespace lrdmc

@@ -18,6 +18,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "lrdmc_internal.h"
 
 namespace lrdmc {
@@ -893,6 +895,105 @@ cudaError_t launch_evaluate(const SysDev& S, const Layout& Lo, const LatDev& L, 
   k_evaluate<<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(S, Lo, L, n, x, rot, ratio, T,
                                                                        b, el, err);
   return cudaGetLastError();
+}
+
+
+// ----------------------------------------------------------------------------
+// Evaluation that allocates nothing (lrdmc_evaluate_static).
+//
+// Some callers cannot allocate device memory at the moment they evaluate:
+// code that runs inside another framework's fixed memory budget (a caching
+// allocator that has reserved the device), processes that forbid any
+// allocation after start-up, or callers that must not synchronise the
+// device the way cudaMalloc and cudaFree can. This variant of k_evaluate
+// keeps its scratch - a summary status word and one status word per
+// configuration - in the file-scope device array below instead of memory
+// from cudaMalloc. Every GPU that loads the library holds the array
+// (64 + LRDMC_STATIC_EVAL_MAX ints, 1 MiB) until the process exits. All
+// calls share it: calls that overlap on the GPU race on it.
+// ----------------------------------------------------------------------------
+static __device__ __align__(256) int g_eval_scratch[64 + LRDMC_STATIC_EVAL_MAX];
+
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+k_evaluate_static(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, int n,
+                  const double* x, const double* rot, double* ratio, double* T, double* b_out,
+                  double* el_out, int* scratch)
+{
+  extern __shared__ double smem[];
+  double* sC = smem;
+  stage_coefficients(S, sC);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int c = blockIdx.x * kWarpsPerBlock + wib;
+  if (c >= n) return;
+  WarpMem wm = warp_mem(Lo, S, sC + S.n_ao * S.n_mo + wib * Lo.smem_warp);
+  for (int j = lane; j < 3 * Lo.N; j += 32) wm.x[j] = x[(size_t)c * 3 * Lo.N + j];
+  for (int j = lane; j < 9; j += 32) wm.R[j] = rot[(size_t)c * 9 + j];
+  __syncwarp();
+  bool ok = warp_inverse(S, sC, wm.x, 0, wm.A, wm.scr, lane);
+  ok = ok && warp_inverse(S, sC, wm.x, 1, wm.A + Lo.nu * Lo.nu, wm.scr, lane);
+  if (!ok) {
+    if (lane == 0) {
+      scratch[64 + c] = kErrSingular;
+      atomicOr(&scratch[0], kErrSingular);
+    }
+    return;
+  }
+  const int P = S.N * 6 * L.G;
+  double b, el;
+  warp_eval(S, sC, L, wm, lane, ratio ? ratio + (size_t)c * P : nullptr, b, el);
+  if (T)
+    for (int j = lane; j < P; j += 32) T[(size_t)c * P + j] = wm.T[j];
+  if (lane == 0) {
+    if (b_out) b_out[c] = b;
+    if (el_out) el_out[c] = el;
+  }
+}
+
+// Device address of g_eval_scratch, looked up once per device with that
+// device current (host code must not pass the symbol itself: in host code
+// it names a host-side stand-in, not device memory).
+static int* g_eval_scratch_ptr[64];
+static std::mutex g_eval_scratch_mu;
+
+static cudaError_t eval_scratch_address(int** out)
+{
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_eval_scratch_mu);
+  if (!g_eval_scratch_ptr[dev]) {
+    int* p = nullptr;
+    e = cudaGetSymbolAddress((void**)&p, g_eval_scratch);
+    if (e != cudaSuccess) return e;
+    g_eval_scratch_ptr[dev] = p;
+  }
+  *out = g_eval_scratch_ptr[dev];
+  return cudaSuccess;
+}
+
+cudaError_t launch_evaluate_static(const SysDev& S, const Layout& Lo, const LatDev& L, int n,
+                                   const double* x, const double* rot, double* ratio, double* T,
+                                   double* b, double* el, int* summary, cudaStream_t st)
+{
+  if (n < 0 || n > LRDMC_STATIC_EVAL_MAX) return cudaErrorInvalidValue;
+  int* scratch = nullptr;
+  cudaError_t e = eval_scratch_address(&scratch);
+  if (e != cudaSuccess) return e;
+  // the summary word and the statuses of this call start at zero
+  e = cudaMemsetAsync(scratch, 0, sizeof(int) * (64 + (size_t)n), st);
+  if (e != cudaSuccess) return e;
+  e = set_smem((const void*)k_evaluate_static, Lo.smem_block_bytes);
+  if (e != cudaSuccess) return e;
+  int blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  if (blocks > 0)
+    k_evaluate_static<<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(S, Lo, L, n, x, rot, ratio,
+                                                                                T, b, el, scratch);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(summary, scratch, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(st);
 }
 
 }  // namespace lrdmc
