@@ -151,7 +151,8 @@ def run_ours(args):
     a = WORKLOAD["a"]
     seed = SEED + 7919 * rank
     x0 = S.initial_positions(system, W, seed)
-    g = pkg.LrdmcSystem(system)
+    prec = pkg.PRECISION_DF64 if args.precision == "df64" else pkg.PRECISION_FP64
+    g = pkg.LrdmcSystem(system).set_precision(prec)
     cap = args.warmup + args.steps + 8
     g.init_walkers(torch.tensor(x0, device=dev), seed=seed, tau=WORKLOAD["tau"], e_trial=WORKLOAD["e_trial"],
                    recompute_every=WORKLOAD["recompute_every"], trace_capacity=cap)
@@ -189,7 +190,7 @@ def run_ours(args):
     x0h = torch.tensor(x0).pin_memory()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    g2 = pkg.LrdmcSystem(system)
+    g2 = pkg.LrdmcSystem(system).set_precision(prec)
     g2.init_walkers(x0h.numpy(), seed=seed, tau=WORKLOAD["tau"], e_trial=WORKLOAD["e_trial"],
                     recompute_every=WORKLOAD["recompute_every"], trace_capacity=cap)
     d2h = 0
@@ -235,10 +236,10 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": "f32x2 (double-float evaluation) + f64 state" if args.precision == "df64" else "f64",
         "data": "synthetic",
         "config": {"workload": "Ne all-electron, 4096 walkers, a=0.2 bohr, smart double grid (this work), "
-                               "tau=0.025, FP64", **WORKLOAD,
+                               "tau=0.025, FP64-parity arithmetic", **WORKLOAD, "evaluation": args.precision,
                    "walkers_per_gpu": W, "l2": "flushed between timed steps (512 MiB write)",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_all / t_e2e_all, "unit": "walker-moves/s",
@@ -339,6 +340,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="CPU-baseline budget (<= 0: no CPU baseline)")
+    ap.add_argument("--precision", default="df64", choices=["df64", "fp64"],
+                    help="evaluation arithmetic: double-float on the FP32 pipe or IEEE double")
     ap.add_argument("--walkers", type=int, default=WORKLOAD["n_walkers"],
                     help="walkers per GPU (smaller cases for profiling)")
     args = ap.parse_args()

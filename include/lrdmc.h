@@ -213,6 +213,20 @@ LRDMC_API lrdmc_status lrdmc_evaluate_static(lrdmc_system_t sys, int n_configs, 
 LRDMC_API lrdmc_status lrdmc_save(lrdmc_system_t sys, const char* path);
 LRDMC_API lrdmc_status lrdmc_load(lrdmc_system_t sys, const char* path);
 
+/* Arithmetic of the evaluation kernels. LRDMC_PRECISION_FP64 runs every
+ * step in IEEE double on the FP64 pipe. LRDMC_PRECISION_DF64 (default)
+ * evaluates the lattice moves and the local energy in double-float
+ * arithmetic on the FP32 pipe (pairs of floats, about 48 significant bits,
+ * relative error ~1e-14; GB300 runs FP64 at 1/69 of its FP32 rate) and
+ * keeps the inverse Slater matrices, Sherman-Morrison updates, weights,
+ * heat bath and reconfiguration in IEEE double. Values below about 1e-30
+ * lose low-order bits in double-float (their contribution to any sum is
+ * then negligible); arguments of exp below -87 give 0. Takes effect at the
+ * next lrdmc_step / lrdmc_evaluate call. */
+#define LRDMC_PRECISION_FP64 0
+#define LRDMC_PRECISION_DF64 1
+LRDMC_API lrdmc_status lrdmc_set_precision(lrdmc_system_t sys, int precision);
+
 /* Kernel timing for measurement. With profiling on, lrdmc_step brackets
  * every launch of its interval kernel and of its reconfiguration kernel
  * with CUDA events on the system's stream and accumulates their durations

@@ -26,12 +26,13 @@ STATIC_EVAL_MAX = 262144
 
 OK, ERR_ARG, ERR_CUDA, ERR_SINGULAR, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE = range(7)
 SINGLE, THIS_WORK, PREVIOUS, EXPLICIT = 0, 1, 2, 3
+PRECISION_FP64, PRECISION_DF64 = 0, 1
 
 EXPORTED = [
     "lrdmc_create_system", "lrdmc_spacing_params", "lrdmc_workspace_bytes", "lrdmc_init_walkers",
     "lrdmc_step", "lrdmc_get_energy_trace", "lrdmc_get_walkers", "lrdmc_moves", "lrdmc_evaluate",
     "lrdmc_evaluate_static",
-    "lrdmc_save", "lrdmc_load", "lrdmc_set_profiling", "lrdmc_kernel_times", "lrdmc_last_error",
+    "lrdmc_save", "lrdmc_load", "lrdmc_set_precision", "lrdmc_set_profiling", "lrdmc_kernel_times", "lrdmc_last_error",
     "lrdmc_destroy",
 ]
 
@@ -108,6 +109,8 @@ def load_library():
     L.lrdmc_save.argtypes = [vp, ct.c_char_p]
     L.lrdmc_load.restype = i
     L.lrdmc_load.argtypes = [vp, ct.c_char_p]
+    L.lrdmc_set_precision.restype = i
+    L.lrdmc_set_precision.argtypes = [vp, i]
     L.lrdmc_set_profiling.restype = i
     L.lrdmc_set_profiling.argtypes = [vp, i]
     L.lrdmc_kernel_times.restype = i
@@ -245,6 +248,12 @@ class LrdmcSystem:
         m = ct.c_longlong()
         self._check(load_library().lrdmc_moves(self.h, ct.byref(m)))
         return m.value
+
+    def set_precision(self, precision):
+        """PRECISION_FP64 (IEEE double everywhere) or PRECISION_DF64 (default:
+        double-float evaluation on the FP32 pipe, FP64 state and updates)."""
+        self._check(load_library().lrdmc_set_precision(self.h, int(precision)))
+        return self
 
     def set_profiling(self, on=True):
         self._check(load_library().lrdmc_set_profiling(self.h, int(on)))

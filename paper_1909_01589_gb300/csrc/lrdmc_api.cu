@@ -188,6 +188,7 @@ static lrdmc_status lattice_from(lrdmc_system_t s, double a, const lrdmc_spacing
       L.G = 1;
       L.ap = a;
       L.inv2ap2 = L.inv2a2;
+      fill_lattice_df(L);
       return LRDMC_OK;
     case LRDMC_DOUBLE_THIS_WORK: {
       if (!(sp->beta > 0.0) || !(sp->kappa > 0.0)) return fail(s, LRDMC_ERR_ARG, "beta and kappa must be > 0");
@@ -219,6 +220,7 @@ static lrdmc_status lattice_from(lrdmc_system_t s, double a, const lrdmc_spacing
   L.inv2ap2 = 0.5 / (L.ap * L.ap);
   L.rc = rc;
   L.p_coef = (L.pkind == 0) ? 1.0 / (2.0 * rc * rc) : rc * rc;
+  fill_lattice_df(L);
   return LRDMC_OK;
 }
 
@@ -314,6 +316,8 @@ lrdmc_status lrdmc_create_system(int n_nuc, const double* nuc_xyz, const double*
     return LRDMC_ERR_ARG;
   }
   for (int j = 0; j < n_ao * n_mo; ++j) S.C[j] = mo_coeff[j];
+  S.precision = LRDMC_PRECISION_DF64;
+  fill_df_constants(S);
   s->Lo = make_layout(S);
   *out = s;
   return LRDMC_OK;
@@ -676,6 +680,15 @@ lrdmc_status lrdmc_load(lrdmc_system_t s, const char* path)
   s->k = (uint64_t)hdr[4];
   s->have_eval = hdr[5] != 0;
   s->eval_lat = L;
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_set_precision(lrdmc_system_t s, int precision)
+{
+  if (!s) return fail(s, LRDMC_ERR_ARG, "");
+  if (precision != LRDMC_PRECISION_FP64 && precision != LRDMC_PRECISION_DF64)
+    return fail(s, LRDMC_ERR_ARG, "set_precision: unknown precision");
+  s->S.precision = precision;
   return LRDMC_OK;
 }
 

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "../../include/lrdmc.h"
+#include "df64.cuh"
 
 namespace lrdmc {
 
@@ -41,6 +42,22 @@ struct ShellDev {
   double coef[kMaxPrim];
 };
 
+// Double-float copies of the constants the double-float evaluation reads
+// (split on the host so that no kernel converts them on the FP64 pipe).
+struct DfShell {
+  df m, zeta;
+  df alpha[kMaxPrim], coef[kMaxPrim];
+};
+
+struct DfSys {
+  df nuc[kMaxNuc][3];
+  df Z[kMaxNuc];
+  df en_b1[kMaxNuc];
+  df b_ee, c_par, c_anti, en_b2;
+  DfShell sh[kMaxShell];
+  ExpTable exp;
+};
+
 // Trial function and Hamiltonian constants, passed by value as a kernel
 // parameter (__grid_constant__); the MO coefficients are staged in shared
 // memory by every block.
@@ -55,6 +72,9 @@ struct SysDev {
   double V_nn;
   ShellDev sh[kMaxShell];
   double C[kMaxAO * kMaxMO];  // [n_ao][n_mo]
+  int precision;  // LRDMC_PRECISION_FP64 or LRDMC_PRECISION_DF64
+  int pad;
+  DfSys D;
 };
 
 struct LatDev {
@@ -65,6 +85,8 @@ struct LatDev {
   double p_coef;    // Gaussian: 1/(2 r_c^2); Pade: r_c^2
   int G;            // 1 single grid, 2 double grid
   int pkind;        // 0 Gaussian (Eq. 3), 1 Pade (Eq. 2)
+  // the same values as double-floats
+  df a_df, ap_df, inv2a2_df, inv2ap2_df, p_coef_df;
 };
 
 // Walker record layout (doubles) in the double-buffered population.
@@ -72,6 +94,7 @@ struct Layout {
   int N, nu, nd, P_max;
   int off_x, off_au, off_ad, off_R, off_T, off_b, off_el;
   int rec;  // doubles per record (multiple of 4)
+  int head;       // doubles of shared memory per block before the warp regions
   int smem_warp;  // doubles of shared memory per warp
   int smem_block_bytes;
 };
@@ -95,6 +118,9 @@ struct PopDev {
   uint64_t seed;
   double tau, e_trial;
 };
+
+void fill_df_constants(SysDev& S);
+void fill_lattice_df(LatDev& L);
 
 cudaError_t launch_init(const SysDev& S, const Layout& Lo, const PopDev& P, const double* x0,
                         cudaStream_t st);

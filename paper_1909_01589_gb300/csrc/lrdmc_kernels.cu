@@ -314,6 +314,10 @@ struct WarpMem {
   double* T;    // [P_max]
   double* v;    // [N][n_ao]
   double* Ssum; // [N]
+  df* xd;       // [N][3]      double-float copies for the DF64 evaluation
+  df* vd;       // [N][n_ao]
+  df* Sd;       // [N]
+  df* Rd;       // [12]
   double* scr;  // scratch
 };
 
@@ -326,8 +330,28 @@ __device__ __forceinline__ WarpMem warp_mem(const Layout& Lo, const SysDev& S, d
   m.T = m.R + 12;
   m.v = m.T + Lo.P_max;
   m.Ssum = m.v + Lo.N * S.n_ao;
-  m.scr = m.Ssum + Lo.N;
+  m.xd = reinterpret_cast<df*>(m.Ssum + Lo.N);
+  m.vd = m.xd + 3 * Lo.N;
+  m.Sd = m.vd + Lo.N * S.n_ao;
+  m.Rd = m.Sd + Lo.N;
+  m.scr = reinterpret_cast<double*>(m.Rd + 12);
   return m;
+}
+
+// Block-shared tables: MO coefficients, then the 2^(j/64) table (floats).
+struct BlockMem {
+  double* C;
+  float* thi;
+  float* tlo;
+};
+
+__device__ __forceinline__ BlockMem block_mem(const SysDev& S, double* smem)
+{
+  BlockMem b;
+  b.C = smem;
+  b.thi = reinterpret_cast<float*>(smem + S.n_ao * S.n_mo);
+  b.tlo = b.thi + 64;
+  return b;
 }
 
 // ----------------------------------------------------------------------------
@@ -496,6 +520,355 @@ __device__ void warp_eval(const SysDev& S, const double* sC, const LatDev& L, co
 }
 
 // ----------------------------------------------------------------------------
+// The same evaluation in double-float arithmetic on the FP32 pipe
+// (LRDMC_PRECISION_DF64). Inputs are converted once per evaluation
+// (positions, rotation, projected inverse columns); every lattice move and
+// the local energy are computed in double-float; rates and the local energy
+// are converted back to double.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ df dfz() { return df_make(0.0f, 0.0f); }
+
+__device__ __forceinline__ df df_dot3(df a0, df a1, df a2)
+{
+  return df_add_fast(df_add_fast(df_sqr(a0), df_sqr(a1)), df_sqr(a2));
+}
+
+// Slater radial part r^m e^(-zeta r) as double-float (e given).
+__device__ __forceinline__ df radial_value_df(const SysDev& S, const ShellDev& sh, const DfShell& dsh,
+                                              df r, df r2, df e, const BlockMem& bm)
+{
+  if (sh.kind == 0) {
+    if (sh.m_int >= 0) {
+      df pw = df_make(1.0f, 0.0f);
+      for (int j = 0; j < sh.m_int; ++j) pw = df_mul(pw, r);
+      return df_mul(pw, e);
+    }
+    df lr = df_log(r, S.D.exp.K, bm.thi, bm.tlo);
+    return df_mul(df_exp(df_mul(dsh.m, lr), S.D.exp.K, bm.thi, bm.tlo), e);
+  }
+  df R = dfz();
+  for (int p = 0; p < sh.n_prim; ++p)
+    R = df_add(R, df_mul(dsh.coef[p], df_exp(df_neg(df_mul(dsh.alpha[p], r2)), S.D.exp.K, bm.thi, bm.tlo)));
+  return R;
+}
+
+__device__ __forceinline__ int solid_df(int l, const df d[3], df Sv[5])
+{
+  if (l == 0) {
+    Sv[0] = df_make(1.0f, 0.0f);
+    return 1;
+  }
+  if (l == 1) {
+    Sv[0] = d[0]; Sv[1] = d[1]; Sv[2] = d[2];
+    return 3;
+  }
+  df xx = df_sqr(d[0]), yy = df_sqr(d[1]), zz = df_sqr(d[2]);
+  Sv[0] = df_mul(d[0], d[1]);
+  Sv[1] = df_mul(d[1], d[2]);
+  Sv[2] = df_mul(d[2], d[0]);
+  Sv[3] = df_sub(xx, yy);
+  Sv[4] = df_sub(df_add(zz, zz), df_add(xx, yy));
+  return 5;
+}
+
+// Sum_mu v[mu] chi_mu(p) in double-float.
+__device__ df ao_dot_df(const SysDev& S, const df* v, const df p[3], const BlockMem& bm)
+{
+  df acc = dfz();
+  int prev_c = -1;
+  df d[3] = {dfz(), dfz(), dfz()}, r = dfz(), r2 = dfz(), e = dfz();
+  for (int q = 0; q < S.n_shell; ++q) {
+    const ShellDev& sh = S.sh[q];
+    const DfShell& dsh = S.D.sh[q];
+    if (sh.center != prev_c) {
+      prev_c = sh.center;
+      d[0] = df_sub_fast(p[0], S.D.nuc[prev_c][0]);
+      d[1] = df_sub_fast(p[1], S.D.nuc[prev_c][1]);
+      d[2] = df_sub_fast(p[2], S.D.nuc[prev_c][2]);
+      r2 = df_dot3(d[0], d[1], d[2]);
+      r = df_sqrt(r2);
+    }
+    if (sh.kind == 0 && !sh.same_exp) e = df_exp(df_neg(df_mul(dsh.zeta, r)), S.D.exp.K, bm.thi, bm.tlo);
+    df R = radial_value_df(S, sh, dsh, r, r2, e, bm);
+    df Sv[5];
+    int nf = solid_df(sh.l, d, Sv);
+    df part = dfz();
+    for (int f = 0; f < nf; ++f) part = df_add(part, df_mul(v[sh.ao_offset + f], Sv[f]));
+    acc = df_add(acc, df_mul(part, R));
+  }
+  return acc;
+}
+
+// sum_{j != i} u_ee(|p - r_j|) + sum_I u_en(|p - R_I|) in double-float.
+__device__ df jastrow_terms_df(const SysDev& S, const df* xd, int i, const df p[3])
+{
+  df acc = dfz();
+  const int si = spin_of(S, i);
+  for (int j = 0; j < S.N; ++j) {
+    if (j == i) continue;
+    df d0 = df_sub_fast(p[0], xd[3 * j]), d1 = df_sub_fast(p[1], xd[3 * j + 1]), d2 = df_sub_fast(p[2], xd[3 * j + 2]);
+    df r = df_sqrt(df_dot3(d0, d1, d2));
+    df c = (spin_of(S, j) == si) ? S.D.c_par : S.D.c_anti;
+    df den = df_add_f(df_mul(S.D.b_ee, r), 1.0f);
+    acc = df_add_fast(acc, df_div(df_mul(c, r), den));
+  }
+  for (int I = 0; I < S.n_nuc; ++I) {
+    df d0 = df_sub_fast(p[0], S.D.nuc[I][0]), d1 = df_sub_fast(p[1], S.D.nuc[I][1]), d2 = df_sub_fast(p[2], S.D.nuc[I][2]);
+    df r = df_sqrt(df_dot3(d0, d1, d2));
+    df den = df_add_f(df_mul(S.D.en_b2, r), 1.0f);
+    acc = df_sub(acc, df_div(df_mul(S.D.en_b1[I], r), den));
+  }
+  return acc;
+}
+
+__device__ __forceinline__ df p_weight_df(const SysDev& S, const LatDev& L, const df m[3], const BlockMem& bm)
+{
+  df best = df_make(INFINITY, 0.0f);
+  for (int I = 0; I < S.n_nuc; ++I) {
+    if (!S.heavy[I]) continue;
+    df d0 = df_sub_fast(m[0], S.D.nuc[I][0]), d1 = df_sub_fast(m[1], S.D.nuc[I][1]), d2 = df_sub_fast(m[2], S.D.nuc[I][2]);
+    df d2s = df_dot3(d0, d1, d2);
+    if (d2s.hi < best.hi || (d2s.hi == best.hi && d2s.lo < best.lo)) best = d2s;
+  }
+  if (L.pkind == 0) return df_exp(df_neg(df_mul(best, L.p_coef_df)), S.D.exp.K, bm.thi, bm.tlo);
+  return df_rcp(df_add_f(df_mul(L.p_coef_df, best), 1.0f));
+}
+
+__device__ __forceinline__ df shfl_df(df v, int src)
+{
+  return df_make(__shfl_sync(FULL_MASK, v.hi, src), __shfl_sync(FULL_MASK, v.lo, src));
+}
+
+__device__ __forceinline__ df warp_sum_df(df v)
+{
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    v = df_add(v, df_make(__shfl_xor_sync(FULL_MASK, v.hi, o), __shfl_xor_sync(FULL_MASK, v.lo, o)));
+  return v;
+}
+
+// Partial sums of the local energy of electron i over the shells q, the
+// electrons j and the nuclei I congruent to part modulo L.
+struct ElParts {
+  df gD[3], lD, gJ[3], lJ, S, V;
+};
+
+__device__ __forceinline__ void el_zero(ElParts& o)
+{
+  o.lD = dfz(); o.lJ = dfz(); o.S = dfz(); o.V = dfz();
+  for (int k = 0; k < 3; ++k) { o.gD[k] = dfz(); o.gJ[k] = dfz(); }
+}
+
+__device__ void el_parts_df(const SysDev& S, const WarpMem& wm, int i, int part, int L, const BlockMem& bm,
+                            ElParts& o)
+{
+  const int nao = S.n_ao;
+  const df* v = &wm.vd[i * nao];
+  const df* ri = &wm.xd[3 * i];
+  el_zero(o);
+  // basis: gradient and Laplacian contracted with v. Shells sharing one
+  // Slater exponential form a group; groups are dealt to the parts.
+  int prev_c = -1, grp = -1;
+  df d[3] = {dfz(), dfz(), dfz()}, r = dfz(), r2 = dfz(), ir = dfz(), e = dfz();
+  for (int q = 0; q < S.n_shell; ++q) {
+    const ShellDev& sh = S.sh[q];
+    const DfShell& dsh = S.D.sh[q];
+    if (!(sh.kind == 0 && sh.same_exp)) ++grp;
+    if ((grp % L) != part) continue;
+    if (sh.center != prev_c) {
+      prev_c = sh.center;
+      d[0] = df_sub_fast(ri[0], S.D.nuc[prev_c][0]);
+      d[1] = df_sub_fast(ri[1], S.D.nuc[prev_c][1]);
+      d[2] = df_sub_fast(ri[2], S.D.nuc[prev_c][2]);
+      r2 = df_dot3(d[0], d[1], d[2]);
+      r = df_sqrt(r2);
+      ir = df_rcp(r);
+    }
+    if (sh.kind == 0 && !sh.same_exp) e = df_exp(df_neg(df_mul(dsh.zeta, r)), S.D.exp.K, bm.thi, bm.tlo);
+    df R, R1, R2;
+    if (sh.kind == 0) {
+      R = radial_value_df(S, sh, dsh, r, r2, e, bm);
+      df t = df_sub(df_mul(dsh.m, ir), dsh.zeta);
+      R1 = df_mul(df_mul(t, R), ir);
+      R2 = df_mul(df_sub(df_sqr(t), df_mul(dsh.m, df_sqr(ir))), R);
+    } else {
+      R = dfz(); R1 = dfz(); R2 = dfz();
+      for (int p = 0; p < sh.n_prim; ++p) {
+        df al = dsh.alpha[p];
+        df g = df_mul(dsh.coef[p], df_exp(df_neg(df_mul(al, r2)), S.D.exp.K, bm.thi, bm.tlo));
+        R = df_add(R, g);
+        df m2a = df_mul_f(al, -2.0f);
+        R1 = df_add(R1, df_mul(m2a, g));
+        df four_a2r2 = df_mul_f(df_mul(df_sqr(al), r2), 4.0f);
+        R2 = df_add(R2, df_mul(df_add(four_a2r2, m2a), g));
+      }
+    }
+    df Sv[5];
+    int nf = solid_df(sh.l, d, Sv);
+    df radlap = df_add(R2, df_mul_f(R1, 2.0f * (sh.l + 1)));
+    for (int f = 0; f < nf; ++f) {
+      df c = v[sh.ao_offset + f];
+      df cS = df_mul(c, Sv[f]);
+      // grad S of the solid harmonics
+      df gS[3];
+      if (sh.l == 0) { gS[0] = dfz(); gS[1] = dfz(); gS[2] = dfz(); }
+      else if (sh.l == 1) { gS[0] = dfz(); gS[1] = dfz(); gS[2] = dfz(); gS[f] = df_make(1.0f, 0.0f); }
+      else {
+        switch (f) {
+          case 0: gS[0] = d[1]; gS[1] = d[0]; gS[2] = dfz(); break;
+          case 1: gS[0] = dfz(); gS[1] = d[2]; gS[2] = d[1]; break;
+          case 2: gS[0] = d[2]; gS[1] = dfz(); gS[2] = d[0]; break;
+          case 3: gS[0] = df_mul_f(d[0], 2.0f); gS[1] = df_mul_f(d[1], -2.0f); gS[2] = dfz(); break;
+          default: gS[0] = df_mul_f(d[0], -2.0f); gS[1] = df_mul_f(d[1], -2.0f); gS[2] = df_mul_f(d[2], 4.0f); break;
+        }
+      }
+      df cSR1 = df_mul(cS, R1);
+      for (int k = 0; k < 3; ++k)
+        o.gD[k] = df_add(o.gD[k], df_add(df_mul(df_mul(c, R), gS[k]), df_mul(cSR1, d[k])));
+      o.lD = df_add(o.lD, df_mul(cS, radlap));
+    }
+  }
+  // e-e pairs
+  const int si = spin_of(S, i);
+  for (int j = part; j < S.N; j += L) {
+    if (j == i) continue;
+    df d0 = df_sub_fast(ri[0], wm.xd[3 * j]), d1 = df_sub_fast(ri[1], wm.xd[3 * j + 1]), d2 = df_sub_fast(ri[2], wm.xd[3 * j + 2]);
+    df rr = df_sqrt(df_dot3(d0, d1, d2));
+    df c = (spin_of(S, j) == si) ? S.D.c_par : S.D.c_anti;
+    df inv = df_rcp(df_add_f(df_mul(S.D.b_ee, rr), 1.0f));
+    df inv2 = df_sqr(inv);
+    df u1 = df_mul(c, inv2);
+    df u2 = df_mul_f(df_mul(df_mul(S.D.b_ee, c), df_mul(inv2, inv)), -2.0f);
+    df irr = df_rcp(rr);
+    df u1ir = df_mul(u1, irr);
+    o.gJ[0] = df_add(o.gJ[0], df_mul(u1ir, d0));
+    o.gJ[1] = df_add(o.gJ[1], df_mul(u1ir, d1));
+    o.gJ[2] = df_add(o.gJ[2], df_mul(u1ir, d2));
+    o.lJ = df_add(o.lJ, df_add(u2, df_mul_f(u1ir, 2.0f)));
+    o.S = df_add(o.S, df_mul(df_mul(c, rr), inv));
+    if (j > i && S.ee_on) o.V = df_add(o.V, irr);
+  }
+  // e-n terms
+  for (int I = part; I < S.n_nuc; I += L) {
+    df d0 = df_sub_fast(ri[0], S.D.nuc[I][0]), d1 = df_sub_fast(ri[1], S.D.nuc[I][1]), d2 = df_sub_fast(ri[2], S.D.nuc[I][2]);
+    df rr = df_sqrt(df_dot3(d0, d1, d2));
+    df b1 = S.D.en_b1[I];
+    df inv = df_rcp(df_add_f(df_mul(S.D.en_b2, rr), 1.0f));
+    df inv2 = df_sqr(inv);
+    df u1 = df_neg(df_mul(b1, inv2));
+    df u2 = df_mul_f(df_mul(df_mul(S.D.en_b2, b1), df_mul(inv2, inv)), 2.0f);
+    df irr = df_rcp(rr);
+    df u1ir = df_mul(u1, irr);
+    o.gJ[0] = df_add(o.gJ[0], df_mul(u1ir, d0));
+    o.gJ[1] = df_add(o.gJ[1], df_mul(u1ir, d1));
+    o.gJ[2] = df_add(o.gJ[2], df_mul(u1ir, d2));
+    o.lJ = df_add(o.lJ, df_add(u2, df_mul_f(u1ir, 2.0f)));
+    o.S = df_sub(o.S, df_mul(df_mul(b1, rr), inv));
+    o.V = df_sub(o.V, df_mul(S.D.Z[I], irr));
+  }
+}
+
+__device__ __forceinline__ void el_combine(ElParts& o, int src, bool take)
+{
+  df t;
+#define ELC(field)                         \
+  t = shfl_df(o.field, src);               \
+  if (take) o.field = df_add(o.field, t);
+  ELC(lD) ELC(lJ) ELC(S) ELC(V)
+  ELC(gD[0]) ELC(gD[1]) ELC(gD[2]) ELC(gJ[0]) ELC(gJ[1]) ELC(gJ[2])
+#undef ELC
+}
+
+__device__ __forceinline__ df el_local(const ElParts& o)
+{
+  df dot = df_add(df_add(df_mul(o.gD[0], o.gJ[0]), df_mul(o.gD[1], o.gJ[1])), df_mul(o.gD[2], o.gJ[2]));
+  df gg = df_add(df_add(df_sqr(o.gJ[0]), df_sqr(o.gJ[1])), df_sqr(o.gJ[2]));
+  df lap = df_add(df_add(o.lD, df_mul_f(dot, 2.0f)), df_add(o.lJ, gg));
+  return df_add(df_mul_f(lap, -0.5f), o.V);
+}
+
+__device__ void warp_eval_df(const SysDev& S, const double* sC, const LatDev& L, const WarpMem& wm,
+                             int lane, double* ratio_out, double& b, double& el)
+{
+  const int N = S.N, nao = S.n_ao, nu = S.n_up;
+  const BlockMem bm = block_mem(S, const_cast<double*>(sC));
+  // projected inverse columns in FP64, then converted with the positions
+  for (int idx = lane; idx < N * nao; idx += 32) {
+    int i = idx / nao, mu = idx % nao;
+    int spin = i < nu ? 0 : 1, l = i < nu ? i : i - nu, n = spin ? S.n_dn : nu;
+    const double* A = spin ? wm.A + nu * nu : wm.A;
+    double acc = 0.0;
+    for (int m = 0; m < n; ++m) acc += sC[mu * S.n_mo + m] * A[m * n + l];
+    wm.vd[idx] = df_from_double(acc);
+  }
+  for (int j = lane; j < 3 * N; j += 32) wm.xd[j] = df_from_double(wm.x[j]);
+  if (lane < 9) wm.Rd[lane] = df_from_double(wm.R[lane]);
+  __syncwarp();
+  // local energy: Lp lanes per electron share its shells, electrons and nuclei
+  df epart = dfz();
+  if (N <= 32) {
+    const int Lp = 32 / N;
+    const int i = lane % N, part = lane / N;
+    const bool act = lane < N * Lp;
+    ElParts o;
+    if (act) el_parts_df(S, wm, i, part, Lp, bm, o);
+    else el_zero(o);
+    for (int pp = 1; pp < Lp; ++pp) {
+      int src = lane + pp * N;
+      el_combine(o, src < 32 ? src : lane, part == 0 && src < N * Lp);
+    }
+    if (part == 0 && act) {
+      wm.Sd[i] = o.S;
+      epart = el_local(o);
+    }
+  } else {
+    for (int i = lane; i < N; i += 32) {
+      ElParts o;
+      el_parts_df(S, wm, i, 0, 1, bm, o);
+      wm.Sd[i] = o.S;
+      epart = df_add(epart, el_local(o));
+    }
+  }
+  df etot = warp_sum_df(epart);
+  el = df_to_double(etot) + S.V_nn;
+  __syncwarp();
+  // the P lattice moves
+  const int G = L.G, per_e = 6 * G, P = N * per_e;
+  for (int c = lane; c < P; c += 32) {
+    int i = c / per_e, rem = c - i * per_e, g = rem / 6, k = (rem % 6) >> 1;
+    df h = g ? L.ap_df : L.a_df;
+    if (c & 1) h = df_neg(h);
+    const df e0 = wm.Rd[k], e1 = wm.Rd[3 + k], e2 = wm.Rd[6 + k];
+    const df* ri = &wm.xd[3 * i];
+    df p[3] = {df_add(ri[0], df_mul(h, e0)), df_add(ri[1], df_mul(h, e1)), df_add(ri[2], df_mul(h, e2))};
+    df rdet = ao_dot_df(S, &wm.vd[i * nao], p, bm);
+    df dJ = df_sub(jastrow_terms_df(S, wm.xd, i, p), wm.Sd[i]);
+    df rho = df_mul(rdet, df_exp(dJ, S.D.exp.K, bm.thi, bm.tlo));
+    df w = df_make(1.0f, 0.0f);
+    if (G == 2) {
+      df hh = df_make(0.5f * h.hi, 0.5f * h.lo);
+      df mid[3] = {df_add(ri[0], df_mul(hh, e0)), df_add(ri[1], df_mul(hh, e1)), df_add(ri[2], df_mul(hh, e2))};
+      df pm = p_weight_df(S, L, mid, bm);
+      w = g ? df_add_f(df_neg(pm), 1.0f) : pm;
+    }
+    double T = 0.0;
+    if (rho.hi > 0.0f) T = df_to_double(df_mul(df_mul(w, g ? L.inv2ap2_df : L.inv2a2_df), rho));
+    wm.T[c] = T;
+    if (ratio_out) ratio_out[c] = df_to_double(rho);
+  }
+  __syncwarp();
+  b = warp_scan(wm.T, P, lane, 0.0, nullptr, nullptr);
+}
+
+__device__ __forceinline__ void warp_eval_any(const SysDev& S, const double* sC, const LatDev& L,
+                                              const WarpMem& wm, int lane, double* ratio_out, double& b,
+                                              double& el)
+{
+  if (S.precision == LRDMC_PRECISION_DF64) warp_eval_df(S, sC, L, wm, lane, ratio_out, b, el);
+  else warp_eval(S, sC, L, wm, lane, ratio_out, b, el);
+}
+
+// ----------------------------------------------------------------------------
 // Sherman-Morrison update for electron i moving to p (warp-cooperative):
 // y_n = sum_m phi_m(p) Ainv[m][n], ratio = y_l,
 // Ainv[m][n] -= Ainv[m][l] (y_n - delta_nl) / ratio.
@@ -568,6 +941,11 @@ __device__ __forceinline__ void store_record(const Layout& Lo, double* rec, cons
 __device__ __forceinline__ void stage_coefficients(const SysDev& S, double* sC)
 {
   for (int j = threadIdx.x; j < S.n_ao * S.n_mo; j += blockDim.x) sC[j] = S.C[j];
+  BlockMem bm = block_mem(S, sC);
+  for (int j = threadIdx.x; j < 64; j += blockDim.x) {
+    bm.thi[j] = S.D.exp.t_hi[j];
+    bm.tlo[j] = S.D.exp.t_lo[j];
+  }
   __syncthreads();
 }
 
@@ -583,7 +961,7 @@ k_init(const __grid_constant__ SysDev S, const Layout Lo, const PopDev P, const 
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int s = blockIdx.x * kWarpsPerBlock + wib;
   if (s >= P.W) return;
-  WarpMem wm = warp_mem(Lo, S, sC + S.n_ao * S.n_mo + wib * Lo.smem_warp);
+  WarpMem wm = warp_mem(Lo, S, sC + Lo.head + wib * Lo.smem_warp);
   for (int j = lane; j < 3 * Lo.N; j += 32) wm.x[j] = x0[(size_t)s * 3 * Lo.N + j];
   for (int j = lane; j < Lo.P_max; j += 32) wm.T[j] = 0.0;
   __syncwarp();
@@ -608,11 +986,11 @@ k_eval_all(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int s = blockIdx.x * kWarpsPerBlock + wib;
   if (s >= P.W) return;
-  WarpMem wm = warp_mem(Lo, S, sC + S.n_ao * S.n_mo + wib * Lo.smem_warp);
+  WarpMem wm = warp_mem(Lo, S, sC + Lo.head + wib * Lo.smem_warp);
   double* rec = P.rec_src + (size_t)s * Lo.rec;
   double b, el;
   load_record(Lo, rec, wm, lane, b, el);
-  warp_eval(S, sC, L, wm, lane, nullptr, b, el);
+  warp_eval_any(S, sC, L, wm, lane, nullptr, b, el);
   if (!isfinite(el) || !isfinite(b)) {
     if (lane == 0) atomicOr(P.err, kErrNonFinite);
   }
@@ -631,7 +1009,7 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
   double* sC = smem;
   stage_coefficients(S, sC);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  WarpMem wm = warp_mem(Lo, S, sC + S.n_ao * S.n_mo + wib * Lo.smem_warp);
+  WarpMem wm = warp_mem(Lo, S, sC + Lo.head + wib * Lo.smem_warp);
   const int P_moves = S.N * 6 * L.G;
   for (;;) {
     int s = 0;
@@ -682,7 +1060,7 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
       __syncwarp();
       if (lane == 0) rotation_matrix(ur[0], ur[1], ur[2], wm.R);
       __syncwarp();
-      warp_eval(S, sC, L, wm, lane, nullptr, b, el);
+      warp_eval_any(S, sC, L, wm, lane, nullptr, b, el);
       ++jumps;
       if (!isfinite(el) || !isfinite(b)) {
         if (lane == 0) atomicOr(P.err, kErrNonFinite);
@@ -779,7 +1157,7 @@ k_evaluate(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, in
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int c = blockIdx.x * kWarpsPerBlock + wib;
   if (c >= n) return;
-  WarpMem wm = warp_mem(Lo, S, sC + S.n_ao * S.n_mo + wib * Lo.smem_warp);
+  WarpMem wm = warp_mem(Lo, S, sC + Lo.head + wib * Lo.smem_warp);
   for (int j = lane; j < 3 * Lo.N; j += 32) wm.x[j] = x[(size_t)c * 3 * Lo.N + j];
   for (int j = lane; j < 9; j += 32) wm.R[j] = rot[(size_t)c * 9 + j];
   __syncwarp();
@@ -791,7 +1169,7 @@ k_evaluate(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, in
   }
   const int P = S.N * 6 * L.G;
   double b, el;
-  warp_eval(S, sC, L, wm, lane, ratio ? ratio + (size_t)c * P : nullptr, b, el);
+  warp_eval_any(S, sC, L, wm, lane, ratio ? ratio + (size_t)c * P : nullptr, b, el);
   if (T)
     for (int j = lane; j < P; j += 32) T[(size_t)c * P + j] = wm.T[j];
   if (lane == 0) {
@@ -803,6 +1181,59 @@ k_evaluate(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, in
 // ----------------------------------------------------------------------------
 // Host launchers.
 // ----------------------------------------------------------------------------
+static df split_ld(long double x)
+{
+  float h = (float)x;
+  float l = (float)(x - (long double)h);
+  return df_make(h, l);
+}
+
+void fill_df_constants(SysDev& S)
+{
+  DfSys& D = S.D;
+  for (int I = 0; I < S.n_nuc; ++I) {
+    for (int k = 0; k < 3; ++k) D.nuc[I][k] = split_ld(S.nuc[I][k]);
+    D.Z[I] = split_ld(S.Z[I]);
+    D.en_b1[I] = split_ld(S.en_b1[I]);
+  }
+  D.b_ee = split_ld(S.b_ee);
+  D.c_par = split_ld(S.c_par);
+  D.c_anti = split_ld(S.c_anti);
+  D.en_b2 = split_ld(S.en_b2);
+  for (int q = 0; q < S.n_shell; ++q) {
+    D.sh[q].m = split_ld(S.sh[q].m);
+    D.sh[q].zeta = split_ld(S.sh[q].zeta);
+    for (int p = 0; p < kMaxPrim; ++p) {
+      D.sh[q].alpha[p] = split_ld(S.sh[q].alpha[p]);
+      D.sh[q].coef[p] = split_ld(S.sh[q].coef[p]);
+    }
+  }
+  // Tang's table: 2^(j/64) and ln2/64, from long double arithmetic
+  const long double ln2 = logl(2.0L);
+  df c = split_ld(ln2 / 64.0L);
+  D.exp.K.ln2_64_hi = c.hi;
+  D.exp.K.ln2_64_lo = c.lo;
+  D.exp.K.inv_ln2_64 = (float)(64.0L / ln2);
+  D.exp.K.pad = 0.0f;
+  for (int j = 0; j < 64; ++j) {
+    df t = split_ld(exp2l((long double)j / 64.0L));
+    D.exp.t_hi[j] = t.hi;
+    D.exp.t_lo[j] = t.lo;
+  }
+}
+
+void fill_lattice_df(LatDev& L)
+{
+  L.a_df = split_ld(L.a);
+  L.ap_df = split_ld(L.ap);
+  L.inv2a2_df = split_ld(L.inv2a2);
+  L.inv2ap2_df = split_ld(L.inv2ap2);
+  L.p_coef_df = split_ld(L.p_coef);
+}
+
+static_assert(sizeof(SysDev) + sizeof(Layout) + sizeof(LatDev) + sizeof(PopDev) + 64 < 32764,
+              "kernel parameters exceed the 32 KB limit");
+
 Layout make_layout(const SysDev& S)
 {
   Layout Lo;
@@ -822,9 +1253,11 @@ Layout make_layout(const SysDev& S)
   int scr = 2 * n * n + n * S.n_ao;          // Gauss-Jordan + orbital rows
   int scr_sm = S.n_ao + 3 * n;               // Sherman-Morrison
   if (scr_sm > scr) scr = scr_sm;
-  Lo.smem_warp = 3 * S.N + S.n_up * S.n_up + S.n_dn * S.n_dn + 12 + Lo.P_max + S.N * S.n_ao + S.N + scr;
+  Lo.smem_warp = 3 * S.N + S.n_up * S.n_up + S.n_dn * S.n_dn + 12 + Lo.P_max + S.N * S.n_ao + S.N +
+                 (3 * S.N + S.N * S.n_ao + S.N + 12) + scr;
   Lo.smem_warp = (Lo.smem_warp + 1) & ~1;
-  Lo.smem_block_bytes = (int)sizeof(double) * (S.n_ao * S.n_mo + kWarpsPerBlock * Lo.smem_warp);
+  Lo.head = ((S.n_ao * S.n_mo + 64) + 1) & ~1;
+  Lo.smem_block_bytes = (int)sizeof(double) * (Lo.head + kWarpsPerBlock * Lo.smem_warp);
   return Lo;
 }
 
@@ -925,7 +1358,7 @@ k_evaluate_static(const __grid_constant__ SysDev S, const Layout Lo, const LatDe
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int c = blockIdx.x * kWarpsPerBlock + wib;
   if (c >= n) return;
-  WarpMem wm = warp_mem(Lo, S, sC + S.n_ao * S.n_mo + wib * Lo.smem_warp);
+  WarpMem wm = warp_mem(Lo, S, sC + Lo.head + wib * Lo.smem_warp);
   for (int j = lane; j < 3 * Lo.N; j += 32) wm.x[j] = x[(size_t)c * 3 * Lo.N + j];
   for (int j = lane; j < 9; j += 32) wm.R[j] = rot[(size_t)c * 9 + j];
   __syncwarp();
@@ -940,7 +1373,7 @@ k_evaluate_static(const __grid_constant__ SysDev S, const Layout Lo, const LatDe
   }
   const int P = S.N * 6 * L.G;
   double b, el;
-  warp_eval(S, sC, L, wm, lane, ratio ? ratio + (size_t)c * P : nullptr, b, el);
+  warp_eval_any(S, sC, L, wm, lane, ratio ? ratio + (size_t)c * P : nullptr, b, el);
   if (T)
     for (int j = lane; j < P; j += 32) T[(size_t)c * P + j] = wm.T[j];
   if (lane == 0) {

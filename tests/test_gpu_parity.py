@@ -53,14 +53,23 @@ EVAL_CASES = [
 ]
 
 
+PRECISIONS = ["fp64", "df64"]
+
+
+def _prec(pkg, name):
+    return pkg.PRECISION_FP64 if name == "fp64" else pkg.PRECISION_DF64
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
 @pytest.mark.parametrize("name,kind,a", EVAL_CASES)
-def test_evaluate_matches_oracle(pkg, oracle_mod, name, kind, a):
+def test_evaluate_matches_oracle(pkg, oracle_mod, name, kind, a, prec):
     """All 6N / 12N ratios, rates, total rate and local energy of 37
-    configurations (nine warps of four, a ragged last block)."""
+    configurations (nine warps of four, a ragged last block), in IEEE double
+    and in double-float arithmetic."""
     system = S.make_system(name)
     if name == "H" and kind == "this_work":
         system = S.hydrogen(0.8)
-    g = pkg.LrdmcSystem(system)
+    g = pkg.LrdmcSystem(system).set_precision(_prec(pkg, prec))
     o = oracle_mod.OracleSystem(system)
     n = 37
     x = S.initial_positions(system, n, 101)
@@ -76,12 +85,13 @@ def test_evaluate_matches_oracle(pkg, oracle_mod, name, kind, a):
         assert abs(el[c] - ref["EL"]) <= RTOL * max(1.0, abs(ref["EL"]))
 
 
-def test_evaluate_full_size_sampled(pkg, oracle_mod):
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_evaluate_full_size_sampled(pkg, oracle_mod, prec):
     """The Ne workload at full size (4096 configurations, double grid with
     the paper's parameters, a = 0.2): 64 sampled configurations against the
     oracle one by one, every total rate positive and finite."""
     system = S.neon()
-    g = pkg.LrdmcSystem(system)
+    g = pkg.LrdmcSystem(system).set_precision(_prec(pkg, prec))
     o = oracle_mod.OracleSystem(system)
     n = 4096
     x = S.initial_positions(system, n, 201)
@@ -96,8 +106,9 @@ def test_evaluate_full_size_sampled(pkg, oracle_mod):
         assert abs(el[c] - ref["EL"]) <= RTOL * abs(ref["EL"])
 
 
-def _compare_runs(pkg, oracle_mod, system, kind, a, W, n_steps, tau, seed, e_trial, rc_every=3):
-    g = pkg.LrdmcSystem(system)
+def _compare_runs(pkg, oracle_mod, system, kind, a, W, n_steps, tau, seed, e_trial, rc_every=3,
+                  prec="df64"):
+    g = pkg.LrdmcSystem(system).set_precision(_prec(pkg, prec))
     o = oracle_mod.OracleSystem(system)
     x0 = S.initial_positions(system, W, seed)
     sp, lat = spacing_pair(pkg, oracle_mod, system, a, kind)
@@ -127,6 +138,7 @@ def _compare_runs(pkg, oracle_mod, system, kind, a, W, n_steps, tau, seed, e_tri
     return compared, False
 
 
+@pytest.mark.parametrize("prec", PRECISIONS)
 @pytest.mark.parametrize("name,kind,a,W,steps,tau,et", [
     ("He", "single", 0.2, 64, 25, 0.02, -2.9),
     ("He", "this_work", 0.2, 61, 25, 0.02, -2.9),
@@ -135,17 +147,20 @@ def _compare_runs(pkg, oracle_mod, system, kind, a, W, n_steps, tau, seed, e_tri
     ("Be_bare", "explicit", 0.2, 16, 10, 0.02, -20.0),
     ("H", "single", 0.3, 5, 10, 0.05, -0.5),
 ])
-def test_projection_matches_oracle(pkg, oracle_mod, name, kind, a, W, steps, tau, et):
+def test_projection_matches_oracle(pkg, oracle_mod, name, kind, a, W, steps, tau, et, prec):
     """Whole intervals: waiting times, heat-bath choices, Sherman-Morrison
     updates, inverse recomputation, weights and comb reconfiguration."""
-    compared, parted = _compare_runs(pkg, oracle_mod, S.make_system(name), kind, a, W, steps, tau, 11, et)
+    compared, parted = _compare_runs(pkg, oracle_mod, S.make_system(name), kind, a, W, steps, tau, 11, et,
+                                     prec=prec)
     assert compared >= (1 if parted else steps)
 
 
-def test_projection_full_size(pkg, oracle_mod):
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_projection_full_size(pkg, oracle_mod, prec):
     """The Ne workload at full size (4096 walkers, a = 0.2, the paper's
     double grid, tau = 0.025) for two intervals, walker by walker."""
-    compared, parted = _compare_runs(pkg, oracle_mod, S.neon(), "this_work", 0.2, 4096, 2, 0.025, 5, -128.9)
+    compared, parted = _compare_runs(pkg, oracle_mod, S.neon(), "this_work", 0.2, 4096, 2, 0.025, 5, -128.9,
+                                     prec=prec)
     assert compared >= 1
 
 
