@@ -159,6 +159,7 @@ def run_ours(args):
     stream = g.stream
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     g.step(args.warmup, a, spacing)
+    g.sync()
     torch.cuda.synchronize()
     g.set_profiling(True)
     g.kernel_times(reset=True)
@@ -176,6 +177,7 @@ def run_ours(args):
             starts[k].record(stream)
             g.step(1, a, spacing)
             stops[k].record(stream)
+        g.sync()
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall0
     if dist is not None:

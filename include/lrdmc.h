@@ -154,10 +154,17 @@ LRDMC_API lrdmc_status lrdmc_init_walkers(lrdmc_system_t sys, int n_walkers, con
  * continuous-time loop (waiting time of rate b_x, weight exp(-t (E_L -
  * e_trial)), heat-bath jump, Sherman-Morrison update, new rotation and
  * evaluation of all P moves), then comb reconfiguration and one trace entry
- * per interval. Asynchronous on the stream except for one 4-byte read of
- * the error word at the end. Fails with LRDMC_ERR_ARG when the trace would
- * exceed its capacity. */
+ * per interval. Asynchronous: the call enqueues the kernels and a copy of
+ * the device error word on the stream and returns; errors raised by the
+ * kernels (singular matrix, non-finite energy, iteration limit) are
+ * reported by the next synchronising call (lrdmc_sync and every read-back
+ * function). Fails at once with LRDMC_ERR_ARG when the trace would exceed
+ * its capacity. */
 LRDMC_API lrdmc_status lrdmc_step(lrdmc_system_t sys, int n_steps, double a, const lrdmc_spacing_fn* spacing);
+
+/* Waits for the system's stream and reports any error the enqueued steps
+ * raised. */
+LRDMC_API lrdmc_status lrdmc_sync(lrdmc_system_t sys);
 
 /* Copies the trace to host arrays (each nullable, length >= max_n): e_k =
  * weighted mean local energy at the end of interval k, wbar_k = mean weight

@@ -30,7 +30,7 @@ PRECISION_FP64, PRECISION_DF64 = 0, 1
 
 EXPORTED = [
     "lrdmc_create_system", "lrdmc_spacing_params", "lrdmc_workspace_bytes", "lrdmc_init_walkers",
-    "lrdmc_step", "lrdmc_get_energy_trace", "lrdmc_get_walkers", "lrdmc_moves", "lrdmc_evaluate",
+    "lrdmc_step", "lrdmc_sync", "lrdmc_get_energy_trace", "lrdmc_get_walkers", "lrdmc_moves", "lrdmc_evaluate",
     "lrdmc_evaluate_static",
     "lrdmc_save", "lrdmc_load", "lrdmc_set_precision", "lrdmc_set_profiling", "lrdmc_kernel_times", "lrdmc_last_error",
     "lrdmc_destroy",
@@ -95,6 +95,8 @@ def load_library():
     L.lrdmc_init_walkers.argtypes = [vp, i, vp, ct.c_uint64, d, d, i, i, vp, sz, vp]
     L.lrdmc_step.restype = i
     L.lrdmc_step.argtypes = [vp, i, d, vp]
+    L.lrdmc_sync.restype = i
+    L.lrdmc_sync.argtypes = [vp]
     L.lrdmc_get_energy_trace.restype = i
     L.lrdmc_get_energy_trace.argtypes = [vp, vp, vp, vp, i, ct.POINTER(i)]
     L.lrdmc_get_walkers.restype = i
@@ -222,6 +224,10 @@ class LrdmcSystem:
         sp = spacing.c()
         self._check(load_library().lrdmc_step(self.h, int(n_steps), float(a), ct.byref(sp)))
         self.lattice_G = 1 if spacing.kind == SINGLE else 2
+
+    def sync(self):
+        """Wait for the enqueued steps and raise any error they reported."""
+        self._check(load_library().lrdmc_sync(self.h))
 
     def energy_trace(self, max_n=1 << 20):
         n = ct.c_int()

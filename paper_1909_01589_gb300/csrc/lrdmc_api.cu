@@ -39,6 +39,8 @@ struct lrdmc_system_s {
   // kernel timing (lrdmc_set_profiling)
   bool profiling = false;
   std::vector<cudaEvent_t> events;  // 4 per step: interval start/stop, reconfig start/stop
+  size_t ev_used = 0;               // events recorded since the last collection
+  bool pending = false;             // steps enqueued since the last synchronisation
   double t_interval_ms = 0.0, t_reconfig_ms = 0.0;
   long long n_interval = 0, n_reconfig = 0;
   std::string last_error;
@@ -454,7 +456,7 @@ lrdmc_status lrdmc_step(lrdmc_system_t s, int n_steps, double a, const lrdmc_spa
   if (st != LRDMC_OK) return st;
   cudaError_t e;
   if (s->profiling) {
-    while (s->events.size() < 4 * (size_t)n_steps) {
+    while (s->events.size() < s->ev_used + 4 * (size_t)n_steps) {
       cudaEvent_t ev;
       e = cudaEventCreate(&ev);
       if (e != cudaSuccess) return cuda_fail(s, e, "profiling event");
@@ -475,7 +477,11 @@ lrdmc_status lrdmc_step(lrdmc_system_t s, int n_steps, double a, const lrdmc_spa
     const int recompute = (k > 0 && s->recompute_every > 0 && k % (uint64_t)s->recompute_every == 0) ? 1 : 0;
     P.rec_src = s->rec[s->cur];
     P.rec_dst = s->rec[1 - s->cur];
-    cudaEvent_t* ev = s->profiling ? &s->events[4 * n] : nullptr;
+    cudaEvent_t* ev = nullptr;
+    if (s->profiling) {
+      ev = &s->events[s->ev_used];
+      s->ev_used += 4;
+    }
     if (ev) cudaEventRecord(ev[0], s->stream);
     e = launch_interval(s->S, s->Lo, L, P, k, recompute, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "k_interval launch");
@@ -489,19 +495,37 @@ lrdmc_status lrdmc_step(lrdmc_system_t s, int n_steps, double a, const lrdmc_spa
     s->cur = 1 - s->cur;
     s->k++;
   }
-  lrdmc_status rs = read_error_word(s);
-  if (s->profiling && rs == LRDMC_OK) {
-    for (int n = 0; n < n_steps; ++n) {
-      float a_ms = 0.f, b_ms = 0.f;
-      cudaEventElapsedTime(&a_ms, s->events[4 * n], s->events[4 * n + 1]);
-      cudaEventElapsedTime(&b_ms, s->events[4 * n + 2], s->events[4 * n + 3]);
-      s->t_interval_ms += a_ms;
-      s->t_reconfig_ms += b_ms;
-    }
-    s->n_interval += n_steps;
-    s->n_reconfig += n_steps;
+  // the error word travels to pinned host memory behind the step's kernels;
+  // it is examined at the next synchronising call
+  e = cudaMemcpyAsync(s->err_host, s->P.err, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "error word read");
+  s->pending = true;
+  return LRDMC_OK;
+}
+
+// Waits for the stream, folds the recorded kernel events into the timing
+// totals and reports the device error word.
+static lrdmc_status sync_system(lrdmc_system_t s)
+{
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "stream synchronize");
+  for (size_t n = 0; n + 3 < s->ev_used; n += 4) {
+    float a_ms = 0.f, b_ms = 0.f;
+    cudaEventElapsedTime(&a_ms, s->events[n], s->events[n + 1]);
+    cudaEventElapsedTime(&b_ms, s->events[n + 2], s->events[n + 3]);
+    s->t_interval_ms += a_ms;
+    s->t_reconfig_ms += b_ms;
+    s->n_interval += 1;
+    s->n_reconfig += 1;
   }
-  return rs;
+  s->ev_used = 0;
+  if (!s->pending) return LRDMC_OK;
+  s->pending = false;
+  int w = *s->err_host;
+  if (w & kErrSingular) return fail(s, LRDMC_ERR_SINGULAR, "singular Slater matrix or zero update ratio");
+  if (w & kErrNonFinite) return fail(s, LRDMC_ERR_NONFINITE, "non-finite local energy or rate");
+  if (w & kErrIters) return fail(s, LRDMC_ERR_TIMEOUT, "an interval exceeded its iteration limit");
+  return LRDMC_OK;
 }
 
 lrdmc_status lrdmc_get_energy_trace(lrdmc_system_t s, double* e_out, double* w_out, double* j_out,
@@ -509,6 +533,8 @@ lrdmc_status lrdmc_get_energy_trace(lrdmc_system_t s, double* e_out, double* w_o
 {
   if (!s) return fail(s, LRDMC_ERR_ARG, "");
   if (!s->have_pop) return fail(s, LRDMC_ERR_STATE, "trace before init_walkers");
+  lrdmc_status ss = sync_system(s);
+  if (ss != LRDMC_OK) return ss;
   int n = (int)((uint64_t)max_n < s->k ? (uint64_t)max_n : s->k);
   if (n < 0) n = 0;
   double* outs[3] = {e_out, w_out, j_out};
@@ -529,6 +555,8 @@ lrdmc_status lrdmc_get_walkers(lrdmc_system_t s, double* x, double* el, double* 
 {
   if (!s) return fail(s, LRDMC_ERR_ARG, "");
   if (!s->have_pop) return fail(s, LRDMC_ERR_STATE, "get_walkers before init_walkers");
+  lrdmc_status ss = sync_system(s);
+  if (ss != LRDMC_OK) return ss;
   const int W = s->W;
   const Layout& Lo = s->Lo;
   std::vector<double> rec((size_t)W * Lo.rec);
@@ -560,6 +588,8 @@ lrdmc_status lrdmc_moves(lrdmc_system_t s, long long* moves)
 {
   if (!s || !moves) return fail(s, LRDMC_ERR_ARG, "moves: NULL");
   if (!s->have_pop) return fail(s, LRDMC_ERR_STATE, "moves before init_walkers");
+  lrdmc_status ss = sync_system(s);
+  if (ss != LRDMC_OK) return ss;
   unsigned long long m = 0;
   cudaError_t e = cudaMemcpyAsync(&m, s->P.moves, sizeof(m), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -623,6 +653,8 @@ lrdmc_status lrdmc_save(lrdmc_system_t s, const char* path)
 {
   if (!s || !path) return fail(s, LRDMC_ERR_ARG, "save: NULL");
   if (!s->have_pop) return fail(s, LRDMC_ERR_STATE, "save before init_walkers");
+  lrdmc_status ss = sync_system(s);
+  if (ss != LRDMC_OK) return ss;
   const int W = s->W;
   std::vector<double> rec((size_t)W * s->Lo.rec), trace(3 * (size_t)s->trace_cap);
   std::vector<int> par(W);
@@ -649,6 +681,8 @@ lrdmc_status lrdmc_load(lrdmc_system_t s, const char* path)
 {
   if (!s || !path) return fail(s, LRDMC_ERR_ARG, "load: NULL");
   if (!s->have_pop) return fail(s, LRDMC_ERR_STATE, "load needs an initialised population of the same size");
+  lrdmc_status ss = sync_system(s);
+  if (ss != LRDMC_OK) return ss;
   FILE* f = fopen(path, "rb");
   if (!f) return fail(s, LRDMC_ERR_ARG, std::string("load: cannot open ") + path);
   int64_t hdr[8];
@@ -699,10 +733,21 @@ lrdmc_status lrdmc_set_profiling(lrdmc_system_t s, int on)
   return LRDMC_OK;
 }
 
+lrdmc_status lrdmc_sync(lrdmc_system_t s)
+{
+  if (!s) return fail(s, LRDMC_ERR_ARG, "");
+  if (!s->have_pop) return LRDMC_OK;
+  return sync_system(s);
+}
+
 lrdmc_status lrdmc_kernel_times(lrdmc_system_t s, double* interval_ms, double* reconfig_ms,
                                 long long* interval_launches, long long* reconfig_launches, int reset)
 {
   if (!s) return fail(s, LRDMC_ERR_ARG, "");
+  if (s->have_pop) {
+    lrdmc_status ss = sync_system(s);
+    if (ss != LRDMC_OK) return ss;
+  }
   if (interval_ms) *interval_ms = s->t_interval_ms;
   if (reconfig_ms) *reconfig_ms = s->t_reconfig_ms;
   if (interval_launches) *interval_launches = s->n_interval;

@@ -220,6 +220,7 @@ def test_errors_are_reported_not_faulted(pkg):
     g2.init_walkers(torch.tensor(S.initial_positions(system, 8, 11), device="cuda"), seed=1, tau=0.01,
                     trace_capacity=2)
     g2.step(2, 0.2)
+    g2.sync()
     with pytest.raises(pkg.LrdmcError) as e:
         g2.step(1, 0.2)  # trace capacity exhausted
     assert e.value.status == pkg.ERR_ARG
