@@ -137,17 +137,17 @@ __host__ __device__ __forceinline__ float f_rsqrt_approx(float x)
 #endif
 }
 
-// a / b: FP32 quotient, then one correction with the exact remainder.
+// a / b: FP32 quotient q1, then one correction q2 = (a - b q1) / b from the
+// exactly computed remainder (relative error ~2^-45).
 __host__ __device__ __forceinline__ df df_div(df a, df b)
 {
   float r = f_rcp_approx(b.hi);
   float q1 = DF_MUL(a.hi, r);
-  df rem = df_sub(a, df_mul_f(b, q1));
+  df p = two_prod(b.hi, q1);
+  p.lo = DF_FMA(b.lo, q1, p.lo);
+  df rem = df_sub(a, p);
   float q2 = DF_MUL(rem.hi, r);
-  rem = df_sub(rem, df_mul_f(b, q2));
-  float q3 = DF_MUL(rem.hi, r);
-  df q = fast_two_sum(q1, q2);
-  return df_add_f(q, q3);
+  return fast_two_sum(q1, q2);
 }
 
 // 1 / b
@@ -161,11 +161,7 @@ __host__ __device__ __forceinline__ df df_sqrt(df a)
   float s = DF_MUL(a.hi, y);
   df res = df_sub(a, two_prod(s, s));
   float c = DF_MUL(res.hi, DF_MUL(0.5f, y));
-  df r = fast_two_sum(s, c);
-  // second correction (the seed is only ~22 bits)
-  res = df_sub(a, df_sqr(r));
-  c = DF_MUL(res.hi, DF_MUL(0.5f, y));
-  return df_add_f(r, c);
+  return fast_two_sum(s, c);
 }
 
 // Constants of the exponential: ln2/64 split in two floats and 64/ln2.

@@ -600,18 +600,22 @@ __device__ df ao_dot_df(const SysDev& S, const df* v, const df p[3], const Block
 }
 
 // sum_{j != i} u_ee(|p - r_j|) + sum_I u_en(|p - R_I|) in double-float.
+// The e-e Pade terms c r/(1 + b r) (all of one sign) are summed as one
+// running fraction num/den, so one division serves all partners.
 __device__ df jastrow_terms_df(const SysDev& S, const df* xd, int i, const df p[3])
 {
-  df acc = dfz();
+  df num = dfz(), den = df_make(1.0f, 0.0f);
   const int si = spin_of(S, i);
   for (int j = 0; j < S.N; ++j) {
     if (j == i) continue;
     df d0 = df_sub_fast(p[0], xd[3 * j]), d1 = df_sub_fast(p[1], xd[3 * j + 1]), d2 = df_sub_fast(p[2], xd[3 * j + 2]);
     df r = df_sqrt(df_dot3(d0, d1, d2));
     df c = (spin_of(S, j) == si) ? S.D.c_par : S.D.c_anti;
-    df den = df_add_f(df_mul(S.D.b_ee, r), 1.0f);
-    acc = df_add_fast(acc, df_div(df_mul(c, r), den));
+    df dj = df_add_f(df_mul(S.D.b_ee, r), 1.0f);
+    num = df_add_fast(df_mul(num, dj), df_mul(df_mul(c, r), den));
+    den = df_mul(den, dj);
   }
+  df acc = df_div(num, den);
   for (int I = 0; I < S.n_nuc; ++I) {
     df d0 = df_sub_fast(p[0], S.D.nuc[I][0]), d1 = df_sub_fast(p[1], S.D.nuc[I][1]), d2 = df_sub_fast(p[2], S.D.nuc[I][2]);
     df r = df_sqrt(df_dot3(d0, d1, d2));
@@ -860,11 +864,12 @@ __device__ void warp_eval_df(const SysDev& S, const double* sC, const LatDev& L,
   b = warp_scan(wm.T, P, lane, 0.0, nullptr, nullptr);
 }
 
+template <int PREC>
 __device__ __forceinline__ void warp_eval_any(const SysDev& S, const double* sC, const LatDev& L,
                                               const WarpMem& wm, int lane, double* ratio_out, double& b,
                                               double& el)
 {
-  if (S.precision == LRDMC_PRECISION_DF64) warp_eval_df(S, sC, L, wm, lane, ratio_out, b, el);
+  if (PREC == LRDMC_PRECISION_DF64) warp_eval_df(S, sC, L, wm, lane, ratio_out, b, el);
   else warp_eval(S, sC, L, wm, lane, ratio_out, b, el);
 }
 
@@ -873,6 +878,35 @@ __device__ __forceinline__ void warp_eval_any(const SysDev& S, const double* sC,
 // y_n = sum_m phi_m(p) Ainv[m][n], ratio = y_l,
 // Ainv[m][n] -= Ainv[m][l] (y_n - delta_nl) / ratio.
 // ----------------------------------------------------------------------------
+// chi_mu(p) for all AOs in double-float, one lane per group of shells that
+// share an exponential, written back as doubles.
+__device__ void ao_values_df_lanes(const SysDev& S, const double* p, double* out, int lane, const BlockMem& bm)
+{
+  df pd[3] = {df_from_double(p[0]), df_from_double(p[1]), df_from_double(p[2])};
+  int prev_c = -1, grp = -1;
+  df d[3] = {dfz(), dfz(), dfz()}, r = dfz(), r2 = dfz(), e = dfz();
+  for (int q = 0; q < S.n_shell; ++q) {
+    const ShellDev& sh = S.sh[q];
+    const DfShell& dsh = S.D.sh[q];
+    if (!(sh.kind == 0 && sh.same_exp)) ++grp;
+    if ((grp & 31) != lane) continue;
+    if (sh.center != prev_c) {
+      prev_c = sh.center;
+      d[0] = df_sub_fast(pd[0], S.D.nuc[prev_c][0]);
+      d[1] = df_sub_fast(pd[1], S.D.nuc[prev_c][1]);
+      d[2] = df_sub_fast(pd[2], S.D.nuc[prev_c][2]);
+      r2 = df_dot3(d[0], d[1], d[2]);
+      r = df_sqrt(r2);
+    }
+    if (sh.kind == 0 && !sh.same_exp) e = df_exp(df_neg(df_mul(dsh.zeta, r)), S.D.exp.K, bm.thi, bm.tlo);
+    df R = radial_value_df(S, sh, dsh, r, r2, e, bm);
+    df Sv[5];
+    int nf = solid_df(sh.l, d, Sv);
+    for (int f = 0; f < nf; ++f) out[sh.ao_offset + f] = df_to_double(df_mul(Sv[f], R));
+  }
+}
+
+template <int PREC>
 __device__ bool warp_sm_update(const SysDev& S, const double* sC, const WarpMem& wm, int i,
                                const double* p, int lane)
 {
@@ -883,7 +917,8 @@ __device__ bool warp_sm_update(const SysDev& S, const double* sC, const WarpMem&
   double* phi = chi + S.n_ao;      // [n]
   double* y = phi + n;             // [n]
   double* col = y + n;             // [n]
-  if (lane == 0) ao_values(S, p, chi);
+  if (PREC == LRDMC_PRECISION_DF64) ao_values_df_lanes(S, p, chi, lane, block_mem(S, const_cast<double*>(sC)));
+  else if (lane == 0) ao_values(S, p, chi);
   __syncwarp();
   for (int m = lane; m < n; m += 32) {
     double a = 0.0;
@@ -977,6 +1012,7 @@ k_init(const __grid_constant__ SysDev S, const Layout Lo, const PopDev P, const 
   store_record(Lo, P.rec_src + (size_t)s * Lo.rec, wm, lane, NAN, NAN);
 }
 
+template <int PREC>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 k_eval_all(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, const PopDev P)
 {
@@ -990,7 +1026,7 @@ k_eval_all(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
   double* rec = P.rec_src + (size_t)s * Lo.rec;
   double b, el;
   load_record(Lo, rec, wm, lane, b, el);
-  warp_eval_any(S, sC, L, wm, lane, nullptr, b, el);
+  warp_eval_any<PREC>(S, sC, L, wm, lane, nullptr, b, el);
   if (!isfinite(el) || !isfinite(b)) {
     if (lane == 0) atomicOr(P.err, kErrNonFinite);
   }
@@ -1001,7 +1037,8 @@ k_eval_all(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
 // projection of the cited LRDMC method): wait for an exponential time of
 // rate b_x, decrease log w by (E_L - E_T) times the time spent, and at the
 // end of the wait jump to move c with probability T_c / b_x.
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+template <int PREC>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
 k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, const PopDev P,
            uint64_t k, int recompute)
 {
@@ -1050,7 +1087,7 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
       double pnew[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) pnew[d] = wm.x[3 * i + d] + sign * h * wm.R[3 * d + kx];
-      if (!warp_sm_update(S, sC, wm, i, pnew, lane)) {
+      if (!warp_sm_update<PREC>(S, sC, wm, i, pnew, lane)) {
         if (lane == 0) atomicOr(P.err, kErrSingular);
         break;
       }
@@ -1060,7 +1097,7 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
       __syncwarp();
       if (lane == 0) rotation_matrix(ur[0], ur[1], ur[2], wm.R);
       __syncwarp();
-      warp_eval_any(S, sC, L, wm, lane, nullptr, b, el);
+      warp_eval_any<PREC>(S, sC, L, wm, lane, nullptr, b, el);
       ++jumps;
       if (!isfinite(el) || !isfinite(b)) {
         if (lane == 0) atomicOr(P.err, kErrNonFinite);
@@ -1146,6 +1183,7 @@ __global__ void __launch_bounds__(1024) k_reconfig(const PopDev P, uint64_t k)
 }
 
 // Stateless evaluation of given configurations (one warp per configuration).
+template <int PREC>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 k_evaluate(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, int n,
            const double* x, const double* rot, double* ratio, double* T, double* b_out,
@@ -1169,7 +1207,7 @@ k_evaluate(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, in
   }
   const int P = S.N * 6 * L.G;
   double b, el;
-  warp_eval_any(S, sC, L, wm, lane, ratio ? ratio + (size_t)c * P : nullptr, b, el);
+  warp_eval_any<PREC>(S, sC, L, wm, lane, ratio ? ratio + (size_t)c * P : nullptr, b, el);
   if (T)
     for (int j = lane; j < P; j += 32) T[(size_t)c * P + j] = wm.T[j];
   if (lane == 0) {
@@ -1277,21 +1315,32 @@ cudaError_t launch_init(const SysDev& S, const Layout& Lo, const PopDev& P, cons
   return cudaGetLastError();
 }
 
-cudaError_t launch_eval_all(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P,
-                            cudaStream_t st)
+template <int PREC>
+static cudaError_t launch_eval_all_t(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P,
+                                     cudaStream_t st)
 {
-  cudaError_t e = set_smem((const void*)k_eval_all, Lo.smem_block_bytes);
+  cudaError_t e = set_smem((const void*)k_eval_all<PREC>, Lo.smem_block_bytes);
   if (e != cudaSuccess) return e;
   int blocks = (P.W + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  k_eval_all<<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(S, Lo, L, P);
+  k_eval_all<PREC><<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(S, Lo, L, P);
   return cudaGetLastError();
 }
 
-cudaError_t launch_interval(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P,
-                            uint64_t k, int recompute, cudaStream_t st)
+cudaError_t launch_eval_all(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P,
+                            cudaStream_t st)
+{
+  if (S.precision == LRDMC_PRECISION_DF64) return launch_eval_all_t<LRDMC_PRECISION_DF64>(S, Lo, L, P, st);
+  return launch_eval_all_t<LRDMC_PRECISION_FP64>(S, Lo, L, P, st);
+}
+
+// Persistent grid: as many blocks as fit on the GPU at once (capped by the
+// walker count); the warps fetch walkers from an atomic counter.
+template <int PREC>
+static cudaError_t launch_interval_t(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P,
+                                     uint64_t k, int recompute, cudaStream_t st)
 {
   static int blocks_per_sm = -1, sm_count = 0, cached_smem = -1;
-  cudaError_t e = set_smem((const void*)k_interval, Lo.smem_block_bytes);
+  cudaError_t e = set_smem((const void*)k_interval<PREC>, Lo.smem_block_bytes);
   if (e != cudaSuccess) return e;
   if (cached_smem != Lo.smem_block_bytes) {
     int dev;
@@ -1299,7 +1348,7 @@ cudaError_t launch_interval(const SysDev& S, const Layout& Lo, const LatDev& L, 
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_interval, kWarpsPerBlock * 32,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_interval<PREC>, kWarpsPerBlock * 32,
                                                       Lo.smem_block_bytes);
     if (e != cudaSuccess) return e;
     if (blocks_per_sm < 1) blocks_per_sm = 1;
@@ -1308,8 +1357,16 @@ cudaError_t launch_interval(const SysDev& S, const Layout& Lo, const LatDev& L, 
   int need = (P.W + kWarpsPerBlock - 1) / kWarpsPerBlock;
   int blocks = blocks_per_sm * sm_count;
   if (blocks > need) blocks = need;
-  k_interval<<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(S, Lo, L, P, k, recompute);
+  k_interval<PREC><<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(S, Lo, L, P, k, recompute);
   return cudaGetLastError();
+}
+
+cudaError_t launch_interval(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P,
+                            uint64_t k, int recompute, cudaStream_t st)
+{
+  if (S.precision == LRDMC_PRECISION_DF64)
+    return launch_interval_t<LRDMC_PRECISION_DF64>(S, Lo, L, P, k, recompute, st);
+  return launch_interval_t<LRDMC_PRECISION_FP64>(S, Lo, L, P, k, recompute, st);
 }
 
 cudaError_t launch_reconfig(const PopDev& P, uint64_t k, cudaStream_t st)
@@ -1322,11 +1379,17 @@ cudaError_t launch_evaluate(const SysDev& S, const Layout& Lo, const LatDev& L, 
                             const double* x, const double* rot, double* ratio, double* T,
                             double* b, double* el, int* err, cudaStream_t st)
 {
-  cudaError_t e = set_smem((const void*)k_evaluate, Lo.smem_block_bytes);
+  const bool df = S.precision == LRDMC_PRECISION_DF64;
+  const void* fn = df ? (const void*)k_evaluate<LRDMC_PRECISION_DF64> : (const void*)k_evaluate<LRDMC_PRECISION_FP64>;
+  cudaError_t e = set_smem(fn, Lo.smem_block_bytes);
   if (e != cudaSuccess) return e;
   int blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  k_evaluate<<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(S, Lo, L, n, x, rot, ratio, T,
-                                                                       b, el, err);
+  if (df)
+    k_evaluate<LRDMC_PRECISION_DF64><<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(
+        S, Lo, L, n, x, rot, ratio, T, b, el, err);
+  else
+    k_evaluate<LRDMC_PRECISION_FP64><<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(
+        S, Lo, L, n, x, rot, ratio, T, b, el, err);
   return cudaGetLastError();
 }
 
@@ -1347,6 +1410,7 @@ cudaError_t launch_evaluate(const SysDev& S, const Layout& Lo, const LatDev& L, 
 // ----------------------------------------------------------------------------
 static __device__ __align__(256) int g_eval_scratch[64 + LRDMC_STATIC_EVAL_MAX];
 
+template <int PREC>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 k_evaluate_static(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, int n,
                   const double* x, const double* rot, double* ratio, double* T, double* b_out,
@@ -1373,7 +1437,7 @@ k_evaluate_static(const __grid_constant__ SysDev S, const Layout Lo, const LatDe
   }
   const int P = S.N * 6 * L.G;
   double b, el;
-  warp_eval_any(S, sC, L, wm, lane, ratio ? ratio + (size_t)c * P : nullptr, b, el);
+  warp_eval_any<PREC>(S, sC, L, wm, lane, ratio ? ratio + (size_t)c * P : nullptr, b, el);
   if (T)
     for (int j = lane; j < P; j += 32) T[(size_t)c * P + j] = wm.T[j];
   if (lane == 0) {
@@ -1416,12 +1480,18 @@ cudaError_t launch_evaluate_static(const SysDev& S, const Layout& Lo, const LatD
   // the summary word and the statuses of this call start at zero
   e = cudaMemsetAsync(scratch, 0, sizeof(int) * (64 + (size_t)n), st);
   if (e != cudaSuccess) return e;
-  e = set_smem((const void*)k_evaluate_static, Lo.smem_block_bytes);
+  const bool df = S.precision == LRDMC_PRECISION_DF64;
+  e = set_smem(df ? (const void*)k_evaluate_static<LRDMC_PRECISION_DF64>
+                  : (const void*)k_evaluate_static<LRDMC_PRECISION_FP64>,
+               Lo.smem_block_bytes);
   if (e != cudaSuccess) return e;
   int blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  if (blocks > 0)
-    k_evaluate_static<<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(S, Lo, L, n, x, rot, ratio,
-                                                                                T, b, el, scratch);
+  if (blocks > 0 && df)
+    k_evaluate_static<LRDMC_PRECISION_DF64><<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(
+        S, Lo, L, n, x, rot, ratio, T, b, el, scratch);
+  else if (blocks > 0)
+    k_evaluate_static<LRDMC_PRECISION_FP64><<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(
+        S, Lo, L, n, x, rot, ratio, T, b, el, scratch);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = cudaMemcpyAsync(summary, scratch, sizeof(int), cudaMemcpyDeviceToHost, st);
