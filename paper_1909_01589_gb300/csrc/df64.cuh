@@ -171,14 +171,14 @@ struct ExpConsts {
   float pad;
 };
 
-// Table of 2^(j/64), j = 0..63, as double-floats (hi[j], lo[j]).
+// Table of 2^(j/64), j = 0..63, as double-floats (x = hi, y = lo).
 struct ExpTable {
   ExpConsts K;
-  float t_hi[64], t_lo[64];
+  float2 t[64];
 };
 
-// e^a for a in about [-87, 88]; 0 below, +inf above. thi/tlo: the table.
-__host__ __device__ __forceinline__ df df_exp(df a, const ExpConsts& K, const float* thi, const float* tlo)
+// e^a for a in about [-87, 88]; 0 below, +inf above. tab: the table.
+__host__ __device__ __forceinline__ df df_exp(df a, const ExpConsts& K, const float2* tab)
 {
   if (a.hi < -87.0f) return df_make(0.0f, 0.0f);
   if (a.hi > 88.0f) return df_make(INFINITY, 0.0f);
@@ -202,7 +202,8 @@ __host__ __device__ __forceinline__ df df_exp(df a, const ExpConsts& K, const fl
   e = df_add_f(e, 1.0f);
   int j = m & 63;
   int n = (m - j) >> 6;
-  e = df_mul(e, df_make(thi[j], tlo[j]));
+  const float2 tj = tab[j];
+  e = df_mul(e, df_make(tj.x, tj.y));
   // scale by 2^n in two steps so that intermediate factors stay normal
   int n1 = n >> 1, n2 = n - n1;
 #ifdef __CUDA_ARCH__
@@ -214,10 +215,10 @@ __host__ __device__ __forceinline__ df df_exp(df a, const ExpConsts& K, const fl
 }
 
 // log(a), a > 0: FP32 seed y0, then one Newton step y0 + a e^(-y0) - 1.
-__host__ __device__ __forceinline__ df df_log(df a, const ExpConsts& K, const float* thi, const float* tlo)
+__host__ __device__ __forceinline__ df df_log(df a, const ExpConsts& K, const float2* tab)
 {
   float y0 = logf(a.hi);
-  df t = df_mul(a, df_exp(df_make(-y0, 0.0f), K, thi, tlo));
+  df t = df_mul(a, df_exp(df_make(-y0, 0.0f), K, tab));
   t = df_add_f(t, -1.0f);
   return df_add_f(t, y0);
 }

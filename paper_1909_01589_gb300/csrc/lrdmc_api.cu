@@ -34,6 +34,7 @@ struct lrdmc_system_s {
   bool have_pop = false;
   bool have_eval = false;
   LatDev eval_lat;
+  int eval_prec = LRDMC_PRECISION_DF64;  // arithmetic of the cached rates (their storage format)
   int* err_host = nullptr;  // pinned
   int* eval_err = nullptr;  // device error word of lrdmc_evaluate
   // kernel timing (lrdmc_set_profiling)
@@ -284,10 +285,36 @@ lrdmc_status lrdmc_create_system(int n_nuc, const double* nuc_xyz, const double*
       vnn += Z[I] * Z[J] / sqrt(dx * dx + dy * dy + dz * dz);
     }
   S.V_nn = vnn;
+  // shells are stored sorted by centre (stable); AOs follow the sorted
+  // shells, so the MO coefficient rows are permuted to match
+  int order[kMaxShell];
+  {
+    int n = 0;
+    for (int I = 0; I < n_nuc; ++I) {
+      S.nuc_shell_begin[I] = n;
+      for (int q = 0; q < n_shells; ++q)
+        if (shells[q].center == I) order[n++] = q;
+    }
+    S.nuc_shell_begin[n_nuc] = n;
+    if (n != n_shells) {
+      delete s;
+      g_static_error = "create_system: invalid shell centre";
+      return LRDMC_ERR_ARG;
+    }
+  }
+  int user_off[kMaxShell];
+  {
+    int o = 0;
+    for (int q = 0; q < n_shells; ++q) {
+      user_off[q] = o;
+      o += 2 * shells[q].l + 1;
+    }
+  }
   int off = 0;
-  for (int q = 0; q < n_shells; ++q) {
+  for (int qs = 0; qs < n_shells; ++qs) {
+    const int q = order[qs];
     const lrdmc_shell& in = shells[q];
-    ShellDev& sh = S.sh[q];
+    ShellDev& sh = S.sh[qs];
     if (in.center < 0 || in.center >= n_nuc || in.l < 0 || in.l > 2 || (in.kind != 0 && in.kind != 1) ||
         (in.kind == 1 && (in.n_prim < 1 || in.n_prim > kMaxPrim)) ||
         (in.kind == 0 && !(in.zeta > 0.0)) || (in.kind == 0 && in.n_eff - 1.0 - in.l < 0.0)) {
@@ -308,8 +335,9 @@ lrdmc_status lrdmc_create_system(int n_nuc, const double* nuc_xyz, const double*
       sh.alpha[p] = in.alpha[p];
       sh.coef[p] = in.coef[p];
     }
-    sh.same_exp = (q > 0 && in.kind == 0 && shells[q - 1].kind == 0 && shells[q - 1].center == in.center &&
-                   shells[q - 1].zeta == in.zeta) ? 1 : 0;
+    const lrdmc_shell* prev = qs > 0 ? &shells[order[qs - 1]] : nullptr;
+    sh.same_exp = (prev && in.kind == 0 && prev->kind == 0 && prev->center == in.center && prev->zeta == in.zeta)
+                      ? 1 : 0;
     off += 2 * in.l + 1;
   }
   if (off != n_ao) {
@@ -317,7 +345,12 @@ lrdmc_status lrdmc_create_system(int n_nuc, const double* nuc_xyz, const double*
     g_static_error = "create_system: n_ao differs from the shells' 2l+1 count";
     return LRDMC_ERR_ARG;
   }
-  for (int j = 0; j < n_ao * n_mo; ++j) S.C[j] = mo_coeff[j];
+  for (int qs = 0; qs < n_shells; ++qs) {
+    const int q = order[qs];
+    for (int f = 0; f < 2 * shells[q].l + 1; ++f)
+      for (int m = 0; m < n_mo; ++m)
+        S.C[(S.sh[qs].ao_offset + f) * n_mo + m] = mo_coeff[(user_off[q] + f) * n_mo + m];
+  }
   S.precision = LRDMC_PRECISION_DF64;
   fill_df_constants(S);
   s->Lo = make_layout(S);
@@ -340,7 +373,7 @@ lrdmc_status lrdmc_spacing_params(lrdmc_system_t s, double a, const lrdmc_spacin
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct WsPlan {
-  size_t rec, parent, logw, el, jumps, cum, trace, moves, err, counter, total;
+  size_t rec, parent, order, logw, el, jumps, cum, trace, moves, err, counter, total;
 };
 
 static WsPlan plan_ws(const Layout& Lo, int W, int cap)
@@ -349,6 +382,7 @@ static WsPlan plan_ws(const Layout& Lo, int W, int cap)
   size_t o = 0;
   p.rec = o; o += align256(sizeof(double) * (size_t)W * Lo.rec) * 2;
   p.parent = o; o += align256(sizeof(int) * (size_t)W);
+  p.order = o; o += align256(sizeof(int) * (size_t)W);
   p.logw = o; o += align256(sizeof(double) * (size_t)W);
   p.el = o; o += align256(sizeof(double) * (size_t)W);
   p.jumps = o; o += align256(sizeof(int) * (size_t)W);
@@ -412,6 +446,7 @@ lrdmc_status lrdmc_init_walkers(lrdmc_system_t s, int W, const double* x0, uint6
   s->cur = 0;
   PopDev& P = s->P;
   P.parent = (int*)(s->ws + p.parent);
+  P.order = (int*)(s->ws + p.order);
   P.logw = (double*)(s->ws + p.logw);
   P.el_end = (double*)(s->ws + p.el);
   P.jumps = (int*)(s->ws + p.jumps);
@@ -471,6 +506,7 @@ lrdmc_status lrdmc_step(lrdmc_system_t s, int n_steps, double a, const lrdmc_spa
     if (e != cudaSuccess) return cuda_fail(s, e, "k_eval_all launch");
     s->have_eval = true;
     s->eval_lat = L;
+    s->eval_prec = s->S.precision;
   }
   for (int n = 0; n < n_steps; ++n) {
     const uint64_t k = s->k;
@@ -489,7 +525,7 @@ lrdmc_status lrdmc_step(lrdmc_system_t s, int n_steps, double a, const lrdmc_spa
       cudaEventRecord(ev[1], s->stream);
       cudaEventRecord(ev[2], s->stream);
     }
-    e = launch_reconfig(P, k, s->stream);
+    e = launch_reconfig(P, s->Lo, k, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "k_reconfig launch");
     if (ev) cudaEventRecord(ev[3], s->stream);
     s->cur = 1 - s->cur;
@@ -578,7 +614,15 @@ lrdmc_status lrdmc_get_walkers(lrdmc_system_t s, double* x, double* el, double* 
     if (x) memcpy(&x[(size_t)t * 3 * Lo.N], r + Lo.off_x, sizeof(double) * 3 * Lo.N);
     if (el) el[t] = r[Lo.off_el];
     if (b) b[t] = r[Lo.off_b];
-    if (T && P) memcpy(&T[(size_t)t * P], r + Lo.off_T, sizeof(double) * P);
+    if (T && P) {
+      if (s->eval_prec == LRDMC_PRECISION_DF64) {
+        // rates cached as double-floats (two floats per slot)
+        const float* f = reinterpret_cast<const float*>(r + Lo.off_T);
+        for (int c = 0; c < P; ++c) T[(size_t)t * P + c] = (double)f[2 * c] + (double)f[2 * c + 1];
+      } else {
+        memcpy(&T[(size_t)t * P], r + Lo.off_T, sizeof(double) * P);
+      }
+    }
   }
   if (parent) memcpy(parent, par.data(), sizeof(int) * W);
   return LRDMC_OK;
@@ -667,7 +711,8 @@ lrdmc_status lrdmc_save(lrdmc_system_t s, const char* path)
   if (e != cudaSuccess) return cuda_fail(s, e, "save copy");
   FILE* f = fopen(path, "wb");
   if (!f) return fail(s, LRDMC_ERR_ARG, std::string("save: cannot open ") + path);
-  int64_t hdr[8] = {(int64_t)kMagic, W, s->Lo.rec, s->trace_cap, (int64_t)s->k, s->have_eval ? 1 : 0, 0, 0};
+  int64_t hdr[8] = {(int64_t)kMagic, W, s->Lo.rec, s->trace_cap, (int64_t)s->k, s->have_eval ? 1 : 0,
+                    s->eval_prec, 0};
   bool ok = fwrite(hdr, sizeof(hdr), 1, f) == 1 && fwrite(&s->eval_lat, sizeof(LatDev), 1, f) == 1 &&
             fwrite(rec.data(), sizeof(double), rec.size(), f) == rec.size() &&
             fwrite(par.data(), sizeof(int), W, f) == (size_t)W &&
@@ -712,7 +757,8 @@ lrdmc_status lrdmc_load(lrdmc_system_t s, const char* path)
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "load copy");
   s->k = (uint64_t)hdr[4];
-  s->have_eval = hdr[5] != 0;
+  s->have_eval = hdr[5] != 0 && hdr[6] == s->S.precision;
+  s->eval_prec = (int)hdr[6];
   s->eval_lat = L;
   return LRDMC_OK;
 }
@@ -722,6 +768,7 @@ lrdmc_status lrdmc_set_precision(lrdmc_system_t s, int precision)
   if (!s) return fail(s, LRDMC_ERR_ARG, "");
   if (precision != LRDMC_PRECISION_FP64 && precision != LRDMC_PRECISION_DF64)
     return fail(s, LRDMC_ERR_ARG, "set_precision: unknown precision");
+  if (precision != s->S.precision) s->have_eval = false;  // cached rates change format
   s->S.precision = precision;
   return LRDMC_OK;
 }

@@ -68,6 +68,7 @@ struct SysDev {
   double Z[kMaxNuc];
   double en_b1[kMaxNuc];
   int heavy[kMaxNuc];  // 1 for the nuclei with Z = Z_max (centres of p)
+  int nuc_shell_begin[kMaxNuc + 1];  // shells are sorted by centre: [begin[I], begin[I+1])
   double b_ee, c_par, c_anti, en_b2;
   double V_nn;
   ShellDev sh[kMaxShell];
@@ -105,6 +106,7 @@ struct PopDev {
   double* rec_src;
   double* rec_dst;
   int* parent;
+  int* order;  // processing order of the slots (longest expected interval first)
   double* logw;
   double* el_end;
   int* jumps;
@@ -128,7 +130,7 @@ cudaError_t launch_eval_all(const SysDev& S, const Layout& Lo, const LatDev& L, 
                             cudaStream_t st);
 cudaError_t launch_interval(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P,
                             uint64_t k, int recompute, cudaStream_t st);
-cudaError_t launch_reconfig(const PopDev& P, uint64_t k, cudaStream_t st);
+cudaError_t launch_reconfig(const PopDev& P, const Layout& Lo, uint64_t k, cudaStream_t st);
 cudaError_t launch_evaluate(const SysDev& S, const Layout& Lo, const LatDev& L, int n,
                             const double* x, const double* rot, double* ratio, double* T,
                             double* b, double* el, int* err, cudaStream_t st);

@@ -112,6 +112,35 @@ __device__ double warp_scan(const double* T, int P, int lane, double target, int
   return carry;
 }
 
+__device__ __forceinline__ bool df_lt(df a, df b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+
+// The chunked scan of warp_scan over double-float rates.
+__device__ df warp_scan_df(const df* T, int P, int lane, df target, int* pick, int* last)
+{
+  df carry = df_make(0.0f, 0.0f);
+  int p = -1, lp = -1;
+  for (int base = 0; base < P; base += 32) {
+    int c = base + lane;
+    df t = (c < P) ? T[c] : df_make(0.0f, 0.0f);
+    df v = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      df y = df_make(__shfl_up_sync(FULL_MASK, v.hi, o), __shfl_up_sync(FULL_MASK, v.lo, o));
+      if (lane >= o) v = df_add(v, y);
+    }
+    df C = df_add(carry, v);
+    if (pick) {
+      unsigned hit = __ballot_sync(FULL_MASK, (c < P) && df_lt(target, C));
+      if (p < 0 && hit) p = base + __ffs(hit) - 1;
+      unsigned pos = __ballot_sync(FULL_MASK, (c < P) && (t.hi > 0.0f));
+      if (pos) lp = base + 31 - __clz(pos);
+    }
+    carry = df_make(__shfl_sync(FULL_MASK, C.hi, 31), __shfl_sync(FULL_MASK, C.lo, 31));
+  }
+  if (pick) { *pick = p; *last = lp; }
+  return carry;
+}
+
 // ----------------------------------------------------------------------------
 // Atomic orbitals: chi = S(d) R(|d|), d = r - R_centre, S a real solid
 // harmonic of degree l, R Slater r^m exp(-zeta r) or a Gaussian contraction.
@@ -338,19 +367,17 @@ __device__ __forceinline__ WarpMem warp_mem(const Layout& Lo, const SysDev& S, d
   return m;
 }
 
-// Block-shared tables: MO coefficients, then the 2^(j/64) table (floats).
+// Block-shared tables: MO coefficients, then the 2^(j/64) table.
 struct BlockMem {
   double* C;
-  float* thi;
-  float* tlo;
+  float2* tab;
 };
 
 __device__ __forceinline__ BlockMem block_mem(const SysDev& S, double* smem)
 {
   BlockMem b;
   b.C = smem;
-  b.thi = reinterpret_cast<float*>(smem + S.n_ao * S.n_mo);
-  b.tlo = b.thi + 64;
+  b.tab = reinterpret_cast<float2*>(smem + S.n_ao * S.n_mo);
   return b;
 }
 
@@ -543,12 +570,12 @@ __device__ __forceinline__ df radial_value_df(const SysDev& S, const ShellDev& s
       for (int j = 0; j < sh.m_int; ++j) pw = df_mul(pw, r);
       return df_mul(pw, e);
     }
-    df lr = df_log(r, S.D.exp.K, bm.thi, bm.tlo);
-    return df_mul(df_exp(df_mul(dsh.m, lr), S.D.exp.K, bm.thi, bm.tlo), e);
+    df lr = df_log(r, S.D.exp.K, bm.tab);
+    return df_mul(df_exp(df_mul(dsh.m, lr), S.D.exp.K, bm.tab), e);
   }
   df R = dfz();
   for (int p = 0; p < sh.n_prim; ++p)
-    R = df_add(R, df_mul(dsh.coef[p], df_exp(df_neg(df_mul(dsh.alpha[p], r2)), S.D.exp.K, bm.thi, bm.tlo)));
+    R = df_add(R, df_mul(dsh.coef[p], df_exp(df_neg(df_mul(dsh.alpha[p], r2)), S.D.exp.K, bm.tab)));
   return R;
 }
 
@@ -588,7 +615,7 @@ __device__ df ao_dot_df(const SysDev& S, const df* v, const df p[3], const Block
       r2 = df_dot3(d[0], d[1], d[2]);
       r = df_sqrt(r2);
     }
-    if (sh.kind == 0 && !sh.same_exp) e = df_exp(df_neg(df_mul(dsh.zeta, r)), S.D.exp.K, bm.thi, bm.tlo);
+    if (sh.kind == 0 && !sh.same_exp) e = df_exp(df_neg(df_mul(dsh.zeta, r)), S.D.exp.K, bm.tab);
     df R = radial_value_df(S, sh, dsh, r, r2, e, bm);
     df Sv[5];
     int nf = solid_df(sh.l, d, Sv);
@@ -597,6 +624,60 @@ __device__ df ao_dot_df(const SysDev& S, const df* v, const df p[3], const Block
     acc = df_add(acc, df_mul(part, R));
   }
   return acc;
+}
+
+// Per nucleus I (one distance each): the determinant ratio
+// sum_mu v[mu] chi_mu(p) over the shells centred on I, and the e-n Jastrow
+// sum_I b1_I r/(1 + b2 r) (returned with the sign of J).
+__device__ void nucleus_terms_df(const SysDev& S, const df* v, const df p[3], const BlockMem& bm, df& rdet,
+                                 df& jen)
+{
+  rdet = dfz();
+  jen = dfz();
+  for (int I = 0; I < S.n_nuc; ++I) {
+    df d[3] = {df_sub_fast(p[0], S.D.nuc[I][0]), df_sub_fast(p[1], S.D.nuc[I][1]),
+               df_sub_fast(p[2], S.D.nuc[I][2])};
+    df r2 = df_dot3(d[0], d[1], d[2]);
+    df r = df_sqrt(r2);
+    if (S.en_b1[I] != 0.0)
+      jen = df_sub(jen, df_div(df_mul(S.D.en_b1[I], r), df_add_f(df_mul(S.D.en_b2, r), 1.0f)));
+    df e = dfz();
+    for (int q = S.nuc_shell_begin[I]; q < S.nuc_shell_begin[I + 1]; ++q) {
+      const ShellDev& sh = S.sh[q];
+      const DfShell& dsh = S.D.sh[q];
+      if (sh.kind == 0 && !sh.same_exp) e = df_exp(df_neg(df_mul(dsh.zeta, r)), S.D.exp.K, bm.tab);
+      df R = radial_value_df(S, sh, dsh, r, r2, e, bm);
+      df part;
+      if (sh.l == 0) {
+        part = v[sh.ao_offset];
+      } else {
+        df Sv[5];
+        int nf = solid_df(sh.l, d, Sv);
+        part = dfz();
+        for (int f = 0; f < nf; ++f) part = df_add(part, df_mul(v[sh.ao_offset + f], Sv[f]));
+      }
+      rdet = df_add(rdet, df_mul(part, R));
+    }
+  }
+}
+
+// sum_{j != i} u_ee(|p - r_j|): the Pade terms c r/(1 + b r) (all of one
+// sign) are summed as one running fraction num/den, so one division serves
+// all partners.
+__device__ df jastrow_ee_df(const SysDev& S, const df* xd, int i, const df p[3])
+{
+  df num = dfz(), den = df_make(1.0f, 0.0f);
+  const int si = spin_of(S, i);
+  for (int j = 0; j < S.N; ++j) {
+    if (j == i) continue;
+    df d0 = df_sub_fast(p[0], xd[3 * j]), d1 = df_sub_fast(p[1], xd[3 * j + 1]), d2 = df_sub_fast(p[2], xd[3 * j + 2]);
+    df r = df_sqrt(df_dot3(d0, d1, d2));
+    df c = (spin_of(S, j) == si) ? S.D.c_par : S.D.c_anti;
+    df dj = df_add_f(df_mul(S.D.b_ee, r), 1.0f);
+    num = df_add_fast(df_mul(num, dj), df_mul(df_mul(c, r), den));
+    den = df_mul(den, dj);
+  }
+  return df_div(num, den);
 }
 
 // sum_{j != i} u_ee(|p - r_j|) + sum_I u_en(|p - R_I|) in double-float.
@@ -634,7 +715,7 @@ __device__ __forceinline__ df p_weight_df(const SysDev& S, const LatDev& L, cons
     df d2s = df_dot3(d0, d1, d2);
     if (d2s.hi < best.hi || (d2s.hi == best.hi && d2s.lo < best.lo)) best = d2s;
   }
-  if (L.pkind == 0) return df_exp(df_neg(df_mul(best, L.p_coef_df)), S.D.exp.K, bm.thi, bm.tlo);
+  if (L.pkind == 0) return df_exp(df_neg(df_mul(best, L.p_coef_df)), S.D.exp.K, bm.tab);
   return df_rcp(df_add_f(df_mul(L.p_coef_df, best), 1.0f));
 }
 
@@ -688,7 +769,7 @@ __device__ void el_parts_df(const SysDev& S, const WarpMem& wm, int i, int part,
       r = df_sqrt(r2);
       ir = df_rcp(r);
     }
-    if (sh.kind == 0 && !sh.same_exp) e = df_exp(df_neg(df_mul(dsh.zeta, r)), S.D.exp.K, bm.thi, bm.tlo);
+    if (sh.kind == 0 && !sh.same_exp) e = df_exp(df_neg(df_mul(dsh.zeta, r)), S.D.exp.K, bm.tab);
     df R, R1, R2;
     if (sh.kind == 0) {
       R = radial_value_df(S, sh, dsh, r, r2, e, bm);
@@ -699,7 +780,7 @@ __device__ void el_parts_df(const SysDev& S, const WarpMem& wm, int i, int part,
       R = dfz(); R1 = dfz(); R2 = dfz();
       for (int p = 0; p < sh.n_prim; ++p) {
         df al = dsh.alpha[p];
-        df g = df_mul(dsh.coef[p], df_exp(df_neg(df_mul(al, r2)), S.D.exp.K, bm.thi, bm.tlo));
+        df g = df_mul(dsh.coef[p], df_exp(df_neg(df_mul(al, r2)), S.D.exp.K, bm.tab));
         R = df_add(R, g);
         df m2a = df_mul_f(al, -2.0f);
         R1 = df_add(R1, df_mul(m2a, g));
@@ -792,7 +873,7 @@ __device__ __forceinline__ df el_local(const ElParts& o)
 }
 
 __device__ void warp_eval_df(const SysDev& S, const double* sC, const LatDev& L, const WarpMem& wm,
-                             int lane, double* ratio_out, double& b, double& el)
+                             int lane, double* ratio_out, double& b, df& bdf, double& el)
 {
   const int N = S.N, nao = S.n_ao, nu = S.n_up;
   const BlockMem bm = block_mem(S, const_cast<double*>(sC));
@@ -845,9 +926,10 @@ __device__ void warp_eval_df(const SysDev& S, const double* sC, const LatDev& L,
     const df e0 = wm.Rd[k], e1 = wm.Rd[3 + k], e2 = wm.Rd[6 + k];
     const df* ri = &wm.xd[3 * i];
     df p[3] = {df_add(ri[0], df_mul(h, e0)), df_add(ri[1], df_mul(h, e1)), df_add(ri[2], df_mul(h, e2))};
-    df rdet = ao_dot_df(S, &wm.vd[i * nao], p, bm);
-    df dJ = df_sub(jastrow_terms_df(S, wm.xd, i, p), wm.Sd[i]);
-    df rho = df_mul(rdet, df_exp(dJ, S.D.exp.K, bm.thi, bm.tlo));
+    df rdet, jen;
+    nucleus_terms_df(S, &wm.vd[i * nao], p, bm, rdet, jen);
+    df dJ = df_sub(df_add(jastrow_ee_df(S, wm.xd, i, p), jen), wm.Sd[i]);
+    df rho = df_mul(rdet, df_exp(dJ, S.D.exp.K, bm.tab));
     df w = df_make(1.0f, 0.0f);
     if (G == 2) {
       df hh = df_make(0.5f * h.hi, 0.5f * h.lo);
@@ -855,22 +937,27 @@ __device__ void warp_eval_df(const SysDev& S, const double* sC, const LatDev& L,
       df pm = p_weight_df(S, L, mid, bm);
       w = g ? df_add_f(df_neg(pm), 1.0f) : pm;
     }
-    double T = 0.0;
-    if (rho.hi > 0.0f) T = df_to_double(df_mul(df_mul(w, g ? L.inv2ap2_df : L.inv2a2_df), rho));
-    wm.T[c] = T;
+    df T = dfz();
+    if (rho.hi > 0.0f) T = df_mul(df_mul(w, g ? L.inv2ap2_df : L.inv2a2_df), rho);
+    reinterpret_cast<df*>(wm.T)[c] = T;  // rates stay double-float in this mode
     if (ratio_out) ratio_out[c] = df_to_double(rho);
   }
   __syncwarp();
-  b = warp_scan(wm.T, P, lane, 0.0, nullptr, nullptr);
+  bdf = warp_scan_df(reinterpret_cast<const df*>(wm.T), P, lane, dfz(), nullptr, nullptr);
+  b = df_to_double(bdf);
 }
 
 template <int PREC>
 __device__ __forceinline__ void warp_eval_any(const SysDev& S, const double* sC, const LatDev& L,
                                               const WarpMem& wm, int lane, double* ratio_out, double& b,
-                                              double& el)
+                                              df& bdf, double& el)
 {
-  if (PREC == LRDMC_PRECISION_DF64) warp_eval_df(S, sC, L, wm, lane, ratio_out, b, el);
-  else warp_eval(S, sC, L, wm, lane, ratio_out, b, el);
+  if (PREC == LRDMC_PRECISION_DF64) {
+    warp_eval_df(S, sC, L, wm, lane, ratio_out, b, bdf, el);
+  } else {
+    warp_eval(S, sC, L, wm, lane, ratio_out, b, el);
+    bdf = df_make(0.0f, 0.0f);
+  }
 }
 
 // ----------------------------------------------------------------------------
@@ -898,7 +985,7 @@ __device__ void ao_values_df_lanes(const SysDev& S, const double* p, double* out
       r2 = df_dot3(d[0], d[1], d[2]);
       r = df_sqrt(r2);
     }
-    if (sh.kind == 0 && !sh.same_exp) e = df_exp(df_neg(df_mul(dsh.zeta, r)), S.D.exp.K, bm.thi, bm.tlo);
+    if (sh.kind == 0 && !sh.same_exp) e = df_exp(df_neg(df_mul(dsh.zeta, r)), S.D.exp.K, bm.tab);
     df R = radial_value_df(S, sh, dsh, r, r2, e, bm);
     df Sv[5];
     int nf = solid_df(sh.l, d, Sv);
@@ -977,10 +1064,7 @@ __device__ __forceinline__ void stage_coefficients(const SysDev& S, double* sC)
 {
   for (int j = threadIdx.x; j < S.n_ao * S.n_mo; j += blockDim.x) sC[j] = S.C[j];
   BlockMem bm = block_mem(S, sC);
-  for (int j = threadIdx.x; j < 64; j += blockDim.x) {
-    bm.thi[j] = S.D.exp.t_hi[j];
-    bm.tlo[j] = S.D.exp.t_lo[j];
-  }
+  for (int j = threadIdx.x; j < 64; j += blockDim.x) bm.tab[j] = S.D.exp.t[j];
   __syncthreads();
 }
 
@@ -1008,6 +1092,7 @@ k_init(const __grid_constant__ SysDev S, const Layout Lo, const PopDev P, const 
     draw_uniforms(P.seed, (uint64_t)s, kIntervalInit, 0, kTagRot, u);
     rotation_matrix(u[0], u[1], u[2], wm.R);
     P.parent[s] = s;
+    P.order[s] = s;
   }
   store_record(Lo, P.rec_src + (size_t)s * Lo.rec, wm, lane, NAN, NAN);
 }
@@ -1025,8 +1110,9 @@ k_eval_all(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
   WarpMem wm = warp_mem(Lo, S, sC + Lo.head + wib * Lo.smem_warp);
   double* rec = P.rec_src + (size_t)s * Lo.rec;
   double b, el;
+  df bdf;
   load_record(Lo, rec, wm, lane, b, el);
-  warp_eval_any<PREC>(S, sC, L, wm, lane, nullptr, b, el);
+  warp_eval_any<PREC>(S, sC, L, wm, lane, nullptr, b, bdf, el);
   if (!isfinite(el) || !isfinite(b)) {
     if (lane == 0) atomicOr(P.err, kErrNonFinite);
   }
@@ -1048,14 +1134,17 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   WarpMem wm = warp_mem(Lo, S, sC + Lo.head + wib * Lo.smem_warp);
   const int P_moves = S.N * 6 * L.G;
+  const BlockMem bm = block_mem(S, sC);
   for (;;) {
-    int s = 0;
-    if (lane == 0) s = atomicAdd(P.counter, 1);
-    s = __shfl_sync(FULL_MASK, s, 0);
-    if (s >= P.W) break;
+    int idx = 0;
+    if (lane == 0) idx = atomicAdd(P.counter, 1);
+    idx = __shfl_sync(FULL_MASK, idx, 0);
+    if (idx >= P.W) break;
+    const int s = P.order[idx];
     const int src = P.parent[s];
     double b, el;
     load_record(Lo, P.rec_src + (size_t)src * Lo.rec, wm, lane, b, el);
+    df bdf = df_from_double(b);
     if (recompute) {
       bool ok = warp_inverse(S, sC, wm.x, 0, wm.A, wm.scr, lane);
       ok = ok && warp_inverse(S, sC, wm.x, 1, wm.A + Lo.nu * Lo.nu, wm.scr, lane);
@@ -1066,7 +1155,12 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
     for (uint64_t m = 0;; ++m) {
       double u[4];
       draw_uniforms(P.seed, (uint64_t)s, k, m, kTagTimeHB, u);
-      double t = b > 0.0 ? -log(u[0]) / b : INFINITY;
+      double t;
+      if (PREC == LRDMC_PRECISION_DF64)
+        t = b > 0.0 ? df_to_double(df_div(df_neg(df_log(df_from_double(u[0]), S.D.exp.K, bm.tab)), bdf))
+                    : INFINITY;
+      else
+        t = b > 0.0 ? -log(u[0]) / b : INFINITY;
       if (t >= tau_left) {
         logw -= tau_left * (el - P.e_trial);
         break;
@@ -1075,7 +1169,11 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
       tau_left -= t;
       // heat bath over the cached rates
       int pick, last;
-      warp_scan(wm.T, P_moves, lane, u[1] * b, &pick, &last);
+      if (PREC == LRDMC_PRECISION_DF64)
+        warp_scan_df(reinterpret_cast<const df*>(wm.T), P_moves, lane, df_mul(df_from_double(u[1]), bdf), &pick,
+                     &last);
+      else
+        warp_scan(wm.T, P_moves, lane, u[1] * b, &pick, &last);
       if (pick < 0) pick = last;
       if (pick < 0) {  // no allowed move: cannot happen with b > 0
         if (lane == 0) atomicOr(P.err, kErrNonFinite);
@@ -1097,7 +1195,7 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
       __syncwarp();
       if (lane == 0) rotation_matrix(ur[0], ur[1], ur[2], wm.R);
       __syncwarp();
-      warp_eval_any<PREC>(S, sC, L, wm, lane, nullptr, b, el);
+      warp_eval_any<PREC>(S, sC, L, wm, lane, nullptr, b, bdf, el);
       ++jumps;
       if (!isfinite(el) || !isfinite(b)) {
         if (lane == 0) atomicOr(P.err, kErrNonFinite);
@@ -1121,7 +1219,8 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
 // Reconfiguration at the end of interval k (one block of 1024 threads):
 // w_s = exp(log w_s), trace (weighted mean E_L, mean weight, mean jumps),
 // comb parents: slot t takes the smallest s with (t + xi) C_W / W < C_s.
-__global__ void __launch_bounds__(1024) k_reconfig(const PopDev P, uint64_t k)
+__global__ void __launch_bounds__(1024) k_reconfig(const PopDev P, const double* rec_next, int rec_stride,
+                                                  int off_b, uint64_t k)
 {
   __shared__ double s_run[1024];
   __shared__ double s_e[32], s_j[32], s_w[32];
@@ -1180,6 +1279,61 @@ __global__ void __launch_bounds__(1024) k_reconfig(const PopDev P, uint64_t k)
     *P.moves += (unsigned long long)(s_w[1] + 0.5);
     *P.counter = 0;
   }
+  // Processing order of the next interval, longest expected first: a slot's
+  // number of jumps is about tau times the total rate b of the walker it
+  // receives, so the slots are bucketed by that b in descending order (a
+  // counting sort over 64 buckets; the order inside a bucket is arbitrary and
+  // does not affect any result).
+  __shared__ int s_cnt[64];
+  __shared__ float s_lo[32], s_hi[32];
+  float bmin = INFINITY, bmax = -INFINITY;
+  for (int tt = lo; tt < hi; ++tt) {
+    float bt = (float)rec_next[(size_t)P.parent[tt] * rec_stride + off_b];
+    bmin = fminf(bmin, bt);
+    bmax = fmaxf(bmax, bt);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    bmin = fminf(bmin, __shfl_xor_sync(FULL_MASK, bmin, o));
+    bmax = fmaxf(bmax, __shfl_xor_sync(FULL_MASK, bmax, o));
+  }
+  if ((t & 31) == 0) { s_lo[t >> 5] = bmin; s_hi[t >> 5] = bmax; }
+  if (t < 64) s_cnt[t] = 0;
+  __syncthreads();
+  if (t < 32) {
+    float a = (t < (nt >> 5)) ? s_lo[t] : INFINITY, c = (t < (nt >> 5)) ? s_hi[t] : -INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a = fminf(a, __shfl_xor_sync(FULL_MASK, a, o));
+      c = fmaxf(c, __shfl_xor_sync(FULL_MASK, c, o));
+    }
+    if (t == 0) { s_lo[0] = a; s_hi[0] = c; }
+  }
+  __syncthreads();
+  const float gmin = s_lo[0], gmax = s_hi[0];
+  const float scale = (gmax > gmin) ? 64.0f / (gmax - gmin) : 0.0f;
+  for (int tt = lo; tt < hi; ++tt) {
+    float bt = (float)rec_next[(size_t)P.parent[tt] * rec_stride + off_b];
+    int q = (int)((bt - gmin) * scale);
+    q = 63 - min(63, max(0, q));
+    atomicAdd(&s_cnt[q], 1);
+  }
+  __syncthreads();
+  if (t == 0) {
+    int run = 0;
+    for (int q = 0; q < 64; ++q) {
+      int c = s_cnt[q];
+      s_cnt[q] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  for (int tt = lo; tt < hi; ++tt) {
+    float bt = (float)rec_next[(size_t)P.parent[tt] * rec_stride + off_b];
+    int q = (int)((bt - gmin) * scale);
+    q = 63 - min(63, max(0, q));
+    P.order[atomicAdd(&s_cnt[q], 1)] = tt;
+  }
 }
 
 // Stateless evaluation of given configurations (one warp per configuration).
@@ -1207,9 +1361,12 @@ k_evaluate(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, in
   }
   const int P = S.N * 6 * L.G;
   double b, el;
-  warp_eval_any<PREC>(S, sC, L, wm, lane, ratio ? ratio + (size_t)c * P : nullptr, b, el);
+  df bdf;
+  warp_eval_any<PREC>(S, sC, L, wm, lane, ratio ? ratio + (size_t)c * P : nullptr, b, bdf, el);
   if (T)
-    for (int j = lane; j < P; j += 32) T[(size_t)c * P + j] = wm.T[j];
+    for (int j = lane; j < P; j += 32)
+      T[(size_t)c * P + j] = (PREC == LRDMC_PRECISION_DF64) ? df_to_double(reinterpret_cast<const df*>(wm.T)[j])
+                                                            : wm.T[j];
   if (lane == 0) {
     if (b_out) b_out[c] = b;
     if (el_out) el_out[c] = el;
@@ -1255,8 +1412,7 @@ void fill_df_constants(SysDev& S)
   D.exp.K.pad = 0.0f;
   for (int j = 0; j < 64; ++j) {
     df t = split_ld(exp2l((long double)j / 64.0L));
-    D.exp.t_hi[j] = t.hi;
-    D.exp.t_lo[j] = t.lo;
+    D.exp.t[j] = make_float2(t.hi, t.lo);
   }
 }
 
@@ -1369,9 +1525,9 @@ cudaError_t launch_interval(const SysDev& S, const Layout& Lo, const LatDev& L, 
   return launch_interval_t<LRDMC_PRECISION_FP64>(S, Lo, L, P, k, recompute, st);
 }
 
-cudaError_t launch_reconfig(const PopDev& P, uint64_t k, cudaStream_t st)
+cudaError_t launch_reconfig(const PopDev& P, const Layout& Lo, uint64_t k, cudaStream_t st)
 {
-  k_reconfig<<<1, 1024, 0, st>>>(P, k);
+  k_reconfig<<<1, 1024, 0, st>>>(P, P.rec_dst, Lo.rec, Lo.off_b, k);
   return cudaGetLastError();
 }
 
@@ -1437,9 +1593,12 @@ k_evaluate_static(const __grid_constant__ SysDev S, const Layout Lo, const LatDe
   }
   const int P = S.N * 6 * L.G;
   double b, el;
-  warp_eval_any<PREC>(S, sC, L, wm, lane, ratio ? ratio + (size_t)c * P : nullptr, b, el);
+  df bdf;
+  warp_eval_any<PREC>(S, sC, L, wm, lane, ratio ? ratio + (size_t)c * P : nullptr, b, bdf, el);
   if (T)
-    for (int j = lane; j < P; j += 32) T[(size_t)c * P + j] = wm.T[j];
+    for (int j = lane; j < P; j += 32)
+      T[(size_t)c * P + j] = (PREC == LRDMC_PRECISION_DF64) ? df_to_double(reinterpret_cast<const df*>(wm.T)[j])
+                                                            : wm.T[j];
   if (lane == 0) {
     if (b_out) b_out[c] = b;
     if (el_out) el_out[c] = el;
