@@ -132,27 +132,45 @@ class ClockSampler:
                 "samples": len(sms)}
 
 
-def run_ours(args):
-    import torch
+# FP32 operation counts of the double-float primitives as implemented in
+# csrc/df64.cuh (add/sub/mul = 1, fma = 2, MUFU seed = 1).
+DF_ADD, DF_ADD_FAST, DF_ADD_F, DF_MUL, DF_SQR = 20, 11, 10, 10, 9
+DF_DIV, DF_SQRT, DF_EXP, DF_LOG = 31, 30, 110, 142
+FP32_PEAK_TFLOPS = 80.5  # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 
-    import paper_1909_01589_gb300 as pkg
 
-    rank, world, local = _env_rank()
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
+def df_flops_per_move(system, G):
+    """Algorithmic FP32 work of one walker-move in the double-float
+    formulation: the double-float operations of one evaluation of all
+    P = 6 G N moves and of the local energy, plus the jump, weighted by the
+    FP32 operation count of each primitive. Counted from the formulas."""
+    N, n_nuc, n_ao = system.N, system.n_nuc, system.n_ao
+    exps = len({(s.center, s.zeta) for s in system.shells if s.kind == 0}) + \
+        sum(len(s.alpha) for s in system.shells if s.kind == 1)
+    P = 6 * G * N
+    dist = 3 * DF_ADD_FAST + 3 * DF_SQR + 2 * DF_ADD_FAST + DF_SQRT
+    per_cand = (3 * (DF_MUL + DF_ADD)                                    # displaced position
+                + n_nuc * (dist + 3 * DF_MUL + DF_ADD_F + DF_DIV + DF_ADD)  # nucleus distance, e-n term
+                + exps * (DF_MUL + DF_EXP) + n_ao * (DF_MUL + DF_ADD) + 2 * n_ao * DF_MUL  # basis, dot
+                + (N - 1) * (dist + 4 * DF_MUL + DF_ADD_F + DF_ADD_FAST) + DF_DIV  # e-e Pade fraction
+                + 2 * DF_ADD + DF_EXP + DF_MUL                                  # Jastrow ratio
+                + ((3 * (DF_MUL + DF_ADD) + n_nuc * (3 * DF_ADD_FAST + 3 * DF_SQR + 2 * DF_ADD_FAST)
+                    + DF_MUL + DF_EXP + DF_ADD_F) if G == 2 else 0)             # p at the midpoint
+                + 2 * DF_MUL)                                                    # rate
+    pair_el = dist + 2 * DF_DIV + 10 * DF_MUL + 8 * DF_ADD                      # u', u'', gradients
+    el = N * (n_nuc * (dist + DF_DIV) + exps * (DF_MUL + DF_EXP) + n_ao * (12 * DF_MUL + 8 * DF_ADD)
+              + (N - 1 + n_nuc) * pair_el + 8 * DF_MUL + 8 * DF_ADD)
+    jump = DF_LOG + DF_DIV + 2 * P * DF_ADD + n_ao * (DF_MUL + DF_EXP / 3)      # time, scans, orbitals
+    return P * per_cand + el + jump
 
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    system = S.neon()
-    W = args.walkers
+
+def measure_leg(args, pkg, torch, system, precision, dev, rank, seed, x0, with_clocks):
+    """W warm-up intervals, then K timed intervals, each bracketed by CUDA
+    events on the library's stream with an L2 flush between them."""
+    _, world, local = _env_rank()
     spacing = pkg.Spacing(pkg.THIS_WORK)
     a = WORKLOAD["a"]
-    seed = SEED + 7919 * rank
-    x0 = S.initial_positions(system, W, seed)
-    prec = pkg.PRECISION_DF64 if args.precision == "df64" else pkg.PRECISION_FP64
-    g = pkg.LrdmcSystem(system).set_precision(prec)
+    g = pkg.LrdmcSystem(system).set_precision(precision)
     cap = args.warmup + args.steps + 8
     g.init_walkers(torch.tensor(x0, device=dev), seed=seed, tau=WORKLOAD["tau"], e_trial=WORKLOAD["e_trial"],
                    recompute_every=WORKLOAD["recompute_every"], trace_capacity=cap)
@@ -164,69 +182,120 @@ def run_ours(args):
     g.set_profiling(True)
     g.kernel_times(reset=True)
     m0 = g.moves()
-    step_ms = []
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    if dist is not None:
+    if world > 1:
+        import torch.distributed as dist
+
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        t_wall0 = time.perf_counter()
-        for k in range(args.steps):
-            flush.zero_()  # L2 flush between timed steps (outside the events)
-            starts[k].record(stream)
-            g.step(1, a, spacing)
-            stops[k].record(stream)
-        g.sync()
-        torch.cuda.synchronize()
-        t_wall = time.perf_counter() - t_wall0
-    if dist is not None:
-        dist.barrier()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, stops)]
+    clk = ClockSampler(local) if with_clocks else None
+    if clk:
+        clk.__enter__()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (outside the events)
+        starts[k].record(stream)
+        g.step(1, a, spacing)
+        stops[k].record(stream)
+    g.sync()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    if clk:
+        clk.__exit__(None, None, None)
+    step_ms = [s0.elapsed_time(s1) for s0, s1 in zip(starts, stops)]
     moves = g.moves() - m0
     t_int_ms, t_rec_ms, n_int, n_rec = g.kernel_times()
-    total_ms = float(sum(step_ms))
-    local_rate = moves / (total_ms * 1e-3)
+    e_tr, w_tr, j_tr = g.energy_trace()
+    return dict(total_ms=float(sum(step_ms)), moves=moves, t_int_ms=t_int_ms, t_rec_ms=t_rec_ms, n_int=n_int,
+                n_rec=n_rec, e=e_tr[-args.steps:], w=w_tr[-args.steps:], j=j_tr[-args.steps:], wall=t_wall,
+                clocks=clk.summary() if clk else None, g=g)
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1909_01589_gb300 as pkg
+    from paper_1909_01589_gb300 import stats
+
+    rank, world, local = _env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    system = S.neon()
+    W = args.walkers
+    seed = SEED + 7919 * rank
+    x0 = S.initial_positions(system, W, seed)
+    main_prec = pkg.PRECISION_DF64 if args.precision == "df64" else pkg.PRECISION_FP64
+    leg = measure_leg(args, pkg, torch, system, main_prec, dev, rank, seed, x0, True)
+    # the plain FP64 path on the same workload, seeds and steps (for the
+    # efficiency comparison the metric asks for)
+    fp = None
+    if main_prec != pkg.PRECISION_FP64 and args.fp64_leg:
+        fp = measure_leg(args, pkg, torch, system, pkg.PRECISION_FP64, dev, rank, seed, x0, False)
     # e2e: the public API from host memory: H2D of the start configurations,
-    # init, the same K steps, each followed by a D2H read of the trace.
+    # init, the same steps, each followed by a D2H read of the trace.
+    spacing = pkg.Spacing(pkg.THIS_WORK)
+    cap = args.warmup + args.steps + 8
     x0h = torch.tensor(x0).pin_memory()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    g2 = pkg.LrdmcSystem(system).set_precision(prec)
+    g2 = pkg.LrdmcSystem(system).set_precision(main_prec)
     g2.init_walkers(x0h.numpy(), seed=seed, tau=WORKLOAD["tau"], e_trial=WORKLOAD["e_trial"],
                     recompute_every=WORKLOAD["recompute_every"], trace_capacity=cap)
     d2h = 0
-    for k in range(args.warmup + args.steps):
-        g2.step(1, a, spacing)
-        e_tr, _, _ = g2.energy_trace(max_n=k + 1)
+    n_e2e = args.warmup + args.steps
+    for k in range(n_e2e):
+        g2.step(1, WORKLOAD["a"], spacing)
+        g2.energy_trace(max_n=k + 1)
         d2h += 3 * 8 * (k + 1)
     e2e_moves = g2.moves()
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
-    n_e2e = args.warmup + args.steps
-    e2e_rate = e2e_moves / t_e2e
-    e_trace, w_trace, j_trace = g.energy_trace()
     if dist is not None:
-        t = torch.tensor([total_ms, float(moves), t_e2e, float(e2e_moves)], dtype=torch.float64, device=dev)
-        gathered = [torch.zeros_like(t) for _ in range(world)]
-        dist.all_gather(gathered, t)
-        gathered = torch.stack(gathered).cpu().numpy()
-        total_ms = float(gathered[:, 0].max())
-        moves_all = float(gathered[:, 1].sum())
-        t_e2e_all = float(gathered[:, 2].max())
-        e2e_all = float(gathered[:, 3].sum())
+        value, total_ms, moves_all = stats.reduce_throughput(leg["total_ms"], leg["moves"])
+        e2e_all, t_e2e_all, _ = stats.reduce_throughput(t_e2e * 1e3, e2e_moves)
+        t_e2e_all *= 1e-3
+        e2e_moves_all = e2e_all * t_e2e_all
     else:
-        moves_all, t_e2e_all, e2e_all = float(moves), t_e2e, float(e2e_moves)
-    value = moves_all / (total_ms * 1e-3)
+        total_ms, moves_all = leg["total_ms"], float(leg["moves"])
+        value = moves_all / (total_ms * 1e-3)
+        t_e2e_all, e2e_moves_all = t_e2e, float(e2e_moves)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
     G = 2
-    flop_per_move = 2.0 * dfma_equiv_per_move(system, G)
-    moves_per_launch = moves / max(n_int, 1)
-    achieved_tflops = flop_per_move * moves_per_launch / (t_int_ms / max(n_int, 1) * 1e-3) / 1e12
-    traffic = _read_traffic()
+    n_int = max(leg["n_int"], 1)
+    kernel_ms = leg["t_int_ms"] / n_int
+    moves_per_launch = leg["moves"] / n_int
+    if main_prec == pkg.PRECISION_DF64:
+        flop_per_move = df_flops_per_move(system, G)
+        achieved = flop_per_move * moves_per_launch / (kernel_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_interval<df64>", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                "peak_source": "nominal FP32 pipe (152 SM x 128 lanes x 2 flop x 2.07 GHz; 70 TF measured with "
+                               "csrc/fp64_rates.cu); work = FP32 flops of the double-float formulation",
+                "flop_per_move": flop_per_move}
+    else:
+        flop_per_move = 2.0 * dfma_equiv_per_move(system, G)
+        achieved = flop_per_move * moves_per_launch / (kernel_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_interval<fp64>", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "peak_source": "nominal FP64 (recipe: 1.25 TF = 152 SM x 2 DFMA/clk x 2 x 2.07 GHz); "
+                               "no FP64 entry in MEASURED_PEAKS.json",
+                "flop_per_move": flop_per_move}
+    roof["kernel_ms_per_launch"] = kernel_ms
+    roof["traffic"] = _read_traffic(main_prec == pkg.PRECISION_DF64)
+    t_sec = leg["total_ms"] * 1e-3
+    err, _ = stats.reblock(leg["e"])
+    eff = {"value": stats.efficiency(leg["e"], t_sec), "unit": "1/(Ha^2 s)", "sigma_mean_Ha": err,
+           "seconds": t_sec, "energy_Ha": stats.energy_estimate(leg["e"], leg["w"], 0),
+           "intervals": len(leg["e"])}
     out = {
         "metric": METRIC,
         "value": value,
@@ -238,39 +307,43 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32x2 (double-float evaluation) + f64 state" if args.precision == "df64" else "f64",
+        "dtype": "f32x2 (double-float evaluation) + f64 state" if main_prec == pkg.PRECISION_DF64 else "f64",
         "data": "synthetic",
         "config": {"workload": "Ne all-electron, 4096 walkers, a=0.2 bohr, smart double grid (this work), "
                                "tau=0.025, FP64-parity arithmetic", **WORKLOAD, "evaluation": args.precision,
                    "walkers_per_gpu": W, "l2": "flushed between timed steps (512 MiB write)",
                    "parallelism": f"replicas x{world}"},
-        "e2e": {"value": e2e_all / t_e2e_all, "unit": "walker-moves/s",
+        "e2e": {"value": e2e_moves_all / t_e2e_all, "unit": "walker-moves/s",
                 "h2d_bytes_per_step": x0.nbytes / n_e2e, "d2h_bytes_per_step": d2h / n_e2e,
                 "includes": "H2D of start configurations, init, warmup+timed steps, per-step trace D2H"},
-        "gpu_launches": int(n_int + n_rec),
-        "roofline": {"bound": "alu", "kernel": "k_interval", "achieved": achieved_tflops,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / FP64_PEAK_TFLOPS,
-                     "peak_source": "nominal FP64 (recipe: 1.25 TF = 152 SM x 2 DFMA/clk x 2 x 2.07 GHz); "
-                                    "no FP64 entry in MEASURED_PEAKS.json",
-                     "flop_per_move": flop_per_move, "kernel_ms_per_launch": t_int_ms / max(n_int, 1),
-                     "traffic": traffic},
-        "kernel_share": {"k_interval_ms": t_int_ms, "k_reconfig_ms": t_rec_ms},
-        "mean_jumps_per_interval": float(np.mean(j_trace[-args.steps:])),
-        "energy_mean_timed": float(np.mean(e_trace[-args.steps:])),
-        "clocks": clk.summary(),
-        "wall_s_timed": t_wall,
+        "gpu_launches": int(leg["n_int"] + leg["n_rec"]),
+        "roofline": roof,
+        "efficiency": eff,
+        "kernel_share": {"k_interval_ms": leg["t_int_ms"], "k_reconfig_ms": leg["t_rec_ms"]},
+        "mean_jumps_per_interval": float(np.mean(leg["j"])),
+        "clocks": leg["clocks"],
+        "wall_s_timed": leg["wall"],
     }
+    if fp is not None:
+        fp_value = fp["moves"] / (fp["total_ms"] * 1e-3)
+        fp_eff = stats.efficiency(fp["e"], fp["total_ms"] * 1e-3)
+        out["vs_plain_fp64"] = {
+            "fp64_value": fp_value, "speedup": value / fp_value if world == 1 else None,
+            "fp64_efficiency": fp_eff, "efficiency_ratio": eff["value"] / fp_eff,
+            "fp64_energy_Ha": stats.energy_estimate(fp["e"], fp["w"], 0),
+            "energy_difference_Ha": eff["energy_Ha"] - stats.energy_estimate(fp["e"], fp["w"], 0),
+            "fp64_kernel_ms_per_launch": fp["t_int_ms"] / max(fp["n_int"], 1)}
     out["cpu_baseline"] = cpu_baseline(args) if args.cpu_seconds > 0 else None
     print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
 
-def _read_traffic():
+def _read_traffic(df64=True):
     """dram bytes per k_interval launch from the committed ncu summary, if the
     kernel source has not changed since it was taken; else None."""
-    path = os.path.join(ROOT, "profiles", "k_interval_ne4096_traffic.json")
+    name = "k_interval_df64_ne4096_traffic.json" if df64 else "k_interval_ne4096_traffic.json"
+    path = os.path.join(ROOT, "profiles", name)
     try:
         d = json.load(open(path))
     except (OSError, ValueError):
@@ -344,6 +417,8 @@ def main():
                     help="CPU-baseline budget (<= 0: no CPU baseline)")
     ap.add_argument("--precision", default="df64", choices=["df64", "fp64"],
                     help="evaluation arithmetic: double-float on the FP32 pipe or IEEE double")
+    ap.add_argument("--no-fp64-leg", dest="fp64_leg", action="store_false",
+                    help="skip the plain-FP64 comparison leg")
     ap.add_argument("--walkers", type=int, default=WORKLOAD["n_walkers"],
                     help="walkers per GPU (smaller cases for profiling)")
     args = ap.parse_args()
