@@ -30,6 +30,9 @@ def _inputs():
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile liblrdmc.so unless it is newer than every source. Extra nvcc
+    flags (tuning macros such as -DLRDMC_DF_OUTLINE) come from the
+    environment variable LRDMC_NVCC_FLAGS."""
     if not force and os.path.exists(LIB):
         newest = max(os.path.getmtime(f) for f in _inputs())
         if os.path.getmtime(LIB) >= newest:
@@ -38,6 +41,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
     extra = ["-Xptxas", "-v"] if verbose else []
+    extra += os.environ.get("LRDMC_NVCC_FLAGS", "").split()
 
     def compile_one(src):
         obj = os.path.join(build_dir, os.path.splitext(src)[0] + ".o")

@@ -24,6 +24,15 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+// Functions with long bodies (exp, log, sqrt, division) are kept out of
+// line in device code when LRDMC_DF_OUTLINE is defined, trading call
+// overhead for a smaller instruction footprint.
+#if defined(__CUDA_ARCH__) && defined(LRDMC_DF_OUTLINE)
+#define DF_HEAVY __host__ __device__ __noinline__
+#else
+#define DF_HEAVY __host__ __device__ __forceinline__
+#endif
+
 namespace lrdmc {
 
 struct df {
@@ -139,7 +148,7 @@ __host__ __device__ __forceinline__ float f_rsqrt_approx(float x)
 
 // a / b: FP32 quotient q1, then one correction q2 = (a - b q1) / b from the
 // exactly computed remainder (relative error ~2^-45).
-__host__ __device__ __forceinline__ df df_div(df a, df b)
+DF_HEAVY df df_div(df a, df b)
 {
   float r = f_rcp_approx(b.hi);
   float q1 = DF_MUL(a.hi, r);
@@ -154,7 +163,7 @@ __host__ __device__ __forceinline__ df df_div(df a, df b)
 __host__ __device__ __forceinline__ df df_rcp(df b) { return df_div(df_make(1.0f, 0.0f), b); }
 
 // sqrt(a), a >= 0: s = a_hi rsqrt(a_hi), corrected by the exact residual.
-__host__ __device__ __forceinline__ df df_sqrt(df a)
+DF_HEAVY df df_sqrt(df a)
 {
   if (!(a.hi > 0.0f)) return df_make(0.0f, 0.0f);
   float y = f_rsqrt_approx(a.hi);
@@ -178,7 +187,7 @@ struct ExpTable {
 };
 
 // e^a for a in about [-87, 88]; 0 below, +inf above. tab: the table.
-__host__ __device__ __forceinline__ df df_exp(df a, const ExpConsts& K, const float2* tab)
+DF_HEAVY df df_exp(df a, const ExpConsts& K, const float2* tab)
 {
   if (a.hi < -87.0f) return df_make(0.0f, 0.0f);
   if (a.hi > 88.0f) return df_make(INFINITY, 0.0f);
@@ -215,7 +224,7 @@ __host__ __device__ __forceinline__ df df_exp(df a, const ExpConsts& K, const fl
 }
 
 // log(a), a > 0: FP32 seed y0, then one Newton step y0 + a e^(-y0) - 1.
-__host__ __device__ __forceinline__ df df_log(df a, const ExpConsts& K, const float2* tab)
+DF_HEAVY df df_log(df a, const ExpConsts& K, const float2* tab)
 {
   float y0 = logf(a.hi);
   df t = df_mul(a, df_exp(df_make(-y0, 0.0f), K, tab));

@@ -1123,8 +1123,11 @@ k_eval_all(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
 // projection of the cited LRDMC method): wait for an exponential time of
 // rate b_x, decrease log w by (E_L - E_T) times the time spent, and at the
 // end of the wait jump to move c with probability T_c / b_x.
+#ifndef LRDMC_INTERVAL_MIN_BLOCKS
+#define LRDMC_INTERVAL_MIN_BLOCKS 4
+#endif
 template <int PREC>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, LRDMC_INTERVAL_MIN_BLOCKS)
 k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, const PopDev P,
            uint64_t k, int recompute)
 {
