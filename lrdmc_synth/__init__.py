@@ -200,12 +200,146 @@ def tiny_mixed(seed: int = 7) -> System:
     )
 
 
+# ---------------------------------------------------------------- Gaussian fits
+_FIT_CACHE = {}
+
+
+def sto_gaussian_fit(m: float, l: int, n: int = 6):
+    """Even-tempered least-squares fit of a Slater radial function r^m e^(-r)
+    (zeta = 1) by n Gaussians sum_p c_p exp(-alpha_p r^2), alpha_p =
+    alpha_0 beta^p, weighted by the volume element of the whole function
+    r^(2 + 2l). The even-tempered form keeps the exponents apart so the
+    coefficients stay well conditioned. For exponent zeta the primitives
+    are alpha_p zeta^2 with coefficients c_p zeta^m (the radial part scales
+    as zeta^-m (zeta r)^m e^(-zeta r))."""
+    key = (float(m), int(l), int(n))
+    if key in _FIT_CACHE:
+        return _FIT_CACHE[key]
+    from scipy.optimize import least_squares
+
+    r = np.concatenate([np.linspace(1e-4, 0.5, 300), np.linspace(0.5, 30.0, 1500)])
+    wgt = r ** (1 + l)
+    target = r ** m * np.exp(-r)
+
+    def solve(p):
+        a = np.exp(p[0]) * np.exp(p[1]) ** np.arange(n)
+        G = np.exp(-np.outer(r * r, a))
+        c, *_ = np.linalg.lstsq(G * wgt[:, None], target * wgt, rcond=None)
+        return a, c, (G @ c - target) * wgt
+
+    res = least_squares(lambda p: solve(p)[2], [np.log(0.04), np.log(3.0)],
+                        bounds=([np.log(1e-3), np.log(1.6)], [np.log(10.0), np.log(8.0)]),
+                        xtol=1e-12, ftol=1e-12)
+    a, c, _ = solve(res.x)
+    _FIT_CACHE[key] = (a, c)
+    return a, c
+
+
+def gto_shell(center: int, l: int, n_eff: float, zeta: float) -> Shell:
+    """Contracted-Gaussian stand-in for the Slater shell r^(n-1-l) e^(-zeta r)."""
+    m = n_eff - 1.0 - l
+    a, c = sto_gaussian_fit(m, l)
+    return Shell(center, l, GTO, alpha=list(a * zeta * zeta), coef=list(c * zeta ** m))
+
+
+def _slater_atom_shells(Z: int):
+    """(n, l, n*, zeta, electrons) of a closed-shell atom by Slater's rules
+    (occupations in Madelung order)."""
+    nstar = {1: 1.0, 2: 2.0, 3: 3.0, 4: 3.7, 5: 4.0}
+    groups = {  # Z -> list of (n, kind, occupation) in Slater's order
+        18: [(1, "sp", 2), (2, "sp", 8), (3, "sp", 8)],
+        36: [(1, "sp", 2), (2, "sp", 8), (3, "sp", 8), (3, "d", 10), (4, "sp", 8)],
+        8: [(1, "sp", 2), (2, "sp", 6)],
+    }[Z]
+    out = []
+    for gi, (n, kind, occ) in enumerate(groups):
+        s = (occ - 1) * (0.30 if n == 1 else 0.35)
+        for gj, (n2, kind2, occ2) in enumerate(groups):
+            if gj == gi:
+                continue
+            if kind == "sp":
+                if n2 == n - 1:
+                    s += 0.85 * occ2
+                elif n2 < n - 1:
+                    s += occ2
+            elif gj < gi:
+                s += occ2
+        zeta = (Z - s) / nstar[n]
+        if kind == "sp":
+            out.append((n, 0, nstar[n], zeta))
+            if occ > 2:
+                out.append((n, 1, nstar[n], zeta))
+        else:
+            out.append((n, 2, nstar[n], zeta))
+    return out
+
+
+def _gto_atom(Z: int, name: str) -> System:
+    """Closed-shell atom Z with one determinant of STO-6G-style orbitals
+    (Slater's-rule exponents, each Slater function fitted by 6 Gaussians);
+    Gaussians have no nuclear cusp, so the e-n factor -Z r/(1 + Z r) supplies
+    all of it (slope -Z at the nucleus, bounded far away)."""
+    xyz, Zs = _atom(Z)
+    shells = [gto_shell(0, l, nst, zeta) for (n, l, nst, zeta) in _slater_atom_shells(Z)]
+    n_ao = sum(2 * s.l + 1 for s in shells)
+    nel = Z // 2
+    C = np.eye(n_ao)[:, :nel]
+    orbital_shell = []
+    for q, s in enumerate(shells):
+        orbital_shell += [q] * (2 * s.l + 1)
+    return System(
+        name=name, nuc_xyz=xyz, Z=Zs, n_up=nel, n_dn=nel, shells=shells, C=C,
+        b_ee=1.0, c_par=0.25, c_anti=0.5, en_b1=np.array([float(Z)]), en_b2=float(Z),
+        orbital_shell=orbital_shell[:nel],
+    )
+
+
+def argon() -> System:
+    """Ar (Z = 18, 9 up / 9 down): 1s, 2s, 2p, 3s, 3p STO-6G-style orbitals."""
+    return _gto_atom(18, "Ar")
+
+
+def krypton() -> System:
+    """Kr (Z = 36, 18 up / 18 down): 1s ... 4s, 4p and 3d STO-6G-style
+    orbitals; the 4s/4p Slater functions have the non-integer n* = 3.7."""
+    return _gto_atom(36, "Kr")
+
+
+WATER_H = np.array([[1.430, 1.107, 0.0], [-1.430, 1.107, 0.0]])
+
+
+def water() -> System:
+    """H2O: O at the origin, H at (+-1.430, 1.107, 0) bohr; STO-6G-style O 1s,
+    2s, 2p (Slater's rules) and H 1s (zeta = 1.24) Gaussians; five doubly
+    occupied orbitals from a fixed, non-degenerate mixing; e-n factors with
+    the full cusps -Z_I r/(1 + 4 r)."""
+    xyz = np.vstack([np.zeros(3), WATER_H])
+    Zs = np.array([8.0, 1.0, 1.0])
+    oshells = [gto_shell(0, l, nst, zeta) for (n, l, nst, zeta) in _slater_atom_shells(8)]
+    shells = oshells + [gto_shell(1, 0, 1.0, 1.24), gto_shell(2, 0, 1.0, 1.24)]
+    # AOs: O1s, O2s, O2px, O2py, O2pz, H1 1s, H2 1s
+    C = np.zeros((7, 5))
+    C[0, 0] = 1.0
+    C[1, 1], C[5, 1], C[6, 1] = 1.0, 0.3, 0.3
+    C[2, 2], C[5, 2], C[6, 2] = 1.0, 0.4, -0.4
+    C[3, 3], C[5, 3], C[6, 3] = 1.0, 0.25, 0.25
+    C[4, 4] = 1.0
+    return System(
+        name="H2O", nuc_xyz=xyz, Z=Zs, n_up=5, n_dn=5, shells=shells, C=C,
+        b_ee=1.0, c_par=0.25, c_anti=0.5, en_b1=Zs.copy(), en_b2=4.0,
+        orbital_shell=[0, 1, 2, 2, 2],
+    )
+
+
 SYSTEMS = {
     "H": hydrogen,
     "He": helium,
     "Ne": neon,
     "Be_bare": be_bare,
     "tiny_mixed": tiny_mixed,
+    "Ar": argon,
+    "Kr": krypton,
+    "H2O": water,
 }
 
 

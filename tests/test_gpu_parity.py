@@ -49,7 +49,8 @@ def spacing_pair(pkg, oracle_mod, system, a, kind, rc=0.5, ratio=1.5):
 EVAL_CASES = [
     ("He", "single", 0.2), ("He", "this_work", 0.2), ("Ne", "single", 0.1), ("Ne", "this_work", 0.2),
     ("Ne", "previous", 0.4), ("tiny_mixed", "explicit", 0.3), ("Be_bare", "explicit", 0.25),
-    ("H", "this_work", 0.3),
+    ("H", "this_work", 0.3), ("Ar", "this_work", 1 / 63), ("Kr", "this_work", 1 / 126),
+    ("Kr", "single", 0.05), ("H2O", "this_work", 0.1),
 ]
 
 
@@ -146,6 +147,9 @@ def _compare_runs(pkg, oracle_mod, system, kind, a, W, n_steps, tau, seed, e_tri
     ("Ne", "previous", 0.3, 9, 6, 0.01, -128.9),
     ("Be_bare", "explicit", 0.2, 16, 10, 0.02, -20.0),
     ("H", "single", 0.3, 5, 10, 0.05, -0.5),
+    ("Ar", "this_work", 1 / 63, 12, 3, 2e-4, -527.5),
+    ("Kr", "this_work", 1 / 126, 6, 2, 3e-5, -2752.0),
+    ("H2O", "this_work", 0.1, 20, 4, 0.005, -76.0),
 ])
 def test_projection_matches_oracle(pkg, oracle_mod, name, kind, a, W, steps, tau, et, prec):
     """Whole intervals: waiting times, heat-bath choices, Sherman-Morrison

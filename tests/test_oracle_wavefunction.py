@@ -113,7 +113,7 @@ def test_en_cusp(oracle_mod):
     assert abs(E[1] - E[2]) < 1e-5 and abs(E[0] - E[1]) < 1e-3
 
 
-@pytest.mark.parametrize("name", ["He", "Ne", "tiny_mixed", "Be_bare"])
+@pytest.mark.parametrize("name", ["He", "Ne", "tiny_mixed", "Be_bare", "Ar", "H2O"])
 def test_lattice_ratios_match_brute_force(oracle_mod, name):
     """Every psi_G(x')/psi_G(x) of the lattice evaluation (inverse-column
     route) equals the ratio of brute-force determinants and Jastrow sums."""
@@ -282,3 +282,44 @@ def test_rates_and_sign_flip(oracle_mod):
         assert abs(ev["b"] - np.sum(ev["T"])) < 1e-12 * ev["b"]
         flips += int(np.sum(ev["ratio"] < 0))
     assert flips > 0
+
+
+def test_heavy_atom_rule_polyatomic(oracle_mod):
+    """Large systems: R_c runs over the heaviest atoms only, so near an H of
+    H2O p is still the Gaussian of the distance to O."""
+    s, o = _osys(oracle_mod, "H2O")
+    lat = oracle_mod.lattice_for(s, 0.1, oracle_mod.THIS_WORK)
+    near_h = S.WATER_H[0] + np.array([0.05, -0.02, 0.01])
+    d2 = float(np.sum(near_h ** 2))
+    assert abs(o.p(lat, near_h) - np.exp(-d2 / (2 * lat.rc ** 2))) < 1e-15
+    # r_c and a'/a come from the heaviest atom (Z = 8)
+    assert abs(lat.rc - oracle_mod.rc_this_work(0.1, 8.0)) < 1e-15
+
+
+@pytest.mark.parametrize("name", ["Ar", "Kr", "H2O"])
+def test_gaussian_atoms_cusp_and_laplacian(oracle_mod, name):
+    """STO-6G-style atoms: the e-n factor carries the whole nuclear cusp, so
+    E_L stays finite as an electron reaches a nucleus; the analytic Laplacian
+    matches second differences of the brute-force psi."""
+    s, o = _osys(oracle_mod, name)
+    x = S.initial_positions(s, 1, 61)[0]
+    d = np.array([0.3, -0.5, 0.81]) / np.linalg.norm([0.3, -0.5, 0.81])
+    E = []
+    for eps in (1e-5, 1e-7):
+        y = x.copy()
+        y[0] = s.nuc_xyz[0] + eps * d
+        E.append(o.local_energy(y))
+    assert abs(E[0] - E[1]) < 1e-2 * max(1.0, abs(E[1]))
+    lap, _ = o.laplacian_terms(x)
+    h = 1e-4
+    la0, _ = o.log_psi(x)
+    fd = 0.0
+    for i in range(s.N):
+        for k in range(3):
+            for sg in (1, -1):
+                y = x.copy()
+                y[i, k] += sg * h
+                la, sgn = o.log_psi(y)
+                fd += np.exp(la - la0)
+    fd = (fd - 6 * s.N) / (h * h)
+    assert abs(fd - lap) < 1e-4 * max(1.0, abs(lap))
