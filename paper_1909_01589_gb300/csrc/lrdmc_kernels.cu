@@ -405,15 +405,22 @@ __device__ bool warp_inverse(const SysDev& S, const double* sC, const double* sx
     }
   }
   __syncwarp();
-  // scale of the matrix: a pivot below 1e-13 of it means a numerically
-  // singular Slater matrix (e.g. two equal-spin electrons on one point)
-  double scale = 0.0;
-  for (int idx = lane; idx < n * n; idx += 32) scale = fmax(scale, fabs(M[(idx / n) * w2 + idx % n]));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) scale = fmax(scale, __shfl_xor_sync(FULL_MASK, scale, o));
-  const double tiny = 1e-13 * scale;
-  bool ok = scale > 0.0;
+  // A pivot below 1e-13 of the largest entry its column had before the
+  // elimination marks a numerically singular Slater matrix (two equal-spin
+  // electrons on one point leave a residual row of rounding size). The
+  // test is per column: orbitals of very different size (core and valence
+  // of a heavy atom) make pivots legitimately small against the largest
+  // entry of the whole matrix.
+  double* colmax = chi;  // [n], chi rows are no longer needed
+  for (int m = lane; m < n; m += 32) {
+    double c = 0.0;
+    for (int l = 0; l < n; ++l) c = fmax(c, fabs(M[l * w2 + m]));
+    colmax[m] = c;
+  }
+  __syncwarp();
+  bool ok = true;
   for (int col = 0; col < n && ok; ++col) {
+    const double tiny = 1e-13 * colmax[col];
     // pivot row: largest |M[r][col]| for r >= col, lowest r on ties
     double best = -1.0;
     int br = col;
