@@ -230,13 +230,17 @@ def run_ours(args):
     W = args.walkers
     seed = SEED + 7919 * rank
     x0 = S.initial_positions(system, W, seed)
-    main_prec = pkg.PRECISION_DF64 if args.precision == "df64" else pkg.PRECISION_FP64
+    main_prec = {"df64": pkg.PRECISION_DF64, "fp64": pkg.PRECISION_FP64, "fp32": pkg.PRECISION_FP32}[args.precision]
     leg = measure_leg(args, pkg, torch, system, main_prec, dev, rank, seed, x0, True)
     # the plain FP64 path on the same workload, seeds and steps (for the
     # efficiency comparison the metric asks for)
     fp = None
     if main_prec != pkg.PRECISION_FP64 and args.fp64_leg:
         fp = measure_leg(args, pkg, torch, system, pkg.PRECISION_FP64, dev, rank, seed, x0, False)
+    # the mixed-precision form (single-precision evaluation, FP64 state)
+    mx = None
+    if args.mixed_leg and main_prec != pkg.PRECISION_FP32:
+        mx = measure_leg(args, pkg, torch, system, pkg.PRECISION_FP32, dev, rank, seed, x0, False)
     # e2e: the public API from host memory: H2D of the start configurations,
     # init, the same steps, each followed by a D2H read of the trace.
     spacing = pkg.Spacing(pkg.THIS_WORK)
@@ -333,6 +337,22 @@ def run_ours(args):
             "fp64_energy_Ha": stats.energy_estimate(fp["e"], fp["w"], 0),
             "energy_difference_Ha": eff["energy_Ha"] - stats.energy_estimate(fp["e"], fp["w"], 0),
             "fp64_kernel_ms_per_launch": fp["t_int_ms"] / max(fp["n_int"], 1)}
+    if mx is not None:
+        mx_value = mx["moves"] / (mx["total_ms"] * 1e-3)
+        mx_err, _ = stats.reblock(mx["e"])
+        mx_energy = stats.energy_estimate(mx["e"], mx["w"], 0)
+        ref_leg = fp if fp is not None else leg
+        ref_err, _ = stats.reblock(ref_leg["e"])
+        ref_energy = stats.energy_estimate(ref_leg["e"], ref_leg["w"], 0)
+        out["mixed_precision"] = {
+            "mode": "fp32 evaluation, fp64 inverse/weights/reconfiguration", "value": mx_value,
+            "efficiency": stats.efficiency(mx["e"], mx["total_ms"] * 1e-3),
+            "efficiency_ratio_vs_fp64": stats.efficiency(mx["e"], mx["total_ms"] * 1e-3) /
+            stats.efficiency(ref_leg["e"], ref_leg["total_ms"] * 1e-3),
+            "energy_Ha": mx_energy, "sigma_mean_Ha": mx_err,
+            "energy_minus_fp64_Ha": mx_energy - ref_energy,
+            "combined_sigma_Ha": float(np.hypot(mx_err, ref_err)),
+            "kernel_ms_per_launch": mx["t_int_ms"] / max(mx["n_int"], 1)}
     out["cpu_baseline"] = cpu_baseline(args) if args.cpu_seconds > 0 else None
     print(json.dumps(out), flush=True)
     if dist is not None:
@@ -415,10 +435,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="CPU-baseline budget (<= 0: no CPU baseline)")
-    ap.add_argument("--precision", default="df64", choices=["df64", "fp64"],
+    ap.add_argument("--precision", default="df64", choices=["df64", "fp64", "fp32"],
                     help="evaluation arithmetic: double-float on the FP32 pipe or IEEE double")
     ap.add_argument("--no-fp64-leg", dest="fp64_leg", action="store_false",
                     help="skip the plain-FP64 comparison leg")
+    ap.add_argument("--no-mixed-leg", dest="mixed_leg", action="store_false",
+                    help="skip the mixed-precision (FP32 evaluation) leg")
     ap.add_argument("--walkers", type=int, default=WORKLOAD["n_walkers"],
                     help="walkers per GPU (smaller cases for profiling)")
     args = ap.parse_args()

@@ -226,12 +226,18 @@ LRDMC_API lrdmc_status lrdmc_load(lrdmc_system_t sys, const char* path);
  * arithmetic on the FP32 pipe (pairs of floats, about 48 significant bits,
  * relative error ~1e-14; GB300 runs FP64 at 1/69 of its FP32 rate) and
  * keeps the inverse Slater matrices, Sherman-Morrison updates, weights,
- * heat bath and reconfiguration in IEEE double. Values below about 1e-30
- * lose low-order bits in double-float (their contribution to any sum is
- * then negligible); arguments of exp below -87 give 0. Takes effect at the
- * next lrdmc_step / lrdmc_evaluate call. */
+ * and reconfiguration in IEEE double. Values below about 1e-30 lose
+ * low-order bits in double-float (their contribution to any sum is then
+ * negligible); arguments of exp below -87 give 0. LRDMC_PRECISION_FP32 is
+ * the mixed-precision mode: the same evaluation, waiting time and heat bath
+ * in IEEE single precision (ratios and local energies to ~1e-6 relative),
+ * with FP64 kept for the inverse Slater matrices (updates and periodic
+ * recomputation), weights and reconfiguration; its results are not
+ * FP64-parity results but statistically equivalent ones. Takes effect at
+ * the next lrdmc_step / lrdmc_evaluate call. */
 #define LRDMC_PRECISION_FP64 0
 #define LRDMC_PRECISION_DF64 1
+#define LRDMC_PRECISION_FP32 2
 LRDMC_API lrdmc_status lrdmc_set_precision(lrdmc_system_t sys, int precision);
 
 /* Kernel timing for measurement. With profiling on, lrdmc_step brackets

@@ -26,7 +26,7 @@ STATIC_EVAL_MAX = 262144
 
 OK, ERR_ARG, ERR_CUDA, ERR_SINGULAR, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE = range(7)
 SINGLE, THIS_WORK, PREVIOUS, EXPLICIT = 0, 1, 2, 3
-PRECISION_FP64, PRECISION_DF64 = 0, 1
+PRECISION_FP64, PRECISION_DF64, PRECISION_FP32 = 0, 1, 2
 
 EXPORTED = [
     "lrdmc_create_system", "lrdmc_spacing_params", "lrdmc_workspace_bytes", "lrdmc_init_walkers",
@@ -256,8 +256,9 @@ class LrdmcSystem:
         return m.value
 
     def set_precision(self, precision):
-        """PRECISION_FP64 (IEEE double everywhere) or PRECISION_DF64 (default:
-        double-float evaluation on the FP32 pipe, FP64 state and updates)."""
+        """PRECISION_FP64 (IEEE double everywhere), PRECISION_DF64 (default:
+        double-float evaluation on the FP32 pipe, FP64 state and updates) or
+        PRECISION_FP32 (mixed: single-precision evaluation, FP64 state)."""
         self._check(load_library().lrdmc_set_precision(self.h, int(precision)))
         return self
 

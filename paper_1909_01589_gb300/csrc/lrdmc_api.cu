@@ -615,7 +615,7 @@ lrdmc_status lrdmc_get_walkers(lrdmc_system_t s, double* x, double* el, double* 
     if (el) el[t] = r[Lo.off_el];
     if (b) b[t] = r[Lo.off_b];
     if (T && P) {
-      if (s->eval_prec == LRDMC_PRECISION_DF64) {
+      if (s->eval_prec != LRDMC_PRECISION_FP64) {
         // rates cached as double-floats (two floats per slot)
         const float* f = reinterpret_cast<const float*>(r + Lo.off_T);
         for (int c = 0; c < P; ++c) T[(size_t)t * P + c] = (double)f[2 * c] + (double)f[2 * c + 1];
@@ -766,7 +766,7 @@ lrdmc_status lrdmc_load(lrdmc_system_t s, const char* path)
 lrdmc_status lrdmc_set_precision(lrdmc_system_t s, int precision)
 {
   if (!s) return fail(s, LRDMC_ERR_ARG, "");
-  if (precision != LRDMC_PRECISION_FP64 && precision != LRDMC_PRECISION_DF64)
+  if (precision != LRDMC_PRECISION_FP64 && precision != LRDMC_PRECISION_DF64 && precision != LRDMC_PRECISION_FP32)
     return fail(s, LRDMC_ERR_ARG, "set_precision: unknown precision");
   if (precision != s->S.precision) s->have_eval = false;  // cached rates change format
   s->S.precision = precision;

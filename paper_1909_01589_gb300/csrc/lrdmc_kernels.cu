@@ -21,6 +21,7 @@
 #include <mutex>
 
 #include "lrdmc_internal.h"
+#include "mixed_arith.cuh"
 
 namespace lrdmc {
 
@@ -107,35 +108,6 @@ __device__ double warp_scan(const double* T, int P, int lane, double target, int
       if (pos) lp = base + 31 - __clz(pos);
     }
     carry = __shfl_sync(FULL_MASK, C, 31);
-  }
-  if (pick) { *pick = p; *last = lp; }
-  return carry;
-}
-
-__device__ __forceinline__ bool df_lt(df a, df b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
-
-// The chunked scan of warp_scan over double-float rates.
-__device__ df warp_scan_df(const df* T, int P, int lane, df target, int* pick, int* last)
-{
-  df carry = df_make(0.0f, 0.0f);
-  int p = -1, lp = -1;
-  for (int base = 0; base < P; base += 32) {
-    int c = base + lane;
-    df t = (c < P) ? T[c] : df_make(0.0f, 0.0f);
-    df v = t;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      df y = df_make(__shfl_up_sync(FULL_MASK, v.hi, o), __shfl_up_sync(FULL_MASK, v.lo, o));
-      if (lane >= o) v = df_add(v, y);
-    }
-    df C = df_add(carry, v);
-    if (pick) {
-      unsigned hit = __ballot_sync(FULL_MASK, (c < P) && df_lt(target, C));
-      if (p < 0 && hit) p = base + __ffs(hit) - 1;
-      unsigned pos = __ballot_sync(FULL_MASK, (c < P) && (t.hi > 0.0f));
-      if (pos) lp = base + 31 - __clz(pos);
-    }
-    carry = df_make(__shfl_sync(FULL_MASK, C.hi, 31), __shfl_sync(FULL_MASK, C.lo, 31));
   }
   if (pick) { *pick = p; *last = lp; }
   return carry;
@@ -554,116 +526,97 @@ __device__ void warp_eval(const SysDev& S, const double* sC, const LatDev& L, co
 }
 
 // ----------------------------------------------------------------------------
-// The same evaluation in double-float arithmetic on the FP32 pipe
-// (LRDMC_PRECISION_DF64). Inputs are converted once per evaluation
-// (positions, rotation, projected inverse columns); every lattice move and
-// the local energy are computed in double-float; rates and the local energy
-// are converted back to double.
+// The evaluation on the FP32 pipe, templated on the number type NT:
+//   NT = df    double-float (LRDMC_PRECISION_DF64), accurate to FP64 parity;
+//   NT = float single precision (LRDMC_PRECISION_FP32), the mixed mode.
+// Inputs are converted once per evaluation (positions, rotation, projected
+// inverse columns) and kept as double-floats in shared memory (the FP32 mode
+// reads their high parts); every lattice move and the local energy are
+// computed in NT; rates stay in NT (stored as double-floats), the local
+// energy is converted to double.
 // ----------------------------------------------------------------------------
-__device__ __forceinline__ df dfz() { return df_make(0.0f, 0.0f); }
-
-__device__ __forceinline__ df df_dot3(df a0, df a1, df a2)
+template <class NT>
+__device__ __forceinline__ NT dot3(NT a0, NT a1, NT a2)
 {
-  return df_add_fast(df_add_fast(df_sqr(a0), df_sqr(a1)), df_sqr(a2));
+  typedef Ar<NT> A;
+  return A::add_fast(A::add_fast(A::sqr(a0), A::sqr(a1)), A::sqr(a2));
 }
 
-// Slater radial part r^m e^(-zeta r) as double-float (e given).
-__device__ __forceinline__ df radial_value_df(const SysDev& S, const ShellDev& sh, const DfShell& dsh,
-                                              df r, df r2, df e, const BlockMem& bm)
+// Slater radial part r^m e^(-zeta r) (e given) or a Gaussian contraction.
+template <class NT>
+__device__ __forceinline__ NT radial_value_m(const SysDev& S, const ShellDev& sh, const DfShell& dsh, NT r, NT r2,
+                                             NT e, const BlockMem& bm)
 {
+  typedef Ar<NT> A;
   if (sh.kind == 0) {
     if (sh.m_int >= 0) {
-      df pw = df_make(1.0f, 0.0f);
-      for (int j = 0; j < sh.m_int; ++j) pw = df_mul(pw, r);
-      return df_mul(pw, e);
+      NT pw = A::one();
+      for (int j = 0; j < sh.m_int; ++j) pw = A::mul(pw, r);
+      return A::mul(pw, e);
     }
-    df lr = df_log(r, S.D.exp.K, bm.tab);
-    return df_mul(df_exp(df_mul(dsh.m, lr), S.D.exp.K, bm.tab), e);
+    NT lr = A::log(r, S.D.exp.K, bm.tab);
+    return A::mul(A::exp(A::mul(A::c(dsh.m), lr), S.D.exp.K, bm.tab), e);
   }
-  df R = dfz();
+  NT acc = A::zero();
   for (int p = 0; p < sh.n_prim; ++p)
-    R = df_add(R, df_mul(dsh.coef[p], df_exp(df_neg(df_mul(dsh.alpha[p], r2)), S.D.exp.K, bm.tab)));
-  return R;
+    acc = A::add(acc, A::mul(A::c(dsh.coef[p]),
+                             A::exp(A::neg(A::mul(A::c(dsh.alpha[p]), r2)), S.D.exp.K, bm.tab)));
+  return acc;
 }
 
-__device__ __forceinline__ int solid_df(int l, const df d[3], df Sv[5])
+template <class NT>
+__device__ __forceinline__ int solid_m(int l, const NT d[3], NT Sv[5])
 {
+  typedef Ar<NT> A;
   if (l == 0) {
-    Sv[0] = df_make(1.0f, 0.0f);
+    Sv[0] = A::one();
     return 1;
   }
   if (l == 1) {
     Sv[0] = d[0]; Sv[1] = d[1]; Sv[2] = d[2];
     return 3;
   }
-  df xx = df_sqr(d[0]), yy = df_sqr(d[1]), zz = df_sqr(d[2]);
-  Sv[0] = df_mul(d[0], d[1]);
-  Sv[1] = df_mul(d[1], d[2]);
-  Sv[2] = df_mul(d[2], d[0]);
-  Sv[3] = df_sub(xx, yy);
-  Sv[4] = df_sub(df_add(zz, zz), df_add(xx, yy));
+  NT xx = A::sqr(d[0]), yy = A::sqr(d[1]), zz = A::sqr(d[2]);
+  Sv[0] = A::mul(d[0], d[1]);
+  Sv[1] = A::mul(d[1], d[2]);
+  Sv[2] = A::mul(d[2], d[0]);
+  Sv[3] = A::sub(xx, yy);
+  Sv[4] = A::sub(A::add(zz, zz), A::add(xx, yy));
   return 5;
-}
-
-// Sum_mu v[mu] chi_mu(p) in double-float.
-__device__ df ao_dot_df(const SysDev& S, const df* v, const df p[3], const BlockMem& bm)
-{
-  df acc = dfz();
-  int prev_c = -1;
-  df d[3] = {dfz(), dfz(), dfz()}, r = dfz(), r2 = dfz(), e = dfz();
-  for (int q = 0; q < S.n_shell; ++q) {
-    const ShellDev& sh = S.sh[q];
-    const DfShell& dsh = S.D.sh[q];
-    if (sh.center != prev_c) {
-      prev_c = sh.center;
-      d[0] = df_sub_fast(p[0], S.D.nuc[prev_c][0]);
-      d[1] = df_sub_fast(p[1], S.D.nuc[prev_c][1]);
-      d[2] = df_sub_fast(p[2], S.D.nuc[prev_c][2]);
-      r2 = df_dot3(d[0], d[1], d[2]);
-      r = df_sqrt(r2);
-    }
-    if (sh.kind == 0 && !sh.same_exp) e = df_exp(df_neg(df_mul(dsh.zeta, r)), S.D.exp.K, bm.tab);
-    df R = radial_value_df(S, sh, dsh, r, r2, e, bm);
-    df Sv[5];
-    int nf = solid_df(sh.l, d, Sv);
-    df part = dfz();
-    for (int f = 0; f < nf; ++f) part = df_add(part, df_mul(v[sh.ao_offset + f], Sv[f]));
-    acc = df_add(acc, df_mul(part, R));
-  }
-  return acc;
 }
 
 // Per nucleus I (one distance each): the determinant ratio
 // sum_mu v[mu] chi_mu(p) over the shells centred on I, and the e-n Jastrow
-// sum_I b1_I r/(1 + b2 r) (returned with the sign of J).
-__device__ void nucleus_terms_df(const SysDev& S, const df* v, const df p[3], const BlockMem& bm, df& rdet,
-                                 df& jen)
+// -sum_I b1_I r/(1 + b2 r).
+template <class NT>
+__device__ void nucleus_terms_m(const SysDev& S, const df* v, const NT p[3], const BlockMem& bm, NT& rdet, NT& jen)
 {
-  rdet = dfz();
-  jen = dfz();
+  typedef Ar<NT> A;
+  rdet = A::zero();
+  jen = A::zero();
   for (int I = 0; I < S.n_nuc; ++I) {
-    df d[3] = {df_sub_fast(p[0], S.D.nuc[I][0]), df_sub_fast(p[1], S.D.nuc[I][1]),
-               df_sub_fast(p[2], S.D.nuc[I][2])};
-    df r2 = df_dot3(d[0], d[1], d[2]);
-    df r = df_sqrt(r2);
+    NT d[3] = {A::sub_fast(p[0], A::c(S.D.nuc[I][0])), A::sub_fast(p[1], A::c(S.D.nuc[I][1])),
+               A::sub_fast(p[2], A::c(S.D.nuc[I][2]))};
+    NT r2 = dot3<NT>(d[0], d[1], d[2]);
+    NT r = A::sqrt(r2);
     if (S.en_b1[I] != 0.0)
-      jen = df_sub(jen, df_div(df_mul(S.D.en_b1[I], r), df_add_f(df_mul(S.D.en_b2, r), 1.0f)));
-    df e = dfz();
+      jen = A::sub(jen, A::div(A::mul(A::c(S.D.en_b1[I]), r), A::add_f(A::mul(A::c(S.D.en_b2), r), 1.0f)));
+    NT e = A::zero();
     for (int q = S.nuc_shell_begin[I]; q < S.nuc_shell_begin[I + 1]; ++q) {
       const ShellDev& sh = S.sh[q];
       const DfShell& dsh = S.D.sh[q];
-      if (sh.kind == 0 && !sh.same_exp) e = df_exp(df_neg(df_mul(dsh.zeta, r)), S.D.exp.K, bm.tab);
-      df R = radial_value_df(S, sh, dsh, r, r2, e, bm);
-      df part;
+      if (sh.kind == 0 && !sh.same_exp) e = A::exp(A::neg(A::mul(A::c(dsh.zeta), r)), S.D.exp.K, bm.tab);
+      NT Rv = radial_value_m<NT>(S, sh, dsh, r, r2, e, bm);
+      NT part;
       if (sh.l == 0) {
-        part = v[sh.ao_offset];
+        part = A::c(v[sh.ao_offset]);
       } else {
-        df Sv[5];
-        int nf = solid_df(sh.l, d, Sv);
-        part = dfz();
-        for (int f = 0; f < nf; ++f) part = df_add(part, df_mul(v[sh.ao_offset + f], Sv[f]));
+        NT Sv[5];
+        int nf = solid_m<NT>(sh.l, d, Sv);
+        part = A::zero();
+        for (int f = 0; f < nf; ++f) part = A::add(part, A::mul(A::c(v[sh.ao_offset + f]), Sv[f]));
       }
-      rdet = df_add(rdet, df_mul(part, R));
+      rdet = A::add(rdet, A::mul(part, Rv));
     }
   }
 }
@@ -671,97 +624,108 @@ __device__ void nucleus_terms_df(const SysDev& S, const df* v, const df p[3], co
 // sum_{j != i} u_ee(|p - r_j|): the Pade terms c r/(1 + b r) (all of one
 // sign) are summed as one running fraction num/den, so one division serves
 // all partners.
-__device__ df jastrow_ee_df(const SysDev& S, const df* xd, int i, const df p[3])
+template <class NT>
+__device__ NT jastrow_ee_m(const SysDev& S, const df* xd, int i, const NT p[3])
 {
-  df num = dfz(), den = df_make(1.0f, 0.0f);
+  typedef Ar<NT> A;
+  NT num = A::zero(), den = A::one();
   const int si = spin_of(S, i);
+  const NT b = A::c(S.D.b_ee), cp = A::c(S.D.c_par), ca = A::c(S.D.c_anti);
   for (int j = 0; j < S.N; ++j) {
     if (j == i) continue;
-    df d0 = df_sub_fast(p[0], xd[3 * j]), d1 = df_sub_fast(p[1], xd[3 * j + 1]), d2 = df_sub_fast(p[2], xd[3 * j + 2]);
-    df r = df_sqrt(df_dot3(d0, d1, d2));
-    df c = (spin_of(S, j) == si) ? S.D.c_par : S.D.c_anti;
-    df dj = df_add_f(df_mul(S.D.b_ee, r), 1.0f);
-    num = df_add_fast(df_mul(num, dj), df_mul(df_mul(c, r), den));
-    den = df_mul(den, dj);
+    NT d0 = A::sub_fast(p[0], A::c(xd[3 * j])), d1 = A::sub_fast(p[1], A::c(xd[3 * j + 1])),
+       d2 = A::sub_fast(p[2], A::c(xd[3 * j + 2]));
+    NT r = A::sqrt(dot3<NT>(d0, d1, d2));
+    NT c = (spin_of(S, j) == si) ? cp : ca;
+    NT dj = A::add_f(A::mul(b, r), 1.0f);
+    num = A::add_fast(A::mul(num, dj), A::mul(A::mul(c, r), den));
+    den = A::mul(den, dj);
   }
-  return df_div(num, den);
+  return A::div(num, den);
 }
 
-// sum_{j != i} u_ee(|p - r_j|) + sum_I u_en(|p - R_I|) in double-float.
-// The e-e Pade terms c r/(1 + b r) (all of one sign) are summed as one
-// running fraction num/den, so one division serves all partners.
-__device__ df jastrow_terms_df(const SysDev& S, const df* xd, int i, const df p[3])
+template <class NT>
+__device__ __forceinline__ NT p_weight_m(const SysDev& S, const LatDev& L, const NT m[3], const BlockMem& bm)
 {
-  df num = dfz(), den = df_make(1.0f, 0.0f);
-  const int si = spin_of(S, i);
-  for (int j = 0; j < S.N; ++j) {
-    if (j == i) continue;
-    df d0 = df_sub_fast(p[0], xd[3 * j]), d1 = df_sub_fast(p[1], xd[3 * j + 1]), d2 = df_sub_fast(p[2], xd[3 * j + 2]);
-    df r = df_sqrt(df_dot3(d0, d1, d2));
-    df c = (spin_of(S, j) == si) ? S.D.c_par : S.D.c_anti;
-    df dj = df_add_f(df_mul(S.D.b_ee, r), 1.0f);
-    num = df_add_fast(df_mul(num, dj), df_mul(df_mul(c, r), den));
-    den = df_mul(den, dj);
-  }
-  df acc = df_div(num, den);
-  for (int I = 0; I < S.n_nuc; ++I) {
-    df d0 = df_sub_fast(p[0], S.D.nuc[I][0]), d1 = df_sub_fast(p[1], S.D.nuc[I][1]), d2 = df_sub_fast(p[2], S.D.nuc[I][2]);
-    df r = df_sqrt(df_dot3(d0, d1, d2));
-    df den = df_add_f(df_mul(S.D.en_b2, r), 1.0f);
-    acc = df_sub(acc, df_div(df_mul(S.D.en_b1[I], r), den));
-  }
-  return acc;
-}
-
-__device__ __forceinline__ df p_weight_df(const SysDev& S, const LatDev& L, const df m[3], const BlockMem& bm)
-{
-  df best = df_make(INFINITY, 0.0f);
+  typedef Ar<NT> A;
+  NT best = A::inf();
   for (int I = 0; I < S.n_nuc; ++I) {
     if (!S.heavy[I]) continue;
-    df d0 = df_sub_fast(m[0], S.D.nuc[I][0]), d1 = df_sub_fast(m[1], S.D.nuc[I][1]), d2 = df_sub_fast(m[2], S.D.nuc[I][2]);
-    df d2s = df_dot3(d0, d1, d2);
-    if (d2s.hi < best.hi || (d2s.hi == best.hi && d2s.lo < best.lo)) best = d2s;
+    NT d0 = A::sub_fast(m[0], A::c(S.D.nuc[I][0])), d1 = A::sub_fast(m[1], A::c(S.D.nuc[I][1])),
+       d2 = A::sub_fast(m[2], A::c(S.D.nuc[I][2]));
+    NT d2s = dot3<NT>(d0, d1, d2);
+    if (A::lt(d2s, best)) best = d2s;
   }
-  if (L.pkind == 0) return df_exp(df_neg(df_mul(best, L.p_coef_df)), S.D.exp.K, bm.tab);
-  return df_rcp(df_add_f(df_mul(L.p_coef_df, best), 1.0f));
+  if (L.pkind == 0) return A::exp(A::neg(A::mul(best, A::c(L.p_coef_df))), S.D.exp.K, bm.tab);
+  return A::rcp(A::add_f(A::mul(A::c(L.p_coef_df), best), 1.0f));
 }
 
-__device__ __forceinline__ df shfl_df(df v, int src)
+template <class NT>
+__device__ __forceinline__ NT warp_sum_m(NT v)
 {
-  return df_make(__shfl_sync(FULL_MASK, v.hi, src), __shfl_sync(FULL_MASK, v.lo, src));
-}
-
-__device__ __forceinline__ df warp_sum_df(df v)
-{
+  typedef Ar<NT> A;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
-    v = df_add(v, df_make(__shfl_xor_sync(FULL_MASK, v.hi, o), __shfl_xor_sync(FULL_MASK, v.lo, o)));
+  for (int o = 16; o > 0; o >>= 1) v = A::add(v, A::shfl_xor(v, o));
   return v;
+}
+
+// Chunked inclusive scan of the rates (as warp_scan) in NT.
+template <class NT>
+__device__ NT warp_scan_m(const df* T, int P, int lane, NT target, int* pick, int* last)
+{
+  typedef Ar<NT> A;
+  NT carry = A::zero();
+  int p = -1, lp = -1;
+  for (int base = 0; base < P; base += 32) {
+    int c = base + lane;
+    NT t = (c < P) ? A::c(T[c]) : A::zero();
+    NT v = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      NT y = A::shfl_up(v, o);
+      if (lane >= o) v = A::add(v, y);
+    }
+    NT C = A::add(carry, v);
+    if (pick) {
+      unsigned hit = __ballot_sync(FULL_MASK, (c < P) && A::lt(target, C));
+      if (p < 0 && hit) p = base + __ffs(hit) - 1;
+      unsigned pos = __ballot_sync(FULL_MASK, (c < P) && A::positive(t));
+      if (pos) lp = base + 31 - __clz(pos);
+    }
+    carry = A::shfl(C, 31);
+  }
+  if (pick) { *pick = p; *last = lp; }
+  return carry;
 }
 
 // Partial sums of the local energy of electron i over the shells q, the
 // electrons j and the nuclei I congruent to part modulo L.
+template <class NT>
 struct ElParts {
-  df gD[3], lD, gJ[3], lJ, S, V;
+  NT gD[3], lD, gJ[3], lJ, S, V;
 };
 
-__device__ __forceinline__ void el_zero(ElParts& o)
+template <class NT>
+__device__ __forceinline__ void el_zero(ElParts<NT>& o)
 {
-  o.lD = dfz(); o.lJ = dfz(); o.S = dfz(); o.V = dfz();
-  for (int k = 0; k < 3; ++k) { o.gD[k] = dfz(); o.gJ[k] = dfz(); }
+  typedef Ar<NT> A;
+  o.lD = A::zero(); o.lJ = A::zero(); o.S = A::zero(); o.V = A::zero();
+  for (int k = 0; k < 3; ++k) { o.gD[k] = A::zero(); o.gJ[k] = A::zero(); }
 }
 
-__device__ void el_parts_df(const SysDev& S, const WarpMem& wm, int i, int part, int L, const BlockMem& bm,
-                            ElParts& o)
+template <class NT>
+__device__ void el_parts_m(const SysDev& S, const WarpMem& wm, int i, int part, int L, const BlockMem& bm,
+                           ElParts<NT>& o)
 {
+  typedef Ar<NT> A;
   const int nao = S.n_ao;
   const df* v = &wm.vd[i * nao];
-  const df* ri = &wm.xd[3 * i];
-  el_zero(o);
+  const NT ri[3] = {A::c(wm.xd[3 * i]), A::c(wm.xd[3 * i + 1]), A::c(wm.xd[3 * i + 2])};
+  el_zero<NT>(o);
   // basis: gradient and Laplacian contracted with v. Shells sharing one
   // Slater exponential form a group; groups are dealt to the parts.
   int prev_c = -1, grp = -1;
-  df d[3] = {dfz(), dfz(), dfz()}, r = dfz(), r2 = dfz(), ir = dfz(), e = dfz();
+  NT d[3] = {A::zero(), A::zero(), A::zero()}, r = A::zero(), r2 = A::zero(), ir = A::zero(), e = A::zero();
   for (int q = 0; q < S.n_shell; ++q) {
     const ShellDev& sh = S.sh[q];
     const DfShell& dsh = S.D.sh[q];
@@ -769,189 +733,200 @@ __device__ void el_parts_df(const SysDev& S, const WarpMem& wm, int i, int part,
     if ((grp % L) != part) continue;
     if (sh.center != prev_c) {
       prev_c = sh.center;
-      d[0] = df_sub_fast(ri[0], S.D.nuc[prev_c][0]);
-      d[1] = df_sub_fast(ri[1], S.D.nuc[prev_c][1]);
-      d[2] = df_sub_fast(ri[2], S.D.nuc[prev_c][2]);
-      r2 = df_dot3(d[0], d[1], d[2]);
-      r = df_sqrt(r2);
-      ir = df_rcp(r);
+      d[0] = A::sub_fast(ri[0], A::c(S.D.nuc[prev_c][0]));
+      d[1] = A::sub_fast(ri[1], A::c(S.D.nuc[prev_c][1]));
+      d[2] = A::sub_fast(ri[2], A::c(S.D.nuc[prev_c][2]));
+      r2 = dot3<NT>(d[0], d[1], d[2]);
+      r = A::sqrt(r2);
+      ir = A::rcp(r);
     }
-    if (sh.kind == 0 && !sh.same_exp) e = df_exp(df_neg(df_mul(dsh.zeta, r)), S.D.exp.K, bm.tab);
-    df R, R1, R2;
+    if (sh.kind == 0 && !sh.same_exp) e = A::exp(A::neg(A::mul(A::c(dsh.zeta), r)), S.D.exp.K, bm.tab);
+    NT Rv, R1, R2;
     if (sh.kind == 0) {
-      R = radial_value_df(S, sh, dsh, r, r2, e, bm);
-      df t = df_sub(df_mul(dsh.m, ir), dsh.zeta);
-      R1 = df_mul(df_mul(t, R), ir);
-      R2 = df_mul(df_sub(df_sqr(t), df_mul(dsh.m, df_sqr(ir))), R);
+      Rv = radial_value_m<NT>(S, sh, dsh, r, r2, e, bm);
+      NT t = A::sub(A::mul(A::c(dsh.m), ir), A::c(dsh.zeta));
+      R1 = A::mul(A::mul(t, Rv), ir);
+      R2 = A::mul(A::sub(A::sqr(t), A::mul(A::c(dsh.m), A::sqr(ir))), Rv);
     } else {
-      R = dfz(); R1 = dfz(); R2 = dfz();
+      Rv = A::zero(); R1 = A::zero(); R2 = A::zero();
       for (int p = 0; p < sh.n_prim; ++p) {
-        df al = dsh.alpha[p];
-        df g = df_mul(dsh.coef[p], df_exp(df_neg(df_mul(al, r2)), S.D.exp.K, bm.tab));
-        R = df_add(R, g);
-        df m2a = df_mul_f(al, -2.0f);
-        R1 = df_add(R1, df_mul(m2a, g));
-        df four_a2r2 = df_mul_f(df_mul(df_sqr(al), r2), 4.0f);
-        R2 = df_add(R2, df_mul(df_add(four_a2r2, m2a), g));
+        NT al = A::c(dsh.alpha[p]);
+        NT g = A::mul(A::c(dsh.coef[p]), A::exp(A::neg(A::mul(al, r2)), S.D.exp.K, bm.tab));
+        Rv = A::add(Rv, g);
+        NT m2a = A::mul_f(al, -2.0f);
+        R1 = A::add(R1, A::mul(m2a, g));
+        NT four_a2r2 = A::mul_f(A::mul(A::sqr(al), r2), 4.0f);
+        R2 = A::add(R2, A::mul(A::add(four_a2r2, m2a), g));
       }
     }
-    df Sv[5];
-    int nf = solid_df(sh.l, d, Sv);
-    df radlap = df_add(R2, df_mul_f(R1, 2.0f * (sh.l + 1)));
+    NT Sv[5];
+    int nf = solid_m<NT>(sh.l, d, Sv);
+    NT radlap = A::add(R2, A::mul_f(R1, 2.0f * (sh.l + 1)));
     for (int f = 0; f < nf; ++f) {
-      df c = v[sh.ao_offset + f];
-      df cS = df_mul(c, Sv[f]);
+      NT cc = A::c(v[sh.ao_offset + f]);
+      NT cS = A::mul(cc, Sv[f]);
       // grad S of the solid harmonics
-      df gS[3];
-      if (sh.l == 0) { gS[0] = dfz(); gS[1] = dfz(); gS[2] = dfz(); }
-      else if (sh.l == 1) { gS[0] = dfz(); gS[1] = dfz(); gS[2] = dfz(); gS[f] = df_make(1.0f, 0.0f); }
+      NT gS[3];
+      if (sh.l == 0) { gS[0] = A::zero(); gS[1] = A::zero(); gS[2] = A::zero(); }
+      else if (sh.l == 1) { gS[0] = A::zero(); gS[1] = A::zero(); gS[2] = A::zero(); gS[f] = A::one(); }
       else {
         switch (f) {
-          case 0: gS[0] = d[1]; gS[1] = d[0]; gS[2] = dfz(); break;
-          case 1: gS[0] = dfz(); gS[1] = d[2]; gS[2] = d[1]; break;
-          case 2: gS[0] = d[2]; gS[1] = dfz(); gS[2] = d[0]; break;
-          case 3: gS[0] = df_mul_f(d[0], 2.0f); gS[1] = df_mul_f(d[1], -2.0f); gS[2] = dfz(); break;
-          default: gS[0] = df_mul_f(d[0], -2.0f); gS[1] = df_mul_f(d[1], -2.0f); gS[2] = df_mul_f(d[2], 4.0f); break;
+          case 0: gS[0] = d[1]; gS[1] = d[0]; gS[2] = A::zero(); break;
+          case 1: gS[0] = A::zero(); gS[1] = d[2]; gS[2] = d[1]; break;
+          case 2: gS[0] = d[2]; gS[1] = A::zero(); gS[2] = d[0]; break;
+          case 3: gS[0] = A::mul_f(d[0], 2.0f); gS[1] = A::mul_f(d[1], -2.0f); gS[2] = A::zero(); break;
+          default: gS[0] = A::mul_f(d[0], -2.0f); gS[1] = A::mul_f(d[1], -2.0f); gS[2] = A::mul_f(d[2], 4.0f); break;
         }
       }
-      df cSR1 = df_mul(cS, R1);
-      for (int k = 0; k < 3; ++k)
-        o.gD[k] = df_add(o.gD[k], df_add(df_mul(df_mul(c, R), gS[k]), df_mul(cSR1, d[k])));
-      o.lD = df_add(o.lD, df_mul(cS, radlap));
+      NT cSR1 = A::mul(cS, R1);
+      NT cR = A::mul(cc, Rv);
+      for (int k = 0; k < 3; ++k) o.gD[k] = A::add(o.gD[k], A::add(A::mul(cR, gS[k]), A::mul(cSR1, d[k])));
+      o.lD = A::add(o.lD, A::mul(cS, radlap));
     }
   }
   // e-e pairs
   const int si = spin_of(S, i);
+  const NT b = A::c(S.D.b_ee);
   for (int j = part; j < S.N; j += L) {
     if (j == i) continue;
-    df d0 = df_sub_fast(ri[0], wm.xd[3 * j]), d1 = df_sub_fast(ri[1], wm.xd[3 * j + 1]), d2 = df_sub_fast(ri[2], wm.xd[3 * j + 2]);
-    df rr = df_sqrt(df_dot3(d0, d1, d2));
-    df c = (spin_of(S, j) == si) ? S.D.c_par : S.D.c_anti;
-    df inv = df_rcp(df_add_f(df_mul(S.D.b_ee, rr), 1.0f));
-    df inv2 = df_sqr(inv);
-    df u1 = df_mul(c, inv2);
-    df u2 = df_mul_f(df_mul(df_mul(S.D.b_ee, c), df_mul(inv2, inv)), -2.0f);
-    df irr = df_rcp(rr);
-    df u1ir = df_mul(u1, irr);
-    o.gJ[0] = df_add(o.gJ[0], df_mul(u1ir, d0));
-    o.gJ[1] = df_add(o.gJ[1], df_mul(u1ir, d1));
-    o.gJ[2] = df_add(o.gJ[2], df_mul(u1ir, d2));
-    o.lJ = df_add(o.lJ, df_add(u2, df_mul_f(u1ir, 2.0f)));
-    o.S = df_add(o.S, df_mul(df_mul(c, rr), inv));
-    if (j > i && S.ee_on) o.V = df_add(o.V, irr);
+    NT d0 = A::sub_fast(ri[0], A::c(wm.xd[3 * j])), d1 = A::sub_fast(ri[1], A::c(wm.xd[3 * j + 1])),
+       d2 = A::sub_fast(ri[2], A::c(wm.xd[3 * j + 2]));
+    NT rr = A::sqrt(dot3<NT>(d0, d1, d2));
+    NT c = (spin_of(S, j) == si) ? A::c(S.D.c_par) : A::c(S.D.c_anti);
+    NT inv = A::rcp(A::add_f(A::mul(b, rr), 1.0f));
+    NT inv2 = A::sqr(inv);
+    NT u1 = A::mul(c, inv2);
+    NT u2 = A::mul_f(A::mul(A::mul(b, c), A::mul(inv2, inv)), -2.0f);
+    NT irr = A::rcp(rr);
+    NT u1ir = A::mul(u1, irr);
+    o.gJ[0] = A::add(o.gJ[0], A::mul(u1ir, d0));
+    o.gJ[1] = A::add(o.gJ[1], A::mul(u1ir, d1));
+    o.gJ[2] = A::add(o.gJ[2], A::mul(u1ir, d2));
+    o.lJ = A::add(o.lJ, A::add(u2, A::mul_f(u1ir, 2.0f)));
+    o.S = A::add(o.S, A::mul(A::mul(c, rr), inv));
+    if (j > i && S.ee_on) o.V = A::add(o.V, irr);
   }
   // e-n terms
   for (int I = part; I < S.n_nuc; I += L) {
-    df d0 = df_sub_fast(ri[0], S.D.nuc[I][0]), d1 = df_sub_fast(ri[1], S.D.nuc[I][1]), d2 = df_sub_fast(ri[2], S.D.nuc[I][2]);
-    df rr = df_sqrt(df_dot3(d0, d1, d2));
-    df b1 = S.D.en_b1[I];
-    df inv = df_rcp(df_add_f(df_mul(S.D.en_b2, rr), 1.0f));
-    df inv2 = df_sqr(inv);
-    df u1 = df_neg(df_mul(b1, inv2));
-    df u2 = df_mul_f(df_mul(df_mul(S.D.en_b2, b1), df_mul(inv2, inv)), 2.0f);
-    df irr = df_rcp(rr);
-    df u1ir = df_mul(u1, irr);
-    o.gJ[0] = df_add(o.gJ[0], df_mul(u1ir, d0));
-    o.gJ[1] = df_add(o.gJ[1], df_mul(u1ir, d1));
-    o.gJ[2] = df_add(o.gJ[2], df_mul(u1ir, d2));
-    o.lJ = df_add(o.lJ, df_add(u2, df_mul_f(u1ir, 2.0f)));
-    o.S = df_sub(o.S, df_mul(df_mul(b1, rr), inv));
-    o.V = df_sub(o.V, df_mul(S.D.Z[I], irr));
+    NT d0 = A::sub_fast(ri[0], A::c(S.D.nuc[I][0])), d1 = A::sub_fast(ri[1], A::c(S.D.nuc[I][1])),
+       d2 = A::sub_fast(ri[2], A::c(S.D.nuc[I][2]));
+    NT rr = A::sqrt(dot3<NT>(d0, d1, d2));
+    NT b1 = A::c(S.D.en_b1[I]), b2 = A::c(S.D.en_b2);
+    NT inv = A::rcp(A::add_f(A::mul(b2, rr), 1.0f));
+    NT inv2 = A::sqr(inv);
+    NT u1 = A::neg(A::mul(b1, inv2));
+    NT u2 = A::mul_f(A::mul(A::mul(b2, b1), A::mul(inv2, inv)), 2.0f);
+    NT irr = A::rcp(rr);
+    NT u1ir = A::mul(u1, irr);
+    o.gJ[0] = A::add(o.gJ[0], A::mul(u1ir, d0));
+    o.gJ[1] = A::add(o.gJ[1], A::mul(u1ir, d1));
+    o.gJ[2] = A::add(o.gJ[2], A::mul(u1ir, d2));
+    o.lJ = A::add(o.lJ, A::add(u2, A::mul_f(u1ir, 2.0f)));
+    o.S = A::sub(o.S, A::mul(A::mul(b1, rr), inv));
+    o.V = A::sub(o.V, A::mul(A::c(S.D.Z[I]), irr));
   }
 }
 
-__device__ __forceinline__ void el_combine(ElParts& o, int src, bool take)
+template <class NT>
+__device__ __forceinline__ void el_combine(ElParts<NT>& o, int src, bool take)
 {
-  df t;
-#define ELC(field)                         \
-  t = shfl_df(o.field, src);               \
-  if (take) o.field = df_add(o.field, t);
+  typedef Ar<NT> A;
+  NT t;
+#define ELC(field)            \
+  t = A::shfl(o.field, src);  \
+  if (take) o.field = A::add(o.field, t);
   ELC(lD) ELC(lJ) ELC(S) ELC(V)
   ELC(gD[0]) ELC(gD[1]) ELC(gD[2]) ELC(gJ[0]) ELC(gJ[1]) ELC(gJ[2])
 #undef ELC
 }
 
-__device__ __forceinline__ df el_local(const ElParts& o)
+template <class NT>
+__device__ __forceinline__ NT el_local(const ElParts<NT>& o)
 {
-  df dot = df_add(df_add(df_mul(o.gD[0], o.gJ[0]), df_mul(o.gD[1], o.gJ[1])), df_mul(o.gD[2], o.gJ[2]));
-  df gg = df_add(df_add(df_sqr(o.gJ[0]), df_sqr(o.gJ[1])), df_sqr(o.gJ[2]));
-  df lap = df_add(df_add(o.lD, df_mul_f(dot, 2.0f)), df_add(o.lJ, gg));
-  return df_add(df_mul_f(lap, -0.5f), o.V);
+  typedef Ar<NT> A;
+  NT dot = A::add(A::add(A::mul(o.gD[0], o.gJ[0]), A::mul(o.gD[1], o.gJ[1])), A::mul(o.gD[2], o.gJ[2]));
+  NT gg = A::add(A::add(A::sqr(o.gJ[0]), A::sqr(o.gJ[1])), A::sqr(o.gJ[2]));
+  NT lap = A::add(A::add(o.lD, A::mul_f(dot, 2.0f)), A::add(o.lJ, gg));
+  return A::add(A::mul_f(lap, -0.5f), o.V);
 }
 
-__device__ void warp_eval_df(const SysDev& S, const double* sC, const LatDev& L, const WarpMem& wm,
-                             int lane, double* ratio_out, double& b, df& bdf, double& el)
+template <class NT>
+__device__ void warp_eval_m(const SysDev& S, const double* sC, const LatDev& L, const WarpMem& wm, int lane,
+                            double* ratio_out, double& b, df& bdf, double& el)
 {
+  typedef Ar<NT> A;
   const int N = S.N, nao = S.n_ao, nu = S.n_up;
   const BlockMem bm = block_mem(S, const_cast<double*>(sC));
   // projected inverse columns in FP64, then converted with the positions
   for (int idx = lane; idx < N * nao; idx += 32) {
     int i = idx / nao, mu = idx % nao;
     int spin = i < nu ? 0 : 1, l = i < nu ? i : i - nu, n = spin ? S.n_dn : nu;
-    const double* A = spin ? wm.A + nu * nu : wm.A;
+    const double* Am = spin ? wm.A + nu * nu : wm.A;
     double acc = 0.0;
-    for (int m = 0; m < n; ++m) acc += sC[mu * S.n_mo + m] * A[m * n + l];
-    wm.vd[idx] = df_from_double(acc);
+    for (int m = 0; m < n; ++m) acc += sC[mu * S.n_mo + m] * Am[m * n + l];
+    wm.vd[idx] = A::store(A::from_double(acc));
   }
-  for (int j = lane; j < 3 * N; j += 32) wm.xd[j] = df_from_double(wm.x[j]);
-  if (lane < 9) wm.Rd[lane] = df_from_double(wm.R[lane]);
+  for (int j = lane; j < 3 * N; j += 32) wm.xd[j] = A::store(A::from_double(wm.x[j]));
+  if (lane < 9) wm.Rd[lane] = A::store(A::from_double(wm.R[lane]));
   __syncwarp();
   // local energy: Lp lanes per electron share its shells, electrons and nuclei
-  df epart = dfz();
+  NT epart = A::zero();
   if (N <= 32) {
     const int Lp = 32 / N;
     const int i = lane % N, part = lane / N;
     const bool act = lane < N * Lp;
-    ElParts o;
-    if (act) el_parts_df(S, wm, i, part, Lp, bm, o);
-    else el_zero(o);
+    ElParts<NT> o;
+    if (act) el_parts_m<NT>(S, wm, i, part, Lp, bm, o);
+    else el_zero<NT>(o);
     for (int pp = 1; pp < Lp; ++pp) {
       int src = lane + pp * N;
-      el_combine(o, src < 32 ? src : lane, part == 0 && src < N * Lp);
+      el_combine<NT>(o, src < 32 ? src : lane, part == 0 && src < N * Lp);
     }
     if (part == 0 && act) {
-      wm.Sd[i] = o.S;
-      epart = el_local(o);
+      wm.Sd[i] = A::store(o.S);
+      epart = el_local<NT>(o);
     }
   } else {
     for (int i = lane; i < N; i += 32) {
-      ElParts o;
-      el_parts_df(S, wm, i, 0, 1, bm, o);
-      wm.Sd[i] = o.S;
-      epart = df_add(epart, el_local(o));
+      ElParts<NT> o;
+      el_parts_m<NT>(S, wm, i, 0, 1, bm, o);
+      wm.Sd[i] = A::store(o.S);
+      epart = A::add(epart, el_local<NT>(o));
     }
   }
-  df etot = warp_sum_df(epart);
-  el = df_to_double(etot) + S.V_nn;
+  NT etot = warp_sum_m<NT>(epart);
+  el = A::to_double(etot) + S.V_nn;
   __syncwarp();
   // the P lattice moves
   const int G = L.G, per_e = 6 * G, P = N * per_e;
+  df* Td = reinterpret_cast<df*>(wm.T);  // rates stay in NT, stored as double-floats
   for (int c = lane; c < P; c += 32) {
     int i = c / per_e, rem = c - i * per_e, g = rem / 6, k = (rem % 6) >> 1;
-    df h = g ? L.ap_df : L.a_df;
-    if (c & 1) h = df_neg(h);
-    const df e0 = wm.Rd[k], e1 = wm.Rd[3 + k], e2 = wm.Rd[6 + k];
-    const df* ri = &wm.xd[3 * i];
-    df p[3] = {df_add(ri[0], df_mul(h, e0)), df_add(ri[1], df_mul(h, e1)), df_add(ri[2], df_mul(h, e2))};
-    df rdet, jen;
-    nucleus_terms_df(S, &wm.vd[i * nao], p, bm, rdet, jen);
-    df dJ = df_sub(df_add(jastrow_ee_df(S, wm.xd, i, p), jen), wm.Sd[i]);
-    df rho = df_mul(rdet, df_exp(dJ, S.D.exp.K, bm.tab));
-    df w = df_make(1.0f, 0.0f);
+    NT h = g ? A::c(L.ap_df) : A::c(L.a_df);
+    if (c & 1) h = A::neg(h);
+    const NT e0 = A::c(wm.Rd[k]), e1 = A::c(wm.Rd[3 + k]), e2 = A::c(wm.Rd[6 + k]);
+    const NT ri[3] = {A::c(wm.xd[3 * i]), A::c(wm.xd[3 * i + 1]), A::c(wm.xd[3 * i + 2])};
+    NT p[3] = {A::add(ri[0], A::mul(h, e0)), A::add(ri[1], A::mul(h, e1)), A::add(ri[2], A::mul(h, e2))};
+    NT rdet, jen;
+    nucleus_terms_m<NT>(S, &wm.vd[i * nao], p, bm, rdet, jen);
+    NT dJ = A::sub(A::add(jastrow_ee_m<NT>(S, wm.xd, i, p), jen), A::c(wm.Sd[i]));
+    NT rho = A::mul(rdet, A::exp(dJ, S.D.exp.K, bm.tab));
+    NT w = A::one();
     if (G == 2) {
-      df hh = df_make(0.5f * h.hi, 0.5f * h.lo);
-      df mid[3] = {df_add(ri[0], df_mul(hh, e0)), df_add(ri[1], df_mul(hh, e1)), df_add(ri[2], df_mul(hh, e2))};
-      df pm = p_weight_df(S, L, mid, bm);
-      w = g ? df_add_f(df_neg(pm), 1.0f) : pm;
+      NT hh = A::half(h);
+      NT mid[3] = {A::add(ri[0], A::mul(hh, e0)), A::add(ri[1], A::mul(hh, e1)), A::add(ri[2], A::mul(hh, e2))};
+      NT pm = p_weight_m<NT>(S, L, mid, bm);
+      w = g ? A::add_f(A::neg(pm), 1.0f) : pm;
     }
-    df T = dfz();
-    if (rho.hi > 0.0f) T = df_mul(df_mul(w, g ? L.inv2ap2_df : L.inv2a2_df), rho);
-    reinterpret_cast<df*>(wm.T)[c] = T;  // rates stay double-float in this mode
-    if (ratio_out) ratio_out[c] = df_to_double(rho);
+    NT T = A::zero();
+    if (A::positive(rho)) T = A::mul(A::mul(w, g ? A::c(L.inv2ap2_df) : A::c(L.inv2a2_df)), rho);
+    Td[c] = A::store(T);
+    if (ratio_out) ratio_out[c] = A::to_double(rho);
   }
   __syncwarp();
-  bdf = warp_scan_df(reinterpret_cast<const df*>(wm.T), P, lane, dfz(), nullptr, nullptr);
-  b = df_to_double(bdf);
+  NT btot = warp_scan_m<NT>(Td, P, lane, A::zero(), nullptr, nullptr);
+  bdf = A::store(btot);
+  b = A::to_double(btot);
 }
 
 template <int PREC>
@@ -960,7 +935,9 @@ __device__ __forceinline__ void warp_eval_any(const SysDev& S, const double* sC,
                                               df& bdf, double& el)
 {
   if (PREC == LRDMC_PRECISION_DF64) {
-    warp_eval_df(S, sC, L, wm, lane, ratio_out, b, bdf, el);
+    warp_eval_m<df>(S, sC, L, wm, lane, ratio_out, b, bdf, el);
+  } else if (PREC == LRDMC_PRECISION_FP32) {
+    warp_eval_m<float>(S, sC, L, wm, lane, ratio_out, b, bdf, el);
   } else {
     warp_eval(S, sC, L, wm, lane, ratio_out, b, el);
     bdf = df_make(0.0f, 0.0f);
@@ -976,9 +953,10 @@ __device__ __forceinline__ void warp_eval_any(const SysDev& S, const double* sC,
 // share an exponential, written back as doubles.
 __device__ void ao_values_df_lanes(const SysDev& S, const double* p, double* out, int lane, const BlockMem& bm)
 {
+  typedef Ar<df> A;
   df pd[3] = {df_from_double(p[0]), df_from_double(p[1]), df_from_double(p[2])};
   int prev_c = -1, grp = -1;
-  df d[3] = {dfz(), dfz(), dfz()}, r = dfz(), r2 = dfz(), e = dfz();
+  df d[3] = {A::zero(), A::zero(), A::zero()}, r = A::zero(), r2 = A::zero(), e = A::zero();
   for (int q = 0; q < S.n_shell; ++q) {
     const ShellDev& sh = S.sh[q];
     const DfShell& dsh = S.D.sh[q];
@@ -989,14 +967,14 @@ __device__ void ao_values_df_lanes(const SysDev& S, const double* p, double* out
       d[0] = df_sub_fast(pd[0], S.D.nuc[prev_c][0]);
       d[1] = df_sub_fast(pd[1], S.D.nuc[prev_c][1]);
       d[2] = df_sub_fast(pd[2], S.D.nuc[prev_c][2]);
-      r2 = df_dot3(d[0], d[1], d[2]);
+      r2 = dot3<df>(d[0], d[1], d[2]);
       r = df_sqrt(r2);
     }
     if (sh.kind == 0 && !sh.same_exp) e = df_exp(df_neg(df_mul(dsh.zeta, r)), S.D.exp.K, bm.tab);
-    df R = radial_value_df(S, sh, dsh, r, r2, e, bm);
+    df Rv = radial_value_m<df>(S, sh, dsh, r, r2, e, bm);
     df Sv[5];
-    int nf = solid_df(sh.l, d, Sv);
-    for (int f = 0; f < nf; ++f) out[sh.ao_offset + f] = df_to_double(df_mul(Sv[f], R));
+    int nf = solid_m<df>(sh.l, d, Sv);
+    for (int f = 0; f < nf; ++f) out[sh.ao_offset + f] = df_to_double(df_mul(Sv[f], Rv));
   }
 }
 
@@ -1011,7 +989,7 @@ __device__ bool warp_sm_update(const SysDev& S, const double* sC, const WarpMem&
   double* phi = chi + S.n_ao;      // [n]
   double* y = phi + n;             // [n]
   double* col = y + n;             // [n]
-  if (PREC == LRDMC_PRECISION_DF64) ao_values_df_lanes(S, p, chi, lane, block_mem(S, const_cast<double*>(sC)));
+  if (PREC != LRDMC_PRECISION_FP64) ao_values_df_lanes(S, p, chi, lane, block_mem(S, const_cast<double*>(sC)));
   else if (lane == 0) ao_values(S, p, chi);
   __syncwarp();
   for (int m = lane; m < n; m += 32) {
@@ -1169,6 +1147,8 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
       if (PREC == LRDMC_PRECISION_DF64)
         t = b > 0.0 ? df_to_double(df_div(df_neg(df_log(df_from_double(u[0]), S.D.exp.K, bm.tab)), bdf))
                     : INFINITY;
+      else if (PREC == LRDMC_PRECISION_FP32)
+        t = b > 0.0 ? (double)(-logf((float)u[0]) / bdf.hi) : INFINITY;
       else
         t = b > 0.0 ? -log(u[0]) / b : INFINITY;
       if (t >= tau_left) {
@@ -1180,8 +1160,10 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
       // heat bath over the cached rates
       int pick, last;
       if (PREC == LRDMC_PRECISION_DF64)
-        warp_scan_df(reinterpret_cast<const df*>(wm.T), P_moves, lane, df_mul(df_from_double(u[1]), bdf), &pick,
-                     &last);
+        warp_scan_m<df>(reinterpret_cast<const df*>(wm.T), P_moves, lane, df_mul(df_from_double(u[1]), bdf), &pick,
+                        &last);
+      else if (PREC == LRDMC_PRECISION_FP32)
+        warp_scan_m<float>(reinterpret_cast<const df*>(wm.T), P_moves, lane, (float)u[1] * bdf.hi, &pick, &last);
       else
         warp_scan(wm.T, P_moves, lane, u[1] * b, &pick, &last);
       if (pick < 0) pick = last;
@@ -1375,7 +1357,7 @@ k_evaluate(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, in
   warp_eval_any<PREC>(S, sC, L, wm, lane, ratio ? ratio + (size_t)c * P : nullptr, b, bdf, el);
   if (T)
     for (int j = lane; j < P; j += 32)
-      T[(size_t)c * P + j] = (PREC == LRDMC_PRECISION_DF64) ? df_to_double(reinterpret_cast<const df*>(wm.T)[j])
+      T[(size_t)c * P + j] = (PREC != LRDMC_PRECISION_FP64) ? df_to_double(reinterpret_cast<const df*>(wm.T)[j])
                                                             : wm.T[j];
   if (lane == 0) {
     if (b_out) b_out[c] = b;
@@ -1496,6 +1478,7 @@ cudaError_t launch_eval_all(const SysDev& S, const Layout& Lo, const LatDev& L, 
                             cudaStream_t st)
 {
   if (S.precision == LRDMC_PRECISION_DF64) return launch_eval_all_t<LRDMC_PRECISION_DF64>(S, Lo, L, P, st);
+  if (S.precision == LRDMC_PRECISION_FP32) return launch_eval_all_t<LRDMC_PRECISION_FP32>(S, Lo, L, P, st);
   return launch_eval_all_t<LRDMC_PRECISION_FP64>(S, Lo, L, P, st);
 }
 
@@ -1532,6 +1515,8 @@ cudaError_t launch_interval(const SysDev& S, const Layout& Lo, const LatDev& L, 
 {
   if (S.precision == LRDMC_PRECISION_DF64)
     return launch_interval_t<LRDMC_PRECISION_DF64>(S, Lo, L, P, k, recompute, st);
+  if (S.precision == LRDMC_PRECISION_FP32)
+    return launch_interval_t<LRDMC_PRECISION_FP32>(S, Lo, L, P, k, recompute, st);
   return launch_interval_t<LRDMC_PRECISION_FP64>(S, Lo, L, P, k, recompute, st);
 }
 
@@ -1545,17 +1530,24 @@ cudaError_t launch_evaluate(const SysDev& S, const Layout& Lo, const LatDev& L, 
                             const double* x, const double* rot, double* ratio, double* T,
                             double* b, double* el, int* err, cudaStream_t st)
 {
-  const bool df = S.precision == LRDMC_PRECISION_DF64;
-  const void* fn = df ? (const void*)k_evaluate<LRDMC_PRECISION_DF64> : (const void*)k_evaluate<LRDMC_PRECISION_FP64>;
-  cudaError_t e = set_smem(fn, Lo.smem_block_bytes);
-  if (e != cudaSuccess) return e;
   int blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  if (df)
+  cudaError_t e;
+  if (S.precision == LRDMC_PRECISION_DF64) {
+    e = set_smem((const void*)k_evaluate<LRDMC_PRECISION_DF64>, Lo.smem_block_bytes);
+    if (e != cudaSuccess) return e;
     k_evaluate<LRDMC_PRECISION_DF64><<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(
         S, Lo, L, n, x, rot, ratio, T, b, el, err);
-  else
+  } else if (S.precision == LRDMC_PRECISION_FP32) {
+    e = set_smem((const void*)k_evaluate<LRDMC_PRECISION_FP32>, Lo.smem_block_bytes);
+    if (e != cudaSuccess) return e;
+    k_evaluate<LRDMC_PRECISION_FP32><<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(
+        S, Lo, L, n, x, rot, ratio, T, b, el, err);
+  } else {
+    e = set_smem((const void*)k_evaluate<LRDMC_PRECISION_FP64>, Lo.smem_block_bytes);
+    if (e != cudaSuccess) return e;
     k_evaluate<LRDMC_PRECISION_FP64><<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(
         S, Lo, L, n, x, rot, ratio, T, b, el, err);
+  }
   return cudaGetLastError();
 }
 
@@ -1607,7 +1599,7 @@ k_evaluate_static(const __grid_constant__ SysDev S, const Layout Lo, const LatDe
   warp_eval_any<PREC>(S, sC, L, wm, lane, ratio ? ratio + (size_t)c * P : nullptr, b, bdf, el);
   if (T)
     for (int j = lane; j < P; j += 32)
-      T[(size_t)c * P + j] = (PREC == LRDMC_PRECISION_DF64) ? df_to_double(reinterpret_cast<const df*>(wm.T)[j])
+      T[(size_t)c * P + j] = (PREC != LRDMC_PRECISION_FP64) ? df_to_double(reinterpret_cast<const df*>(wm.T)[j])
                                                             : wm.T[j];
   if (lane == 0) {
     if (b_out) b_out[c] = b;
@@ -1649,18 +1641,26 @@ cudaError_t launch_evaluate_static(const SysDev& S, const Layout& Lo, const LatD
   // the summary word and the statuses of this call start at zero
   e = cudaMemsetAsync(scratch, 0, sizeof(int) * (64 + (size_t)n), st);
   if (e != cudaSuccess) return e;
-  const bool df = S.precision == LRDMC_PRECISION_DF64;
-  e = set_smem(df ? (const void*)k_evaluate_static<LRDMC_PRECISION_DF64>
-                  : (const void*)k_evaluate_static<LRDMC_PRECISION_FP64>,
-               Lo.smem_block_bytes);
-  if (e != cudaSuccess) return e;
   int blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  if (blocks > 0 && df)
-    k_evaluate_static<LRDMC_PRECISION_DF64><<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(
-        S, Lo, L, n, x, rot, ratio, T, b, el, scratch);
-  else if (blocks > 0)
-    k_evaluate_static<LRDMC_PRECISION_FP64><<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(
-        S, Lo, L, n, x, rot, ratio, T, b, el, scratch);
+  if (S.precision == LRDMC_PRECISION_DF64) {
+    e = set_smem((const void*)k_evaluate_static<LRDMC_PRECISION_DF64>, Lo.smem_block_bytes);
+    if (e != cudaSuccess) return e;
+    if (blocks > 0)
+      k_evaluate_static<LRDMC_PRECISION_DF64><<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(
+          S, Lo, L, n, x, rot, ratio, T, b, el, scratch);
+  } else if (S.precision == LRDMC_PRECISION_FP32) {
+    e = set_smem((const void*)k_evaluate_static<LRDMC_PRECISION_FP32>, Lo.smem_block_bytes);
+    if (e != cudaSuccess) return e;
+    if (blocks > 0)
+      k_evaluate_static<LRDMC_PRECISION_FP32><<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(
+          S, Lo, L, n, x, rot, ratio, T, b, el, scratch);
+  } else {
+    e = set_smem((const void*)k_evaluate_static<LRDMC_PRECISION_FP64>, Lo.smem_block_bytes);
+    if (e != cudaSuccess) return e;
+    if (blocks > 0)
+      k_evaluate_static<LRDMC_PRECISION_FP64><<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(
+          S, Lo, L, n, x, rot, ratio, T, b, el, scratch);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = cudaMemcpyAsync(summary, scratch, sizeof(int), cudaMemcpyDeviceToHost, st);

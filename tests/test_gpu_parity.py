@@ -243,3 +243,51 @@ def test_host_buffers_and_single_walker(pkg, oracle_mod):
     pop = oracle_mod.OraclePopulation(o, x0, seed=12, tau=0.05, e_trial=-0.5, recompute_every=1)
     pop.step(oracle_mod.lattice_for(system, 0.2, oracle_mod.SINGLE), 20, 1)
     assert np.allclose(g.energy_trace()[0], pop.trace()[0], rtol=RTOL, atol=0)
+
+
+# ---------------------------------------------------------------- mixed precision
+FP32_RTOL = 2e-4
+
+
+@pytest.mark.parametrize("name,kind,a", [("He", "this_work", 0.2), ("Ne", "this_work", 0.2),
+                                         ("Ar", "this_work", 1 / 63), ("H2O", "this_work", 0.1)])
+def test_fp32_evaluation_error(pkg, oracle_mod, name, kind, a):
+    """The mixed-precision mode (single-precision evaluation): every ratio
+    within 2e-4 of the FP64 oracle relative to max(1, |ratio|), the local
+    energy within 2e-4 relative; the measured error is far above FP64 parity
+    and far below the statistical noise of a projection."""
+    system = S.make_system(name)
+    g = pkg.LrdmcSystem(system).set_precision(pkg.PRECISION_FP32)
+    o = oracle_mod.OracleSystem(system)
+    n = 64
+    x = S.initial_positions(system, n, 301)
+    R = S.random_rotations(n, 302)
+    sp, lat = spacing_pair(pkg, oracle_mod, system, a, kind)
+    ratio, T, b, el = (t.cpu().numpy() for t in g.evaluate(torch.tensor(x, device="cuda"),
+                                                           torch.tensor(R, device="cuda"), a, sp))
+    worst_r = worst_e = 0.0
+    for c in range(n):
+        ref = o.lattice_eval(lat, x[c], R[c])
+        worst_r = max(worst_r, float(np.max(np.abs(ratio[c] - ref["ratio"]) / np.maximum(1.0, np.abs(ref["ratio"])))))
+        worst_e = max(worst_e, abs(el[c] - ref["EL"]) / abs(ref["EL"]))
+    assert worst_r < FP32_RTOL and worst_e < FP32_RTOL, (worst_r, worst_e)
+
+
+def test_fp32_projection_energy_matches_fp64(pkg):
+    """He, 8192 walkers, 600 intervals after 100 of equilibration: the mixed
+    mode's energy agrees with the FP64 mode's within 4 combined standard
+    errors plus 0.5 mHa."""
+    from paper_1909_01589_gb300 import stats
+
+    system = S.helium()
+    res = {}
+    for prec in (pkg.PRECISION_FP64, pkg.PRECISION_FP32):
+        g = pkg.LrdmcSystem(system).set_precision(prec)
+        g.init_walkers(torch.tensor(S.initial_positions(system, 8192, 77), device="cuda"), seed=77, tau=0.02,
+                       e_trial=-2.9, recompute_every=5, trace_capacity=700)
+        g.step(700, 0.2, pkg.Spacing(pkg.THIS_WORK))
+        e, w, _ = g.energy_trace()
+        e = e[100:]
+        res[prec] = (stats.energy_estimate(e, w[100:], 0), stats.reblock(e)[0])
+    (e64, s64), (e32, s32) = res[pkg.PRECISION_FP64], res[pkg.PRECISION_FP32]
+    assert abs(e64 - e32) < 4 * np.hypot(s64, s32) + 5e-4, (e64, s64, e32, s32)
