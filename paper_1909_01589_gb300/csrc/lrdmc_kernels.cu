@@ -72,6 +72,53 @@ __device__ void rotation_matrix(double u1, double u2, double u3, double* R)
   R[6] = 2.0 * (x * z - y * w);       R[7] = 2.0 * (y * z + x * w);       R[8] = 1.0 - 2.0 * (x * x + y * y);
 }
 
+// The same rotation with the work spread over the warp: lanes 0-3 evaluate
+// sqrt(1-u1), sqrt(u1), sincospi(2 u2) and sincospi(2 u3), lanes 0-8 then
+// form one entry of R each (the same operations as rotation_matrix, so the
+// result is identical). In the FP32 mode the rotation is computed in single
+// precision. All lanes must call it; R is written to shared memory.
+template <int PREC>
+__device__ __forceinline__ void rotation_matrix_warp(double u1, double u2, double u3, double* R, int lane)
+{
+  double q[4];
+  if (PREC == LRDMC_PRECISION_FP32) {
+    float a = 0.0f, c = 0.0f;
+    if (lane == 0) a = sqrtf(1.0f - (float)u1);
+    else if (lane == 1) a = sqrtf((float)u1);
+    else if (lane == 2) sincospif(2.0f * (float)u2, &a, &c);
+    else if (lane == 3) sincospif(2.0f * (float)u3, &a, &c);
+    float s1 = __shfl_sync(FULL_MASK, a, 0), s2 = __shfl_sync(FULL_MASK, a, 1);
+    float sa = __shfl_sync(FULL_MASK, a, 2), ca = __shfl_sync(FULL_MASK, c, 2);
+    float sb = __shfl_sync(FULL_MASK, a, 3), cb = __shfl_sync(FULL_MASK, c, 3);
+    q[0] = s1 * sa; q[1] = s1 * ca; q[2] = s2 * sb; q[3] = s2 * cb;
+  } else {
+    double a = 0.0, c = 0.0;
+    if (lane == 0) a = sqrt(1.0 - u1);
+    else if (lane == 1) a = sqrt(u1);
+    else if (lane == 2) sincospi(2.0 * u2, &a, &c);
+    else if (lane == 3) sincospi(2.0 * u3, &a, &c);
+    double s1 = __shfl_sync(FULL_MASK, a, 0), s2 = __shfl_sync(FULL_MASK, a, 1);
+    double sa = __shfl_sync(FULL_MASK, a, 2), ca = __shfl_sync(FULL_MASK, c, 2);
+    double sb = __shfl_sync(FULL_MASK, a, 3), cb = __shfl_sync(FULL_MASK, c, 3);
+    q[0] = s1 * sa; q[1] = s1 * ca; q[2] = s2 * sb; q[3] = s2 * cb;
+  }
+  const double x = q[0], y = q[1], z = q[2], w = q[3];
+  double v = 0.0;
+  switch (lane) {
+    case 0: v = 1.0 - 2.0 * (y * y + z * z); break;
+    case 1: v = 2.0 * (x * y - z * w); break;
+    case 2: v = 2.0 * (x * z + y * w); break;
+    case 3: v = 2.0 * (x * y + z * w); break;
+    case 4: v = 1.0 - 2.0 * (x * x + z * z); break;
+    case 5: v = 2.0 * (y * z - x * w); break;
+    case 6: v = 2.0 * (x * z - y * w); break;
+    case 7: v = 2.0 * (y * z + x * w); break;
+    case 8: v = 1.0 - 2.0 * (x * x + y * y); break;
+    default: break;
+  }
+  if (lane < 9) R[lane] = v;
+}
+
 // ----------------------------------------------------------------------------
 // Warp helpers.
 // ----------------------------------------------------------------------------
@@ -339,17 +386,21 @@ __device__ __forceinline__ WarpMem warp_mem(const Layout& Lo, const SysDev& S, d
   return m;
 }
 
-// Block-shared tables: MO coefficients, then the 2^(j/64) table.
+// Block-shared tables: MO coefficients (double, then a float copy), then
+// the 2^(j/64) table.
 struct BlockMem {
   double* C;
+  float* Cf;
   float2* tab;
 };
 
 __device__ __forceinline__ BlockMem block_mem(const SysDev& S, double* smem)
 {
   BlockMem b;
+  const int nc = S.n_ao * S.n_mo;
   b.C = smem;
-  b.tab = reinterpret_cast<float2*>(smem + S.n_ao * S.n_mo);
+  b.Cf = reinterpret_cast<float*>(smem + nc);
+  b.tab = reinterpret_cast<float2*>(smem + nc + (nc + 1) / 2);
   return b;
 }
 
@@ -857,14 +908,21 @@ __device__ void warp_eval_m(const SysDev& S, const double* sC, const LatDev& L, 
   typedef Ar<NT> A;
   const int N = S.N, nao = S.n_ao, nu = S.n_up;
   const BlockMem bm = block_mem(S, const_cast<double*>(sC));
-  // projected inverse columns in FP64, then converted with the positions
+  // projected inverse columns (FP64, or FP32 in the mixed mode), then
+  // converted with the positions
   for (int idx = lane; idx < N * nao; idx += 32) {
     int i = idx / nao, mu = idx % nao;
     int spin = i < nu ? 0 : 1, l = i < nu ? i : i - nu, n = spin ? S.n_dn : nu;
     const double* Am = spin ? wm.A + nu * nu : wm.A;
-    double acc = 0.0;
-    for (int m = 0; m < n; ++m) acc += sC[mu * S.n_mo + m] * Am[m * n + l];
-    wm.vd[idx] = A::store(A::from_double(acc));
+    if (sizeof(NT) == sizeof(float)) {
+      float acc = 0.0f;
+      for (int m = 0; m < n; ++m) acc += bm.Cf[mu * S.n_mo + m] * (float)Am[m * n + l];
+      wm.vd[idx] = df_make(acc, 0.0f);
+    } else {
+      double acc = 0.0;
+      for (int m = 0; m < n; ++m) acc += sC[mu * S.n_mo + m] * Am[m * n + l];
+      wm.vd[idx] = A::store(A::from_double(acc));
+    }
   }
   for (int j = lane; j < 3 * N; j += 32) wm.xd[j] = A::store(A::from_double(wm.x[j]));
   if (lane < 9) wm.Rd[lane] = A::store(A::from_double(wm.R[lane]));
@@ -1047,8 +1105,11 @@ __device__ __forceinline__ void store_record(const Layout& Lo, double* rec, cons
 
 __device__ __forceinline__ void stage_coefficients(const SysDev& S, double* sC)
 {
-  for (int j = threadIdx.x; j < S.n_ao * S.n_mo; j += blockDim.x) sC[j] = S.C[j];
   BlockMem bm = block_mem(S, sC);
+  for (int j = threadIdx.x; j < S.n_ao * S.n_mo; j += blockDim.x) {
+    sC[j] = S.C[j];
+    bm.Cf[j] = (float)S.C[j];
+  }
   for (int j = threadIdx.x; j < 64; j += blockDim.x) bm.tab[j] = S.D.exp.t[j];
   __syncthreads();
 }
@@ -1185,7 +1246,7 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
       double ur[4];
       draw_uniforms(P.seed, (uint64_t)s, k, m, kTagRot, ur);
       __syncwarp();
-      if (lane == 0) rotation_matrix(ur[0], ur[1], ur[2], wm.R);
+      rotation_matrix_warp<PREC>(ur[0], ur[1], ur[2], wm.R, lane);
       __syncwarp();
       warp_eval_any<PREC>(S, sC, L, wm, lane, nullptr, b, bdf, el);
       ++jumps;
@@ -1442,7 +1503,7 @@ Layout make_layout(const SysDev& S)
   Lo.smem_warp = 3 * S.N + S.n_up * S.n_up + S.n_dn * S.n_dn + 12 + Lo.P_max + S.N * S.n_ao + S.N +
                  (3 * S.N + S.N * S.n_ao + S.N + 12) + scr;
   Lo.smem_warp = (Lo.smem_warp + 1) & ~1;
-  Lo.head = ((S.n_ao * S.n_mo + 64) + 1) & ~1;
+  Lo.head = ((S.n_ao * S.n_mo + (S.n_ao * S.n_mo + 1) / 2 + 64) + 1) & ~1;
   Lo.smem_block_bytes = (int)sizeof(double) * (Lo.head + kWarpsPerBlock * Lo.smem_warp);
   return Lo;
 }
