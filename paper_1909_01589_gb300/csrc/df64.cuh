@@ -243,6 +243,38 @@ __host__ __device__ __forceinline__ df df_add_fast(df a, df b)
 
 __host__ __device__ __forceinline__ df df_sub_fast(df a, df b) { return df_add_fast(a, df_neg(b)); }
 
+// sin(pi x) and cos(pi x) for a double-float x in about [0, 2]: x = (n +
+// r)/2 with integer n and |r| <= 1/2, theta = r pi/2 (|theta| <= pi/4),
+// Taylor series of sin and cos in theta^2 to degree 15 and 16 (truncation
+// below 5e-16), then the quadrant n mod 4. inv_fact[k] = 1/k! and half_pi
+// as double-floats.
+DF_HEAVY void df_sincospi(df x, const df* inv_fact, df half_pi, df* s_out, df* c_out)
+{
+  df t = df_make(DF_ADD(x.hi, x.hi), DF_ADD(x.lo, x.lo));
+  float n = rintf(t.hi);
+  df r = df_add_f(t, -n);
+  df th = df_mul(r, half_pi);
+  df z = df_sqr(th);
+  df ps = df_neg(inv_fact[15]);
+  for (int j = 6; j >= 0; --j) {
+    df cj = inv_fact[2 * j + 1];
+    ps = df_add(df_mul(ps, z), (j & 1) ? df_neg(cj) : cj);
+  }
+  df sn = df_mul(th, ps);
+  df pc = inv_fact[16];
+  for (int j = 7; j >= 0; --j) {
+    df cj = inv_fact[2 * j];
+    pc = df_add(df_mul(pc, z), (j & 1) ? df_neg(cj) : cj);
+  }
+  const int q = ((int)n) & 3;
+  df so = sn, co = pc;
+  if (q == 1) { so = pc; co = df_neg(sn); }
+  else if (q == 2) { so = df_neg(sn); co = df_neg(pc); }
+  else if (q == 3) { so = df_neg(pc); co = sn; }
+  *s_out = so;
+  *c_out = co;
+}
+
 // Conversions (each touches the FP64 pipe: use them outside inner loops).
 __host__ __device__ __forceinline__ df df_from_double(double d)
 {

@@ -56,6 +56,8 @@ struct DfSys {
   df b_ee, c_par, c_anti, en_b2;
   DfShell sh[kMaxShell];
   ExpTable exp;
+  df inv_fact[18];  // 1/k!, k = 0..17 (series of sin and cos)
+  df half_pi;
 };
 
 // Trial function and Hamiltonian constants, passed by value as a kernel

@@ -59,6 +59,29 @@ __device__ __forceinline__ void draw_uniforms(uint64_t seed, uint64_t slot, uint
   for (int j = 0; j < 4; ++j) u[j] = to_u01(c[j]);
 }
 
+// The same uniform ((bits >> 12) + 1/2) 2^-52 as a double-float, built from
+// the integer without the FP64 pipe: the top 24 of the 52 bits give hi, the
+// remaining 28 bits (plus the half) give lo.
+__device__ __forceinline__ df df_u01(uint64_t bits)
+{
+  uint64_t v = bits >> 12;
+  float hi = (float)(uint32_t)(v >> 28) * 0x1.0p-24f;
+  float lo = ((float)(uint32_t)(v & 0xFFFFFFFull) + 0.5f) * 0x1.0p-52f;
+  return fast_two_sum(hi, lo);
+}
+
+// A single-precision uniform from the top 24 bits, in (0, 1).
+__device__ __forceinline__ float f_u01(uint64_t bits)
+{
+  return ((float)(uint32_t)(bits >> 40) + 0.5f) * 0x1.0p-24f;
+}
+
+__device__ __forceinline__ uint64_t shfl_u64(uint64_t v, int src)
+{
+  uint32_t lo = __shfl_sync(0xffffffffu, (uint32_t)v, src), hi = __shfl_sync(0xffffffffu, (uint32_t)(v >> 32), src);
+  return ((uint64_t)hi << 32) | lo;
+}
+
 // Uniformly random rotation (Shoemake's unit quaternion from three uniforms).
 __device__ void rotation_matrix(double u1, double u2, double u3, double* R)
 {
@@ -72,37 +95,80 @@ __device__ void rotation_matrix(double u1, double u2, double u3, double* R)
   R[6] = 2.0 * (x * z - y * w);       R[7] = 2.0 * (y * z + x * w);       R[8] = 1.0 - 2.0 * (x * x + y * y);
 }
 
-// The same rotation with the work spread over the warp: lanes 0-3 evaluate
-// sqrt(1-u1), sqrt(u1), sincospi(2 u2) and sincospi(2 u3), lanes 0-8 then
-// form one entry of R each (the same operations as rotation_matrix, so the
-// result is identical). In the FP32 mode the rotation is computed in single
-// precision. All lanes must call it; R is written to shared memory.
+// The same rotation from the three uniforms of bits[0..2], with the work
+// spread over the warp: lanes 0-3 evaluate sqrt(1-u1), sqrt(u1),
+// sincospi(2 u2) and sincospi(2 u3), lanes 0-8 then form one entry of R
+// each. FP64 mode: IEEE double (the same operations as rotation_matrix).
+// DF64 mode: double-float (the FP32 pipe), accurate to ~1e-15. FP32 mode:
+// single precision. All lanes must call it; R (double) goes to shared memory.
 template <int PREC>
-__device__ __forceinline__ void rotation_matrix_warp(double u1, double u2, double u3, double* R, int lane)
+__device__ __forceinline__ void rotation_matrix_warp(const uint64_t* bits, double* R, int lane, const SysDev& S)
 {
-  double q[4];
+  double x, y, z, w;
   if (PREC == LRDMC_PRECISION_FP32) {
     float a = 0.0f, c = 0.0f;
-    if (lane == 0) a = sqrtf(1.0f - (float)u1);
-    else if (lane == 1) a = sqrtf((float)u1);
-    else if (lane == 2) sincospif(2.0f * (float)u2, &a, &c);
-    else if (lane == 3) sincospif(2.0f * (float)u3, &a, &c);
+    if (lane == 0) a = sqrtf(1.0f - f_u01(bits[0]));
+    else if (lane == 1) a = sqrtf(f_u01(bits[0]));
+    else if (lane == 2) sincospif(2.0f * f_u01(bits[1]), &a, &c);
+    else if (lane == 3) sincospif(2.0f * f_u01(bits[2]), &a, &c);
     float s1 = __shfl_sync(FULL_MASK, a, 0), s2 = __shfl_sync(FULL_MASK, a, 1);
     float sa = __shfl_sync(FULL_MASK, a, 2), ca = __shfl_sync(FULL_MASK, c, 2);
     float sb = __shfl_sync(FULL_MASK, a, 3), cb = __shfl_sync(FULL_MASK, c, 3);
-    q[0] = s1 * sa; q[1] = s1 * ca; q[2] = s2 * sb; q[3] = s2 * cb;
-  } else {
+    float qx = s1 * sa, qy = s1 * ca, qz = s2 * sb, qw = s2 * cb;
+    float v = 0.0f;
+    switch (lane) {
+      case 0: v = 1.0f - 2.0f * (qy * qy + qz * qz); break;
+      case 1: v = 2.0f * (qx * qy - qz * qw); break;
+      case 2: v = 2.0f * (qx * qz + qy * qw); break;
+      case 3: v = 2.0f * (qx * qy + qz * qw); break;
+      case 4: v = 1.0f - 2.0f * (qx * qx + qz * qz); break;
+      case 5: v = 2.0f * (qy * qz - qx * qw); break;
+      case 6: v = 2.0f * (qx * qz - qy * qw); break;
+      case 7: v = 2.0f * (qy * qz + qx * qw); break;
+      case 8: v = 1.0f - 2.0f * (qx * qx + qy * qy); break;
+      default: break;
+    }
+    if (lane < 9) R[lane] = (double)v;
+    return;
+  }
+  if (PREC == LRDMC_PRECISION_DF64) {
+    df a = df_make(0.0f, 0.0f), c = df_make(0.0f, 0.0f);
+    if (lane == 0) a = df_sqrt(df_add_f(df_neg(df_u01(bits[0])), 1.0f));
+    else if (lane == 1) a = df_sqrt(df_u01(bits[0]));
+    else if (lane == 2) df_sincospi(df_mul_f(df_u01(bits[1]), 2.0f), S.D.inv_fact, S.D.half_pi, &a, &c);
+    else if (lane == 3) df_sincospi(df_mul_f(df_u01(bits[2]), 2.0f), S.D.inv_fact, S.D.half_pi, &a, &c);
+    typedef Ar<df> A;
+    df s1 = A::shfl(a, 0), s2 = A::shfl(a, 1), sa = A::shfl(a, 2), ca = A::shfl(c, 2);
+    df sb = A::shfl(a, 3), cb = A::shfl(c, 3);
+    df qx = df_mul(s1, sa), qy = df_mul(s1, ca), qz = df_mul(s2, sb), qw = df_mul(s2, cb);
+    df v = df_make(0.0f, 0.0f);
+    switch (lane) {
+      case 0: v = df_add_f(df_mul_f(df_add(df_sqr(qy), df_sqr(qz)), -2.0f), 1.0f); break;
+      case 1: v = df_mul_f(df_sub(df_mul(qx, qy), df_mul(qz, qw)), 2.0f); break;
+      case 2: v = df_mul_f(df_add(df_mul(qx, qz), df_mul(qy, qw)), 2.0f); break;
+      case 3: v = df_mul_f(df_add(df_mul(qx, qy), df_mul(qz, qw)), 2.0f); break;
+      case 4: v = df_add_f(df_mul_f(df_add(df_sqr(qx), df_sqr(qz)), -2.0f), 1.0f); break;
+      case 5: v = df_mul_f(df_sub(df_mul(qy, qz), df_mul(qx, qw)), 2.0f); break;
+      case 6: v = df_mul_f(df_sub(df_mul(qx, qz), df_mul(qy, qw)), 2.0f); break;
+      case 7: v = df_mul_f(df_add(df_mul(qy, qz), df_mul(qx, qw)), 2.0f); break;
+      case 8: v = df_add_f(df_mul_f(df_add(df_sqr(qx), df_sqr(qy)), -2.0f), 1.0f); break;
+      default: break;
+    }
+    if (lane < 9) R[lane] = df_to_double(v);
+    return;
+  }
+  {
     double a = 0.0, c = 0.0;
+    const double u1 = to_u01(bits[0]);
     if (lane == 0) a = sqrt(1.0 - u1);
     else if (lane == 1) a = sqrt(u1);
-    else if (lane == 2) sincospi(2.0 * u2, &a, &c);
-    else if (lane == 3) sincospi(2.0 * u3, &a, &c);
+    else if (lane == 2) sincospi(2.0 * to_u01(bits[1]), &a, &c);
+    else if (lane == 3) sincospi(2.0 * to_u01(bits[2]), &a, &c);
     double s1 = __shfl_sync(FULL_MASK, a, 0), s2 = __shfl_sync(FULL_MASK, a, 1);
     double sa = __shfl_sync(FULL_MASK, a, 2), ca = __shfl_sync(FULL_MASK, c, 2);
     double sb = __shfl_sync(FULL_MASK, a, 3), cb = __shfl_sync(FULL_MASK, c, 3);
-    q[0] = s1 * sa; q[1] = s1 * ca; q[2] = s2 * sb; q[3] = s2 * cb;
+    x = s1 * sa; y = s1 * ca; z = s2 * sb; w = s2 * cb;
   }
-  const double x = q[0], y = q[1], z = q[2], w = q[3];
   double v = 0.0;
   switch (lane) {
     case 0: v = 1.0 - 2.0 * (y * y + z * z); break;
@@ -390,6 +456,7 @@ __device__ __forceinline__ WarpMem warp_mem(const Layout& Lo, const SysDev& S, d
 // the 2^(j/64) table.
 struct BlockMem {
   double* C;
+  df* Cd;
   float* Cf;
   float2* tab;
 };
@@ -399,8 +466,9 @@ __device__ __forceinline__ BlockMem block_mem(const SysDev& S, double* smem)
   BlockMem b;
   const int nc = S.n_ao * S.n_mo;
   b.C = smem;
-  b.Cf = reinterpret_cast<float*>(smem + nc);
-  b.tab = reinterpret_cast<float2*>(smem + nc + (nc + 1) / 2);
+  b.Cd = reinterpret_cast<df*>(smem + nc);
+  b.Cf = reinterpret_cast<float*>(smem + 2 * nc);
+  b.tab = reinterpret_cast<float2*>(smem + 2 * nc + (nc + 1) / 2);
   return b;
 }
 
@@ -1036,6 +1104,74 @@ __device__ void ao_values_df_lanes(const SysDev& S, const double* p, double* out
   }
 }
 
+// chi_mu(p) for all AOs in double-float into out (df), lanes by exponent group.
+__device__ void ao_values_df_out(const SysDev& S, const df* pd, df* out, int lane, const BlockMem& bm)
+{
+  typedef Ar<df> A;
+  int prev_c = -1, grp = -1;
+  df d[3] = {A::zero(), A::zero(), A::zero()}, r = A::zero(), r2 = A::zero(), e = A::zero();
+  for (int q = 0; q < S.n_shell; ++q) {
+    const ShellDev& sh = S.sh[q];
+    const DfShell& dsh = S.D.sh[q];
+    if (!(sh.kind == 0 && sh.same_exp)) ++grp;
+    if ((grp & 31) != lane) continue;
+    if (sh.center != prev_c) {
+      prev_c = sh.center;
+      d[0] = df_sub_fast(pd[0], S.D.nuc[prev_c][0]);
+      d[1] = df_sub_fast(pd[1], S.D.nuc[prev_c][1]);
+      d[2] = df_sub_fast(pd[2], S.D.nuc[prev_c][2]);
+      r2 = dot3<df>(d[0], d[1], d[2]);
+      r = df_sqrt(r2);
+    }
+    if (sh.kind == 0 && !sh.same_exp) e = df_exp(df_neg(df_mul(dsh.zeta, r)), S.D.exp.K, bm.tab);
+    df Rv = radial_value_m<df>(S, sh, dsh, r, r2, e, bm);
+    df Sv[5];
+    int nf = solid_m<df>(sh.l, d, Sv);
+    for (int f = 0; f < nf; ++f) out[sh.ao_offset + f] = df_mul(Sv[f], Rv);
+  }
+}
+
+// Sherman-Morrison update in double-float arithmetic (modes other than
+// FP64): the orbitals at the new position, y = phi A^-1, ratio = y_l, and
+// the rank-one update, with the spin block read from and written back to
+// its IEEE-double copy. pd: the new position as a double-float.
+__device__ bool warp_sm_update_df(const SysDev& S, const BlockMem& bm, const WarpMem& wm, int i, const df* pd,
+                                  int lane)
+{
+  const int nu = S.n_up;
+  const int spin = i < nu ? 0 : 1, l = i < nu ? i : i - nu, n = spin ? S.n_dn : nu;
+  double* A = spin ? wm.A + nu * nu : wm.A;
+  df* chi = reinterpret_cast<df*>(wm.scr);  // [n_ao]
+  df* phi = chi + S.n_ao;                   // [n]
+  df* y = phi + n;                          // [n]
+  df* Ad = y + n;                           // [n][n]
+  ao_values_df_out(S, pd, chi, lane, bm);
+  for (int idx = lane; idx < n * n; idx += 32) Ad[idx] = df_from_double(A[idx]);
+  __syncwarp();
+  for (int m = lane; m < n; m += 32) {
+    df a = df_make(0.0f, 0.0f);
+    for (int mu = 0; mu < S.n_ao; ++mu) a = df_add(a, df_mul(bm.Cd[mu * S.n_mo + m], chi[mu]));
+    phi[m] = a;
+  }
+  __syncwarp();
+  for (int q = lane; q < n; q += 32) {
+    df a = df_make(0.0f, 0.0f);
+    for (int m = 0; m < n; ++m) a = df_add(a, df_mul(phi[m], Ad[m * n + q]));
+    y[q] = a;
+  }
+  __syncwarp();
+  const df ratio = y[l];
+  if (ratio.hi == 0.0f) return false;
+  const df inv = df_rcp(ratio);
+  for (int idx = lane; idx < n * n; idx += 32) {
+    int m = idx / n, q = idx % n;
+    df yq = (q == l) ? df_add_f(y[q], -1.0f) : y[q];
+    A[idx] = df_to_double(df_sub(Ad[idx], df_mul(Ad[m * n + l], df_mul(yq, inv))));
+  }
+  __syncwarp();
+  return true;
+}
+
 template <int PREC>
 __device__ bool warp_sm_update(const SysDev& S, const double* sC, const WarpMem& wm, int i,
                                const double* p, int lane)
@@ -1108,6 +1244,7 @@ __device__ __forceinline__ void stage_coefficients(const SysDev& S, double* sC)
   BlockMem bm = block_mem(S, sC);
   for (int j = threadIdx.x; j < S.n_ao * S.n_mo; j += blockDim.x) {
     sC[j] = S.C[j];
+    bm.Cd[j] = df_from_double(S.C[j]);
     bm.Cf[j] = (float)S.C[j];
   }
   for (int j = threadIdx.x; j < 64; j += blockDim.x) bm.tab[j] = S.D.exp.t[j];
@@ -1202,16 +1339,23 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
     double tau_left = P.tau, logw = 0.0;
     int jumps = 0;
     for (uint64_t m = 0;; ++m) {
-      double u[4];
-      draw_uniforms(P.seed, (uint64_t)s, k, m, kTagTimeHB, u);
+      // both draws of this iteration at once: even lanes compute the
+      // (waiting time, heat bath) block, odd lanes the rotation block
+      uint64_t cb[4] = {(uint64_t)s, k, m, (lane & 1) ? kTagRot : kTagTimeHB};
+      philox4x64_10(cb, P.seed, 0ull);
+      uint64_t b0[4], b1[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        b0[j] = shfl_u64(cb[j], 0);
+        b1[j] = shfl_u64(cb[j], 1);
+      }
       double t;
       if (PREC == LRDMC_PRECISION_DF64)
-        t = b > 0.0 ? df_to_double(df_div(df_neg(df_log(df_from_double(u[0]), S.D.exp.K, bm.tab)), bdf))
-                    : INFINITY;
+        t = b > 0.0 ? df_to_double(df_div(df_neg(df_log(df_u01(b0[0]), S.D.exp.K, bm.tab)), bdf)) : INFINITY;
       else if (PREC == LRDMC_PRECISION_FP32)
-        t = b > 0.0 ? (double)(-logf((float)u[0]) / bdf.hi) : INFINITY;
+        t = b > 0.0 ? (double)(-logf(f_u01(b0[0])) / bdf.hi) : INFINITY;
       else
-        t = b > 0.0 ? -log(u[0]) / b : INFINITY;
+        t = b > 0.0 ? -log(to_u01(b0[0])) / b : INFINITY;
       if (t >= tau_left) {
         logw -= tau_left * (el - P.e_trial);
         break;
@@ -1221,12 +1365,11 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
       // heat bath over the cached rates
       int pick, last;
       if (PREC == LRDMC_PRECISION_DF64)
-        warp_scan_m<df>(reinterpret_cast<const df*>(wm.T), P_moves, lane, df_mul(df_from_double(u[1]), bdf), &pick,
-                        &last);
+        warp_scan_m<df>(reinterpret_cast<const df*>(wm.T), P_moves, lane, df_mul(df_u01(b0[1]), bdf), &pick, &last);
       else if (PREC == LRDMC_PRECISION_FP32)
-        warp_scan_m<float>(reinterpret_cast<const df*>(wm.T), P_moves, lane, (float)u[1] * bdf.hi, &pick, &last);
+        warp_scan_m<float>(reinterpret_cast<const df*>(wm.T), P_moves, lane, f_u01(b0[1]) * bdf.hi, &pick, &last);
       else
-        warp_scan(wm.T, P_moves, lane, u[1] * b, &pick, &last);
+        warp_scan(wm.T, P_moves, lane, to_u01(b0[1]) * b, &pick, &last);
       if (pick < 0) pick = last;
       if (pick < 0) {  // no allowed move: cannot happen with b > 0
         if (lane == 0) atomicOr(P.err, kErrNonFinite);
@@ -1238,15 +1381,25 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
       double pnew[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) pnew[d] = wm.x[3 * i + d] + sign * h * wm.R[3 * d + kx];
-      if (!warp_sm_update<PREC>(S, sC, wm, i, pnew, lane)) {
+      bool sm_ok;
+      if (PREC == LRDMC_PRECISION_FP64) {
+        sm_ok = warp_sm_update<PREC>(S, sC, wm, i, pnew, lane);
+      } else {
+        // the new position as a double-float: the candidate position of the evaluation
+        df hd = g ? L.ap_df : L.a_df;
+        if (pick & 1) hd = df_neg(hd);
+        df pd[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) pd[d] = df_add(wm.xd[3 * i + d], df_mul(hd, wm.Rd[3 * d + kx]));
+        sm_ok = warp_sm_update_df(S, bm, wm, i, pd, lane);
+      }
+      if (!sm_ok) {
         if (lane == 0) atomicOr(P.err, kErrSingular);
         break;
       }
       if (lane < 3) wm.x[3 * i + lane] = pnew[lane];
-      double ur[4];
-      draw_uniforms(P.seed, (uint64_t)s, k, m, kTagRot, ur);
       __syncwarp();
-      rotation_matrix_warp<PREC>(ur[0], ur[1], ur[2], wm.R, lane);
+      rotation_matrix_warp<PREC>(b1, wm.R, lane, S);
       __syncwarp();
       warp_eval_any<PREC>(S, sC, L, wm, lane, nullptr, b, bdf, el);
       ++jumps;
@@ -1467,6 +1620,12 @@ void fill_df_constants(SysDev& S)
     df t = split_ld(exp2l((long double)j / 64.0L));
     D.exp.t[j] = make_float2(t.hi, t.lo);
   }
+  long double f = 1.0L;
+  for (int k = 0; k < 18; ++k) {
+    if (k > 0) f *= (long double)k;
+    D.inv_fact[k] = split_ld(1.0L / f);
+  }
+  D.half_pi = split_ld(2.0L * atanl(1.0L));
 }
 
 void fill_lattice_df(LatDev& L)
@@ -1498,12 +1657,12 @@ Layout make_layout(const SysDev& S)
   Lo.rec = (Lo.off_el + 1 + 3) & ~3;
   const int n = S.n_up;
   int scr = 2 * n * n + n * S.n_ao;          // Gauss-Jordan + orbital rows
-  int scr_sm = S.n_ao + 3 * n;               // Sherman-Morrison
+  int scr_sm = S.n_ao + 3 * n + n * n;       // Sherman-Morrison (FP64 or double-float)
   if (scr_sm > scr) scr = scr_sm;
   Lo.smem_warp = 3 * S.N + S.n_up * S.n_up + S.n_dn * S.n_dn + 12 + Lo.P_max + S.N * S.n_ao + S.N +
                  (3 * S.N + S.N * S.n_ao + S.N + 12) + scr;
   Lo.smem_warp = (Lo.smem_warp + 1) & ~1;
-  Lo.head = ((S.n_ao * S.n_mo + (S.n_ao * S.n_mo + 1) / 2 + 64) + 1) & ~1;
+  Lo.head = ((2 * S.n_ao * S.n_mo + (S.n_ao * S.n_mo + 1) / 2 + 64) + 1) & ~1;
   Lo.smem_block_bytes = (int)sizeof(double) * (Lo.head + kWarpsPerBlock * Lo.smem_warp);
   return Lo;
 }
