@@ -1385,12 +1385,10 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
       if (PREC == LRDMC_PRECISION_FP64) {
         sm_ok = warp_sm_update<PREC>(S, sC, wm, i, pnew, lane);
       } else {
-        // the new position as a double-float: the candidate position of the evaluation
-        df hd = g ? L.ap_df : L.a_df;
-        if (pick & 1) hd = df_neg(hd);
-        df pd[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) pd[d] = df_add(wm.xd[3 * i + d], df_mul(hd, wm.Rd[3 * d + kx]));
+        // the new position as a double-float (the shared-memory double-float
+        // copies of x and R belong to the last evaluation, which for the
+        // first jump of an interval may have been another walker's)
+        df pd[3] = {df_from_double(pnew[0]), df_from_double(pnew[1]), df_from_double(pnew[2])};
         sm_ok = warp_sm_update_df(S, bm, wm, i, pd, lane);
       }
       if (!sm_ok) {
