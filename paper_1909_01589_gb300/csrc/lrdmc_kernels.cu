@@ -59,14 +59,19 @@ __device__ __forceinline__ void draw_uniforms(uint64_t seed, uint64_t slot, uint
   for (int j = 0; j < 4; ++j) u[j] = to_u01(c[j]);
 }
 
-// The same uniform ((bits >> 12) + 1/2) 2^-52 as a double-float, built from
-// the integer without the FP64 pipe: the top 24 of the 52 bits give hi, the
-// remaining 28 bits (plus the half) give lo.
+// The same uniform ((bits >> 12) + 1/2) 2^-52 = N 2^-53, N = 2 (bits >> 12)
+// + 1 < 2^53, as a double-float built with integer operations only (no FP64
+// pipe): the 24 bits below N's leading bit give hi exactly, the remaining
+// low bits (at most 29) give lo, so the relative error is below 2^-47 for
+// every uniform, however small.
 __device__ __forceinline__ df df_u01(uint64_t bits)
 {
-  uint64_t v = bits >> 12;
-  float hi = (float)(uint32_t)(v >> 28) * 0x1.0p-24f;
-  float lo = ((float)(uint32_t)(v & 0xFFFFFFFull) + 0.5f) * 0x1.0p-52f;
+  const uint64_t N = ((bits >> 12) << 1) | 1ull;
+  const int sh = (63 - __clzll((long long)N)) - 23;  // shift that leaves 24 bits
+  const uint64_t top = sh >= 0 ? (N >> sh) : (N << (-sh));
+  const uint64_t rem = sh > 0 ? (N - (top << sh)) : 0ull;
+  const float hi = (float)(uint32_t)top * __int_as_float((127 + sh - 53) << 23);
+  const float lo = (float)(uint32_t)rem * 0x1.0p-53f;
   return fast_two_sum(hi, lo);
 }
 
