@@ -1136,8 +1136,8 @@ __device__ void ao_values_df_out(const SysDev& S, const df* pd, df* out, int lan
   }
 }
 
-// Sherman-Morrison update in double-float arithmetic (modes other than
-// FP64): the orbitals at the new position, y = phi A^-1, ratio = y_l, and
+// Sherman-Morrison update in double-float arithmetic (the FP32 mode): the
+// orbitals at the new position, y = phi A^-1, ratio = y_l, and
 // the rank-one update, with the spin block read from and written back to
 // its IEEE-double copy. pd: the new position as a double-float.
 __device__ bool warp_sm_update_df(const SysDev& S, const BlockMem& bm, const WarpMem& wm, int i, const df* pd,
@@ -1387,7 +1387,11 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
 #pragma unroll
       for (int d = 0; d < 3; ++d) pnew[d] = wm.x[3 * i + d] + sign * h * wm.R[3 * d + kx];
       bool sm_ok;
-      if (PREC == LRDMC_PRECISION_FP64) {
+      if (PREC != LRDMC_PRECISION_FP32) {
+        // the parity modes keep the update in IEEE double: near a node the
+        // update amplifies rounding by the condition number of the Slater
+        // matrix, and a double-float update (2^-48) parts trajectories from
+        // the FP64 reference in rare walkers
         sm_ok = warp_sm_update<PREC>(S, sC, wm, i, pnew, lane);
       } else {
         // the new position as a double-float (the shared-memory double-float
