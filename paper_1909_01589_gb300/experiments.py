@@ -1,0 +1,134 @@
+"""Paper-style experiments on the GPU path: single vs double grid.
+
+For atoms at the paper's lattice spacing a = 1/(alpha Z) (alpha = 3.5 in
+Table I and Fig. 2), the same population is projected with the single grid,
+with the double grid of this work (Eq. 3, S-13, Eq. 6/7) and with the
+previous double grid (Eq. 2, Eq. 4). Reported per run: the energy and its
+blocked error, the mean number of jumps per interval (the acceptance-rate
+analogue of the acceleration column of Table S-I), the GPU time, and the
+efficiency 1/(sigma^2 t). Ratios to the single grid give the bias (energy
+difference) and the acceleration at fixed error (efficiency ratio), the
+quantities of Table I, Table S-I and Fig. 2.
+
+The trial functions are this library's synthetic Slater-Jastrow atoms, not
+the paper's optimised JAGP wavefunctions, so the numbers show the method's
+behaviour on these systems and are context for, not reproductions of, the
+paper's tables.
+
+Usage: python -m paper_1909_01589_gb300.experiments [--systems He,Ne,Ar,Kr]
+       [--steps 1000] [--out results/single_vs_double.json]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import time
+
+import numpy as np
+
+from . import LrdmcSystem, Spacing, SINGLE, THIS_WORK, PREVIOUS, PRECISION_DF64
+from . import stats
+
+DEFAULTS = {  # system: (walkers, e_trial, target jumps per interval)
+    "He": (4096, -2.90, 10.0),
+    "Ne": (4096, -128.9, 10.0),
+    "Ar": (2048, -527.5, 10.0),
+    "Kr": (1024, -2753.0, 10.0),
+    "H2O": (4096, -76.0, 10.0),
+}
+
+
+def run(system, a, spacing, W, steps, equil, tau, e_trial, seed=1, precision=PRECISION_DF64, device="cuda"):
+    """One projection; returns energy, error, jumps/interval, GPU seconds."""
+    import torch
+
+    import lrdmc_synth as S
+
+    g = LrdmcSystem(system).set_precision(precision)
+    x0 = S.initial_positions(system, W, seed)
+    g.init_walkers(torch.tensor(x0, device=device), seed=seed, tau=tau, e_trial=e_trial, recompute_every=5,
+                   trace_capacity=steps + equil + 4)
+    g.step(equil, a, spacing)
+    g.sync()
+    torch.cuda.synchronize()
+    m0 = g.moves()
+    t0 = time.perf_counter()
+    g.step(steps, a, spacing)
+    g.sync()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    moves = g.moves() - m0
+    e, w, j = g.energy_trace()
+    e, w, j = e[equil:], w[equil:], j[equil:]
+    err, _ = stats.reblock(e)
+    return {"energy": stats.energy_estimate(e, w, 0), "error": err, "jumps_per_interval": float(np.mean(j)),
+            "seconds": dt, "moves": int(moves), "efficiency": stats.efficiency(e, dt), "intervals": steps}
+
+
+def _tau_for(system, a, e_trial, jumps, seed):
+    """Interval length giving the single grid about `jumps` jumps per walker:
+    jumps / <b> with <b> the mean total rate of 256 equilibrated walkers."""
+    import torch
+
+    import lrdmc_synth as S
+
+    g = LrdmcSystem(system)
+    g.init_walkers(torch.tensor(S.initial_positions(system, 256, seed), device="cuda"), seed=seed, tau=1e-6,
+                   e_trial=e_trial, recompute_every=5, trace_capacity=4)
+    g.step(2, a, Spacing(SINGLE))
+    b = g.walkers()["b"]
+    return float(jumps / np.mean(b))
+
+
+def single_vs_double(names=("He", "Ne", "Ar", "Kr"), alpha=3.5, steps=1000, equil=200, seed=1):
+    import lrdmc_synth as S
+
+    rows = []
+    for name in names:
+        system = S.make_system(name)
+        Z = float(np.max(system.Z))
+        a = 1.0 / (alpha * Z)
+        W, e_trial, jumps = DEFAULTS[name]
+        g = LrdmcSystem(system)
+        ratio, rc = g.spacing_params(a, Spacing(THIS_WORK))
+        tau = _tau_for(system, a, e_trial, jumps, seed)
+        res = {}
+        for label, sp in (("single", Spacing(SINGLE)), ("double_this_work", Spacing(THIS_WORK)),
+                          ("double_previous", Spacing(PREVIOUS))):
+            res[label] = run(system, a, sp, W, steps, equil, tau, e_trial, seed)
+        s = res["single"]
+        row = {"system": name, "Z": Z, "a": a, "alpha": alpha, "aprime_over_a": ratio, "rc": rc, "tau": tau,
+               "walkers": W, **{k: v for k, v in res.items()}}
+        for label in ("double_this_work", "double_previous"):
+            d = res[label]
+            row[label + "_bias_mHa"] = 1e3 * (d["energy"] - s["energy"])
+            row[label + "_bias_err_mHa"] = 1e3 * float(np.hypot(d["error"], s["error"]))
+            row[label + "_acceleration_jumps"] = s["jumps_per_interval"] / max(d["jumps_per_interval"], 1e-12)
+            row[label + "_acceleration_efficiency"] = d["efficiency"] / s["efficiency"]
+        rows.append(row)
+    return rows
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--systems", default="He,Ne,Ar,Kr")
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--equil", type=int, default=200)
+    ap.add_argument("--alpha", type=float, default=3.5)
+    ap.add_argument("--out", default="results/single_vs_double.json")
+    args = ap.parse_args()
+    rows = single_vs_double(args.systems.split(","), args.alpha, args.steps, args.equil)
+    os.makedirs(os.path.dirname(args.out) or ".", exist_ok=True)
+    json.dump(rows, open(args.out, "w"), indent=1)
+    for r in rows:
+        print(f"{r['system']:3s} Z={r['Z']:4.0f} a={r['a']:.5f} a'/a={r['aprime_over_a']:.3f} "
+              f"E_single={r['single']['energy']:.5f}({1e3 * r['single']['error']:.1f}mHa) "
+              f"bias_this={r['double_this_work_bias_mHa']:+.2f}({r['double_this_work_bias_err_mHa']:.2f}) "
+              f"bias_prev={r['double_previous_bias_mHa']:+.2f}({r['double_previous_bias_err_mHa']:.2f}) "
+              f"acc_jumps={r['double_this_work_acceleration_jumps']:.2f} "
+              f"acc_eff={r['double_this_work_acceleration_efficiency']:.2f}", flush=True)
+
+
+if __name__ == "__main__":
+    main()
