@@ -143,7 +143,8 @@ LRDMC_API lrdmc_status lrdmc_workspace_bytes(lrdmc_system_t sys, int n_walkers, 
  * number of intervals between full recomputations of the inverse Slater
  * matrices (0 = never). stream is a cudaStream_t (NULL = default stream).
  * Fails with LRDMC_ERR_SINGULAR if a start configuration has a singular
- * Slater matrix. */
+ * Slater matrix: two electrons of one spin on the same point, or a zero or
+ * non-finite pivot in the elimination. */
 LRDMC_API lrdmc_status lrdmc_init_walkers(lrdmc_system_t sys, int n_walkers, const double* x0,
                                 uint64_t seed, double tau, double e_trial, int recompute_every,
                                 int trace_capacity, void* workspace, size_t workspace_bytes,

@@ -480,7 +480,7 @@ __device__ __forceinline__ BlockMem block_mem(const SysDev& S, double* smem)
 // ----------------------------------------------------------------------------
 // Inverse Slater matrix of one spin block by Gauss-Jordan elimination with
 // partial pivoting (warp-cooperative). A[l][m] = phi_m(r_l); the inverse is
-// stored as Ainv[m][l]. Returns false if a pivot is zero.
+// stored as Ainv[m][l]. Returns false for a singular matrix (below).
 // ----------------------------------------------------------------------------
 __device__ bool warp_inverse(const SysDev& S, const double* sC, const double* sx, int spin,
                              double* Ainv, double* scr, int lane)
@@ -501,22 +501,25 @@ __device__ bool warp_inverse(const SysDev& S, const double* sC, const double* sx
     }
   }
   __syncwarp();
-  // A pivot below 1e-13 of the largest entry its column had before the
-  // elimination marks a numerically singular Slater matrix (two equal-spin
-  // electrons on one point leave a residual row of rounding size). The
-  // test is per column: orbitals of very different size (core and valence
-  // of a heavy atom) make pivots legitimately small against the largest
-  // entry of the whole matrix.
-  double* colmax = chi;  // [n], chi rows are no longer needed
-  for (int m = lane; m < n; m += 32) {
-    double c = 0.0;
-    for (int l = 0; l < n; ++l) c = fmax(c, fabs(M[l * w2 + m]));
-    colmax[m] = c;
+  // Singular Slater matrix: two equal-spin electrons on one point (the
+  // determinant vanishes by antisymmetry; elimination would leave a residual
+  // row of rounding size, not an exact zero), or a pivot that is zero or not
+  // finite. No relative pivot threshold is applied: the orbitals of a heavy
+  // atom span many orders of magnitude (a 1s value at a valence electron),
+  // so pivots far below the largest entry of their column are legitimate,
+  // and rounding noise amplified by that scale spread cannot be told apart
+  // from a small genuine pivot.
+  int coincide = 0;
+  for (int pr = lane; pr < n * n; pr += 32) {
+    const int l = pr / n, q = pr % n;
+    if (q <= l) continue;
+    const double* a = &sx[3 * (off + l)];
+    const double* c = &sx[3 * (off + q)];
+    coincide |= (a[0] == c[0] && a[1] == c[1] && a[2] == c[2]);
   }
-  __syncwarp();
+  if (__any_sync(FULL_MASK, coincide)) return false;
   bool ok = true;
   for (int col = 0; col < n && ok; ++col) {
-    const double tiny = 1e-13 * colmax[col];
     // pivot row: largest |M[r][col]| for r >= col, lowest r on ties
     double best = -1.0;
     int br = col;
@@ -530,7 +533,7 @@ __device__ bool warp_inverse(const SysDev& S, const double* sC, const double* sx
       int orr = __shfl_xor_sync(FULL_MASK, br, o);
       if (ob > best || (ob == best && orr < br)) { best = ob; br = orr; }
     }
-    if (!(best > tiny)) { ok = false; break; }
+    if (!(best > 0.0) || !isfinite(best)) { ok = false; break; }
     if (br != col) {
       for (int j = lane; j < w2; j += 32) {
         double t = M[col * w2 + j];
