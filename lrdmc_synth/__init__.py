@@ -376,3 +376,58 @@ def random_rotations(n: int, seed: int) -> np.ndarray:
     from scipy.spatial.transform import Rotation
 
     return Rotation.random(n, random_state=seed).as_matrix().reshape(n, 9).copy()
+
+
+# ---------------------------------------------------------------- neural pair Jastrow: data only
+@dataclass
+class NeuralSpec:
+    """Shape of the neural pair term of the Jastrow factor (data only).
+
+    Channels: 0 = electron pairs of equal spin, 1 = opposite spins,
+    2 + s = electron-nucleus pairs of nucleus species s (``species[I]`` per
+    nucleus). The network reads the radial features r^2/(r^2 + ell_k^2) and
+    a one-hot channel code; ``r_cut`` per channel ends the term smoothly;
+    the lattice projection interpolates it on ``n_cells`` cells per channel.
+    Parameters are a flat float32 vector: W1 [hidden][n_in], b1 [hidden],
+    W2 [hidden][hidden], b2 [hidden], w3 [hidden], b3 [1]."""
+
+    ell: tuple
+    r_cut: tuple
+    species: tuple
+    hidden: int = 64
+    n_cells: int = 512
+
+    @property
+    def n_ch(self) -> int:
+        return len(self.r_cut)
+
+    @property
+    def n_in(self) -> int:
+        return len(self.ell) + self.n_ch
+
+    @property
+    def n_params(self) -> int:
+        H, D = self.hidden, self.n_in
+        return H * D + H + H * H + H + H + 1
+
+
+def default_neural_spec(system: System, n_cells: int = 512) -> NeuralSpec:
+    """Six feature lengths from 0.5/Z_max to 4 bohr (geometric), e-e terms cut
+    at 6 bohr, e-n terms at 5 bohr; one e-n channel per distinct Z (heaviest
+    first)."""
+    Zs = sorted({float(z) for z in system.Z}, reverse=True)
+    species = tuple(Zs.index(float(z)) for z in system.Z)
+    lo, hi = 0.5 / Zs[0], 4.0
+    ell = tuple(float(lo * (hi / lo) ** (k / 5.0)) for k in range(6))
+    r_cut = (6.0, 6.0) + tuple(5.0 for _ in Zs)
+    return NeuralSpec(ell=ell, r_cut=r_cut, species=species, n_cells=n_cells)
+
+
+def neural_init(spec: NeuralSpec, seed: int, out_scale: float = 0.0) -> np.ndarray:
+    """Seeded initial parameters (float32): W1 ~ N(0, 1/n_in), W2 ~ N(0, 1/hidden),
+    biases 0, w3 ~ out_scale * N(0, 1/hidden) (0: the term starts at zero)."""
+    rng = np.random.default_rng(seed)
+    H, D = spec.hidden, spec.n_in
+    parts = [rng.normal(size=H * D) / np.sqrt(D), np.zeros(H), rng.normal(size=H * H) / np.sqrt(H), np.zeros(H),
+             out_scale * rng.normal(size=H) / np.sqrt(H), np.zeros(1)]
+    return np.concatenate(parts).astype(np.float32)

@@ -76,6 +76,10 @@ def lib():
         L.orc_local_energy.argtypes = [vp, vp, vp, vp]
         L.orc_sm_update.restype = i
         L.orc_sm_update.argtypes = [vp, i, vp, i, vp, vp]
+        L.orc_grad_log_psi.argtypes = [vp, vp, vp, vp, vp]
+        L.orc_system_set_neural.restype = i
+        L.orc_system_set_neural.argtypes = [vp, i, i, vp, vp, vp]
+        L.orc_neural_pair.argtypes = [vp, i, d, vp, vp, vp]
         L.orc_n_candidates.restype = i
         L.orc_n_candidates.argtypes = [vp, i]
         L.orc_p.restype = d
@@ -256,6 +260,35 @@ class OracleSystem:
         if Au is None:
             Au, Ad = self.inverses(x)
         return lib().orc_local_energy(self.h, _p(_f64(x)), _p(Au), _p(Ad))
+
+    def grad_log_psi(self, x, Au=None, Ad=None):
+        """grad_i log|psi_G| for every electron, [N][3]."""
+        if Au is None:
+            Au, Ad = self.inverses(x)
+        g = np.zeros((self.N, 3))
+        lib().orc_grad_log_psi(self.h, _p(_f64(x)), _p(Au), _p(Ad), _p(g))
+        return g
+
+    def set_neural(self, table):
+        """Install (or, with None, remove) the tabulated neural pair term:
+        ``table`` is an oracle.neural.Table."""
+        if table is None:
+            rc = lib().orc_system_set_neural(self.h, 0, 0, None, None, None)
+            self._nj = None
+        else:
+            rcut = _f64(table.r_cut)
+            species = np.ascontiguousarray(table.species, dtype=np.int32)
+            nodes = _f64(table.nodes)
+            self._nj = (rcut, species, nodes)
+            rc = lib().orc_system_set_neural(self.h, len(rcut), table.n_cells, _p(rcut), _p(species), _p(nodes))
+        if rc:
+            raise ValueError("oracle rejected the neural table")
+        return self
+
+    def neural_pair(self, channel, r):
+        g, g1, g2 = ct.c_double(), ct.c_double(), ct.c_double()
+        lib().orc_neural_pair(self.h, channel, float(r), ct.byref(g), ct.byref(g1), ct.byref(g2))
+        return g.value, g1.value, g2.value
 
     def sm_update(self, spin, Ainv, l, r_new):
         A = np.ascontiguousarray(Ainv, dtype=np.float64).copy()

@@ -216,6 +216,11 @@ struct orc_system {
   double b_ee, c_par, c_anti, en_b2;
   double en_b1[ORC_MAX_NUC];
   int ee_on;
+  /* optional neural pair term (section 3b) */
+  int nj_ch, nj_cells;
+  double nj_rcut[ORC_NJ_MAX_CH];
+  int nj_species[ORC_MAX_NUC];
+  double* nj_nodes; /* [ch][cells + 1][3]: g, g', g'' at the nodes, or NULL */
 };
 
 orc_system* orc_system_create(int n_nuc, const double* nuc_xyz, const double* Z,
@@ -268,6 +273,7 @@ orc_system* orc_system_create(int n_nuc, const double* nuc_xyz, const double* Z,
 void orc_system_destroy(orc_system* s)
 {
   if (!s) return;
+  free(s->nj_nodes);
   free(s->sh_center); free(s->sh_l); free(s->sh_kind); free(s->sh_nprim);
   free(s->sh_neff); free(s->sh_zeta); free(s->prim_alpha); free(s->prim_coef);
   free(s->C); free(s);
@@ -404,15 +410,121 @@ static int lu_inverse(int n, const double* A_in, double* Ainv, double* log_abs, 
   return rc;
 }
 
-/* Pade pair functions of the Jastrow factor, u(r) = c r / (1 + b r). */
+/* =========================================================================
+ * 3b. Optional neural pair term of the Jastrow factor.
+ *
+ * J_NN(x) = sum_{i<j} g_{c(i,j)}(r_ij) + sum_{i,I} g_{2+species(I)}(r_iI),
+ * channel 0 for equal-spin electron pairs, 1 for opposite spins, 2+s for the
+ * electron-nucleus pairs of nucleus species s. Each g_c is the quintic
+ * Hermite interpolant of a radial network on the nodes
+ * r_k = r_cut (k/n)^2, k = 0..n: in cell k, with t = (r - r_k)/w_k and
+ * w_k = r_{k+1} - r_k, it is the degree-5 polynomial that takes the node
+ * values g, w g', w^2 g'' at t = 0 and t = 1 (so g is twice continuously
+ * differentiable); g = 0 for r >= r_cut. The node data come from the
+ * network (oracle/neural.py); this file only interpolates.
+ * ========================================================================= */
+int orc_system_set_neural(orc_system* s, int n_ch, int n_cells, const double* r_cut,
+                          const int* species, const double* nodes)
+{
+  free(s->nj_nodes);
+  s->nj_nodes = NULL;
+  s->nj_ch = 0;
+  if (n_ch == 0) return 0;
+  if (n_ch < 2 || n_ch > ORC_NJ_MAX_CH || n_cells < 1) return 1;
+  for (int I = 0; I < s->n_nuc; ++I)
+    if (species[I] < 0 || 2 + species[I] >= n_ch) return 1;
+  for (int c = 0; c < n_ch; ++c)
+    if (!(r_cut[c] > 0.0)) return 1;
+  s->nj_ch = n_ch;
+  s->nj_cells = n_cells;
+  for (int c = 0; c < n_ch; ++c) s->nj_rcut[c] = r_cut[c];
+  for (int I = 0; I < s->n_nuc; ++I) s->nj_species[I] = species[I];
+  size_t len = (size_t)n_ch * (n_cells + 1) * 3;
+  s->nj_nodes = (double*)malloc(sizeof(double) * len);
+  memcpy(s->nj_nodes, nodes, sizeof(double) * len);
+  return 0;
+}
+
+/* g_c(r), g_c'(r), g_c''(r) by the quintic Hermite basis on [0, 1]:
+ *   H0 = 1 - 10t^3 + 15t^4 - 6t^5   (value at 0)
+ *   H1 = t - 6t^3 + 8t^4 - 3t^5     (first derivative at 0)
+ *   H2 = (t^2 - 3t^3 + 3t^4 - t^5)/2 (second derivative at 0)
+ *   H3 = 10t^3 - 15t^4 + 6t^5       (value at 1)
+ *   H4 = -4t^3 + 7t^4 - 3t^5        (first derivative at 1)
+ *   H5 = (t^3 - 2t^4 + t^5)/2       (second derivative at 1) */
+void orc_neural_pair(const orc_system* s, int c, double r, double* g, double* g1, double* g2)
+{
+  *g = 0.0; *g1 = 0.0; *g2 = 0.0;
+  if (!s->nj_nodes || c < 0 || c >= s->nj_ch) return;
+  const double rc = s->nj_rcut[c];
+  const int n = s->nj_cells;
+  if (!(r < rc)) return;
+  int k = (int)floor(sqrt(r / rc) * n);
+  if (k < 0) k = 0;
+  if (k > n - 1) k = n - 1;
+  double r0 = rc * ((double)k / n) * ((double)k / n);
+  double r1 = rc * ((double)(k + 1) / n) * ((double)(k + 1) / n);
+  double w = r1 - r0, t = (r - r0) / w;
+  const double* A = &s->nj_nodes[((size_t)c * (n + 1) + k) * 3];
+  const double* B = A + 3;
+  double f[6] = {A[0], w * A[1], w * w * A[2], B[0], w * B[1], w * w * B[2]};
+  double t2 = t * t, t3 = t2 * t, t4 = t3 * t, t5 = t4 * t;
+  double H[6] = {1 - 10 * t3 + 15 * t4 - 6 * t5, t - 6 * t3 + 8 * t4 - 3 * t5,
+                 0.5 * (t2 - 3 * t3 + 3 * t4 - t5), 10 * t3 - 15 * t4 + 6 * t5,
+                 -4 * t3 + 7 * t4 - 3 * t5, 0.5 * (t3 - 2 * t4 + t5)};
+  double D1[6] = {-30 * t2 + 60 * t3 - 30 * t4, 1 - 18 * t2 + 32 * t3 - 15 * t4,
+                  0.5 * (2 * t - 9 * t2 + 12 * t3 - 5 * t4), 30 * t2 - 60 * t3 + 30 * t4,
+                  -12 * t2 + 28 * t3 - 15 * t4, 0.5 * (3 * t2 - 8 * t3 + 5 * t4)};
+  double D2[6] = {-60 * t + 180 * t2 - 120 * t3, -36 * t + 96 * t2 - 60 * t3,
+                  0.5 * (2 - 18 * t + 36 * t2 - 20 * t3), 60 * t - 180 * t2 + 120 * t3,
+                  -24 * t + 84 * t2 - 60 * t3, 0.5 * (6 * t - 24 * t2 + 20 * t3)};
+  double v = 0.0, d1 = 0.0, d2 = 0.0;
+  for (int q = 0; q < 6; ++q) { v += f[q] * H[q]; d1 += f[q] * D1[q]; d2 += f[q] * D2[q]; }
+  *g = v;
+  *g1 = d1 / w;
+  *g2 = d2 / (w * w);
+}
+
+/* Pade pair functions of the Jastrow factor, u(r) = c r / (1 + b r), plus
+ * the neural pair term when one is set. pair_ee / pair_en return u, du/dr
+ * and d2u/dr2. */
+static void pair_ee(const orc_system* s, int i, int j, double r, double* u, double* u1, double* u2)
+{
+  int same = spin_of(s, i) == spin_of(s, j);
+  double c = same ? s->c_par : s->c_anti;
+  double den = 1.0 + s->b_ee * r;
+  *u = c * r / den;
+  *u1 = c / (den * den);
+  *u2 = -2.0 * s->b_ee * c / (den * den * den);
+  if (s->nj_nodes) {
+    double g, g1, g2;
+    orc_neural_pair(s, same ? 0 : 1, r, &g, &g1, &g2);
+    *u += g; *u1 += g1; *u2 += g2;
+  }
+}
+static void pair_en(const orc_system* s, int I, double r, double* u, double* u1, double* u2)
+{
+  double den = 1.0 + s->en_b2 * r;
+  *u = -s->en_b1[I] * r / den;
+  *u1 = -s->en_b1[I] / (den * den);
+  *u2 = 2.0 * s->en_b2 * s->en_b1[I] / (den * den * den);
+  if (s->nj_nodes) {
+    double g, g1, g2;
+    orc_neural_pair(s, 2 + s->nj_species[I], r, &g, &g1, &g2);
+    *u += g; *u1 += g1; *u2 += g2;
+  }
+}
 static double u_ee(const orc_system* s, int i, int j, double r)
 {
-  double c = (spin_of(s, i) == spin_of(s, j)) ? s->c_par : s->c_anti;
-  return c * r / (1.0 + s->b_ee * r);
+  double u, u1, u2;
+  pair_ee(s, i, j, r, &u, &u1, &u2);
+  return u;
 }
 static double u_en(const orc_system* s, int I, double r)
 {
-  return -s->en_b1[I] * r / (1.0 + s->en_b2 * r);
+  double u, u1, u2;
+  pair_en(s, I, r, &u, &u1, &u2);
+  return u;
 }
 static double dist(const double* p, const double* q)
 {
@@ -471,8 +583,9 @@ int orc_inverses(const orc_system* s, const double* x, double* Ainv_up, double* 
  *                               + lap_i J + |grad_i J|^2 ],
  * with grad_i D/D = sum_m grad phi_m(r_i) Ainv[m][l_i] (same for lap), and
  * V = sum_{i<j} 1/r_ij - sum_{i,I} Z_I / r_iI + sum_{I<J} Z_I Z_J / R_IJ. */
-void orc_laplacian_terms(const orc_system* s, const double* x, const double* Ainv_up,
-                         const double* Ainv_dn, double* lap_over_psi, double* V_out)
+static void laplacian_terms(const orc_system* s, const double* x, const double* Ainv_up,
+                            const double* Ainv_dn, double* lap_over_psi, double* V_out,
+                            double* grad_log_psi)
 {
   const int nao = s->n_ao;
   double* chi = (double*)malloc(sizeof(double) * nao);
@@ -500,22 +613,23 @@ void orc_laplacian_terms(const orc_system* s, const double* x, const double* Ain
     double gJ[3] = {0, 0, 0}, lJ = 0.0;
     for (int j = 0; j < s->N; ++j) {
       if (j == i) continue;
-      double c = (spin_of(s, i) == spin_of(s, j)) ? s->c_par : s->c_anti;
       double r = dist(&x[3 * i], &x[3 * j]);
-      double den = 1.0 + s->b_ee * r;
-      double u1 = c / (den * den), u2 = -2.0 * s->b_ee * c / (den * den * den);
+      double u, u1, u2;
+      pair_ee(s, i, j, r, &u, &u1, &u2);
       for (int k = 0; k < 3; ++k) gJ[k] += u1 * (x[3 * i + k] - x[3 * j + k]) / r;
       lJ += u2 + 2.0 * u1 / r;
       if (j > i && s->ee_on) V += 1.0 / r;
     }
     for (int I = 0; I < s->n_nuc; ++I) {
       double r = dist(&x[3 * i], s->R[I]);
-      double den = 1.0 + s->en_b2 * r;
-      double u1 = -s->en_b1[I] / (den * den), u2 = 2.0 * s->en_b2 * s->en_b1[I] / (den * den * den);
+      double u, u1, u2;
+      pair_en(s, I, r, &u, &u1, &u2);
       for (int k = 0; k < 3; ++k) gJ[k] += u1 * (x[3 * i + k] - s->R[I][k]) / r;
       lJ += u2 + 2.0 * u1 / r;
       V -= s->Z[I] / r;
     }
+    if (grad_log_psi)
+      for (int k = 0; k < 3; ++k) grad_log_psi[3 * i + k] = gD[k] + gJ[k];
     total += lD + 2.0 * (gD[0] * gJ[0] + gD[1] * gJ[1] + gD[2] * gJ[2]) + lJ
              + gJ[0] * gJ[0] + gJ[1] * gJ[1] + gJ[2] * gJ[2];
   }
@@ -524,6 +638,20 @@ void orc_laplacian_terms(const orc_system* s, const double* x, const double* Ain
   free(chi); free(g); free(lp);
   *lap_over_psi = total;
   *V_out = V;
+}
+
+void orc_laplacian_terms(const orc_system* s, const double* x, const double* Ainv_up,
+                         const double* Ainv_dn, double* lap_over_psi, double* V_out)
+{
+  laplacian_terms(s, x, Ainv_up, Ainv_dn, lap_over_psi, V_out, NULL);
+}
+
+/* grad_i log|psi_G(x)| = grad_i D/D + grad_i J for every electron ([N][3]). */
+void orc_grad_log_psi(const orc_system* s, const double* x, const double* Ainv_up,
+                      const double* Ainv_dn, double* grad)
+{
+  double lap, V;
+  laplacian_terms(s, x, Ainv_up, Ainv_dn, &lap, &V, grad);
 }
 
 /* E_L(x) = -1/2 lap psi_G / psi_G + V(x). The lattice-regularized local

@@ -30,6 +30,7 @@ extern "C" {
 
 #define ORC_MAX_NUC 16
 #define ORC_MAX_PRIM 16
+#define ORC_NJ_MAX_CH 8
 
 /* ---- parameters of the double grid (Eq. 2-10, S-12..S-14) ---- */
 double orc_rc_this_work(double a, double Z, double beta, double kappa);
@@ -66,6 +67,15 @@ void   orc_laplacian_terms(const orc_system* s, const double* x, const double* A
                            const double* Ainv_dn, double* lap_over_psi, double* V);
 double orc_local_energy(const orc_system* s, const double* x, const double* Ainv_up,
                         const double* Ainv_dn);
+void   orc_grad_log_psi(const orc_system* s, const double* x, const double* Ainv_up,
+                        const double* Ainv_dn, double* grad /*[N][3]*/);
+
+/* ---- optional neural pair term (tabulated, quintic Hermite) ---- */
+int    orc_system_set_neural(orc_system* s, int n_ch, int n_cells, const double* r_cut,
+                             const int* species /*[n_nuc]*/,
+                             const double* nodes /*[n_ch][n_cells+1][3]*/);
+void   orc_neural_pair(const orc_system* s, int channel, double r, double* g, double* g1,
+                       double* g2);
 int    orc_sm_update(const orc_system* s, int spin, double* Ainv, int l,
                      const double r_new[3], double* ratio);
 
