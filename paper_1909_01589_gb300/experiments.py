@@ -110,6 +110,49 @@ def single_vs_double(names=("He", "Ne", "Ar", "Kr"), alpha=3.5, steps=1000, equi
     return rows
 
 
+def summarize(rows):
+    """Derived quantities of the Fig. 2 analogue: GPU seconds per walker per
+    unit of projection time (single grid, this work's double grid, the
+    previous double grid), their ratio (the acceleration at equal projection
+    time, which equals the acceleration at fixed error when the variance per
+    unit projection time is the same for both lattices), and the exponents
+    x of a least-squares fit cost ~ Z^x over the systems."""
+    out = []
+    for r in rows:
+        W, tau = r["walkers"], r["tau"]
+        cost = {k: r[k]["seconds"] / (W * r[k]["intervals"] * tau)
+                for k in ("single", "double_this_work", "double_previous")}
+        out.append({"system": r["system"], "Z": r["Z"], "cost": cost,
+                    "acceleration_time": cost["single"] / cost["double_this_work"],
+                    "acceleration_jumps": r["double_this_work_acceleration_jumps"]})
+    fit = {}
+    if len(out) >= 2:
+        lz = np.log([o["Z"] for o in out])
+        for k in ("single", "double_this_work", "double_previous"):
+            fit[k] = float(np.polyfit(lz, np.log([o["cost"][k] for o in out]), 1)[0])
+    return out, fit
+
+
+def markdown(rows):
+    derived, fit = summarize(rows)
+    lines = ["| system | Z | a | a'/a | E single (Ha) | bias this work (mHa) | bias previous (mHa) | "
+             "jumps single/double | GPU time single/double | efficiency ratio |",
+             "|---|---|---|---|---|---|---|---|---|---|"]
+    for r, d in zip(rows, derived):
+        lines.append(
+            f"| {r['system']} | {r['Z']:.0f} | {r['a']:.5f} | {r['aprime_over_a']:.3f} | "
+            f"{r['single']['energy']:.4f} ({1e3 * r['single']['error']:.1f} mHa) | "
+            f"{r['double_this_work_bias_mHa']:+.1f} ({r['double_this_work_bias_err_mHa']:.1f}) | "
+            f"{r['double_previous_bias_mHa']:+.1f} ({r['double_previous_bias_err_mHa']:.1f}) | "
+            f"{d['acceleration_jumps']:.2f} | {d['acceleration_time']:.2f} | "
+            f"{r['double_this_work_acceleration_efficiency']:.2f} |")
+    if fit:
+        lines.append("")
+        lines.append("GPU cost per walker per unit projection time ~ Z^x: " +
+                     ", ".join(f"{k} x = {v:.2f}" for k, v in fit.items()))
+    return "\n".join(lines)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--systems", default="He,Ne,Ar,Kr")
@@ -117,7 +160,15 @@ def main():
     ap.add_argument("--equil", type=int, default=200)
     ap.add_argument("--alpha", type=float, default=3.5)
     ap.add_argument("--out", default="results/single_vs_double.json")
+    ap.add_argument("--summarize", nargs="*", help="only write the markdown table of these result files")
     args = ap.parse_args()
+    if args.summarize:
+        rows = []
+        for f in args.summarize:
+            rows += json.load(open(f))
+        rows.sort(key=lambda r: r["Z"])
+        print(markdown(rows))
+        return
     rows = single_vs_double(args.systems.split(","), args.alpha, args.steps, args.equil)
     os.makedirs(os.path.dirname(args.out) or ".", exist_ok=True)
     json.dump(rows, open(args.out, "w"), indent=1)
