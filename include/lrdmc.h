@@ -252,6 +252,86 @@ LRDMC_API lrdmc_status lrdmc_kernel_times(lrdmc_system_t sys, double* interval_m
                                           long long* interval_launches, long long* reconfig_launches,
                                           int reset);
 
+/* -------------------------------------------------------------------------
+ * Neural pair term of the Jastrow factor. The paper's guiding functions are
+ * fixed (JSD/JAGP); this term is an addition that leaves the lattice method
+ * itself unchanged, because the lattice Laplacian needs only values of
+ * psi_G at the displaced points:
+ *   J_NN(x) = sum_{i<j} g_{c(i,j)}(r_ij) + sum_{i,I} g_{2+species[I]}(r_iI),
+ * channel c = 0 for equal-spin electron pairs, 1 for opposite spins,
+ * 2 + s for an electron with a nucleus of species s;
+ *   g_c(r) = m(r, c) s(r / r_cut[c]),  s(t) = 1 - 10t^3 + 15t^4 - 6t^5 (t < 1), 0 beyond,
+ *   m = w3 . silu(W2 silu(W1 z + b1) + b2) + b3,
+ *   z = [r^2 / (r^2 + ell_k^2) for k < n_feat, one-hot(c)].
+ * Every feature is flat at r = 0 and s'(0) = 0, so g'(0) = 0: the Pade
+ * factor keeps the cusp conditions. Parameters are one float32 vector,
+ * row-major: W1 [hidden][n_feat + n_ch], b1 [hidden], W2 [hidden][hidden],
+ * b2 [hidden], w3 [hidden], b3 [1]. With bf16 = 1 every parameter enters
+ * as its bfloat16 rounding (to nearest, ties to even).
+ * ---------------------------------------------------------------------- */
+#define LRDMC_NJ_MAX_CH 8
+#define LRDMC_NJ_MAX_FEAT 12
+#define LRDMC_NJ_HIDDEN 64
+#define LRDMC_NJ_MAX_CELLS 8192
+typedef struct {
+  int n_feat;           /* 1..LRDMC_NJ_MAX_FEAT                          */
+  const double* ell;    /* [n_feat] feature lengths (bohr, > 0)          */
+  int n_ch;             /* 2 + number of nucleus species, <= LRDMC_NJ_MAX_CH */
+  const double* r_cut;  /* [n_ch] cut-off radius per channel (bohr, > 0) */
+  const int* species;   /* [n_nuc] species of every nucleus, 0..n_ch-3   */
+  int hidden;           /* must equal LRDMC_NJ_HIDDEN                    */
+  int bf16;             /* 1: bfloat16-rounded parameters                */
+  int n_cells;          /* table cells per channel, 1..LRDMC_NJ_MAX_CELLS */
+} lrdmc_nj_spec;
+
+/* Number of parameters of a spec (0 for an invalid spec). */
+LRDMC_API int lrdmc_nj_n_params(const lrdmc_nj_spec* spec);
+
+/* Installs the term in the projection and in every evaluation (params:
+ * host float32, copied); spec = NULL removes it. The projection uses the
+ * quintic Hermite interpolant of each g_c on the nodes r_k = r_cut (k/n)^2,
+ * k = 0..n (n = n_cells): the node values g, g', g'' are computed here, in
+ * IEEE double, from the parameters, and each cell holds the degree-5
+ * polynomial that matches them at both ends, so the term is twice
+ * continuously differentiable and the local energy stays continuous.
+ * Host work plus one upload of 128 n_ch n_cells bytes; synchronous. Takes
+ * effect at the next step or evaluation (a cached evaluation of the
+ * population is recomputed). */
+LRDMC_API lrdmc_status lrdmc_set_neural_jastrow(lrdmc_system_t sys, const lrdmc_nj_spec* spec,
+                                                const float* params);
+
+/* Base terms of the variance objective, in IEEE double: for every
+ * configuration x [n][N][3] (device), grad_out [n][N][3] = grad_i log|psi_G|
+ * and e_out [n] = E_L of the trial function WITHOUT the neural term
+ * (whether or not one is installed). Device outputs; synchronises the
+ * stream; LRDMC_ERR_SINGULAR for a singular configuration. */
+LRDMC_API lrdmc_status lrdmc_base_terms(lrdmc_system_t sys, int n, const double* x, double* grad_out,
+                                        double* e_out, void* stream);
+
+/* Training forward pass, FP32 arithmetic, the network's exact radial
+ * derivatives (no table). For every configuration x [n][N][3] with base
+ * terms grad_base [n][N][3], e_base [n] (from lrdmc_base_terms):
+ *   E_L = e_base - 1/2 sum_i [2 a_i . G_i + |G_i|^2 + L_i],  J = J_NN(x),
+ * a_i = grad_base_i, G_i = grad_i J_NN, L_i = lap_i J_NN. Writes el_out [n],
+ * j_out [n] and q_out [n][N][3] = a + G (float32; lrdmc_nj_backward reads
+ * it) and pair_out [n][n_pairs][3] = g, g', g'' of every pair
+ * (n_pairs = N(N-1)/2 + N n_nuc, electron pairs i < j first, row-major,
+ * then electron-nucleus pairs i-major). params: device float32. All
+ * pointers device; asynchronous on stream. */
+LRDMC_API lrdmc_status lrdmc_nj_forward(lrdmc_system_t sys, const lrdmc_nj_spec* spec, const float* params,
+                                        int n, const double* x, const double* grad_base,
+                                        const double* e_base, float* el_out, float* j_out, float* q_out,
+                                        float* pair_out, void* stream);
+
+/* Training backward pass: grad_out (float32 [n_params], overwritten) =
+ * d/dparams of sum_x (d_el[x] E_L(x) + d_j[x] J(x)), from the q of the
+ * matching forward call; derivatives are taken with respect to the values
+ * the network computes with (the bfloat16 roundings when spec->bf16).
+ * All pointers device; asynchronous on stream. */
+LRDMC_API lrdmc_status lrdmc_nj_backward(lrdmc_system_t sys, const lrdmc_nj_spec* spec, const float* params,
+                                         int n, const double* x, const float* q, const float* d_el,
+                                         const float* d_j, float* grad_out, void* stream);
+
 /* Last error message of the system (static string if sys is NULL). */
 LRDMC_API const char* lrdmc_last_error(lrdmc_system_t sys);
 

@@ -33,8 +33,10 @@ EXPORTED = [
     "lrdmc_step", "lrdmc_sync", "lrdmc_get_energy_trace", "lrdmc_get_walkers", "lrdmc_moves", "lrdmc_evaluate",
     "lrdmc_evaluate_static",
     "lrdmc_save", "lrdmc_load", "lrdmc_set_precision", "lrdmc_set_profiling", "lrdmc_kernel_times", "lrdmc_last_error",
-    "lrdmc_destroy",
+    "lrdmc_destroy", "lrdmc_nj_n_params", "lrdmc_set_neural_jastrow", "lrdmc_base_terms", "lrdmc_nj_forward",
+    "lrdmc_nj_backward",
 ]
+NJ_MAX_CH, NJ_MAX_FEAT, NJ_HIDDEN, NJ_MAX_CELLS = 8, 12, 64, 8192
 
 
 class LrdmcError(RuntimeError):
@@ -57,6 +59,23 @@ class _Jastrow(ct.Structure):
 class _Spacing(ct.Structure):
     _fields_ = [("kind", ct.c_int), ("beta", ct.c_double), ("kappa", ct.c_double),
                 ("rc", ct.c_double), ("aprime_over_a", ct.c_double)]
+
+
+class _NjSpec(ct.Structure):
+    _fields_ = [("n_feat", ct.c_int), ("ell", ct.c_void_p), ("n_ch", ct.c_int), ("r_cut", ct.c_void_p),
+                ("species", ct.c_void_p), ("hidden", ct.c_int), ("bf16", ct.c_int), ("n_cells", ct.c_int)]
+
+
+def _nj_spec(spec, bf16):
+    """ctypes image of a neural-term spec (any object with ell, r_cut,
+    species, hidden, n_cells); the arrays are kept alive on the result."""
+    ell = np.ascontiguousarray(spec.ell, dtype=np.float64)
+    rcut = np.ascontiguousarray(spec.r_cut, dtype=np.float64)
+    species = np.ascontiguousarray(spec.species, dtype=np.int32)
+    c = _NjSpec(len(ell), _np_ptr(ell), len(rcut), _np_ptr(rcut), _np_ptr(species), int(spec.hidden), int(bool(bf16)),
+                int(spec.n_cells))
+    c._keep = (ell, rcut, species)
+    return c
 
 
 @dataclass(frozen=True)
@@ -122,6 +141,16 @@ def load_library():
     L.lrdmc_last_error.argtypes = [vp]
     L.lrdmc_destroy.restype = None
     L.lrdmc_destroy.argtypes = [vp]
+    L.lrdmc_nj_n_params.restype = i
+    L.lrdmc_nj_n_params.argtypes = [vp]
+    L.lrdmc_set_neural_jastrow.restype = i
+    L.lrdmc_set_neural_jastrow.argtypes = [vp, vp, vp]
+    L.lrdmc_base_terms.restype = i
+    L.lrdmc_base_terms.argtypes = [vp, i, vp, vp, vp, vp]
+    L.lrdmc_nj_forward.restype = i
+    L.lrdmc_nj_forward.argtypes = [vp, vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.lrdmc_nj_backward.restype = i
+    L.lrdmc_nj_backward.argtypes = [vp, vp, vp, i, vp, vp, vp, vp, vp, vp]
     _lib = L
     return L
 
@@ -328,6 +357,78 @@ class LrdmcSystem:
                                                   _t_ptr(ratio), _t_ptr(T), _t_ptr(b), _t_ptr(el),
                                                   ct.c_void_p(stream.cuda_stream)))
         return ratio, T, b, el
+
+
+    # ---------------------------------------------------------------- neural pair term
+    def set_neural_jastrow(self, spec, params, bf16=True):
+        """Install the neural pair term (params: float32 array or tensor of
+        lrdmc_nj_n_params entries) in the projection and every evaluation;
+        ``spec=None`` removes it."""
+        if spec is None:
+            self._check(load_library().lrdmc_set_neural_jastrow(self.h, None, None))
+            return self
+        p = np.ascontiguousarray(params.detach().cpu().numpy() if hasattr(params, "detach") else params,
+                                 dtype=np.float32)
+        c = _nj_spec(spec, bf16)
+        self._check(load_library().lrdmc_set_neural_jastrow(self.h, ct.byref(c), _np_ptr(p)))
+        return self
+
+    def nj_n_params(self, spec):
+        return load_library().lrdmc_nj_n_params(ct.byref(_nj_spec(spec, True)))
+
+    def base_terms(self, x, stream=None):
+        """grad_i log|psi_G| [n][N][3] and E_L [n] without the neural term, in
+        FP64, for configurations x [n][N][3] (float64 CUDA tensor)."""
+        import torch
+
+        x = x.contiguous()
+        n = int(x.shape[0])
+        grad = torch.empty((n, self.N, 3), dtype=torch.float64, device=x.device)
+        e = torch.empty(n, dtype=torch.float64, device=x.device)
+        if stream is None:
+            stream = torch.cuda.current_stream(x.device)
+        self._check(load_library().lrdmc_base_terms(self.h, n, _t_ptr(x), _t_ptr(grad), _t_ptr(e),
+                                                    ct.c_void_p(stream.cuda_stream)))
+        return grad, e
+
+    def nj_forward(self, spec, params, x, grad_base, e_base, bf16=True, stream=None):
+        """Training forward pass (FP32): E_L [n], J_NN [n], q = a + G [n][N][3]
+        and the pair values [n][n_pairs][3]."""
+        import torch
+
+        n = int(x.shape[0])
+        n_pairs = self.N * (self.N - 1) // 2 + self.N * self.sys.n_nuc
+        dev = x.device
+        el = torch.empty(n, dtype=torch.float32, device=dev)
+        j = torch.empty(n, dtype=torch.float32, device=dev)
+        q = torch.empty((n, self.N, 3), dtype=torch.float32, device=dev)
+        pairs = torch.empty((n, n_pairs, 3), dtype=torch.float32, device=dev)
+        if stream is None:
+            stream = torch.cuda.current_stream(dev)
+        c = _nj_spec(spec, bf16)
+        p = params.detach().contiguous()
+        assert p.dtype == torch.float32 and p.is_cuda
+        self._check(load_library().lrdmc_nj_forward(
+            self.h, ct.byref(c), _t_ptr(p), n, _t_ptr(x.contiguous()), _t_ptr(grad_base.contiguous()),
+            _t_ptr(e_base.contiguous()), _t_ptr(el), _t_ptr(j), _t_ptr(q), _t_ptr(pairs),
+            ct.c_void_p(stream.cuda_stream)))
+        return el, j, q, pairs
+
+    def nj_backward(self, spec, params, x, q, d_el, d_j, bf16=True, stream=None):
+        """Gradient of sum(d_el E_L + d_j J_NN) with respect to the parameters
+        (float32 CUDA tensor)."""
+        import torch
+
+        n = int(x.shape[0])
+        p = params.detach().contiguous()
+        grad = torch.empty_like(p)
+        if stream is None:
+            stream = torch.cuda.current_stream(x.device)
+        c = _nj_spec(spec, bf16)
+        self._check(load_library().lrdmc_nj_backward(
+            self.h, ct.byref(c), _t_ptr(p), n, _t_ptr(x.contiguous()), _t_ptr(q.contiguous()),
+            _t_ptr(d_el.contiguous()), _t_ptr(d_j.contiguous()), _t_ptr(grad), ct.c_void_p(stream.cuda_stream)))
+        return grad
 
 
 def create_system(system) -> LrdmcSystem:

@@ -45,6 +45,10 @@ struct lrdmc_system_s {
   double t_interval_ms = 0.0, t_reconfig_ms = 0.0;
   long long n_interval = 0, n_reconfig = 0;
   std::string last_error;
+  // neural pair term (lrdmc_set_neural_jastrow)
+  double* nj_tab = nullptr;
+  df* nj_tab_df = nullptr;
+  int* base_err = nullptr;
 };
 
 static const char* g_static_error = "";
@@ -806,6 +810,159 @@ lrdmc_status lrdmc_kernel_times(lrdmc_system_t s, double* interval_ms, double* r
   return LRDMC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Neural pair term.
+// ---------------------------------------------------------------------------
+static bool nj_spec_ok(lrdmc_system_t s, const lrdmc_nj_spec* sp, std::string& why)
+{
+  if (!sp) { why = "spec is NULL"; return false; }
+  if (sp->n_feat < 1 || sp->n_feat > LRDMC_NJ_MAX_FEAT || !sp->ell) { why = "n_feat out of range"; return false; }
+  for (int f = 0; f < sp->n_feat; ++f)
+    if (!(sp->ell[f] > 0.0) || !isfinite(sp->ell[f])) { why = "ell must be positive and finite"; return false; }
+  if (sp->n_ch < 2 || sp->n_ch > LRDMC_NJ_MAX_CH || !sp->r_cut) { why = "n_ch out of range"; return false; }
+  for (int c = 0; c < sp->n_ch; ++c)
+    if (!(sp->r_cut[c] > 0.0) || !isfinite(sp->r_cut[c])) { why = "r_cut must be positive and finite"; return false; }
+  if (!sp->species) { why = "species is NULL"; return false; }
+  for (int I = 0; I < s->S.n_nuc; ++I)
+    if (sp->species[I] < 0 || 2 + sp->species[I] >= sp->n_ch) { why = "species out of range"; return false; }
+  if (sp->hidden != LRDMC_NJ_HIDDEN) { why = "hidden must equal LRDMC_NJ_HIDDEN"; return false; }
+  if (sp->n_cells < 1 || sp->n_cells > LRDMC_NJ_MAX_CELLS) { why = "n_cells out of range"; return false; }
+  return true;
+}
+
+static NjGeom nj_geom(lrdmc_system_t s, const lrdmc_nj_spec* sp)
+{
+  NjGeom G{};
+  G.N = s->S.N;
+  G.n_up = s->S.n_up;
+  G.n_nuc = s->S.n_nuc;
+  G.n_pairs = G.N * (G.N - 1) / 2 + G.N * G.n_nuc;
+  for (int I = 0; I < G.n_nuc; ++I) {
+    for (int k = 0; k < 3; ++k) G.nuc[I][k] = s->S.nuc[I][k];
+    G.species[I] = sp->species[I];
+  }
+  return G;
+}
+
+static NjNetDev nj_net(const lrdmc_nj_spec* sp)
+{
+  NjNetDev N{};
+  N.F = sp->n_feat;
+  N.C = sp->n_ch;
+  N.D = N.F + N.C;
+  N.bf16 = sp->bf16 != 0;
+  for (int f = 0; f < N.F; ++f) N.ell2[f] = (float)(sp->ell[f] * sp->ell[f]);
+  for (int c = 0; c < N.C; ++c) N.rcut[c] = (float)sp->r_cut[c];
+  return N;
+}
+
+int lrdmc_nj_n_params(const lrdmc_nj_spec* sp)
+{
+  if (!sp || sp->n_feat < 1 || sp->n_feat > LRDMC_NJ_MAX_FEAT || sp->n_ch < 2 || sp->n_ch > LRDMC_NJ_MAX_CH ||
+      sp->hidden != LRDMC_NJ_HIDDEN)
+    return 0;
+  return nj_n_params(sp->n_feat, sp->n_ch, sp->hidden);
+}
+
+lrdmc_status lrdmc_set_neural_jastrow(lrdmc_system_t s, const lrdmc_nj_spec* sp, const float* params)
+{
+  if (!s) return fail(s, LRDMC_ERR_ARG, "");
+  if (!sp) {
+    s->S.nj_on = 0;
+    s->have_eval = false;
+    return LRDMC_OK;
+  }
+  std::string why;
+  if (!nj_spec_ok(s, sp, why)) return fail(s, LRDMC_ERR_ARG, "set_neural_jastrow: " + why);
+  if (!params) return fail(s, LRDMC_ERR_ARG, "set_neural_jastrow: params is NULL");
+  const int np = nj_n_params(sp->n_feat, sp->n_ch, sp->hidden);
+  for (int q = 0; q < np; ++q)
+    if (!isfinite(params[q])) return fail(s, LRDMC_ERR_ARG, "set_neural_jastrow: non-finite parameter");
+  std::vector<double> tab;
+  nj_build_table(*sp, params, tab);
+  for (double v : tab)
+    if (!isfinite(v)) return fail(s, LRDMC_ERR_NONFINITE, "set_neural_jastrow: non-finite table entry");
+  std::vector<df> tdf(tab.size());
+  for (size_t q = 0; q < tab.size(); ++q) {
+    const float hi = (float)tab[q];
+    tdf[q] = df_make(hi, (float)(tab[q] - (double)hi));
+  }
+  if (s->nj_tab) cudaFree(s->nj_tab);
+  if (s->nj_tab_df) cudaFree(s->nj_tab_df);
+  s->nj_tab = nullptr;
+  s->nj_tab_df = nullptr;
+  s->S.nj_on = 0;
+  cudaError_t e = cudaMalloc((void**)&s->nj_tab, sizeof(double) * tab.size());
+  if (e == cudaSuccess) e = cudaMalloc((void**)&s->nj_tab_df, sizeof(df) * tdf.size());
+  if (e == cudaSuccess) e = cudaMemcpy(s->nj_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->nj_tab_df, tdf.data(), sizeof(df) * tdf.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(s, e, "set_neural_jastrow upload");
+  s->S.nj_tab = s->nj_tab;
+  s->S.nj_tab_df = s->nj_tab_df;
+  s->S.nj_cells = sp->n_cells;
+  for (int c = 0; c < sp->n_ch; ++c) {
+    s->S.nj_rcut[c] = sp->r_cut[c];
+    s->S.nj_rcut_f[c] = (float)sp->r_cut[c];
+    s->S.nj_scale_f[c] = (float)(sp->n_cells / sqrt(sp->r_cut[c]));
+  }
+  for (int I = 0; I < s->S.n_nuc; ++I) s->S.nj_species[I] = sp->species[I];
+  s->S.nj_on = 1;
+  s->have_eval = false;
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_base_terms(lrdmc_system_t s, int n, const double* x, double* grad_out, double* e_out,
+                              void* stream)
+{
+  if (!s) return fail(s, LRDMC_ERR_ARG, "");
+  if (n < 0 || (n > 0 && (!x || !grad_out || !e_out))) return fail(s, LRDMC_ERR_ARG, "base_terms: bad arguments");
+  if (n == 0) return LRDMC_OK;
+  cudaStream_t cs = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (!s->base_err) e = cudaMalloc((void**)&s->base_err, sizeof(int));
+  if (e == cudaSuccess && !s->err_host) e = cudaMallocHost((void**)&s->err_host, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(s, e, "base_terms error word");
+  SysDev S = s->S;
+  S.nj_on = 0;  // the base terms exclude the neural term
+  e = cudaMemsetAsync(s->base_err, 0, sizeof(int), cs);
+  if (e == cudaSuccess) e = launch_base_terms(S, s->Lo, n, x, grad_out, e_out, s->base_err, cs);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->err_host, s->base_err, sizeof(int), cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  if (e != cudaSuccess) return cuda_fail(s, e, "base_terms");
+  if (*s->err_host & kErrSingular) return fail(s, LRDMC_ERR_SINGULAR, "base_terms: singular Slater matrix");
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_nj_forward(lrdmc_system_t s, const lrdmc_nj_spec* sp, const float* params, int n,
+                              const double* x, const double* grad_base, const double* e_base, float* el_out,
+                              float* j_out, float* q_out, float* pair_out, void* stream)
+{
+  if (!s) return fail(s, LRDMC_ERR_ARG, "");
+  std::string why;
+  if (!nj_spec_ok(s, sp, why)) return fail(s, LRDMC_ERR_ARG, "nj_forward: " + why);
+  if (n < 0 || (n > 0 && (!params || !x || !grad_base || !e_base || !el_out || !j_out || !q_out || !pair_out)))
+    return fail(s, LRDMC_ERR_ARG, "nj_forward: bad arguments");
+  cudaError_t e = launch_nj_forward(nj_geom(s, sp), nj_net(sp), params, n, x, grad_base, e_base, el_out, j_out,
+                                    q_out, pair_out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "nj_forward");
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_nj_backward(lrdmc_system_t s, const lrdmc_nj_spec* sp, const float* params, int n,
+                               const double* x, const float* q, const float* d_el, const float* d_j,
+                               float* grad_out, void* stream)
+{
+  if (!s) return fail(s, LRDMC_ERR_ARG, "");
+  std::string why;
+  if (!nj_spec_ok(s, sp, why)) return fail(s, LRDMC_ERR_ARG, "nj_backward: " + why);
+  if (n < 0 || !grad_out || (n > 0 && (!params || !x || !q || !d_el || !d_j)))
+    return fail(s, LRDMC_ERR_ARG, "nj_backward: bad arguments");
+  cudaError_t e = launch_nj_backward(nj_geom(s, sp), nj_net(sp), params, n, x, q, d_el, d_j, grad_out,
+                                     (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "nj_backward");
+  return LRDMC_OK;
+}
+
 const char* lrdmc_last_error(lrdmc_system_t s) { return s ? s->last_error.c_str() : g_static_error; }
 
 void lrdmc_destroy(lrdmc_system_t s)
@@ -813,6 +970,9 @@ void lrdmc_destroy(lrdmc_system_t s)
   if (!s) return;
   if (s->err_host) cudaFreeHost(s->err_host);
   if (s->eval_err) cudaFree(s->eval_err);
+  if (s->nj_tab) cudaFree(s->nj_tab);
+  if (s->nj_tab_df) cudaFree(s->nj_tab_df);
+  if (s->base_err) cudaFree(s->base_err);
   for (cudaEvent_t ev : s->events) cudaEventDestroy(ev);
   delete s;
 }

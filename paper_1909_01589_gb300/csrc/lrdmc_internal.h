@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/lrdmc.h"
 #include "df64.cuh"
 
@@ -15,6 +17,7 @@ constexpr int kMaxPrim = LRDMC_MAX_PRIM;
 constexpr int kMaxAO = LRDMC_MAX_AO;
 constexpr int kMaxSpin = LRDMC_MAX_SPIN;
 constexpr int kMaxMO = LRDMC_MAX_SPIN;
+constexpr int kMaxNjCh = LRDMC_NJ_MAX_CH;
 constexpr int kWarpsPerBlock = 4;
 constexpr int kMaxItersPerInterval = 1 << 20;
 
@@ -76,7 +79,17 @@ struct SysDev {
   ShellDev sh[kMaxShell];
   double C[kMaxAO * kMaxMO];  // [n_ao][n_mo]
   int precision;  // LRDMC_PRECISION_FP64 or LRDMC_PRECISION_DF64
-  int pad;
+  // neural pair term of the Jastrow factor, tabulated: channel c, cell k
+  // (uniform in sqrt(r) on [0, r_cut_c)) holds r_k, 1/w_k and the
+  // coefficients c_0..c_5 of g_c = sum_q c_q t^q, t = (r - r_k)/w_k
+  int nj_on;
+  int nj_cells;
+  const double* nj_tab;   // [n_ch][nj_cells][8]
+  const df* nj_tab_df;    // the same as double-floats
+  double nj_rcut[kMaxNjCh];
+  float nj_rcut_f[kMaxNjCh];
+  float nj_scale_f[kMaxNjCh];  // nj_cells / sqrt(r_cut_c)
+  int nj_species[kMaxNuc];     // e-n channel of nucleus I is 2 + nj_species[I]
   DfSys D;
 };
 
@@ -136,6 +149,30 @@ cudaError_t launch_reconfig(const PopDev& P, const Layout& Lo, uint64_t k, cudaS
 cudaError_t launch_evaluate(const SysDev& S, const Layout& Lo, const LatDev& L, int n,
                             const double* x, const double* rot, double* ratio, double* T,
                             double* b, double* el, int* err, cudaStream_t st);
+
+// Neural pair term: geometry and network shape for the training kernels.
+struct NjGeom {
+  int N, n_up, n_nuc, n_pairs;  // n_pairs = N(N-1)/2 + N n_nuc
+  double nuc[kMaxNuc][3];
+  int species[kMaxNuc];
+};
+struct NjNetDev {
+  int F, C, D, bf16;  // features, channels, F + C, bfloat16 parameters
+  float ell2[LRDMC_NJ_MAX_FEAT];
+  float rcut[kMaxNjCh];
+};
+
+int nj_n_params(int n_feat, int n_ch, int hidden);
+float nj_bf16(float x);
+void nj_build_table(const lrdmc_nj_spec& spec, const float* params, std::vector<double>& tab);
+cudaError_t launch_nj_forward(const NjGeom& G, const NjNetDev& N, const float* params, int n, const double* x,
+                              const double* grad_base, const double* e_base, float* el, float* j, float* q,
+                              float* pair_out, cudaStream_t st);
+cudaError_t launch_nj_backward(const NjGeom& G, const NjNetDev& N, const float* params, int n, const double* x,
+                               const float* q, const float* d_el, const float* d_j, float* grad, cudaStream_t st);
+
+cudaError_t launch_base_terms(const SysDev& S, const Layout& Lo, int n, const double* x, double* grad,
+                              double* e, int* err, cudaStream_t st);
 
 cudaError_t launch_evaluate_static(const SysDev& S, const Layout& Lo, const LatDev& L, int n,
                                    const double* x, const double* rot, double* ratio, double* T,

@@ -387,6 +387,47 @@ __device__ void ao_values(const SysDev& S, const double* p, double* out)
 // ----------------------------------------------------------------------------
 __device__ __forceinline__ int spin_of(const SysDev& S, int i) { return i < S.n_up ? 0 : 1; }
 
+// Neural pair term, tabulated: the cell of r (uniform in sqrt(r) on
+// [0, r_cut)) holds r_k, 1/w_k and c_0..c_5; g = sum_q c_q t^q with
+// t = (r - r_k)/w_k (Horner), 0 from r_cut on. The cell index is taken in
+// single precision: next to a cell edge either neighbour's polynomial
+// agrees with the other to second order at the edge, so the choice is
+// immaterial.
+__device__ __forceinline__ int nj_ch_ee(const SysDev& S, int i, int j) { return spin_of(S, i) == spin_of(S, j) ? 0 : 1; }
+
+__device__ __forceinline__ const double* nj_cell(const SysDev& S, int c, double r)
+{
+  int k = (int)(sqrtf((float)r) * S.nj_scale_f[c]);
+  k = min(max(k, 0), S.nj_cells - 1);
+  return S.nj_tab + ((size_t)c * S.nj_cells + k) * 8;
+}
+
+__device__ __forceinline__ double nj_value(const SysDev& S, int c, double r)
+{
+  if (!(r < S.nj_rcut[c])) return 0.0;
+  const double* e = nj_cell(S, c, r);
+  const double t = (r - __ldg(e)) * __ldg(e + 1);
+  double v = __ldg(e + 7);
+#pragma unroll
+  for (int q = 6; q >= 2; --q) v = fma(v, t, __ldg(e + q));
+  return v;
+}
+
+__device__ __forceinline__ void nj_value3(const SysDev& S, int c, double r, double& g, double& g1, double& g2)
+{
+  g = 0.0; g1 = 0.0; g2 = 0.0;
+  if (!(r < S.nj_rcut[c])) return;
+  const double* e = nj_cell(S, c, r);
+  const double iw = __ldg(e + 1), t = (r - __ldg(e)) * iw;
+  const double c0 = __ldg(e + 2), c1 = __ldg(e + 3), c2 = __ldg(e + 4), c3 = __ldg(e + 5), c4 = __ldg(e + 6),
+               c5 = __ldg(e + 7);
+  g = c0 + t * (c1 + t * (c2 + t * (c3 + t * (c4 + t * c5))));
+  const double d1 = c1 + t * (2.0 * c2 + t * (3.0 * c3 + t * (4.0 * c4 + t * 5.0 * c5)));
+  const double d2 = 2.0 * c2 + t * (6.0 * c3 + t * (12.0 * c4 + t * 20.0 * c5));
+  g1 = d1 * iw;
+  g2 = d2 * iw * iw;
+}
+
 // sum_{j != i} u_ee(|p - r_j|) + sum_I u_en(|p - R_I|).
 __device__ double jastrow_terms(const SysDev& S, const double* sx, int i, double px, double py,
                                 double pz)
@@ -399,11 +440,13 @@ __device__ double jastrow_terms(const SysDev& S, const double* sx, int i, double
     double r = sqrt(dx * dx + dy * dy + dz * dz);
     double c = (spin_of(S, j) == si) ? S.c_par : S.c_anti;
     acc += c * r / (1.0 + S.b_ee * r);
+    if (S.nj_on) acc += nj_value(S, nj_ch_ee(S, i, j), r);
   }
   for (int I = 0; I < S.n_nuc; ++I) {
     double dx = px - S.nuc[I][0], dy = py - S.nuc[I][1], dz = pz - S.nuc[I][2];
     double r = sqrt(dx * dx + dy * dy + dz * dz);
     acc -= S.en_b1[I] * r / (1.0 + S.en_b2 * r);
+    if (S.nj_on) acc += nj_value(S, 2 + S.nj_species[I], r);
   }
   return acc;
 }
@@ -571,7 +614,8 @@ __device__ bool warp_inverse(const SysDev& S, const double* sC, const double* sx
 // nullable) receives psi_G(x')/psi_G(x) for every move.
 // ----------------------------------------------------------------------------
 __device__ void warp_eval(const SysDev& S, const double* sC, const LatDev& L, const WarpMem& wm,
-                          int lane, double* ratio_out, double& b, double& el)
+                          int lane, double* ratio_out, double& b, double& el, double* grad_out = nullptr,
+                          bool moves = true)
 {
   const int N = S.N, nao = S.n_ao, nu = S.n_up;
   // projected inverse columns: v[i][mu] = sum_m C[mu][m] Ainv_sigma[m][l_i]
@@ -601,9 +645,14 @@ __device__ void warp_eval(const SysDev& S, const double* sC, const LatDev& L, co
       double u1 = c * inv * inv;
       double u2 = -2.0 * S.b_ee * c * inv * inv * inv;
       double ir = 1.0 / r;
+      Ssum += c * r * inv;
+      if (S.nj_on) {
+        double g, g1, g2;
+        nj_value3(S, nj_ch_ee(S, i, j), r, g, g1, g2);
+        u1 += g1; u2 += g2; Ssum += g;
+      }
       gJ[0] += u1 * d0 * ir; gJ[1] += u1 * d1 * ir; gJ[2] += u1 * d2 * ir;
       lJ += u2 + 2.0 * u1 * ir;
-      Ssum += c * r * inv;
       if (j > i && S.ee_on) V += ir;
     }
     for (int I = 0; I < S.n_nuc; ++I) {
@@ -614,18 +663,29 @@ __device__ void warp_eval(const SysDev& S, const double* sC, const LatDev& L, co
       double u1 = -b1 * inv * inv;
       double u2 = 2.0 * S.en_b2 * b1 * inv * inv * inv;
       double ir = 1.0 / r;
+      Ssum -= b1 * r * inv;
+      if (S.nj_on) {
+        double g, g1, g2;
+        nj_value3(S, 2 + S.nj_species[I], r, g, g1, g2);
+        u1 += g1; u2 += g2; Ssum += g;
+      }
       gJ[0] += u1 * d0 * ir; gJ[1] += u1 * d1 * ir; gJ[2] += u1 * d2 * ir;
       lJ += u2 + 2.0 * u1 * ir;
-      Ssum -= b1 * r * inv;
       V -= S.Z[I] * ir;
     }
     wm.Ssum[i] = Ssum;
+    if (grad_out)
+      for (int k = 0; k < 3; ++k) grad_out[3 * i + k] = gD[k] + gJ[k];
     double lap = lD + 2.0 * (gD[0] * gJ[0] + gD[1] * gJ[1] + gD[2] * gJ[2]) + lJ +
                  gJ[0] * gJ[0] + gJ[1] * gJ[1] + gJ[2] * gJ[2];
     part += -0.5 * lap + V;
   }
   el = warp_sum(part) + S.V_nn;
   __syncwarp();
+  if (!moves) {
+    b = 0.0;
+    return;
+  }
   // the P lattice moves: lanes over candidates
   const int G = L.G, per_e = 6 * G, P = N * per_e;
   for (int c = lane; c < P; c += 32) {
@@ -715,6 +775,70 @@ __device__ __forceinline__ int solid_m(int l, const NT d[3], NT Sv[5])
 // Per nucleus I (one distance each): the determinant ratio
 // sum_mu v[mu] chi_mu(p) over the shells centred on I, and the e-n Jastrow
 // -sum_I b1_I r/(1 + b2 r).
+// The neural pair term in NT arithmetic (same table, double-float copy).
+template <class NT>
+__device__ __forceinline__ const df* nj_cell_m(const SysDev& S, int c, float rf)
+{
+  int k = (int)(sqrtf(rf) * S.nj_scale_f[c]);
+  k = min(max(k, 0), S.nj_cells - 1);
+  return S.nj_tab_df + ((size_t)c * S.nj_cells + k) * 8;
+}
+
+__device__ __forceinline__ void nj_load(const df* e, df E[8])
+{
+  const float4* q = reinterpret_cast<const float4*>(e);
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    float4 v = __ldg(q + h);
+    E[2 * h] = df_make(v.x, v.y);
+    E[2 * h + 1] = df_make(v.z, v.w);
+  }
+}
+
+template <class NT>
+__device__ __forceinline__ NT nj_value_m(const SysDev& S, int c, NT r)
+{
+  typedef Ar<NT> A;
+  const float rf = A::approx(r);
+  if (!(rf < S.nj_rcut_f[c])) return A::zero();
+  df E[8];
+  nj_load(nj_cell_m<NT>(S, c, rf), E);
+  const NT t = A::mul(A::sub(r, A::c(E[0])), A::c(E[1]));
+  NT v = A::c(E[7]);
+#pragma unroll
+  for (int q = 6; q >= 2; --q) v = A::add(A::mul(v, t), A::c(E[q]));
+  return v;
+}
+
+template <class NT>
+__device__ __forceinline__ void nj_value3_m(const SysDev& S, int c, NT r, NT& g, NT& g1, NT& g2)
+{
+  typedef Ar<NT> A;
+  g = A::zero(); g1 = A::zero(); g2 = A::zero();
+  const float rf = A::approx(r);
+  if (!(rf < S.nj_rcut_f[c])) return;
+  df E[8];
+  nj_load(nj_cell_m<NT>(S, c, rf), E);
+  const NT iw = A::c(E[1]);
+  const NT t = A::mul(A::sub(r, A::c(E[0])), iw);
+  const NT c1 = A::c(E[3]), c2 = A::c(E[4]), c3 = A::c(E[5]), c4 = A::c(E[6]), c5 = A::c(E[7]);
+  NT v = c5, d1 = A::mul_f(c5, 5.0f), d2 = A::mul_f(c5, 20.0f);
+  v = A::add(A::mul(v, t), c4);
+  v = A::add(A::mul(v, t), c3);
+  v = A::add(A::mul(v, t), c2);
+  v = A::add(A::mul(v, t), c1);
+  g = A::add(A::mul(v, t), A::c(E[2]));
+  d1 = A::add(A::mul(d1, t), A::mul_f(c4, 4.0f));
+  d1 = A::add(A::mul(d1, t), A::mul_f(c3, 3.0f));
+  d1 = A::add(A::mul(d1, t), A::mul_f(c2, 2.0f));
+  d1 = A::add(A::mul(d1, t), c1);
+  d2 = A::add(A::mul(d2, t), A::mul_f(c4, 12.0f));
+  d2 = A::add(A::mul(d2, t), A::mul_f(c3, 6.0f));
+  d2 = A::add(A::mul(d2, t), A::mul_f(c2, 2.0f));
+  g1 = A::mul(d1, iw);
+  g2 = A::mul(d2, A::sqr(iw));
+}
+
 template <class NT>
 __device__ void nucleus_terms_m(const SysDev& S, const df* v, const NT p[3], const BlockMem& bm, NT& rdet, NT& jen)
 {
@@ -728,6 +852,7 @@ __device__ void nucleus_terms_m(const SysDev& S, const df* v, const NT p[3], con
     NT r = A::sqrt(r2);
     if (S.en_b1[I] != 0.0)
       jen = A::sub(jen, A::div(A::mul(A::c(S.D.en_b1[I]), r), A::add_f(A::mul(A::c(S.D.en_b2), r), 1.0f)));
+    if (S.nj_on) jen = A::add(jen, nj_value_m<NT>(S, 2 + S.nj_species[I], r));
     NT e = A::zero();
     for (int q = S.nuc_shell_begin[I]; q < S.nuc_shell_begin[I + 1]; ++q) {
       const ShellDev& sh = S.sh[q];
@@ -755,7 +880,7 @@ template <class NT>
 __device__ NT jastrow_ee_m(const SysDev& S, const df* xd, int i, const NT p[3])
 {
   typedef Ar<NT> A;
-  NT num = A::zero(), den = A::one();
+  NT num = A::zero(), den = A::one(), nn = A::zero();
   const int si = spin_of(S, i);
   const NT b = A::c(S.D.b_ee), cp = A::c(S.D.c_par), ca = A::c(S.D.c_anti);
   for (int j = 0; j < S.N; ++j) {
@@ -767,8 +892,9 @@ __device__ NT jastrow_ee_m(const SysDev& S, const df* xd, int i, const NT p[3])
     NT dj = A::add_f(A::mul(b, r), 1.0f);
     num = A::add_fast(A::mul(num, dj), A::mul(A::mul(c, r), den));
     den = A::mul(den, dj);
+    if (S.nj_on) nn = A::add(nn, nj_value_m<NT>(S, nj_ch_ee(S, i, j), r));
   }
-  return A::div(num, den);
+  return A::add(A::div(num, den), nn);
 }
 
 template <class NT>
@@ -924,13 +1050,18 @@ __device__ void el_parts_m(const SysDev& S, const WarpMem& wm, int i, int part, 
     NT inv2 = A::sqr(inv);
     NT u1 = A::mul(c, inv2);
     NT u2 = A::mul_f(A::mul(A::mul(b, c), A::mul(inv2, inv)), -2.0f);
+    o.S = A::add(o.S, A::mul(A::mul(c, rr), inv));
+    if (S.nj_on) {
+      NT g, g1, g2;
+      nj_value3_m<NT>(S, nj_ch_ee(S, i, j), rr, g, g1, g2);
+      u1 = A::add(u1, g1); u2 = A::add(u2, g2); o.S = A::add(o.S, g);
+    }
     NT irr = A::rcp(rr);
     NT u1ir = A::mul(u1, irr);
     o.gJ[0] = A::add(o.gJ[0], A::mul(u1ir, d0));
     o.gJ[1] = A::add(o.gJ[1], A::mul(u1ir, d1));
     o.gJ[2] = A::add(o.gJ[2], A::mul(u1ir, d2));
     o.lJ = A::add(o.lJ, A::add(u2, A::mul_f(u1ir, 2.0f)));
-    o.S = A::add(o.S, A::mul(A::mul(c, rr), inv));
     if (j > i && S.ee_on) o.V = A::add(o.V, irr);
   }
   // e-n terms
@@ -943,13 +1074,18 @@ __device__ void el_parts_m(const SysDev& S, const WarpMem& wm, int i, int part, 
     NT inv2 = A::sqr(inv);
     NT u1 = A::neg(A::mul(b1, inv2));
     NT u2 = A::mul_f(A::mul(A::mul(b2, b1), A::mul(inv2, inv)), 2.0f);
+    o.S = A::sub(o.S, A::mul(A::mul(b1, rr), inv));
+    if (S.nj_on) {
+      NT g, g1, g2;
+      nj_value3_m<NT>(S, 2 + S.nj_species[I], rr, g, g1, g2);
+      u1 = A::add(u1, g1); u2 = A::add(u2, g2); o.S = A::add(o.S, g);
+    }
     NT irr = A::rcp(rr);
     NT u1ir = A::mul(u1, irr);
     o.gJ[0] = A::add(o.gJ[0], A::mul(u1ir, d0));
     o.gJ[1] = A::add(o.gJ[1], A::mul(u1ir, d1));
     o.gJ[2] = A::add(o.gJ[2], A::mul(u1ir, d2));
     o.lJ = A::add(o.lJ, A::add(u2, A::mul_f(u1ir, 2.0f)));
-    o.S = A::sub(o.S, A::mul(A::mul(b1, rr), inv));
     o.V = A::sub(o.V, A::mul(A::c(S.D.Z[I]), irr));
   }
 }
@@ -1753,6 +1889,48 @@ cudaError_t launch_interval(const SysDev& S, const Layout& Lo, const LatDev& L, 
 cudaError_t launch_reconfig(const PopDev& P, const Layout& Lo, uint64_t k, cudaStream_t st)
 {
   k_reconfig<<<1, 1024, 0, st>>>(P, P.rec_dst, Lo.rec, Lo.off_b, k);
+  return cudaGetLastError();
+}
+
+// Base terms of the neural objective: grad_i log|psi_G| and E_L of every
+// configuration in IEEE double, one warp per configuration (the caller
+// passes the system with the neural term switched off).
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+k_base_terms(const __grid_constant__ SysDev S, const Layout Lo, int n, const double* x, double* grad,
+             double* e, int* err)
+{
+  extern __shared__ double smem[];
+  double* sC = smem;
+  stage_coefficients(S, sC);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int s = blockIdx.x * kWarpsPerBlock + wib;
+  if (s >= n) return;
+  WarpMem wm = warp_mem(Lo, S, sC + Lo.head + wib * Lo.smem_warp);
+  for (int j = lane; j < 3 * Lo.N; j += 32) wm.x[j] = x[(size_t)s * 3 * Lo.N + j];
+  __syncwarp();
+  bool ok = warp_inverse(S, sC, wm.x, 0, wm.A, wm.scr, lane);
+  ok = ok && warp_inverse(S, sC, wm.x, 1, wm.A + Lo.nu * Lo.nu, wm.scr, lane);
+  if (!ok) {
+    if (lane == 0) atomicOr(err, kErrSingular);
+    for (int j = lane; j < 3 * Lo.N; j += 32) grad[(size_t)s * 3 * Lo.N + j] = NAN;
+    if (lane == 0) e[s] = NAN;
+    return;
+  }
+  LatDev L{};
+  L.G = 1;
+  double b, el;
+  warp_eval(S, sC, L, wm, lane, nullptr, b, el, grad + (size_t)s * 3 * Lo.N, false);
+  if (lane == 0) e[s] = el;
+}
+
+cudaError_t launch_base_terms(const SysDev& S, const Layout& Lo, int n, const double* x, double* grad,
+                              double* e_out, int* err, cudaStream_t st)
+{
+  if (n <= 0) return cudaSuccess;
+  cudaError_t e = set_smem((const void*)k_base_terms, Lo.smem_block_bytes);
+  if (e != cudaSuccess) return e;
+  const int blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  k_base_terms<<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(S, Lo, n, x, grad, e_out, err);
   return cudaGetLastError();
 }
 

@@ -42,6 +42,7 @@ struct Ar<df> {
   static __device__ __forceinline__ df half(df a) { return df_make(0.5f * a.hi, 0.5f * a.lo); }
   static __device__ __forceinline__ df exp(df a, const ExpConsts& K, const float2* tab) { return df_exp(a, K, tab); }
   static __device__ __forceinline__ df log(df a, const ExpConsts& K, const float2* tab) { return df_log(a, K, tab); }
+  static __device__ __forceinline__ float approx(df a) { return a.hi; }
   static __device__ __forceinline__ bool positive(df a) { return a.hi > 0.0f; }
   static __device__ __forceinline__ bool lt(df a, df b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
   static __device__ __forceinline__ df shfl(df v, int src)
@@ -83,6 +84,7 @@ struct Ar<float> {
   static __device__ __forceinline__ float half(float a) { return 0.5f * a; }
   static __device__ __forceinline__ float exp(float a, const ExpConsts&, const float2*) { return expf(a); }
   static __device__ __forceinline__ float log(float a, const ExpConsts&, const float2*) { return logf(a); }
+  static __device__ __forceinline__ float approx(float a) { return a; }
   static __device__ __forceinline__ bool positive(float a) { return a > 0.0f; }
   static __device__ __forceinline__ bool lt(float a, float b) { return a < b; }
   static __device__ __forceinline__ float shfl(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
