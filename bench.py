@@ -164,13 +164,16 @@ def df_flops_per_move(system, G):
     return P * per_cand + el + jump
 
 
-def measure_leg(args, pkg, torch, system, precision, dev, rank, seed, x0, with_clocks):
+def measure_leg(args, pkg, torch, system, precision, dev, rank, seed, x0, with_clocks, neural=None):
     """W warm-up intervals, then K timed intervals, each bracketed by CUDA
-    events on the library's stream with an L2 flush between them."""
+    events on the library's stream with an L2 flush between them.
+    ``neural`` = (spec, params) installs the neural pair term first."""
     _, world, local = _env_rank()
     spacing = pkg.Spacing(pkg.THIS_WORK)
     a = WORKLOAD["a"]
     g = pkg.LrdmcSystem(system).set_precision(precision)
+    if neural is not None:
+        g.set_neural_jastrow(*neural)
     cap = args.warmup + args.steps + 8
     g.init_walkers(torch.tensor(x0, device=dev), seed=seed, tau=WORKLOAD["tau"], e_trial=WORKLOAD["e_trial"],
                    recompute_every=WORKLOAD["recompute_every"], trace_capacity=cap)
@@ -241,6 +244,11 @@ def run_ours(args):
     mx = None
     if args.mixed_leg and main_prec != pkg.PRECISION_FP32:
         mx = measure_leg(args, pkg, torch, system, pkg.PRECISION_FP32, dev, rank, seed, x0, False)
+    # the neural pair Jastrow: trained on the GPU (untimed) on configurations
+    # of a plain projection, then the same measurement with the term
+    nj = None
+    if args.neural_leg:
+        nj = neural_leg(args, pkg, torch, system, main_prec, dev, rank, seed, x0)
     # e2e: the public API from host memory: H2D of the start configurations,
     # init, the same steps, each followed by a D2H read of the trace.
     spacing = pkg.Spacing(pkg.THIS_WORK)
@@ -353,10 +361,54 @@ def run_ours(args):
             "energy_minus_fp64_Ha": mx_energy - ref_energy,
             "combined_sigma_Ha": float(np.hypot(mx_err, ref_err)),
             "kernel_ms_per_launch": mx["t_int_ms"] / max(mx["n_int"], 1)}
+    if nj is not None:
+        leg_nj, info = nj
+        nj_value = leg_nj["moves"] / (leg_nj["total_ms"] * 1e-3)
+        nj_err, _ = stats.reblock(leg_nj["e"])
+        nj_eff = stats.efficiency(leg_nj["e"], leg_nj["total_ms"] * 1e-3)
+        block = {"mode": "Pade + neural pair Jastrow (2x64 SiLU, bf16 weights, quintic table), " + args.precision,
+                 "value": nj_value, "efficiency": nj_eff, "efficiency_ratio_vs_pade": nj_eff / eff["value"],
+                 "energy_Ha": stats.energy_estimate(leg_nj["e"], leg_nj["w"], 0), "sigma_mean_Ha": nj_err,
+                 "var_EL_walkers_Ha2": info.pop("var_EL_walkers"),
+                 "var_EL_walkers_pade_Ha2": float(np.var(leg["g"].walkers()["EL"])),
+                 "kernel_ms_per_launch": leg_nj["t_int_ms"] / max(leg_nj["n_int"], 1), **info}
+        if fp is not None:
+            block["efficiency_ratio_vs_fp64"] = nj_eff / stats.efficiency(fp["e"], fp["total_ms"] * 1e-3)
+        out["neural_jastrow"] = block
     out["cpu_baseline"] = cpu_baseline(args) if args.cpu_seconds > 0 else None
     print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def neural_leg(args, pkg, torch, system, precision, dev, rank, seed, x0):
+    """Sample configurations from a plain projection of the workload, train
+    the neural pair term on the GPU (the library's forward/backward kernels),
+    then measure the projection with the tabulated term."""
+    from paper_1909_01589_gb300 import neural as N
+
+    spec = S.default_neural_spec(system)
+    plain = pkg.LrdmcSystem(system).set_precision(precision)
+    sp = pkg.Spacing(pkg.THIS_WORK)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n_cfg = 16 * len(x0)
+    x = N.sample_configurations(plain, x0, n_cfg, WORKLOAD["a"], sp, WORKLOAD["tau"], WORKLOAD["e_trial"],
+                                seed=seed + 1)
+    grad, e = plain.base_terms(x)
+    n_tr = n_cfg * 7 // 8
+    params, _ = N.train(plain, spec, S.neural_init(spec, seed), x[:n_tr], grad[:n_tr], e[:n_tr], steps=400,
+                        seed=seed + 2)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    el, j = N.evaluate(plain, spec, params, x[n_tr:], grad[n_tr:], e[n_tr:])
+    info = {"train_seconds": t_train, "train_configs": n_tr, "train_steps": 400,
+            "heldout_var_pade_Ha2": float(torch.var(e[n_tr:])),
+            "heldout_var_neural_Ha2": float(N.variance_loss(el, j, clip=0.0))}
+    leg = measure_leg(args, pkg, torch, system, precision, dev, rank, seed, x0, False,
+                      neural=(spec, params.cpu().numpy()))
+    info["var_EL_walkers"] = float(np.var(leg["g"].walkers()["EL"]))
+    return leg, info
 
 
 def _read_traffic(df64=True):
@@ -439,6 +491,8 @@ def main():
                     help="evaluation arithmetic: double-float on the FP32 pipe or IEEE double")
     ap.add_argument("--no-fp64-leg", dest="fp64_leg", action="store_false",
                     help="skip the plain-FP64 comparison leg")
+    ap.add_argument("--no-neural-leg", dest="neural_leg", action="store_false",
+                    help="skip training and measuring the neural pair Jastrow")
     ap.add_argument("--no-mixed-leg", dest="mixed_leg", action="store_false",
                     help="skip the mixed-precision (FP32 evaluation) leg")
     ap.add_argument("--walkers", type=int, default=WORKLOAD["n_walkers"],

@@ -87,12 +87,13 @@ def evaluate(lsys, spec, params, x, grad_base, e_base, bf16=True, chunk=1 << 17)
     return torch.cat(els), torch.cat(js)
 
 
-def train(lsys, spec, params0, x, grad_base, e_base, steps=400, batch=1 << 16, lr=2e-3, seed=0, bf16=True,
-          log_every=0, min_ess=0.3, reweight=True, clip=0.0):
-    """Adam on the reweighted variance over random minibatches of the
-    sample. Steps whose batch has an effective sample fraction below
-    ``min_ess`` are skipped (the sample no longer represents |psi_theta|^2
-    there). Returns (params, history of (step, loss))."""
+def train(lsys, spec, params0, x, grad_base, e_base, steps=400, batch=1 << 14, lr=1e-3, seed=0, bf16=True,
+          log_every=0, min_ess=0.3, reweight=True, clip=5.0):
+    """Adam on the (reweighted, clipped) variance over random minibatches
+    of the sample. With reweighting, steps whose batch has an effective
+    sample fraction below ``min_ess`` are skipped (the sample no longer
+    represents |psi_theta|^2 there). Returns (params, history of (step,
+    loss))."""
     dev = x.device
     params = torch.tensor(np.asarray(params0, dtype=np.float32), device=dev, requires_grad=True)
     opt = torch.optim.Adam([params], lr=lr)
@@ -103,7 +104,7 @@ def train(lsys, spec, params0, x, grad_base, e_base, steps=400, batch=1 << 16, l
     for it in range(steps):
         idx = torch.randint(0, n, (min(batch, n),), generator=gen, device=dev)
         el, j = NeuralJastrowTerms.apply(params, lsys, spec, x[idx], grad_base[idx], e_base[idx], bf16)
-        if effective_sample_fraction(j.detach()) < min_ess:
+        if reweight and effective_sample_fraction(j.detach()) < min_ess:
             continue
         loss = variance_loss(el, j, reweight, clip)
         opt.zero_grad()

@@ -206,25 +206,27 @@ def test_training_backward_finite_difference(pkg, oracle_mod, nn):
 
 
 def test_training_gain_on_neon(pkg, oracle_mod, nn):
-    """What the trained term gains: configurations from a plain projection
-    of Ne (a = 0.2, double grid), 300 Adam steps on the GPU, then the
-    variance of E_L on held-out configurations and over a fresh projection
-    with the tabulated term, both against the plain Pade Jastrow."""
+    """What the trained term gains: 65536 configurations from a plain
+    projection of Ne (a = 0.2, double grid), 400 Adam steps on the GPU
+    (reweighted variance, local energies clipped at the median +- 5 mean
+    absolute deviations), then the variance of E_L on held-out
+    configurations and over a fresh projection with the tabulated term,
+    both against the plain Pade Jastrow."""
     from paper_1909_01589_gb300 import neural as N
 
     system = S.neon()
     spec = S.default_neural_spec(system)
     plain = pkg.LrdmcSystem(system)
     sp = pkg.Spacing(pkg.THIS_WORK)
-    x = N.sample_configurations(plain, S.initial_positions(system, 4096, 31), 49152, 0.2, sp, 0.02, -128.9, seed=31)
+    x = N.sample_configurations(plain, S.initial_positions(system, 4096, 31), 65536, 0.2, sp, 0.02, -128.9, seed=31)
     grad, e = plain.base_terms(x)
-    train_idx, hold = slice(0, 40960), slice(40960, None)
+    train_idx, hold = slice(0, 57344), slice(57344, None)
     params, _ = N.train(plain, spec, S.neural_init(spec, 32), x[train_idx], grad[train_idx], e[train_idx],
-                        steps=300, batch=8192, lr=3e-3, seed=33)
+                        steps=400, seed=33)
     el, j = N.evaluate(plain, spec, params, x[hold], grad[hold], e[hold])
     var_plain = float(torch.var(e[hold]))
-    var_nn = float(N.variance_loss(el, j))
-    assert var_nn < 0.8 * var_plain, (var_nn, var_plain)
+    var_nn = float(N.variance_loss(el, j, clip=0.0))
+    assert var_nn < 0.85 * var_plain, (var_nn, var_plain)
     # the projection with the trained term has a smaller local-energy spread
     x0 = S.initial_positions(system, 4096, 34)
     spreads = []
@@ -240,4 +242,4 @@ def test_training_gain_on_neon(pkg, oracle_mod, nn):
             gsys.step(4, 0.2, sp)
             v.append(np.var(gsys.walkers()["EL"]))
         spreads.append(np.median(v))
-    assert spreads[1] < 0.85 * spreads[0], spreads
+    assert spreads[1] < 0.8 * spreads[0], spreads
