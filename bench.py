@@ -249,6 +249,7 @@ def run_ours(args):
     nj = None
     if args.neural_leg:
         nj = neural_leg(args, pkg, torch, system, main_prec, dev, rank, seed, x0)
+    bt = batched_leg(args, pkg, torch, main_prec, seed) if args.batch_leg else None
     # e2e: the public API from host memory: H2D of the start configurations,
     # init, the same steps, each followed by a D2H read of the trace.
     spacing = pkg.Spacing(pkg.THIS_WORK)
@@ -375,6 +376,8 @@ def run_ours(args):
         if fp is not None:
             block["efficiency_ratio_vs_fp64"] = nj_eff / stats.efficiency(fp["e"], fp["total_ms"] * 1e-3)
         out["neural_jastrow"] = block
+    if bt is not None:
+        out["batched"] = bt
     out["cpu_baseline"] = cpu_baseline(args) if args.cpu_seconds > 0 else None
     print(json.dumps(out), flush=True)
     if dist is not None:
@@ -409,6 +412,67 @@ def neural_leg(args, pkg, torch, system, precision, dev, rank, seed, x0):
                       neural=(spec, params.cpu().numpy()))
     info["var_EL_walkers"] = float(np.var(leg["g"].walkers()["EL"]))
     return leg, info
+
+
+BATCH_SYSTEMS = ("He", "Ne", "Ar", "Kr", "H2O")
+BATCH_E_TRIAL = {"He": -2.90, "Ne": -128.9, "Ar": -527.5, "Kr": -2753.0, "H2O": -76.0}
+
+
+def batched_leg(args, pkg, torch, precision, seed):
+    """Heterogeneous batch: 8192 walkers each of He, Ne, Ar, Kr and H2O
+    (N = 2..36), each at a = 1/(3.5 Z_max) on this work's double grid with
+    tau for about 10 jumps per walker per interval, tuned grids, one CUDA
+    graph per step; against the same steps made system by system."""
+    from paper_1909_01589_gb300 import batch as B
+
+    W = args.batch_walkers
+    sp = pkg.Spacing(pkg.THIS_WORK)
+    systems, a, taus = [], [], []
+    for q, name in enumerate(BATCH_SYSTEMS):
+        system = S.make_system(name)
+        ai = 1.0 / (3.5 * float(np.max(system.Z)))
+        x = S.initial_positions(system, 256, seed + q)
+        tau = B.tau_for(pkg, system, ai, sp, 10.0, x, S.random_rotations(256, seed + q))
+        systems.append(system)
+        a.append(ai)
+        taus.append(tau)
+    K = args.batch_steps
+    cap = 64 + 2 * K
+
+    def make():
+        gs = []
+        for q, (system, tau) in enumerate(zip(systems, taus)):
+            g = pkg.LrdmcSystem(system).set_precision(precision)
+            g.init_walkers(torch.tensor(S.initial_positions(system, W, seed + 100 + q), device="cuda"),
+                           seed=seed + 200 + q, tau=tau, e_trial=BATCH_E_TRIAL[BATCH_SYSTEMS[q]],
+                           recompute_every=5, trace_capacity=cap)
+            gs.append(g)
+        return gs
+
+    gs = make()
+    batch = pkg.LrdmcBatch(gs, a, [sp] * len(gs))
+    report = B.tune(batch, a, [sp] * len(gs), trial_steps=2)
+    m0 = sum(g.moves() for g in gs)
+    ms = B._time_batch_steps(torch, batch, K)
+    moves_b = sum(g.moves() for g in gs) - m0
+    # the same systems one by one (default grids), same number of steps
+    solo = make()
+    t_seq = 0.0
+    moves_s = 0
+    for g, ai in zip(solo, a):
+        g.step(1, ai, sp)
+        g.sync()
+        m = g.moves()
+        t_seq += B._time_system_steps(torch, g, K, ai, sp) * K
+        moves_s += g.moves() - m
+    value_b = moves_b / (ms * K * 1e-3)
+    value_s = moves_s / (t_seq * 1e-3)
+    return {"systems": list(BATCH_SYSTEMS), "walkers_each": W, "a": a, "tau": taus, "steps": K,
+            "evaluation": args.precision, "value_batched": value_b, "value_sequential": value_s,
+            "speedup": value_b / value_s, "unit": "walker-moves/s", "ms_per_batched_step": ms,
+            "ms_per_sequential_round": t_seq / K, "tuning": report,
+            "note": "one CUDA graph per step with every system's kernels as parallel branches; "
+                    "grid sizes chosen by measurement"}
 
 
 def _read_traffic(df64=True):
@@ -491,6 +555,10 @@ def main():
                     help="evaluation arithmetic: double-float on the FP32 pipe or IEEE double")
     ap.add_argument("--no-fp64-leg", dest="fp64_leg", action="store_false",
                     help="skip the plain-FP64 comparison leg")
+    ap.add_argument("--no-batch-leg", dest="batch_leg", action="store_false",
+                    help="skip the heterogeneous batch (He, Ne, Ar, Kr, H2O in one graph per step)")
+    ap.add_argument("--batch-walkers", type=int, default=8192)
+    ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--no-neural-leg", dest="neural_leg", action="store_false",
                     help="skip training and measuring the neural pair Jastrow")
     ap.add_argument("--no-mixed-leg", dest="mixed_leg", action="store_false",

@@ -332,6 +332,44 @@ LRDMC_API lrdmc_status lrdmc_nj_backward(lrdmc_system_t sys, const lrdmc_nj_spec
                                          int n, const double* x, const float* q, const float* d_el,
                                          const float* d_j, float* grad_out, void* stream);
 
+/* -------------------------------------------------------------------------
+ * Persistent grid size and batches of systems.
+ *
+ * The interval kernel runs a persistent grid whose warps fetch walkers
+ * through an atomic counter. By default the grid holds as many blocks as fit
+ * on the GPU for the system's shared-memory footprint;
+ * lrdmc_set_interval_blocks overrides that (0 restores the default) and
+ * lrdmc_interval_blocks reports the current and default sizes. The grid
+ * size never changes results, only how the GPU is shared.
+ * ---------------------------------------------------------------------- */
+LRDMC_API lrdmc_status lrdmc_set_interval_blocks(lrdmc_system_t sys, int blocks);
+LRDMC_API lrdmc_status lrdmc_interval_blocks(lrdmc_system_t sys, int* current, int* occupancy_default);
+
+/* A batch projects several systems (different atoms, electron counts and
+ * spacings) together. Every step is one CUDA graph: a fork, then per system
+ * on its own stream its interval kernel, its reconfiguration kernel and the
+ * copy of its error word, then a join. The systems' persistent grids run
+ * concurrently and share the GPU in proportion to their grid sizes. Graphs
+ * are captured on first use (one per parity of the double-buffered
+ * populations) and captured again when a system's kernel arguments change
+ * (precision, neural term, grid size, init, load). Each system keeps its
+ * own population, trace and results: a batched step gives bit for bit the
+ * results of the same step made with lrdmc_step. n_systems <= 64; every
+ * system must have a population; a[i] and spacing[i] are system i's
+ * lattice. The batch borrows the systems (destroy it first); its streams
+ * are its own, and each system's stream waits for the batch after every
+ * batch_step. Asynchronous; lrdmc_batch_sync waits and reports the first
+ * system error. */
+typedef struct lrdmc_batch_s* lrdmc_batch_t;
+LRDMC_API lrdmc_status lrdmc_batch_create(lrdmc_system_t* systems, int n_systems, const double* a,
+                                          const lrdmc_spacing_fn* spacing, lrdmc_batch_t* out);
+LRDMC_API lrdmc_status lrdmc_batch_step(lrdmc_batch_t batch, int n_steps);
+LRDMC_API lrdmc_status lrdmc_batch_sync(lrdmc_batch_t batch);
+/* The batch's own stream (a cudaStream_t), for timing with events. */
+LRDMC_API lrdmc_status lrdmc_batch_stream(lrdmc_batch_t batch, void** stream);
+LRDMC_API const char* lrdmc_batch_last_error(lrdmc_batch_t batch);
+LRDMC_API void lrdmc_batch_destroy(lrdmc_batch_t batch);
+
 /* Last error message of the system (static string if sys is NULL). */
 LRDMC_API const char* lrdmc_last_error(lrdmc_system_t sys);
 

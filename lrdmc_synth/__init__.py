@@ -239,7 +239,10 @@ def gto_shell(center: int, l: int, n_eff: float, zeta: float) -> Shell:
     """Contracted-Gaussian stand-in for the Slater shell r^(n-1-l) e^(-zeta r)."""
     m = n_eff - 1.0 - l
     a, c = sto_gaussian_fit(m, l)
-    return Shell(center, l, GTO, alpha=list(a * zeta * zeta), coef=list(c * zeta ** m))
+    # n_eff and zeta record the Slater shell the contraction stands in for
+    # (start positions use its radial density); the evaluation reads only
+    # the Gaussian exponents and coefficients of a GTO shell
+    return Shell(center, l, GTO, n_eff=n_eff, zeta=zeta, alpha=list(a * zeta * zeta), coef=list(c * zeta ** m))
 
 
 def _slater_atom_shells(Z: int):
@@ -351,18 +354,16 @@ def initial_positions(system: System, n_walkers: int, seed: int) -> np.ndarray:
     """Start configurations [W][N][3]: electron i of a spin block occupies
     orbital i of that block; its distance from the orbital's centre is drawn
     from the radial density r^(2n) exp(-2 zeta r) of the Slater shell seeding
-    that orbital (a Gamma(2n + 1, 1/(2 zeta)) variate; for a Gaussian shell a
-    Gamma(3, 1/2) variate in bohr), its direction uniformly on the sphere."""
+    that orbital (a Gamma(2n + 1, 1/(2 zeta)) variate; a Gaussian shell uses
+    the Slater shell its contraction was fitted to), its direction uniformly
+    on the sphere."""
     rng = np.random.default_rng(np.random.PCG64(seed))
     N = system.N
     x = np.empty((n_walkers, N, 3))
     for i in range(N):
         m = i if i < system.n_up else i - system.n_up
         sh = system.shells[system.orbital_shell[m % len(system.orbital_shell)]]
-        if sh.kind == STO:
-            r = rng.gamma(2.0 * sh.n_eff + 1.0, 1.0 / (2.0 * sh.zeta), n_walkers)
-        else:
-            r = rng.gamma(3.0, 0.5, n_walkers)
+        r = rng.gamma(2.0 * sh.n_eff + 1.0, 1.0 / (2.0 * sh.zeta), n_walkers)
         v = rng.normal(size=(n_walkers, 3))
         v /= np.linalg.norm(v, axis=1, keepdims=True)
         x[:, i, :] = system.nuc_xyz[sh.center][None, :] + r[:, None] * v

@@ -34,7 +34,8 @@ EXPORTED = [
     "lrdmc_evaluate_static",
     "lrdmc_save", "lrdmc_load", "lrdmc_set_precision", "lrdmc_set_profiling", "lrdmc_kernel_times", "lrdmc_last_error",
     "lrdmc_destroy", "lrdmc_nj_n_params", "lrdmc_set_neural_jastrow", "lrdmc_base_terms", "lrdmc_nj_forward",
-    "lrdmc_nj_backward",
+    "lrdmc_nj_backward", "lrdmc_set_interval_blocks", "lrdmc_interval_blocks", "lrdmc_batch_create",
+    "lrdmc_batch_step", "lrdmc_batch_sync", "lrdmc_batch_stream", "lrdmc_batch_last_error", "lrdmc_batch_destroy",
 ]
 NJ_MAX_CH, NJ_MAX_FEAT, NJ_HIDDEN, NJ_MAX_CELLS = 8, 12, 64, 8192
 
@@ -151,6 +152,22 @@ def load_library():
     L.lrdmc_nj_forward.argtypes = [vp, vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp]
     L.lrdmc_nj_backward.restype = i
     L.lrdmc_nj_backward.argtypes = [vp, vp, vp, i, vp, vp, vp, vp, vp, vp]
+    L.lrdmc_set_interval_blocks.restype = i
+    L.lrdmc_set_interval_blocks.argtypes = [vp, i]
+    L.lrdmc_interval_blocks.restype = i
+    L.lrdmc_interval_blocks.argtypes = [vp, ct.POINTER(i), ct.POINTER(i)]
+    L.lrdmc_batch_create.restype = i
+    L.lrdmc_batch_create.argtypes = [vp, i, vp, vp, ct.POINTER(vp)]
+    L.lrdmc_batch_step.restype = i
+    L.lrdmc_batch_step.argtypes = [vp, i]
+    L.lrdmc_batch_sync.restype = i
+    L.lrdmc_batch_sync.argtypes = [vp]
+    L.lrdmc_batch_stream.restype = i
+    L.lrdmc_batch_stream.argtypes = [vp, ct.POINTER(vp)]
+    L.lrdmc_batch_last_error.restype = ct.c_char_p
+    L.lrdmc_batch_last_error.argtypes = [vp]
+    L.lrdmc_batch_destroy.restype = None
+    L.lrdmc_batch_destroy.argtypes = [vp]
     _lib = L
     return L
 
@@ -359,6 +376,17 @@ class LrdmcSystem:
         return ratio, T, b, el
 
 
+    def set_interval_blocks(self, blocks):
+        """Persistent grid size of the interval kernel (0 = occupancy default)."""
+        self._check(load_library().lrdmc_set_interval_blocks(self.h, int(blocks)))
+        return self
+
+    def interval_blocks(self):
+        """(current setting, occupancy default) of the interval grid."""
+        c, d = ct.c_int(), ct.c_int()
+        self._check(load_library().lrdmc_interval_blocks(self.h, ct.byref(c), ct.byref(d)))
+        return c.value, d.value
+
     # ---------------------------------------------------------------- neural pair term
     def set_neural_jastrow(self, spec, params, bf16=True):
         """Install the neural pair term (params: float32 array or tensor of
@@ -429,6 +457,49 @@ class LrdmcSystem:
             self.h, ct.byref(c), _t_ptr(p), n, _t_ptr(x.contiguous()), _t_ptr(q.contiguous()),
             _t_ptr(d_el.contiguous()), _t_ptr(d_j.contiguous()), _t_ptr(grad), ct.c_void_p(stream.cuda_stream)))
         return grad
+
+
+class LrdmcBatch:
+    """Several systems projected together, one CUDA graph per step (see
+    lrdmc_batch_create). ``systems`` are LrdmcSystem objects with
+    populations; ``a`` and ``spacing`` give each system's lattice."""
+
+    def __init__(self, systems, a, spacing):
+        L = load_library()
+        n = len(systems)
+        self.systems = list(systems)
+        hs = (ct.c_void_p * n)(*[s.h for s in systems])
+        av = np.ascontiguousarray(a, dtype=np.float64)
+        sp = (_Spacing * n)(*[x.c() for x in spacing])
+        h = ct.c_void_p()
+        st = L.lrdmc_batch_create(ct.cast(hs, ct.c_void_p), n, _np_ptr(av), ct.cast(sp, ct.c_void_p), ct.byref(h))
+        if st != OK:
+            raise LrdmcError(st, "batch_create failed (systems need populations; no duplicates; valid lattices)")
+        self.h = h
+        self._G = [1 if x.kind == SINGLE else 2 for x in spacing]
+        for s, G in zip(self.systems, self._G):
+            s.lattice_G = G
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            load_library().lrdmc_batch_destroy(self.h)
+            self.h = None
+
+    def _check(self, st):
+        if st != OK:
+            raise LrdmcError(st, load_library().lrdmc_batch_last_error(self.h).decode())
+
+    def step(self, n_steps):
+        self._check(load_library().lrdmc_batch_step(self.h, int(n_steps)))
+
+    def sync(self):
+        self._check(load_library().lrdmc_batch_sync(self.h))
+
+    @property
+    def stream_ptr(self):
+        p = ct.c_void_p()
+        self._check(load_library().lrdmc_batch_stream(self.h, ct.byref(p)))
+        return p.value
 
 
 def create_system(system) -> LrdmcSystem:

@@ -45,6 +45,8 @@ struct lrdmc_system_s {
   double t_interval_ms = 0.0, t_reconfig_ms = 0.0;
   long long n_interval = 0, n_reconfig = 0;
   std::string last_error;
+  int blocks = 0;  // persistent grid of the interval kernel (0 = occupancy default)
+  uint64_t version = 0;  // bumped whenever kernel arguments change (batches re-capture)
   // neural pair term (lrdmc_set_neural_jastrow)
   double* nj_tab = nullptr;
   df* nj_tab_df = nullptr;
@@ -377,7 +379,7 @@ lrdmc_status lrdmc_spacing_params(lrdmc_system_t s, double a, const lrdmc_spacin
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct WsPlan {
-  size_t rec, parent, order, logw, el, jumps, cum, trace, moves, err, counter, total;
+  size_t rec, parent, order, logw, el, jumps, cum, trace, moves, err, counter, kdev, total;
 };
 
 static WsPlan plan_ws(const Layout& Lo, int W, int cap)
@@ -395,6 +397,7 @@ static WsPlan plan_ws(const Layout& Lo, int W, int cap)
   p.moves = o; o += 256;
   p.err = o; o += 256;
   p.counter = o; o += 256;
+  p.kdev = o; o += 256;
   p.total = o;
   return p;
 }
@@ -459,12 +462,14 @@ lrdmc_status lrdmc_init_walkers(lrdmc_system_t s, int W, const double* x0, uint6
   P.moves = (unsigned long long*)(s->ws + p.moves);
   P.err = (int*)(s->ws + p.err);
   P.counter = (int*)(s->ws + p.counter);
+  P.kdev = (unsigned long long*)(s->ws + p.kdev);
+  P.recompute_every = recompute_every;
   P.W = W;
   P.trace_cap = cap;
   P.seed = seed;
   P.tau = tau;
   P.e_trial = e_trial;
-  cudaError_t e = cudaMemsetAsync(s->ws + p.moves, 0, 3 * 256, s->stream);
+  cudaError_t e = cudaMemsetAsync(s->ws + p.moves, 0, 4 * 256, s->stream);  // moves, err, counter, kdev
   if (e != cudaSuccess) return cuda_fail(s, e, "workspace clear");
   e = cudaMemsetAsync(P.logw, 0, sizeof(double) * W, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(P.jumps, 0, sizeof(int) * W, s->stream);
@@ -480,6 +485,7 @@ lrdmc_status lrdmc_init_walkers(lrdmc_system_t s, int W, const double* x0, uint6
   s->k = 0;
   s->have_pop = true;
   s->have_eval = false;
+  s->version++;
   return read_error_word(s);
 }
 
@@ -513,8 +519,6 @@ lrdmc_status lrdmc_step(lrdmc_system_t s, int n_steps, double a, const lrdmc_spa
     s->eval_prec = s->S.precision;
   }
   for (int n = 0; n < n_steps; ++n) {
-    const uint64_t k = s->k;
-    const int recompute = (k > 0 && s->recompute_every > 0 && k % (uint64_t)s->recompute_every == 0) ? 1 : 0;
     P.rec_src = s->rec[s->cur];
     P.rec_dst = s->rec[1 - s->cur];
     cudaEvent_t* ev = nullptr;
@@ -523,13 +527,13 @@ lrdmc_status lrdmc_step(lrdmc_system_t s, int n_steps, double a, const lrdmc_spa
       s->ev_used += 4;
     }
     if (ev) cudaEventRecord(ev[0], s->stream);
-    e = launch_interval(s->S, s->Lo, L, P, k, recompute, s->stream);
+    e = launch_interval(s->S, s->Lo, L, P, s->blocks, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "k_interval launch");
     if (ev) {
       cudaEventRecord(ev[1], s->stream);
       cudaEventRecord(ev[2], s->stream);
     }
-    e = launch_reconfig(P, s->Lo, k, s->stream);
+    e = launch_reconfig(P, s->Lo, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "k_reconfig launch");
     if (ev) cudaEventRecord(ev[3], s->stream);
     s->cur = 1 - s->cur;
@@ -758,9 +762,12 @@ lrdmc_status lrdmc_load(lrdmc_system_t s, const char* path)
   if (e == cudaSuccess) e = cudaMemcpyAsync(s->P.parent, par.data(), sizeof(int) * W, cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(s->P.trace, trace.data(), sizeof(double) * trace.size(), cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(s->P.moves, &moves, sizeof(moves), cudaMemcpyHostToDevice, s->stream);
+  const unsigned long long kload = (unsigned long long)hdr[4];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->P.kdev, &kload, sizeof(kload), cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "load copy");
   s->k = (uint64_t)hdr[4];
+  s->version++;
   s->have_eval = hdr[5] != 0 && hdr[6] == s->S.precision;
   s->eval_prec = (int)hdr[6];
   s->eval_lat = L;
@@ -774,6 +781,7 @@ lrdmc_status lrdmc_set_precision(lrdmc_system_t s, int precision)
     return fail(s, LRDMC_ERR_ARG, "set_precision: unknown precision");
   if (precision != s->S.precision) s->have_eval = false;  // cached rates change format
   s->S.precision = precision;
+  s->version++;
   return LRDMC_OK;
 }
 
@@ -870,6 +878,7 @@ lrdmc_status lrdmc_set_neural_jastrow(lrdmc_system_t s, const lrdmc_nj_spec* sp,
   if (!sp) {
     s->S.nj_on = 0;
     s->have_eval = false;
+    s->version++;
     return LRDMC_OK;
   }
   std::string why;
@@ -908,6 +917,7 @@ lrdmc_status lrdmc_set_neural_jastrow(lrdmc_system_t s, const lrdmc_nj_spec* sp,
   for (int I = 0; I < s->S.n_nuc; ++I) s->S.nj_species[I] = sp->species[I];
   s->S.nj_on = 1;
   s->have_eval = false;
+  s->version++;
   return LRDMC_OK;
 }
 
@@ -961,6 +971,251 @@ lrdmc_status lrdmc_nj_backward(lrdmc_system_t s, const lrdmc_nj_spec* sp, const 
                                      (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "nj_backward");
   return LRDMC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Persistent grid size and batches of systems.
+// ---------------------------------------------------------------------------
+lrdmc_status lrdmc_set_interval_blocks(lrdmc_system_t s, int blocks)
+{
+  if (!s) return fail(s, LRDMC_ERR_ARG, "");
+  if (blocks < 0) return fail(s, LRDMC_ERR_ARG, "set_interval_blocks: blocks < 0");
+  s->blocks = blocks;
+  s->version++;
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_interval_blocks(lrdmc_system_t s, int* current, int* occupancy_default)
+{
+  if (!s) return fail(s, LRDMC_ERR_ARG, "");
+  if (current) *current = s->blocks;
+  if (occupancy_default) *occupancy_default = interval_default_blocks(s->S, s->Lo);
+  return LRDMC_OK;
+}
+
+}  // extern "C"
+
+struct lrdmc_batch_s {
+  std::vector<lrdmc_system_t> sys;
+  std::vector<LatDev> lat;
+  std::vector<cudaStream_t> branch;  // one per system, owned
+  std::vector<cudaEvent_t> join, ready;
+  cudaStream_t main = nullptr;
+  cudaEvent_t fork = nullptr, done = nullptr;
+  struct Graph {
+    uint64_t parity;
+    std::vector<uint64_t> versions;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;
+  std::string last_error;
+};
+
+static lrdmc_status bfail(lrdmc_batch_t b, lrdmc_status st, const std::string& msg)
+{
+  if (b) b->last_error = msg;
+  return st;
+}
+
+static lrdmc_status bcuda(lrdmc_batch_t b, cudaError_t e, const char* where)
+{
+  return bfail(b, LRDMC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+static void batch_release(lrdmc_batch_t b)
+{
+  for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
+  b->graphs.clear();
+  for (cudaStream_t st : b->branch) if (st) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : b->join) if (ev) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : b->ready) if (ev) cudaEventDestroy(ev);
+  if (b->main) cudaStreamDestroy(b->main);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->done) cudaEventDestroy(b->done);
+}
+
+// One step of every system as one graph: a fork on the batch stream, per
+// system on its own branch stream the interval kernel, the reconfiguration
+// kernel and the copy of its error word, then a join.
+static cudaError_t capture_step(lrdmc_batch_t b, cudaGraphExec_t* out)
+{
+  cudaError_t e = cudaStreamBeginCapture(b->main, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return e;
+  cudaError_t first = cudaEventRecord(b->fork, b->main);
+  for (size_t i = 0; i < b->sys.size() && first == cudaSuccess; ++i) {
+    lrdmc_system_t s = b->sys[i];
+    PopDev P = s->P;
+    P.rec_src = s->rec[s->cur];
+    P.rec_dst = s->rec[1 - s->cur];
+    first = cudaStreamWaitEvent(b->branch[i], b->fork, 0);
+    if (first == cudaSuccess) first = launch_interval(s->S, s->Lo, b->lat[i], P, s->blocks, b->branch[i]);
+    if (first == cudaSuccess) first = launch_reconfig(P, s->Lo, b->branch[i]);
+    if (first == cudaSuccess)
+      first = cudaMemcpyAsync(s->err_host, s->P.err, sizeof(int), cudaMemcpyDeviceToHost, b->branch[i]);
+    if (first == cudaSuccess) first = cudaEventRecord(b->join[i], b->branch[i]);
+    if (first == cudaSuccess) first = cudaStreamWaitEvent(b->main, b->join[i], 0);
+  }
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(b->main, &g);
+  if (first != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return first;
+  }
+  if (e != cudaSuccess) return e;
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  return e;
+}
+
+extern "C" {
+
+lrdmc_status lrdmc_batch_create(lrdmc_system_t* systems, int n, const double* a, const lrdmc_spacing_fn* spacing,
+                                lrdmc_batch_t* out)
+{
+  if (!out) return LRDMC_ERR_ARG;
+  *out = nullptr;
+  if (!systems || !a || !spacing || n < 1 || n > 64) return LRDMC_ERR_ARG;
+  lrdmc_batch_t b = new lrdmc_batch_s();
+  for (int i = 0; i < n; ++i) {
+    lrdmc_system_t s = systems[i];
+    if (!s || !s->have_pop) {
+      delete b;
+      return LRDMC_ERR_STATE;
+    }
+    for (int j = 0; j < i; ++j)
+      if (systems[j] == s) {
+        delete b;
+        return LRDMC_ERR_ARG;
+      }
+    LatDev L;
+    if (lattice_from(s, a[i], &spacing[i], L) != LRDMC_OK) {
+      delete b;
+      return LRDMC_ERR_ARG;
+    }
+    b->sys.push_back(s);
+    b->lat.push_back(L);
+  }
+  cudaError_t e = cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+  b->branch.assign(n, nullptr);
+  b->join.assign(n, nullptr);
+  b->ready.assign(n, nullptr);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&b->branch[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ready[i], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    batch_release(b);
+    delete b;
+    return LRDMC_ERR_CUDA;
+  }
+  *out = b;
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_batch_step(lrdmc_batch_t b, int n_steps)
+{
+  if (!b) return LRDMC_ERR_ARG;
+  if (n_steps < 0) return bfail(b, LRDMC_ERR_ARG, "batch_step: n_steps < 0");
+  const size_t n = b->sys.size();
+  for (size_t i = 0; i < n; ++i) {
+    lrdmc_system_t s = b->sys[i];
+    if (!s->have_pop) return bfail(b, LRDMC_ERR_STATE, "batch_step: a system has no population");
+    if (s->k + (uint64_t)n_steps > (uint64_t)s->trace_cap)
+      return bfail(b, LRDMC_ERR_ARG, "batch_step: the trace of system " + std::to_string(i) + " would overflow");
+  }
+  if (n_steps == 0) return LRDMC_OK;
+  // the first evaluation of a population (or after a lattice change) on the
+  // system's own stream, then the batch stream waits for every system
+  cudaError_t e = cudaSuccess;
+  for (size_t i = 0; i < n && e == cudaSuccess; ++i) {
+    lrdmc_system_t s = b->sys[i];
+    if (!s->have_eval || !same_lattice(b->lat[i], s->eval_lat)) {
+      PopDev P = s->P;
+      P.rec_src = s->rec[s->cur];
+      P.rec_dst = s->rec[1 - s->cur];
+      e = launch_eval_all(s->S, s->Lo, b->lat[i], P, s->stream);
+      if (e != cudaSuccess) break;
+      s->have_eval = true;
+      s->eval_lat = b->lat[i];
+      s->eval_prec = s->S.precision;
+    }
+    e = cudaEventRecord(b->ready[i], s->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->main, b->ready[i], 0);
+  }
+  if (e != cudaSuccess) return bcuda(b, e, "batch_step: preparation");
+  for (int step = 0; step < n_steps; ++step) {
+    uint64_t parity = 0;
+    for (size_t i = 0; i < n; ++i) parity |= (uint64_t)b->sys[i]->cur << i;
+    cudaGraphExec_t exec = nullptr;
+    for (auto& g : b->graphs) {
+      if (g.parity != parity) continue;
+      bool same = true;
+      for (size_t i = 0; i < n; ++i) same = same && g.versions[i] == b->sys[i]->version;
+      if (same) { exec = g.exec; break; }
+    }
+    if (!exec) {
+      // drop graphs of stale kernel arguments, then capture this parity
+      std::vector<lrdmc_batch_s::Graph> keep;
+      for (auto& g : b->graphs) {
+        bool same = true;
+        for (size_t i = 0; i < n; ++i) same = same && g.versions[i] == b->sys[i]->version;
+        if (same) keep.push_back(g); else cudaGraphExecDestroy(g.exec);
+      }
+      b->graphs = keep;
+      e = capture_step(b, &exec);
+      if (e != cudaSuccess) return bcuda(b, e, "batch_step: graph capture");
+      lrdmc_batch_s::Graph g;
+      g.parity = parity;
+      g.exec = exec;
+      for (size_t i = 0; i < n; ++i) g.versions.push_back(b->sys[i]->version);
+      b->graphs.push_back(g);
+    }
+    e = cudaGraphLaunch(exec, b->main);
+    if (e != cudaSuccess) return bcuda(b, e, "batch_step: graph launch");
+    for (size_t i = 0; i < n; ++i) {
+      lrdmc_system_t s = b->sys[i];
+      s->cur = 1 - s->cur;
+      s->k++;
+      s->pending = true;
+    }
+  }
+  // later work on each system's own stream follows the batch
+  e = cudaEventRecord(b->done, b->main);
+  for (size_t i = 0; i < n && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(b->sys[i]->stream, b->done, 0);
+  if (e != cudaSuccess) return bcuda(b, e, "batch_step: join");
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_batch_sync(lrdmc_batch_t b)
+{
+  if (!b) return LRDMC_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize(b->main);
+  if (e != cudaSuccess) return bcuda(b, e, "batch_sync");
+  for (size_t i = 0; i < b->sys.size(); ++i) {
+    lrdmc_status st = sync_system(b->sys[i]);
+    if (st != LRDMC_OK) return bfail(b, st, "system " + std::to_string(i) + ": " + b->sys[i]->last_error);
+  }
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_batch_stream(lrdmc_batch_t b, void** stream)
+{
+  if (!b || !stream) return LRDMC_ERR_ARG;
+  *stream = (void*)b->main;
+  return LRDMC_OK;
+}
+
+const char* lrdmc_batch_last_error(lrdmc_batch_t b) { return b ? b->last_error.c_str() : g_static_error; }
+
+void lrdmc_batch_destroy(lrdmc_batch_t b)
+{
+  if (!b) return;
+  cudaStreamSynchronize(b->main);
+  batch_release(b);
+  delete b;
 }
 
 const char* lrdmc_last_error(lrdmc_system_t s) { return s ? s->last_error.c_str() : g_static_error; }

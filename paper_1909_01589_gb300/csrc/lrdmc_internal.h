@@ -130,6 +130,12 @@ struct PopDev {
   unsigned long long* moves;
   int* err;
   int* counter;
+  // interval counter k on the device: the interval kernel reads it (Philox
+  // counters, the recompute decision), the reconfiguration kernel reads it
+  // (comb uniform, trace slot) and advances it, so a captured step replays
+  // correctly
+  unsigned long long* kdev;
+  int recompute_every;
   int W;
   int trace_cap;
   uint64_t seed;
@@ -143,9 +149,10 @@ cudaError_t launch_init(const SysDev& S, const Layout& Lo, const PopDev& P, cons
                         cudaStream_t st);
 cudaError_t launch_eval_all(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P,
                             cudaStream_t st);
-cudaError_t launch_interval(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P,
-                            uint64_t k, int recompute, cudaStream_t st);
-cudaError_t launch_reconfig(const PopDev& P, const Layout& Lo, uint64_t k, cudaStream_t st);
+cudaError_t launch_interval(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P, int blocks,
+                            cudaStream_t st);
+cudaError_t launch_reconfig(const PopDev& P, const Layout& Lo, cudaStream_t st);
+int interval_default_blocks(const SysDev& S, const Layout& Lo);
 cudaError_t launch_evaluate(const SysDev& S, const Layout& Lo, const LatDev& L, int n,
                             const double* x, const double* rot, double* ratio, double* T,
                             double* b, double* el, int* err, cudaStream_t st);

@@ -1455,11 +1455,15 @@ k_eval_all(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
 #endif
 template <int PREC>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, LRDMC_INTERVAL_MIN_BLOCKS)
-k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, const PopDev P,
-           uint64_t k, int recompute)
+k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, const PopDev P)
 {
   extern __shared__ double smem[];
   double* sC = smem;
+  // interval k from the device counter (advanced by k_reconfig); the inverse
+  // Slater matrices are recomputed at the start of every recompute_every-th
+  // interval
+  const uint64_t k = *P.kdev;
+  const bool recompute = k > 0 && P.recompute_every > 0 && k % (uint64_t)P.recompute_every == 0;
   stage_coefficients(S, sC);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   WarpMem wm = warp_mem(Lo, S, sC + Lo.head + wib * Lo.smem_warp);
@@ -1572,8 +1576,9 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
 // w_s = exp(log w_s), trace (weighted mean E_L, mean weight, mean jumps),
 // comb parents: slot t takes the smallest s with (t + xi) C_W / W < C_s.
 __global__ void __launch_bounds__(1024) k_reconfig(const PopDev P, const double* rec_next, int rec_stride,
-                                                  int off_b, uint64_t k)
+                                                  int off_b)
 {
+  const uint64_t k = *P.kdev;
   __shared__ double s_run[1024];
   __shared__ double s_e[32], s_j[32], s_w[32];
   __shared__ double s_total;
@@ -1686,6 +1691,9 @@ __global__ void __launch_bounds__(1024) k_reconfig(const PopDev P, const double*
     q = 63 - min(63, max(0, q));
     P.order[atomicAdd(&s_cnt[q], 1)] = tt;
   }
+  // every thread has read k (it is used above, behind barriers): advance it
+  __syncthreads();
+  if (t == 0) *P.kdev = k + 1;
 }
 
 // Stateless evaluation of given configurations (one warp per configuration).
@@ -1848,47 +1856,66 @@ cudaError_t launch_eval_all(const SysDev& S, const Layout& Lo, const LatDev& L, 
   return launch_eval_all_t<LRDMC_PRECISION_FP64>(S, Lo, L, P, st);
 }
 
-// Persistent grid: as many blocks as fit on the GPU at once (capped by the
-// walker count); the warps fetch walkers from an atomic counter.
+// Persistent grid of the interval kernel: as many blocks as fit on the GPU
+// at once (occupancy for this system's shared memory), at most one warp per
+// walker.
+template <int PREC>
+static cudaError_t interval_occupancy(const Layout& Lo, int* blocks)
+{
+  int dev, sm_count = 0, per_sm = 0;
+  cudaError_t e = set_smem((const void*)k_interval<PREC>, Lo.smem_block_bytes);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interval<PREC>, kWarpsPerBlock * 32,
+                                                      Lo.smem_block_bytes);
+  *blocks = (per_sm < 1 ? 1 : per_sm) * sm_count;
+  return e;
+}
+
+int interval_default_blocks(const SysDev& S, const Layout& Lo)
+{
+  int b = 0;
+  if (S.precision == LRDMC_PRECISION_DF64) interval_occupancy<LRDMC_PRECISION_DF64>(Lo, &b);
+  else if (S.precision == LRDMC_PRECISION_FP32) interval_occupancy<LRDMC_PRECISION_FP32>(Lo, &b);
+  else interval_occupancy<LRDMC_PRECISION_FP64>(Lo, &b);
+  return b;
+}
+
 template <int PREC>
 static cudaError_t launch_interval_t(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P,
-                                     uint64_t k, int recompute, cudaStream_t st)
+                                     int blocks, cudaStream_t st)
 {
-  static int blocks_per_sm = -1, sm_count = 0, cached_smem = -1;
+  static int cached_blocks = -1, cached_smem = -1;
   cudaError_t e = set_smem((const void*)k_interval<PREC>, Lo.smem_block_bytes);
   if (e != cudaSuccess) return e;
-  if (cached_smem != Lo.smem_block_bytes) {
-    int dev;
-    e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_interval<PREC>, kWarpsPerBlock * 32,
-                                                      Lo.smem_block_bytes);
-    if (e != cudaSuccess) return e;
-    if (blocks_per_sm < 1) blocks_per_sm = 1;
-    cached_smem = Lo.smem_block_bytes;
+  if (blocks <= 0) {
+    if (cached_smem != Lo.smem_block_bytes) {
+      e = interval_occupancy<PREC>(Lo, &cached_blocks);
+      if (e != cudaSuccess) return e;
+      cached_smem = Lo.smem_block_bytes;
+    }
+    blocks = cached_blocks;
   }
-  int need = (P.W + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  int blocks = blocks_per_sm * sm_count;
+  const int need = (P.W + kWarpsPerBlock - 1) / kWarpsPerBlock;
   if (blocks > need) blocks = need;
-  k_interval<PREC><<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(S, Lo, L, P, k, recompute);
+  k_interval<PREC><<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(S, Lo, L, P);
   return cudaGetLastError();
 }
 
-cudaError_t launch_interval(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P,
-                            uint64_t k, int recompute, cudaStream_t st)
+cudaError_t launch_interval(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P, int blocks,
+                            cudaStream_t st)
 {
   if (S.precision == LRDMC_PRECISION_DF64)
-    return launch_interval_t<LRDMC_PRECISION_DF64>(S, Lo, L, P, k, recompute, st);
+    return launch_interval_t<LRDMC_PRECISION_DF64>(S, Lo, L, P, blocks, st);
   if (S.precision == LRDMC_PRECISION_FP32)
-    return launch_interval_t<LRDMC_PRECISION_FP32>(S, Lo, L, P, k, recompute, st);
-  return launch_interval_t<LRDMC_PRECISION_FP64>(S, Lo, L, P, k, recompute, st);
+    return launch_interval_t<LRDMC_PRECISION_FP32>(S, Lo, L, P, blocks, st);
+  return launch_interval_t<LRDMC_PRECISION_FP64>(S, Lo, L, P, blocks, st);
 }
 
-cudaError_t launch_reconfig(const PopDev& P, const Layout& Lo, uint64_t k, cudaStream_t st)
+cudaError_t launch_reconfig(const PopDev& P, const Layout& Lo, cudaStream_t st)
 {
-  k_reconfig<<<1, 1024, 0, st>>>(P, P.rec_dst, Lo.rec, Lo.off_b, k);
+  k_reconfig<<<1, 1024, 0, st>>>(P, P.rec_dst, Lo.rec, Lo.off_b);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,35 @@
+"""Host logic of the batch autotuner: candidate grids and the choice."""
+from paper_1909_01589_gb300.batch import candidate_grids, choose
+
+
+def test_candidates_respect_limits_and_proportions():
+    defaults = [608, 608, 456, 304, 608]
+    work = [0.2, 1.5, 6.0, 30.0, 2.0]
+    need = [2048, 2048, 2048, 2048, 2048]
+    cands = candidate_grids(defaults, work, need)
+    names = [c[0] for c in cands]
+    assert names[0] == "default" and cands[0][1] == defaults
+    for _, b in cands:
+        assert all(1 <= x <= min(d, m) for x, d, m in zip(b, defaults, need))
+    prop = dict(cands)["proportional x1"]
+    # more work, larger share of its own default grid
+    shares = [b / d for b, d in zip(prop, defaults)]
+    order = sorted(range(5), key=lambda i: work[i])
+    assert [shares[i] for i in order] == sorted(shares)
+    # candidates are distinct
+    assert len({tuple(b) for _, b in cands}) == len(cands)
+
+
+def test_small_populations_cap_the_grid():
+    cands = candidate_grids([608, 608], [1.0, 1.0], [3, 600])
+    for _, b in cands:
+        assert b[0] <= 3 and b[1] <= 600
+
+
+def test_single_system_has_only_the_default():
+    assert candidate_grids([608], [1.0], [100]) == [("default", [100])]
+
+
+def test_choose_takes_the_fastest():
+    t = [("default", [608, 608], 10.0), ("proportional x1", [100, 500], 7.5), ("equal", [304, 304], 8.0)]
+    assert choose(t) == ("proportional x1", [100, 500], 7.5)

@@ -1,0 +1,121 @@
+"""Batches of heterogeneous systems (one CUDA graph per step) against the
+same systems stepped one by one: the walkers, traces and move counts agree
+bit for bit, across graph re-captures (precision change, grid sizes) and
+after the autotuner has chosen the grids."""
+import numpy as np
+import pytest
+
+import lrdmc_synth as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1909_01589_gb300 import build
+
+    build.build()
+    import paper_1909_01589_gb300 as p
+
+    p.load_library()
+    return p
+
+
+CASES = [  # name, walkers, a, spacing, tau, e_trial
+    ("He", 300, 0.2, "single", 0.05, -2.9),
+    ("Ne", 512, 0.2, "this_work", 0.02, -128.9),
+    ("H2O", 384, 0.1, "previous", 0.01, -76.0),
+    ("Ar", 130, 1 / 63, "this_work", 2e-4, -527.0),
+]
+
+
+def _spacing(pkg, kind):
+    return pkg.Spacing({"single": pkg.SINGLE, "this_work": pkg.THIS_WORK, "previous": pkg.PREVIOUS}[kind])
+
+
+def _make(pkg, seed0):
+    out = []
+    for q, (name, W, a, kind, tau, et) in enumerate(CASES):
+        system = S.make_system(name)
+        g = pkg.LrdmcSystem(system)
+        g.init_walkers(torch.tensor(S.initial_positions(system, W, seed0 + q), device="cuda"), seed=seed0 + 10 * q,
+                       tau=tau, e_trial=et, recompute_every=3, trace_capacity=64)
+        out.append(g)
+    return out
+
+
+def _state(g):
+    w = g.walkers()
+    e, wb, j = g.energy_trace()
+    return w["x"], w["EL"], w["parent"], e, wb, g.moves()
+
+
+def _equal(s1, s2):
+    return all(np.array_equal(a, b) for a, b in zip(s1[:5], s2[:5])) and s1[5] == s2[5]
+
+
+def test_batched_steps_equal_single_steps(pkg):
+    a = [c[2] for c in CASES]
+    sp = [_spacing(pkg, c[3]) for c in CASES]
+    solo = _make(pkg, 100)
+    for g, ai, s in zip(solo, a, sp):
+        g.step(7, ai, s)
+        g.sync()
+    batched = _make(pkg, 100)
+    batch = pkg.LrdmcBatch(batched, a, sp)
+    batch.step(3)   # odd: the next call starts from the other buffer parity
+    batch.step(4)
+    batch.sync()
+    for g1, g2 in zip(solo, batched):
+        assert _equal(_state(g1), _state(g2))
+    # a precision change and new grid sizes force re-captures; a single step
+    # of one system in between is ordered with the batch
+    for g in solo + batched:
+        g.set_precision(pkg.PRECISION_FP64)
+    for g, b in zip(batched, (7, 3, 11, 2)):
+        g.set_interval_blocks(b)
+    for g, ai, s in zip(solo, a, sp):
+        g.step(2, ai, s)
+    batched[1].step(1, a[1], sp[1])
+    batch.step(1)
+    for q, g in enumerate(batched):
+        if q != 1:
+            g.step(1, a[q], sp[q])
+    batch.sync()
+    for g1, g2 in zip(solo, batched):
+        assert _equal(_state(g1), _state(g2))
+
+
+def test_tuned_batch_keeps_results(pkg):
+    from paper_1909_01589_gb300 import batch as B
+
+    a = [c[2] for c in CASES]
+    sp = [_spacing(pkg, c[3]) for c in CASES]
+    batched = _make(pkg, 200)
+    batch = pkg.LrdmcBatch(batched, a, sp)
+    report = B.tune(batch, a, sp, trial_steps=2)
+    assert report["choice"]["ms_per_step"] > 0 and len(report["candidates"]) >= 2
+    steps_done = [g.energy_trace()[0].shape[0] for g in batched]
+    batch.step(3)
+    batch.sync()
+    solo = _make(pkg, 200)
+    for g, ai, s, n in zip(solo, a, sp, steps_done):
+        g.step(n + 3, ai, s)
+        g.sync()
+    for g1, g2 in zip(solo, batched):
+        assert _equal(_state(g1), _state(g2))
+
+
+def test_batch_errors(pkg):
+    a = [c[2] for c in CASES[:2]]
+    sp = [_spacing(pkg, c[3]) for c in CASES[:2]]
+    gs = _make(pkg, 300)[:2]
+    batch = pkg.LrdmcBatch(gs, a, sp)
+    with pytest.raises(pkg.LrdmcError) as e:
+        batch.step(65)  # beyond the trace capacity of 64
+    assert e.value.status == pkg.ERR_ARG
+    with pytest.raises(pkg.LrdmcError):
+        pkg.LrdmcBatch([gs[0], gs[0]], a, sp)  # a system twice
