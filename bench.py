@@ -437,7 +437,7 @@ def batched_leg(args, pkg, torch, precision, seed):
         a.append(ai)
         taus.append(tau)
     K = args.batch_steps
-    cap = 64 + 2 * K
+    cap = 128 + 2 * K
 
     def make():
         gs = []

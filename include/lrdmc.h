@@ -346,9 +346,10 @@ LRDMC_API lrdmc_status lrdmc_set_interval_blocks(lrdmc_system_t sys, int blocks)
 LRDMC_API lrdmc_status lrdmc_interval_blocks(lrdmc_system_t sys, int* current, int* occupancy_default);
 
 /* A batch projects several systems (different atoms, electron counts and
- * spacings) together. Every step is one CUDA graph: a fork, then per system
- * on its own stream its interval kernel, its reconfiguration kernel and the
- * copy of its error word, then a join. The systems' persistent grids run
+ * spacings) together. Every step is one CUDA graph: per execution group
+ * (lrdmc_batch_set_groups) a fork, then per system of the group on its own
+ * stream its interval kernel, its reconfiguration kernel and the copy of
+ * its error word, then a join. The systems' persistent grids run
  * concurrently and share the GPU in proportion to their grid sizes. Graphs
  * are captured on first use (one per parity of the double-buffered
  * populations) and captured again when a system's kernel arguments change
@@ -365,6 +366,18 @@ LRDMC_API lrdmc_status lrdmc_batch_create(lrdmc_system_t* systems, int n_systems
                                           const lrdmc_spacing_fn* spacing, lrdmc_batch_t* out);
 LRDMC_API lrdmc_status lrdmc_batch_step(lrdmc_batch_t batch, int n_steps);
 LRDMC_API lrdmc_status lrdmc_batch_sync(lrdmc_batch_t batch);
+/* Execution groups: group[i] >= 0 for every system; the systems of one
+ * group run concurrently and the groups run one after another in
+ * increasing group number, all inside the step's graph (default: one
+ * group). Takes effect at the next batch_step (the graphs are captured
+ * again). Results do not depend on the grouping. */
+LRDMC_API lrdmc_status lrdmc_batch_set_groups(lrdmc_batch_t batch, const int* group);
+/* Preferred shared-memory share (percent of the unified L1/shared storage,
+ * 0..100, or -1 for the driver's default) of the batched interval launches:
+ * kernels of different systems on one SM run together only under one
+ * L1/shared split. A launch attribute of the batch's launches; lrdmc_step
+ * is unaffected. Takes effect at the next batch_step. */
+LRDMC_API lrdmc_status lrdmc_batch_set_carveout(lrdmc_batch_t batch, int carveout);
 /* The batch's own stream (a cudaStream_t), for timing with events. */
 LRDMC_API lrdmc_status lrdmc_batch_stream(lrdmc_batch_t batch, void** stream);
 LRDMC_API const char* lrdmc_batch_last_error(lrdmc_batch_t batch);

@@ -36,6 +36,7 @@ EXPORTED = [
     "lrdmc_destroy", "lrdmc_nj_n_params", "lrdmc_set_neural_jastrow", "lrdmc_base_terms", "lrdmc_nj_forward",
     "lrdmc_nj_backward", "lrdmc_set_interval_blocks", "lrdmc_interval_blocks", "lrdmc_batch_create",
     "lrdmc_batch_step", "lrdmc_batch_sync", "lrdmc_batch_stream", "lrdmc_batch_last_error", "lrdmc_batch_destroy",
+    "lrdmc_batch_set_groups", "lrdmc_batch_set_carveout",
 ]
 NJ_MAX_CH, NJ_MAX_FEAT, NJ_HIDDEN, NJ_MAX_CELLS = 8, 12, 64, 8192
 
@@ -162,6 +163,10 @@ def load_library():
     L.lrdmc_batch_step.argtypes = [vp, i]
     L.lrdmc_batch_sync.restype = i
     L.lrdmc_batch_sync.argtypes = [vp]
+    L.lrdmc_batch_set_carveout.restype = i
+    L.lrdmc_batch_set_carveout.argtypes = [vp, i]
+    L.lrdmc_batch_set_groups.restype = i
+    L.lrdmc_batch_set_groups.argtypes = [vp, vp]
     L.lrdmc_batch_stream.restype = i
     L.lrdmc_batch_stream.argtypes = [vp, ct.POINTER(vp)]
     L.lrdmc_batch_last_error.restype = ct.c_char_p
@@ -494,6 +499,17 @@ class LrdmcBatch:
 
     def sync(self):
         self._check(load_library().lrdmc_batch_sync(self.h))
+
+    def set_groups(self, groups):
+        """Execution groups: systems of one group run concurrently, groups
+        one after another (in increasing number)."""
+        gv = np.ascontiguousarray(groups, dtype=np.int32)
+        self._check(load_library().lrdmc_batch_set_groups(self.h, _np_ptr(gv)))
+
+    def set_carveout(self, carveout):
+        """Preferred shared-memory carveout (percent) of the batched interval
+        launches, or -1 for the default."""
+        self._check(load_library().lrdmc_batch_set_carveout(self.h, int(carveout)))
 
     @property
     def stream_ptr(self):

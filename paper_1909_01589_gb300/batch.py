@@ -9,10 +9,11 @@ results. ``tune`` chooses the grid sizes by measurement:
 
 1. every system alone at its occupancy-default grid gives its GPU time per
    step, w_i;
-2. candidate grids: the defaults; shares proportional to w_i (so that the
-   branches finish together) at several oversubscription factors; equal
-   shares;
-3. each candidate is timed over a few batched steps with CUDA events on the
+2. candidate plans: every system concurrent with its default grid, or
+   with grids proportional to w_i (so that the branches finish together)
+   at several oversubscription factors; every system in turn on the whole
+   GPU; the heaviest system alone, then the rest concurrently;
+3. each plan is timed over a few batched steps with CUDA events on the
    batch stream, and the fastest is kept.
 
 The tuning steps are real projection steps of the populations (they count
@@ -27,13 +28,15 @@ import numpy as np
 WARPS_PER_BLOCK = 4
 
 
-def candidate_grids(defaults, work, need, factors=(1.0, 1.25, 1.5, 2.0)):
-    """Candidate persistent-grid sizes for systems sharing one GPU.
+def candidate_grids(defaults, work, need, factors=(1.0, 1.5, 2.0)):
+    """Candidate persistent-grid sizes for systems sharing one GPU at once.
 
     defaults[i]: occupancy-default blocks of system i (the whole GPU);
     work[i]: GPU time per step of system i alone on its default grid;
     need[i]: blocks that give every walker its own warp.
-    Returns [(name, [blocks_i])] with 1 <= blocks_i <= min(defaults_i, need_i)."""
+    Returns [(name, [blocks_i])] with 1 <= blocks_i <= min(defaults_i, need_i):
+    the defaults, then shares proportional to work (so that concurrent
+    branches finish together) at several oversubscription factors."""
     n = len(defaults)
     cap = [max(1, min(int(d), int(m))) for d, m in zip(defaults, need)]
     total = float(sum(work))
@@ -44,7 +47,6 @@ def candidate_grids(defaults, work, need, factors=(1.0, 1.25, 1.5, 2.0)):
     for f in factors:
         out.append((f"proportional x{f:g}",
                     [max(1, min(c, int(math.ceil(f * s * d)))) for c, s, d in zip(cap, share, defaults)]))
-    out.append(("equal", [max(1, min(c, int(math.ceil(d / n)))) for c, d in zip(cap, defaults)]))
     seen, uniq = set(), []
     for name, b in out:
         key = tuple(b)
@@ -54,10 +56,41 @@ def candidate_grids(defaults, work, need, factors=(1.0, 1.25, 1.5, 2.0)):
     return uniq
 
 
+def candidate_plans(defaults, work, need):
+    """Execution plans [(name, groups, blocks, carveout)]: every system
+    concurrent (with each candidate grid, under the default and under the
+    maximal shared-memory carveout), every system in turn on the whole GPU
+    (heaviest first), and the heaviest alone followed by the rest
+    concurrently (grids proportional to the rest's work)."""
+    n = len(defaults)
+    cap = [max(1, min(int(d), int(m))) for d, m in zip(defaults, need)]
+    grids = candidate_grids(defaults, work, need)
+    plans = [("concurrent " + name, [0] * n, b, -1) for name, b in grids]
+    plans += [("concurrent " + name + ", max shared carveout", [0] * n, b, 100) for name, b in grids]
+    if n == 1:
+        return plans
+    by_work = sorted(range(n), key=lambda i: -work[i])
+    serial = [0] * n
+    for rank, i in enumerate(by_work):
+        serial[i] = rank
+    plans.append(("serial", serial, list(cap), -1))
+    heavy = by_work[0]
+    rest = [i for i in range(n) if i != heavy]
+    rest_grids = candidate_grids([defaults[i] for i in rest], [work[i] for i in rest], [need[i] for i in rest],
+                                 factors=(1.5,))
+    for name, b in rest_grids:
+        blocks = list(cap)
+        for i, bi in zip(rest, b):
+            blocks[i] = bi
+        split = [0 if i == heavy else 1 for i in range(n)]
+        plans.append((f"heaviest alone, rest concurrent {name}", split, blocks, -1))
+        plans.append((f"heaviest alone, rest concurrent {name}, max shared carveout", split, blocks, 100))
+    return plans
+
+
 def choose(timings):
-    """Name and grid of the fastest candidate; timings = [(name, blocks, ms)]."""
-    name, blocks, ms = min(timings, key=lambda t: t[2])
-    return name, blocks, ms
+    """The fastest plan; timings = [(name, groups, blocks, carveout, ms)]."""
+    return min(timings, key=lambda t: t[-1])
 
 
 def _time_system_steps(torch, g, n, a, spacing):
@@ -98,19 +131,24 @@ def tune(batch, a, spacing, trial_steps=3):
         g.step(1, ai, sp)  # first evaluation outside the timing
         work.append(_time_system_steps(torch, g, trial_steps, ai, sp))
     timings = []
-    for name, blocks in candidate_grids(defaults, work, need):
+    for name, groups, blocks, carve in candidate_plans(defaults, work, need):
+        batch.set_groups(groups)
+        batch.set_carveout(carve)
         for g, b in zip(systems, blocks):
             g.set_interval_blocks(b)
-        batch.step(1)  # capture the graphs of this candidate
+        batch.step(1)  # capture the graphs of this plan
         batch.step(1)
         batch.sync()
-        timings.append((name, blocks, _time_batch_steps(torch, batch, trial_steps)))
-    name, blocks, ms = choose(timings)
+        timings.append((name, groups, blocks, carve, _time_batch_steps(torch, batch, trial_steps)))
+    name, groups, blocks, carve, ms = choose(timings)
+    batch.set_groups(groups)
+    batch.set_carveout(carve)
     for g, b in zip(systems, blocks):
         g.set_interval_blocks(b)
     return {"alone_ms_per_step": work, "sum_alone_ms": float(np.sum(work)), "defaults": defaults,
-            "candidates": [{"name": n, "blocks": b, "ms_per_step": t} for n, b, t in timings],
-            "choice": {"name": name, "blocks": blocks, "ms_per_step": ms}}
+            "candidates": [{"name": n, "groups": gr, "blocks": b, "carveout": c, "ms_per_step": t}
+                           for n, gr, b, c, t in timings],
+            "choice": {"name": name, "groups": groups, "blocks": blocks, "carveout": carve, "ms_per_step": ms}}
 
 
 def tau_for(pkg, system, a, spacing, jumps, x, rot):

@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -998,6 +999,9 @@ lrdmc_status lrdmc_interval_blocks(lrdmc_system_t s, int* current, int* occupanc
 struct lrdmc_batch_s {
   std::vector<lrdmc_system_t> sys;
   std::vector<LatDev> lat;
+  std::vector<int> group;  // systems of one group run concurrently; groups run in order
+  uint64_t group_version = 0;
+  int carveout = -1;       // shared-memory carveout of the batched interval launches (-1: default)
   std::vector<cudaStream_t> branch;  // one per system, owned
   std::vector<cudaEvent_t> join, ready;
   cudaStream_t main = nullptr;
@@ -1005,6 +1009,7 @@ struct lrdmc_batch_s {
   struct Graph {
     uint64_t parity;
     std::vector<uint64_t> versions;
+    uint64_t group_version;
     cudaGraphExec_t exec;
   };
   std::vector<Graph> graphs;
@@ -1034,26 +1039,35 @@ static void batch_release(lrdmc_batch_t b)
   if (b->done) cudaEventDestroy(b->done);
 }
 
-// One step of every system as one graph: a fork on the batch stream, per
-// system on its own branch stream the interval kernel, the reconfiguration
-// kernel and the copy of its error word, then a join.
+// One step of every system as one graph. The groups run in increasing
+// group number; within a group, a fork on the batch stream, per system on
+// its own branch stream the interval kernel, the reconfiguration kernel and
+// the copy of its error word, then a join.
 static cudaError_t capture_step(lrdmc_batch_t b, cudaGraphExec_t* out)
 {
   cudaError_t e = cudaStreamBeginCapture(b->main, cudaStreamCaptureModeRelaxed);
   if (e != cudaSuccess) return e;
-  cudaError_t first = cudaEventRecord(b->fork, b->main);
-  for (size_t i = 0; i < b->sys.size() && first == cudaSuccess; ++i) {
-    lrdmc_system_t s = b->sys[i];
-    PopDev P = s->P;
-    P.rec_src = s->rec[s->cur];
-    P.rec_dst = s->rec[1 - s->cur];
-    first = cudaStreamWaitEvent(b->branch[i], b->fork, 0);
-    if (first == cudaSuccess) first = launch_interval(s->S, s->Lo, b->lat[i], P, s->blocks, b->branch[i]);
-    if (first == cudaSuccess) first = launch_reconfig(P, s->Lo, b->branch[i]);
-    if (first == cudaSuccess)
-      first = cudaMemcpyAsync(s->err_host, s->P.err, sizeof(int), cudaMemcpyDeviceToHost, b->branch[i]);
-    if (first == cudaSuccess) first = cudaEventRecord(b->join[i], b->branch[i]);
-    if (first == cudaSuccess) first = cudaStreamWaitEvent(b->main, b->join[i], 0);
+  cudaError_t first = cudaSuccess;
+  std::vector<int> order(b->group);
+  std::sort(order.begin(), order.end());
+  order.erase(std::unique(order.begin(), order.end()), order.end());
+  for (int grp : order) {
+    if (first == cudaSuccess) first = cudaEventRecord(b->fork, b->main);
+    for (size_t i = 0; i < b->sys.size() && first == cudaSuccess; ++i) {
+      if (b->group[i] != grp) continue;
+      lrdmc_system_t s = b->sys[i];
+      PopDev P = s->P;
+      P.rec_src = s->rec[s->cur];
+      P.rec_dst = s->rec[1 - s->cur];
+      first = cudaStreamWaitEvent(b->branch[i], b->fork, 0);
+      if (first == cudaSuccess)
+        first = launch_interval(s->S, s->Lo, b->lat[i], P, s->blocks, b->branch[i], b->carveout);
+      if (first == cudaSuccess) first = launch_reconfig(P, s->Lo, b->branch[i]);
+      if (first == cudaSuccess)
+        first = cudaMemcpyAsync(s->err_host, s->P.err, sizeof(int), cudaMemcpyDeviceToHost, b->branch[i]);
+      if (first == cudaSuccess) first = cudaEventRecord(b->join[i], b->branch[i]);
+      if (first == cudaSuccess) first = cudaStreamWaitEvent(b->main, b->join[i], 0);
+    }
   }
   cudaGraph_t g = nullptr;
   e = cudaStreamEndCapture(b->main, &g);
@@ -1094,6 +1108,7 @@ lrdmc_status lrdmc_batch_create(lrdmc_system_t* systems, int n, const double* a,
     }
     b->sys.push_back(s);
     b->lat.push_back(L);
+    b->group.push_back(0);
   }
   cudaError_t e = cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
@@ -1151,7 +1166,7 @@ lrdmc_status lrdmc_batch_step(lrdmc_batch_t b, int n_steps)
     for (size_t i = 0; i < n; ++i) parity |= (uint64_t)b->sys[i]->cur << i;
     cudaGraphExec_t exec = nullptr;
     for (auto& g : b->graphs) {
-      if (g.parity != parity) continue;
+      if (g.parity != parity || g.group_version != b->group_version) continue;
       bool same = true;
       for (size_t i = 0; i < n; ++i) same = same && g.versions[i] == b->sys[i]->version;
       if (same) { exec = g.exec; break; }
@@ -1160,7 +1175,7 @@ lrdmc_status lrdmc_batch_step(lrdmc_batch_t b, int n_steps)
       // drop graphs of stale kernel arguments, then capture this parity
       std::vector<lrdmc_batch_s::Graph> keep;
       for (auto& g : b->graphs) {
-        bool same = true;
+        bool same = g.group_version == b->group_version;
         for (size_t i = 0; i < n; ++i) same = same && g.versions[i] == b->sys[i]->version;
         if (same) keep.push_back(g); else cudaGraphExecDestroy(g.exec);
       }
@@ -1169,6 +1184,7 @@ lrdmc_status lrdmc_batch_step(lrdmc_batch_t b, int n_steps)
       if (e != cudaSuccess) return bcuda(b, e, "batch_step: graph capture");
       lrdmc_batch_s::Graph g;
       g.parity = parity;
+      g.group_version = b->group_version;
       g.exec = exec;
       for (size_t i = 0; i < n; ++i) g.versions.push_back(b->sys[i]->version);
       b->graphs.push_back(g);
@@ -1198,6 +1214,26 @@ lrdmc_status lrdmc_batch_sync(lrdmc_batch_t b)
     lrdmc_status st = sync_system(b->sys[i]);
     if (st != LRDMC_OK) return bfail(b, st, "system " + std::to_string(i) + ": " + b->sys[i]->last_error);
   }
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_batch_set_groups(lrdmc_batch_t b, const int* group)
+{
+  if (!b) return LRDMC_ERR_ARG;
+  if (!group) return bfail(b, LRDMC_ERR_ARG, "batch_set_groups: NULL");
+  for (size_t i = 0; i < b->sys.size(); ++i)
+    if (group[i] < 0) return bfail(b, LRDMC_ERR_ARG, "batch_set_groups: negative group");
+  for (size_t i = 0; i < b->sys.size(); ++i) b->group[i] = group[i];
+  b->group_version++;
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_batch_set_carveout(lrdmc_batch_t b, int carveout)
+{
+  if (!b) return LRDMC_ERR_ARG;
+  if (carveout < -1 || carveout > 100) return bfail(b, LRDMC_ERR_ARG, "batch_set_carveout: -1 or 0..100");
+  b->carveout = carveout;
+  b->group_version++;
   return LRDMC_OK;
 }
 

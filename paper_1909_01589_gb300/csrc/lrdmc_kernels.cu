@@ -477,8 +477,8 @@ struct WarpMem {
   double* v;    // [N][n_ao]
   double* Ssum; // [N]
   df* xd;       // [N][3]      double-float copies for the DF64 evaluation
-  df* vd;       // [N][n_ao]
-  df* Sd;       // [N]
+  df* vd;       // [N][n_ao]   (aliases v)
+  df* Sd;       // [N]         (aliases Ssum)
   df* Rd;       // [12]
   double* scr;  // scratch
 };
@@ -492,10 +492,13 @@ __device__ __forceinline__ WarpMem warp_mem(const Layout& Lo, const SysDev& S, d
   m.T = m.R + 12;
   m.v = m.T + Lo.P_max;
   m.Ssum = m.v + Lo.N * S.n_ao;
+  // the FP64 evaluation uses v and Ssum, the FP32-pipe evaluations their
+  // double-float images vd and Sd: one precision runs per launch, so they
+  // share the storage
+  m.vd = reinterpret_cast<df*>(m.v);
+  m.Sd = reinterpret_cast<df*>(m.Ssum);
   m.xd = reinterpret_cast<df*>(m.Ssum + Lo.N);
-  m.vd = m.xd + 3 * Lo.N;
-  m.Sd = m.vd + Lo.N * S.n_ao;
-  m.Rd = m.Sd + Lo.N;
+  m.Rd = m.xd + 3 * Lo.N;
   m.scr = reinterpret_cast<double*>(m.Rd + 12);
   return m;
 }
@@ -1814,7 +1817,7 @@ Layout make_layout(const SysDev& S)
   int scr_sm = S.n_ao + 3 * n + n * n;       // Sherman-Morrison (FP64 or double-float)
   if (scr_sm > scr) scr = scr_sm;
   Lo.smem_warp = 3 * S.N + S.n_up * S.n_up + S.n_dn * S.n_dn + 12 + Lo.P_max + S.N * S.n_ao + S.N +
-                 (3 * S.N + S.N * S.n_ao + S.N + 12) + scr;
+                 (3 * S.N + 12) + scr;
   Lo.smem_warp = (Lo.smem_warp + 1) & ~1;
   Lo.head = ((2 * S.n_ao * S.n_mo + (S.n_ao * S.n_mo + 1) / 2 + 64) + 1) & ~1;
   Lo.smem_block_bytes = (int)sizeof(double) * (Lo.head + kWarpsPerBlock * Lo.smem_warp);
@@ -1884,7 +1887,7 @@ int interval_default_blocks(const SysDev& S, const Layout& Lo)
 
 template <int PREC>
 static cudaError_t launch_interval_t(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P,
-                                     int blocks, cudaStream_t st)
+                                     int blocks, int carveout, cudaStream_t st)
 {
   static int cached_blocks = -1, cached_smem = -1;
   cudaError_t e = set_smem((const void*)k_interval<PREC>, Lo.smem_block_bytes);
@@ -1899,18 +1902,34 @@ static cudaError_t launch_interval_t(const SysDev& S, const Layout& Lo, const La
   }
   const int need = (P.W + kWarpsPerBlock - 1) / kWarpsPerBlock;
   if (blocks > need) blocks = need;
-  k_interval<PREC><<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(S, Lo, L, P);
-  return cudaGetLastError();
+  if (carveout < 0) {
+    k_interval<PREC><<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(S, Lo, L, P);
+    return cudaGetLastError();
+  }
+  // the same launch with a preferred shared-memory carveout for this launch
+  // only (kernels of different systems sharing the SMs then ask for the same
+  // L1/shared split)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(kWarpsPerBlock * 32);
+  cfg.dynamicSmemBytes = Lo.smem_block_bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributePreferredSharedMemoryCarveout;
+  attr[0].val.sharedMemCarveout = (unsigned)carveout;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_interval<PREC>, S, Lo, L, P);
 }
 
 cudaError_t launch_interval(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P, int blocks,
-                            cudaStream_t st)
+                            cudaStream_t st, int carveout)
 {
   if (S.precision == LRDMC_PRECISION_DF64)
-    return launch_interval_t<LRDMC_PRECISION_DF64>(S, Lo, L, P, blocks, st);
+    return launch_interval_t<LRDMC_PRECISION_DF64>(S, Lo, L, P, blocks, carveout, st);
   if (S.precision == LRDMC_PRECISION_FP32)
-    return launch_interval_t<LRDMC_PRECISION_FP32>(S, Lo, L, P, blocks, st);
-  return launch_interval_t<LRDMC_PRECISION_FP64>(S, Lo, L, P, blocks, st);
+    return launch_interval_t<LRDMC_PRECISION_FP32>(S, Lo, L, P, blocks, carveout, st);
+  return launch_interval_t<LRDMC_PRECISION_FP64>(S, Lo, L, P, blocks, carveout, st);
 }
 
 cudaError_t launch_reconfig(const PopDev& P, const Layout& Lo, cudaStream_t st)

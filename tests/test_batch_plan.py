@@ -1,5 +1,5 @@
 """Host logic of the batch autotuner: candidate grids and the choice."""
-from paper_1909_01589_gb300.batch import candidate_grids, choose
+from paper_1909_01589_gb300.batch import candidate_grids, candidate_plans, choose
 
 
 def test_candidates_respect_limits_and_proportions():
@@ -30,6 +30,22 @@ def test_single_system_has_only_the_default():
     assert candidate_grids([608], [1.0], [100]) == [("default", [100])]
 
 
+def test_plans_cover_concurrent_serial_and_split():
+    defaults = [608, 608, 304]
+    work = [2.0, 10.0, 50.0]
+    need = [4096, 4096, 4096]
+    plans = candidate_plans(defaults, work, need)
+    names = [p[0] for p in plans]
+    assert names[0] == "concurrent default"
+    serial = dict((p[0], p[1]) for p in plans)["serial"]
+    assert sorted(serial) == [0, 1, 2] and serial[2] == 0 and serial[0] == 2  # heaviest first
+    split = [p for p in plans if p[0].startswith("heaviest alone")]
+    assert split and all(p[1] == [1, 1, 0] for p in split)
+    for _, groups, blocks, carve in plans:
+        assert len(groups) == 3 and all(1 <= b <= d for b, d in zip(blocks, defaults)) and carve in (-1, 100)
+    assert any(p[3] == 100 for p in plans) and any(p[3] == -1 for p in plans)
+
+
 def test_choose_takes_the_fastest():
-    t = [("default", [608, 608], 10.0), ("proportional x1", [100, 500], 7.5), ("equal", [304, 304], 8.0)]
-    assert choose(t) == ("proportional x1", [100, 500], 7.5)
+    t = [("a", [0, 0], [608, 608], -1, 10.0), ("b", [0, 1], [100, 500], 100, 7.5), ("c", [0, 0], [304, 304], -1, 8.0)]
+    assert choose(t) == ("b", [0, 1], [100, 500], 100, 7.5)

@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import lrdmc_synth as S
+from _parity_util import ratio_scale
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -66,8 +67,9 @@ def test_evaluate_with_neural_term(pkg, oracle_mod, nn, name, a, prec):
     moved = 0.0
     for c in range(n):
         ref = o.lattice_eval(lat, x[c], R[c])
-        assert np.all(np.abs(ratio[c] - ref["ratio"]) <= RTOL * np.maximum(1.0, np.abs(ref["ratio"])))
-        assert np.all(np.abs(T[c] - ref["T"]) <= RTOL * np.max(ref["T"]))
+        scale = ratio_scale(o, system, lat, x[c], R[c], ref["ratio"])
+        assert np.all(np.abs(ratio[c] - ref["ratio"]) <= RTOL * scale)
+        assert np.all(np.abs(T[c] - ref["T"]) <= RTOL * np.max(ref["T"] * scale))
         assert abs(b[c] - ref["b"]) <= RTOL * ref["b"]
         assert abs(el[c] - ref["EL"]) <= RTOL * max(1.0, abs(ref["EL"]))
         moved = max(moved, abs(ref["EL"] - plain.local_energy(x[c])))

@@ -1,7 +1,9 @@
 """GPU-vs-oracle parity of the CUDA path, through the C ABI.
 
 Bar (FP64): lattice-move ratios, rates, total rates and local energies
-within 1e-10 relative (ratios: relative to max(1, |ratio|)); positions,
+within 1e-10 relative (ratios: relative to the magnitude of the terms of
+their determinant dot product, at least max(1, |ratio|); see
+_parity_util.ratio_scale); positions,
 log-weights and trace energies within 1e-10; jump counts, comb parents and
 move choices identical, except after a decision the oracle reports within
 1e-9 of a bin edge (then the trajectories may part and the comparison
@@ -13,6 +15,7 @@ import numpy as np
 import pytest
 
 import lrdmc_synth as S
+from _parity_util import ratio_scale
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -80,8 +83,10 @@ def test_evaluate_matches_oracle(pkg, oracle_mod, name, kind, a, prec):
     ratio, T, b, el = (t.cpu().numpy() for t in (ratio, T, b, el))
     for c in range(n):
         ref = o.lattice_eval(lat, x[c], R[c])
-        assert np.all(np.abs(ratio[c] - ref["ratio"]) <= RTOL * np.maximum(1.0, np.abs(ref["ratio"])))
-        assert np.all(np.abs(T[c] - ref["T"]) <= RTOL * np.max(ref["T"]))
+        scale = ratio_scale(o, system, lat, x[c], R[c], ref["ratio"])
+        err = np.abs(ratio[c] - ref["ratio"])
+        assert np.all(err <= RTOL * scale), (c, np.max(err / scale))
+        assert np.all(np.abs(T[c] - ref["T"]) <= RTOL * np.max(ref["T"] * scale))
         assert abs(b[c] - ref["b"]) <= RTOL * ref["b"]
         assert abs(el[c] - ref["EL"]) <= RTOL * max(1.0, abs(ref["EL"]))
 
@@ -103,7 +108,8 @@ def test_evaluate_full_size_sampled(pkg, oracle_mod, prec):
     assert np.all(np.isfinite(el)) and np.all(b > 0)
     for c in np.random.default_rng(3).choice(n, 64, replace=False):
         ref = o.lattice_eval(lat, x[c], R[c])
-        assert np.all(np.abs(ratio[c] - ref["ratio"]) <= RTOL * np.maximum(1.0, np.abs(ref["ratio"])))
+        scale = ratio_scale(o, system, lat, x[c], R[c], ref["ratio"])
+        assert np.all(np.abs(ratio[c] - ref["ratio"]) <= RTOL * scale)
         assert abs(el[c] - ref["EL"]) <= RTOL * abs(ref["EL"])
 
 
