@@ -33,8 +33,8 @@ from . import stats
 DEFAULTS = {  # system: (walkers, e_trial, target jumps per interval)
     "He": (4096, -2.90, 10.0),
     "Ne": (4096, -128.9, 10.0),
-    "Ar": (2048, -527.5, 10.0),
-    "Kr": (1024, -2753.0, 10.0),
+    "Ar": (4096, -527.5, 10.0),
+    "Kr": (4096, -2753.0, 10.0),
     "H2O": (4096, -76.0, 10.0),
 }
 
@@ -66,22 +66,26 @@ def run(system, a, spacing, W, steps, equil, tau, e_trial, seed=1, precision=PRE
             "seconds": dt, "moves": int(moves), "efficiency": stats.efficiency(e, dt), "intervals": steps}
 
 
-def _tau_for(system, a, e_trial, jumps, seed):
-    """Interval length giving the single grid about `jumps` jumps per walker:
-    jumps / <b> with <b> the mean total rate of 256 equilibrated walkers."""
-    import torch
-
+def _tau_for(system, a, spacing, jumps, seed):
+    """Interval length giving about ``jumps`` jumps per walker on this
+    lattice: jumps / <b>, <b> the mean total rate over 256 start
+    configurations (one stateless evaluation)."""
     import lrdmc_synth as S
 
-    g = LrdmcSystem(system)
-    g.init_walkers(torch.tensor(S.initial_positions(system, 256, seed), device="cuda"), seed=seed, tau=1e-6,
-                   e_trial=e_trial, recompute_every=5, trace_capacity=4)
-    g.step(2, a, Spacing(SINGLE))
-    b = g.walkers()["b"]
-    return float(jumps / np.mean(b))
+    from .batch import tau_for
+
+    import paper_1909_01589_gb300 as pkg
+
+    x = S.initial_positions(system, 256, seed)
+    return tau_for(pkg, system, a, spacing, jumps, x, S.random_rotations(256, seed + 1))
 
 
 def single_vs_double(names=("He", "Ne", "Ar", "Kr"), alpha=3.5, steps=1000, equil=200, seed=1):
+    """Every lattice gets its own interval length (about 10 jumps per walker
+    per interval, so that the intervals are not dominated by the longest
+    walker) and the same total projection time: the single grid runs
+    ``steps`` intervals of tau_single, each double grid steps * tau_single /
+    tau_double intervals (equilibration alike)."""
     import lrdmc_synth as S
 
     rows = []
@@ -92,19 +96,27 @@ def single_vs_double(names=("He", "Ne", "Ar", "Kr"), alpha=3.5, steps=1000, equi
         W, e_trial, jumps = DEFAULTS[name]
         g = LrdmcSystem(system)
         ratio, rc = g.spacing_params(a, Spacing(THIS_WORK))
-        tau = _tau_for(system, a, e_trial, jumps, seed)
-        res = {}
+        res, taus = {}, {}
         for label, sp in (("single", Spacing(SINGLE)), ("double_this_work", Spacing(THIS_WORK)),
                           ("double_previous", Spacing(PREVIOUS))):
-            res[label] = run(system, a, sp, W, steps, equil, tau, e_trial, seed)
+            taus[label] = _tau_for(system, a, sp, jumps, seed)
+        for label, sp in (("single", Spacing(SINGLE)), ("double_this_work", Spacing(THIS_WORK)),
+                          ("double_previous", Spacing(PREVIOUS))):
+            f = taus["single"] / taus[label]
+            n_steps = max(64, int(round(steps * f)))
+            n_equil = max(16, int(round(equil * f)))
+            res[label] = run(system, a, sp, W, n_steps, n_equil, taus[label], e_trial, seed)
+            res[label]["tau"] = taus[label]
         s = res["single"]
-        row = {"system": name, "Z": Z, "a": a, "alpha": alpha, "aprime_over_a": ratio, "rc": rc, "tau": tau,
-               "walkers": W, **{k: v for k, v in res.items()}}
+        row = {"system": name, "Z": Z, "a": a, "alpha": alpha, "aprime_over_a": ratio, "rc": rc,
+               "tau": taus["single"], "walkers": W, **{k: v for k, v in res.items()}}
         for label in ("double_this_work", "double_previous"):
             d = res[label]
             row[label + "_bias_mHa"] = 1e3 * (d["energy"] - s["energy"])
             row[label + "_bias_err_mHa"] = 1e3 * float(np.hypot(d["error"], s["error"]))
-            row[label + "_acceleration_jumps"] = s["jumps_per_interval"] / max(d["jumps_per_interval"], 1e-12)
+            # jumps per unit projection time
+            row[label + "_acceleration_jumps"] = (s["jumps_per_interval"] / s["tau"]) / max(
+                d["jumps_per_interval"] / d["tau"], 1e-300)
             row[label + "_acceleration_efficiency"] = d["efficiency"] / s["efficiency"]
         rows.append(row)
     return rows
@@ -119,8 +131,8 @@ def summarize(rows):
     x of a least-squares fit cost ~ Z^x over the systems."""
     out = []
     for r in rows:
-        W, tau = r["walkers"], r["tau"]
-        cost = {k: r[k]["seconds"] / (W * r[k]["intervals"] * tau)
+        W = r["walkers"]
+        cost = {k: r[k]["seconds"] / (W * r[k]["intervals"] * r[k].get("tau", r["tau"]))
                 for k in ("single", "double_this_work", "double_previous")}
         out.append({"system": r["system"], "Z": r["Z"], "cost": cost,
                     "acceleration_time": cost["single"] / cost["double_this_work"],
@@ -136,7 +148,7 @@ def summarize(rows):
 def markdown(rows):
     derived, fit = summarize(rows)
     lines = ["| system | Z | a | a'/a | E single (Ha) | bias this work (mHa) | bias previous (mHa) | "
-             "jumps single/double | GPU time single/double | efficiency ratio |",
+             "jumps per unit time single/double | GPU time per unit time single/double | efficiency ratio |",
              "|---|---|---|---|---|---|---|---|---|---|"]
     for r, d in zip(rows, derived):
         lines.append(
