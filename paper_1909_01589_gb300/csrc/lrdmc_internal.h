@@ -113,6 +113,7 @@ struct Layout {
   int head;       // doubles of shared memory per block before the warp regions
   int smem_warp;  // doubles of shared memory per warp
   int smem_block_bytes;
+  int n_pc;       // electron pairs with a cached distance and projections (0: no cache)
 };
 
 Layout make_layout(const SysDev& S);

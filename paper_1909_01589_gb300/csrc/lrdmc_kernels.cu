@@ -30,6 +30,29 @@ namespace lrdmc {
 // ----------------------------------------------------------------------------
 // Counter-based random numbers: Philox4x64-10 (Salmon, Moraes, Dror, Shaw,
 // SC'11), key (seed, 0), counter (slot, interval, iteration, tag).
+// Inlining of the large, once-per-jump or rarely executed parts of the
+// interval loop (tuning switches; the default inlines everything):
+//   LRDMC_NOINLINE_COLD  the Gauss-Jordan recompute (every few intervals)
+//   LRDMC_NOINLINE_JUMP  the Sherman-Morrison update and the new rotation
+//   LRDMC_NOINLINE_EL    the local-energy parts of an evaluation
+#ifdef LRDMC_NOINLINE_COLD
+#define LRDMC_COLD __noinline__
+#else
+#define LRDMC_COLD
+#endif
+#ifdef LRDMC_NOINLINE_JUMP
+#define LRDMC_JUMP __noinline__
+#define LRDMC_JUMP_INLINE __noinline__
+#else
+#define LRDMC_JUMP
+#define LRDMC_JUMP_INLINE __forceinline__
+#endif
+#ifdef LRDMC_NOINLINE_EL
+#define LRDMC_EL __noinline__
+#else
+#define LRDMC_EL
+#endif
+
 // ----------------------------------------------------------------------------
 __device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1)
 {
@@ -107,7 +130,7 @@ __device__ void rotation_matrix(double u1, double u2, double u3, double* R)
 // DF64 mode: double-float (the FP32 pipe), accurate to ~1e-15. FP32 mode:
 // single precision. All lanes must call it; R (double) goes to shared memory.
 template <int PREC>
-__device__ __forceinline__ void rotation_matrix_warp(const uint64_t* bits, double* R, int lane, const SysDev& S)
+__device__ LRDMC_JUMP_INLINE void rotation_matrix_warp(const uint64_t* bits, double* R, int lane, const SysDev& S)
 {
   double x, y, z, w;
   if (PREC == LRDMC_PRECISION_FP32) {
@@ -137,28 +160,36 @@ __device__ __forceinline__ void rotation_matrix_warp(const uint64_t* bits, doubl
     return;
   }
   if (PREC == LRDMC_PRECISION_DF64) {
+    // lanes 0 and 1: sqrt(1 - u1) and sqrt(u1); lanes 2 and 3: sincospi of
+    // 2 u2 and 2 u3 - one pass each, the operand chosen per lane
     df a = df_make(0.0f, 0.0f), c = df_make(0.0f, 0.0f);
-    if (lane == 0) a = df_sqrt(df_add_f(df_neg(df_u01(bits[0])), 1.0f));
-    else if (lane == 1) a = df_sqrt(df_u01(bits[0]));
-    else if (lane == 2) df_sincospi(df_mul_f(df_u01(bits[1]), 2.0f), S.D.inv_fact, S.D.half_pi, &a, &c);
-    else if (lane == 3) df_sincospi(df_mul_f(df_u01(bits[2]), 2.0f), S.D.inv_fact, S.D.half_pi, &a, &c);
+    if (lane < 2) {
+      const df u = df_u01(bits[0]);
+      a = df_sqrt(lane == 0 ? df_add_f(df_neg(u), 1.0f) : u);
+    } else if (lane < 4) {
+      df_sincospi(df_mul_f(df_u01(bits[lane - 1]), 2.0f), S.D.inv_fact, S.D.half_pi, &a, &c);
+    }
     typedef Ar<df> A;
     df s1 = A::shfl(a, 0), s2 = A::shfl(a, 1), sa = A::shfl(a, 2), ca = A::shfl(c, 2);
     df sb = A::shfl(a, 3), cb = A::shfl(c, 3);
-    df qx = df_mul(s1, sa), qy = df_mul(s1, ca), qz = df_mul(s2, sb), qw = df_mul(s2, cb);
-    df v = df_make(0.0f, 0.0f);
-    switch (lane) {
-      case 0: v = df_add_f(df_mul_f(df_add(df_sqr(qy), df_sqr(qz)), -2.0f), 1.0f); break;
-      case 1: v = df_mul_f(df_sub(df_mul(qx, qy), df_mul(qz, qw)), 2.0f); break;
-      case 2: v = df_mul_f(df_add(df_mul(qx, qz), df_mul(qy, qw)), 2.0f); break;
-      case 3: v = df_mul_f(df_add(df_mul(qx, qy), df_mul(qz, qw)), 2.0f); break;
-      case 4: v = df_add_f(df_mul_f(df_add(df_sqr(qx), df_sqr(qz)), -2.0f), 1.0f); break;
-      case 5: v = df_mul_f(df_sub(df_mul(qy, qz), df_mul(qx, qw)), 2.0f); break;
-      case 6: v = df_mul_f(df_sub(df_mul(qx, qz), df_mul(qy, qw)), 2.0f); break;
-      case 7: v = df_mul_f(df_add(df_mul(qy, qz), df_mul(qx, qw)), 2.0f); break;
-      case 8: v = df_add_f(df_mul_f(df_add(df_sqr(qx), df_sqr(qy)), -2.0f), 1.0f); break;
-      default: break;
-    }
+    const df q[4] = {df_mul(s1, sa), df_mul(s1, ca), df_mul(s2, sb), df_mul(s2, cb)};  // x, y, z, w
+    // entry (row, col) = lane: delta + 2 (s1 q[a] q[b] + s2 q[c] q[d]); the
+    // operand indices and signs of the nine entries, packed per lane
+    //   R00 = 1 - 2(yy + zz)  R01 = 2(xy - zw)  R02 = 2(xz + yw)
+    //   R10 = 2(xy + zw)  R11 = 1 - 2(xx + zz)  R12 = 2(yz - xw)
+    //   R20 = 2(xz - yw)  R21 = 2(yz + xw)  R22 = 1 - 2(xx + yy)
+    const int L = lane < 9 ? lane : 0;
+    const unsigned long long ka = 0x10100001ull, kb = 0x22201211ull;
+    const unsigned long long kc = 0x101022122ull, kd = 0x133323332ull;
+    const unsigned ia = (ka >> (4 * L)) & 0xF, ib = (kb >> (4 * L)) & 0xF;
+    const unsigned ic = (kc >> (4 * L)) & 0xF, id = (kd >> (4 * L)) & 0xF;
+    const bool diag = L == 0 || L == 4 || L == 8;
+    const bool minus2 = L == 1 || L == 5 || L == 6;
+    auto pick = [&](unsigned k) { return k == 0 ? q[0] : k == 1 ? q[1] : k == 2 ? q[2] : q[3]; };
+    df t1 = df_mul(pick(ia), pick(ib)), t2 = df_mul(pick(ic), pick(id));
+    df v;
+    if (diag) v = df_add_f(df_mul_f(df_add(t1, t2), -2.0f), 1.0f);
+    else v = df_mul_f(minus2 ? df_sub(t1, t2) : df_add(t1, t2), 2.0f);
     if (lane < 9) R[lane] = df_to_double(v);
     return;
   }
@@ -480,7 +511,9 @@ struct WarpMem {
   df* vd;       // [N][n_ao]   (aliases v)
   df* Sd;       // [N]         (aliases Ssum)
   df* Rd;       // [12]
+  df* pc;       // [n_pc][4] pair cache: |r_a - r_b|^2 and e_k . (r_a - r_b), a < b
   double* scr;  // scratch
+  int n_pc;     // pairs in the cache (0: no cache)
 };
 
 __device__ __forceinline__ WarpMem warp_mem(const Layout& Lo, const SysDev& S, double* base)
@@ -499,7 +532,9 @@ __device__ __forceinline__ WarpMem warp_mem(const Layout& Lo, const SysDev& S, d
   m.Sd = reinterpret_cast<df*>(m.Ssum);
   m.xd = reinterpret_cast<df*>(m.Ssum + Lo.N);
   m.Rd = m.xd + 3 * Lo.N;
-  m.scr = reinterpret_cast<double*>(m.Rd + 12);
+  m.pc = m.Rd + 12;
+  m.scr = reinterpret_cast<double*>(m.pc + 4 * Lo.n_pc);
+  m.n_pc = Lo.n_pc;
   return m;
 }
 
@@ -528,7 +563,7 @@ __device__ __forceinline__ BlockMem block_mem(const SysDev& S, double* smem)
 // partial pivoting (warp-cooperative). A[l][m] = phi_m(r_l); the inverse is
 // stored as Ainv[m][l]. Returns false for a singular matrix (below).
 // ----------------------------------------------------------------------------
-__device__ bool warp_inverse(const SysDev& S, const double* sC, const double* sx, int spin,
+__device__ LRDMC_COLD bool warp_inverse(const SysDev& S, const double* sC, const double* sx, int spin,
                              double* Ainv, double* scr, int lane)
 {
   const int n = spin == 0 ? S.n_up : S.n_dn;
@@ -876,6 +911,58 @@ __device__ void nucleus_terms_m(const SysDev& S, const df* v, const NT p[3], con
   }
 }
 
+// Index of the electron pair (a, b), a < b, in the pair cache.
+__device__ __forceinline__ int pair_index(int N, int a, int b) { return a * N - a * (a + 1) / 2 + (b - a - 1); }
+
+// The pair cache of one evaluation: for every pair a < b, D = |r_a - r_b|^2
+// and P_k = e_k . (r_a - r_b) on the evaluation's rotated axes. A lattice
+// move r_i -> r_i + h e_k then has |r' - r_j|^2 = D + 2 h s P_k + h^2, with
+// s = +1 for i = a and -1 for i = b.
+template <class NT>
+__device__ void fill_pair_cache(const SysDev& S, const WarpMem& wm, int lane)
+{
+  typedef Ar<NT> A;
+  const int N = S.N;
+  for (int q = lane; q < wm.n_pc; q += 32) {
+    int a = 0, base = 0;
+    while (base + (N - 1 - a) <= q) { base += N - 1 - a; ++a; }
+    const int b = a + 1 + (q - base);
+    NT d[3];
+    for (int k = 0; k < 3; ++k) d[k] = A::sub_fast(A::c(wm.xd[3 * a + k]), A::c(wm.xd[3 * b + k]));
+    df* e = &wm.pc[4 * q];
+    e[0] = A::store(dot3<NT>(d[0], d[1], d[2]));
+    for (int k = 0; k < 3; ++k) {
+      NT pk = A::add(A::add(A::mul(A::c(wm.Rd[k]), d[0]), A::mul(A::c(wm.Rd[3 + k]), d[1])),
+                     A::mul(A::c(wm.Rd[6 + k]), d[2]));
+      e[1 + k] = A::store(pk);
+    }
+  }
+}
+
+// sum_{j != i} u_ee(|r_i + h e_k - r_j|) from the pair cache (h carries
+// the sign of the move, h2 = h^2); the Pade terms as one running fraction.
+template <class NT>
+__device__ NT jastrow_ee_cached_m(const SysDev& S, const df* pc, int i, int k, NT h, NT h2)
+{
+  typedef Ar<NT> A;
+  NT num = A::zero(), den = A::one(), nn = A::zero();
+  const int si = spin_of(S, i), N = S.N;
+  const NT b = A::c(S.D.b_ee), cp = A::c(S.D.c_par), ca = A::c(S.D.c_anti);
+  for (int j = 0; j < N; ++j) {
+    if (j == i) continue;
+    const df* e = &pc[4 * pair_index(N, min(i, j), max(i, j))];
+    NT hp = A::mul(h, A::c(e[1 + k]));
+    hp = A::mul_f(hp, i < j ? 2.0f : -2.0f);
+    NT r = A::sqrt(A::add(A::add(A::c(e[0]), hp), h2));
+    NT c = (spin_of(S, j) == si) ? cp : ca;
+    NT dj = A::add_f(A::mul(b, r), 1.0f);
+    num = A::add_fast(A::mul(num, dj), A::mul(A::mul(c, r), den));
+    den = A::mul(den, dj);
+    if (S.nj_on) nn = A::add(nn, nj_value_m<NT>(S, nj_ch_ee(S, i, j), r));
+  }
+  return A::add(A::div(num, den), nn);
+}
+
 // sum_{j != i} u_ee(|p - r_j|): the Pade terms c r/(1 + b r) (all of one
 // sign) are summed as one running fraction num/den, so one division serves
 // all partners.
@@ -970,7 +1057,7 @@ __device__ __forceinline__ void el_zero(ElParts<NT>& o)
 }
 
 template <class NT>
-__device__ void el_parts_m(const SysDev& S, const WarpMem& wm, int i, int part, int L, const BlockMem& bm,
+__device__ LRDMC_EL void el_parts_m(const SysDev& S, const WarpMem& wm, int i, int part, int L, const BlockMem& bm,
                            ElParts<NT>& o)
 {
   typedef Ar<NT> A;
@@ -1142,6 +1229,8 @@ __device__ void warp_eval_m(const SysDev& S, const double* sC, const LatDev& L, 
   for (int j = lane; j < 3 * N; j += 32) wm.xd[j] = A::store(A::from_double(wm.x[j]));
   if (lane < 9) wm.Rd[lane] = A::store(A::from_double(wm.R[lane]));
   __syncwarp();
+  constexpr bool kUsePairCache = sizeof(NT) == sizeof(df);
+  if (kUsePairCache) fill_pair_cache<NT>(S, wm, lane);
   // local energy: Lp lanes per electron share its shells, electrons and nuclei
   NT epart = A::zero();
   if (N <= 32) {
@@ -1182,7 +1271,11 @@ __device__ void warp_eval_m(const SysDev& S, const double* sC, const LatDev& L, 
     NT p[3] = {A::add(ri[0], A::mul(h, e0)), A::add(ri[1], A::mul(h, e1)), A::add(ri[2], A::mul(h, e2))};
     NT rdet, jen;
     nucleus_terms_m<NT>(S, &wm.vd[i * nao], p, bm, rdet, jen);
-    NT dJ = A::sub(A::add(jastrow_ee_m<NT>(S, wm.xd, i, p), jen), A::c(wm.Sd[i]));
+    // the pair cache pays in double-float arithmetic only (single precision
+    // recomputes a distance faster than it reads it back)
+    NT jee = (kUsePairCache && wm.n_pc) ? jastrow_ee_cached_m<NT>(S, wm.pc, i, k, h, A::sqr(h))
+                                        : jastrow_ee_m<NT>(S, wm.xd, i, p);
+    NT dJ = A::sub(A::add(jee, jen), A::c(wm.Sd[i]));
     NT rho = A::mul(rdet, A::exp(dJ, S.D.exp.K, bm.tab));
     NT w = A::one();
     if (G == 2) {
@@ -1282,7 +1375,7 @@ __device__ void ao_values_df_out(const SysDev& S, const df* pd, df* out, int lan
 // orbitals at the new position, y = phi A^-1, ratio = y_l, and
 // the rank-one update, with the spin block read from and written back to
 // its IEEE-double copy. pd: the new position as a double-float.
-__device__ bool warp_sm_update_df(const SysDev& S, const BlockMem& bm, const WarpMem& wm, int i, const df* pd,
+__device__ LRDMC_JUMP bool warp_sm_update_df(const SysDev& S, const BlockMem& bm, const WarpMem& wm, int i, const df* pd,
                                   int lane)
 {
   const int nu = S.n_up;
@@ -1320,7 +1413,7 @@ __device__ bool warp_sm_update_df(const SysDev& S, const BlockMem& bm, const War
 }
 
 template <int PREC>
-__device__ bool warp_sm_update(const SysDev& S, const double* sC, const WarpMem& wm, int i,
+__device__ LRDMC_JUMP bool warp_sm_update(const SysDev& S, const double* sC, const WarpMem& wm, int i,
                                const double* p, int lane)
 {
   const int nu = S.n_up;
@@ -1816,8 +1909,11 @@ Layout make_layout(const SysDev& S)
   int scr = 2 * n * n + n * S.n_ao;          // Gauss-Jordan + orbital rows
   int scr_sm = S.n_ao + 3 * n + n * n;       // Sherman-Morrison (FP64 or double-float)
   if (scr_sm > scr) scr = scr_sm;
+  // the pair cache of the FP32-pipe evaluations, up to 24 electrons (beyond,
+  // 4 df per pair would cost blocks per SM)
+  Lo.n_pc = S.N <= 24 ? S.N * (S.N - 1) / 2 : 0;
   Lo.smem_warp = 3 * S.N + S.n_up * S.n_up + S.n_dn * S.n_dn + 12 + Lo.P_max + S.N * S.n_ao + S.N +
-                 (3 * S.N + 12) + scr;
+                 (3 * S.N + 12) + 4 * Lo.n_pc + scr;
   Lo.smem_warp = (Lo.smem_warp + 1) & ~1;
   Lo.head = ((2 * S.n_ao * S.n_mo + (S.n_ao * S.n_mo + 1) / 2 + 64) + 1) & ~1;
   Lo.smem_block_bytes = (int)sizeof(double) * (Lo.head + kWarpsPerBlock * Lo.smem_warp);
