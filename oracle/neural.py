@@ -199,7 +199,7 @@ def loss_and_grad(theta, spec, x, n_up, nuc_xyz, grad_base, e_base, bf16=True):
     EL, J = energy_terms(th, spec, x, n_up, nuc_xyz, grad_base, e_base, bf16)
     loss = variance_loss(EL, J)
     loss.backward()
-    return float(loss), th.grad.numpy().copy(), EL.detach().numpy(), J.detach().numpy()
+    return float(loss.detach()), th.grad.numpy().copy(), EL.detach().numpy(), J.detach().numpy()
 
 
 def base_terms(osys, x):

@@ -17,6 +17,8 @@ paper's tables.
 
 Usage: python -m paper_1909_01589_gb300.experiments [--systems He,Ne,Ar,Kr]
        [--steps 1000] [--out results/single_vs_double.json]
+       python -m paper_1909_01589_gb300.experiments --neural --systems Ne,Ar
+       [--steps 600] [--out results/neural_vs_pade.json]
 """
 from __future__ import annotations
 
@@ -122,6 +124,81 @@ def single_vs_double(names=("He", "Ne", "Ar", "Kr"), alpha=3.5, steps=1000, equi
     return rows
 
 
+# system: (e_trial, a). Ar at a = 0.2 (a Z = 3.6, a lattice coarser than its
+# core) gives no stable projection with the synthetic Gaussian-basis trial
+# function (the population collapses to about -1650 Ha); a = 0.05 (a Z = 0.9)
+NEURAL_DEFAULTS = {"Ne": (-128.9, 0.2), "Ar": (-527.5, 0.05)}
+
+
+def neural_vs_pade(names=("Ne", "Ar"), W=16384, steps=600, equil=150, n_train=1 << 20, train_steps=600,
+                   seed=3):
+    """The neural pair Jastrow against the plain Pade Jastrow: configurations
+    from a plain projection (a, this work's double grid, W walkers), training
+    on the GPU, then a projection with and without the tabulated term over
+    the same number of intervals. Reported per system: held-out variance of
+    E_L, the walkers' E_L variance in the projection, energy and blocked
+    error, walker-moves/s and the efficiency 1/(sigma^2 t)."""
+    import torch
+
+    import lrdmc_synth as S
+
+    from . import neural as N
+
+    rows = []
+    sp = Spacing(THIS_WORK)
+    for name in names:
+        system = S.make_system(name)
+        e_trial, a = NEURAL_DEFAULTS[name]
+        tau = _tau_for(system, a, sp, 10.0, seed)
+        spec = S.default_neural_spec(system)
+        plain = LrdmcSystem(system)
+        t0 = time.perf_counter()
+        x = N.sample_configurations(plain, S.initial_positions(system, W, seed), n_train, a, sp, tau, e_trial,
+                                    seed=seed, equil=equil)
+        grad, e = plain.base_terms(x)
+        n_tr = len(x) * 7 // 8
+        params, hist = N.train(plain, spec, S.neural_init(spec, seed), x[:n_tr], grad[:n_tr], e[:n_tr],
+                               steps=train_steps, seed=seed + 1, log_every=100)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        el, j = N.evaluate(plain, spec, params, x[n_tr:], grad[n_tr:], e[n_tr:])
+        row = {"system": name, "walkers": W, "a": a, "tau": tau, "train_configs": n_tr, "train_steps": train_steps,
+               "train_seconds": t_train, "train_loss": hist,
+               "heldout_var_pade": float(torch.var(e[n_tr:])),
+               "heldout_var_neural": float(N.variance_loss(el, j, clip=0.0))}
+        x0 = S.initial_positions(system, W, seed + 7)
+        for label, use in (("pade", False), ("neural", True)):
+            g = LrdmcSystem(system)
+            if use:
+                g.set_neural_jastrow(spec, params.cpu().numpy())
+            g.init_walkers(torch.tensor(x0, device="cuda"), seed=seed + 8, tau=tau, e_trial=e_trial,
+                           recompute_every=5, trace_capacity=steps + equil + 4)
+            g.step(equil, a, sp)
+            g.sync()
+            torch.cuda.synchronize()
+            m0 = g.moves()
+            t1 = time.perf_counter()
+            g.step(steps, a, sp)
+            g.sync()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t1
+            et, wt, jt = g.energy_trace()
+            et, wt = et[equil:], wt[equil:]
+            err, _ = stats.reblock(et)
+            row[label] = {"energy": stats.energy_estimate(et, wt, 0), "error": err, "seconds": dt,
+                          "moves_per_s": (g.moves() - m0) / dt, "efficiency": stats.efficiency(et, dt),
+                          "var_EL_walkers": float(np.var(g.walkers()["EL"]))}
+        row["efficiency_ratio"] = row["neural"]["efficiency"] / row["pade"]["efficiency"]
+        rows.append(row)
+        print(f"{name}: held-out var {row['heldout_var_pade']:.2f} -> {row['heldout_var_neural']:.2f}; "
+              f"walker var {row['pade']['var_EL_walkers']:.2f} -> {row['neural']['var_EL_walkers']:.2f}; "
+              f"E {row['pade']['energy']:.4f}({1e3 * row['pade']['error']:.1f}) -> "
+              f"{row['neural']['energy']:.4f}({1e3 * row['neural']['error']:.1f}); "
+              f"moves/s {row['pade']['moves_per_s']:.3g} -> {row['neural']['moves_per_s']:.3g}; "
+              f"efficiency x{row['efficiency_ratio']:.2f}", flush=True)
+    return rows
+
+
 def summarize(rows):
     """Derived quantities of the Fig. 2 analogue: GPU seconds per walker per
     unit of projection time (single grid, this work's double grid, the
@@ -173,7 +250,13 @@ def main():
     ap.add_argument("--alpha", type=float, default=3.5)
     ap.add_argument("--out", default="results/single_vs_double.json")
     ap.add_argument("--summarize", nargs="*", help="only write the markdown table of these result files")
+    ap.add_argument("--neural", action="store_true", help="the neural Jastrow against Pade instead")
     args = ap.parse_args()
+    if args.neural:
+        rows = neural_vs_pade(args.systems.split(","), steps=args.steps, equil=args.equil)
+        os.makedirs(os.path.dirname(args.out) or ".", exist_ok=True)
+        json.dump(rows, open(args.out, "w"), indent=1)
+        return
     if args.summarize:
         rows = []
         for f in args.summarize:

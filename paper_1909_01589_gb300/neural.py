@@ -111,7 +111,7 @@ def train(lsys, spec, params0, x, grad_base, e_base, steps=400, batch=1 << 14, l
         loss.backward()
         opt.step()
         if log_every and it % log_every == 0:
-            hist.append((it, float(loss)))
+            hist.append((it, float(loss.detach())))
     return params.detach(), hist
 
 
