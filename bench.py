@@ -492,7 +492,11 @@ def _read_traffic(df64=True):
     return d.get("dram_bytes_per_launch")
 
 
-def _oracle_rate(n_walkers, budget_s, threads):
+def _oracle_rate(n_walkers, budget_s, threads, steps=None, warmup=1):
+    """The oracle's walker-moves/s on n_walkers of the workload: ``warmup``
+    untimed intervals (the first one includes the first evaluation), then
+    exactly ``steps`` timed intervals, or as many as fit in budget_s seconds
+    when steps is None."""
     import oracle
 
     system = S.neon()
@@ -501,15 +505,15 @@ def _oracle_rate(n_walkers, budget_s, threads):
     pop = oracle.OraclePopulation(o, x0, seed=SEED, tau=WORKLOAD["tau"], e_trial=WORKLOAD["e_trial"],
                                   recompute_every=WORKLOAD["recompute_every"])
     lat = oracle.lattice_for(system, WORKLOAD["a"], oracle.THIS_WORK)
-    pop.step(lat, 1, threads)  # first evaluation and one interval, untimed
+    pop.step(lat, max(1, warmup), threads)
     m0 = pop.moves
     t0 = time.perf_counter()
-    steps = 0
-    while time.perf_counter() - t0 < budget_s:
+    n = 0
+    while (n < steps) if steps is not None else (time.perf_counter() - t0 < budget_s):
         pop.step(lat, 1, threads)
-        steps += 1
+        n += 1
     dt = time.perf_counter() - t0
-    return (pop.moves - m0) / dt, steps, dt
+    return (pop.moves - m0) / dt, n, dt
 
 
 def cpu_baseline(args):
@@ -522,13 +526,15 @@ def cpu_baseline(args):
 
 
 def run_reference(args):
+    """The oracle as the reference arm: W warm-up and exactly K timed
+    intervals, each one interval of 1024 of the workload's 4096 walkers on
+    the host cores (OpenMP over walkers)."""
     rank, world, _ = _env_rank()
     if rank != 0:
         return
     threads = os.cpu_count() or 1
     W = 1024
-    _oracle_rate(W, 2.0, threads)  # warm-up
-    rate, steps, dt = _oracle_rate(W, args.cpu_seconds, threads)
+    rate, steps, dt = _oracle_rate(W, 0.0, threads, steps=args.steps, warmup=args.warmup)
     out = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": "walker-moves/s", "n_gpus": world,
         "steps": steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(steps, 1),
@@ -537,7 +543,8 @@ def run_reference(args):
         "config": {"workload": "Ne all-electron, 4096 walkers, a=0.2 bohr, smart double grid (this work), "
                                "tau=0.025, FP64", **WORKLOAD},
         "cpu_baseline": {"value": rate, "unit": "walker-moves/s", "cores": threads, "kind": "oracle",
-                         "sample": f"Ne, {W} walkers per interval, {steps} intervals in {dt:.1f} s"},
+                         "sample": f"Ne, {W} of the 4096 walkers per step (one interval), {steps} timed "
+                                   f"intervals in {dt:.1f} s"},
         "e2e": {"value": rate, "unit": "walker-moves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
