@@ -512,6 +512,7 @@ struct WarpMem {
   df* Sd;       // [N]         (aliases Ssum)
   df* Rd;       // [12]
   df* pc;       // [n_pc][4] pair cache: |r_a - r_b|^2 and e_k . (r_a - r_b), a < b
+  df* enc;      // [N][n_nuc][8] electron-nucleus cache: d, |d|^2, e_k . d
   double* scr;  // scratch
   int n_pc;     // pairs in the cache (0: no cache)
 };
@@ -533,7 +534,8 @@ __device__ __forceinline__ WarpMem warp_mem(const Layout& Lo, const SysDev& S, d
   m.xd = reinterpret_cast<df*>(m.Ssum + Lo.N);
   m.Rd = m.xd + 3 * Lo.N;
   m.pc = m.Rd + 12;
-  m.scr = reinterpret_cast<double*>(m.pc + 4 * Lo.n_pc);
+  m.enc = m.pc + 4 * Lo.n_pc;
+  m.scr = reinterpret_cast<double*>(m.enc + 8 * Lo.N * S.n_nuc);
   m.n_pc = Lo.n_pc;
   return m;
 }
@@ -842,6 +844,16 @@ __device__ __forceinline__ NT nj_value_m(const SysDev& S, int c, NT r)
   df E[8];
   nj_load(nj_cell_m<NT>(S, c, rf), E);
   const NT t = A::mul(A::sub(r, A::c(E[0])), A::c(E[1]));
+  if (sizeof(NT) == sizeof(df)) {
+    // the cubic to quintic terms are below 1e-5 of the value on these narrow
+    // cells (c_q ~ w^q g^(q)/q!), so single precision carries them to well
+    // below the double-float rounding of the sum; the low orders in NT
+    const float tf = A::approx(t);
+    const float hi = fmaf(fmaf(E[7].hi, tf, E[6].hi), tf, E[5].hi);
+    NT v = A::add(A::c(E[4]), A::mul_f(t, hi));
+    v = A::add(A::mul(v, t), A::c(E[3]));
+    return A::add(A::mul(v, t), A::c(E[2]));
+  }
   NT v = A::c(E[7]);
 #pragma unroll
   for (int q = 6; q >= 2; --q) v = A::add(A::mul(v, t), A::c(E[q]));
@@ -877,6 +889,38 @@ __device__ __forceinline__ void nj_value3_m(const SysDev& S, int c, NT r, NT& g,
   g2 = A::mul(d2, A::sqr(iw));
 }
 
+// One nucleus's part of a lattice move: the e-n Jastrow terms (Pade and,
+// when set, neural) into jen and the basis functions centred on it,
+// contracted with the projected inverse column v, into rdet. d = r' - R_I,
+// r2 = |d|^2.
+template <class NT>
+__device__ __forceinline__ void nucleus_term_m(const SysDev& S, const df* v, int I, const NT d[3], NT r2,
+                                               const BlockMem& bm, NT& rdet, NT& jen)
+{
+  typedef Ar<NT> A;
+  NT r = A::sqrt(r2);
+  if (S.en_b1[I] != 0.0)
+    jen = A::sub(jen, A::div(A::mul(A::c(S.D.en_b1[I]), r), A::add_f(A::mul(A::c(S.D.en_b2), r), 1.0f)));
+  if (S.nj_on) jen = A::add(jen, nj_value_m<NT>(S, 2 + S.nj_species[I], r));
+  NT e = A::zero();
+  for (int q = S.nuc_shell_begin[I]; q < S.nuc_shell_begin[I + 1]; ++q) {
+    const ShellDev& sh = S.sh[q];
+    const DfShell& dsh = S.D.sh[q];
+    if (sh.kind == 0 && !sh.same_exp) e = A::exp(A::neg(A::mul(A::c(dsh.zeta), r)), S.D.exp.K, bm.tab);
+    NT Rv = radial_value_m<NT>(S, sh, dsh, r, r2, e, bm);
+    NT part;
+    if (sh.l == 0) {
+      part = A::c(v[sh.ao_offset]);
+    } else {
+      NT Sv[5];
+      int nf = solid_m<NT>(sh.l, d, Sv);
+      part = A::zero();
+      for (int f = 0; f < nf; ++f) part = A::add(part, A::mul(A::c(v[sh.ao_offset + f]), Sv[f]));
+    }
+    rdet = A::add(rdet, A::mul(part, Rv));
+  }
+}
+
 template <class NT>
 __device__ void nucleus_terms_m(const SysDev& S, const df* v, const NT p[3], const BlockMem& bm, NT& rdet, NT& jen)
 {
@@ -886,29 +930,66 @@ __device__ void nucleus_terms_m(const SysDev& S, const df* v, const NT p[3], con
   for (int I = 0; I < S.n_nuc; ++I) {
     NT d[3] = {A::sub_fast(p[0], A::c(S.D.nuc[I][0])), A::sub_fast(p[1], A::c(S.D.nuc[I][1])),
                A::sub_fast(p[2], A::c(S.D.nuc[I][2]))};
-    NT r2 = dot3<NT>(d[0], d[1], d[2]);
-    NT r = A::sqrt(r2);
-    if (S.en_b1[I] != 0.0)
-      jen = A::sub(jen, A::div(A::mul(A::c(S.D.en_b1[I]), r), A::add_f(A::mul(A::c(S.D.en_b2), r), 1.0f)));
-    if (S.nj_on) jen = A::add(jen, nj_value_m<NT>(S, 2 + S.nj_species[I], r));
-    NT e = A::zero();
-    for (int q = S.nuc_shell_begin[I]; q < S.nuc_shell_begin[I + 1]; ++q) {
-      const ShellDev& sh = S.sh[q];
-      const DfShell& dsh = S.D.sh[q];
-      if (sh.kind == 0 && !sh.same_exp) e = A::exp(A::neg(A::mul(A::c(dsh.zeta), r)), S.D.exp.K, bm.tab);
-      NT Rv = radial_value_m<NT>(S, sh, dsh, r, r2, e, bm);
-      NT part;
-      if (sh.l == 0) {
-        part = A::c(v[sh.ao_offset]);
-      } else {
-        NT Sv[5];
-        int nf = solid_m<NT>(sh.l, d, Sv);
-        part = A::zero();
-        for (int f = 0; f < nf; ++f) part = A::add(part, A::mul(A::c(v[sh.ao_offset + f]), Sv[f]));
-      }
-      rdet = A::add(rdet, A::mul(part, Rv));
+    nucleus_term_m<NT>(S, v, I, d, dot3<NT>(d[0], d[1], d[2]), bm, rdet, jen);
+  }
+}
+
+// The electron-nucleus cache of one evaluation: for electron i and nucleus
+// I, d = r_i - R_I, |d|^2 and e_k . d on the rotated axes (8 double-floats,
+// the last unused). A move r_i -> r_i + h e_k has r' - R_I = d + h e_k,
+// |r' - R_I|^2 = |d|^2 + 2 h (e_k . d) + h^2, and its bond midpoint
+// |d|^2 + h (e_k . d) + h^2/4.
+template <class NT>
+__device__ void fill_en_cache(const SysDev& S, const WarpMem& wm, int lane)
+{
+  typedef Ar<NT> A;
+  const int n = S.N * S.n_nuc;
+  for (int q = lane; q < n; q += 32) {
+    const int i = q / S.n_nuc, I = q - i * S.n_nuc;
+    NT d[3];
+    for (int k = 0; k < 3; ++k) d[k] = A::sub_fast(A::c(wm.xd[3 * i + k]), A::c(S.D.nuc[I][k]));
+    df* e = &wm.enc[8 * q];
+    for (int k = 0; k < 3; ++k) e[k] = A::store(d[k]);
+    e[3] = A::store(dot3<NT>(d[0], d[1], d[2]));
+    for (int k = 0; k < 3; ++k)
+      e[4 + k] = A::store(A::add(A::add(A::mul(A::c(wm.Rd[k]), d[0]), A::mul(A::c(wm.Rd[3 + k]), d[1])),
+                                 A::mul(A::c(wm.Rd[6 + k]), d[2])));
+  }
+}
+
+// All nuclei's parts of a move from the cache, and (double grid) the
+// squared distance of the bond midpoint from the nearest heavy nucleus.
+template <class NT>
+__device__ __forceinline__ void nucleus_terms_cached_m(const SysDev& S, const df* v, const df* en, int k, NT h,
+                                                       const NT he[3], NT h2, const BlockMem& bm, NT& rdet,
+                                                       NT& jen, NT& mid2)
+{
+  typedef Ar<NT> A;
+  rdet = A::zero();
+  jen = A::zero();
+  mid2 = A::inf();
+  const NT h2q = A::mul_f(h2, 0.25f);
+  for (int I = 0; I < S.n_nuc; ++I) {
+    const df* e = &en[8 * I];
+    const NT hp = A::mul(h, A::c(e[4 + k]));
+    const NT D = A::c(e[3]);
+    NT d[3] = {A::add(A::c(e[0]), he[0]), A::add(A::c(e[1]), he[1]), A::add(A::c(e[2]), he[2])};
+    nucleus_term_m<NT>(S, v, I, d, A::add(A::add(D, A::mul_f(hp, 2.0f)), h2), bm, rdet, jen);
+    if (S.heavy[I]) {
+      NT m2 = A::add(A::add(D, hp), h2q);
+      if (A::lt(m2, mid2)) mid2 = m2;
     }
   }
+}
+
+// p from the squared distance to the nearest heavy nucleus: Eq. 3
+// (Gaussian) or Eq. 2 (Pade).
+template <class NT>
+__device__ __forceinline__ NT p_from_d2_m(const SysDev& S, const LatDev& L, NT best, const BlockMem& bm)
+{
+  typedef Ar<NT> A;
+  if (L.pkind == 0) return A::exp(A::neg(A::mul(best, A::c(L.p_coef_df))), S.D.exp.K, bm.tab);
+  return A::rcp(A::add_f(A::mul(A::c(L.p_coef_df), best), 1.0f));
 }
 
 // Index of the electron pair (a, b), a < b, in the pair cache.
@@ -1230,7 +1311,10 @@ __device__ void warp_eval_m(const SysDev& S, const double* sC, const LatDev& L, 
   if (lane < 9) wm.Rd[lane] = A::store(A::from_double(wm.R[lane]));
   __syncwarp();
   constexpr bool kUsePairCache = sizeof(NT) == sizeof(df);
-  if (kUsePairCache) fill_pair_cache<NT>(S, wm, lane);
+  if (kUsePairCache) {
+    fill_pair_cache<NT>(S, wm, lane);
+    fill_en_cache<NT>(S, wm, lane);
+  }
   // local energy: Lp lanes per electron share its shells, electrons and nuclei
   NT epart = A::zero();
   if (N <= 32) {
@@ -1267,23 +1351,39 @@ __device__ void warp_eval_m(const SysDev& S, const double* sC, const LatDev& L, 
     NT h = g ? A::c(L.ap_df) : A::c(L.a_df);
     if (c & 1) h = A::neg(h);
     const NT e0 = A::c(wm.Rd[k]), e1 = A::c(wm.Rd[3 + k]), e2 = A::c(wm.Rd[6 + k]);
-    const NT ri[3] = {A::c(wm.xd[3 * i]), A::c(wm.xd[3 * i + 1]), A::c(wm.xd[3 * i + 2])};
-    NT p[3] = {A::add(ri[0], A::mul(h, e0)), A::add(ri[1], A::mul(h, e1)), A::add(ri[2], A::mul(h, e2))};
-    NT rdet, jen;
-    nucleus_terms_m<NT>(S, &wm.vd[i * nao], p, bm, rdet, jen);
-    // the pair cache pays in double-float arithmetic only (single precision
-    // recomputes a distance faster than it reads it back)
-    NT jee = (kUsePairCache && wm.n_pc) ? jastrow_ee_cached_m<NT>(S, wm.pc, i, k, h, A::sqr(h))
-                                        : jastrow_ee_m<NT>(S, wm.xd, i, p);
+    NT rdet, jen, jee, pm = A::one();
+    if (kUsePairCache) {
+      // the caches pay in double-float arithmetic only (single precision
+      // recomputes a distance faster than it reads it back)
+      const NT h2 = A::sqr(h);
+      const NT he[3] = {A::mul(h, e0), A::mul(h, e1), A::mul(h, e2)};
+      NT mid2;
+      nucleus_terms_cached_m<NT>(S, &wm.vd[i * nao], &wm.enc[8 * i * S.n_nuc], k, h, he, h2, bm, rdet, jen,
+                                 mid2);
+      if (wm.n_pc) {
+        jee = jastrow_ee_cached_m<NT>(S, wm.pc, i, k, h, h2);
+      } else {
+        const NT p[3] = {A::add(A::c(wm.xd[3 * i]), he[0]), A::add(A::c(wm.xd[3 * i + 1]), he[1]),
+                         A::add(A::c(wm.xd[3 * i + 2]), he[2])};
+        jee = jastrow_ee_m<NT>(S, wm.xd, i, p);
+      }
+      if (G == 2) pm = p_from_d2_m<NT>(S, L, mid2, bm);
+    } else {
+      const NT ri[3] = {A::c(wm.xd[3 * i]), A::c(wm.xd[3 * i + 1]), A::c(wm.xd[3 * i + 2])};
+      const NT p[3] = {A::add(ri[0], A::mul(h, e0)), A::add(ri[1], A::mul(h, e1)), A::add(ri[2], A::mul(h, e2))};
+      nucleus_terms_m<NT>(S, &wm.vd[i * nao], p, bm, rdet, jen);
+      jee = jastrow_ee_m<NT>(S, wm.xd, i, p);
+      if (G == 2) {
+        const NT hh = A::half(h);
+        const NT mid[3] = {A::add(ri[0], A::mul(hh, e0)), A::add(ri[1], A::mul(hh, e1)),
+                           A::add(ri[2], A::mul(hh, e2))};
+        pm = p_weight_m<NT>(S, L, mid, bm);
+      }
+    }
     NT dJ = A::sub(A::add(jee, jen), A::c(wm.Sd[i]));
     NT rho = A::mul(rdet, A::exp(dJ, S.D.exp.K, bm.tab));
     NT w = A::one();
-    if (G == 2) {
-      NT hh = A::half(h);
-      NT mid[3] = {A::add(ri[0], A::mul(hh, e0)), A::add(ri[1], A::mul(hh, e1)), A::add(ri[2], A::mul(hh, e2))};
-      NT pm = p_weight_m<NT>(S, L, mid, bm);
-      w = g ? A::add_f(A::neg(pm), 1.0f) : pm;
-    }
+    if (G == 2) w = g ? A::add_f(A::neg(pm), 1.0f) : pm;
     NT T = A::zero();
     if (A::positive(rho)) T = A::mul(A::mul(w, g ? A::c(L.inv2ap2_df) : A::c(L.inv2a2_df)), rho);
     Td[c] = A::store(T);
@@ -1913,7 +2013,7 @@ Layout make_layout(const SysDev& S)
   // 4 df per pair would cost blocks per SM)
   Lo.n_pc = S.N <= 24 ? S.N * (S.N - 1) / 2 : 0;
   Lo.smem_warp = 3 * S.N + S.n_up * S.n_up + S.n_dn * S.n_dn + 12 + Lo.P_max + S.N * S.n_ao + S.N +
-                 (3 * S.N + 12) + 4 * Lo.n_pc + scr;
+                 (3 * S.N + 12) + 4 * Lo.n_pc + 8 * S.N * S.n_nuc + scr;
   Lo.smem_warp = (Lo.smem_warp + 1) & ~1;
   Lo.head = ((2 * S.n_ao * S.n_mo + (S.n_ao * S.n_mo + 1) / 2 + 64) + 1) & ~1;
   Lo.smem_block_bytes = (int)sizeof(double) * (Lo.head + kWarpsPerBlock * Lo.smem_warp);
