@@ -114,6 +114,7 @@ struct Layout {
   int smem_warp;  // doubles of shared memory per warp
   int smem_block_bytes;
   int n_pc;       // electron pairs with a cached distance and projections (0: no cache)
+  int pcw;        // double-floats per cached pair: 4 (distance, projections) or 8 (+ Jastrow pair terms)
 };
 
 Layout make_layout(const SysDev& S);

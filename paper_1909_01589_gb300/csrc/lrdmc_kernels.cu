@@ -460,6 +460,7 @@ __device__ __forceinline__ void nj_value3(const SysDev& S, int c, double r, doub
 }
 
 // sum_{j != i} u_ee(|p - r_j|) + sum_I u_en(|p - R_I|).
+template <bool NJ>
 __device__ double jastrow_terms(const SysDev& S, const double* sx, int i, double px, double py,
                                 double pz)
 {
@@ -471,13 +472,13 @@ __device__ double jastrow_terms(const SysDev& S, const double* sx, int i, double
     double r = sqrt(dx * dx + dy * dy + dz * dz);
     double c = (spin_of(S, j) == si) ? S.c_par : S.c_anti;
     acc += c * r / (1.0 + S.b_ee * r);
-    if (S.nj_on) acc += nj_value(S, nj_ch_ee(S, i, j), r);
+    if (NJ) acc += nj_value(S, nj_ch_ee(S, i, j), r);
   }
   for (int I = 0; I < S.n_nuc; ++I) {
     double dx = px - S.nuc[I][0], dy = py - S.nuc[I][1], dz = pz - S.nuc[I][2];
     double r = sqrt(dx * dx + dy * dy + dz * dz);
     acc -= S.en_b1[I] * r / (1.0 + S.en_b2 * r);
-    if (S.nj_on) acc += nj_value(S, 2 + S.nj_species[I], r);
+    if (NJ) acc += nj_value(S, 2 + S.nj_species[I], r);
   }
   return acc;
 }
@@ -511,10 +512,12 @@ struct WarpMem {
   df* vd;       // [N][n_ao]   (aliases v)
   df* Sd;       // [N]         (aliases Ssum)
   df* Rd;       // [12]
-  df* pc;       // [n_pc][4] pair cache: |r_a - r_b|^2 and e_k . (r_a - r_b), a < b
+  df* pc;       // [n_pc][pcw] pair cache: |r_a - r_b|^2, e_k . (r_a - r_b) (a < b) and, with
+                //   pcw = 8, the pair's Jastrow terms u, u'/r, u'' + 2u'/r and 1/r
   df* enc;      // [N][n_nuc][8] electron-nucleus cache: d, |d|^2, e_k . d
   double* scr;  // scratch
   int n_pc;     // pairs in the cache (0: no cache)
+  int pcw;      // double-floats per cached pair
 };
 
 __device__ __forceinline__ WarpMem warp_mem(const Layout& Lo, const SysDev& S, double* base)
@@ -534,9 +537,10 @@ __device__ __forceinline__ WarpMem warp_mem(const Layout& Lo, const SysDev& S, d
   m.xd = reinterpret_cast<df*>(m.Ssum + Lo.N);
   m.Rd = m.xd + 3 * Lo.N;
   m.pc = m.Rd + 12;
-  m.enc = m.pc + 4 * Lo.n_pc;
+  m.enc = m.pc + Lo.pcw * Lo.n_pc;
   m.scr = reinterpret_cast<double*>(m.enc + 8 * Lo.N * S.n_nuc);
   m.n_pc = Lo.n_pc;
+  m.pcw = Lo.pcw;
   return m;
 }
 
@@ -653,6 +657,7 @@ __device__ LRDMC_COLD bool warp_inverse(const SysDev& S, const double* sC, const
 // On return sT holds T_c, b and el are warp-uniform. ratio_out (global,
 // nullable) receives psi_G(x')/psi_G(x) for every move.
 // ----------------------------------------------------------------------------
+template <bool NJ>
 __device__ void warp_eval(const SysDev& S, const double* sC, const LatDev& L, const WarpMem& wm,
                           int lane, double* ratio_out, double& b, double& el, double* grad_out = nullptr,
                           bool moves = true)
@@ -686,7 +691,7 @@ __device__ void warp_eval(const SysDev& S, const double* sC, const LatDev& L, co
       double u2 = -2.0 * S.b_ee * c * inv * inv * inv;
       double ir = 1.0 / r;
       Ssum += c * r * inv;
-      if (S.nj_on) {
+      if (NJ) {
         double g, g1, g2;
         nj_value3(S, nj_ch_ee(S, i, j), r, g, g1, g2);
         u1 += g1; u2 += g2; Ssum += g;
@@ -704,7 +709,7 @@ __device__ void warp_eval(const SysDev& S, const double* sC, const LatDev& L, co
       double u2 = 2.0 * S.en_b2 * b1 * inv * inv * inv;
       double ir = 1.0 / r;
       Ssum -= b1 * r * inv;
-      if (S.nj_on) {
+      if (NJ) {
         double g, g1, g2;
         nj_value3(S, 2 + S.nj_species[I], r, g, g1, g2);
         u1 += g1; u2 += g2; Ssum += g;
@@ -736,7 +741,7 @@ __device__ void warp_eval(const SysDev& S, const double* sC, const LatDev& L, co
     const double* ri = &wm.x[3 * i];
     double px = ri[0] + sign * h * ex, py = ri[1] + sign * h * ey, pz = ri[2] + sign * h * ez;
     double rdet = ao_dot(S, &wm.v[i * nao], px, py, pz);
-    double dJ = jastrow_terms(S, wm.x, i, px, py, pz) - wm.Ssum[i];
+    double dJ = jastrow_terms<NJ>(S, wm.x, i, px, py, pz) - wm.Ssum[i];
     double rho = rdet * exp(dJ);
     double w = 1.0;
     if (G == 2) {
@@ -893,7 +898,7 @@ __device__ __forceinline__ void nj_value3_m(const SysDev& S, int c, NT r, NT& g,
 // when set, neural) into jen and the basis functions centred on it,
 // contracted with the projected inverse column v, into rdet. d = r' - R_I,
 // r2 = |d|^2.
-template <class NT>
+template <class NT, bool NJ>
 __device__ __forceinline__ void nucleus_term_m(const SysDev& S, const df* v, int I, const NT d[3], NT r2,
                                                const BlockMem& bm, NT& rdet, NT& jen)
 {
@@ -901,7 +906,7 @@ __device__ __forceinline__ void nucleus_term_m(const SysDev& S, const df* v, int
   NT r = A::sqrt(r2);
   if (S.en_b1[I] != 0.0)
     jen = A::sub(jen, A::div(A::mul(A::c(S.D.en_b1[I]), r), A::add_f(A::mul(A::c(S.D.en_b2), r), 1.0f)));
-  if (S.nj_on) jen = A::add(jen, nj_value_m<NT>(S, 2 + S.nj_species[I], r));
+  if (NJ) jen = A::add(jen, nj_value_m<NT>(S, 2 + S.nj_species[I], r));
   NT e = A::zero();
   for (int q = S.nuc_shell_begin[I]; q < S.nuc_shell_begin[I + 1]; ++q) {
     const ShellDev& sh = S.sh[q];
@@ -921,7 +926,7 @@ __device__ __forceinline__ void nucleus_term_m(const SysDev& S, const df* v, int
   }
 }
 
-template <class NT>
+template <class NT, bool NJ>
 __device__ void nucleus_terms_m(const SysDev& S, const df* v, const NT p[3], const BlockMem& bm, NT& rdet, NT& jen)
 {
   typedef Ar<NT> A;
@@ -930,7 +935,7 @@ __device__ void nucleus_terms_m(const SysDev& S, const df* v, const NT p[3], con
   for (int I = 0; I < S.n_nuc; ++I) {
     NT d[3] = {A::sub_fast(p[0], A::c(S.D.nuc[I][0])), A::sub_fast(p[1], A::c(S.D.nuc[I][1])),
                A::sub_fast(p[2], A::c(S.D.nuc[I][2]))};
-    nucleus_term_m<NT>(S, v, I, d, dot3<NT>(d[0], d[1], d[2]), bm, rdet, jen);
+    nucleus_term_m<NT, NJ>(S, v, I, d, dot3<NT>(d[0], d[1], d[2]), bm, rdet, jen);
   }
 }
 
@@ -959,7 +964,7 @@ __device__ void fill_en_cache(const SysDev& S, const WarpMem& wm, int lane)
 
 // All nuclei's parts of a move from the cache, and (double grid) the
 // squared distance of the bond midpoint from the nearest heavy nucleus.
-template <class NT>
+template <class NT, bool NJ>
 __device__ __forceinline__ void nucleus_terms_cached_m(const SysDev& S, const df* v, const df* en, int k, NT h,
                                                        const NT he[3], NT h2, const BlockMem& bm, NT& rdet,
                                                        NT& jen, NT& mid2)
@@ -974,7 +979,7 @@ __device__ __forceinline__ void nucleus_terms_cached_m(const SysDev& S, const df
     const NT hp = A::mul(h, A::c(e[4 + k]));
     const NT D = A::c(e[3]);
     NT d[3] = {A::add(A::c(e[0]), he[0]), A::add(A::c(e[1]), he[1]), A::add(A::c(e[2]), he[2])};
-    nucleus_term_m<NT>(S, v, I, d, A::add(A::add(D, A::mul_f(hp, 2.0f)), h2), bm, rdet, jen);
+    nucleus_term_m<NT, NJ>(S, v, I, d, A::add(A::add(D, A::mul_f(hp, 2.0f)), h2), bm, rdet, jen);
     if (S.heavy[I]) {
       NT m2 = A::add(A::add(D, hp), h2q);
       if (A::lt(m2, mid2)) mid2 = m2;
@@ -999,7 +1004,7 @@ __device__ __forceinline__ int pair_index(int N, int a, int b) { return a * N - 
 // and P_k = e_k . (r_a - r_b) on the evaluation's rotated axes. A lattice
 // move r_i -> r_i + h e_k then has |r' - r_j|^2 = D + 2 h s P_k + h^2, with
 // s = +1 for i = a and -1 for i = b.
-template <class NT>
+template <class NT, bool NJ>
 __device__ void fill_pair_cache(const SysDev& S, const WarpMem& wm, int lane)
 {
   typedef Ar<NT> A;
@@ -1010,20 +1015,45 @@ __device__ void fill_pair_cache(const SysDev& S, const WarpMem& wm, int lane)
     const int b = a + 1 + (q - base);
     NT d[3];
     for (int k = 0; k < 3; ++k) d[k] = A::sub_fast(A::c(wm.xd[3 * a + k]), A::c(wm.xd[3 * b + k]));
-    df* e = &wm.pc[4 * q];
-    e[0] = A::store(dot3<NT>(d[0], d[1], d[2]));
+    df* e = &wm.pc[wm.pcw * q];
+    const NT D = dot3<NT>(d[0], d[1], d[2]);
+    e[0] = A::store(D);
     for (int k = 0; k < 3; ++k) {
       NT pk = A::add(A::add(A::mul(A::c(wm.Rd[k]), d[0]), A::mul(A::c(wm.Rd[3 + k]), d[1])),
                      A::mul(A::c(wm.Rd[6 + k]), d[2]));
       e[1 + k] = A::store(pk);
+    }
+    if ((wm.pcw == 8 && NJ)) {
+      // with the neural term, the pair's Jastrow terms for the local energy
+      // (Pade plus neural): u, u'/r, u'' + 2 u'/r, and 1/r (with the Pade
+      // factor alone, evaluating them inside the local energy is faster)
+      const NT rr = A::sqrt(D);
+      const NT bb = A::c(S.D.b_ee);
+      const NT c = (spin_of(S, a) == spin_of(S, b)) ? A::c(S.D.c_par) : A::c(S.D.c_anti);
+      const NT inv = A::rcp(A::add_f(A::mul(bb, rr), 1.0f));
+      const NT inv2 = A::sqr(inv);
+      NT u = A::mul(A::mul(c, rr), inv);
+      NT u1 = A::mul(c, inv2);
+      NT u2 = A::mul_f(A::mul(A::mul(bb, c), A::mul(inv2, inv)), -2.0f);
+      if (NJ) {
+        NT g, g1, g2;
+        nj_value3_m<NT>(S, nj_ch_ee(S, a, b), rr, g, g1, g2);
+        u1 = A::add(u1, g1); u2 = A::add(u2, g2); u = A::add(u, g);
+      }
+      const NT irr = A::rcp(rr);
+      const NT u1ir = A::mul(u1, irr);
+      e[4] = A::store(u);
+      e[5] = A::store(u1ir);
+      e[6] = A::store(A::add(u2, A::mul_f(u1ir, 2.0f)));
+      e[7] = A::store(irr);
     }
   }
 }
 
 // sum_{j != i} u_ee(|r_i + h e_k - r_j|) from the pair cache (h carries
 // the sign of the move, h2 = h^2); the Pade terms as one running fraction.
-template <class NT>
-__device__ NT jastrow_ee_cached_m(const SysDev& S, const df* pc, int i, int k, NT h, NT h2)
+template <class NT, bool NJ>
+__device__ NT jastrow_ee_cached_m(const SysDev& S, const df* pc, int pcw, int i, int k, NT h, NT h2)
 {
   typedef Ar<NT> A;
   NT num = A::zero(), den = A::one(), nn = A::zero();
@@ -1031,7 +1061,7 @@ __device__ NT jastrow_ee_cached_m(const SysDev& S, const df* pc, int i, int k, N
   const NT b = A::c(S.D.b_ee), cp = A::c(S.D.c_par), ca = A::c(S.D.c_anti);
   for (int j = 0; j < N; ++j) {
     if (j == i) continue;
-    const df* e = &pc[4 * pair_index(N, min(i, j), max(i, j))];
+    const df* e = &pc[pcw * pair_index(N, min(i, j), max(i, j))];
     NT hp = A::mul(h, A::c(e[1 + k]));
     hp = A::mul_f(hp, i < j ? 2.0f : -2.0f);
     NT r = A::sqrt(A::add(A::add(A::c(e[0]), hp), h2));
@@ -1039,7 +1069,7 @@ __device__ NT jastrow_ee_cached_m(const SysDev& S, const df* pc, int i, int k, N
     NT dj = A::add_f(A::mul(b, r), 1.0f);
     num = A::add_fast(A::mul(num, dj), A::mul(A::mul(c, r), den));
     den = A::mul(den, dj);
-    if (S.nj_on) nn = A::add(nn, nj_value_m<NT>(S, nj_ch_ee(S, i, j), r));
+    if (NJ) nn = A::add(nn, nj_value_m<NT>(S, nj_ch_ee(S, i, j), r));
   }
   return A::add(A::div(num, den), nn);
 }
@@ -1047,7 +1077,7 @@ __device__ NT jastrow_ee_cached_m(const SysDev& S, const df* pc, int i, int k, N
 // sum_{j != i} u_ee(|p - r_j|): the Pade terms c r/(1 + b r) (all of one
 // sign) are summed as one running fraction num/den, so one division serves
 // all partners.
-template <class NT>
+template <class NT, bool NJ>
 __device__ NT jastrow_ee_m(const SysDev& S, const df* xd, int i, const NT p[3])
 {
   typedef Ar<NT> A;
@@ -1063,7 +1093,7 @@ __device__ NT jastrow_ee_m(const SysDev& S, const df* xd, int i, const NT p[3])
     NT dj = A::add_f(A::mul(b, r), 1.0f);
     num = A::add_fast(A::mul(num, dj), A::mul(A::mul(c, r), den));
     den = A::mul(den, dj);
-    if (S.nj_on) nn = A::add(nn, nj_value_m<NT>(S, nj_ch_ee(S, i, j), r));
+    if (NJ) nn = A::add(nn, nj_value_m<NT>(S, nj_ch_ee(S, i, j), r));
   }
   return A::add(A::div(num, den), nn);
 }
@@ -1137,7 +1167,7 @@ __device__ __forceinline__ void el_zero(ElParts<NT>& o)
   for (int k = 0; k < 3; ++k) { o.gD[k] = A::zero(); o.gJ[k] = A::zero(); }
 }
 
-template <class NT>
+template <class NT, bool NJ>
 __device__ LRDMC_EL void el_parts_m(const SysDev& S, const WarpMem& wm, int i, int part, int L, const BlockMem& bm,
                            ElParts<NT>& o)
 {
@@ -1211,6 +1241,22 @@ __device__ LRDMC_EL void el_parts_m(const SysDev& S, const WarpMem& wm, int i, i
   // e-e pairs
   const int si = spin_of(S, i);
   const NT b = A::c(S.D.b_ee);
+  if (sizeof(NT) == sizeof(df) && (wm.pcw == 8 && NJ)) {
+    // every pair's terms come from the pair cache (evaluated once per pair)
+    for (int j = part; j < S.N; j += L) {
+      if (j == i) continue;
+      const df* e = &wm.pc[8 * pair_index(S.N, min(i, j), max(i, j))];
+      NT d0 = A::sub_fast(ri[0], A::c(wm.xd[3 * j])), d1 = A::sub_fast(ri[1], A::c(wm.xd[3 * j + 1])),
+         d2 = A::sub_fast(ri[2], A::c(wm.xd[3 * j + 2]));
+      const NT u1ir = A::c(e[5]);
+      o.gJ[0] = A::add(o.gJ[0], A::mul(u1ir, d0));
+      o.gJ[1] = A::add(o.gJ[1], A::mul(u1ir, d1));
+      o.gJ[2] = A::add(o.gJ[2], A::mul(u1ir, d2));
+      o.lJ = A::add(o.lJ, A::c(e[6]));
+      o.S = A::add(o.S, A::c(e[4]));
+      if (j > i && S.ee_on) o.V = A::add(o.V, A::c(e[7]));
+    }
+  } else
   for (int j = part; j < S.N; j += L) {
     if (j == i) continue;
     NT d0 = A::sub_fast(ri[0], A::c(wm.xd[3 * j])), d1 = A::sub_fast(ri[1], A::c(wm.xd[3 * j + 1])),
@@ -1222,7 +1268,7 @@ __device__ LRDMC_EL void el_parts_m(const SysDev& S, const WarpMem& wm, int i, i
     NT u1 = A::mul(c, inv2);
     NT u2 = A::mul_f(A::mul(A::mul(b, c), A::mul(inv2, inv)), -2.0f);
     o.S = A::add(o.S, A::mul(A::mul(c, rr), inv));
-    if (S.nj_on) {
+    if (NJ) {
       NT g, g1, g2;
       nj_value3_m<NT>(S, nj_ch_ee(S, i, j), rr, g, g1, g2);
       u1 = A::add(u1, g1); u2 = A::add(u2, g2); o.S = A::add(o.S, g);
@@ -1246,7 +1292,7 @@ __device__ LRDMC_EL void el_parts_m(const SysDev& S, const WarpMem& wm, int i, i
     NT u1 = A::neg(A::mul(b1, inv2));
     NT u2 = A::mul_f(A::mul(A::mul(b2, b1), A::mul(inv2, inv)), 2.0f);
     o.S = A::sub(o.S, A::mul(A::mul(b1, rr), inv));
-    if (S.nj_on) {
+    if (NJ) {
       NT g, g1, g2;
       nj_value3_m<NT>(S, 2 + S.nj_species[I], rr, g, g1, g2);
       u1 = A::add(u1, g1); u2 = A::add(u2, g2); o.S = A::add(o.S, g);
@@ -1284,7 +1330,7 @@ __device__ __forceinline__ NT el_local(const ElParts<NT>& o)
   return A::add(A::mul_f(lap, -0.5f), o.V);
 }
 
-template <class NT>
+template <class NT, bool NJ>
 __device__ void warp_eval_m(const SysDev& S, const double* sC, const LatDev& L, const WarpMem& wm, int lane,
                             double* ratio_out, double& b, df& bdf, double& el)
 {
@@ -1312,8 +1358,9 @@ __device__ void warp_eval_m(const SysDev& S, const double* sC, const LatDev& L, 
   __syncwarp();
   constexpr bool kUsePairCache = sizeof(NT) == sizeof(df);
   if (kUsePairCache) {
-    fill_pair_cache<NT>(S, wm, lane);
+    fill_pair_cache<NT, NJ>(S, wm, lane);
     fill_en_cache<NT>(S, wm, lane);
+    __syncwarp();
   }
   // local energy: Lp lanes per electron share its shells, electrons and nuclei
   NT epart = A::zero();
@@ -1322,7 +1369,7 @@ __device__ void warp_eval_m(const SysDev& S, const double* sC, const LatDev& L, 
     const int i = lane % N, part = lane / N;
     const bool act = lane < N * Lp;
     ElParts<NT> o;
-    if (act) el_parts_m<NT>(S, wm, i, part, Lp, bm, o);
+    if (act) el_parts_m<NT, NJ>(S, wm, i, part, Lp, bm, o);
     else el_zero<NT>(o);
     for (int pp = 1; pp < Lp; ++pp) {
       int src = lane + pp * N;
@@ -1335,7 +1382,7 @@ __device__ void warp_eval_m(const SysDev& S, const double* sC, const LatDev& L, 
   } else {
     for (int i = lane; i < N; i += 32) {
       ElParts<NT> o;
-      el_parts_m<NT>(S, wm, i, 0, 1, bm, o);
+      el_parts_m<NT, NJ>(S, wm, i, 0, 1, bm, o);
       wm.Sd[i] = A::store(o.S);
       epart = A::add(epart, el_local<NT>(o));
     }
@@ -1358,21 +1405,21 @@ __device__ void warp_eval_m(const SysDev& S, const double* sC, const LatDev& L, 
       const NT h2 = A::sqr(h);
       const NT he[3] = {A::mul(h, e0), A::mul(h, e1), A::mul(h, e2)};
       NT mid2;
-      nucleus_terms_cached_m<NT>(S, &wm.vd[i * nao], &wm.enc[8 * i * S.n_nuc], k, h, he, h2, bm, rdet, jen,
+      nucleus_terms_cached_m<NT, NJ>(S, &wm.vd[i * nao], &wm.enc[8 * i * S.n_nuc], k, h, he, h2, bm, rdet, jen,
                                  mid2);
       if (wm.n_pc) {
-        jee = jastrow_ee_cached_m<NT>(S, wm.pc, i, k, h, h2);
+        jee = jastrow_ee_cached_m<NT, NJ>(S, wm.pc, wm.pcw, i, k, h, h2);
       } else {
         const NT p[3] = {A::add(A::c(wm.xd[3 * i]), he[0]), A::add(A::c(wm.xd[3 * i + 1]), he[1]),
                          A::add(A::c(wm.xd[3 * i + 2]), he[2])};
-        jee = jastrow_ee_m<NT>(S, wm.xd, i, p);
+        jee = jastrow_ee_m<NT, NJ>(S, wm.xd, i, p);
       }
       if (G == 2) pm = p_from_d2_m<NT>(S, L, mid2, bm);
     } else {
       const NT ri[3] = {A::c(wm.xd[3 * i]), A::c(wm.xd[3 * i + 1]), A::c(wm.xd[3 * i + 2])};
       const NT p[3] = {A::add(ri[0], A::mul(h, e0)), A::add(ri[1], A::mul(h, e1)), A::add(ri[2], A::mul(h, e2))};
-      nucleus_terms_m<NT>(S, &wm.vd[i * nao], p, bm, rdet, jen);
-      jee = jastrow_ee_m<NT>(S, wm.xd, i, p);
+      nucleus_terms_m<NT, NJ>(S, &wm.vd[i * nao], p, bm, rdet, jen);
+      jee = jastrow_ee_m<NT, NJ>(S, wm.xd, i, p);
       if (G == 2) {
         const NT hh = A::half(h);
         const NT mid[3] = {A::add(ri[0], A::mul(hh, e0)), A::add(ri[1], A::mul(hh, e1)),
@@ -1395,17 +1442,17 @@ __device__ void warp_eval_m(const SysDev& S, const double* sC, const LatDev& L, 
   b = A::to_double(btot);
 }
 
-template <int PREC>
+template <int PREC, bool NJ>
 __device__ __forceinline__ void warp_eval_any(const SysDev& S, const double* sC, const LatDev& L,
                                               const WarpMem& wm, int lane, double* ratio_out, double& b,
                                               df& bdf, double& el)
 {
   if (PREC == LRDMC_PRECISION_DF64) {
-    warp_eval_m<df>(S, sC, L, wm, lane, ratio_out, b, bdf, el);
+    warp_eval_m<df, NJ>(S, sC, L, wm, lane, ratio_out, b, bdf, el);
   } else if (PREC == LRDMC_PRECISION_FP32) {
-    warp_eval_m<float>(S, sC, L, wm, lane, ratio_out, b, bdf, el);
+    warp_eval_m<float, NJ>(S, sC, L, wm, lane, ratio_out, b, bdf, el);
   } else {
-    warp_eval(S, sC, L, wm, lane, ratio_out, b, el);
+    warp_eval<NJ>(S, sC, L, wm, lane, ratio_out, b, el);
     bdf = df_make(0.0f, 0.0f);
   }
 }
@@ -1624,6 +1671,8 @@ template <int PREC>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 k_eval_all(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, const PopDev P)
 {
+  constexpr int PR = PREC & 3;         // the arithmetic (LRDMC_PRECISION_*)
+  constexpr bool NJ = (PREC & 8) != 0;  // the neural pair term is set
   extern __shared__ double smem[];
   double* sC = smem;
   stage_coefficients(S, sC);
@@ -1635,7 +1684,7 @@ k_eval_all(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
   double b, el;
   df bdf;
   load_record(Lo, rec, wm, lane, b, el);
-  warp_eval_any<PREC>(S, sC, L, wm, lane, nullptr, b, bdf, el);
+  warp_eval_any<PR, NJ>(S, sC, L, wm, lane, nullptr, b, bdf, el);
   if (!isfinite(el) || !isfinite(b)) {
     if (lane == 0) atomicOr(P.err, kErrNonFinite);
   }
@@ -1653,6 +1702,8 @@ template <int PREC>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, LRDMC_INTERVAL_MIN_BLOCKS)
 k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, const PopDev P)
 {
+  constexpr int PR = PREC & 3;         // the arithmetic (LRDMC_PRECISION_*)
+  constexpr bool NJ = (PREC & 8) != 0;  // the neural pair term is set
   extern __shared__ double smem[];
   double* sC = smem;
   // interval k from the device counter (advanced by k_reconfig); the inverse
@@ -1694,9 +1745,9 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
         b1[j] = shfl_u64(cb[j], 1);
       }
       double t;
-      if (PREC == LRDMC_PRECISION_DF64)
+      if (PR == LRDMC_PRECISION_DF64)
         t = b > 0.0 ? df_to_double(df_div(df_neg(df_log(df_u01(b0[0]), S.D.exp.K, bm.tab)), bdf)) : INFINITY;
-      else if (PREC == LRDMC_PRECISION_FP32)
+      else if (PR == LRDMC_PRECISION_FP32)
         t = b > 0.0 ? (double)(-logf(f_u01(b0[0])) / bdf.hi) : INFINITY;
       else
         t = b > 0.0 ? -log(to_u01(b0[0])) / b : INFINITY;
@@ -1708,9 +1759,9 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
       tau_left -= t;
       // heat bath over the cached rates
       int pick, last;
-      if (PREC == LRDMC_PRECISION_DF64)
+      if (PR == LRDMC_PRECISION_DF64)
         warp_scan_m<df>(reinterpret_cast<const df*>(wm.T), P_moves, lane, df_mul(df_u01(b0[1]), bdf), &pick, &last);
-      else if (PREC == LRDMC_PRECISION_FP32)
+      else if (PR == LRDMC_PRECISION_FP32)
         warp_scan_m<float>(reinterpret_cast<const df*>(wm.T), P_moves, lane, f_u01(b0[1]) * bdf.hi, &pick, &last);
       else
         warp_scan(wm.T, P_moves, lane, to_u01(b0[1]) * b, &pick, &last);
@@ -1726,12 +1777,12 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
 #pragma unroll
       for (int d = 0; d < 3; ++d) pnew[d] = wm.x[3 * i + d] + sign * h * wm.R[3 * d + kx];
       bool sm_ok;
-      if (PREC != LRDMC_PRECISION_FP32) {
+      if (PR != LRDMC_PRECISION_FP32) {
         // the parity modes keep the update in IEEE double: near a node the
         // update amplifies rounding by the condition number of the Slater
         // matrix, and a double-float update (2^-48) parts trajectories from
         // the FP64 reference in rare walkers
-        sm_ok = warp_sm_update<PREC>(S, sC, wm, i, pnew, lane);
+        sm_ok = warp_sm_update<PR>(S, sC, wm, i, pnew, lane);
       } else {
         // the new position as a double-float (the shared-memory double-float
         // copies of x and R belong to the last evaluation, which for the
@@ -1745,9 +1796,9 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
       }
       if (lane < 3) wm.x[3 * i + lane] = pnew[lane];
       __syncwarp();
-      rotation_matrix_warp<PREC>(b1, wm.R, lane, S);
+      rotation_matrix_warp<PR>(b1, wm.R, lane, S);
       __syncwarp();
-      warp_eval_any<PREC>(S, sC, L, wm, lane, nullptr, b, bdf, el);
+      warp_eval_any<PR, NJ>(S, sC, L, wm, lane, nullptr, b, bdf, el);
       ++jumps;
       if (!isfinite(el) || !isfinite(b)) {
         if (lane == 0) atomicOr(P.err, kErrNonFinite);
@@ -1899,6 +1950,8 @@ k_evaluate(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, in
            const double* x, const double* rot, double* ratio, double* T, double* b_out,
            double* el_out, int* err)
 {
+  constexpr int PR = PREC & 3;         // the arithmetic (LRDMC_PRECISION_*)
+  constexpr bool NJ = (PREC & 8) != 0;  // the neural pair term is set
   extern __shared__ double smem[];
   double* sC = smem;
   stage_coefficients(S, sC);
@@ -1918,10 +1971,10 @@ k_evaluate(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, in
   const int P = S.N * 6 * L.G;
   double b, el;
   df bdf;
-  warp_eval_any<PREC>(S, sC, L, wm, lane, ratio ? ratio + (size_t)c * P : nullptr, b, bdf, el);
+  warp_eval_any<PR, NJ>(S, sC, L, wm, lane, ratio ? ratio + (size_t)c * P : nullptr, b, bdf, el);
   if (T)
     for (int j = lane; j < P; j += 32)
-      T[(size_t)c * P + j] = (PREC != LRDMC_PRECISION_FP64) ? df_to_double(reinterpret_cast<const df*>(wm.T)[j])
+      T[(size_t)c * P + j] = (PR != LRDMC_PRECISION_FP64) ? df_to_double(reinterpret_cast<const df*>(wm.T)[j])
                                                             : wm.T[j];
   if (lane == 0) {
     if (b_out) b_out[c] = b;
@@ -2011,9 +2064,13 @@ Layout make_layout(const SysDev& S)
   if (scr_sm > scr) scr = scr_sm;
   // the pair cache of the FP32-pipe evaluations, up to 24 electrons (beyond,
   // 4 df per pair would cost blocks per SM)
+  // (distance and projections); up to 12 electrons room for the pair's
+  // Jastrow terms too (used with the neural term: the local energy then
+  // evaluates every pair once)
   Lo.n_pc = S.N <= 24 ? S.N * (S.N - 1) / 2 : 0;
+  Lo.pcw = S.N <= 12 ? 8 : 4;
   Lo.smem_warp = 3 * S.N + S.n_up * S.n_up + S.n_dn * S.n_dn + 12 + Lo.P_max + S.N * S.n_ao + S.N +
-                 (3 * S.N + 12) + 4 * Lo.n_pc + 8 * S.N * S.n_nuc + scr;
+                 (3 * S.N + 12) + Lo.pcw * Lo.n_pc + 8 * S.N * S.n_nuc + scr;
   Lo.smem_warp = (Lo.smem_warp + 1) & ~1;
   Lo.head = ((2 * S.n_ao * S.n_mo + (S.n_ao * S.n_mo + 1) / 2 + 64) + 1) & ~1;
   Lo.smem_block_bytes = (int)sizeof(double) * (Lo.head + kWarpsPerBlock * Lo.smem_warp);
@@ -2036,6 +2093,26 @@ cudaError_t launch_init(const SysDev& S, const Layout& Lo, const PopDev& P, cons
   return cudaGetLastError();
 }
 
+// Kernel variant of a system: the arithmetic in bits 0-1 of the template
+// argument, the neural pair term in bit 3 (kernels without it carry none of
+// its code).
+constexpr int kNjBit = 8;
+
+#define LRDMC_DISPATCH(S, ...)                                                     \
+  do {                                                                             \
+    const bool nj_ = (S).nj_on != 0;                                               \
+    if ((S).precision == LRDMC_PRECISION_DF64) {                                   \
+      if (nj_) { constexpr int V = LRDMC_PRECISION_DF64 | kNjBit; __VA_ARGS__; }          \
+      else { constexpr int V = LRDMC_PRECISION_DF64; __VA_ARGS__; }                       \
+    } else if ((S).precision == LRDMC_PRECISION_FP32) {                            \
+      if (nj_) { constexpr int V = LRDMC_PRECISION_FP32 | kNjBit; __VA_ARGS__; }          \
+      else { constexpr int V = LRDMC_PRECISION_FP32; __VA_ARGS__; }                       \
+    } else {                                                                       \
+      if (nj_) { constexpr int V = LRDMC_PRECISION_FP64 | kNjBit; __VA_ARGS__; }          \
+      else { constexpr int V = LRDMC_PRECISION_FP64; __VA_ARGS__; }                       \
+    }                                                                              \
+  } while (0)
+
 template <int PREC>
 static cudaError_t launch_eval_all_t(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P,
                                      cudaStream_t st)
@@ -2050,9 +2127,8 @@ static cudaError_t launch_eval_all_t(const SysDev& S, const Layout& Lo, const La
 cudaError_t launch_eval_all(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P,
                             cudaStream_t st)
 {
-  if (S.precision == LRDMC_PRECISION_DF64) return launch_eval_all_t<LRDMC_PRECISION_DF64>(S, Lo, L, P, st);
-  if (S.precision == LRDMC_PRECISION_FP32) return launch_eval_all_t<LRDMC_PRECISION_FP32>(S, Lo, L, P, st);
-  return launch_eval_all_t<LRDMC_PRECISION_FP64>(S, Lo, L, P, st);
+  LRDMC_DISPATCH(S, return launch_eval_all_t<V>(S, Lo, L, P, st));
+  return cudaErrorInvalidValue;
 }
 
 // Persistent grid of the interval kernel: as many blocks as fit on the GPU
@@ -2075,9 +2151,7 @@ static cudaError_t interval_occupancy(const Layout& Lo, int* blocks)
 int interval_default_blocks(const SysDev& S, const Layout& Lo)
 {
   int b = 0;
-  if (S.precision == LRDMC_PRECISION_DF64) interval_occupancy<LRDMC_PRECISION_DF64>(Lo, &b);
-  else if (S.precision == LRDMC_PRECISION_FP32) interval_occupancy<LRDMC_PRECISION_FP32>(Lo, &b);
-  else interval_occupancy<LRDMC_PRECISION_FP64>(Lo, &b);
+  LRDMC_DISPATCH(S, interval_occupancy<V>(Lo, &b));
   return b;
 }
 
@@ -2121,11 +2195,8 @@ static cudaError_t launch_interval_t(const SysDev& S, const Layout& Lo, const La
 cudaError_t launch_interval(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P, int blocks,
                             cudaStream_t st, int carveout)
 {
-  if (S.precision == LRDMC_PRECISION_DF64)
-    return launch_interval_t<LRDMC_PRECISION_DF64>(S, Lo, L, P, blocks, carveout, st);
-  if (S.precision == LRDMC_PRECISION_FP32)
-    return launch_interval_t<LRDMC_PRECISION_FP32>(S, Lo, L, P, blocks, carveout, st);
-  return launch_interval_t<LRDMC_PRECISION_FP64>(S, Lo, L, P, blocks, carveout, st);
+  LRDMC_DISPATCH(S, return launch_interval_t<V>(S, Lo, L, P, blocks, carveout, st));
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_reconfig(const PopDev& P, const Layout& Lo, cudaStream_t st)
@@ -2161,7 +2232,7 @@ k_base_terms(const __grid_constant__ SysDev S, const Layout Lo, int n, const dou
   LatDev L{};
   L.G = 1;
   double b, el;
-  warp_eval(S, sC, L, wm, lane, nullptr, b, el, grad + (size_t)s * 3 * Lo.N, false);
+  warp_eval<false>(S, sC, L, wm, lane, nullptr, b, el, grad + (size_t)s * 3 * Lo.N, false);
   if (lane == 0) e[s] = el;
 }
 
@@ -2176,29 +2247,25 @@ cudaError_t launch_base_terms(const SysDev& S, const Layout& Lo, int n, const do
   return cudaGetLastError();
 }
 
+template <int PREC>
+static cudaError_t launch_evaluate_t(const SysDev& S, const Layout& Lo, const LatDev& L, int n, const double* x,
+                                     const double* rot, double* ratio, double* T, double* b, double* el, int* err,
+                                     cudaStream_t st)
+{
+  const int blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  cudaError_t e = set_smem((const void*)k_evaluate<PREC>, Lo.smem_block_bytes);
+  if (e != cudaSuccess) return e;
+  k_evaluate<PREC><<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(S, Lo, L, n, x, rot, ratio, T, b, el,
+                                                                            err);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_evaluate(const SysDev& S, const Layout& Lo, const LatDev& L, int n,
                             const double* x, const double* rot, double* ratio, double* T,
                             double* b, double* el, int* err, cudaStream_t st)
 {
-  int blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  cudaError_t e;
-  if (S.precision == LRDMC_PRECISION_DF64) {
-    e = set_smem((const void*)k_evaluate<LRDMC_PRECISION_DF64>, Lo.smem_block_bytes);
-    if (e != cudaSuccess) return e;
-    k_evaluate<LRDMC_PRECISION_DF64><<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(
-        S, Lo, L, n, x, rot, ratio, T, b, el, err);
-  } else if (S.precision == LRDMC_PRECISION_FP32) {
-    e = set_smem((const void*)k_evaluate<LRDMC_PRECISION_FP32>, Lo.smem_block_bytes);
-    if (e != cudaSuccess) return e;
-    k_evaluate<LRDMC_PRECISION_FP32><<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(
-        S, Lo, L, n, x, rot, ratio, T, b, el, err);
-  } else {
-    e = set_smem((const void*)k_evaluate<LRDMC_PRECISION_FP64>, Lo.smem_block_bytes);
-    if (e != cudaSuccess) return e;
-    k_evaluate<LRDMC_PRECISION_FP64><<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(
-        S, Lo, L, n, x, rot, ratio, T, b, el, err);
-  }
-  return cudaGetLastError();
+  LRDMC_DISPATCH(S, return launch_evaluate_t<V>(S, Lo, L, n, x, rot, ratio, T, b, el, err, st));
+  return cudaErrorInvalidValue;
 }
 
 
@@ -2224,6 +2291,8 @@ k_evaluate_static(const __grid_constant__ SysDev S, const Layout Lo, const LatDe
                   const double* x, const double* rot, double* ratio, double* T, double* b_out,
                   double* el_out, int* scratch)
 {
+  constexpr int PR = PREC & 3;         // the arithmetic (LRDMC_PRECISION_*)
+  constexpr bool NJ = (PREC & 8) != 0;  // the neural pair term is set
   extern __shared__ double smem[];
   double* sC = smem;
   stage_coefficients(S, sC);
@@ -2246,10 +2315,10 @@ k_evaluate_static(const __grid_constant__ SysDev S, const Layout Lo, const LatDe
   const int P = S.N * 6 * L.G;
   double b, el;
   df bdf;
-  warp_eval_any<PREC>(S, sC, L, wm, lane, ratio ? ratio + (size_t)c * P : nullptr, b, bdf, el);
+  warp_eval_any<PR, NJ>(S, sC, L, wm, lane, ratio ? ratio + (size_t)c * P : nullptr, b, bdf, el);
   if (T)
     for (int j = lane; j < P; j += 32)
-      T[(size_t)c * P + j] = (PREC != LRDMC_PRECISION_FP64) ? df_to_double(reinterpret_cast<const df*>(wm.T)[j])
+      T[(size_t)c * P + j] = (PR != LRDMC_PRECISION_FP64) ? df_to_double(reinterpret_cast<const df*>(wm.T)[j])
                                                             : wm.T[j];
   if (lane == 0) {
     if (b_out) b_out[c] = b;
@@ -2291,26 +2360,14 @@ cudaError_t launch_evaluate_static(const SysDev& S, const Layout& Lo, const LatD
   // the summary word and the statuses of this call start at zero
   e = cudaMemsetAsync(scratch, 0, sizeof(int) * (64 + (size_t)n), st);
   if (e != cudaSuccess) return e;
-  int blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  if (S.precision == LRDMC_PRECISION_DF64) {
-    e = set_smem((const void*)k_evaluate_static<LRDMC_PRECISION_DF64>, Lo.smem_block_bytes);
+  const int blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  LRDMC_DISPATCH(S, {
+    e = set_smem((const void*)k_evaluate_static<V>, Lo.smem_block_bytes);
     if (e != cudaSuccess) return e;
     if (blocks > 0)
-      k_evaluate_static<LRDMC_PRECISION_DF64><<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(
-          S, Lo, L, n, x, rot, ratio, T, b, el, scratch);
-  } else if (S.precision == LRDMC_PRECISION_FP32) {
-    e = set_smem((const void*)k_evaluate_static<LRDMC_PRECISION_FP32>, Lo.smem_block_bytes);
-    if (e != cudaSuccess) return e;
-    if (blocks > 0)
-      k_evaluate_static<LRDMC_PRECISION_FP32><<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(
-          S, Lo, L, n, x, rot, ratio, T, b, el, scratch);
-  } else {
-    e = set_smem((const void*)k_evaluate_static<LRDMC_PRECISION_FP64>, Lo.smem_block_bytes);
-    if (e != cudaSuccess) return e;
-    if (blocks > 0)
-      k_evaluate_static<LRDMC_PRECISION_FP64><<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(
-          S, Lo, L, n, x, rot, ratio, T, b, el, scratch);
-  }
+      k_evaluate_static<V><<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(S, Lo, L, n, x, rot, ratio,
+                                                                                    T, b, el, scratch);
+  });
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = cudaMemcpyAsync(summary, scratch, sizeof(int), cudaMemcpyDeviceToHost, st);
