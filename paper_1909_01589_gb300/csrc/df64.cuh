@@ -146,30 +146,31 @@ __host__ __device__ __forceinline__ float f_rsqrt_approx(float x)
 #endif
 }
 
-// a / b: FP32 quotient q1, then one correction q2 = (a - b q1) / b from the
-// exactly computed remainder (relative error ~2^-45).
+// a / b: FP32 quotient q1, then one correction q2 = (a - b q1) / b. The
+// remainder a_hi - b_hi q1 comes from one FMA (exact up to one rounding of a
+// quantity ~2^-22 a_hi), plus a_lo - b_lo q1 (relative error ~2^-44).
 DF_HEAVY df df_div(df a, df b)
 {
   float r = f_rcp_approx(b.hi);
   float q1 = DF_MUL(a.hi, r);
-  df p = two_prod(b.hi, q1);
-  p.lo = DF_FMA(b.lo, q1, p.lo);
-  df rem = df_sub(a, p);
-  float q2 = DF_MUL(rem.hi, r);
+  float rem = DF_FMA(-q1, b.hi, a.hi);
+  rem = DF_ADD(rem, DF_FMA(-q1, b.lo, a.lo));
+  float q2 = DF_MUL(rem, r);
   return fast_two_sum(q1, q2);
 }
 
 // 1 / b
 __host__ __device__ __forceinline__ df df_rcp(df b) { return df_div(df_make(1.0f, 0.0f), b); }
 
-// sqrt(a), a >= 0: s = a_hi rsqrt(a_hi), corrected by the exact residual.
+// sqrt(a), a >= 0: s = a_hi rsqrt(a_hi), corrected by the residual
+// a - s^2 (one FMA, plus a_lo) times 1/(2s) (relative error ~2^-44).
 DF_HEAVY df df_sqrt(df a)
 {
   if (!(a.hi > 0.0f)) return df_make(0.0f, 0.0f);
   float y = f_rsqrt_approx(a.hi);
   float s = DF_MUL(a.hi, y);
-  df res = df_sub(a, two_prod(s, s));
-  float c = DF_MUL(res.hi, DF_MUL(0.5f, y));
+  float res = DF_ADD(DF_FMA(-s, s, a.hi), a.lo);
+  float c = DF_MUL(res, DF_MUL(0.5f, y));
   return fast_two_sum(s, c);
 }
 

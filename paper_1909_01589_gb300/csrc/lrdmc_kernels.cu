@@ -1059,17 +1059,28 @@ __device__ NT jastrow_ee_cached_m(const SysDev& S, const df* pc, int pcw, int i,
   NT num = A::zero(), den = A::one(), nn = A::zero();
   const int si = spin_of(S, i), N = S.N;
   const NT b = A::c(S.D.b_ee), cp = A::c(S.D.c_par), ca = A::c(S.D.c_anti);
+  // 2h s for the partners after i (s = +1) and before i (s = -1): scaling by
+  // a power of two is exact
+  const NT h2p = A::mul_f(h, 2.0f), h2m = A::neg(h2p);
+  // pair (j, i), j < i, sits at j N - j (j + 1)/2 + (i - j - 1), which grows by
+  // N - j - 2 from j to j + 1; pair (i, j), j > i, at q0 + (j - i - 1)
+  int q = i - 1;  // pair (0, i)
   for (int j = 0; j < N; ++j) {
-    if (j == i) continue;
-    const df* e = &pc[pcw * pair_index(N, min(i, j), max(i, j))];
-    NT hp = A::mul(h, A::c(e[1 + k]));
-    hp = A::mul_f(hp, i < j ? 2.0f : -2.0f);
-    NT r = A::sqrt(A::add(A::add(A::c(e[0]), hp), h2));
+    if (j == i) {
+      q = pair_index(N, i, i + 1);  // the next partner's pair (unused when i = N - 1)
+      continue;
+    }
+    const df* e = &pc[pcw * q];
+    const NT hp = A::mul(j > i ? h2p : h2m, A::c(e[1 + k]));
+    // |r' - r_j|^2 = D + 2 h s P_k + h^2: the cheap addition suffices (its
+    // error ~2^-44 (D + |2hP| + h^2) is far below what the ratios resolve)
+    NT r = A::sqrt(A::add_fast(A::add_fast(A::c(e[0]), hp), h2));
     NT c = (spin_of(S, j) == si) ? cp : ca;
     NT dj = A::add_f(A::mul(b, r), 1.0f);
     num = A::add_fast(A::mul(num, dj), A::mul(A::mul(c, r), den));
     den = A::mul(den, dj);
     if (NJ) nn = A::add(nn, nj_value_m<NT>(S, nj_ch_ee(S, i, j), r));
+    q += (j < i) ? N - j - 2 : 1;
   }
   return A::add(A::div(num, den), nn);
 }
