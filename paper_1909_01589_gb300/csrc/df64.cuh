@@ -96,6 +96,17 @@ __host__ __device__ __forceinline__ df df_add(df a, df b)
 
 __host__ __device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
 
+// Cheaper addition for operands whose sum is used with an absolute error
+// of about 2^-44 (|a| + |b|) (distances, Jastrow terms): one two_sum.
+__host__ __device__ __forceinline__ df df_add_fast(df a, df b)
+{
+  df s = two_sum(a.hi, b.hi);
+  float e = DF_ADD(s.lo, DF_ADD(a.lo, b.lo));
+  return fast_two_sum(s.hi, e);
+}
+
+__host__ __device__ __forceinline__ df df_sub_fast(df a, df b) { return df_add_fast(a, df_neg(b)); }
+
 __host__ __device__ __forceinline__ df df_add_f(df a, float b)
 {
   df s = two_sum(a.hi, b);
@@ -207,7 +218,7 @@ DF_HEAVY df df_exp(df a, const ExpConsts& K, const float2* tab)
   df r2 = df_sqr(r);
   r2.hi = DF_MUL(r2.hi, 0.5f);
   r2.lo = DF_MUL(r2.lo, 0.5f);
-  df e = df_add(r, r2);
+  df e = df_add_fast(r, r2);  // r2 = r^2/2 <= |r| ln2/256: no cancellation
   e = df_add_f(e, tail);
   e = df_add_f(e, 1.0f);
   int j = m & 63;
@@ -233,17 +244,6 @@ DF_HEAVY df df_log(df a, const ExpConsts& K, const float2* tab)
   return df_add_f(t, y0);
 }
 
-// Cheaper addition for operands whose sum is used with an absolute error
-// of about 2^-44 (|a| + |b|) (distances, Jastrow terms): one two_sum.
-__host__ __device__ __forceinline__ df df_add_fast(df a, df b)
-{
-  df s = two_sum(a.hi, b.hi);
-  float e = DF_ADD(s.lo, DF_ADD(a.lo, b.lo));
-  return fast_two_sum(s.hi, e);
-}
-
-__host__ __device__ __forceinline__ df df_sub_fast(df a, df b) { return df_add_fast(a, df_neg(b)); }
-
 // sin(pi x) and cos(pi x) for a double-float x in about [0, 2]: x = (n +
 // r)/2 with integer n and |r| <= 1/2, theta = r pi/2 (|theta| <= pi/4),
 // Taylor series of sin and cos in theta^2 to degree 15 and 16 (truncation
@@ -259,13 +259,13 @@ DF_HEAVY void df_sincospi(df x, const df* inv_fact, df half_pi, df* s_out, df* c
   df ps = df_neg(inv_fact[15]);
   for (int j = 6; j >= 0; --j) {
     df cj = inv_fact[2 * j + 1];
-    ps = df_add(df_mul(ps, z), (j & 1) ? df_neg(cj) : cj);
+    ps = df_add_fast(df_mul(ps, z), (j & 1) ? df_neg(cj) : cj);
   }
   df sn = df_mul(th, ps);
   df pc = inv_fact[16];
   for (int j = 7; j >= 0; --j) {
     df cj = inv_fact[2 * j];
-    pc = df_add(df_mul(pc, z), (j & 1) ? df_neg(cj) : cj);
+    pc = df_add_fast(df_mul(pc, z), (j & 1) ? df_neg(cj) : cj);
   }
   const int q = ((int)n) & 3;
   df so = sn, co = pc;
