@@ -134,34 +134,48 @@ class ClockSampler:
 
 # FP32 operation counts of the double-float primitives as implemented in
 # csrc/df64.cuh (add/sub/mul = 1, fma = 2, MUFU seed = 1).
-DF_ADD, DF_ADD_FAST, DF_ADD_F, DF_MUL, DF_SQR = 20, 11, 10, 10, 9
-DF_DIV, DF_SQRT, DF_EXP, DF_LOG = 31, 30, 110, 142
+DF_ADD, DF_ADD_FAST, DF_ADD_F, DF_MUL, DF_SQR = 11, 11, 10, 10, 9
+DF_DIV, DF_SQRT, DF_EXP, DF_LOG = 11, 10, 101, 132
 FP32_PEAK_TFLOPS = 80.5  # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 
 
 def df_flops_per_move(system, G):
     """Algorithmic FP32 work of one walker-move in the double-float
-    formulation: the double-float operations of one evaluation of all
-    P = 6 G N moves and of the local energy, plus the jump, weighted by the
-    FP32 operation count of each primitive. Counted from the formulas."""
+    formulation the kernels use: the double-float operations of one
+    evaluation of all P = 6 G N moves (from the electron-pair and
+    electron-nucleus caches, which the evaluation fills once) and of the
+    local energy, plus the jump, each weighted by the FP32 flops of its
+    primitive (FMA = 2; additions inside the evaluation are the one-two_sum
+    form, division and square root one FMA-residual correction). Counted
+    from the formulas."""
     N, n_nuc, n_ao = system.N, system.n_nuc, system.n_ao
     exps = len({(s.center, s.zeta) for s in system.shells if s.kind == 0}) + \
         sum(len(s.alpha) for s in system.shells if s.kind == 1)
     P = 6 * G * N
     dist = 3 * DF_ADD_FAST + 3 * DF_SQR + 2 * DF_ADD_FAST + DF_SQRT
-    per_cand = (3 * (DF_MUL + DF_ADD)                                    # displaced position
-                + n_nuc * (dist + 3 * DF_MUL + DF_ADD_F + DF_DIV + DF_ADD)  # nucleus distance, e-n term
+    proj = 9 * DF_MUL + 6 * DF_ADD                                           # e_k . d on three axes
+    cached = N <= 24
+    if cached:
+        fill = N * (N - 1) // 2 * (3 * DF_ADD + 3 * DF_SQR + 2 * DF_ADD + proj) + \
+            N * n_nuc * (3 * DF_ADD + 3 * DF_SQR + 2 * DF_ADD + proj)
+        ee = (N - 1) * (DF_MUL + 2 * DF_ADD + DF_SQRT + 4 * DF_MUL + DF_ADD_F + DF_ADD) + DF_DIV
+    else:
+        fill = N * n_nuc * (3 * DF_ADD + 3 * DF_SQR + 2 * DF_ADD + proj)
+        ee = (N - 1) * (dist + 4 * DF_MUL + DF_ADD_F + DF_ADD) + DF_DIV
+    per_cand = (3 * DF_MUL                                                    # h e_k
+                + n_nuc * (DF_MUL + 3 * DF_ADD + 2 * DF_ADD + DF_SQRT           # d, |d|^2 from the cache
+                           + DF_MUL + DF_ADD_F + DF_DIV + DF_ADD                 # e-n term
+                           + (2 * DF_ADD if G == 2 else 0))                      # midpoint distance
                 + exps * (DF_MUL + DF_EXP) + n_ao * (DF_MUL + DF_ADD) + 2 * n_ao * DF_MUL  # basis, dot
-                + (N - 1) * (dist + 4 * DF_MUL + DF_ADD_F + DF_ADD_FAST) + DF_DIV  # e-e Pade fraction
-                + 2 * DF_ADD + DF_EXP + DF_MUL                                  # Jastrow ratio
-                + ((3 * (DF_MUL + DF_ADD) + n_nuc * (3 * DF_ADD_FAST + 3 * DF_SQR + 2 * DF_ADD_FAST)
-                    + DF_MUL + DF_EXP + DF_ADD_F) if G == 2 else 0)             # p at the midpoint
+                + ee                                                             # e-e Pade terms
+                + 2 * DF_ADD + DF_EXP + DF_MUL                                   # Jastrow ratio
+                + ((DF_MUL + DF_EXP + DF_ADD_F) if G == 2 else 0)                # p at the midpoint
                 + 2 * DF_MUL)                                                    # rate
     pair_el = dist + 2 * DF_DIV + 10 * DF_MUL + 8 * DF_ADD                      # u', u'', gradients
     el = N * (n_nuc * (dist + DF_DIV) + exps * (DF_MUL + DF_EXP) + n_ao * (12 * DF_MUL + 8 * DF_ADD)
               + (N - 1 + n_nuc) * pair_el + 8 * DF_MUL + 8 * DF_ADD)
     jump = DF_LOG + DF_DIV + 2 * P * DF_ADD + n_ao * (DF_MUL + DF_EXP / 3)      # time, scans, orbitals
-    return P * per_cand + el + jump
+    return P * per_cand + fill + el + jump
 
 
 def measure_leg(args, pkg, torch, system, precision, dev, rank, seed, x0, with_clocks, neural=None):
