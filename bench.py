@@ -407,6 +407,11 @@ def neural_leg(args, pkg, torch, system, precision, dev, rank, seed, x0):
     spec = S.default_neural_spec(system)
     plain = pkg.LrdmcSystem(system).set_precision(precision)
     sp = pkg.Spacing(pkg.THIS_WORK)
+    # one untimed training step on a few start configurations first: PyTorch
+    # compiles its own kernels (loss reductions, the optimiser) on first use
+    xw = torch.tensor(x0[:256], device="cuda")
+    gw, ew = plain.base_terms(xw)
+    N.train(plain, spec, S.neural_init(spec, seed), xw, gw, ew, steps=1, batch=256, seed=seed)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     n_cfg = 16 * len(x0)

@@ -19,6 +19,8 @@ Usage: python -m paper_1909_01589_gb300.experiments [--systems He,Ne,Ar,Kr]
        [--steps 1000] [--out results/single_vs_double.json]
        python -m paper_1909_01589_gb300.experiments --neural --systems Ne,Ar
        [--steps 600] [--out results/neural_vs_pade.json]
+       python -m paper_1909_01589_gb300.experiments --extrapolate --systems He
+       [--steps 2000] [--out results/extrapolation_he.json]
 """
 from __future__ import annotations
 
@@ -199,6 +201,38 @@ def neural_vs_pade(names=("Ne", "Ar"), W=16384, steps=600, equil=150, n_train=1 
     return rows
 
 
+def extrapolation(name="He", a_values=(0.4, 0.3, 0.2, 0.15, 0.1), W=8192, steps=2000, equil=200, seed=5):
+    """E(a) on the single grid and on this work's double grid at several
+    lattice spacings, and the a -> 0 limits from the weighted least-squares
+    fit E(a) = E0 + k1 a^2 + k2 a^4 (the three-parameter fit of the paper's
+    benzene footnote). For He the guiding function is nodeless, so both
+    limits must reach the exact ground-state energy."""
+    import lrdmc_synth as S
+
+    system = S.make_system(name)
+    e_trial = DEFAULTS[name][1]
+    out = {"system": name, "a": list(a_values), "walkers": W, "steps": steps}
+    for label, sp in (("single", Spacing(SINGLE)), ("double_this_work", Spacing(THIS_WORK))):
+        E, err = [], []
+        for a in a_values:
+            tau = _tau_for(system, a, sp, 10.0, seed)
+            r = run(system, a, sp, W, steps, equil, tau, e_trial, seed)
+            E.append(r["energy"])
+            err.append(r["error"])
+        E, err = np.array(E), np.array(err)
+        A = np.stack([np.ones_like(E), np.asarray(a_values) ** 2, np.asarray(a_values) ** 4], 1)
+        wt = 1.0 / err ** 2
+        cov = np.linalg.inv(A.T @ (A * wt[:, None]))
+        coef = cov @ (A.T @ (wt * E))
+        chi2 = float(np.sum(wt * (A @ coef - E) ** 2))
+        out[label] = {"E": E.tolist(), "error": err.tolist(), "E0": float(coef[0]),
+                      "E0_error": float(np.sqrt(cov[0, 0])), "k1": float(coef[1]), "k2": float(coef[2]),
+                      "chi2_per_dof": chi2 / max(1, len(E) - 3)}
+        print(f"{name} {label}: E0 = {coef[0]:.5f} +- {np.sqrt(cov[0, 0]):.5f} (chi2/dof "
+              f"{out[label]['chi2_per_dof']:.2f}); E(a) = {np.round(E, 5).tolist()}", flush=True)
+    return out
+
+
 def summarize(rows):
     """Derived quantities of the Fig. 2 analogue: GPU seconds per walker per
     unit of projection time (single grid, this work's double grid, the
@@ -251,7 +285,13 @@ def main():
     ap.add_argument("--out", default="results/single_vs_double.json")
     ap.add_argument("--summarize", nargs="*", help="only write the markdown table of these result files")
     ap.add_argument("--neural", action="store_true", help="the neural Jastrow against Pade instead")
+    ap.add_argument("--extrapolate", action="store_true", help="E(a) and the a -> 0 fit instead (first system)")
     args = ap.parse_args()
+    if args.extrapolate:
+        row = extrapolation(args.systems.split(",")[0], steps=args.steps, equil=args.equil)
+        os.makedirs(os.path.dirname(args.out) or ".", exist_ok=True)
+        json.dump(row, open(args.out, "w"), indent=1)
+        return
     if args.neural:
         rows = neural_vs_pade(args.systems.split(","), steps=args.steps, equil=args.equil)
         os.makedirs(os.path.dirname(args.out) or ".", exist_ok=True)
