@@ -1,13 +1,21 @@
-"""LRDMC throughput benchmark: walker-moves/s of the GB300 FP64 path.
+"""LRDMC throughput benchmark: walker-moves/s and efficiency 1/(sigma^2 t)
+of the GB300 library against its plain FP64 form.
 
 Workload: all-electron Ne (Z = 10, 5 up / 5 down), Slater-Jastrow trial
 function, 4096 walkers, lattice spacing a = 0.2 bohr with the paper's
 double grid (Gaussian p of Eq. 3, r_c from S-13, a'/a from Eq. 6/7),
-tau = 0.025 Ha^-1 per reconfiguration interval, FP64. One step = one
-interval: for every walker the continuous-time loop of waiting time,
-heat-bath jump, Sherman-Morrison update, new lattice rotation and
-evaluation of all 12 N = 120 lattice moves and the local energy, then comb
-reconfiguration of the population.
+tau = 0.025 Ha^-1 per reconfiguration interval. One step = one interval:
+for every walker the continuous-time loop of waiting time, heat-bath jump,
+Sherman-Morrison update, new lattice rotation and evaluation of all
+12 N = 120 lattice moves and the local energy, then comb reconfiguration
+of the population.
+
+The headline line times the default arithmetic (double-float evaluation
+with FP64 state, the FP64-parity mode; --precision chooses another). Extra
+legs on the same line: the plain FP64 mode, the mixed FP32 mode, the
+trained neural pair Jastrow, a heterogeneous batch of five systems, the
+end-to-end figure through the public API from host memory, and the CPU
+oracle as a baseline.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun (N > 1) every rank runs an independent population (replicas;

@@ -1,18 +1,24 @@
-// CUDA kernels (sm_103a, FP64) of the LRDMC hot path.
+// CUDA kernels (sm_103a) of the LRDMC hot path.
 //
 // One warp owns one walker at a time. Shared memory holds the walker's
 // positions, inverse Slater matrices, lattice rotation, the P jump rates of
-// its cached evaluation and per-electron work vectors; the MO coefficients
-// are staged once per block. The lanes split the P lattice moves of an
-// evaluation, the electrons of the local energy, the orbitals and matrix
-// entries of the Sherman-Morrison update, and the rows of the Gauss-Jordan
-// inverse. Kernels:
+// its cached evaluation, per-electron work vectors and (double-float mode)
+// the electron-pair and electron-nucleus caches of the evaluation; the MO
+// coefficients are staged once per block. The lanes split the P lattice
+// moves of an evaluation, the electrons of the local energy, the orbitals
+// and matrix entries of the Sherman-Morrison update, and the rows of the
+// Gauss-Jordan inverse. The evaluation runs in IEEE double, in double-float
+// on the FP32 pipe, or in single precision (the kernels' template argument
+// carries the arithmetic and whether the neural pair term is set); inverses,
+// updates, weights and reconfiguration stay in IEEE double. Kernels:
 //   k_init      start configurations -> inverses, first rotation
 //   k_eval_all  evaluate every walker (after a change of lattice)
 //   k_interval  one interval tau of continuous-time projection per walker,
 //               walkers fetched dynamically by the warps (ragged jump counts)
 //   k_reconfig  weights, trace entry and comb parents (one block)
-//   k_evaluate  stateless evaluation of given configurations
+//   k_evaluate  stateless evaluation of given configurations (and the
+//               variant with static scratch, k_evaluate_static)
+//   k_base_terms  gradients and local energies without the neural term
 // The population is double-buffered: k_interval gathers the record of
 // parent[s] from the source buffer, so reconfiguration needs no copy pass.
 #include <math.h>
