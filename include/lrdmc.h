@@ -116,7 +116,15 @@ typedef struct {
  * [n_ao][n_mo] row-major shared by both spins (spin down uses the first
  * n_dn columns), Jastrow parameters. All inputs are host memory, copied.
  * Limits: n_nuc <= LRDMC_MAX_NUC, n_shell <= LRDMC_MAX_SHELL,
- * n_ao <= LRDMC_MAX_AO, n_up <= LRDMC_MAX_SPIN, n_mo >= n_up. No GPU work. */
+ * n_ao <= LRDMC_MAX_AO, n_up <= LRDMC_MAX_SPIN, n_mo >= n_up; and the
+ * shared memory of one block of four walkers (positions, inverse Slater
+ * matrices, rates, projected inverse columns and scratch, which grow as
+ * N^2 and N n_ao) must fit in 227 KB. A system whose block fits only
+ * without the double-float evaluation caches is laid out without them
+ * (same results, slower double-float evaluation): e.g. 48 electrons on 8
+ * centres with 42 AOs. 64 electrons with 62 AOs do not fit at all; such
+ * systems fail with LRDMC_ERR_ARG and a message giving the size. No GPU
+ * work. */
 LRDMC_API lrdmc_status lrdmc_create_system(int n_nuc, const double* nuc_xyz, const double* Z,
                                  int n_up, int n_dn, const lrdmc_shell* shells, int n_shells,
                                  const double* mo_coeff, int n_ao, int n_mo,

@@ -200,6 +200,40 @@ def tiny_mixed(seed: int = 7) -> System:
     )
 
 
+def cluster(n_centers: int = 8, n_per_spin: int = 24, d_shells: int = 0, seed: int = 3) -> System:
+    """Synthetic many-centre system for size checks: nuclei (Z = 3) on a
+    cube-like grid 2.5 bohr apart, each with a 1s (zeta 2.2) and a 2p
+    (zeta 1.1) Slater shell, 3d shells (zeta 0.9) on the first d_shells
+    centres; n_per_spin electrons per spin in the first orbitals of a
+    diagonally dominant coefficient matrix (orbital m is AO m plus small
+    admixtures), e-n factors with the 1s cusp."""
+    rng = np.random.default_rng(seed)
+    pts = [(i, j, k) for i in range(2) for j in range(2) for k in range(2)]
+    pts += [(i, j, 2) for i in range(2) for j in range(2)]
+    xyz = 2.5 * np.array(pts[:n_centers], dtype=np.float64)
+    Zs = np.full(n_centers, 3.0)
+    shells = []
+    for c in range(n_centers):
+        shells.append(Shell(c, 0, STO, 1.0, 2.2))
+        shells.append(Shell(c, 1, STO, 2.0, 1.1))
+    for c in range(d_shells):
+        shells.append(Shell(c, 2, STO, 3.0, 0.9))
+    n_ao = sum(2 * sh.l + 1 for sh in shells)
+    if n_per_spin > n_ao:
+        raise ValueError("more electrons per spin than orbitals")
+    C = 0.05 * rng.normal(size=(n_ao, n_per_spin))
+    for m in range(n_per_spin):
+        C[m, m] += 1.0
+    owner = []
+    for q, sh in enumerate(shells):
+        owner += [q] * (2 * sh.l + 1)
+    return System(
+        name="cluster", nuc_xyz=xyz, Z=Zs, n_up=n_per_spin, n_dn=n_per_spin, shells=shells, C=C,
+        b_ee=1.0, c_par=0.25, c_anti=0.5, en_b1=np.full(n_centers, 3.0 - 2.2), en_b2=1.0,
+        orbital_shell=owner[:n_per_spin],
+    )
+
+
 # ---------------------------------------------------------------- Gaussian fits
 _FIT_CACHE = {}
 

@@ -360,7 +360,20 @@ lrdmc_status lrdmc_create_system(int n_nuc, const double* nuc_xyz, const double*
   }
   S.precision = LRDMC_PRECISION_DF64;
   fill_df_constants(S);
-  s->Lo = make_layout(S);
+  // one block holds kWarpsPerBlock walkers in shared memory; without room
+  // for the evaluation caches the system runs without them, and a system
+  // that does not fit even then is rejected
+  s->Lo = make_layout(S, true);
+  if (s->Lo.smem_block_bytes > kMaxSmemBlock) s->Lo = make_layout(S, false);
+  if (s->Lo.smem_block_bytes > kMaxSmemBlock) {
+    static std::string msg;
+    msg = "create_system: " + std::to_string(S.N) + " electrons with " + std::to_string(n_ao) +
+          " AOs need " + std::to_string(s->Lo.smem_block_bytes / 1024) + " KB of shared memory per block of " +
+          std::to_string(kWarpsPerBlock) + " walkers (at most " + std::to_string(kMaxSmemBlock / 1024) + " KB)";
+    g_static_error = msg.c_str();
+    delete s;
+    return LRDMC_ERR_ARG;
+  }
   *out = s;
   return LRDMC_OK;
 }

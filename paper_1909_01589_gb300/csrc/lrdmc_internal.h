@@ -115,9 +115,14 @@ struct Layout {
   int smem_block_bytes;
   int n_pc;       // electron pairs with a cached distance and projections (0: no cache)
   int pcw;        // double-floats per cached pair: 4 (distance, projections) or 8 (+ Jastrow pair terms)
+  int enc;        // 1: the electron-nucleus cache (and the pair cache, if any) is in the layout
 };
 
-Layout make_layout(const SysDev& S);
+// Shared-memory layout of a system; caches = false leaves out the
+// evaluation caches (for systems that would not fit otherwise).
+Layout make_layout(const SysDev& S, bool caches);
+// Largest dynamic shared memory of one block on sm_100-class GPUs (227 KB).
+constexpr int kMaxSmemBlock = 232448;
 
 struct PopDev {
   double* rec_src;

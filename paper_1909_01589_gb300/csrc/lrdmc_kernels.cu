@@ -544,7 +544,7 @@ __device__ __forceinline__ WarpMem warp_mem(const Layout& Lo, const SysDev& S, d
   m.Rd = m.xd + 3 * Lo.N;
   m.pc = m.Rd + 12;
   m.enc = m.pc + Lo.pcw * Lo.n_pc;
-  m.scr = reinterpret_cast<double*>(m.enc + 8 * Lo.N * S.n_nuc);
+  m.scr = reinterpret_cast<double*>(m.enc + (Lo.enc ? 8 * Lo.N * S.n_nuc : 0));
   m.n_pc = Lo.n_pc;
   m.pcw = Lo.pcw;
   return m;
@@ -1029,7 +1029,7 @@ __device__ void fill_pair_cache(const SysDev& S, const WarpMem& wm, int lane)
                      A::mul(A::c(wm.Rd[6 + k]), d[2]));
       e[1 + k] = A::store(pk);
     }
-    if ((wm.pcw == 8 && NJ)) {
+    if ((wm.pcw == 8 && wm.n_pc > 0 && NJ)) {
       // with the neural term, the pair's Jastrow terms for the local energy
       // (Pade plus neural): u, u'/r, u'' + 2 u'/r, and 1/r (with the Pade
       // factor alone, evaluating them inside the local energy is faster)
@@ -1054,6 +1054,24 @@ __device__ void fill_pair_cache(const SysDev& S, const WarpMem& wm, int lane)
       e[7] = A::store(irr);
     }
   }
+}
+
+// num and den times the power of two that brings den (positive, normal,
+// below 2^127) into [1, 2): exact, so num/den keeps its value bit for bit.
+__device__ __forceinline__ void pow2_rescale(float& num, float& den)
+{
+  const float s = __int_as_float((254 - ((__float_as_int(den) >> 23) & 0xff)) << 23);
+  num *= s;
+  den *= s;
+}
+
+__device__ __forceinline__ void pow2_rescale(df& num, df& den)
+{
+  const float s = __int_as_float((254 - ((__float_as_int(den.hi) >> 23) & 0xff)) << 23);
+  num.hi *= s;
+  num.lo *= s;
+  den.hi *= s;
+  den.lo *= s;
 }
 
 // sum_{j != i} u_ee(|r_i + h e_k - r_j|) from the pair cache (h carries
@@ -1087,13 +1105,18 @@ __device__ NT jastrow_ee_cached_m(const SysDev& S, const df* pc, int pcw, int i,
     den = A::mul(den, dj);
     if (NJ) nn = A::add(nn, nj_value_m<NT>(S, nj_ch_ee(S, i, j), r));
     q += (j < i) ? N - j - 2 : 1;
+    if ((j & 15) == 15) pow2_rescale(num, den);  // every 16 partners, as in jastrow_ee_m
   }
   return A::add(A::div(num, den), nn);
 }
 
 // sum_{j != i} u_ee(|p - r_j|): the Pade terms c r/(1 + b r) (all of one
 // sign) are summed as one running fraction num/den, so one division serves
-// all partners.
+// all partners. Every 16 partners pow2_rescale brings den back into [1, 2):
+// the product of the (1 + b r) would otherwise leave the float exponent
+// range (about 3.4e38) that double-floats and floats share, as 47 partners
+// a few bohr away do; 16 factors fit while their geometric mean stays
+// below 200.
 template <class NT, bool NJ>
 __device__ NT jastrow_ee_m(const SysDev& S, const df* xd, int i, const NT p[3])
 {
@@ -1111,6 +1134,7 @@ __device__ NT jastrow_ee_m(const SysDev& S, const df* xd, int i, const NT p[3])
     num = A::add_fast(A::mul(num, dj), A::mul(A::mul(c, r), den));
     den = A::mul(den, dj);
     if (NJ) nn = A::add(nn, nj_value_m<NT>(S, nj_ch_ee(S, i, j), r));
+    if ((j & 15) == 15) pow2_rescale(num, den);
   }
   return A::add(A::div(num, den), nn);
 }
@@ -1258,7 +1282,7 @@ __device__ LRDMC_EL void el_parts_m(const SysDev& S, const WarpMem& wm, int i, i
   // e-e pairs
   const int si = spin_of(S, i);
   const NT b = A::c(S.D.b_ee);
-  if (sizeof(NT) == sizeof(df) && (wm.pcw == 8 && NJ)) {
+  if (sizeof(NT) == sizeof(df) && (wm.pcw == 8 && wm.n_pc > 0 && NJ)) {
     // every pair's terms come from the pair cache (evaluated once per pair)
     for (int j = part; j < S.N; j += L) {
       if (j == i) continue;
@@ -1347,7 +1371,7 @@ __device__ __forceinline__ NT el_local(const ElParts<NT>& o)
   return A::add(A::mul_f(lap, -0.5f), o.V);
 }
 
-template <class NT, bool NJ>
+template <class NT, bool NJ, bool NC>
 __device__ void warp_eval_m(const SysDev& S, const double* sC, const LatDev& L, const WarpMem& wm, int lane,
                             double* ratio_out, double& b, df& bdf, double& el)
 {
@@ -1373,7 +1397,10 @@ __device__ void warp_eval_m(const SysDev& S, const double* sC, const LatDev& L, 
   for (int j = lane; j < 3 * N; j += 32) wm.xd[j] = A::store(A::from_double(wm.x[j]));
   if (lane < 9) wm.Rd[lane] = A::store(A::from_double(wm.R[lane]));
   __syncwarp();
-  constexpr bool kUsePairCache = sizeof(NT) == sizeof(df);
+  // the caches pay in double-float arithmetic only, and exist only when
+  // the system's layout has room for them (NC is set otherwise: the
+  // kernels of such systems carry no cached code)
+  constexpr bool kUsePairCache = sizeof(NT) == sizeof(df) && !NC;
   if (kUsePairCache) {
     fill_pair_cache<NT, NJ>(S, wm, lane);
     fill_en_cache<NT>(S, wm, lane);
@@ -1459,15 +1486,15 @@ __device__ void warp_eval_m(const SysDev& S, const double* sC, const LatDev& L, 
   b = A::to_double(btot);
 }
 
-template <int PREC, bool NJ>
+template <int PREC, bool NJ, bool NC>
 __device__ __forceinline__ void warp_eval_any(const SysDev& S, const double* sC, const LatDev& L,
                                               const WarpMem& wm, int lane, double* ratio_out, double& b,
                                               df& bdf, double& el)
 {
   if (PREC == LRDMC_PRECISION_DF64) {
-    warp_eval_m<df, NJ>(S, sC, L, wm, lane, ratio_out, b, bdf, el);
+    warp_eval_m<df, NJ, NC>(S, sC, L, wm, lane, ratio_out, b, bdf, el);
   } else if (PREC == LRDMC_PRECISION_FP32) {
-    warp_eval_m<float, NJ>(S, sC, L, wm, lane, ratio_out, b, bdf, el);
+    warp_eval_m<float, NJ, true>(S, sC, L, wm, lane, ratio_out, b, bdf, el);
   } else {
     warp_eval<NJ>(S, sC, L, wm, lane, ratio_out, b, el);
     bdf = df_make(0.0f, 0.0f);
@@ -1690,6 +1717,7 @@ k_eval_all(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
 {
   constexpr int PR = PREC & 3;         // the arithmetic (LRDMC_PRECISION_*)
   constexpr bool NJ = (PREC & 8) != 0;  // the neural pair term is set
+  constexpr bool NC = (PREC & 4) != 0;  // the layout has no evaluation caches
   extern __shared__ double smem[];
   double* sC = smem;
   stage_coefficients(S, sC);
@@ -1701,7 +1729,7 @@ k_eval_all(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
   double b, el;
   df bdf;
   load_record(Lo, rec, wm, lane, b, el);
-  warp_eval_any<PR, NJ>(S, sC, L, wm, lane, nullptr, b, bdf, el);
+  warp_eval_any<PR, NJ, NC>(S, sC, L, wm, lane, nullptr, b, bdf, el);
   if (!isfinite(el) || !isfinite(b)) {
     if (lane == 0) atomicOr(P.err, kErrNonFinite);
   }
@@ -1721,6 +1749,7 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
 {
   constexpr int PR = PREC & 3;         // the arithmetic (LRDMC_PRECISION_*)
   constexpr bool NJ = (PREC & 8) != 0;  // the neural pair term is set
+  constexpr bool NC = (PREC & 4) != 0;  // the layout has no evaluation caches
   extern __shared__ double smem[];
   double* sC = smem;
   // interval k from the device counter (advanced by k_reconfig); the inverse
@@ -1815,7 +1844,7 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
       __syncwarp();
       rotation_matrix_warp<PR>(b1, wm.R, lane, S);
       __syncwarp();
-      warp_eval_any<PR, NJ>(S, sC, L, wm, lane, nullptr, b, bdf, el);
+      warp_eval_any<PR, NJ, NC>(S, sC, L, wm, lane, nullptr, b, bdf, el);
       ++jumps;
       if (!isfinite(el) || !isfinite(b)) {
         if (lane == 0) atomicOr(P.err, kErrNonFinite);
@@ -1969,6 +1998,7 @@ k_evaluate(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, in
 {
   constexpr int PR = PREC & 3;         // the arithmetic (LRDMC_PRECISION_*)
   constexpr bool NJ = (PREC & 8) != 0;  // the neural pair term is set
+  constexpr bool NC = (PREC & 4) != 0;  // the layout has no evaluation caches
   extern __shared__ double smem[];
   double* sC = smem;
   stage_coefficients(S, sC);
@@ -1988,7 +2018,7 @@ k_evaluate(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, in
   const int P = S.N * 6 * L.G;
   double b, el;
   df bdf;
-  warp_eval_any<PR, NJ>(S, sC, L, wm, lane, ratio ? ratio + (size_t)c * P : nullptr, b, bdf, el);
+  warp_eval_any<PR, NJ, NC>(S, sC, L, wm, lane, ratio ? ratio + (size_t)c * P : nullptr, b, bdf, el);
   if (T)
     for (int j = lane; j < P; j += 32)
       T[(size_t)c * P + j] = (PR != LRDMC_PRECISION_FP64) ? df_to_double(reinterpret_cast<const df*>(wm.T)[j])
@@ -2060,7 +2090,7 @@ void fill_lattice_df(LatDev& L)
 static_assert(sizeof(SysDev) + sizeof(Layout) + sizeof(LatDev) + sizeof(PopDev) + 64 < 32764,
               "kernel parameters exceed the 32 KB limit");
 
-Layout make_layout(const SysDev& S)
+Layout make_layout(const SysDev& S, bool caches)
 {
   Layout Lo;
   Lo.N = S.N;
@@ -2079,15 +2109,16 @@ Layout make_layout(const SysDev& S)
   int scr = 2 * n * n + n * S.n_ao;          // Gauss-Jordan + orbital rows
   int scr_sm = S.n_ao + 3 * n + n * n;       // Sherman-Morrison (FP64 or double-float)
   if (scr_sm > scr) scr = scr_sm;
-  // the pair cache of the FP32-pipe evaluations, up to 24 electrons (beyond,
-  // 4 df per pair would cost blocks per SM)
-  // (distance and projections); up to 12 electrons room for the pair's
-  // Jastrow terms too (used with the neural term: the local energy then
-  // evaluates every pair once)
-  Lo.n_pc = S.N <= 24 ? S.N * (S.N - 1) / 2 : 0;
+  // The caches of the double-float evaluation (omitted when caches is false):
+  // the electron-nucleus cache (8 df per electron and nucleus), and the pair
+  // cache up to 24 electrons (beyond, its 4 df per pair would cost blocks
+  // per SM), with room for the pair's Jastrow terms up to 12 electrons (used
+  // with the neural term: the local energy then evaluates every pair once)
+  Lo.n_pc = (caches && S.N <= 24) ? S.N * (S.N - 1) / 2 : 0;
   Lo.pcw = S.N <= 12 ? 8 : 4;
+  Lo.enc = caches ? 1 : 0;
   Lo.smem_warp = 3 * S.N + S.n_up * S.n_up + S.n_dn * S.n_dn + 12 + Lo.P_max + S.N * S.n_ao + S.N +
-                 (3 * S.N + 12) + Lo.pcw * Lo.n_pc + 8 * S.N * S.n_nuc + scr;
+                 (3 * S.N + 12) + Lo.pcw * Lo.n_pc + (Lo.enc ? 8 * S.N * S.n_nuc : 0) + scr;
   Lo.smem_warp = (Lo.smem_warp + 1) & ~1;
   Lo.head = ((2 * S.n_ao * S.n_mo + (S.n_ao * S.n_mo + 1) / 2 + 64) + 1) & ~1;
   Lo.smem_block_bytes = (int)sizeof(double) * (Lo.head + kWarpsPerBlock * Lo.smem_warp);
@@ -2111,22 +2142,27 @@ cudaError_t launch_init(const SysDev& S, const Layout& Lo, const PopDev& P, cons
 }
 
 // Kernel variant of a system: the arithmetic in bits 0-1 of the template
-// argument, the neural pair term in bit 3 (kernels without it carry none of
-// its code).
+// argument, bit 2 for a double-float system whose layout has no evaluation
+// caches, the neural pair term in bit 3 (kernels without a feature carry
+// none of its code).
+constexpr int kNoCacheBit = 4;
 constexpr int kNjBit = 8;
 
-#define LRDMC_DISPATCH(S, ...)                                                     \
+#define LRDMC_DISPATCH_NJ(S, BASE, ...)                                            \
   do {                                                                             \
-    const bool nj_ = (S).nj_on != 0;                                               \
+    if ((S).nj_on != 0) { constexpr int V = (BASE) | kNjBit; __VA_ARGS__; }        \
+    else { constexpr int V = (BASE); __VA_ARGS__; }                                \
+  } while (0)
+
+#define LRDMC_DISPATCH(S, Lo, ...)                                                 \
+  do {                                                                             \
     if ((S).precision == LRDMC_PRECISION_DF64) {                                   \
-      if (nj_) { constexpr int V = LRDMC_PRECISION_DF64 | kNjBit; __VA_ARGS__; }          \
-      else { constexpr int V = LRDMC_PRECISION_DF64; __VA_ARGS__; }                       \
+      if ((Lo).enc) LRDMC_DISPATCH_NJ(S, LRDMC_PRECISION_DF64, __VA_ARGS__);       \
+      else LRDMC_DISPATCH_NJ(S, LRDMC_PRECISION_DF64 | kNoCacheBit, __VA_ARGS__);  \
     } else if ((S).precision == LRDMC_PRECISION_FP32) {                            \
-      if (nj_) { constexpr int V = LRDMC_PRECISION_FP32 | kNjBit; __VA_ARGS__; }          \
-      else { constexpr int V = LRDMC_PRECISION_FP32; __VA_ARGS__; }                       \
+      LRDMC_DISPATCH_NJ(S, LRDMC_PRECISION_FP32, __VA_ARGS__);                     \
     } else {                                                                       \
-      if (nj_) { constexpr int V = LRDMC_PRECISION_FP64 | kNjBit; __VA_ARGS__; }          \
-      else { constexpr int V = LRDMC_PRECISION_FP64; __VA_ARGS__; }                       \
+      LRDMC_DISPATCH_NJ(S, LRDMC_PRECISION_FP64, __VA_ARGS__);                     \
     }                                                                              \
   } while (0)
 
@@ -2144,7 +2180,7 @@ static cudaError_t launch_eval_all_t(const SysDev& S, const Layout& Lo, const La
 cudaError_t launch_eval_all(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P,
                             cudaStream_t st)
 {
-  LRDMC_DISPATCH(S, return launch_eval_all_t<V>(S, Lo, L, P, st));
+  LRDMC_DISPATCH(S, Lo, return launch_eval_all_t<V>(S, Lo, L, P, st));
   return cudaErrorInvalidValue;
 }
 
@@ -2168,7 +2204,7 @@ static cudaError_t interval_occupancy(const Layout& Lo, int* blocks)
 int interval_default_blocks(const SysDev& S, const Layout& Lo)
 {
   int b = 0;
-  LRDMC_DISPATCH(S, interval_occupancy<V>(Lo, &b));
+  LRDMC_DISPATCH(S, Lo, interval_occupancy<V>(Lo, &b));
   return b;
 }
 
@@ -2212,7 +2248,7 @@ static cudaError_t launch_interval_t(const SysDev& S, const Layout& Lo, const La
 cudaError_t launch_interval(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P, int blocks,
                             cudaStream_t st, int carveout)
 {
-  LRDMC_DISPATCH(S, return launch_interval_t<V>(S, Lo, L, P, blocks, carveout, st));
+  LRDMC_DISPATCH(S, Lo, return launch_interval_t<V>(S, Lo, L, P, blocks, carveout, st));
   return cudaErrorInvalidValue;
 }
 
@@ -2281,7 +2317,7 @@ cudaError_t launch_evaluate(const SysDev& S, const Layout& Lo, const LatDev& L, 
                             const double* x, const double* rot, double* ratio, double* T,
                             double* b, double* el, int* err, cudaStream_t st)
 {
-  LRDMC_DISPATCH(S, return launch_evaluate_t<V>(S, Lo, L, n, x, rot, ratio, T, b, el, err, st));
+  LRDMC_DISPATCH(S, Lo, return launch_evaluate_t<V>(S, Lo, L, n, x, rot, ratio, T, b, el, err, st));
   return cudaErrorInvalidValue;
 }
 
@@ -2310,6 +2346,7 @@ k_evaluate_static(const __grid_constant__ SysDev S, const Layout Lo, const LatDe
 {
   constexpr int PR = PREC & 3;         // the arithmetic (LRDMC_PRECISION_*)
   constexpr bool NJ = (PREC & 8) != 0;  // the neural pair term is set
+  constexpr bool NC = (PREC & 4) != 0;  // the layout has no evaluation caches
   extern __shared__ double smem[];
   double* sC = smem;
   stage_coefficients(S, sC);
@@ -2332,7 +2369,7 @@ k_evaluate_static(const __grid_constant__ SysDev S, const Layout Lo, const LatDe
   const int P = S.N * 6 * L.G;
   double b, el;
   df bdf;
-  warp_eval_any<PR, NJ>(S, sC, L, wm, lane, ratio ? ratio + (size_t)c * P : nullptr, b, bdf, el);
+  warp_eval_any<PR, NJ, NC>(S, sC, L, wm, lane, ratio ? ratio + (size_t)c * P : nullptr, b, bdf, el);
   if (T)
     for (int j = lane; j < P; j += 32)
       T[(size_t)c * P + j] = (PR != LRDMC_PRECISION_FP64) ? df_to_double(reinterpret_cast<const df*>(wm.T)[j])
@@ -2378,7 +2415,7 @@ cudaError_t launch_evaluate_static(const SysDev& S, const Layout& Lo, const LatD
   e = cudaMemsetAsync(scratch, 0, sizeof(int) * (64 + (size_t)n), st);
   if (e != cudaSuccess) return e;
   const int blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  LRDMC_DISPATCH(S, {
+  LRDMC_DISPATCH(S, Lo, {
     e = set_smem((const void*)k_evaluate_static<V>, Lo.smem_block_bytes);
     if (e != cudaSuccess) return e;
     if (blocks > 0)

@@ -50,6 +50,16 @@ def test_create_system_rejects_bad_sizes(pkg):
         pkg.LrdmcSystem(s)
 
 
+def test_create_system_rejects_a_layout_beyond_shared_memory(pkg):
+    """A block of four walkers of 64 electrons with 62 AOs needs more than
+    227 KB of shared memory: rejected at creation with a message that says
+    so. 48 electrons with 42 AOs fit (without the evaluation caches)."""
+    with pytest.raises(pkg.LrdmcError) as e:
+        pkg.LrdmcSystem(S.cluster(8, 32, 6))
+    assert e.value.status == pkg.ERR_ARG and "shared memory" in str(e.value)
+    pkg.LrdmcSystem(S.cluster(8, 24, 2))
+
+
 def test_step_before_init_is_a_state_error(pkg):
     g = pkg.LrdmcSystem(S.helium())
     with pytest.raises(pkg.LrdmcError) as e:

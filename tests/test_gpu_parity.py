@@ -297,3 +297,32 @@ def test_fp32_projection_energy_matches_fp64(pkg):
         res[prec] = (stats.energy_estimate(e, w[100:], 0), stats.reblock(e)[0])
     (e64, s64), (e32, s32) = res[pkg.PRECISION_FP64], res[pkg.PRECISION_FP32]
     assert abs(e64 - e32) < 4 * np.hypot(s64, s32) + 5e-4, (e64, s64, e32, s32)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_large_system_without_caches(pkg, oracle_mod, prec):
+    """48 electrons on 8 centres with 42 AOs: the largest kind of system
+    whose four-walker block fits in shared memory only without the
+    evaluation caches. Every ratio, rate and local energy of 5
+    configurations, then two projection intervals of 6 walkers, against the
+    oracle."""
+    system = S.cluster(8, 24, 2)
+    g = pkg.LrdmcSystem(system).set_precision(_prec(pkg, prec))
+    o = oracle_mod.OracleSystem(system)
+    n = 5
+    x = S.initial_positions(system, n, 11)
+    R = S.random_rotations(n, 12)
+    sp, lat = spacing_pair(pkg, oracle_mod, system, 0.3, "this_work")
+    ratio, T, b, el = (t.cpu().numpy() for t in g.evaluate(torch.tensor(x, device="cuda"),
+                                                           torch.tensor(R, device="cuda"), 0.3, sp))
+    for c in range(n):
+        ref = o.lattice_eval(lat, x[c], R[c])
+        scale = ratio_scale(o, system, lat, x[c], R[c], ref["ratio"])
+        err = np.abs(ratio[c] - ref["ratio"]) / (RTOL * scale)
+        worst = int(np.argmax(err))
+        assert err.max() <= 1.0, (c, worst, float(err.max()), float(ratio[c].flat[worst]),
+                                  float(ref["ratio"].flat[worst]))
+        assert abs(b[c] - ref["b"]) <= RTOL * ref["b"]
+        assert abs(el[c] - ref["EL"]) <= RTOL * max(1.0, abs(ref["EL"]))
+    compared, parted = _compare_runs(pkg, oracle_mod, system, "this_work", 0.3, 6, 2, 0.002, 13, 40.0, prec=prec)
+    assert compared == 2 or parted
