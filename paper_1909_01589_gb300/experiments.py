@@ -19,7 +19,7 @@ Usage: python -m paper_1909_01589_gb300.experiments [--systems He,Ne,Ar,Kr]
        [--steps 1000] [--out results/single_vs_double.json]
        python -m paper_1909_01589_gb300.experiments --neural --systems Ne,Ar
        [--steps 600] [--out results/neural_vs_pade.json]
-       python -m paper_1909_01589_gb300.experiments --extrapolate --systems He
+       python -m paper_1909_01589_gb300.experiments --extrapolate [--neural] --systems He
        [--steps 2000] [--out results/extrapolation_he.json]
 """
 from __future__ import annotations
@@ -43,13 +43,17 @@ DEFAULTS = {  # system: (walkers, e_trial, target jumps per interval)
 }
 
 
-def run(system, a, spacing, W, steps, equil, tau, e_trial, seed=1, precision=PRECISION_DF64, device="cuda"):
-    """One projection; returns energy, error, jumps/interval, GPU seconds."""
+def run(system, a, spacing, W, steps, equil, tau, e_trial, seed=1, precision=PRECISION_DF64, device="cuda",
+        neural=None):
+    """One projection; returns energy, error, jumps/interval, GPU seconds.
+    ``neural`` = (spec, params) installs the neural pair term."""
     import torch
 
     import lrdmc_synth as S
 
     g = LrdmcSystem(system).set_precision(precision)
+    if neural is not None:
+        g.set_neural_jastrow(*neural)
     x0 = S.initial_positions(system, W, seed)
     g.init_walkers(torch.tensor(x0, device=device), seed=seed, tau=tau, e_trial=e_trial, recompute_every=5,
                    trace_capacity=steps + equil + 4)
@@ -201,22 +205,55 @@ def neural_vs_pade(names=("Ne", "Ar"), W=16384, steps=600, equil=150, n_train=1 
     return rows
 
 
-def extrapolation(name="He", a_values=(0.4, 0.3, 0.2, 0.15, 0.1), W=8192, steps=2000, equil=200, seed=5):
+def extrapolation(name="He", a_values=(0.4, 0.3, 0.2, 0.15, 0.1), W=8192, steps=2000, equil=200, seed=5,
+                  neural=False, n_train=1 << 18, train_steps=600, a_train=0.2):
     """E(a) on the single grid and on this work's double grid at several
     lattice spacings, and the a -> 0 limits from the weighted least-squares
     fit E(a) = E0 + k1 a^2 + k2 a^4 (the three-parameter fit of the paper's
     benzene footnote). For He the guiding function is nodeless, so both
-    limits must reach the exact ground-state energy."""
+    limits must reach the exact ground-state energy.
+
+    With ``neural`` the neural pair term is trained once on the GPU
+    (configurations of a plain projection at a_train on this work's double
+    grid) and installed in every run: the guiding function changes E(a) at
+    finite a, not the fixed-node limit, so the limits must agree with the
+    plain ones."""
     import lrdmc_synth as S
 
     system = S.make_system(name)
     e_trial = DEFAULTS[name][1]
-    out = {"system": name, "a": list(a_values), "walkers": W, "steps": steps}
+    out = {"system": name, "a": list(a_values), "walkers": W, "steps": steps, "neural": bool(neural)}
+    nj = None
+    if neural:
+        import torch
+
+        from . import neural as N
+
+        sp = Spacing(THIS_WORK)
+        tau = _tau_for(system, a_train, sp, 10.0, seed)
+        spec = S.default_neural_spec(system)
+        plain = LrdmcSystem(system)
+        t0 = time.perf_counter()
+        x = N.sample_configurations(plain, S.initial_positions(system, W, seed + 50), n_train, a_train, sp, tau,
+                                    e_trial, seed=seed + 50)
+        grad, e = plain.base_terms(x)
+        n_tr = len(x) * 7 // 8
+        params, _ = N.train(plain, spec, S.neural_init(spec, seed), x[:n_tr], grad[:n_tr], e[:n_tr],
+                            steps=train_steps, seed=seed + 51)
+        torch.cuda.synchronize()
+        el, j = N.evaluate(plain, spec, params, x[n_tr:], grad[n_tr:], e[n_tr:])
+        out["train"] = {"a": a_train, "configs": n_tr, "steps": train_steps,
+                        "seconds": time.perf_counter() - t0,
+                        "heldout_var_pade": float(torch.var(e[n_tr:])),
+                        "heldout_var_neural": float(N.variance_loss(el, j, clip=0.0))}
+        nj = (spec, params.cpu().numpy())
+        print(f"{name} neural term: held-out var {out['train']['heldout_var_pade']:.4f} -> "
+              f"{out['train']['heldout_var_neural']:.4f} Ha^2", flush=True)
     for label, sp in (("single", Spacing(SINGLE)), ("double_this_work", Spacing(THIS_WORK))):
         E, err = [], []
         for a in a_values:
             tau = _tau_for(system, a, sp, 10.0, seed)
-            r = run(system, a, sp, W, steps, equil, tau, e_trial, seed)
+            r = run(system, a, sp, W, steps, equil, tau, e_trial, seed, neural=nj)
             E.append(r["energy"])
             err.append(r["error"])
         E, err = np.array(E), np.array(err)
@@ -285,10 +322,11 @@ def main():
     ap.add_argument("--out", default="results/single_vs_double.json")
     ap.add_argument("--summarize", nargs="*", help="only write the markdown table of these result files")
     ap.add_argument("--neural", action="store_true", help="the neural Jastrow against Pade instead")
-    ap.add_argument("--extrapolate", action="store_true", help="E(a) and the a -> 0 fit instead (first system)")
+    ap.add_argument("--extrapolate", action="store_true",
+                    help="E(a) and the a -> 0 fit instead (first system); with --neural, with the trained term")
     args = ap.parse_args()
     if args.extrapolate:
-        row = extrapolation(args.systems.split(",")[0], steps=args.steps, equil=args.equil)
+        row = extrapolation(args.systems.split(",")[0], steps=args.steps, equil=args.equil, neural=args.neural)
         os.makedirs(os.path.dirname(args.out) or ".", exist_ok=True)
         json.dump(row, open(args.out, "w"), indent=1)
         return
