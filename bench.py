@@ -92,14 +92,21 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, path=None):
+        """``path``: where the samples go ({rank} is replaced by the GPU
+        index); by default a file in the temporary directory."""
+        import tempfile
+
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_rank{gpu_index}.csv")
+        if path:
+            self.path = path.replace("{rank}", str(gpu_index))
+        else:
+            self.path = os.path.join(tempfile.gettempdir(), f"lrdmc_clocks_rank{gpu_index}_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            os.makedirs(os.path.dirname(os.path.abspath(self.path)), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -214,7 +221,7 @@ def measure_leg(args, pkg, torch, system, precision, dev, rank, seed, x0, with_c
 
         dist.barrier()
     torch.cuda.synchronize()
-    clk = ClockSampler(local) if with_clocks else None
+    clk = ClockSampler(local, args.clocks_csv) if with_clocks else None
     if clk:
         clk.__enter__()
     t_wall0 = time.perf_counter()
@@ -585,6 +592,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="CPU-baseline budget (<= 0: no CPU baseline)")
+    ap.add_argument("--clocks-csv", default=None,
+                    help="keep the nvidia-smi samples of the timed region in this file ({rank}: GPU index)")
     ap.add_argument("--precision", default="df64", choices=["df64", "fp64", "fp32"],
                     help="evaluation arithmetic: double-float on the FP32 pipe or IEEE double")
     ap.add_argument("--no-fp64-leg", dest="fp64_leg", action="store_false",

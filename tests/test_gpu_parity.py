@@ -326,3 +326,27 @@ def test_large_system_without_caches(pkg, oracle_mod, prec):
         assert abs(el[c] - ref["EL"]) <= RTOL * max(1.0, abs(ref["EL"]))
     compared, parted = _compare_runs(pkg, oracle_mod, system, "this_work", 0.3, 6, 2, 0.002, 13, 40.0, prec=prec)
     assert compared == 2 or parted
+
+
+def test_large_system_fp32_evaluation(pkg, oracle_mod):
+    """The mixed-precision mode on the 48-electron system: its single-precision
+    e-e Pade fraction runs over 47 partners a few bohr away, whose product of
+    (1 + b r) leaves the float range unless it is rescaled. Every ratio
+    within the mode's 2e-4 of the oracle (relative to the magnitude of its
+    determinant terms), every local energy within 2e-4 relative, all finite."""
+    system = S.cluster(8, 24, 2)
+    g = pkg.LrdmcSystem(system).set_precision(pkg.PRECISION_FP32)
+    o = oracle_mod.OracleSystem(system)
+    n = 5
+    x = S.initial_positions(system, n, 11)
+    R = S.random_rotations(n, 12)
+    sp, lat = spacing_pair(pkg, oracle_mod, system, 0.3, "this_work")
+    ratio, T, b, el = (t.cpu().numpy() for t in g.evaluate(torch.tensor(x, device="cuda"),
+                                                           torch.tensor(R, device="cuda"), 0.3, sp))
+    assert np.all(np.isfinite(ratio)) and np.all(np.isfinite(el)) and np.all(b > 0)
+    for c in range(n):
+        ref = o.lattice_eval(lat, x[c], R[c])
+        scale = ratio_scale(o, system, lat, x[c], R[c], ref["ratio"])
+        err = float(np.max(np.abs(ratio[c] - ref["ratio"]) / scale))
+        assert err < FP32_RTOL, (c, err)
+        assert abs(el[c] - ref["EL"]) < FP32_RTOL * abs(ref["EL"]), (c, el[c], ref["EL"])
