@@ -31,3 +31,31 @@ def ratio_scale(o, system, lat, x, R, ratio_ref):
                     if rdet != 0.0:
                         out[c] = max(out[c], np.abs(terms).sum() * abs(ratio_ref[c] / rdet))
     return out
+
+
+def el_scale(system, x, el_ref):
+    """Floating-point scale of local energies: |T| + |V_en| + V_ee + |V_nn|
+    for configurations x [W][N][3] with reference local energies el_ref [W],
+    T = E_L - V the kinetic part (at least |E_L| and 1). E_L is the sum of
+    these terms; near a nucleus of large Z they reach thousands of hartree
+    and cancel, and rounding in any evaluation order is bounded relative to
+    their magnitudes, not to the (possibly small) sum."""
+    x = np.asarray(x, float).reshape(len(el_ref), system.N, 3)
+    nuc = np.asarray(system.nuc_xyz, float).reshape(-1, 3)
+    Z = np.asarray(system.Z, float)
+    v_en = np.zeros(len(el_ref))
+    for I in range(len(Z)):
+        v_en -= Z[I] * np.sum(1.0 / np.linalg.norm(x - nuc[I], axis=2), axis=1)
+    v_ee = np.zeros(len(el_ref))
+    if system.ee_on:
+        for i in range(system.N):
+            for j in range(i + 1, system.N):
+                v_ee += 1.0 / np.linalg.norm(x[:, i] - x[:, j], axis=1)
+    v_nn = 0.0
+    for I in range(len(Z)):
+        for J in range(I + 1, len(Z)):
+            v_nn += Z[I] * Z[J] / np.linalg.norm(nuc[I] - nuc[J])
+    el_ref = np.asarray(el_ref, float)
+    kinetic = el_ref - (v_en + v_ee + v_nn)
+    return np.maximum.reduce([np.ones_like(el_ref), np.abs(el_ref),
+                              np.abs(kinetic) + np.abs(v_en) + v_ee + abs(v_nn)])

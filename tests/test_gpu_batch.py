@@ -120,3 +120,39 @@ def test_batch_errors(pkg):
     assert e.value.status == pkg.ERR_ARG
     with pytest.raises(pkg.LrdmcError):
         pkg.LrdmcBatch([gs[0], gs[0]], a, sp)  # a system twice
+
+
+def test_full_size_batch_equals_single_steps(pkg):
+    """The batched workload at full size: 8192 walkers each of He, Ne, Ar, Kr
+    and H2O at a = 1/(3.5 Z_max) on this work's double grid, tau for about
+    10 jumps per walker, two steps in one CUDA graph each. Walkers, traces
+    and move counts equal those of the same systems stepped one by one."""
+    from paper_1909_01589_gb300 import batch as B
+
+    names = ("He", "Ne", "Ar", "Kr", "H2O")
+    e_trial = (-2.90, -128.9, -527.5, -2753.0, -76.0)
+    sp = pkg.Spacing(pkg.THIS_WORK)
+    systems = [S.make_system(nm) for nm in names]
+    a = [1.0 / (3.5 * float(np.max(s.Z))) for s in systems]
+    taus = [B.tau_for(pkg, s, ai, sp, 10.0, S.initial_positions(s, 256, 500 + q), S.random_rotations(256, 600 + q))
+            for q, (s, ai) in enumerate(zip(systems, a))]
+
+    def make():
+        gs = []
+        for q, (s, tau) in enumerate(zip(systems, taus)):
+            g = pkg.LrdmcSystem(s)
+            g.init_walkers(torch.tensor(S.initial_positions(s, 8192, 700 + q), device="cuda"), seed=800 + q,
+                           tau=tau, e_trial=e_trial[q], recompute_every=5, trace_capacity=8)
+            gs.append(g)
+        return gs
+
+    solo = make()
+    for g, ai in zip(solo, a):
+        g.step(2, ai, sp)
+        g.sync()
+    batched = make()
+    batch = pkg.LrdmcBatch(batched, a, [sp] * len(batched))
+    batch.step(2)
+    batch.sync()
+    for g1, g2 in zip(solo, batched):
+        assert _equal(_state(g1), _state(g2))

@@ -80,6 +80,32 @@ def test_evaluate_with_neural_term(pkg, oracle_mod, nn, name, a, prec):
     assert abs(el0[0] - plain.local_energy(x[0])) <= RTOL * abs(el0[0])
 
 
+@pytest.mark.parametrize("name,a", [("Ne", 0.2), ("Ar", 0.05)])
+def test_evaluate_with_neural_term_full_size_sampled(pkg, oracle_mod, nn, name, a):
+    """The neural workload at full size: 16384 configurations with the
+    tabulated term (weights with a non-zero output layer), this work's
+    double grid, the default double-float mode; 16 sampled configurations
+    against the oracle with the same table installed."""
+    system = S.make_system(name)
+    spec = S.default_neural_spec(system)
+    params = S.neural_init(spec, 13, out_scale=0.6)
+    g = pkg.LrdmcSystem(system).set_neural_jastrow(spec, params)
+    o = oracle_mod.OracleSystem(system).set_neural(nn.table(params, spec))
+    n = 16384
+    x = S.initial_positions(system, n, 311)
+    R = S.random_rotations(n, 312)
+    sp, lat = _lattice(pkg, oracle_mod, system, a)
+    ratio, T, b, el = g.evaluate(torch.tensor(x, device="cuda"), torch.tensor(R, device="cuda"), a, sp)
+    ratio, b, el = ratio.cpu().numpy(), b.cpu().numpy(), el.cpu().numpy()
+    assert np.all(np.isfinite(el)) and np.all(b > 0)
+    for c in np.random.default_rng(5).choice(n, 16, replace=False):
+        ref = o.lattice_eval(lat, x[c], R[c])
+        scale = ratio_scale(o, system, lat, x[c], R[c], ref["ratio"])
+        assert np.all(np.abs(ratio[c] - ref["ratio"]) <= RTOL * scale), c
+        assert abs(b[c] - ref["b"]) <= RTOL * ref["b"], c
+        assert abs(el[c] - ref["EL"]) <= RTOL * max(1.0, abs(ref["EL"])), c
+
+
 @pytest.mark.parametrize("prec", ["fp64", "df64"])
 def test_projection_with_neural_term(pkg, oracle_mod, nn, prec):
     """Ne, 64 walkers, three intervals with the term installed: walker by

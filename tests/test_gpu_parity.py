@@ -3,7 +3,9 @@
 Bar (FP64): lattice-move ratios, rates, total rates and local energies
 within 1e-10 relative (ratios: relative to the magnitude of the terms of
 their determinant dot product, at least max(1, |ratio|); see
-_parity_util.ratio_scale); positions,
+_parity_util.ratio_scale; the local energies of projected walkers, which
+can sit close to a heavy nucleus: relative to the magnitude of their
+kinetic and Coulomb terms, see _parity_util.el_scale); positions,
 log-weights and trace energies within 1e-10; jump counts, comb parents and
 move choices identical, except after a decision the oracle reports within
 1e-9 of a bin edge (then the trajectories may part and the comparison
@@ -15,7 +17,7 @@ import numpy as np
 import pytest
 
 import lrdmc_synth as S
-from _parity_util import ratio_scale
+from _parity_util import el_scale, ratio_scale
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -129,7 +131,7 @@ def _compare_runs(pkg, oracle_mod, system, kind, a, W, n_steps, tau, seed, e_tri
         gw, ow = g.walkers(), pop.walkers(lat.G)
         ok = (np.array_equal(gw["jumps_pre"], ow["jumps_pre"]) and np.array_equal(gw["parent"], ow["parent"])
               and np.all(np.abs(gw["x"] - ow["x"]) <= RTOL * np.maximum(1.0, np.abs(ow["x"])))
-              and np.all(np.abs(gw["EL"] - ow["EL"]) <= RTOL * np.maximum(1.0, np.abs(ow["EL"])))
+              and np.all(np.abs(gw["EL"] - ow["EL"]) <= RTOL * el_scale(system, ow["x"], ow["EL"]))
               and np.all(np.abs(gw["logw_pre"] - ow["logw_pre"]) <= RTOL * np.maximum(1.0, np.abs(ow["logw_pre"]))))
         if not ok:
             mw, mc = pop.margins()
@@ -350,3 +352,39 @@ def test_large_system_fp32_evaluation(pkg, oracle_mod):
         err = float(np.max(np.abs(ratio[c] - ref["ratio"]) / scale))
         assert err < FP32_RTOL, (c, err)
         assert abs(el[c] - ref["EL"]) < FP32_RTOL * abs(ref["EL"]), (c, el[c], ref["EL"])
+
+
+HEAVY_FULL = [("Ar", 1 / 63, 2e-4, -527.5), ("Kr", 1 / 126, 3e-5, -2752.0)]
+
+
+@pytest.mark.parametrize("name,a,tau,et", HEAVY_FULL)
+def test_heavy_atoms_evaluate_full_size_sampled(pkg, oracle_mod, name, a, tau, et):
+    """The Ar and Kr workloads at full size: 16384 configurations of the
+    contracted-Gaussian atoms at a = 1/(3.5 Z) on this work's double grid, in
+    the default double-float mode. 16 sampled configurations are checked
+    against the oracle one by one; every total rate is positive and finite."""
+    system = S.make_system(name)
+    g = pkg.LrdmcSystem(system)
+    o = oracle_mod.OracleSystem(system)
+    n = 16384
+    x = S.initial_positions(system, n, 401)
+    R = S.random_rotations(n, 402)
+    sp, lat = spacing_pair(pkg, oracle_mod, system, a, "this_work")
+    ratio, T, b, el = g.evaluate(torch.tensor(x, device="cuda"), torch.tensor(R, device="cuda"), a, sp)
+    ratio, b, el = ratio.cpu().numpy(), b.cpu().numpy(), el.cpu().numpy()
+    assert np.all(np.isfinite(el)) and np.all(b > 0) and np.all(np.isfinite(b))
+    for c in np.random.default_rng(4).choice(n, 16, replace=False):
+        ref = o.lattice_eval(lat, x[c], R[c])
+        scale = ratio_scale(o, system, lat, x[c], R[c], ref["ratio"])
+        assert np.all(np.abs(ratio[c] - ref["ratio"]) <= RTOL * scale), c
+        assert abs(b[c] - ref["b"]) <= RTOL * ref["b"], c
+        assert abs(el[c] - ref["EL"]) <= RTOL * abs(ref["EL"]), c
+
+
+@pytest.mark.parametrize("name,a,tau,et", HEAVY_FULL)
+def test_heavy_atoms_projection_full_size(pkg, oracle_mod, name, a, tau, et):
+    """One interval of the Ar and Kr workloads at full size (16384 walkers,
+    a = 1/(3.5 Z), this work's double grid, tau for about 9 jumps per
+    walker), walker by walker against the oracle's population."""
+    compared, parted = _compare_runs(pkg, oracle_mod, S.make_system(name), "this_work", a, 16384, 1, tau, 17, et)
+    assert compared == 1 or parted
