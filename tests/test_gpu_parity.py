@@ -388,3 +388,15 @@ def test_heavy_atoms_projection_full_size(pkg, oracle_mod, name, a, tau, et):
     walker), walker by walker against the oracle's population."""
     compared, parted = _compare_runs(pkg, oracle_mod, S.make_system(name), "this_work", a, 16384, 1, tau, 17, et)
     assert compared == 1 or parted
+
+
+@pytest.mark.parametrize("kind", ["single", "this_work"])
+def test_helium_workload_full_length(pkg, oracle_mod, kind):
+    """The He workload at its full length: 256 walkers, a = 0.2, 2000
+    intervals on the single grid and on this work's double grid, walker by
+    walker against the oracle after every interval, then the whole energy
+    trace. Over about 5 million decisions a parting is accepted only after a
+    decision the oracle reports within 1e-9 of a bin edge; at least 100
+    intervals must agree before it."""
+    compared, parted = _compare_runs(pkg, oracle_mod, S.helium(), kind, 0.2, 256, 2000, 0.02, 23, -2.9)
+    assert compared == 2000 or (parted and compared >= 100), compared
