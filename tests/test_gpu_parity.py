@@ -400,3 +400,15 @@ def test_helium_workload_full_length(pkg, oracle_mod, kind):
     intervals must agree before it."""
     compared, parted = _compare_runs(pkg, oracle_mod, S.helium(), kind, 0.2, 256, 2000, 0.02, 23, -2.9)
     assert compared == 2000 or (parted and compared >= 100), compared
+
+
+@pytest.mark.parametrize("kind", ["single", "this_work"])
+@pytest.mark.parametrize("a", [0.4, 0.2, 0.1])
+def test_neon_workload_lattices(pkg, oracle_mod, a, kind):
+    """The Ne workload's lattices at full size: 4096 walkers at a = 0.4, 0.2
+    and 0.1 on the single grid and on this work's double grid, tau scaled as
+    a^2 (about 10 jumps per walker on the double grid), two intervals walker
+    by walker against the oracle."""
+    tau = 0.025 * (a / 0.2) ** 2
+    compared, parted = _compare_runs(pkg, oracle_mod, S.neon(), kind, a, 4096, 2, tau, 29, -128.9)
+    assert compared == 2 or parted
