@@ -15,7 +15,11 @@ with FP64 state, the FP64-parity mode; --precision chooses another). Extra
 legs on the same line: the plain FP64 mode, the mixed FP32 mode, the
 trained neural pair Jastrow, a heterogeneous batch of five systems, the
 end-to-end figure through the public API from host memory, and the CPU
-oracle as a baseline.
+oracle as a baseline. Throughput comes from the K timed intervals; each
+leg's energy, its reblocked error and the efficiency 1/(sigma^2 t) come
+from a continuation of the same population for --eff-steps intervals
+(default 2000), timed as one block, since 200 intervals leave sigma^2
+uncertain by tens of percent.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun (N > 1) every rank runs an independent population (replicas;
@@ -203,7 +207,7 @@ def measure_leg(args, pkg, torch, system, precision, dev, rank, seed, x0, with_c
     g = pkg.LrdmcSystem(system).set_precision(precision)
     if neural is not None:
         g.set_neural_jastrow(*neural)
-    cap = args.warmup + args.steps + 8
+    cap = args.warmup + args.steps + args.eff_steps + 8
     g.init_walkers(torch.tensor(x0, device=dev), seed=seed, tau=WORKLOAD["tau"], e_trial=WORKLOAD["e_trial"],
                    recompute_every=WORKLOAD["recompute_every"], trace_capacity=cap)
     stream = g.stream
@@ -238,10 +242,23 @@ def measure_leg(args, pkg, torch, system, precision, dev, rank, seed, x0, with_c
     step_ms = [s0.elapsed_time(s1) for s0, s1 in zip(starts, stops)]
     moves = g.moves() - m0
     t_int_ms, t_rec_ms, n_int, n_rec = g.kernel_times()
+    g.set_profiling(False)
+    out = dict(total_ms=float(sum(step_ms)), moves=moves, t_int_ms=t_int_ms, t_rec_ms=t_rec_ms, n_int=n_int,
+               n_rec=n_rec, wall=t_wall, clocks=clk.summary() if clk else None, g=g)
     e_tr, w_tr, j_tr = g.energy_trace()
-    return dict(total_ms=float(sum(step_ms)), moves=moves, t_int_ms=t_int_ms, t_rec_ms=t_rec_ms, n_int=n_int,
-                n_rec=n_rec, e=e_tr[-args.steps:], w=w_tr[-args.steps:], j=j_tr[-args.steps:], wall=t_wall,
-                clocks=clk.summary() if clk else None, g=g)
+    out.update(e=e_tr[-args.steps:], w=w_tr[-args.steps:], j=j_tr[-args.steps:], eff_ms=out["total_ms"])
+    if args.eff_steps > 0:
+        # the statistical figures (energy, sigma, efficiency) from a longer
+        # continuation of the same population, timed as one block of steps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.step(args.eff_steps, a, spacing)
+        e1.record(stream)
+        g.sync()
+        torch.cuda.synchronize()
+        e_tr, w_tr, _ = g.energy_trace()
+        out.update(e=e_tr[-args.eff_steps:], w=w_tr[-args.eff_steps:], eff_ms=e0.elapsed_time(e1))
+    return out
 
 
 def run_ours(args):
@@ -333,7 +350,7 @@ def run_ours(args):
                 "flop_per_move": flop_per_move}
     roof["kernel_ms_per_launch"] = kernel_ms
     roof["traffic"] = _read_traffic(main_prec == pkg.PRECISION_DF64)
-    t_sec = leg["total_ms"] * 1e-3
+    t_sec = leg["eff_ms"] * 1e-3
     err, _ = stats.reblock(leg["e"])
     eff = {"value": stats.efficiency(leg["e"], t_sec), "unit": "1/(Ha^2 s)", "sigma_mean_Ha": err,
            "seconds": t_sec, "energy_Ha": stats.energy_estimate(leg["e"], leg["w"], 0),
@@ -368,7 +385,7 @@ def run_ours(args):
     }
     if fp is not None:
         fp_value = fp["moves"] / (fp["total_ms"] * 1e-3)
-        fp_eff = stats.efficiency(fp["e"], fp["total_ms"] * 1e-3)
+        fp_eff = stats.efficiency(fp["e"], fp["eff_ms"] * 1e-3)
         out["vs_plain_fp64"] = {
             "fp64_value": fp_value, "speedup": value / fp_value if world == 1 else None,
             "fp64_efficiency": fp_eff, "efficiency_ratio": eff["value"] / fp_eff,
@@ -384,9 +401,9 @@ def run_ours(args):
         ref_energy = stats.energy_estimate(ref_leg["e"], ref_leg["w"], 0)
         out["mixed_precision"] = {
             "mode": "fp32 evaluation, fp64 inverse/weights/reconfiguration", "value": mx_value,
-            "efficiency": stats.efficiency(mx["e"], mx["total_ms"] * 1e-3),
-            "efficiency_ratio_vs_fp64": stats.efficiency(mx["e"], mx["total_ms"] * 1e-3) /
-            stats.efficiency(ref_leg["e"], ref_leg["total_ms"] * 1e-3),
+            "efficiency": stats.efficiency(mx["e"], mx["eff_ms"] * 1e-3),
+            "efficiency_ratio_vs_fp64": stats.efficiency(mx["e"], mx["eff_ms"] * 1e-3) /
+            stats.efficiency(ref_leg["e"], ref_leg["eff_ms"] * 1e-3),
             "energy_Ha": mx_energy, "sigma_mean_Ha": mx_err,
             "energy_minus_fp64_Ha": mx_energy - ref_energy,
             "combined_sigma_Ha": float(np.hypot(mx_err, ref_err)),
@@ -395,7 +412,7 @@ def run_ours(args):
         leg_nj, info = nj
         nj_value = leg_nj["moves"] / (leg_nj["total_ms"] * 1e-3)
         nj_err, _ = stats.reblock(leg_nj["e"])
-        nj_eff = stats.efficiency(leg_nj["e"], leg_nj["total_ms"] * 1e-3)
+        nj_eff = stats.efficiency(leg_nj["e"], leg_nj["eff_ms"] * 1e-3)
         block = {"mode": "Pade + neural pair Jastrow (2x64 SiLU, bf16 weights, quintic table), " + args.precision,
                  "value": nj_value, "efficiency": nj_eff, "efficiency_ratio_vs_pade": nj_eff / eff["value"],
                  "energy_Ha": stats.energy_estimate(leg_nj["e"], leg_nj["w"], 0), "sigma_mean_Ha": nj_err,
@@ -403,7 +420,7 @@ def run_ours(args):
                  "var_EL_walkers_pade_Ha2": float(np.var(leg["g"].walkers()["EL"])),
                  "kernel_ms_per_launch": leg_nj["t_int_ms"] / max(leg_nj["n_int"], 1), **info}
         if fp is not None:
-            block["efficiency_ratio_vs_fp64"] = nj_eff / stats.efficiency(fp["e"], fp["total_ms"] * 1e-3)
+            block["efficiency_ratio_vs_fp64"] = nj_eff / stats.efficiency(fp["e"], fp["eff_ms"] * 1e-3)
         out["neural_jastrow"] = block
     if bt is not None:
         out["batched"] = bt
@@ -592,6 +609,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="CPU-baseline budget (<= 0: no CPU baseline)")
+    ap.add_argument("--eff-steps", type=int, default=2000,
+                    help="intervals of the longer untimed-for-throughput run each leg continues with for its "
+                         "energy, sigma and efficiency 1/(sigma^2 t) (0: use the timed intervals)")
     ap.add_argument("--clocks-csv", default=None,
                     help="keep the nvidia-smi samples of the timed region in this file ({rank}: GPU index)")
     ap.add_argument("--precision", default="df64", choices=["df64", "fp64", "fp32"],
