@@ -393,7 +393,7 @@ lrdmc_status lrdmc_spacing_params(lrdmc_system_t s, double a, const lrdmc_spacin
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct WsPlan {
-  size_t rec, parent, order, logw, el, jumps, cum, trace, moves, err, counter, kdev, total;
+  size_t rec, parent, order, logw, wgt, el, jumps, cum, trace, moves, err, counter, kdev, total;
 };
 
 static WsPlan plan_ws(const Layout& Lo, int W, int cap)
@@ -404,6 +404,7 @@ static WsPlan plan_ws(const Layout& Lo, int W, int cap)
   p.parent = o; o += align256(sizeof(int) * (size_t)W);
   p.order = o; o += align256(sizeof(int) * (size_t)W);
   p.logw = o; o += align256(sizeof(double) * (size_t)W);
+  p.wgt = o; o += align256(sizeof(double) * (size_t)W);
   p.el = o; o += align256(sizeof(double) * (size_t)W);
   p.jumps = o; o += align256(sizeof(int) * (size_t)W);
   p.cum = o; o += align256(sizeof(double) * (size_t)W);
@@ -469,6 +470,7 @@ lrdmc_status lrdmc_init_walkers(lrdmc_system_t s, int W, const double* x0, uint6
   P.parent = (int*)(s->ws + p.parent);
   P.order = (int*)(s->ws + p.order);
   P.logw = (double*)(s->ws + p.logw);
+  P.wgt = (double*)(s->ws + p.wgt);
   P.el_end = (double*)(s->ws + p.el);
   P.jumps = (int*)(s->ws + p.jumps);
   P.cum = (double*)(s->ws + p.cum);
@@ -486,6 +488,7 @@ lrdmc_status lrdmc_init_walkers(lrdmc_system_t s, int W, const double* x0, uint6
   cudaError_t e = cudaMemsetAsync(s->ws + p.moves, 0, 4 * 256, s->stream);  // moves, err, counter, kdev
   if (e != cudaSuccess) return cuda_fail(s, e, "workspace clear");
   e = cudaMemsetAsync(P.logw, 0, sizeof(double) * W, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P.wgt, 0, sizeof(double) * W, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(P.jumps, 0, sizeof(int) * W, s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "workspace clear");
   // stage x0 (host or device memory) in the second record buffer

@@ -124,15 +124,20 @@ Layout make_layout(const SysDev& S, bool caches);
 // Largest dynamic shared memory of one block on sm_100-class GPUs (227 KB).
 constexpr int kMaxSmemBlock = 232448;
 
+// Populations up to this many walkers keep the comb's running sums in the
+// reconfiguration kernel's shared memory (8 bytes each).
+constexpr int kReconfigSmemW = 16384;
+
 struct PopDev {
   double* rec_src;
   double* rec_dst;
   int* parent;
   int* order;  // processing order of the slots (longest expected interval first)
   double* logw;
+  double* wgt;  // exp(logw) of the last interval, written with logw
   double* el_end;
   int* jumps;
-  double* cum;
+  double* cum;  // running weight sums of the comb (populations above kReconfigSmemW)
   double* trace;  // [3][cap]
   unsigned long long* moves;
   int* err;

@@ -1858,6 +1858,7 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
     store_record(Lo, P.rec_dst + (size_t)s * Lo.rec, wm, lane, b, el);
     if (lane == 0) {
       P.logw[s] = logw;
+      P.wgt[s] = exp(logw);
       P.el_end[s] = el;
       P.jumps[s] = jumps;
     }
@@ -1866,23 +1867,33 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
 }
 
 // Reconfiguration at the end of interval k (one block of 1024 threads):
-// w_s = exp(log w_s), trace (weighted mean E_L, mean weight, mean jumps),
-// comb parents: slot t takes the smallest s with (t + xi) C_W / W < C_s.
+// trace (weighted mean E_L, mean weight, mean jumps) and comb parents: slot
+// t takes the smallest s with (t + xi) C_W / W < C_s. The weights
+// w_s = exp(log w_s) come from the interval kernel (P.wgt), so their FP64
+// exponentials run on every SM, not on this block's one. Up to
+// kReconfigSmemW walkers, the running sums C_s live in dynamic shared memory
+// (the comb's binary searches then read shared memory, not L2), and the same
+// region then holds each slot's next-interval rate for the processing order,
+// read once from the records. Larger populations use P.cum and re-read the
+// records. Either way the sums, and so the parents, are the same numbers.
 __global__ void __launch_bounds__(1024) k_reconfig(const PopDev P, const double* rec_next, int rec_stride,
                                                   int off_b)
 {
   const uint64_t k = *P.kdev;
+  extern __shared__ double s_dyn[];
   __shared__ double s_run[1024];
   __shared__ double s_e[32], s_j[32], s_w[32];
   __shared__ double s_total;
   const int W = P.W, t = threadIdx.x, nt = blockDim.x;
+  const bool in_smem = W <= kReconfigSmemW;
+  double* cum = in_smem ? s_dyn : P.cum;
   const int chunk = (W + nt - 1) / nt;
   const int lo = min(W, t * chunk), hi = min(W, lo + chunk);
   double run = 0.0, swe = 0.0, sj = 0.0;
   for (int s = lo; s < hi; ++s) {
-    double w = exp(P.logw[s]);
+    double w = P.wgt[s];
     run += w;
-    P.cum[s] = run;
+    cum[s] = run;
     swe += w * P.el_end[s];
     sj += (double)P.jumps[s];
   }
@@ -1896,7 +1907,7 @@ __global__ void __launch_bounds__(1024) k_reconfig(const PopDev P, const double*
     __syncthreads();
   }
   double offset = (t > 0) ? s_run[t - 1] : 0.0;
-  for (int s = lo; s < hi; ++s) P.cum[s] += offset;
+  for (int s = lo; s < hi; ++s) cum[s] += offset;
   if (t == nt - 1) s_total = s_run[nt - 1];
   // reductions of swe and sj
   double e = warp_sum(swe), j = warp_sum(sj);
@@ -1913,12 +1924,30 @@ __global__ void __launch_bounds__(1024) k_reconfig(const PopDev P, const double*
   double u[4];
   draw_uniforms(P.seed, kSlotGlobal, k, 0, kTagComb, u);
   const double xi = u[0];
+  // t -> (t + xi) total / W; for W a power of two the product with 1/W is
+  // the same number as the quotient (an exact scaling), and the FP64 pipe of
+  // this one SM is spared W divisions
+  const bool w_pow2 = (W & (W - 1)) == 0;
+  const double inv_w = 1.0 / (double)W;
+  // The targets grow with t, so the parents do too: a thread searches for
+  // its first slot's parent, then steps forward from the previous one (up to
+  // 8 steps, else a search over the rest). Each parent is the smallest s
+  // with target < cum[s] (else W - 1), found with the same comparisons.
+  int a = 0;
   for (int tt = lo; tt < hi; ++tt) {
-    double target = ((double)tt + xi) * total / (double)W;
-    int a = 0, bnd = W - 1;  // smallest s with target < cum[s], else W-1
-    while (a < bnd) {
-      int mid = (a + bnd) >> 1;
-      if (target < P.cum[mid]) bnd = mid; else a = mid + 1;
+    const double num = ((double)tt + xi) * total;
+    const double target = w_pow2 ? num * inv_w : num / (double)W;
+    int steps = 0;
+    while (tt > lo && steps < 8 && a < W - 1 && !(target < cum[a])) {
+      ++a;
+      ++steps;
+    }
+    if (tt == lo || (steps == 8 && a < W - 1 && !(target < cum[a]))) {
+      int bnd = W - 1;
+      while (a < bnd) {
+        int mid = (a + bnd) >> 1;
+        if (target < cum[mid]) bnd = mid; else a = mid + 1;
+      }
     }
     P.parent[tt] = a;
   }
@@ -1936,9 +1965,12 @@ __global__ void __launch_bounds__(1024) k_reconfig(const PopDev P, const double*
   // does not affect any result).
   __shared__ int s_cnt[64];
   __shared__ float s_lo[32], s_hi[32];
+  float* s_b = reinterpret_cast<float*>(s_dyn);
+  __syncthreads();  // every search has finished with the shared sums
   float bmin = INFINITY, bmax = -INFINITY;
   for (int tt = lo; tt < hi; ++tt) {
     float bt = (float)rec_next[(size_t)P.parent[tt] * rec_stride + off_b];
+    if (in_smem) s_b[tt] = bt;
     bmin = fminf(bmin, bt);
     bmax = fmaxf(bmax, bt);
   }
@@ -1963,7 +1995,7 @@ __global__ void __launch_bounds__(1024) k_reconfig(const PopDev P, const double*
   const float gmin = s_lo[0], gmax = s_hi[0];
   const float scale = (gmax > gmin) ? 64.0f / (gmax - gmin) : 0.0f;
   for (int tt = lo; tt < hi; ++tt) {
-    float bt = (float)rec_next[(size_t)P.parent[tt] * rec_stride + off_b];
+    float bt = in_smem ? s_b[tt] : (float)rec_next[(size_t)P.parent[tt] * rec_stride + off_b];
     int q = (int)((bt - gmin) * scale);
     q = 63 - min(63, max(0, q));
     atomicAdd(&s_cnt[q], 1);
@@ -1979,7 +2011,7 @@ __global__ void __launch_bounds__(1024) k_reconfig(const PopDev P, const double*
   }
   __syncthreads();
   for (int tt = lo; tt < hi; ++tt) {
-    float bt = (float)rec_next[(size_t)P.parent[tt] * rec_stride + off_b];
+    float bt = in_smem ? s_b[tt] : (float)rec_next[(size_t)P.parent[tt] * rec_stride + off_b];
     int q = (int)((bt - gmin) * scale);
     q = 63 - min(63, max(0, q));
     P.order[atomicAdd(&s_cnt[q], 1)] = tt;
@@ -2254,7 +2286,12 @@ cudaError_t launch_interval(const SysDev& S, const Layout& Lo, const LatDev& L, 
 
 cudaError_t launch_reconfig(const PopDev& P, const Layout& Lo, cudaStream_t st)
 {
-  k_reconfig<<<1, 1024, 0, st>>>(P, P.rec_dst, Lo.rec, Lo.off_b);
+  const int smem = P.W <= kReconfigSmemW ? (int)sizeof(double) * P.W : 0;
+  // the attribute always takes the largest size, so systems of different
+  // populations (and batches captured in one graph) never lower it
+  cudaError_t e = smem > 0 ? set_smem((const void*)k_reconfig, (int)sizeof(double) * kReconfigSmemW) : cudaSuccess;
+  if (e != cudaSuccess) return e;
+  k_reconfig<<<1, 1024, smem, st>>>(P, P.rec_dst, Lo.rec, Lo.off_b);
   return cudaGetLastError();
 }
 
