@@ -335,7 +335,11 @@ LRDMC_API lrdmc_status lrdmc_nj_forward(lrdmc_system_t sys, const lrdmc_nj_spec*
  * d/dparams of sum_x (d_el[x] E_L(x) + d_j[x] J(x)), from the q of the
  * matching forward call; derivatives are taken with respect to the values
  * the network computes with (the bfloat16 roundings when spec->bf16).
- * All pointers device; asynchronous on stream. */
+ * Every sum runs in a fixed order, so equal inputs give the same bits.
+ * The per-block partial sums go to device scratch the system owns (grid
+ * size x n_params floats, allocated at the first call, grown if needed,
+ * freed by lrdmc_destroy): backward calls on one system must not run
+ * concurrently. All pointers device; asynchronous on stream. */
 LRDMC_API lrdmc_status lrdmc_nj_backward(lrdmc_system_t sys, const lrdmc_nj_spec* spec, const float* params,
                                          int n, const double* x, const float* q, const float* d_el,
                                          const float* d_j, float* grad_out, void* stream);

@@ -52,6 +52,9 @@ struct lrdmc_system_s {
   double* nj_tab = nullptr;
   df* nj_tab_df = nullptr;
   int* base_err = nullptr;
+  // per-block partial gradients of lrdmc_nj_backward (grown on demand)
+  float* nj_partials = nullptr;
+  size_t nj_partials_n = 0;
 };
 
 static const char* g_static_error = "";
@@ -984,7 +987,20 @@ lrdmc_status lrdmc_nj_backward(lrdmc_system_t s, const lrdmc_nj_spec* sp, const 
   if (!nj_spec_ok(s, sp, why)) return fail(s, LRDMC_ERR_ARG, "nj_backward: " + why);
   if (n < 0 || !grad_out || (n > 0 && (!params || !x || !q || !d_el || !d_j)))
     return fail(s, LRDMC_ERR_ARG, "nj_backward: bad arguments");
-  cudaError_t e = launch_nj_backward(nj_geom(s, sp), nj_net(sp), params, n, x, q, d_el, d_j, grad_out,
+  const NjGeom G = nj_geom(s, sp);
+  const NjNetDev N = nj_net(sp);
+  const int max_blocks = nj_backward_max_blocks(G, N);
+  if (max_blocks <= 0) return cuda_fail(s, cudaGetLastError(), "nj_backward: grid size");
+  const size_t need = (size_t)max_blocks * (size_t)nj_n_params(N.F, N.C, LRDMC_NJ_HIDDEN);
+  if (need > s->nj_partials_n) {
+    if (s->nj_partials) cudaFree(s->nj_partials);  // synchronises: no earlier call still reads it
+    s->nj_partials = nullptr;
+    s->nj_partials_n = 0;
+    cudaError_t ea = cudaMalloc((void**)&s->nj_partials, sizeof(float) * need);
+    if (ea != cudaSuccess) return cuda_fail(s, ea, "nj_backward: scratch");
+    s->nj_partials_n = need;
+  }
+  cudaError_t e = launch_nj_backward(G, N, params, n, x, q, d_el, d_j, grad_out, s->nj_partials, max_blocks,
                                      (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "nj_backward");
   return LRDMC_OK;
@@ -1280,6 +1296,7 @@ void lrdmc_destroy(lrdmc_system_t s)
   if (s->nj_tab) cudaFree(s->nj_tab);
   if (s->nj_tab_df) cudaFree(s->nj_tab_df);
   if (s->base_err) cudaFree(s->base_err);
+  if (s->nj_partials) cudaFree(s->nj_partials);
   for (cudaEvent_t ev : s->events) cudaEventDestroy(ev);
   delete s;
 }

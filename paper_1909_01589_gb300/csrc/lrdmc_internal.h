@@ -190,8 +190,12 @@ void nj_build_table(const lrdmc_nj_spec& spec, const float* params, std::vector<
 cudaError_t launch_nj_forward(const NjGeom& G, const NjNetDev& N, const float* params, int n, const double* x,
                               const double* grad_base, const double* e_base, float* el, float* j, float* q,
                               float* pair_out, cudaStream_t st);
+// Grid size of the backward kernel (its per-block partial gradients need
+// that many times n_params floats of scratch); -1 on a CUDA error.
+int nj_backward_max_blocks(const NjGeom& G, const NjNetDev& N);
 cudaError_t launch_nj_backward(const NjGeom& G, const NjNetDev& N, const float* params, int n, const double* x,
-                               const float* q, const float* d_el, const float* d_j, float* grad, cudaStream_t st);
+                               const float* q, const float* d_el, const float* d_j, float* grad, float* partials,
+                               int max_blocks, cudaStream_t st);
 
 cudaError_t launch_base_terms(const SysDev& S, const Layout& Lo, int n, const double* x, double* grad,
                               double* e, int* err, cudaStream_t st);

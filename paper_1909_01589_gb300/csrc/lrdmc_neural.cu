@@ -461,11 +461,14 @@ k_nj_assemble(const __grid_constant__ NjGeom G, int n, const double* x, const do
 // Backward: per pair, the upstream derivatives with respect to g, g', g''
 // from d_el and d_j of its configuration, then reverse through the cut-off,
 // the output layer and both activations (the derivative chains included).
-// Each warp accumulates its gradient in registers; blocks reduce in shared
-// memory and add to grad_out with one atomic per parameter.
+// Every sum runs in a fixed order, so the gradient is the same bits from
+// run to run: each warp accumulates layers 2 and 3 in registers and layer 1
+// in its own shared-memory slice (a lane owns its hidden units), the warps
+// are added in warp order, and each block writes its sums to partials
+// [blockIdx.x][n_params] for k_nj_grad_reduce.
 __global__ void __launch_bounds__(kNjWarps * 32, 2)
 k_nj_pairs_bwd(const __grid_constant__ NjGeom G, const __grid_constant__ NjNetDev N, const float* params, int n,
-               const double* x, const float* qv, const float* d_el, const float* d_j, float* grad_out)
+               const double* x, const float* qv, const float* d_el, const float* d_j, float* partials)
 {
   extern __shared__ float4 nj_smem4[];
   const NjSmem m = nj_stage(G, N, params, reinterpret_cast<float*>(nj_smem4));
@@ -475,10 +478,14 @@ k_nj_pairs_bwd(const __grid_constant__ NjGeom G, const __grid_constant__ NjNetDe
   const int D = N.D;
   const int H = kNjH, oW1 = 0, ob1 = H * D, oW2 = ob1 + H, ob2 = oW2 + H * H, ow3 = ob2 + H, ob3 = ow3 + H;
   const int np = ob3 + 1;
-  // block accumulator of the gradient (layer 1 is added per pair with
-  // shared atomics; the rest is held per warp in registers until the end)
+  // block accumulator of the gradient, then one layer-1 slice per warp
+  // (W1 and b1, the first ob1 + H entries of the parameter vector)
   float* acc = reinterpret_cast<float*>(m.chain + 2 * kNjWarps * kNjH);
+  const int np1 = ob1 + H;
+  float* acc1 = acc + np;
+  float* my1 = acc1 + wib * np1;
   for (int t = threadIdx.x; t < np; t += blockDim.x) acc[t] = 0.0f;
+  for (int t = threadIdx.x; t < kNjWarps * np1; t += blockDim.x) acc1[t] = 0.0f;
   __syncthreads();
   float gW2[2][kNjH];
   float gb2[2] = {0.0f, 0.0f}, gw3[2] = {0.0f, 0.0f};
@@ -556,26 +563,50 @@ k_nj_pairs_bwd(const __grid_constant__ NjGeom G, const __grid_constant__ NjNetDe
       const float dz = da * d1 + da1 * d2 * z1 + da2 * (d3 * z1 * z1 + d2 * z2);
       const float dz1 = da1 * d1 + 2.0f * da2 * d2 * z1;
       const float dz2 = da2 * d1;
-      atomicAdd(&acc[ob1 + v], dz);
-      atomicAdd(&acc[oW1 + v * D + N.F + pg.c], dz);
+      // hidden unit v belongs to this lane alone within the warp's slice
+      my1[ob1 + v] += dz;
+      my1[oW1 + v * D + N.F + pg.c] += dz;
 #pragma unroll
       for (int f = 0; f < kNjMaxF; ++f)
-        if (f < N.F) atomicAdd(&acc[oW1 + v * D + f], dz * f0[f] + dz1 * f1[f] + dz2 * f2[f]);
+        if (f < N.F) my1[oW1 + v * D + f] += dz * f0[f] + dz1 * f1[f] + dz2 * f2[f];
     }
     __syncwarp();
   }
-  // block reduction in shared memory, then one atomic per parameter
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int u = lane + 32 * h;
-#pragma unroll
-    for (int v = 0; v < kNjH; ++v) atomicAdd(&acc[oW2 + u * H + v], gW2[h][v]);
-    atomicAdd(&acc[ob2 + u], gb2[h]);
-    atomicAdd(&acc[ow3 + u], gw3[h]);
-  }
-  if (lane == 0) atomicAdd(&acc[ob3], gb3);
+  // block reduction in warp order (a lane owns output units u, so the adds
+  // of one warp touch distinct entries), layer 1 from the warp slices
   __syncthreads();
-  for (int t = threadIdx.x; t < np; t += blockDim.x) atomicAdd(&grad_out[t], acc[t]);
+  for (int w = 0; w < kNjWarps; ++w) {
+    if (wib == w) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int u = lane + 32 * h;
+#pragma unroll
+        for (int v = 0; v < kNjH; ++v) acc[oW2 + u * H + v] += gW2[h][v];
+        acc[ob2 + u] += gb2[h];
+        acc[ow3 + u] += gw3[h];
+      }
+      if (lane == 0) acc[ob3] += gb3;
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < np1; t += blockDim.x) {
+    float a = 0.0f;
+    for (int w = 0; w < kNjWarps; ++w) a += acc1[w * np1 + t];
+    acc[t] = a;
+  }
+  __syncthreads();
+  float* out = partials + (size_t)blockIdx.x * np;
+  for (int t = threadIdx.x; t < np; t += blockDim.x) out[t] = acc[t];
+}
+
+// grad[t] = sum over the backward blocks of partials[b][t], in block order.
+__global__ void k_nj_grad_reduce(const float* partials, int blocks, int np, float* grad)
+{
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= np) return;
+  float a = 0.0f;
+  for (int b = 0; b < blocks; ++b) a += partials[(size_t)b * np + t];
+  grad[t] = a;
 }
 
 static int nj_smem_bytes(const NjGeom& G, const NjNetDev& N, bool backward)
@@ -583,7 +614,7 @@ static int nj_smem_bytes(const NjGeom& G, const NjNetDev& N, bool backward)
   // staging image and one chain buffer per warp; the backward pass adds a
   // second chain buffer per warp and the block's gradient accumulator
   int f = nj_smem_floats(N.D, G.n_pairs);
-  if (backward) f += 4 * kNjWarps * kNjH + nj_n_params(N.F, N.C, kNjH);
+  if (backward) f += 4 * kNjWarps * kNjH + nj_n_params(N.F, N.C, kNjH) + kNjWarps * (kNjH * N.D + kNjH);
   return (int)sizeof(float) * f;
 }
 
@@ -614,19 +645,31 @@ cudaError_t launch_nj_forward(const NjGeom& G, const NjNetDev& N, const float* p
   return cudaGetLastError();
 }
 
+int nj_backward_max_blocks(const NjGeom& G, const NjNetDev& N)
+{
+  const int smem = nj_smem_bytes(G, N, true);
+  if (cudaFuncSetAttribute((const void*)k_nj_pairs_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+      cudaSuccess)
+    return -1;
+  return nj_grid((const void*)k_nj_pairs_bwd, smem);
+}
+
 cudaError_t launch_nj_backward(const NjGeom& G, const NjNetDev& N, const float* params, int n, const double* x,
-                               const float* q, const float* d_el, const float* d_j, float* grad, cudaStream_t st)
+                               const float* q, const float* d_el, const float* d_j, float* grad, float* partials,
+                               int max_blocks, cudaStream_t st)
 {
   const int np = nj_n_params(N.F, N.C, kNjH);
-  cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(float) * np, st);
-  if (e != cudaSuccess || n <= 0) return e;
+  if (n <= 0) return cudaMemsetAsync(grad, 0, sizeof(float) * np, st);
   const int smem = nj_smem_bytes(G, N, true);
-  e = cudaFuncSetAttribute((const void*)k_nj_pairs_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute((const void*)k_nj_pairs_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       smem);
   if (e != cudaSuccess) return e;
   const long long total = (long long)n * G.n_pairs;
-  long long blocks = nj_grid((const void*)k_nj_pairs_bwd, smem);
-  blocks = std::min(blocks, (total + kNjWarps - 1) / kNjWarps);
-  k_nj_pairs_bwd<<<(int)blocks, kNjWarps * 32, smem, st>>>(G, N, params, n, x, q, d_el, d_j, grad);
+  long long blocks = std::min((long long)max_blocks, (total + kNjWarps - 1) / kNjWarps);
+  k_nj_pairs_bwd<<<(int)blocks, kNjWarps * 32, smem, st>>>(G, N, params, n, x, q, d_el, d_j, partials);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_nj_grad_reduce<<<(np + 255) / 256, 256, 0, st>>>(partials, (int)blocks, np, grad);
   return cudaGetLastError();
 }
 

@@ -233,6 +233,30 @@ def test_training_backward_finite_difference(pkg, oracle_mod, nn):
         assert abs(fd - an) < 3e-2 * max(abs(an), 1e-3 * float(grad.norm())), (fd, an)
 
 
+def test_training_is_bitwise_repeatable(pkg, oracle_mod, nn):
+    """The backward kernel sums in a fixed order: the same inputs give the
+    same gradient bits (over 4096 configurations, so many blocks contribute),
+    and a 30-step training run repeated from the same start ends at the same
+    parameters."""
+    from paper_1909_01589_gb300 import neural as N
+
+    system = S.neon()
+    spec = S.default_neural_spec(system)
+    params = torch.tensor(S.neural_init(spec, 3, out_scale=0.5), device="cuda")
+    g = pkg.LrdmcSystem(system)
+    x = torch.tensor(S.initial_positions(system, 4096, 91), device="cuda")
+    gb, eb = g.base_terms(x)
+    el, j, q, _ = g.nj_forward(spec, params, x, gb, eb)
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    d_el = torch.randn(4096, device="cuda", generator=gen)
+    d_j = torch.randn(4096, device="cuda", generator=gen)
+    g1 = g.nj_backward(spec, params, x, q, d_el, d_j)
+    g2 = g.nj_backward(spec, params, x, q, d_el, d_j)
+    assert torch.count_nonzero(g1) > 0 and torch.equal(g1, g2)
+    runs = [N.train(g, spec, S.neural_init(spec, 3), x, gb, eb, steps=30, batch=1024, seed=7)[0] for _ in range(2)]
+    assert torch.equal(runs[0], runs[1])
+
+
 def test_training_gain_on_neon(pkg, oracle_mod, nn):
     """What the trained term gains: 65536 configurations from a plain
     projection of Ne (a = 0.2, double grid), 400 Adam steps on the GPU
