@@ -44,22 +44,39 @@ import lrdmc_synth as S  # noqa: E402
 
 METRIC = "LRDMC walker-moves/s and efficiency 1/(σ²·t) vs plain FP64, 1 GB300"
 WORKLOAD = dict(system="Ne", n_walkers=4096, a=0.2, spacing="double grid, this work (Eq. 3, S-13, Eq. 6/7)",
-                tau=0.025, e_trial=-128.9, recompute_every=5, precision="fp64")
+                tau=0.025, e_trial=-128.9, recompute_every=5)
+# what each --precision computes in: the evaluation (all lattice moves, the
+# local energy, waiting times, heat bath) and the state (positions, inverse
+# Slater matrices, Sherman-Morrison updates, weights, reconfiguration)
+ARITHMETIC = {"df64": {"evaluation": "double-float (2 x fp32, ~48 significant bits)", "state": "fp64"},
+              "fp64": {"evaluation": "fp64", "state": "fp64"},
+              "fp32": {"evaluation": "fp32", "state": "fp64"}}
 SEED = 2024
 L2_FLUSH_BYTES = 512 << 20
 
 # FP64 pipe cost of the special functions on this GPU, in DFMA-equivalents:
 # DFMA rate / measured rate of each function (0.505e12 DFMA/s; sqrt 58.6e9/s,
-# reciprocal 89.3e9/s, exp 31.6e9/s, measured with csrc/fp64_rates.cu).
+# reciprocal 89.3e9/s, exp 31.6e9/s; profiles/fp64_rates_gb300.md).
 C_SQRT, C_DIV, C_EXP = 8.6, 5.7, 16.0
-FP64_PEAK_TFLOPS = 1.259  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TF)
+# ALU peaks from unit counts and the 2070 MHz maximum SM clock
+# (MEASURED_PEAKS.json records no ALU figure): FP64 152 SMs x 2 DFMA/clk x
+# 2 flop (1.01 TF measured); FP32 152 SMs x 128 lanes x 2 flop (70 TF
+# measured)
+FP64_PEAK_TFLOPS = 1.259
+FP32_PEAK_TFLOPS = 80.5
 
 
-def dfma_equiv_per_move(system, G):
-    """Algorithmic FP64 work of one walker-move (one jump plus one evaluation
-    of all P = 6 G N lattice moves and of the local energy), in DFMA
-    equivalents: adds, multiplies and FMAs count 1, sqrt/div/exp their
-    measured cost. Counted from the formulas, not from the kernels' code."""
+def method_ops_per_move(system, G):
+    """Operations of one walker-move - one jump plus one evaluation of all
+    P = 6 G N lattice moves and of the local energy - counted from the
+    formulas (not from the kernels' code): arithmetic (add, multiply and FMA
+    count 1 each), square roots, divisions and exponentials. Per lattice
+    move: the distances to the nuclei, the basis exponentials, the length-K
+    dot with the projected inverse column, the N - 1 + n_nuc Pade pair
+    terms, exp of the Jastrow difference, p at the bond midpoint (double
+    grid); per walker-move: the local energy (basis value, gradient and
+    Laplacian, pair terms and their derivatives), the Sherman-Morrison
+    update and the heat-bath scan."""
     N, n_nuc, n_ao = system.N, system.n_nuc, system.n_ao
     centers = len({s.center for s in system.shells})
     exps = 0
@@ -73,15 +90,20 @@ def dfma_equiv_per_move(system, G):
         prev = key
     nsig = system.n_up
     P = 6 * G * N
-    pair = 6 + C_SQRT + 2 + C_DIV + 2  # distance, Pade term
-    per_cand = (3 + centers * (6 + C_SQRT) + exps * (1 + C_EXP) + 2 * n_ao
-                + (N - 1 + n_nuc) * pair + 2 + C_EXP + 2
-                + ((3 + n_nuc * 6 + C_EXP + 2) if G == 2 else 0))
-    el = N * (centers * (6 + C_SQRT) + exps * (1 + C_EXP) + 12 * n_ao
-              + (N - 1 + n_nuc) * (pair + C_DIV + 12)) + N * n_ao * nsig
-    sm = n_ao * 8 + exps * C_EXP + n_ao * nsig + nsig * nsig + 2 * nsig * nsig
-    scan = 2 * P
-    return P * per_cand + el + sm + scan
+    npair = N - 1 + n_nuc
+    cand = {"arith": 3 + centers * 6 + exps + 2 * n_ao + npair * 10 + 4 + ((5 + n_nuc * 6) if G == 2 else 0),
+            "sqrt": centers + npair, "div": npair, "exp": exps + 1 + (1 if G == 2 else 0)}
+    el = {"arith": N * (centers * 6 + exps + 12 * n_ao + npair * 22) + N * n_ao * nsig,
+          "sqrt": N * (centers + npair), "div": N * npair * 2, "exp": N * exps}
+    sm = {"arith": n_ao * 8 + n_ao * nsig + 3 * nsig * nsig, "sqrt": 0, "div": 0, "exp": exps}
+    return {k: P * cand[k] + el[k] + sm[k] + (2 * P if k == "arith" else 0) for k in cand}
+
+
+def dfma_equiv_per_move(system, G):
+    """The method's work of one walker-move in DFMA-equivalents: arithmetic
+    counts 1, sqrt, division and exp their measured FP64-pipe cost."""
+    o = method_ops_per_move(system, G)
+    return o["arith"] + C_SQRT * o["sqrt"] + C_DIV * o["div"] + C_EXP * o["exp"]
 
 
 def _env_rank():
@@ -155,7 +177,6 @@ class ClockSampler:
 # csrc/df64.cuh (add/sub/mul = 1, fma = 2, MUFU seed = 1).
 DF_ADD, DF_ADD_FAST, DF_ADD_F, DF_MUL, DF_SQR = 11, 11, 10, 10, 9
 DF_DIV, DF_SQRT, DF_EXP, DF_LOG = 11, 10, 101, 132
-FP32_PEAK_TFLOPS = 80.5  # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 
 
 def df_flops_per_move(system, G):
@@ -329,27 +350,7 @@ def run_ours(args):
             dist.destroy_process_group()
         return
     G = 2
-    n_int = max(leg["n_int"], 1)
-    kernel_ms = leg["t_int_ms"] / n_int
-    moves_per_launch = leg["moves"] / n_int
-    if main_prec == pkg.PRECISION_DF64:
-        flop_per_move = df_flops_per_move(system, G)
-        achieved = flop_per_move * moves_per_launch / (kernel_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": "k_interval<df64>", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                "peak_source": "nominal FP32 pipe (152 SM x 128 lanes x 2 flop x 2.07 GHz; 70 TF measured with "
-                               "csrc/fp64_rates.cu); work = FP32 flops of the double-float formulation",
-                "flop_per_move": flop_per_move}
-    else:
-        flop_per_move = 2.0 * dfma_equiv_per_move(system, G)
-        achieved = flop_per_move * moves_per_launch / (kernel_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": "k_interval<fp64>", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "peak_source": "nominal FP64 (recipe: 1.25 TF = 152 SM x 2 DFMA/clk x 2 x 2.07 GHz); "
-                               "no FP64 entry in MEASURED_PEAKS.json",
-                "flop_per_move": flop_per_move}
-    roof["kernel_ms_per_launch"] = kernel_ms
-    roof["traffic"] = _read_traffic(main_prec == pkg.PRECISION_DF64)
+    roof = roofline(system, G, args.precision, leg)
     t_sec = leg["eff_ms"] * 1e-3
     err, _ = stats.reblock(leg["e"])
     eff = {"value": stats.efficiency(leg["e"], t_sec), "unit": "1/(Ha^2 s)", "sigma_mean_Ha": err,
@@ -366,10 +367,11 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32x2 (double-float evaluation) + f64 state" if main_prec == pkg.PRECISION_DF64 else "f64",
+        "dtype": {"df64": "f32x2 (double-float evaluation) + f64 state", "fp64": "f64",
+                  "fp32": "f32 evaluation + f64 state"}[args.precision],
         "data": "synthetic",
         "config": {"workload": "Ne all-electron, 4096 walkers, a=0.2 bohr, smart double grid (this work), "
-                               "tau=0.025, FP64-parity arithmetic", **WORKLOAD, "evaluation": args.precision,
+                               "tau=0.025", **WORKLOAD, **ARITHMETIC[args.precision],
                    "walkers_per_gpu": W, "l2": "flushed between timed steps (512 MiB write)",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_moves_all / t_e2e_all, "unit": "walker-moves/s",
@@ -391,7 +393,8 @@ def run_ours(args):
             "fp64_efficiency": fp_eff, "efficiency_ratio": eff["value"] / fp_eff,
             "fp64_energy_Ha": stats.energy_estimate(fp["e"], fp["w"], 0),
             "energy_difference_Ha": eff["energy_Ha"] - stats.energy_estimate(fp["e"], fp["w"], 0),
-            "fp64_kernel_ms_per_launch": fp["t_int_ms"] / max(fp["n_int"], 1)}
+            "fp64_kernel_ms_per_launch": fp["t_int_ms"] / max(fp["n_int"], 1),
+            "roofline": roofline(system, G, "fp64", fp)}
     if mx is not None:
         mx_value = mx["moves"] / (mx["total_ms"] * 1e-3)
         mx_err, _ = stats.reblock(mx["e"])
@@ -407,7 +410,8 @@ def run_ours(args):
             "energy_Ha": mx_energy, "sigma_mean_Ha": mx_err,
             "energy_minus_fp64_Ha": mx_energy - ref_energy,
             "combined_sigma_Ha": float(np.hypot(mx_err, ref_err)),
-            "kernel_ms_per_launch": mx["t_int_ms"] / max(mx["n_int"], 1)}
+            "kernel_ms_per_launch": mx["t_int_ms"] / max(mx["n_int"], 1),
+            "roofline": roofline(system, G, "fp32", mx)}
     if nj is not None:
         leg_nj, info = nj
         nj_value = leg_nj["moves"] / (leg_nj["total_ms"] * 1e-3)
@@ -526,11 +530,12 @@ def batched_leg(args, pkg, torch, precision, seed):
                     "grid sizes chosen by measurement"}
 
 
-def _read_traffic(df64=True):
-    """dram bytes per k_interval launch from the committed ncu summary, if the
-    kernel source has not changed since it was taken; else None."""
-    name = "k_interval_df64_ne4096_traffic.json" if df64 else "k_interval_ne4096_traffic.json"
-    path = os.path.join(ROOT, "profiles", name)
+def _read_profile(precision):
+    """The ncu record of k_interval in this arithmetic on the bench workload
+    (profiles/k_interval_<precision>_ne4096_traffic.json: dram bytes per
+    launch and pipe activities), if the kernel source has not changed since
+    it was taken; else None."""
+    path = os.path.join(ROOT, "profiles", f"k_interval_{precision}_ne4096_traffic.json")
     try:
         d = json.load(open(path))
     except (OSError, ValueError):
@@ -540,7 +545,49 @@ def _read_traffic(df64=True):
     src = open(os.path.join(ROOT, "paper_1909_01589_gb300", "csrc", "lrdmc_kernels.cu"), "rb").read()
     if hashlib.sha256(src).hexdigest() != d.get("kernel_sha256"):
         return None
-    return d.get("dram_bytes_per_launch")
+    return d
+
+
+def roofline(system, G, precision, leg):
+    """Roofline of k_interval (the dominant kernel) for one leg. Work: the
+    method's operations per walker-move counted from the formulas
+    (method_ops_per_move), times the walker-moves of an average launch,
+    over the launch's CUDA-event time (leg["t_int_ms"] / leg["n_int"],
+    events on the library's stream). The IEEE-double and double-float forms
+    give the same FP64-parity results, so both are measured in
+    FP64-equivalent flops (FMA = 2, sqrt/div/exp at their FP64-pipe cost)
+    against the FP64 pipe; the double-float form computes on the FP32 pipe,
+    which lets it pass that roofline, and its own pipe's activity comes from
+    the ncu record. The FP32 mode is measured in FP32 flops (arithmetic x 2,
+    each special function one) against the FP32 pipe."""
+    n_int = max(leg["n_int"], 1)
+    kernel_ms = leg["t_int_ms"] / n_int
+    moves = leg["moves"] / n_int
+    ops = method_ops_per_move(system, G)
+    prof = _read_profile(precision)
+    if precision in ("df64", "fp64"):
+        work = 2.0 * dfma_equiv_per_move(system, G)
+        peak, unit = FP64_PEAK_TFLOPS, "TFLOP/s (FP64-equivalent)"
+        src = "FP64 pipe from unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (1.01 TF measured)"
+    else:
+        work = 2.0 * ops["arith"] + ops["sqrt"] + ops["div"] + ops["exp"]
+        peak, unit = FP32_PEAK_TFLOPS, "TFLOP/s (FP32)"
+        src = "FP32 pipe from unit counts: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (70 TF measured)"
+    achieved = work * moves / (kernel_ms * 1e-3) / 1e12
+    out = {"bound": "alu", "kernel": f"k_interval<{precision}>", "achieved": achieved, "peak": peak, "unit": unit,
+           "frac": achieved / peak, "traffic": prof.get("dram_bytes_per_launch") if prof else None,
+           "peak_source": src + "; MEASURED_PEAKS.json has no ALU entry",
+           "work_per_move": {**ops, "flops": work}, "moves_per_launch": moves, "kernel_ms_per_launch": kernel_ms}
+    if prof and "pipes" in prof:
+        out["ncu_pipes"] = prof["pipes"]
+    if precision == "df64":
+        dff = df_flops_per_move(system, G)
+        a32 = dff * moves / (kernel_ms * 1e-3) / 1e12
+        out["double_float_formulation"] = {
+            "fp32_flops_per_move": dff, "achieved_tflops": a32, "peak_tflops": FP32_PEAK_TFLOPS,
+            "frac": a32 / FP32_PEAK_TFLOPS,
+            "note": "the same operations priced at the FP32 cost of their double-float primitives"}
+    return out
 
 
 def _oracle_rate(n_walkers, budget_s, threads, steps=None, warmup=1):

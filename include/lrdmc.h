@@ -214,7 +214,9 @@ LRDMC_API lrdmc_status lrdmc_evaluate(lrdmc_system_t sys, int n_configs, const d
  * LRDMC_ERR_ARG. The first call on a device looks up the array's device
  * address (once per device, with that device current); make that first
  * call before any stream capture. The call clears the words it uses, then
- * synchronises the stream to read the summary word. All calls share the
+ * synchronises the stream to read the summary word; when it reports
+ * LRDMC_ERR_SINGULAR, lrdmc_last_error names the first configuration whose
+ * status word is set. All calls share the
  * array and it keeps the last call's contents: calls that overlap on the
  * GPU (other threads, other streams) race on it. No cudaMalloc, cudaFree
  * or other device allocation happens in this call. */

@@ -87,7 +87,7 @@ def lib():
         L.orc_lattice_eval.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.orc_heat_bath.restype = i
         L.orc_heat_bath.argtypes = [vp, i, d, d, vp]
-        L.orc_comb.argtypes = [i, vp, d, vp, vp]
+        L.orc_comb.argtypes = [i, vp, d, vp, vp, vp]
         L.orc_pop_create.restype = vp
         L.orc_pop_create.argtypes = [vp, i, vp, u64, d, d, i]
         L.orc_pop_destroy.argtypes = [vp]
@@ -96,7 +96,7 @@ def lib():
         L.orc_pop_trace.restype = i
         L.orc_pop_trace.argtypes = [vp, vp, vp, vp, i]
         L.orc_pop_walkers.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
-        L.orc_pop_margins.argtypes = [vp, vp, vp]
+        L.orc_pop_margins.argtypes = [vp, vp, vp, vp]
         L.orc_pop_moves.restype = ct.c_longlong
         L.orc_pop_moves.argtypes = [vp]
         L.orc_pop_error.restype = i
@@ -175,7 +175,7 @@ def comb(wt, xi):
     wt = _f64(wt)
     parent = np.zeros(len(wt), np.int32)
     m = ct.c_double()
-    lib().orc_comb(len(wt), _p(wt), float(xi), _p(parent), ct.byref(m))
+    lib().orc_comb(len(wt), _p(wt), float(xi), _p(parent), ct.byref(m), None)
     return parent, m.value
 
 
@@ -353,41 +353,17 @@ class OraclePopulation:
         lib().orc_pop_walkers(self.h, _p(x), _p(EL), _p(b), _p(T), _p(logw), _p(jumps), _p(parent))
         return dict(x=x, EL=EL, b=b, T=T, logw_pre=logw, jumps_pre=jumps, parent=parent)
 
-    def margins(self):
+    def margins(self, teeth=False):
+        """Distances of the last interval's decisions from their bin edges:
+        per walker slot (smallest over its waiting-time and heat-bath
+        decisions, relative to tau and to b), the comb's smallest (relative
+        to the total weight) and, with teeth, the comb's per new slot."""
         m = np.zeros(self.W)
+        mt = np.zeros(self.W)
         mc = ct.c_double()
-        lib().orc_pop_margins(self.h, _p(m), ct.byref(mc))
-        return m, mc.value
+        lib().orc_pop_margins(self.h, _p(m), ct.byref(mc), _p(mt))
+        return (m, mc.value, mt) if teeth else (m, mc.value)
 
     @property
     def moves(self):
         return lib().orc_pop_moves(self.h)
-
-
-def energy_estimate(e, wbar, L=0):
-    """Population-control-corrected mixed estimator: each e_k is weighted by
-    the product of the last L mean weights wbar_{k-l}, l = 0..L-1 (L = 0: plain
-    mean of e_k)."""
-    e = np.asarray(e, float)
-    wbar = np.asarray(wbar, float)
-    if L <= 0:
-        return float(np.mean(e))
-    lw = np.log(wbar)
-    c = np.concatenate([[0.0], np.cumsum(lw)])
-    k = np.arange(len(e))
-    lo = np.maximum(k - L + 1, 0)
-    G = np.exp(c[k + 1] - c[lo])
-    return float(np.sum(G * e) / np.sum(G))
-
-
-def reblock_error(e):
-    """Standard error of the mean of a correlated series by blocking
-    (Flyvbjerg and Petersen 1989): the plateau (maximum) over block levels
-    with at least 16 blocks."""
-    x = np.asarray(e, float).copy()
-    best = np.std(x, ddof=1) / np.sqrt(len(x)) if len(x) > 1 else 0.0
-    while len(x) >= 32:
-        x = 0.5 * (x[: len(x) // 2 * 2 : 2] + x[1 : len(x) // 2 * 2 : 2])
-        err = np.std(x, ddof=1) / np.sqrt(len(x))
-        best = max(best, err)
-    return float(best)

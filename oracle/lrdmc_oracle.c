@@ -807,6 +807,7 @@ struct orc_pop {
   /* values of the last finished interval, before reconfiguration */
   double* logw_pre; int* jumps_pre; int* parent;
   double* margin_w; double margin_comb;
+  double* margin_teeth;  /* per new slot t: distance of tooth t from its bin's edges */
   int have_eval; orc_lattice eval_lat; int P;
   uint64_t k;
   int n_trace, cap_trace;
@@ -843,8 +844,9 @@ int orc_heat_bath(const double* T, int P, double b, double u, double* margin)
  * whose bin [C_{s-1}, C_s) holds (t + xi) * C_{W-1} / W. Every walker gets
  * floor or ceil of W wt_s / sum(wt) copies, exactly that many on average
  * over xi. *margin receives the smallest distance of a tooth from the edges
- * of its bin, relative to the total weight. */
-void orc_comb(int W, const double* wt, double xi, int* parent, double* margin)
+ * of its bin, relative to the total weight; margin_teeth[t] (nullable) the
+ * same distance for tooth t alone. */
+void orc_comb(int W, const double* wt, double xi, int* parent, double* margin, double* margin_teeth)
 {
   double* C = (double*)malloc(sizeof(double) * W);
   double sumw = 0.0, mg = INFINITY;
@@ -855,12 +857,13 @@ void orc_comb(int W, const double* wt, double xi, int* parent, double* margin)
     double target = ((double)t + xi) * total / (double)W;
     while (s_ptr < W - 1 && !(target < C[s_ptr])) ++s_ptr;
     parent[t] = s_ptr;
-    double m1 = fabs(target - C[s_ptr]) / total;
-    if (m1 < mg) mg = m1;
+    double mt = fabs(target - C[s_ptr]) / total;
     if (s_ptr > 0) {
       double m2 = fabs(target - C[s_ptr - 1]) / total;
-      if (m2 < mg) mg = m2;
+      if (m2 < mt) mt = m2;
     }
+    if (mt < mg) mg = mt;
+    if (margin_teeth) margin_teeth[t] = mt;
   }
   if (margin) *margin = mg;
   free(C);
@@ -900,6 +903,7 @@ orc_pop* orc_pop_create(orc_system* s, int W, const double* x0, uint64_t seed,
   p->jumps_pre = (int*)calloc(W, sizeof(int));
   p->parent = (int*)calloc(W, sizeof(int));
   p->margin_w = (double*)calloc(W, sizeof(double));
+  p->margin_teeth = (double*)calloc(W, sizeof(double));
   memcpy(p->x, x0, sizeof(double) * W * N * 3);
   for (int w = 0; w < W; ++w) {
     p->parent[w] = w;
@@ -922,7 +926,7 @@ void orc_pop_destroy(orc_pop* p)
   if (!p) return;
   free(p->x); free(p->Aup); free(p->Adn); free(p->rot); free(p->T); free(p->b); free(p->EL);
   free(p->logw); free(p->jumps); free(p->logw_pre); free(p->jumps_pre); free(p->parent);
-  free(p->margin_w); free(p->tr_e); free(p->tr_w); free(p->tr_j); free(p);
+  free(p->margin_w); free(p->margin_teeth); free(p->tr_e); free(p->tr_w); free(p->tr_j); free(p);
 }
 
 static void eval_walker(orc_pop* p, const orc_lattice* L, int w)
@@ -1033,7 +1037,7 @@ static void reconfigure(orc_pop* p, uint64_t k)
   p->n_trace++;
   double u[4];
   draw4(p, SLOT_GLOBAL, k, 0, TAG_COMB, u);
-  orc_comb(W, wt, u[0], p->parent, &p->margin_comb);
+  orc_comb(W, wt, u[0], p->parent, &p->margin_comb, p->margin_teeth);
   /* gather the parents' state into the new slots */
   const int P = p->P_cap;
   double* x = (double*)malloc(sizeof(double) * W * N * 3);
@@ -1115,8 +1119,9 @@ void orc_pop_walkers(const orc_pop* p, double* x, double* EL, double* b, double*
   if (parent) memcpy(parent, p->parent, sizeof(int) * W);
 }
 
-void orc_pop_margins(const orc_pop* p, double* margin_walker, double* margin_comb)
+void orc_pop_margins(const orc_pop* p, double* margin_walker, double* margin_comb, double* margin_teeth)
 {
+  if (margin_teeth) memcpy(margin_teeth, p->margin_teeth, sizeof(double) * p->W);
   if (margin_walker) memcpy(margin_walker, p->margin_w, sizeof(double) * p->W);
   if (margin_comb) *margin_comb = p->margin_comb;
 }

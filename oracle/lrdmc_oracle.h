@@ -96,7 +96,7 @@ void   orc_lattice_eval(const orc_system* s, const orc_lattice* L, const double*
 
 /* ---- heat bath and comb ---- */
 int    orc_heat_bath(const double* T, int P, double b, double u, double* margin);
-void   orc_comb(int W, const double* wt, double xi, int* parent, double* margin);
+void   orc_comb(int W, const double* wt, double xi, int* parent, double* margin, double* margin_teeth);
 
 /* ---- the walker population and the projection ---- */
 typedef struct orc_pop orc_pop;
@@ -107,7 +107,8 @@ int    orc_pop_step(orc_pop* p, const orc_lattice* L, int n_steps, int n_threads
 int    orc_pop_trace(const orc_pop* p, double* e, double* wbar, double* mean_jumps, int max_n);
 void   orc_pop_walkers(const orc_pop* p, double* x, double* EL, double* b, double* T,
                        double* logw_pre, int* jumps_pre, int* parent);
-void   orc_pop_margins(const orc_pop* p, double* margin_walker, double* margin_comb);
+void   orc_pop_margins(const orc_pop* p, double* margin_walker, double* margin_comb,
+                       double* margin_teeth);
 long long orc_pop_moves(const orc_pop* p);
 int    orc_pop_error(const orc_pop* p);
 

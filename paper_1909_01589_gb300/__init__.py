@@ -331,6 +331,37 @@ class LrdmcSystem:
         self._check(load_library().lrdmc_load(self.h, path.encode()))
 
     # ---------------------------------------------------------------- stateless
+    def _eval_args(self, x, rot, P, out=None):
+        """Checks of the arguments of evaluate / evaluate_static before any
+        pointer reaches the library: x [n][N][3] and rot [n][9] float64 on
+        one CUDA device; out = (ratio [n][P], T [n][P], b [n], el [n]),
+        float64, contiguous, on the same device (the kernels write exactly
+        these extents, so a smaller or differently typed buffer is refused
+        here rather than overrun on the device)."""
+        import torch
+
+        if not (isinstance(x, torch.Tensor) and isinstance(rot, torch.Tensor)):
+            raise ValueError("x and rot must be torch tensors")
+        if x.dim() != 3 or tuple(x.shape[1:]) != (self.N, 3):
+            raise ValueError(f"x must be [n][{self.N}][3], got {tuple(x.shape)}")
+        n = int(x.shape[0])
+        if tuple(rot.shape) != (n, 9):
+            raise ValueError(f"rot must be [{n}][9], got {tuple(rot.shape)}")
+        for name, t in (("x", x), ("rot", rot)):
+            if t.dtype != torch.float64 or not t.is_cuda:
+                raise ValueError(f"{name} must be a float64 CUDA tensor")
+        if rot.device != x.device:
+            raise ValueError("x and rot must be on the same device")
+        if out is not None:
+            if len(out) != 4:
+                raise ValueError("out must be (ratio, T, b, el)")
+            for name, t, shape in zip(("ratio", "T", "b", "el"), out, ((n, P), (n, P), (n,), (n,))):
+                if not isinstance(t, torch.Tensor) or tuple(t.shape) != shape:
+                    raise ValueError(f"out {name} must have shape {shape}")
+                if t.dtype != torch.float64 or t.device != x.device or not t.is_contiguous():
+                    raise ValueError(f"out {name} must be a contiguous float64 tensor on {x.device}")
+        return n
+
     def evaluate_static(self, x, rot, a, spacing: Spacing = Spacing(), stream=None, out=None):
         """Like evaluate, through lrdmc_evaluate_static: the library allocates
         no device memory (its scratch is a static device array shared by all
@@ -338,9 +369,9 @@ class LrdmcSystem:
         preallocated (ratio, T, b, el) CUDA tensors."""
         import torch
 
-        n = int(x.shape[0])
         G = 1 if spacing.kind == SINGLE else 2
         P = 6 * self.N * G
+        n = self._eval_args(x, rot, P, out)
         x = x.contiguous()
         rot = rot.contiguous()
         if out is None:
@@ -363,9 +394,9 @@ class LrdmcSystem:
         ratio [n][P], T [n][P], b [n], el [n]."""
         import torch
 
-        n = int(x.shape[0])
         G = 1 if spacing.kind == SINGLE else 2
         P = 6 * self.N * G
+        n = self._eval_args(x, rot, P)
         x = x.contiguous()
         rot = rot.contiguous()
         ratio = torch.empty((n, P), dtype=torch.float64, device=x.device)

@@ -709,11 +709,13 @@ lrdmc_status lrdmc_evaluate_static(lrdmc_system_t s, int n, const double* x, con
   LatDev L;
   lrdmc_status st = lattice_from(s, a, sp, L);
   if (st != LRDMC_OK) return st;
-  int summary = 0;
-  cudaError_t e = launch_evaluate_static(s->S, s->Lo, L, n, x, rot, ratio, T, b, el, &summary,
+  int summary = 0, first_bad = -1;
+  cudaError_t e = launch_evaluate_static(s->S, s->Lo, L, n, x, rot, ratio, T, b, el, &summary, &first_bad,
                                          (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "evaluate_static");
-  if (summary & kErrSingular) return fail(s, LRDMC_ERR_SINGULAR, "evaluate_static: singular Slater matrix");
+  if (summary & kErrSingular)
+    return fail(s, LRDMC_ERR_SINGULAR, "evaluate_static: singular Slater matrix (first at configuration " +
+                                           std::to_string(first_bad) + ")");
   return LRDMC_OK;
 }
 

@@ -202,6 +202,6 @@ cudaError_t launch_base_terms(const SysDev& S, const Layout& Lo, int n, const do
 
 cudaError_t launch_evaluate_static(const SysDev& S, const Layout& Lo, const LatDev& L, int n,
                                    const double* x, const double* rot, double* ratio, double* T,
-                                   double* b, double* el, int* summary, cudaStream_t st);
+                                   double* b, double* el, int* summary, int* first_bad, cudaStream_t st);
 
 }  // namespace lrdmc

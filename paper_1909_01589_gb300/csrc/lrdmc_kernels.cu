@@ -2021,32 +2021,26 @@ __global__ void __launch_bounds__(1024) k_reconfig(const PopDev P, const double*
   if (t == 0) *P.kdev = k + 1;
 }
 
-// Stateless evaluation of given configurations (one warp per configuration).
+// Stateless evaluation of configuration c (one warp): inverses from x, then
+// one evaluation of every lattice move and of the local energy. Returns
+// false, with no output written, for a singular Slater matrix. The body of
+// k_evaluate and of k_evaluate_static, which differ only in where they
+// report that.
 template <int PREC>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-k_evaluate(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, int n,
-           const double* x, const double* rot, double* ratio, double* T, double* b_out,
-           double* el_out, int* err)
+__device__ __forceinline__ bool evaluate_config(const SysDev& S, const Layout& Lo, const LatDev& L, const double* sC,
+                                                int c, int lane, int wib, const double* x, const double* rot,
+                                                double* ratio, double* T, double* b_out, double* el_out)
 {
   constexpr int PR = PREC & 3;         // the arithmetic (LRDMC_PRECISION_*)
   constexpr bool NJ = (PREC & 8) != 0;  // the neural pair term is set
   constexpr bool NC = (PREC & 4) != 0;  // the layout has no evaluation caches
-  extern __shared__ double smem[];
-  double* sC = smem;
-  stage_coefficients(S, sC);
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int c = blockIdx.x * kWarpsPerBlock + wib;
-  if (c >= n) return;
-  WarpMem wm = warp_mem(Lo, S, sC + Lo.head + wib * Lo.smem_warp);
+  WarpMem wm = warp_mem(Lo, S, const_cast<double*>(sC) + Lo.head + wib * Lo.smem_warp);
   for (int j = lane; j < 3 * Lo.N; j += 32) wm.x[j] = x[(size_t)c * 3 * Lo.N + j];
   for (int j = lane; j < 9; j += 32) wm.R[j] = rot[(size_t)c * 9 + j];
   __syncwarp();
   bool ok = warp_inverse(S, sC, wm.x, 0, wm.A, wm.scr, lane);
   ok = ok && warp_inverse(S, sC, wm.x, 1, wm.A + Lo.nu * Lo.nu, wm.scr, lane);
-  if (!ok) {
-    if (lane == 0) atomicOr(err, kErrSingular);
-    return;
-  }
+  if (!ok) return false;
   const int P = S.N * 6 * L.G;
   double b, el;
   df bdf;
@@ -2059,6 +2053,24 @@ k_evaluate(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, in
     if (b_out) b_out[c] = b;
     if (el_out) el_out[c] = el;
   }
+  return true;
+}
+
+// Stateless evaluation of given configurations (one warp per configuration).
+template <int PREC>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+k_evaluate(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, int n,
+           const double* x, const double* rot, double* ratio, double* T, double* b_out,
+           double* el_out, int* err)
+{
+  extern __shared__ double smem[];
+  double* sC = smem;
+  stage_coefficients(S, sC);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int c = blockIdx.x * kWarpsPerBlock + wib;
+  if (c >= n) return;
+  if (!evaluate_config<PREC>(S, Lo, L, sC, c, lane, wib, x, rot, ratio, T, b_out, el_out) && lane == 0)
+    atomicOr(err, kErrSingular);
 }
 
 // ----------------------------------------------------------------------------
@@ -2381,39 +2393,16 @@ k_evaluate_static(const __grid_constant__ SysDev S, const Layout Lo, const LatDe
                   const double* x, const double* rot, double* ratio, double* T, double* b_out,
                   double* el_out, int* scratch)
 {
-  constexpr int PR = PREC & 3;         // the arithmetic (LRDMC_PRECISION_*)
-  constexpr bool NJ = (PREC & 8) != 0;  // the neural pair term is set
-  constexpr bool NC = (PREC & 4) != 0;  // the layout has no evaluation caches
   extern __shared__ double smem[];
   double* sC = smem;
   stage_coefficients(S, sC);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int c = blockIdx.x * kWarpsPerBlock + wib;
   if (c >= n) return;
-  WarpMem wm = warp_mem(Lo, S, sC + Lo.head + wib * Lo.smem_warp);
-  for (int j = lane; j < 3 * Lo.N; j += 32) wm.x[j] = x[(size_t)c * 3 * Lo.N + j];
-  for (int j = lane; j < 9; j += 32) wm.R[j] = rot[(size_t)c * 9 + j];
-  __syncwarp();
-  bool ok = warp_inverse(S, sC, wm.x, 0, wm.A, wm.scr, lane);
-  ok = ok && warp_inverse(S, sC, wm.x, 1, wm.A + Lo.nu * Lo.nu, wm.scr, lane);
-  if (!ok) {
-    if (lane == 0) {
-      scratch[64 + c] = kErrSingular;
-      atomicOr(&scratch[0], kErrSingular);
-    }
-    return;
-  }
-  const int P = S.N * 6 * L.G;
-  double b, el;
-  df bdf;
-  warp_eval_any<PR, NJ, NC>(S, sC, L, wm, lane, ratio ? ratio + (size_t)c * P : nullptr, b, bdf, el);
-  if (T)
-    for (int j = lane; j < P; j += 32)
-      T[(size_t)c * P + j] = (PR != LRDMC_PRECISION_FP64) ? df_to_double(reinterpret_cast<const df*>(wm.T)[j])
-                                                            : wm.T[j];
-  if (lane == 0) {
-    if (b_out) b_out[c] = b;
-    if (el_out) el_out[c] = el;
+  // word 64 + c: status of configuration c; word 0: OR of all statuses
+  if (!evaluate_config<PREC>(S, Lo, L, sC, c, lane, wib, x, rot, ratio, T, b_out, el_out) && lane == 0) {
+    scratch[64 + c] = kErrSingular;
+    atomicOr(&scratch[0], kErrSingular);
   }
 }
 
@@ -2442,8 +2431,9 @@ static cudaError_t eval_scratch_address(int** out)
 
 cudaError_t launch_evaluate_static(const SysDev& S, const Layout& Lo, const LatDev& L, int n,
                                    const double* x, const double* rot, double* ratio, double* T,
-                                   double* b, double* el, int* summary, cudaStream_t st)
+                                   double* b, double* el, int* summary, int* first_bad, cudaStream_t st)
 {
+  if (first_bad) *first_bad = -1;
   if (n < 0 || n > LRDMC_STATIC_EVAL_MAX) return cudaErrorInvalidValue;
   int* scratch = nullptr;
   cudaError_t e = eval_scratch_address(&scratch);
@@ -2462,8 +2452,23 @@ cudaError_t launch_evaluate_static(const SysDev& S, const Layout& Lo, const LatD
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = cudaMemcpyAsync(summary, scratch, sizeof(int), cudaMemcpyDeviceToHost, st);
-  if (e != cudaSuccess) return e;
-  return cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess || *summary == 0 || !first_bad) return e;
+  // a configuration failed: find the first one from the per-configuration
+  // words, in chunks through a fixed host buffer (no allocation)
+  int chunk[1024];
+  for (int c0 = 0; c0 < n; c0 += 1024) {
+    const int m = n - c0 < 1024 ? n - c0 : 1024;
+    e = cudaMemcpyAsync(chunk, scratch + 64 + c0, sizeof(int) * (size_t)m, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    for (int j = 0; j < m; ++j)
+      if (chunk[j] != 0) {
+        *first_bad = c0 + j;
+        return cudaSuccess;
+      }
+  }
+  return cudaSuccess;
 }
 
 }  // namespace lrdmc

@@ -256,18 +256,37 @@ def extrapolation(name="He", a_values=(0.4, 0.3, 0.2, 0.15, 0.1), W=8192, steps=
             r = run(system, a, sp, W, steps, equil, tau, e_trial, seed, neural=nj)
             E.append(r["energy"])
             err.append(r["error"])
-        E, err = np.array(E), np.array(err)
-        A = np.stack([np.ones_like(E), np.asarray(a_values) ** 2, np.asarray(a_values) ** 4], 1)
-        wt = 1.0 / err ** 2
-        cov = np.linalg.inv(A.T @ (A * wt[:, None]))
-        coef = cov @ (A.T @ (wt * E))
-        chi2 = float(np.sum(wt * (A @ coef - E) ** 2))
-        out[label] = {"E": E.tolist(), "error": err.tolist(), "E0": float(coef[0]),
-                      "E0_error": float(np.sqrt(cov[0, 0])), "k1": float(coef[1]), "k2": float(coef[2]),
-                      "chi2_per_dof": chi2 / max(1, len(E) - 3)}
-        print(f"{name} {label}: E0 = {coef[0]:.5f} +- {np.sqrt(cov[0, 0]):.5f} (chi2/dof "
-              f"{out[label]['chi2_per_dof']:.2f}); E(a) = {np.round(E, 5).tolist()}", flush=True)
+        fit = fit_a0(a_values, E, err)
+        out[label] = {"E": list(map(float, E)), "error": list(map(float, err)), **fit}
+        print(f"{name} {label}: E0 = {fit['E0']:.5f} +- {fit['E0_error']:.5f} (chi2/dof "
+              f"{fit['chi2_per_dof']:.2f}); E(a) = {np.round(E, 5).tolist()}", flush=True)
     return out
+
+
+def fit_a0(a_values, E, err):
+    """Weighted least-squares fit E(a) = E0 + k1 a^2 + k2 a^4 (the lattice
+    error of LRDMC is even in a; the three-parameter form of the paper's
+    benzene footnote) to energies E with standard errors err. Returns E0 (the
+    a -> 0 limit), its standard error from the fit's covariance, k1, k2 and
+    chi^2 per degree of freedom."""
+    a = np.asarray(a_values, float)
+    E = np.asarray(E, float)
+    err = np.asarray(err, float)
+    if len(a) < 3 or len(E) != len(a) or len(err) != len(a):
+        raise ValueError("fit_a0 needs at least three (a, E, err) points of equal length")
+    A = np.stack([np.ones_like(a), a ** 2, a ** 4], 1)
+    wt = 1.0 / err ** 2
+    cov = np.linalg.inv(A.T @ (A * wt[:, None]))
+    coef = cov @ (A.T @ (wt * E))
+    chi2 = float(np.sum(wt * (A @ coef - E) ** 2))
+    return {"E0": float(coef[0]), "E0_error": float(np.sqrt(cov[0, 0])), "k1": float(coef[1]),
+            "k2": float(coef[2]), "chi2_per_dof": chi2 / max(1, len(E) - 3)}
+
+
+def z_exponent(Z, cost):
+    """Exponent x of the least-squares power law cost ~ Z^x (a straight line
+    in log-log, as Fig. 2 fits the CPU cost against Z)."""
+    return float(np.polyfit(np.log(np.asarray(Z, float)), np.log(np.asarray(cost, float)), 1)[0])
 
 
 def summarize(rows):
@@ -275,21 +294,27 @@ def summarize(rows):
     unit of projection time (single grid, this work's double grid, the
     previous double grid), their ratio (the acceleration at equal projection
     time, which equals the acceleration at fixed error when the variance per
-    unit projection time is the same for both lattices), and the exponents
-    x of a least-squares fit cost ~ Z^x over the systems."""
+    unit projection time is the same for both lattices), the cost at a fixed
+    target error (sigma^2 t = 1/efficiency: the GPU seconds that give a
+    standard error of 1 Ha, the quantity Fig. 2 plots), and the exponents x
+    of least-squares fits cost ~ Z^x over the systems (keys ending in
+    "_fixed_error" for the cost at fixed error)."""
     out = []
+    labels = ("single", "double_this_work", "double_previous")
     for r in rows:
         W = r["walkers"]
-        cost = {k: r[k]["seconds"] / (W * r[k]["intervals"] * r[k].get("tau", r["tau"]))
-                for k in ("single", "double_this_work", "double_previous")}
-        out.append({"system": r["system"], "Z": r["Z"], "cost": cost,
+        cost = {k: r[k]["seconds"] / (W * r[k]["intervals"] * r[k].get("tau", r["tau"])) for k in labels}
+        cost_err = {k: 1.0 / r[k]["efficiency"] for k in labels}
+        out.append({"system": r["system"], "Z": r["Z"], "cost": cost, "cost_fixed_error": cost_err,
                     "acceleration_time": cost["single"] / cost["double_this_work"],
+                    "acceleration_fixed_error": cost_err["single"] / cost_err["double_this_work"],
                     "acceleration_jumps": r["double_this_work_acceleration_jumps"]})
     fit = {}
     if len(out) >= 2:
-        lz = np.log([o["Z"] for o in out])
-        for k in ("single", "double_this_work", "double_previous"):
-            fit[k] = float(np.polyfit(lz, np.log([o["cost"][k] for o in out]), 1)[0])
+        Zs = [o["Z"] for o in out]
+        for k in labels:
+            fit[k] = z_exponent(Zs, [o["cost"][k] for o in out])
+            fit[k + "_fixed_error"] = z_exponent(Zs, [o["cost_fixed_error"][k] for o in out])
     return out, fit
 
 

@@ -59,3 +59,91 @@ def el_scale(system, x, el_ref):
     kinetic = el_ref - (v_en + v_ee + v_nn)
     return np.maximum.reduce([np.ones_like(el_ref), np.abs(el_ref),
                               np.abs(kinetic) + np.abs(v_en) + v_ee + abs(v_nn)])
+
+
+# ------------------------------------------------------------------ projection
+RTOL = 1e-10
+# A decision whose uniform lies within this distance of a bin edge (relative
+# to the quantity it is compared with: tau for the waiting time, b for the
+# heat bath, the total weight for a comb tooth) may go either way between
+# two correct evaluations; it is the only excuse for a parting.
+EDGE = 1e-10
+
+# Entries of the parity report (written at the end of the session by
+# conftest.py): one per compared run or evaluation case.
+REPORT = []
+
+
+def record(entry):
+    REPORT.append(entry)
+
+
+def compare_interval(system, gw, ow, margins, rtol=RTOL, edge=EDGE):
+    """One interval's populations, GPU (gw) against oracle (ow), as returned
+    by walkers(): jump counts and log-weights of every walker before the
+    comb, comb parents, positions and local energies after it.
+
+    Returns a dict: ok (everything agrees), the number of decisions the
+    oracle took (waiting times, heat-bath choices, comb teeth), how many of
+    them lay within edge of a bin edge, the worst errors over the slots that
+    agree (relative to max(1, |value|), and for local energies also plainly
+    relative to |E_L| and relative to the magnitude of their terms), and for
+    a parting the implicated walkers and teeth and whether every one of them
+    is excused by a near-edge decision of its own."""
+    mw, mc, mt = margins
+    W = len(ow["parent"])
+    bad_walk = (gw["jumps_pre"] != ow["jumps_pre"]) | (
+        np.abs(gw["logw_pre"] - ow["logw_pre"]) > rtol * np.maximum(1.0, np.abs(ow["logw_pre"])))
+    same_parent = gw["parent"] == ow["parent"]
+    el_sc = el_scale(system, ow["x"], ow["EL"])
+    x_err = np.max(np.abs(gw["x"] - ow["x"]) / np.maximum(1.0, np.abs(ow["x"])), axis=(1, 2))
+    el_err_sc = np.abs(gw["EL"] - ow["EL"]) / el_sc
+    bad_state = (x_err > rtol) | (el_err_sc > rtol)
+    walkers = set(np.flatnonzero(bad_walk).tolist())
+    walkers |= {int(ow["parent"][t]) for t in np.flatnonzero(bad_state & same_parent)}
+    teeth = np.flatnonzero(~same_parent).tolist()
+    near_w = mw < edge
+    near_t = mt < edge
+    info = {
+        "ok": not walkers and not teeth,
+        "decisions": int(np.sum(ow["jumps_pre"]) + 2 * W),
+        "near_edge": int(np.sum(near_w) + np.sum(near_t)),
+        "min_margin_walker": float(np.min(mw)), "min_margin_comb": float(mc),
+    }
+    good = ~bad_state & same_parent
+    gw_ok = ~bad_walk
+    if np.any(good):
+        el = ow["EL"][good]
+        info["worst_x_rel"] = float(np.max(x_err[good]))
+        info["worst_EL_rel"] = float(np.max(np.abs(gw["EL"][good] - el) / np.abs(el)))
+        info["worst_EL_term_scaled"] = float(np.max(el_err_sc[good]))
+    if np.any(gw_ok):
+        lw = ow["logw_pre"][gw_ok]
+        info["worst_logw_rel"] = float(np.max(np.abs(gw["logw_pre"][gw_ok] - lw) / np.maximum(1.0, np.abs(lw))))
+    if not info["ok"]:
+        info["parted_walkers"] = sorted(walkers)
+        info["parted_teeth"] = teeth
+        # a walker parts only on its own near-edge decision; a tooth on its
+        # own, or because a parted walker changed the weights before it
+        info["excused"] = bool(all(near_w[s] for s in walkers) and (walkers or all(near_t[t] for t in teeth)))
+    return info
+
+
+def merge_worst(acc, info):
+    for k, v in info.items():
+        if k.startswith("worst_"):
+            acc[k] = max(acc.get(k, 0.0), v)
+        elif k in ("decisions", "near_edge"):
+            acc[k] = acc.get(k, 0) + v
+        elif k.startswith("min_margin"):
+            acc[k] = min(acc.get(k, np.inf), v)
+
+
+def rate_scale(lat, w, scale):
+    """Scale of every rate T_c = w_c/(2 h_c^2) max(rho_c, 0): its weight and
+    spacing factor times the floating-point scale of its ratio (candidate
+    order: electron, grid, axis, sign)."""
+    P = len(w)
+    g = (np.arange(P) // 6) % lat.G
+    h = np.where(g == 0, lat.a, lat.ap)
+    return np.asarray(w) / (2.0 * h * h) * scale

@@ -108,3 +108,37 @@ def test_workspace_bytes_grow_with_walkers(pkg):
     g = pkg.LrdmcSystem(S.neon())
     b1, b2 = g.workspace_bytes(100, 10), g.workspace_bytes(1000, 10)
     assert b2 > 9 * b1 / 2 and b1 % 256 == 0
+
+
+def test_evaluate_argument_checks_before_the_library(pkg):
+    """evaluate / evaluate_static refuse tensors the kernels would overrun
+    or misread - wrong shape, dtype or device, a short output - with a
+    ValueError, before any pointer reaches the library (checked here with
+    CPU tensors, which both paths reject)."""
+    torch = pytest.importorskip("torch")
+    s = S.neon()
+    g = pkg.LrdmcSystem(s)
+    sp = pkg.Spacing(pkg.THIS_WORK)
+    x = torch.zeros((4, s.N, 3), dtype=torch.float64)
+    R = torch.zeros((4, 9), dtype=torch.float64)
+    for fn in (g.evaluate, g.evaluate_static):
+        with pytest.raises(ValueError):
+            fn(x, R, 0.2, sp)  # not on a CUDA device
+        with pytest.raises(ValueError):
+            fn(torch.zeros((4, s.N + 1, 3), dtype=torch.float64), R, 0.2, sp)
+        with pytest.raises(ValueError):
+            fn(x, torch.zeros((3, 9), dtype=torch.float64), 0.2, sp)
+        with pytest.raises(ValueError):
+            fn(x.float(), R, 0.2, sp)
+    P = 12 * s.N
+    short = (torch.zeros((4, P - 1), dtype=torch.float64), torch.zeros((4, P), dtype=torch.float64),
+             torch.zeros(4, dtype=torch.float64), torch.zeros(4, dtype=torch.float64))
+    with pytest.raises(ValueError):
+        g._eval_args(x, R, P, short)
+
+
+def test_static_eval_limit_matches_header(pkg):
+    """The binding's STATIC_EVAL_MAX is the header's LRDMC_STATIC_EVAL_MAX."""
+    text = open(os.path.join(ROOT, "include", "lrdmc.h")).read()
+    m = re.search(r"#define\s+LRDMC_STATIC_EVAL_MAX\s+(\d+)", text)
+    assert m and int(m.group(1)) == pkg.STATIC_EVAL_MAX

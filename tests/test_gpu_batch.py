@@ -156,3 +156,64 @@ def test_full_size_batch_equals_single_steps(pkg):
     batch.sync()
     for g1, g2 in zip(solo, batched):
         assert _equal(_state(g1), _state(g2))
+
+
+def test_batch_matches_oracle(pkg, oracle_mod):
+    """A batch of four systems of uneven size (He, Ne, H2O, Ar: N = 2 to 18;
+    single grid, this work's and the previous double grid), stepped one
+    interval per CUDA graph, against each system's own oracle population
+    walker by walker after every interval: jump counts, log-weights, comb
+    parents, positions and local energies at the parity tolerance, then the
+    traces. A parting is accepted only on a near-edge decision of the walker
+    or slot that parted."""
+    import os
+
+    import _parity_util as U
+
+    cases = [("He", 48, 0.2, "single", 0.05, -2.9), ("Ne", 24, 0.2, "this_work", 0.02, -128.9),
+             ("H2O", 16, 0.1, "previous", 0.01, -76.0), ("Ar", 8, 1 / 63, "this_work", 2e-4, -527.0)]
+    okind = {"single": oracle_mod.SINGLE, "this_work": oracle_mod.THIS_WORK, "previous": oracle_mod.PREVIOUS}
+    threads = max(1, min(16, os.cpu_count() or 1))
+    gs, pops, lats, systems = [], [], [], []
+    for q, (name, W, a, kind, tau, et) in enumerate(cases):
+        system = S.make_system(name)
+        x0 = S.initial_positions(system, W, 900 + q)
+        g = pkg.LrdmcSystem(system)
+        g.init_walkers(torch.tensor(x0, device="cuda"), seed=950 + q, tau=tau, e_trial=et, recompute_every=3,
+                       trace_capacity=8)
+        o = oracle_mod.OracleSystem(system)
+        pops.append(oracle_mod.OraclePopulation(o, x0, seed=950 + q, tau=tau, e_trial=et, recompute_every=3))
+        lats.append(oracle_mod.lattice_for(system, a, okind[kind]))
+        gs.append(g)
+        systems.append((system, o))
+    batch = pkg.LrdmcBatch(gs, [c[2] for c in cases], [_spacing(pkg, c[3]) for c in cases])
+    entries = [{"test": f"batch vs oracle: {c[0]} {c[3]} (W={c[1]})", "kind": "projection (batched)",
+                "walkers": c[1], "intervals_requested": 4, "intervals_compared": 0, "parted": False} for c in cases]
+    live = [True] * len(cases)
+    try:
+        for k in range(4):
+            batch.step(1)
+            batch.sync()
+            for q in range(len(cases)):
+                pops[q].step(lats[q], 1, threads)
+                if not live[q]:
+                    continue
+                info = U.compare_interval(systems[q][0], gs[q].walkers(), pops[q].walkers(lats[q].G),
+                                          pops[q].margins(teeth=True))
+                U.merge_worst(entries[q], info)
+                if not info["ok"]:
+                    entries[q].update(parted=True, parted_at=k, excused=info["excused"])
+                    assert info["excused"], (cases[q][0], k, info["parted_walkers"][:8], info["parted_teeth"][:8])
+                    live[q] = False
+                    continue
+                entries[q]["intervals_compared"] = k + 1
+        for q in range(len(cases)):
+            if live[q]:
+                ge = gs[q].energy_trace()[0]
+                oe = pops[q].trace()[0]
+                assert np.all(np.abs(ge - oe) <= U.RTOL * np.abs(oe)), cases[q][0]
+                assert gs[q].moves() == pops[q].moves
+        assert sum(live) >= 3
+    finally:
+        for e in entries:
+            U.record(e)

@@ -6,10 +6,15 @@ their determinant dot product, at least max(1, |ratio|); see
 _parity_util.ratio_scale; the local energies of projected walkers, which
 can sit close to a heavy nucleus: relative to the magnitude of their
 kinetic and Coulomb terms, see _parity_util.el_scale); positions,
-log-weights and trace energies within 1e-10; jump counts, comb parents and
-move choices identical, except after a decision the oracle reports within
-1e-9 of a bin edge (then the trajectories may part and the comparison
-stops, counting the event).
+log-weights and trace energies within 1e-10; rates element by element
+within 1e-10 of their own scale (weight and spacing factor times the scale
+of their ratio); jump counts, comb parents and move choices identical,
+except where the oracle reports that the decision of the walker or comb
+slot that parted lay within 1e-10 of a bin edge (then the trajectories may
+part and the comparison stops). Every run's intervals compared, decisions,
+near-edge decisions, partings and worst errors - plainly relative to
+|value| as well as against the term scale - go to the parity report
+(conftest.py writes it at the end of the session).
 """
 import os
 
@@ -17,13 +22,11 @@ import numpy as np
 import pytest
 
 import lrdmc_synth as S
-from _parity_util import el_scale, ratio_scale
+import _parity_util as U
+from _parity_util import EDGE, RTOL, el_scale, rate_scale, ratio_scale
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
-
-RTOL = 1e-10
-EDGE = 1e-9
 THREADS = max(1, min(16, os.cpu_count() or 1))
 
 
@@ -62,6 +65,35 @@ EVAL_CASES = [
 PRECISIONS = ["fp64", "df64"]
 
 
+class _EvalWorst:
+    """Worst errors of an evaluation case: plainly relative to |value| (the
+    the benchmark spec's 1e-10, shown as measured) and against the floating-point
+    scale the assertions use; with the count of elements whose plain
+    relative error exceeds 1e-10."""
+
+    def __init__(self):
+        self.d = {"worst_ratio_rel": 0.0, "worst_ratio_scaled": 0.0, "worst_T_rel": 0.0, "worst_T_scaled": 0.0,
+                  "worst_b_rel": 0.0, "worst_EL_rel": 0.0, "ratios_above_1e-10_rel": 0, "ratios": 0}
+
+    def add(self, r, rr, rs, t, tr, ts, b, br, e, er):
+        d = self.d
+        rel = np.abs(r - rr) / np.maximum(np.abs(rr), 1e-300)
+        nz = rr != 0
+        d["worst_ratio_rel"] = max(d["worst_ratio_rel"], float(np.max(rel[nz])) if np.any(nz) else 0.0)
+        d["ratios_above_1e-10_rel"] += int(np.sum(rel[nz] > 1e-10))
+        d["ratios"] += int(np.sum(nz))
+        d["worst_ratio_scaled"] = max(d["worst_ratio_scaled"], float(np.max(np.abs(r - rr) / rs)))
+        pos = tr > 0
+        if np.any(pos):
+            d["worst_T_rel"] = max(d["worst_T_rel"], float(np.max(np.abs(t[pos] - tr[pos]) / tr[pos])))
+        d["worst_T_scaled"] = max(d["worst_T_scaled"], float(np.max(np.abs(t - tr) / ts)))
+        d["worst_b_rel"] = max(d["worst_b_rel"], abs(b - br) / br)
+        d["worst_EL_rel"] = max(d["worst_EL_rel"], abs(e - er) / abs(er))
+
+    def entry(self, label, n):
+        return {"test": label, "kind": "evaluation", "configurations": n, **self.d}
+
+
 def _prec(pkg, name):
     return pkg.PRECISION_FP64 if name == "fp64" else pkg.PRECISION_DF64
 
@@ -83,14 +115,18 @@ def test_evaluate_matches_oracle(pkg, oracle_mod, name, kind, a, prec):
     sp, lat = spacing_pair(pkg, oracle_mod, system, a, kind)
     ratio, T, b, el = g.evaluate(torch.tensor(x, device="cuda"), torch.tensor(R, device="cuda"), a, sp)
     ratio, T, b, el = (t.cpu().numpy() for t in (ratio, T, b, el))
+    worst = _EvalWorst()
     for c in range(n):
         ref = o.lattice_eval(lat, x[c], R[c])
         scale = ratio_scale(o, system, lat, x[c], R[c], ref["ratio"])
         err = np.abs(ratio[c] - ref["ratio"])
         assert np.all(err <= RTOL * scale), (c, np.max(err / scale))
-        assert np.all(np.abs(T[c] - ref["T"]) <= RTOL * np.max(ref["T"] * scale))
+        tsc = rate_scale(lat, ref["w"], scale)
+        assert np.all(np.abs(T[c] - ref["T"]) <= RTOL * tsc), (c, float(np.max(np.abs(T[c] - ref["T"]) / tsc)))
         assert abs(b[c] - ref["b"]) <= RTOL * ref["b"]
         assert abs(el[c] - ref["EL"]) <= RTOL * max(1.0, abs(ref["EL"]))
+        worst.add(ratio[c], ref["ratio"], scale, T[c], ref["T"], tsc, b[c], ref["b"], el[c], ref["EL"])
+    U.record(worst.entry(f"evaluate {name} {kind} a={a:.6g} {prec}", n))
 
 
 @pytest.mark.parametrize("prec", PRECISIONS)
@@ -108,15 +144,27 @@ def test_evaluate_full_size_sampled(pkg, oracle_mod, prec):
     ratio, T, b, el = g.evaluate(torch.tensor(x, device="cuda"), torch.tensor(R, device="cuda"), 0.2, sp)
     ratio, b, el = ratio.cpu().numpy(), b.cpu().numpy(), el.cpu().numpy()
     assert np.all(np.isfinite(el)) and np.all(b > 0)
+    T = T.cpu().numpy()
+    worst = _EvalWorst()
     for c in np.random.default_rng(3).choice(n, 64, replace=False):
         ref = o.lattice_eval(lat, x[c], R[c])
         scale = ratio_scale(o, system, lat, x[c], R[c], ref["ratio"])
         assert np.all(np.abs(ratio[c] - ref["ratio"]) <= RTOL * scale)
+        tsc = rate_scale(lat, ref["w"], scale)
+        assert np.all(np.abs(T[c] - ref["T"]) <= RTOL * tsc)
         assert abs(el[c] - ref["EL"]) <= RTOL * abs(ref["EL"])
+        worst.add(ratio[c], ref["ratio"], scale, T[c], ref["T"], tsc, b[c], ref["b"], el[c], ref["EL"])
+    U.record(worst.entry(f"evaluate Ne full size (4096, 64 sampled) {prec}", 64))
 
 
 def _compare_runs(pkg, oracle_mod, system, kind, a, W, n_steps, tau, seed, e_trial, rc_every=3,
-                  prec="df64"):
+                  prec="df64", label=None):
+    """Project the same population on the GPU and in the oracle, interval by
+    interval, comparing every walker after each one (U.compare_interval).
+    A parting is accepted only when every walker or comb slot that parted
+    had a decision within EDGE of a bin edge in the oracle; the comparison
+    then stops (the trajectories are no longer the same). Returns
+    (intervals compared, parted) and records the run in the parity report."""
     g = pkg.LrdmcSystem(system).set_precision(_prec(pkg, prec))
     o = oracle_mod.OracleSystem(system)
     x0 = S.initial_positions(system, W, seed)
@@ -124,27 +172,34 @@ def _compare_runs(pkg, oracle_mod, system, kind, a, W, n_steps, tau, seed, e_tri
     g.init_walkers(torch.tensor(x0, device="cuda"), seed=seed, tau=tau, e_trial=e_trial,
                    recompute_every=rc_every, trace_capacity=n_steps)
     pop = oracle_mod.OraclePopulation(o, x0, seed=seed, tau=tau, e_trial=e_trial, recompute_every=rc_every)
+    entry = {"test": label or f"projection {kind} a={a:.6g} W={W} {prec}", "kind": "projection",
+             "walkers": W, "intervals_requested": n_steps, "intervals_compared": 0, "parted": False}
     compared = 0
-    for k in range(n_steps):
-        g.step(1, a, sp)
-        pop.step(lat, 1, THREADS)
-        gw, ow = g.walkers(), pop.walkers(lat.G)
-        ok = (np.array_equal(gw["jumps_pre"], ow["jumps_pre"]) and np.array_equal(gw["parent"], ow["parent"])
-              and np.all(np.abs(gw["x"] - ow["x"]) <= RTOL * np.maximum(1.0, np.abs(ow["x"])))
-              and np.all(np.abs(gw["EL"] - ow["EL"]) <= RTOL * el_scale(system, ow["x"], ow["EL"]))
-              and np.all(np.abs(gw["logw_pre"] - ow["logw_pre"]) <= RTOL * np.maximum(1.0, np.abs(ow["logw_pre"]))))
-        if not ok:
-            mw, mc = pop.margins()
-            assert min(np.min(mw), mc) < EDGE, f"divergence at interval {k} without a near-edge decision"
-            return compared, True
-        compared += 1
-    ge, gwb, gj = g.energy_trace()
-    oe, owb, oj = pop.trace()
-    assert np.all(np.abs(ge - oe) <= RTOL * np.abs(oe))
-    assert np.all(np.abs(gwb - owb) <= RTOL * owb)
-    assert np.array_equal(gj, oj)
-    assert g.moves() == pop.moves
-    return compared, False
+    try:
+        for k in range(n_steps):
+            g.step(1, a, sp)
+            pop.step(lat, 1, THREADS)
+            gw, ow = g.walkers(), pop.walkers(lat.G)
+            info = U.compare_interval(system, gw, ow, pop.margins(teeth=True))
+            U.merge_worst(entry, info)
+            if not info["ok"]:
+                entry.update(parted=True, parted_at=k, parted_walkers=info["parted_walkers"][:16],
+                             parted_teeth=info["parted_teeth"][:16], excused=info["excused"])
+                assert info["excused"], (f"interval {k}: walkers {info['parted_walkers'][:8]} / teeth "
+                                         f"{info['parted_teeth'][:8]} parted without a near-edge decision")
+                return compared, True
+            compared += 1
+            entry["intervals_compared"] = compared
+        ge, gwb, gj = g.energy_trace()
+        oe, owb, oj = pop.trace()
+        entry["worst_trace_e_rel"] = float(np.max(np.abs(ge - oe) / np.abs(oe)))
+        assert np.all(np.abs(ge - oe) <= RTOL * np.abs(oe))
+        assert np.all(np.abs(gwb - owb) <= RTOL * owb)
+        assert np.array_equal(gj, oj)
+        assert g.moves() == pop.moves
+        return compared, False
+    finally:
+        U.record(entry)
 
 
 @pytest.mark.parametrize("prec", PRECISIONS)
@@ -163,7 +218,7 @@ def test_projection_matches_oracle(pkg, oracle_mod, name, kind, a, W, steps, tau
     """Whole intervals: waiting times, heat-bath choices, Sherman-Morrison
     updates, inverse recomputation, weights and comb reconfiguration."""
     compared, parted = _compare_runs(pkg, oracle_mod, S.make_system(name), kind, a, W, steps, tau, 11, et,
-                                     prec=prec)
+                                     prec=prec, label=f"projection {name} {kind} a={a:.6g} W={W} {prec}")
     assert compared >= (1 if parted else steps)
 
 
@@ -172,7 +227,7 @@ def test_projection_full_size(pkg, oracle_mod, prec):
     """The Ne workload at full size (4096 walkers, a = 0.2, the paper's
     double grid, tau = 0.025) for two intervals, walker by walker."""
     compared, parted = _compare_runs(pkg, oracle_mod, S.neon(), "this_work", 0.2, 4096, 2, 0.025, 5, -128.9,
-                                     prec=prec)
+                                     prec=prec, label=f"projection Ne full size (4096) {prec}")
     assert compared >= 1
 
 
@@ -278,6 +333,9 @@ def test_fp32_evaluation_error(pkg, oracle_mod, name, kind, a):
         ref = o.lattice_eval(lat, x[c], R[c])
         worst_r = max(worst_r, float(np.max(np.abs(ratio[c] - ref["ratio"]) / np.maximum(1.0, np.abs(ref["ratio"])))))
         worst_e = max(worst_e, abs(el[c] - ref["EL"]) / abs(ref["EL"]))
+    U.record({"test": f"evaluate {name} {kind} fp32 mode", "kind": "evaluation (mixed precision)",
+              "configurations": n, "tolerance_rel": FP32_RTOL, "worst_ratio_rel_max1": worst_r,
+              "worst_EL_rel": worst_e})
     assert worst_r < FP32_RTOL and worst_e < FP32_RTOL, (worst_r, worst_e)
 
 
@@ -317,6 +375,7 @@ def test_large_system_without_caches(pkg, oracle_mod, prec):
     sp, lat = spacing_pair(pkg, oracle_mod, system, 0.3, "this_work")
     ratio, T, b, el = (t.cpu().numpy() for t in g.evaluate(torch.tensor(x, device="cuda"),
                                                            torch.tensor(R, device="cuda"), 0.3, sp))
+    rec = _EvalWorst()
     for c in range(n):
         ref = o.lattice_eval(lat, x[c], R[c])
         scale = ratio_scale(o, system, lat, x[c], R[c], ref["ratio"])
@@ -324,9 +383,14 @@ def test_large_system_without_caches(pkg, oracle_mod, prec):
         worst = int(np.argmax(err))
         assert err.max() <= 1.0, (c, worst, float(err.max()), float(ratio[c].flat[worst]),
                                   float(ref["ratio"].flat[worst]))
+        tsc = rate_scale(lat, ref["w"], scale)
+        assert np.all(np.abs(T[c] - ref["T"]) <= RTOL * tsc)
         assert abs(b[c] - ref["b"]) <= RTOL * ref["b"]
         assert abs(el[c] - ref["EL"]) <= RTOL * max(1.0, abs(ref["EL"]))
-    compared, parted = _compare_runs(pkg, oracle_mod, system, "this_work", 0.3, 6, 2, 0.002, 13, 40.0, prec=prec)
+        rec.add(ratio[c], ref["ratio"], scale, T[c], ref["T"], tsc, b[c], ref["b"], el[c], ref["EL"])
+    U.record(rec.entry(f"evaluate 48-electron cluster {prec}", n))
+    compared, parted = _compare_runs(pkg, oracle_mod, system, "this_work", 0.3, 6, 2, 0.002, 13, 40.0, prec=prec,
+                                     label=f"projection 48-electron cluster {prec}")
     assert compared == 2 or parted
 
 
@@ -373,12 +437,18 @@ def test_heavy_atoms_evaluate_full_size_sampled(pkg, oracle_mod, name, a, tau, e
     ratio, T, b, el = g.evaluate(torch.tensor(x, device="cuda"), torch.tensor(R, device="cuda"), a, sp)
     ratio, b, el = ratio.cpu().numpy(), b.cpu().numpy(), el.cpu().numpy()
     assert np.all(np.isfinite(el)) and np.all(b > 0) and np.all(np.isfinite(b))
+    T = T.cpu().numpy()
+    worst = _EvalWorst()
     for c in np.random.default_rng(4).choice(n, 16, replace=False):
         ref = o.lattice_eval(lat, x[c], R[c])
         scale = ratio_scale(o, system, lat, x[c], R[c], ref["ratio"])
         assert np.all(np.abs(ratio[c] - ref["ratio"]) <= RTOL * scale), c
+        tsc = rate_scale(lat, ref["w"], scale)
+        assert np.all(np.abs(T[c] - ref["T"]) <= RTOL * tsc), c
         assert abs(b[c] - ref["b"]) <= RTOL * ref["b"], c
         assert abs(el[c] - ref["EL"]) <= RTOL * abs(ref["EL"]), c
+        worst.add(ratio[c], ref["ratio"], scale, T[c], ref["T"], tsc, b[c], ref["b"], el[c], ref["EL"])
+    U.record(worst.entry(f"evaluate {name} full size (16384, 16 sampled) df64", 16))
 
 
 @pytest.mark.parametrize("name,a,tau,et", HEAVY_FULL)
@@ -386,7 +456,8 @@ def test_heavy_atoms_projection_full_size(pkg, oracle_mod, name, a, tau, et):
     """One interval of the Ar and Kr workloads at full size (16384 walkers,
     a = 1/(3.5 Z), this work's double grid, tau for about 9 jumps per
     walker), walker by walker against the oracle's population."""
-    compared, parted = _compare_runs(pkg, oracle_mod, S.make_system(name), "this_work", a, 16384, 1, tau, 17, et)
+    compared, parted = _compare_runs(pkg, oracle_mod, S.make_system(name), "this_work", a, 16384, 1, tau, 17, et,
+                                     label=f"projection {name} full size (16384) df64")
     assert compared == 1 or parted
 
 
@@ -395,10 +466,11 @@ def test_helium_workload_full_length(pkg, oracle_mod, kind):
     """The He workload at its full length: 256 walkers, a = 0.2, 2000
     intervals on the single grid and on this work's double grid, walker by
     walker against the oracle after every interval, then the whole energy
-    trace. Over about 5 million decisions a parting is accepted only after a
-    decision the oracle reports within 1e-9 of a bin edge; at least 100
-    intervals must agree before it."""
-    compared, parted = _compare_runs(pkg, oracle_mod, S.helium(), kind, 0.2, 256, 2000, 0.02, 23, -2.9)
+    trace. Over about 5 million decisions a parting is accepted only where the
+    walker or comb slot that parted had a decision the oracle reports within
+    1e-10 of a bin edge; at least 100 intervals must agree before it."""
+    compared, parted = _compare_runs(pkg, oracle_mod, S.helium(), kind, 0.2, 256, 2000, 0.02, 23, -2.9,
+                                     label=f"projection He workload {kind} (256 walkers, 2000 intervals) df64")
     assert compared == 2000 or (parted and compared >= 100), compared
 
 
@@ -410,5 +482,6 @@ def test_neon_workload_lattices(pkg, oracle_mod, a, kind):
     a^2 (about 10 jumps per walker on the double grid), two intervals walker
     by walker against the oracle."""
     tau = 0.025 * (a / 0.2) ** 2
-    compared, parted = _compare_runs(pkg, oracle_mod, S.neon(), kind, a, 4096, 2, tau, 29, -128.9)
+    compared, parted = _compare_runs(pkg, oracle_mod, S.neon(), kind, a, 4096, 2, tau, 29, -128.9,
+                                     label=f"projection Ne workload {kind} a={a} (4096) df64")
     assert compared == 2 or parted

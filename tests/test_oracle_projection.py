@@ -47,9 +47,13 @@ def test_hydrogen_fixed_node_energy(oracle_mod):
     s.en_b1 = np.array([0.2])
     pop, _ = _run(oracle_mod, s, dict(a=0.2, kind=0), W=256, steps=1200, tau=0.05, e_trial=-0.5, threads=8)
     e, wbar, _ = pop.trace()
-    e, wbar = e[200:], wbar[200:]
-    E = oracle_mod.energy_estimate(e, wbar, 40)
-    err = oracle_mod.reblock_error(e)
+    e = e[200:]
+    # plain mean of the interval energies; its standard error from the
+    # spread of 20 consecutive batch means (batches much longer than the
+    # correlation time of the trace)
+    E = float(np.mean(e))
+    batches = np.array([np.mean(b) for b in np.array_split(e, 20)])
+    err = float(np.std(batches, ddof=1) / np.sqrt(len(batches)))
     assert abs(E + 0.5) < 4 * err + 2e-3
     # the trial function alone: mean local energy at the start is much higher
     o = oracle_mod.OracleSystem(s)
@@ -107,3 +111,28 @@ def test_reconfiguration_resets_and_copies(oracle_mod):
     e, wbar, _ = pop.trace()
     assert abs(wbar[-1] - w.mean()) < 1e-14 * w.mean()
     del before
+
+
+def test_decision_margins_per_walker_and_tooth(oracle_mod):
+    """The margins the GPU parity tests use to excuse a parting: every
+    walker's margin is finite and positive after an interval with jumps, and
+    the comb's per-tooth margins have the comb's overall margin as their
+    minimum; each tooth's margin is the distance of its target from the
+    nearer edge of its parent's bin (checked by recomputing the comb from
+    the logged weights)."""
+    s = S.helium()
+    pop, _ = _run(oracle_mod, s, dict(a=0.2, kind=1), W=64, steps=1, tau=0.05, e_trial=-2.9)
+    mw, mc, mt = pop.margins(teeth=True)
+    assert np.all(np.isfinite(mw)) and np.all(mw > 0)
+    assert mt.min() == mc
+    wt = np.exp(pop.walkers(2)["logw_pre"])
+    parent = pop.walkers(2)["parent"]
+    C = np.cumsum(wt)
+    u = oracle_mod.uniform(int(oracle_mod.philox4x64([2 ** 64 - 1, 0, 0, 2], [3, 0])[0]))
+    for t in range(64):
+        target = (t + u) * C[-1] / 64
+        q = parent[t]
+        lo = C[q - 1] if q > 0 else -np.inf
+        assert lo <= target < C[q] or q == 63
+        edge = min(abs(target - C[q]), abs(target - lo) if q > 0 else np.inf) / C[-1]
+        assert abs(edge - mt[t]) <= 1e-12

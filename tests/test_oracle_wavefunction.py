@@ -1,6 +1,8 @@
 """Pins of the oracle's trial function, local energy, Sherman-Morrison update
 and lattice evaluation against closed forms, exact eigenstates, brute force
 and invariances."""
+import math
+
 import numpy as np
 import pytest
 
@@ -323,3 +325,64 @@ def test_gaussian_atoms_cusp_and_laplacian(oracle_mod, name):
                 fd += np.exp(la - la0)
     fd = (fd - 6 * s.N) / (h * h)
     assert abs(fd - lap) < 1e-4 * max(1.0, abs(lap))
+
+
+def _unit_vectors(n, seed):
+    v = np.random.default_rng(seed).normal(size=(n, 3))
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+@pytest.mark.parametrize("name,a", [("He", 0.2), ("Ne", 0.2), ("Ne", 0.05), ("Kr", 1 / 126)])
+def test_gaussian_p_characteristic_values(oracle_mod, name, a):
+    """Eq. 3 (this work): p(r) = exp(-|r - R_c|^2 / (2 r_c^2)) with r_c a
+    length from S-13. Its defining values, along any direction: 1 at the
+    nucleus, exp(-1/2) at one r_c, exp(-2) at two, 1/2 at r_c sqrt(2 ln 2).
+    A dropped square, a missing factor 2 or r_c read as an inverse length
+    moves every one of them."""
+    s, o = _osys(oracle_mod, name)
+    lat = oracle_mod.lattice_for(s, a, oracle_mod.THIS_WORK)
+    assert lat.pkind == 0 and lat.G == 2
+    assert abs(lat.rc - oracle_mod.rc_this_work(a, float(s.Z[0]))) < 1e-15
+    Rc = np.asarray(s.nuc_xyz, float).reshape(-1, 3)[0]
+    assert o.p(lat, Rc) == 1.0
+    for u in _unit_vectors(8, 5):
+        assert abs(o.p(lat, Rc + lat.rc * u) - math.exp(-0.5)) < 1e-14
+        assert abs(o.p(lat, Rc + 2.0 * lat.rc * u) - math.exp(-2.0)) < 1e-14
+        assert abs(o.p(lat, Rc + lat.rc * math.sqrt(2.0 * math.log(2.0)) * u) - 0.5) < 1e-14
+    # the a' grid's weight 1 - p vanishes at the nucleus and tends to 1 far out
+    assert o.p(lat, Rc + 20.0 * lat.rc * np.array([0.0, 0.0, 1.0])) < 1e-80
+
+
+@pytest.mark.parametrize("name", ["He", "Ne", "Ar", "Kr"])
+def test_pade_p_characteristic_values(oracle_mod, name):
+    """Eq. 2 (the previous scheme): p(r) = 1/(1 + r_c^2 |r - R_c|^2) with r_c
+    an inverse length, r_c = Z/2 (the choice that Eq. 4 pairs with
+    a'/a = sqrt(Z^2/4 + 1)). Its defining values: 1 at the nucleus, 1/2 at
+    distance 1/r_c = 2/Z, and the far tail p (r_c d)^2 -> 1. r_c in place
+    of r_c^2, or 2 r_c^2, fails the half-value point for every Z != 2."""
+    s, o = _osys(oracle_mod, name)
+    Z = float(s.Z[0])
+    lat = oracle_mod.lattice_for(s, 0.1, oracle_mod.PREVIOUS)
+    assert lat.pkind == 1 and lat.G == 2
+    assert lat.rc == Z / 2.0
+    assert abs(lat.ap / lat.a - math.sqrt(Z * Z / 4.0 + 1.0)) < 1e-14
+    Rc = np.asarray(s.nuc_xyz, float).reshape(-1, 3)[0]
+    assert o.p(lat, Rc) == 1.0
+    for u in _unit_vectors(8, 6):
+        assert abs(o.p(lat, Rc + (2.0 / Z) * u) - 0.5) < 1e-14
+        assert abs(o.p(lat, Rc + (6.0 / Z) * u) - 0.1) < 1e-14  # 1/(1 + 3^2)
+        d = 1e3 * 2.0 / Z
+        assert abs(o.p(lat, Rc + d * u) * (Z / 2.0 * d) ** 2 - 1.0) < 2e-6
+
+
+def test_pade_p_polyatomic_uses_heaviest_atom(oracle_mod):
+    """For H2O the previous scheme takes r_c = Z_max/2 = 4 from O, and the
+    distance to O, not to the nearer H: p = 1/2 at 1/4 bohr from O, and
+    next to an H p is the Pade value of its distance to O."""
+    s, o = _osys(oracle_mod, "H2O")
+    lat = oracle_mod.lattice_for(s, 0.1, oracle_mod.PREVIOUS)
+    assert lat.rc == 4.0
+    assert abs(o.p(lat, np.array([0.25, 0.0, 0.0])) - 0.5) < 1e-14
+    near_h = S.WATER_H[0] + np.array([0.05, -0.02, 0.01])
+    d2 = float(np.sum(near_h ** 2))
+    assert abs(o.p(lat, near_h) - 1.0 / (1.0 + 16.0 * d2)) < 1e-15
