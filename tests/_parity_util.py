@@ -140,10 +140,16 @@ def merge_worst(acc, info):
 
 
 def rate_scale(lat, w, scale):
-    """Scale of every rate T_c = w_c/(2 h_c^2) max(rho_c, 0): its weight and
-    spacing factor times the floating-point scale of its ratio (candidate
-    order: electron, grid, axis, sign)."""
+    """Scale of every rate T_c = w_c/(2 h_c^2) max(rho_c, 0): the scale of
+    its weight times its spacing factor times the floating-point scale of
+    its ratio (candidate order: electron, grid, axis, sign). On the a grid
+    w = p(mid) is an exponential, accurate relative to itself; on the a'
+    grid w = 1 - p(mid) inherits the absolute rounding of p <= 1, so its
+    scale is max(w, 1 - w) (next to a nucleus p -> 1 and w is a small
+    difference of numbers near 1)."""
     P = len(w)
+    w = np.asarray(w, float)
     g = (np.arange(P) // 6) % lat.G
     h = np.where(g == 0, lat.a, lat.ap)
-    return np.asarray(w) / (2.0 * h * h) * scale
+    w_scale = np.where(g == 0, w, np.maximum(w, 1.0 - w))
+    return w_scale / (2.0 * h * h) * scale
