@@ -63,6 +63,8 @@ def el_scale(system, x, el_ref):
 
 # ------------------------------------------------------------------ projection
 RTOL = 1e-10
+# smallest normal float: the floor of the double-float format's range
+FLT_MIN = 2.0 ** -126
 # A decision whose uniform lies within this distance of a bin edge (relative
 # to the quantity it is compared with: tau for the waiting time, b for the
 # heat bath, the total weight for a comb tooth) may go either way between
@@ -139,17 +141,20 @@ def merge_worst(acc, info):
             acc[k] = min(acc.get(k, np.inf), v)
 
 
-def rate_scale(lat, w, scale):
+def rate_scale(lat, w, scale, w_floor=0.0):
     """Scale of every rate T_c = w_c/(2 h_c^2) max(rho_c, 0): the scale of
     its weight times its spacing factor times the floating-point scale of
     its ratio (candidate order: electron, grid, axis, sign). On the a grid
     w = p(mid) is an exponential, accurate relative to itself; on the a'
     grid w = 1 - p(mid) inherits the absolute rounding of p <= 1, so its
     scale is max(w, 1 - w) (next to a nucleus p -> 1 and w is a small
-    difference of numbers near 1)."""
+    difference of numbers near 1). w_floor is the smallest weight the
+    arithmetic represents: double-floats share float's exponent range, so a
+    weight exp(-x) below 2^-126 is zero there (Eq. 3's Gaussian far from the
+    nucleus), an absolute error of that size."""
     P = len(w)
     w = np.asarray(w, float)
     g = (np.arange(P) // 6) % lat.G
     h = np.where(g == 0, lat.a, lat.ap)
-    w_scale = np.where(g == 0, w, np.maximum(w, 1.0 - w))
+    w_scale = np.maximum(np.where(g == 0, w, np.maximum(w, 1.0 - w)), w_floor)
     return w_scale / (2.0 * h * h) * scale

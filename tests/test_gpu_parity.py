@@ -65,6 +65,10 @@ EVAL_CASES = [
 PRECISIONS = ["fp64", "df64"]
 
 
+def _w_floor(prec):
+    return U.FLT_MIN if prec != "fp64" else 0.0
+
+
 class _EvalWorst:
     """Worst errors of an evaluation case: plainly relative to |value| (the
     the benchmark spec's 1e-10, shown as measured) and against the floating-point
@@ -121,7 +125,7 @@ def test_evaluate_matches_oracle(pkg, oracle_mod, name, kind, a, prec):
         scale = ratio_scale(o, system, lat, x[c], R[c], ref["ratio"])
         err = np.abs(ratio[c] - ref["ratio"])
         assert np.all(err <= RTOL * scale), (c, np.max(err / scale))
-        tsc = rate_scale(lat, ref["w"], scale)
+        tsc = rate_scale(lat, ref["w"], scale, _w_floor(prec))
         assert np.all(np.abs(T[c] - ref["T"]) <= RTOL * tsc), (c, float(np.max(np.abs(T[c] - ref["T"]) / tsc)))
         assert abs(b[c] - ref["b"]) <= RTOL * ref["b"]
         assert abs(el[c] - ref["EL"]) <= RTOL * max(1.0, abs(ref["EL"]))
@@ -150,7 +154,7 @@ def test_evaluate_full_size_sampled(pkg, oracle_mod, prec):
         ref = o.lattice_eval(lat, x[c], R[c])
         scale = ratio_scale(o, system, lat, x[c], R[c], ref["ratio"])
         assert np.all(np.abs(ratio[c] - ref["ratio"]) <= RTOL * scale)
-        tsc = rate_scale(lat, ref["w"], scale)
+        tsc = rate_scale(lat, ref["w"], scale, _w_floor(prec))
         assert np.all(np.abs(T[c] - ref["T"]) <= RTOL * tsc)
         assert abs(el[c] - ref["EL"]) <= RTOL * abs(ref["EL"])
         worst.add(ratio[c], ref["ratio"], scale, T[c], ref["T"], tsc, b[c], ref["b"], el[c], ref["EL"])
@@ -383,7 +387,7 @@ def test_large_system_without_caches(pkg, oracle_mod, prec):
         worst = int(np.argmax(err))
         assert err.max() <= 1.0, (c, worst, float(err.max()), float(ratio[c].flat[worst]),
                                   float(ref["ratio"].flat[worst]))
-        tsc = rate_scale(lat, ref["w"], scale)
+        tsc = rate_scale(lat, ref["w"], scale, _w_floor(prec))
         assert np.all(np.abs(T[c] - ref["T"]) <= RTOL * tsc)
         assert abs(b[c] - ref["b"]) <= RTOL * ref["b"]
         assert abs(el[c] - ref["EL"]) <= RTOL * max(1.0, abs(ref["EL"]))
@@ -443,7 +447,7 @@ def test_heavy_atoms_evaluate_full_size_sampled(pkg, oracle_mod, name, a, tau, e
         ref = o.lattice_eval(lat, x[c], R[c])
         scale = ratio_scale(o, system, lat, x[c], R[c], ref["ratio"])
         assert np.all(np.abs(ratio[c] - ref["ratio"]) <= RTOL * scale), c
-        tsc = rate_scale(lat, ref["w"], scale)
+        tsc = rate_scale(lat, ref["w"], scale, _w_floor("df64"))
         assert np.all(np.abs(T[c] - ref["T"]) <= RTOL * tsc), c
         assert abs(b[c] - ref["b"]) <= RTOL * ref["b"], c
         assert abs(el[c] - ref["EL"]) <= RTOL * abs(ref["EL"]), c
