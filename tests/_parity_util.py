@@ -63,8 +63,12 @@ def el_scale(system, x, el_ref):
 
 # ------------------------------------------------------------------ projection
 RTOL = 1e-10
-# smallest normal float: the floor of the double-float format's range
-FLT_MIN = 2.0 ** -126
+# Below about 2^-100 the double-float format loses its relative precision:
+# its low part (about 2^-24 of the high part) falls into float's subnormal
+# range, and an exponential whose value lies there keeps only an absolute
+# accuracy of float's subnormal spacing. Rates are compared down to this
+# floor of their weight.
+DF_FLOOR = 2.0 ** -100
 # A decision whose uniform lies within this distance of a bin edge (relative
 # to the quantity it is compared with: tau for the waiting time, b for the
 # heat bath, the total weight for a comb tooth) may go either way between
@@ -149,9 +153,10 @@ def rate_scale(lat, w, scale, w_floor=0.0):
     grid w = 1 - p(mid) inherits the absolute rounding of p <= 1, so its
     scale is max(w, 1 - w) (next to a nucleus p -> 1 and w is a small
     difference of numbers near 1). w_floor is the smallest weight the
-    arithmetic represents: double-floats share float's exponent range, so a
-    weight exp(-x) below 2^-126 is zero there (Eq. 3's Gaussian far from the
-    nucleus), an absolute error of that size."""
+    arithmetic resolves to its full relative precision (DF_FLOOR for the
+    double-float and FP32 modes: Eq. 3's Gaussian far from the nucleus
+    reaches float's subnormal range and zero), below which the error is an
+    absolute one of that size."""
     P = len(w)
     w = np.asarray(w, float)
     g = (np.arange(P) // 6) % lat.G

@@ -66,7 +66,7 @@ PRECISIONS = ["fp64", "df64"]
 
 
 def _w_floor(prec):
-    return U.FLT_MIN if prec != "fp64" else 0.0
+    return U.DF_FLOOR if prec != "fp64" else 0.0
 
 
 class _EvalWorst:
