@@ -65,6 +65,18 @@ EVAL_CASES = [
 PRECISIONS = ["fp64", "df64"]
 
 
+def _check_rates(c, T, ref, tsc, scale):
+    """Every rate of configuration c within RTOL of its own scale; on
+    failure, the worst move with its weight, ratio and scales."""
+    err = np.abs(T - ref["T"])
+    bad = err > RTOL * tsc
+    if np.any(bad):
+        j = int(np.argmax(np.where(bad, err / np.maximum(tsc, 1e-300), 0.0)))
+        raise AssertionError(f"config {c} move {j} (grid {(j // 6) % 2}): T {T[j]!r} vs {ref['T'][j]!r}, "
+                             f"w {ref['w'][j]!r}, ratio {ref['ratio'][j]!r}, ratio scale {scale[j]!r}, "
+                             f"rate scale {tsc[j]!r}, {int(np.sum(bad))} moves off")
+
+
 def _w_floor(prec):
     return U.DF_FLOOR if prec != "fp64" else 0.0
 
@@ -90,7 +102,7 @@ class _EvalWorst:
         pos = tr > 0
         if np.any(pos):
             d["worst_T_rel"] = max(d["worst_T_rel"], float(np.max(np.abs(t[pos] - tr[pos]) / tr[pos])))
-        d["worst_T_scaled"] = max(d["worst_T_scaled"], float(np.max(np.abs(t - tr) / ts)))
+        d["worst_T_scaled"] = max(d["worst_T_scaled"], float(np.max(np.abs(t - tr) / np.maximum(ts, 1e-300))))
         d["worst_b_rel"] = max(d["worst_b_rel"], abs(b - br) / br)
         d["worst_EL_rel"] = max(d["worst_EL_rel"], abs(e - er) / abs(er))
 
@@ -126,7 +138,7 @@ def test_evaluate_matches_oracle(pkg, oracle_mod, name, kind, a, prec):
         err = np.abs(ratio[c] - ref["ratio"])
         assert np.all(err <= RTOL * scale), (c, np.max(err / scale))
         tsc = rate_scale(lat, ref["w"], scale, _w_floor(prec))
-        assert np.all(np.abs(T[c] - ref["T"]) <= RTOL * tsc), (c, float(np.max(np.abs(T[c] - ref["T"]) / tsc)))
+        _check_rates(c, T[c], ref, tsc, scale)
         assert abs(b[c] - ref["b"]) <= RTOL * ref["b"]
         assert abs(el[c] - ref["EL"]) <= RTOL * max(1.0, abs(ref["EL"]))
         worst.add(ratio[c], ref["ratio"], scale, T[c], ref["T"], tsc, b[c], ref["b"], el[c], ref["EL"])
@@ -155,7 +167,7 @@ def test_evaluate_full_size_sampled(pkg, oracle_mod, prec):
         scale = ratio_scale(o, system, lat, x[c], R[c], ref["ratio"])
         assert np.all(np.abs(ratio[c] - ref["ratio"]) <= RTOL * scale)
         tsc = rate_scale(lat, ref["w"], scale, _w_floor(prec))
-        assert np.all(np.abs(T[c] - ref["T"]) <= RTOL * tsc)
+        _check_rates(c, T[c], ref, tsc, scale)
         assert abs(el[c] - ref["EL"]) <= RTOL * abs(ref["EL"])
         worst.add(ratio[c], ref["ratio"], scale, T[c], ref["T"], tsc, b[c], ref["b"], el[c], ref["EL"])
     U.record(worst.entry(f"evaluate Ne full size (4096, 64 sampled) {prec}", 64))
@@ -388,7 +400,7 @@ def test_large_system_without_caches(pkg, oracle_mod, prec):
         assert err.max() <= 1.0, (c, worst, float(err.max()), float(ratio[c].flat[worst]),
                                   float(ref["ratio"].flat[worst]))
         tsc = rate_scale(lat, ref["w"], scale, _w_floor(prec))
-        assert np.all(np.abs(T[c] - ref["T"]) <= RTOL * tsc)
+        _check_rates(c, T[c], ref, tsc, scale)
         assert abs(b[c] - ref["b"]) <= RTOL * ref["b"]
         assert abs(el[c] - ref["EL"]) <= RTOL * max(1.0, abs(ref["EL"]))
         rec.add(ratio[c], ref["ratio"], scale, T[c], ref["T"], tsc, b[c], ref["b"], el[c], ref["EL"])
@@ -448,7 +460,7 @@ def test_heavy_atoms_evaluate_full_size_sampled(pkg, oracle_mod, name, a, tau, e
         scale = ratio_scale(o, system, lat, x[c], R[c], ref["ratio"])
         assert np.all(np.abs(ratio[c] - ref["ratio"]) <= RTOL * scale), c
         tsc = rate_scale(lat, ref["w"], scale, _w_floor("df64"))
-        assert np.all(np.abs(T[c] - ref["T"]) <= RTOL * tsc), c
+        _check_rates(c, T[c], ref, tsc, scale)
         assert abs(b[c] - ref["b"]) <= RTOL * ref["b"], c
         assert abs(el[c] - ref["EL"]) <= RTOL * abs(ref["EL"]), c
         worst.add(ratio[c], ref["ratio"], scale, T[c], ref["T"], tsc, b[c], ref["b"], el[c], ref["EL"])
