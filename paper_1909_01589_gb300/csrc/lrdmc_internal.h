@@ -25,6 +25,7 @@ constexpr int kMaxItersPerInterval = 1 << 20;
 constexpr int kErrSingular = 1;
 constexpr int kErrNonFinite = 2;
 constexpr int kErrIters = 4;
+constexpr int kErrTimeout = 8;  // a bounded wait of the interval kernel's tail helpers ran out
 
 // Philox counter tags.
 constexpr uint64_t kTagTimeHB = 0;
@@ -121,8 +122,10 @@ struct Layout {
 // Shared-memory layout of a system; caches = false leaves out the
 // evaluation caches (for systems that would not fit otherwise).
 Layout make_layout(const SysDev& S, bool caches);
-// Largest dynamic shared memory of one block on sm_100-class GPUs (227 KB).
-constexpr int kMaxSmemBlock = 232448;
+// Largest dynamic shared memory of one block on sm_100-class GPUs (227 KB),
+// less the interval kernel's static shared memory (the tail helpers' slots,
+// 256 bytes reserved).
+constexpr int kMaxSmemBlock = 232448 - 256;
 
 // Populations up to this many walkers keep the comb's running sums in the
 // reconfiguration kernel's shared memory (8 bytes each).
@@ -152,6 +155,9 @@ struct PopDev {
   int trace_cap;
   uint64_t seed;
   double tau, e_trial;
+  // 1: warps that run out of walkers help the warps of their block that
+  // still run one (double-float and FP32 evaluation); 0: every warp alone
+  int helpers;
 };
 
 void fill_df_constants(SysDev& S);

@@ -1371,74 +1371,151 @@ __device__ __forceinline__ NT el_local(const ElParts<NT>& o)
   return A::add(A::mul_f(lap, -0.5f), o.V);
 }
 
-template <class NT, bool NJ, bool NC>
-__device__ void warp_eval_m(const SysDev& S, const double* sC, const LatDev& L, const WarpMem& wm, int lane,
-                            double* ratio_out, double& b, df& bdf, double& el)
+// ----------------------------------------------------------------------------
+// Tail helpers. Walkers make Poisson-distributed numbers of jumps, so at the
+// end of an interval warps run out of walkers while others still work on
+// their last one. A warp whose fetch finds the queue empty attaches to a
+// warp of its own block that is still running a walker and takes chunks of
+// 32 of that walker's lattice moves in every following evaluation. The
+// owner publishes each evaluation (projected columns, positions, rotation
+// and caches ready), then the Jastrow sums (after its local energy), takes
+// chunks itself, and waits for its helpers before the heat-bath scan. Every
+// wait is bounded (kTeamSpin polls with a short sleep); one that runs out
+// sets kErrTimeout in the error word and gives up, so a fault in this
+// protocol is reported as LRDMC_ERR_TIMEOUT, never a hang.
+// ----------------------------------------------------------------------------
+struct TeamSlot {
+  int attach;  // bit 31: closed to helpers; bits 0-30: helpers attached
+  int pub;     // published evaluation (generation << 4 | participants), or kTeamRelease
+  int sready;  // generation whose Jastrow sums Sd are ready
+  int next;    // next candidate chunk of the current generation
+  int done;    // helpers finished with the current generation
+  int gen;     // owner's generation counter
+  int nh;      // owner: helpers taking part in the current evaluation
+  int pad;
+  int* err;    // the population's error word (a wait that runs out sets kErrTimeout)
+};
+// One slot per warp of an interval-kernel block (only the kernels that run
+// the tail helpers touch them).
+__shared__ TeamSlot g_team[kWarpsPerBlock];
+constexpr int kTeamClosed = (int)0x80000000;
+constexpr int kTeamRelease = -1;
+constexpr int kTeamSpin = 1 << 22;
+
+__device__ __forceinline__ int ld_vol(const int* p) { return *(const volatile int*)p; }
+
+// Owner, every evaluation: records in t->nh the number of helpers taking
+// part (0: alone); a helper that attaches later joins at the next
+// evaluation. A closed slot (helpers off, or no walker) reads as 0.
+__device__ __forceinline__ void team_publish(TeamSlot* t, int lane)
 {
-  typedef Ar<NT> A;
-  const int N = S.N, nao = S.n_ao, nu = S.n_up;
-  const BlockMem bm = block_mem(S, const_cast<double*>(sC));
-  // projected inverse columns (FP64, or FP32 in the mixed mode), then
-  // converted with the positions
-  for (int idx = lane; idx < N * nao; idx += 32) {
-    int i = idx / nao, mu = idx % nao;
-    int spin = i < nu ? 0 : 1, l = i < nu ? i : i - nu, n = spin ? S.n_dn : nu;
-    const double* Am = spin ? wm.A + nu * nu : wm.A;
-    if (sizeof(NT) == sizeof(float)) {
-      float acc = 0.0f;
-      for (int m = 0; m < n; ++m) acc += bm.Cf[mu * S.n_mo + m] * (float)Am[m * n + l];
-      wm.vd[idx] = df_make(acc, 0.0f);
-    } else {
-      double acc = 0.0;
-      for (int m = 0; m < n; ++m) acc += sC[mu * S.n_mo + m] * Am[m * n + l];
-      wm.vd[idx] = A::store(A::from_double(acc));
-    }
+  int nh = 0;
+  if (lane == 0) {
+    nh = ld_vol(&t->attach);
+    nh = nh < 0 ? 0 : nh;
+    t->nh = nh;
   }
-  for (int j = lane; j < 3 * N; j += 32) wm.xd[j] = A::store(A::from_double(wm.x[j]));
-  if (lane < 9) wm.Rd[lane] = A::store(A::from_double(wm.R[lane]));
+  nh = __shfl_sync(FULL_MASK, nh, 0);
+  if (nh == 0) return;
+  __threadfence_block();  // this lane's writes of the evaluation state
   __syncwarp();
-  // the caches pay in double-float arithmetic only, and exist only when
-  // the system's layout has room for them (NC is set otherwise: the
-  // kernels of such systems carry no cached code)
-  constexpr bool kUsePairCache = sizeof(NT) == sizeof(df) && !NC;
-  if (kUsePairCache) {
-    fill_pair_cache<NT, NJ>(S, wm, lane);
-    fill_en_cache<NT>(S, wm, lane);
+  if (lane == 0) {
+    const int g = t->gen + 1;
+    t->gen = g;
+    t->next = 0;
+    t->done = 0;
+    __threadfence_block();
+    atomicExch(&t->pub, (g << 4) | nh);
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ void team_sums_ready(TeamSlot* t, int lane)
+{
+  __threadfence_block();
+  __syncwarp();
+  if (lane == 0) atomicExch(&t->sready, t->gen);
+  __syncwarp();
+}
+
+template <class NT, bool NJ, bool NC>
+__device__ __forceinline__ void candidate_m(const SysDev& S, const LatDev& L, const WarpMem& wm, const BlockMem& bm,
+                                            int c, df* Td, double* ratio_out);
+
+// The moves in chunks of 32: alone (t == nullptr) in order, or taken in
+// turn by the owner and its helpers from t->next.
+template <class NT, bool NJ, bool NC>
+__device__ __forceinline__ void chunked_candidates(const SysDev& S, const LatDev& L, const WarpMem& wm,
+                                                   const BlockMem& bm, TeamSlot* t, int P, int lane,
+                                                   double* ratio_out)
+{
+  df* Td = reinterpret_cast<df*>(wm.T);
+  for (int c0 = 0;; c0 += 32) {
+    if (t) {
+      int c = 0;
+      if (lane == 0) c = atomicAdd(&t->next, 32);
+      c0 = __shfl_sync(FULL_MASK, c, 0);
+    }
+    if (c0 >= P) break;
+    if (c0 + lane < P) candidate_m<NT, NJ, NC>(S, L, wm, bm, c0 + lane, Td, ratio_out);
+  }
+  if (t) {
+    __threadfence_block();
     __syncwarp();
   }
-  // local energy: Lp lanes per electron share its shells, electrons and nuclei
-  NT epart = A::zero();
-  if (N <= 32) {
-    const int Lp = 32 / N;
-    const int i = lane % N, part = lane / N;
-    const bool act = lane < N * Lp;
-    ElParts<NT> o;
-    if (act) el_parts_m<NT, NJ>(S, wm, i, part, Lp, bm, o);
-    else el_zero<NT>(o);
-    for (int pp = 1; pp < Lp; ++pp) {
-      int src = lane + pp * N;
-      el_combine<NT>(o, src < 32 ? src : lane, part == 0 && src < N * Lp);
-    }
-    if (part == 0 && act) {
-      wm.Sd[i] = A::store(o.S);
-      epart = el_local<NT>(o);
-    }
-  } else {
-    for (int i = lane; i < N; i += 32) {
-      ElParts<NT> o;
-      el_parts_m<NT, NJ>(S, wm, i, 0, 1, bm, o);
-      wm.Sd[i] = A::store(o.S);
-      epart = A::add(epart, el_local<NT>(o));
-    }
+}
+
+// Owner: wait until the nh helpers of this generation have written their rates.
+__device__ __forceinline__ void team_wait_helpers(TeamSlot* t, int nh, int lane)
+{
+  if (lane == 0) {
+    int it = 0;
+    while (ld_vol(&t->done) < nh && ++it < kTeamSpin) __nanosleep(32);
+    if (it >= kTeamSpin) atomicOr(t->err, kErrTimeout);
+    __threadfence_block();
   }
-  NT etot = warp_sum_m<NT>(epart);
-  el = A::to_double(etot) + S.V_nn;
   __syncwarp();
-  // the P lattice moves
-  const int G = L.G, per_e = 6 * G, P = N * per_e;
-  df* Td = reinterpret_cast<df*>(wm.T);  // rates stay in NT, stored as double-floats
-  for (int c = lane; c < P; c += 32) {
-    int i = c / per_e, rem = c - i * per_e, g = rem / 6, k = (rem % 6) >> 1;
+}
+
+// Owner, when its walker's interval is over: close the slot and release
+// the helpers attached to it.
+__device__ __forceinline__ void team_close(TeamSlot* t, int lane)
+{
+  if (lane == 0) {
+    atomicOr(&t->attach, kTeamClosed);
+    atomicExch(&t->pub, kTeamRelease);
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ void team_open(TeamSlot* t, int lane)
+{
+  if (lane == 0) {
+    t->pub = 0;
+    t->sready = 0;
+    __threadfence_block();
+    atomicExch(&t->attach, 0);
+  }
+  __syncwarp();
+}
+
+// One lattice move c of an evaluation (Eq. 1 lattice, fixed-node rate): the
+// determinant and Jastrow ratios at the displaced position, p at the bond
+// midpoint on the double grid, the rate T_c into Td[c]. Reads the
+// evaluation's shared-memory state (projected inverse columns, positions,
+// rotation, caches, the Jastrow sums Sd); the same code serves the warp
+// that owns the walker and the warps that help it, so a rate has the same
+// bits whoever computes it.
+template <class NT, bool NJ, bool NC>
+__device__ __forceinline__ void candidate_m(const SysDev& S, const LatDev& L, const WarpMem& wm, const BlockMem& bm,
+                                            int c, df* Td, double* ratio_out)
+{
+  typedef Ar<NT> A;
+  const int nao = S.n_ao;
+  const int G = L.G, per_e = 6 * G;
+  constexpr bool kUsePairCache = sizeof(NT) == sizeof(df) && !NC;
+  {
+    const int i = c / per_e, rem = c - i * per_e, g = rem / 6, k = (rem % 6) >> 1;
     NT h = g ? A::c(L.ap_df) : A::c(L.a_df);
     if (c & 1) h = A::neg(h);
     const NT e0 = A::c(wm.Rd[k]), e1 = A::c(wm.Rd[3 + k]), e2 = A::c(wm.Rd[6 + k]);
@@ -1480,24 +1557,163 @@ __device__ void warp_eval_m(const SysDev& S, const double* sC, const LatDev& L, 
     Td[c] = A::store(T);
     if (ratio_out) ratio_out[c] = A::to_double(rho);
   }
+}
+
+template <class NT, bool NJ, bool NC, bool TEAM>
+__device__ void warp_eval_m(const SysDev& S, const double* sC, const LatDev& L, const WarpMem& wm, int lane,
+                            double* ratio_out, double& b, df& bdf, double& el)
+{
+  typedef Ar<NT> A;
+  const int N = S.N, nao = S.n_ao, nu = S.n_up;
+  const BlockMem bm = block_mem(S, const_cast<double*>(sC));
+  // projected inverse columns (FP64, or FP32 in the mixed mode), then
+  // converted with the positions
+  for (int idx = lane; idx < N * nao; idx += 32) {
+    int i = idx / nao, mu = idx % nao;
+    int spin = i < nu ? 0 : 1, l = i < nu ? i : i - nu, n = spin ? S.n_dn : nu;
+    const double* Am = spin ? wm.A + nu * nu : wm.A;
+    if (sizeof(NT) == sizeof(float)) {
+      float acc = 0.0f;
+      for (int m = 0; m < n; ++m) acc += bm.Cf[mu * S.n_mo + m] * (float)Am[m * n + l];
+      wm.vd[idx] = df_make(acc, 0.0f);
+    } else {
+      double acc = 0.0;
+      for (int m = 0; m < n; ++m) acc += sC[mu * S.n_mo + m] * Am[m * n + l];
+      wm.vd[idx] = A::store(A::from_double(acc));
+    }
+  }
+  for (int j = lane; j < 3 * N; j += 32) wm.xd[j] = A::store(A::from_double(wm.x[j]));
+  if (lane < 9) wm.Rd[lane] = A::store(A::from_double(wm.R[lane]));
+  __syncwarp();
+  // the caches pay in double-float arithmetic only, and exist only when
+  // the system's layout has room for them (NC is set otherwise: the
+  // kernels of such systems carry no cached code)
+  constexpr bool kUsePairCache = sizeof(NT) == sizeof(df) && !NC;
+  if (kUsePairCache) {
+    fill_pair_cache<NT, NJ>(S, wm, lane);
+    fill_en_cache<NT>(S, wm, lane);
+    __syncwarp();
+  }
+  if (TEAM) team_publish(&g_team[threadIdx.x >> 5], lane);
+  // local energy: Lp lanes per electron share its shells, electrons and nuclei
+  NT epart = A::zero();
+  if (N <= 32) {
+    const int Lp = 32 / N;
+    const int i = lane % N, part = lane / N;
+    const bool act = lane < N * Lp;
+    ElParts<NT> o;
+    if (act) el_parts_m<NT, NJ>(S, wm, i, part, Lp, bm, o);
+    else el_zero<NT>(o);
+    for (int pp = 1; pp < Lp; ++pp) {
+      int src = lane + pp * N;
+      el_combine<NT>(o, src < 32 ? src : lane, part == 0 && src < N * Lp);
+    }
+    if (part == 0 && act) {
+      wm.Sd[i] = A::store(o.S);
+      epart = el_local<NT>(o);
+    }
+  } else {
+    for (int i = lane; i < N; i += 32) {
+      ElParts<NT> o;
+      el_parts_m<NT, NJ>(S, wm, i, 0, 1, bm, o);
+      wm.Sd[i] = A::store(o.S);
+      epart = A::add(epart, el_local<NT>(o));
+    }
+  }
+  NT etot = warp_sum_m<NT>(epart);
+  el = A::to_double(etot) + S.V_nn;
+  __syncwarp();
+  TeamSlot* team = nullptr;
+  if (TEAM && g_team[threadIdx.x >> 5].nh > 0) {
+    team = &g_team[threadIdx.x >> 5];
+    team_sums_ready(team, lane);
+  }
+  // the P lattice moves: alone, or (at the end of an interval, when other
+  // warps of the block have run out of walkers) in chunks shared with them
+  const int G = L.G, per_e = 6 * G, P = N * per_e;
+  df* Td = reinterpret_cast<df*>(wm.T);  // rates stay in NT, stored as double-floats
+  chunked_candidates<NT, NJ, NC>(S, L, wm, bm, team, P, lane, ratio_out);
+  if (TEAM && team) team_wait_helpers(team, team->nh, lane);
   __syncwarp();
   NT btot = warp_scan_m<NT>(Td, P, lane, A::zero(), nullptr, nullptr);
   bdf = A::store(btot);
   b = A::to_double(btot);
 }
 
-template <int PREC, bool NJ, bool NC>
+template <int PREC, bool NJ, bool NC, bool TEAM = false>
 __device__ __forceinline__ void warp_eval_any(const SysDev& S, const double* sC, const LatDev& L,
                                               const WarpMem& wm, int lane, double* ratio_out, double& b,
                                               df& bdf, double& el)
 {
   if (PREC == LRDMC_PRECISION_DF64) {
-    warp_eval_m<df, NJ, NC>(S, sC, L, wm, lane, ratio_out, b, bdf, el);
+    warp_eval_m<df, NJ, NC, TEAM>(S, sC, L, wm, lane, ratio_out, b, bdf, el);
   } else if (PREC == LRDMC_PRECISION_FP32) {
-    warp_eval_m<float, NJ, true>(S, sC, L, wm, lane, ratio_out, b, bdf, el);
+    warp_eval_m<float, NJ, true, TEAM>(S, sC, L, wm, lane, ratio_out, b, bdf, el);
   } else {
     warp_eval<NJ>(S, sC, L, wm, lane, ratio_out, b, el);
     bdf = df_make(0.0f, 0.0f);
+  }
+}
+
+// A warp whose fetch found the queue empty: attach to the open slot of its
+// block with the fewest helpers, take chunks of moves in every evaluation
+// its owner publishes, and move on when the owner releases it; return when
+// no warp of the block still runs a walker.
+template <class NT, bool NJ, bool NC>
+__device__ __noinline__ void team_help(const SysDev& S, const Layout& Lo, const LatDev& L, double* sC, int wib, int lane)
+{
+  TeamSlot* slots = g_team;
+  const BlockMem bm = block_mem(S, sC);
+  const int P = S.N * 6 * L.G;
+  for (;;) {
+    int o = -1, k = 0;
+    if (lane == 0) {
+      for (int tries = 0; tries < 64 && o < 0; ++tries) {
+        int best = -1, bc = 0x7fffffff;
+        for (int q = 0; q < kWarpsPerBlock; ++q) {
+          const int a = ld_vol(&slots[q].attach);
+          if (q == wib || a < 0) continue;  // itself, or closed (bit 31)
+          if (a < bc) { bc = a; best = q; }
+        }
+        if (best < 0) break;
+        if (atomicCAS(&slots[best].attach, bc, bc + 1) == bc) { o = best; k = bc; }
+      }
+    }
+    o = __shfl_sync(FULL_MASK, o, 0);
+    k = __shfl_sync(FULL_MASK, k, 0);
+    if (o < 0) return;
+    TeamSlot* t = &slots[o];
+    const WarpMem wm = warp_mem(Lo, S, sC + Lo.head + o * Lo.smem_warp);
+    int last = 0;
+    for (;;) {
+      int g = 0, state = 0;  // state 0: take part in generation g, 1: released, 2: timed out
+      if (lane == 0) {
+        int it = 0;
+        for (;;) {
+          const int pub = ld_vol(&t->pub);
+          if (pub == kTeamRelease) { state = 1; break; }
+          g = pub >> 4;
+          if (g > last && k < (pub & 15)) break;
+          if (++it >= kTeamSpin) { state = 2; break; }
+          __nanosleep(64);
+        }
+        if (state == 0) {
+          it = 0;
+          while (ld_vol(&t->sready) < g && ++it < kTeamSpin) __nanosleep(32);
+          if (it >= kTeamSpin) state = 2;
+        }
+        if (state == 2) atomicOr(slots[wib].err, kErrTimeout);
+        __threadfence_block();
+      }
+      state = __shfl_sync(FULL_MASK, state, 0);
+      g = __shfl_sync(FULL_MASK, g, 0);
+      __syncwarp();  // orders lane 0's observation before every lane's reads
+      if (state == 2) return;
+      if (state == 1) break;
+      chunked_candidates<NT, NJ, NC>(S, L, wm, bm, t, P, lane, nullptr);
+      if (lane == 0) atomicAdd(&t->done, 1);
+      last = g;
+    }
   }
 }
 
@@ -1757,8 +1973,21 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
   // interval
   const uint64_t k = *P.kdev;
   const bool recompute = k > 0 && P.recompute_every > 0 && k % (uint64_t)P.recompute_every == 0;
-  stage_coefficients(S, sC);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  // tail helpers (the FP32-pipe evaluations only): every slot starts closed
+  constexpr bool kTeam = PR != LRDMC_PRECISION_FP64;
+  TeamSlot* team = (kTeam && P.helpers) ? &g_team[wib] : nullptr;
+  if (kTeam && lane == 0) {
+    g_team[wib].attach = kTeamClosed;
+    g_team[wib].pub = 0;
+    g_team[wib].sready = 0;
+    g_team[wib].next = 0;
+    g_team[wib].done = 0;
+    g_team[wib].gen = 0;
+    g_team[wib].nh = 0;
+    g_team[wib].err = P.err;
+  }
+  stage_coefficients(S, sC);  // ends with __syncthreads
   WarpMem wm = warp_mem(Lo, S, sC + Lo.head + wib * Lo.smem_warp);
   const int P_moves = S.N * 6 * L.G;
   const BlockMem bm = block_mem(S, sC);
@@ -1767,6 +1996,7 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
     if (lane == 0) idx = atomicAdd(P.counter, 1);
     idx = __shfl_sync(FULL_MASK, idx, 0);
     if (idx >= P.W) break;
+    if (team) team_open(team, lane);
     const int s = P.order[idx];
     const int src = P.parent[s];
     double b, el;
@@ -1844,7 +2074,7 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
       __syncwarp();
       rotation_matrix_warp<PR>(b1, wm.R, lane, S);
       __syncwarp();
-      warp_eval_any<PR, NJ, NC>(S, sC, L, wm, lane, nullptr, b, bdf, el);
+      warp_eval_any<PR, NJ, NC, kTeam>(S, sC, L, wm, lane, nullptr, b, bdf, el);
       ++jumps;
       if (!isfinite(el) || !isfinite(b)) {
         if (lane == 0) atomicOr(P.err, kErrNonFinite);
@@ -1855,6 +2085,7 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
         break;
       }
     }
+    if (team) team_close(team, lane);
     store_record(Lo, P.rec_dst + (size_t)s * Lo.rec, wm, lane, b, el);
     if (lane == 0) {
       P.logw[s] = logw;
@@ -1863,6 +2094,11 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
       P.jumps[s] = jumps;
     }
     __syncwarp();
+  }
+  // out of walkers: help the warps of this block that still run one
+  if (kTeam && team) {
+    if (PR == LRDMC_PRECISION_DF64) team_help<df, NJ, NC>(S, Lo, L, sC, wib, lane);
+    else team_help<float, NJ, true>(S, Lo, L, sC, wib, lane);
   }
 }
 

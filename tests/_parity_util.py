@@ -63,12 +63,11 @@ def el_scale(system, x, el_ref):
 
 # ------------------------------------------------------------------ projection
 RTOL = 1e-10
-# Below about 2^-100 the double-float format loses its relative precision:
-# its low part (about 2^-24 of the high part) falls into float's subnormal
-# range, and an exponential whose value lies there keeps only an absolute
-# accuracy of float's subnormal spacing. Rates are compared down to this
-# floor of their weight.
-DF_FLOOR = 2.0 ** -100
+# Double-floats share float's exponent range: an exponential whose value
+# lies below float's smallest normal number (2^-126) comes out as zero, so a
+# weight p = exp(-x) of Eq. 3 far from the nucleus carries an absolute error
+# up to 2^-126 in the double-float and FP32 modes.
+W_ABS = 2.0 ** -126
 # A decision whose uniform lies within this distance of a bin edge (relative
 # to the quantity it is compared with: tau for the waiting time, b for the
 # heat bath, the total weight for a comb tooth) may go either way between
@@ -145,21 +144,18 @@ def merge_worst(acc, info):
             acc[k] = min(acc.get(k, np.inf), v)
 
 
-def rate_scale(lat, w, scale, w_floor=0.0):
-    """Scale of every rate T_c = w_c/(2 h_c^2) max(rho_c, 0): the scale of
-    its weight times its spacing factor times the floating-point scale of
-    its ratio (candidate order: electron, grid, axis, sign). On the a grid
-    w = p(mid) is an exponential, accurate relative to itself; on the a'
-    grid w = 1 - p(mid) inherits the absolute rounding of p <= 1, so its
-    scale is max(w, 1 - w) (next to a nucleus p -> 1 and w is a small
-    difference of numbers near 1). w_floor is the smallest weight the
-    arithmetic resolves to its full relative precision (DF_FLOOR for the
-    double-float and FP32 modes: Eq. 3's Gaussian far from the nucleus
-    reaches float's subnormal range and zero), below which the error is an
-    absolute one of that size."""
+def rate_tolerance(lat, w, scale, rtol=RTOL, w_abs=0.0):
+    """Tolerance of every rate T_c = w_c/(2 h_c^2) max(rho_c, 0), candidate
+    order electron, grid, axis, sign: rtol times the scale of its weight,
+    times its spacing factor, times the floating-point scale of its ratio;
+    plus an absolute weight error w_abs (W_ABS in the FP32-pipe modes) times
+    the same factors. On the a grid w = p(mid) is an exponential, accurate
+    relative to itself; on the a' grid w = 1 - p(mid) inherits the absolute
+    rounding of p <= 1, so its scale is max(w, 1 - w) (next to a nucleus
+    p -> 1 and w is a small difference of numbers near 1)."""
     P = len(w)
     w = np.asarray(w, float)
     g = (np.arange(P) // 6) % lat.G
     h = np.where(g == 0, lat.a, lat.ap)
-    w_scale = np.maximum(np.where(g == 0, w, np.maximum(w, 1.0 - w)), w_floor)
-    return w_scale / (2.0 * h * h) * scale
+    w_scale = np.where(g == 0, w, np.maximum(w, 1.0 - w))
+    return (rtol * w_scale + w_abs) / (2.0 * h * h) * scale

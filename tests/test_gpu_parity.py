@@ -23,7 +23,7 @@ import pytest
 
 import lrdmc_synth as S
 import _parity_util as U
-from _parity_util import EDGE, RTOL, el_scale, rate_scale, ratio_scale
+from _parity_util import EDGE, RTOL, el_scale, rate_tolerance, ratio_scale
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -66,19 +66,19 @@ PRECISIONS = ["fp64", "df64"]
 
 
 def _check_rates(c, T, ref, tsc, scale):
-    """Every rate of configuration c within RTOL of its own scale; on
-    failure, the worst move with its weight, ratio and scales."""
+    """Every rate of configuration c within its tolerance (rate_tolerance);
+    on failure, the worst move with its weight, ratio and scales."""
     err = np.abs(T - ref["T"])
-    bad = err > RTOL * tsc
+    bad = err > tsc
     if np.any(bad):
         j = int(np.argmax(np.where(bad, err / np.maximum(tsc, 1e-300), 0.0)))
         raise AssertionError(f"config {c} move {j} (grid {(j // 6) % 2}): T {T[j]!r} vs {ref['T'][j]!r}, "
                              f"w {ref['w'][j]!r}, ratio {ref['ratio'][j]!r}, ratio scale {scale[j]!r}, "
-                             f"rate scale {tsc[j]!r}, {int(np.sum(bad))} moves off")
+                             f"rate tolerance {tsc[j]!r}, {int(np.sum(bad))} moves off")
 
 
-def _w_floor(prec):
-    return U.DF_FLOOR if prec != "fp64" else 0.0
+def _w_abs(prec):
+    return U.W_ABS if prec != "fp64" else 0.0
 
 
 class _EvalWorst:
@@ -102,7 +102,7 @@ class _EvalWorst:
         pos = tr > 0
         if np.any(pos):
             d["worst_T_rel"] = max(d["worst_T_rel"], float(np.max(np.abs(t[pos] - tr[pos]) / tr[pos])))
-        d["worst_T_scaled"] = max(d["worst_T_scaled"], float(np.max(np.abs(t - tr) / np.maximum(ts, 1e-300))))
+        d["worst_T_scaled"] = max(d["worst_T_scaled"], RTOL * float(np.max(np.abs(t - tr) / np.maximum(ts, 1e-300))))
         d["worst_b_rel"] = max(d["worst_b_rel"], abs(b - br) / br)
         d["worst_EL_rel"] = max(d["worst_EL_rel"], abs(e - er) / abs(er))
 
@@ -137,7 +137,7 @@ def test_evaluate_matches_oracle(pkg, oracle_mod, name, kind, a, prec):
         scale = ratio_scale(o, system, lat, x[c], R[c], ref["ratio"])
         err = np.abs(ratio[c] - ref["ratio"])
         assert np.all(err <= RTOL * scale), (c, np.max(err / scale))
-        tsc = rate_scale(lat, ref["w"], scale, _w_floor(prec))
+        tsc = rate_tolerance(lat, ref["w"], scale, w_abs=_w_abs(prec))
         _check_rates(c, T[c], ref, tsc, scale)
         assert abs(b[c] - ref["b"]) <= RTOL * ref["b"]
         assert abs(el[c] - ref["EL"]) <= RTOL * max(1.0, abs(ref["EL"]))
@@ -166,7 +166,7 @@ def test_evaluate_full_size_sampled(pkg, oracle_mod, prec):
         ref = o.lattice_eval(lat, x[c], R[c])
         scale = ratio_scale(o, system, lat, x[c], R[c], ref["ratio"])
         assert np.all(np.abs(ratio[c] - ref["ratio"]) <= RTOL * scale)
-        tsc = rate_scale(lat, ref["w"], scale, _w_floor(prec))
+        tsc = rate_tolerance(lat, ref["w"], scale, w_abs=_w_abs(prec))
         _check_rates(c, T[c], ref, tsc, scale)
         assert abs(el[c] - ref["EL"]) <= RTOL * abs(ref["EL"])
         worst.add(ratio[c], ref["ratio"], scale, T[c], ref["T"], tsc, b[c], ref["b"], el[c], ref["EL"])
@@ -399,7 +399,7 @@ def test_large_system_without_caches(pkg, oracle_mod, prec):
         worst = int(np.argmax(err))
         assert err.max() <= 1.0, (c, worst, float(err.max()), float(ratio[c].flat[worst]),
                                   float(ref["ratio"].flat[worst]))
-        tsc = rate_scale(lat, ref["w"], scale, _w_floor(prec))
+        tsc = rate_tolerance(lat, ref["w"], scale, w_abs=_w_abs(prec))
         _check_rates(c, T[c], ref, tsc, scale)
         assert abs(b[c] - ref["b"]) <= RTOL * ref["b"]
         assert abs(el[c] - ref["EL"]) <= RTOL * max(1.0, abs(ref["EL"]))
@@ -459,7 +459,7 @@ def test_heavy_atoms_evaluate_full_size_sampled(pkg, oracle_mod, name, a, tau, e
         ref = o.lattice_eval(lat, x[c], R[c])
         scale = ratio_scale(o, system, lat, x[c], R[c], ref["ratio"])
         assert np.all(np.abs(ratio[c] - ref["ratio"]) <= RTOL * scale), c
-        tsc = rate_scale(lat, ref["w"], scale, _w_floor("df64"))
+        tsc = rate_tolerance(lat, ref["w"], scale, w_abs=_w_abs("df64"))
         _check_rates(c, T[c], ref, tsc, scale)
         assert abs(b[c] - ref["b"]) <= RTOL * ref["b"], c
         assert abs(el[c] - ref["EL"]) <= RTOL * abs(ref["EL"]), c
