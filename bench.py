@@ -225,7 +225,7 @@ def measure_leg(args, pkg, torch, system, precision, dev, rank, seed, x0, with_c
     _, world, local = _env_rank()
     spacing = pkg.Spacing(pkg.THIS_WORK)
     a = WORKLOAD["a"]
-    g = pkg.LrdmcSystem(system).set_precision(precision).set_tail_helpers(args.tail_helpers)
+    g = pkg.LrdmcSystem(system).set_precision(precision)
     if neural is not None:
         g.set_neural_jastrow(*neural)
     cap = args.warmup + args.steps + args.eff_steps + 8
@@ -317,6 +317,7 @@ def run_ours(args):
     if args.neural_leg:
         nj = neural_leg(args, pkg, torch, system, main_prec, dev, rank, seed, x0)
     bt = batched_leg(args, pkg, torch, main_prec, seed) if args.batch_leg else None
+    tc = tc_leg(args, pkg, torch, seed) if args.tc_leg else None
     # e2e: the public API from host memory: H2D of the start configurations,
     # init, the same steps, each followed by a D2H read of the trace.
     spacing = pkg.Spacing(pkg.THIS_WORK)
@@ -372,8 +373,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": "Ne all-electron, 4096 walkers, a=0.2 bohr, smart double grid (this work), "
                                "tau=0.025", **WORKLOAD, **ARITHMETIC[args.precision],
-                   "walkers_per_gpu": W, "tail_helpers": bool(args.tail_helpers),
-                   "l2": "flushed between timed steps (512 MiB write)",
+                   "walkers_per_gpu": W, "l2": "flushed between timed steps (512 MiB write)",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_moves_all / t_e2e_all, "unit": "walker-moves/s",
                 "h2d_bytes_per_step": x0.nbytes / n_e2e, "d2h_bytes_per_step": d2h / n_e2e,
@@ -429,6 +429,8 @@ def run_ours(args):
         out["neural_jastrow"] = block
     if bt is not None:
         out["batched"] = bt
+    if tc is not None:
+        out["tensor_core_contraction"] = tc
     out["cpu_baseline"] = cpu_baseline(args) if args.cpu_seconds > 0 else None
     print(json.dumps(out), flush=True)
     if dist is not None:
@@ -529,6 +531,42 @@ def batched_leg(args, pkg, torch, precision, seed):
             "ms_per_sequential_round": t_seq / K, "tuning": report,
             "note": "one CUDA graph per step with every system's kernels as parallel branches; "
                     "grid sizes chosen by measurement"}
+
+
+def tc_leg(args, pkg, torch, seed):
+    """A/B of the orbital contraction in the mixed-precision (FP32)
+    evaluation: the projected form (one length-K dot of basis values with
+    the projected inverse column per lattice move, lrdmc_evaluate) against
+    the tensor-core form (basis values of 128 moves as bf16x3 rows, tcgen05
+    MMA with C, lrdmc_evaluate_tc), on 16384 configurations of Kr at
+    a = 1/(3.5 Z) (the mixed-precision workload) and of the bench's Ne.
+    Each call is timed with CUDA events on its stream after 3 warm-up
+    calls, best of 5."""
+    out = {}
+    for name, a in (("Kr", 1.0 / 126.0), ("Ne", WORKLOAD["a"])):
+        system = S.make_system(name)
+        g = pkg.LrdmcSystem(system).set_precision(pkg.PRECISION_FP32)
+        n = 16384
+        x = torch.tensor(S.initial_positions(system, n, seed + 11), device="cuda")
+        R = torch.tensor(S.random_rotations(n, seed + 12), device="cuda")
+        sp = pkg.Spacing(pkg.THIS_WORK)
+        res = {}
+        for label, fn in (("projected", g.evaluate), ("tensor_core", g.evaluate_tc)):
+            for _ in range(3):
+                fn(x, R, a, sp)
+            best = float("inf")
+            st = torch.cuda.current_stream()
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                fn(x, R, a, sp)
+                e1.record(st)
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            res[label] = {"ms": best, "lattice_moves_per_s": n * 12 * system.N / (best * 1e-3)}
+        out[name] = {"configurations": n, "a": a, "K": system.n_ao, "orbitals_per_spin": system.n_up,
+                     **res, "tensor_core_over_projected": res["projected"]["ms"] / res["tensor_core"]["ms"]}
+    return out
 
 
 def _read_profile(precision):
@@ -672,10 +710,10 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--no-neural-leg", dest="neural_leg", action="store_false",
                     help="skip training and measuring the neural pair Jastrow")
+    ap.add_argument("--no-tc-leg", dest="tc_leg", action="store_false",
+                    help="skip the A/B of the tensor-core orbital contraction")
     ap.add_argument("--no-mixed-leg", dest="mixed_leg", action="store_false",
                     help="skip the mixed-precision (FP32 evaluation) leg")
-    ap.add_argument("--tail-helpers", type=int, default=1, choices=[0, 1],
-                    help="warps out of walkers help the others of their block (results are the same bits)")
     ap.add_argument("--walkers", type=int, default=WORKLOAD["n_walkers"],
                     help="walkers per GPU (smaller cases for profiling)")
     args = ap.parse_args()

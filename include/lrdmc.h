@@ -201,6 +201,26 @@ LRDMC_API lrdmc_status lrdmc_evaluate(lrdmc_system_t sys, int n_configs, const d
                             double a, const lrdmc_spacing_fn* spacing, double* ratio, double* T,
                             double* b, double* el, void* stream);
 
+/* The same evaluation with the orbital contraction on the tensor cores, the
+ * mixed-precision form of the basis x MO product the method needs at every
+ * displaced position (Eq. 1 lattice moves; the determinant ratio
+ * psi(x')/psi(x) of the cited LRDMC method): per lattice move the basis
+ * values chi_mu(r') are computed in FP32, split into bfloat16 high and low
+ * parts, and phi_m(r') = sum_mu chi_mu(r') C[mu][m] is formed by tcgen05
+ * MMAs (A_hi B_hi + A_hi B_lo + A_lo B_hi, FP32 accumulation in tensor
+ * memory, about 16 significant bits) for 128 moves of four configurations
+ * at a time; the determinant ratio sum_m phi_m Ainv[m][l], the Jastrow
+ * ratio, p, the rates and the local energy are the FP32 mode's
+ * (LRDMC_PRECISION_FP32, whatever the system's precision setting). Same
+ * arguments, layouts and outputs as lrdmc_evaluate. Requires at most 32
+ * orbitals per spin and room for the operand tiles in one block's shared
+ * memory (LRDMC_ERR_ARG otherwise). LRDMC_ERR_TIMEOUT if a bounded wait for
+ * the tensor core runs out; LRDMC_ERR_SINGULAR for a singular Slater
+ * matrix. Synchronises the stream. */
+LRDMC_API lrdmc_status lrdmc_evaluate_tc(lrdmc_system_t sys, int n_configs, const double* x, const double* rot,
+                                         double a, const lrdmc_spacing_fn* spacing, double* ratio, double* T,
+                                         double* b, double* el, void* stream);
+
 /* Evaluation that allocates nothing. The paper has no counterpart: this
  * is a service for callers that cannot call cudaMalloc when they evaluate -
  * code running inside another framework's reserved memory budget,
@@ -358,18 +378,6 @@ LRDMC_API lrdmc_status lrdmc_nj_backward(lrdmc_system_t sys, const lrdmc_nj_spec
  * ---------------------------------------------------------------------- */
 LRDMC_API lrdmc_status lrdmc_set_interval_blocks(lrdmc_system_t sys, int blocks);
 LRDMC_API lrdmc_status lrdmc_interval_blocks(lrdmc_system_t sys, int* current, int* occupancy_default);
-
-/* Tail helpers (on = 1, the default; 0 = off). Not a step of the paper's
- * method: a schedule of the interval kernel. Jump counts per interval are
- * Poisson-distributed, so near the end of an interval most warps have no
- * walker left while a few still run one; with helpers on, a warp whose
- * fetch finds no walker takes chunks of the lattice moves of a walker that
- * another warp of its block still runs (double-float and FP32 evaluation;
- * the FP64 mode ignores the switch). The rates, and so every result, are
- * bit for bit the same either way. Every wait between the warps is bounded;
- * one that runs out is reported as LRDMC_ERR_TIMEOUT. Takes effect at the
- * next step. */
-LRDMC_API lrdmc_status lrdmc_set_tail_helpers(lrdmc_system_t sys, int on);
 
 /* A batch projects several systems (different atoms, electron counts and
  * spacings) together. Every step is one CUDA graph: per execution group

@@ -31,11 +31,10 @@ PRECISION_FP64, PRECISION_DF64, PRECISION_FP32 = 0, 1, 2
 EXPORTED = [
     "lrdmc_create_system", "lrdmc_spacing_params", "lrdmc_workspace_bytes", "lrdmc_init_walkers",
     "lrdmc_step", "lrdmc_sync", "lrdmc_get_energy_trace", "lrdmc_get_walkers", "lrdmc_moves", "lrdmc_evaluate",
-    "lrdmc_evaluate_static",
+    "lrdmc_evaluate_static", "lrdmc_evaluate_tc",
     "lrdmc_save", "lrdmc_load", "lrdmc_set_precision", "lrdmc_set_profiling", "lrdmc_kernel_times", "lrdmc_last_error",
     "lrdmc_destroy", "lrdmc_nj_n_params", "lrdmc_set_neural_jastrow", "lrdmc_base_terms", "lrdmc_nj_forward",
-    "lrdmc_nj_backward", "lrdmc_set_interval_blocks", "lrdmc_interval_blocks", "lrdmc_set_tail_helpers",
-    "lrdmc_batch_create",
+    "lrdmc_nj_backward", "lrdmc_set_interval_blocks", "lrdmc_interval_blocks", "lrdmc_batch_create",
     "lrdmc_batch_step", "lrdmc_batch_sync", "lrdmc_batch_stream", "lrdmc_batch_last_error", "lrdmc_batch_destroy",
     "lrdmc_batch_set_groups", "lrdmc_batch_set_carveout",
 ]
@@ -129,6 +128,8 @@ def load_library():
     L.lrdmc_evaluate.argtypes = [vp, i, vp, vp, d, vp, vp, vp, vp, vp, vp]
     L.lrdmc_evaluate_static.restype = i
     L.lrdmc_evaluate_static.argtypes = [vp, i, vp, vp, d, vp, vp, vp, vp, vp, vp]
+    L.lrdmc_evaluate_tc.restype = i
+    L.lrdmc_evaluate_tc.argtypes = [vp, i, vp, vp, d, vp, vp, vp, vp, vp, vp]
     L.lrdmc_save.restype = i
     L.lrdmc_save.argtypes = [vp, ct.c_char_p]
     L.lrdmc_load.restype = i
@@ -156,8 +157,6 @@ def load_library():
     L.lrdmc_nj_backward.argtypes = [vp, vp, vp, i, vp, vp, vp, vp, vp, vp]
     L.lrdmc_set_interval_blocks.restype = i
     L.lrdmc_set_interval_blocks.argtypes = [vp, i]
-    L.lrdmc_set_tail_helpers.restype = i
-    L.lrdmc_set_tail_helpers.argtypes = [vp, i]
     L.lrdmc_interval_blocks.restype = i
     L.lrdmc_interval_blocks.argtypes = [vp, ct.POINTER(i), ct.POINTER(i)]
     L.lrdmc_batch_create.restype = i
@@ -395,6 +394,15 @@ class LrdmcSystem:
         """One evaluation of every lattice move of n configurations.
         x: [n][N][3] and rot: [n][9] float64 CUDA tensors. Returns CUDA tensors
         ratio [n][P], T [n][P], b [n], el [n]."""
+        return self._evaluate_with("lrdmc_evaluate", x, rot, a, spacing, stream)
+
+    def evaluate_tc(self, x, rot, a, spacing: Spacing = Spacing(), stream=None):
+        """Like evaluate, through lrdmc_evaluate_tc: the FP32 mode's
+        evaluation with the basis x MO contraction on the tensor cores
+        (bf16x3 operands, FP32 accumulation)."""
+        return self._evaluate_with("lrdmc_evaluate_tc", x, rot, a, spacing, stream)
+
+    def _evaluate_with(self, entry, x, rot, a, spacing, stream):
         import torch
 
         G = 1 if spacing.kind == SINGLE else 2
@@ -409,17 +417,10 @@ class LrdmcSystem:
         if stream is None:
             stream = torch.cuda.current_stream(x.device)
         sp = spacing.c()
-        self._check(load_library().lrdmc_evaluate(self.h, n, _t_ptr(x), _t_ptr(rot), float(a), ct.byref(sp),
-                                                  _t_ptr(ratio), _t_ptr(T), _t_ptr(b), _t_ptr(el),
-                                                  ct.c_void_p(stream.cuda_stream)))
+        fn = getattr(load_library(), entry)
+        self._check(fn(self.h, n, _t_ptr(x), _t_ptr(rot), float(a), ct.byref(sp), _t_ptr(ratio), _t_ptr(T),
+                       _t_ptr(b), _t_ptr(el), ct.c_void_p(stream.cuda_stream)))
         return ratio, T, b, el
-
-
-    def set_tail_helpers(self, on=True):
-        """Warps out of walkers help the warps of their block that still run
-        one (default on; results are bit for bit the same either way)."""
-        self._check(load_library().lrdmc_set_tail_helpers(self.h, int(bool(on))))
-        return self
 
     def set_interval_blocks(self, blocks):
         """Persistent grid size of the interval kernel (0 = occupancy default)."""

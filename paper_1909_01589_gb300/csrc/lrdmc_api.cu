@@ -47,7 +47,6 @@ struct lrdmc_system_s {
   long long n_interval = 0, n_reconfig = 0;
   std::string last_error;
   int blocks = 0;  // persistent grid of the interval kernel (0 = occupancy default)
-  int helpers = 1;  // tail helpers in the interval kernel (lrdmc_set_tail_helpers)
   uint64_t version = 0;  // bumped whenever kernel arguments change (batches re-capture)
   // neural pair term (lrdmc_set_neural_jastrow)
   double* nj_tab = nullptr;
@@ -439,7 +438,6 @@ static lrdmc_status read_error_word(lrdmc_system_t s)
   if (w & kErrSingular) return fail(s, LRDMC_ERR_SINGULAR, "singular Slater matrix or zero update ratio");
   if (w & kErrNonFinite) return fail(s, LRDMC_ERR_NONFINITE, "non-finite local energy or rate");
   if (w & kErrIters) return fail(s, LRDMC_ERR_TIMEOUT, "an interval exceeded its iteration limit");
-  if (w & kErrTimeout) return fail(s, LRDMC_ERR_TIMEOUT, "a tail helper's wait ran out (interval kernel)");
   return LRDMC_OK;
 }
 
@@ -490,7 +488,6 @@ lrdmc_status lrdmc_init_walkers(lrdmc_system_t s, int W, const double* x0, uint6
   P.seed = seed;
   P.tau = tau;
   P.e_trial = e_trial;
-  P.helpers = s->helpers;
   cudaError_t e = cudaMemsetAsync(s->ws + p.moves, 0, 4 * 256, s->stream);  // moves, err, counter, kdev
   if (e != cudaSuccess) return cuda_fail(s, e, "workspace clear");
   e = cudaMemsetAsync(P.logw, 0, sizeof(double) * W, s->stream);
@@ -592,7 +589,6 @@ static lrdmc_status sync_system(lrdmc_system_t s)
   if (w & kErrSingular) return fail(s, LRDMC_ERR_SINGULAR, "singular Slater matrix or zero update ratio");
   if (w & kErrNonFinite) return fail(s, LRDMC_ERR_NONFINITE, "non-finite local energy or rate");
   if (w & kErrIters) return fail(s, LRDMC_ERR_TIMEOUT, "an interval exceeded its iteration limit");
-  if (w & kErrTimeout) return fail(s, LRDMC_ERR_TIMEOUT, "a tail helper's wait ran out (interval kernel)");
   return LRDMC_OK;
 }
 
@@ -697,6 +693,37 @@ lrdmc_status lrdmc_evaluate(lrdmc_system_t s, int n, const double* x, const doub
   if (e != cudaSuccess) return cuda_fail(s, e, "evaluate");
   int h = *s->err_host;
   if (h & kErrSingular) return fail(s, LRDMC_ERR_SINGULAR, "evaluate: singular Slater matrix");
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_evaluate_tc(lrdmc_system_t s, int n, const double* x, const double* rot, double a,
+                               const lrdmc_spacing_fn* sp, double* ratio, double* T, double* b, double* el,
+                               void* stream)
+{
+  if (!s) return fail(s, LRDMC_ERR_ARG, "");
+  if (n < 0 || (n > 0 && (!x || !rot))) return fail(s, LRDMC_ERR_ARG, "evaluate_tc: bad arguments");
+  if (s->S.n_mo > 32) return fail(s, LRDMC_ERR_ARG, "evaluate_tc: more than 32 orbitals per spin");
+  if (evaluate_tc_smem_bytes(s->S, s->Lo) > kMaxSmemBlock)
+    return fail(s, LRDMC_ERR_ARG, "evaluate_tc: the block's shared memory with the tensor-core tiles exceeds " +
+                                      std::to_string(kMaxSmemBlock / 1024) + " KB");
+  if (n == 0) return LRDMC_OK;
+  LatDev L;
+  lrdmc_status st = lattice_from(s, a, sp, L);
+  if (st != LRDMC_OK) return st;
+  cudaStream_t cs = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (!s->eval_err) e = cudaMalloc((void**)&s->eval_err, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(s, e, "evaluate error word");
+  if (!s->err_host) e = cudaMallocHost((void**)&s->err_host, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(s, e, "pinned error word");
+  e = cudaMemsetAsync(s->eval_err, 0, sizeof(int), cs);
+  if (e == cudaSuccess) e = launch_evaluate_tc(s->S, s->Lo, L, n, x, rot, ratio, T, b, el, s->eval_err, cs);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->err_host, s->eval_err, sizeof(int), cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  if (e != cudaSuccess) return cuda_fail(s, e, "evaluate_tc");
+  int h = *s->err_host;
+  if (h & kErrTimeout) return fail(s, LRDMC_ERR_TIMEOUT, "evaluate_tc: the tensor-core barrier wait ran out");
+  if (h & kErrSingular) return fail(s, LRDMC_ERR_SINGULAR, "evaluate_tc: singular Slater matrix");
   return LRDMC_OK;
 }
 
@@ -1020,16 +1047,6 @@ lrdmc_status lrdmc_set_interval_blocks(lrdmc_system_t s, int blocks)
   if (!s) return fail(s, LRDMC_ERR_ARG, "");
   if (blocks < 0) return fail(s, LRDMC_ERR_ARG, "set_interval_blocks: blocks < 0");
   s->blocks = blocks;
-  s->version++;
-  return LRDMC_OK;
-}
-
-lrdmc_status lrdmc_set_tail_helpers(lrdmc_system_t s, int on)
-{
-  if (!s) return fail(s, LRDMC_ERR_ARG, "");
-  if (on != 0 && on != 1) return fail(s, LRDMC_ERR_ARG, "set_tail_helpers: on must be 0 or 1");
-  s->helpers = on;
-  s->P.helpers = on;
   s->version++;
   return LRDMC_OK;
 }

@@ -25,7 +25,7 @@ constexpr int kMaxItersPerInterval = 1 << 20;
 constexpr int kErrSingular = 1;
 constexpr int kErrNonFinite = 2;
 constexpr int kErrIters = 4;
-constexpr int kErrTimeout = 8;  // a bounded wait of the interval kernel's tail helpers ran out
+constexpr int kErrTimeout = 8;  // a bounded wait on the tensor-core MMA barrier ran out
 
 // Philox counter tags.
 constexpr uint64_t kTagTimeHB = 0;
@@ -122,10 +122,8 @@ struct Layout {
 // Shared-memory layout of a system; caches = false leaves out the
 // evaluation caches (for systems that would not fit otherwise).
 Layout make_layout(const SysDev& S, bool caches);
-// Largest dynamic shared memory of one block on sm_100-class GPUs (227 KB),
-// less the interval kernel's static shared memory (the tail helpers' slots,
-// 256 bytes reserved).
-constexpr int kMaxSmemBlock = 232448 - 256;
+// Largest dynamic shared memory of one block on sm_100-class GPUs (227 KB).
+constexpr int kMaxSmemBlock = 232448;
 
 // Populations up to this many walkers keep the comb's running sums in the
 // reconfiguration kernel's shared memory (8 bytes each).
@@ -155,9 +153,6 @@ struct PopDev {
   int trace_cap;
   uint64_t seed;
   double tau, e_trial;
-  // 1: warps that run out of walkers help the warps of their block that
-  // still run one (double-float and FP32 evaluation); 0: every warp alone
-  int helpers;
 };
 
 void fill_df_constants(SysDev& S);
@@ -205,6 +200,15 @@ cudaError_t launch_nj_backward(const NjGeom& G, const NjNetDev& N, const float* 
 
 cudaError_t launch_base_terms(const SysDev& S, const Layout& Lo, int n, const double* x, double* grad,
                               double* e, int* err, cudaStream_t st);
+
+// Evaluation with the orbital contraction on the tensor cores (FP32 mode
+// arithmetic; bf16x3 operands, FP32 accumulation in tensor memory); its
+// shared memory per block, and the launch. err receives kErrSingular and
+// kErrTimeout bits.
+int evaluate_tc_smem_bytes(const SysDev& S, const Layout& Lo);
+cudaError_t launch_evaluate_tc(const SysDev& S, const Layout& Lo, const LatDev& L, int n, const double* x,
+                               const double* rot, double* ratio, double* T, double* b, double* el, int* err,
+                               cudaStream_t st);
 
 cudaError_t launch_evaluate_static(const SysDev& S, const Layout& Lo, const LatDev& L, int n,
                                    const double* x, const double* rot, double* ratio, double* T,

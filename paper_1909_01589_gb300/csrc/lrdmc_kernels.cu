@@ -24,6 +24,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <cuda_bf16.h>
+
 #include <mutex>
 
 #include "lrdmc_internal.h"
@@ -1371,151 +1373,79 @@ __device__ __forceinline__ NT el_local(const ElParts<NT>& o)
   return A::add(A::mul_f(lap, -0.5f), o.V);
 }
 
-// ----------------------------------------------------------------------------
-// Tail helpers. Walkers make Poisson-distributed numbers of jumps, so at the
-// end of an interval warps run out of walkers while others still work on
-// their last one. A warp whose fetch finds the queue empty attaches to a
-// warp of its own block that is still running a walker and takes chunks of
-// 32 of that walker's lattice moves in every following evaluation. The
-// owner publishes each evaluation (projected columns, positions, rotation
-// and caches ready), then the Jastrow sums (after its local energy), takes
-// chunks itself, and waits for its helpers before the heat-bath scan. Every
-// wait is bounded (kTeamSpin polls with a short sleep); one that runs out
-// sets kErrTimeout in the error word and gives up, so a fault in this
-// protocol is reported as LRDMC_ERR_TIMEOUT, never a hang.
-// ----------------------------------------------------------------------------
-struct TeamSlot {
-  int attach;  // bit 31: closed to helpers; bits 0-30: helpers attached
-  int pub;     // published evaluation (generation << 4 | participants), or kTeamRelease
-  int sready;  // generation whose Jastrow sums Sd are ready
-  int next;    // next candidate chunk of the current generation
-  int done;    // helpers finished with the current generation
-  int gen;     // owner's generation counter
-  int nh;      // owner: helpers taking part in the current evaluation
-  int pad;
-  int* err;    // the population's error word (a wait that runs out sets kErrTimeout)
-};
-// One slot per warp of an interval-kernel block (only the kernels that run
-// the tail helpers touch them).
-__shared__ TeamSlot g_team[kWarpsPerBlock];
-constexpr int kTeamClosed = (int)0x80000000;
-constexpr int kTeamRelease = -1;
-constexpr int kTeamSpin = 1 << 22;
-
-__device__ __forceinline__ int ld_vol(const int* p) { return *(const volatile int*)p; }
-
-// Owner, every evaluation: records in t->nh the number of helpers taking
-// part (0: alone); a helper that attaches later joins at the next
-// evaluation. A closed slot (helpers off, or no walker) reads as 0.
-__device__ __forceinline__ void team_publish(TeamSlot* t, int lane)
-{
-  int nh = 0;
-  if (lane == 0) {
-    nh = ld_vol(&t->attach);
-    nh = nh < 0 ? 0 : nh;
-    t->nh = nh;
-  }
-  nh = __shfl_sync(FULL_MASK, nh, 0);
-  if (nh == 0) return;
-  __threadfence_block();  // this lane's writes of the evaluation state
-  __syncwarp();
-  if (lane == 0) {
-    const int g = t->gen + 1;
-    t->gen = g;
-    t->next = 0;
-    t->done = 0;
-    __threadfence_block();
-    atomicExch(&t->pub, (g << 4) | nh);
-  }
-  __syncwarp();
-}
-
-__device__ __forceinline__ void team_sums_ready(TeamSlot* t, int lane)
-{
-  __threadfence_block();
-  __syncwarp();
-  if (lane == 0) atomicExch(&t->sready, t->gen);
-  __syncwarp();
-}
-
-template <class NT, bool NJ, bool NC>
-__device__ __forceinline__ void candidate_m(const SysDev& S, const LatDev& L, const WarpMem& wm, const BlockMem& bm,
-                                            int c, df* Td, double* ratio_out);
-
-// The moves in chunks of 32: alone (t == nullptr) in order, or taken in
-// turn by the owner and its helpers from t->next.
-template <class NT, bool NJ, bool NC>
-__device__ __forceinline__ void chunked_candidates(const SysDev& S, const LatDev& L, const WarpMem& wm,
-                                                   const BlockMem& bm, TeamSlot* t, int P, int lane,
-                                                   double* ratio_out)
-{
-  df* Td = reinterpret_cast<df*>(wm.T);
-  for (int c0 = 0;; c0 += 32) {
-    if (t) {
-      int c = 0;
-      if (lane == 0) c = atomicAdd(&t->next, 32);
-      c0 = __shfl_sync(FULL_MASK, c, 0);
-    }
-    if (c0 >= P) break;
-    if (c0 + lane < P) candidate_m<NT, NJ, NC>(S, L, wm, bm, c0 + lane, Td, ratio_out);
-  }
-  if (t) {
-    __threadfence_block();
-    __syncwarp();
-  }
-}
-
-// Owner: wait until the nh helpers of this generation have written their rates.
-__device__ __forceinline__ void team_wait_helpers(TeamSlot* t, int nh, int lane)
-{
-  if (lane == 0) {
-    int it = 0;
-    while (ld_vol(&t->done) < nh && ++it < kTeamSpin) __nanosleep(32);
-    if (it >= kTeamSpin) atomicOr(t->err, kErrTimeout);
-    __threadfence_block();
-  }
-  __syncwarp();
-}
-
-// Owner, when its walker's interval is over: close the slot and release
-// the helpers attached to it.
-__device__ __forceinline__ void team_close(TeamSlot* t, int lane)
-{
-  if (lane == 0) {
-    atomicOr(&t->attach, kTeamClosed);
-    atomicExch(&t->pub, kTeamRelease);
-  }
-  __syncwarp();
-}
-
-__device__ __forceinline__ void team_open(TeamSlot* t, int lane)
-{
-  if (lane == 0) {
-    t->pub = 0;
-    t->sready = 0;
-    __threadfence_block();
-    atomicExch(&t->attach, 0);
-  }
-  __syncwarp();
-}
-
-// One lattice move c of an evaluation (Eq. 1 lattice, fixed-node rate): the
-// determinant and Jastrow ratios at the displaced position, p at the bond
-// midpoint on the double grid, the rate T_c into Td[c]. Reads the
-// evaluation's shared-memory state (projected inverse columns, positions,
-// rotation, caches, the Jastrow sums Sd); the same code serves the warp
-// that owns the walker and the warps that help it, so a rate has the same
-// bits whoever computes it.
-template <class NT, bool NJ, bool NC>
-__device__ __forceinline__ void candidate_m(const SysDev& S, const LatDev& L, const WarpMem& wm, const BlockMem& bm,
-                                            int c, df* Td, double* ratio_out)
+template <class NT, bool NJ, bool NC, bool MOVES = true>
+__device__ void warp_eval_m(const SysDev& S, const double* sC, const LatDev& L, const WarpMem& wm, int lane,
+                            double* ratio_out, double& b, df& bdf, double& el)
 {
   typedef Ar<NT> A;
-  const int nao = S.n_ao;
-  const int G = L.G, per_e = 6 * G;
+  const int N = S.N, nao = S.n_ao, nu = S.n_up;
+  const BlockMem bm = block_mem(S, const_cast<double*>(sC));
+  // projected inverse columns (FP64, or FP32 in the mixed mode), then
+  // converted with the positions
+  for (int idx = lane; idx < N * nao; idx += 32) {
+    int i = idx / nao, mu = idx % nao;
+    int spin = i < nu ? 0 : 1, l = i < nu ? i : i - nu, n = spin ? S.n_dn : nu;
+    const double* Am = spin ? wm.A + nu * nu : wm.A;
+    if (sizeof(NT) == sizeof(float)) {
+      float acc = 0.0f;
+      for (int m = 0; m < n; ++m) acc += bm.Cf[mu * S.n_mo + m] * (float)Am[m * n + l];
+      wm.vd[idx] = df_make(acc, 0.0f);
+    } else {
+      double acc = 0.0;
+      for (int m = 0; m < n; ++m) acc += sC[mu * S.n_mo + m] * Am[m * n + l];
+      wm.vd[idx] = A::store(A::from_double(acc));
+    }
+  }
+  for (int j = lane; j < 3 * N; j += 32) wm.xd[j] = A::store(A::from_double(wm.x[j]));
+  if (lane < 9) wm.Rd[lane] = A::store(A::from_double(wm.R[lane]));
+  __syncwarp();
+  // the caches pay in double-float arithmetic only, and exist only when
+  // the system's layout has room for them (NC is set otherwise: the
+  // kernels of such systems carry no cached code)
   constexpr bool kUsePairCache = sizeof(NT) == sizeof(df) && !NC;
-  {
-    const int i = c / per_e, rem = c - i * per_e, g = rem / 6, k = (rem % 6) >> 1;
+  if (kUsePairCache) {
+    fill_pair_cache<NT, NJ>(S, wm, lane);
+    fill_en_cache<NT>(S, wm, lane);
+    __syncwarp();
+  }
+  // local energy: Lp lanes per electron share its shells, electrons and nuclei
+  NT epart = A::zero();
+  if (N <= 32) {
+    const int Lp = 32 / N;
+    const int i = lane % N, part = lane / N;
+    const bool act = lane < N * Lp;
+    ElParts<NT> o;
+    if (act) el_parts_m<NT, NJ>(S, wm, i, part, Lp, bm, o);
+    else el_zero<NT>(o);
+    for (int pp = 1; pp < Lp; ++pp) {
+      int src = lane + pp * N;
+      el_combine<NT>(o, src < 32 ? src : lane, part == 0 && src < N * Lp);
+    }
+    if (part == 0 && act) {
+      wm.Sd[i] = A::store(o.S);
+      epart = el_local<NT>(o);
+    }
+  } else {
+    for (int i = lane; i < N; i += 32) {
+      ElParts<NT> o;
+      el_parts_m<NT, NJ>(S, wm, i, 0, 1, bm, o);
+      wm.Sd[i] = A::store(o.S);
+      epart = A::add(epart, el_local<NT>(o));
+    }
+  }
+  NT etot = warp_sum_m<NT>(epart);
+  el = A::to_double(etot) + S.V_nn;
+  __syncwarp();
+  if (!MOVES) {  // local energy and Jastrow sums only (the caller forms the moves)
+    b = 0.0;
+    bdf = A::store(A::zero());
+    return;
+  }
+  // the P lattice moves
+  const int G = L.G, per_e = 6 * G, P = N * per_e;
+  df* Td = reinterpret_cast<df*>(wm.T);  // rates stay in NT, stored as double-floats
+  for (int c = lane; c < P; c += 32) {
+    int i = c / per_e, rem = c - i * per_e, g = rem / 6, k = (rem % 6) >> 1;
     NT h = g ? A::c(L.ap_df) : A::c(L.a_df);
     if (c & 1) h = A::neg(h);
     const NT e0 = A::c(wm.Rd[k]), e1 = A::c(wm.Rd[3 + k]), e2 = A::c(wm.Rd[6 + k]);
@@ -1557,163 +1487,24 @@ __device__ __forceinline__ void candidate_m(const SysDev& S, const LatDev& L, co
     Td[c] = A::store(T);
     if (ratio_out) ratio_out[c] = A::to_double(rho);
   }
-}
-
-template <class NT, bool NJ, bool NC, bool TEAM>
-__device__ void warp_eval_m(const SysDev& S, const double* sC, const LatDev& L, const WarpMem& wm, int lane,
-                            double* ratio_out, double& b, df& bdf, double& el)
-{
-  typedef Ar<NT> A;
-  const int N = S.N, nao = S.n_ao, nu = S.n_up;
-  const BlockMem bm = block_mem(S, const_cast<double*>(sC));
-  // projected inverse columns (FP64, or FP32 in the mixed mode), then
-  // converted with the positions
-  for (int idx = lane; idx < N * nao; idx += 32) {
-    int i = idx / nao, mu = idx % nao;
-    int spin = i < nu ? 0 : 1, l = i < nu ? i : i - nu, n = spin ? S.n_dn : nu;
-    const double* Am = spin ? wm.A + nu * nu : wm.A;
-    if (sizeof(NT) == sizeof(float)) {
-      float acc = 0.0f;
-      for (int m = 0; m < n; ++m) acc += bm.Cf[mu * S.n_mo + m] * (float)Am[m * n + l];
-      wm.vd[idx] = df_make(acc, 0.0f);
-    } else {
-      double acc = 0.0;
-      for (int m = 0; m < n; ++m) acc += sC[mu * S.n_mo + m] * Am[m * n + l];
-      wm.vd[idx] = A::store(A::from_double(acc));
-    }
-  }
-  for (int j = lane; j < 3 * N; j += 32) wm.xd[j] = A::store(A::from_double(wm.x[j]));
-  if (lane < 9) wm.Rd[lane] = A::store(A::from_double(wm.R[lane]));
-  __syncwarp();
-  // the caches pay in double-float arithmetic only, and exist only when
-  // the system's layout has room for them (NC is set otherwise: the
-  // kernels of such systems carry no cached code)
-  constexpr bool kUsePairCache = sizeof(NT) == sizeof(df) && !NC;
-  if (kUsePairCache) {
-    fill_pair_cache<NT, NJ>(S, wm, lane);
-    fill_en_cache<NT>(S, wm, lane);
-    __syncwarp();
-  }
-  if (TEAM) team_publish(&g_team[threadIdx.x >> 5], lane);
-  // local energy: Lp lanes per electron share its shells, electrons and nuclei
-  NT epart = A::zero();
-  if (N <= 32) {
-    const int Lp = 32 / N;
-    const int i = lane % N, part = lane / N;
-    const bool act = lane < N * Lp;
-    ElParts<NT> o;
-    if (act) el_parts_m<NT, NJ>(S, wm, i, part, Lp, bm, o);
-    else el_zero<NT>(o);
-    for (int pp = 1; pp < Lp; ++pp) {
-      int src = lane + pp * N;
-      el_combine<NT>(o, src < 32 ? src : lane, part == 0 && src < N * Lp);
-    }
-    if (part == 0 && act) {
-      wm.Sd[i] = A::store(o.S);
-      epart = el_local<NT>(o);
-    }
-  } else {
-    for (int i = lane; i < N; i += 32) {
-      ElParts<NT> o;
-      el_parts_m<NT, NJ>(S, wm, i, 0, 1, bm, o);
-      wm.Sd[i] = A::store(o.S);
-      epart = A::add(epart, el_local<NT>(o));
-    }
-  }
-  NT etot = warp_sum_m<NT>(epart);
-  el = A::to_double(etot) + S.V_nn;
-  __syncwarp();
-  TeamSlot* team = nullptr;
-  if (TEAM && g_team[threadIdx.x >> 5].nh > 0) {
-    team = &g_team[threadIdx.x >> 5];
-    team_sums_ready(team, lane);
-  }
-  // the P lattice moves: alone, or (at the end of an interval, when other
-  // warps of the block have run out of walkers) in chunks shared with them
-  const int G = L.G, per_e = 6 * G, P = N * per_e;
-  df* Td = reinterpret_cast<df*>(wm.T);  // rates stay in NT, stored as double-floats
-  chunked_candidates<NT, NJ, NC>(S, L, wm, bm, team, P, lane, ratio_out);
-  if (TEAM && team) team_wait_helpers(team, team->nh, lane);
   __syncwarp();
   NT btot = warp_scan_m<NT>(Td, P, lane, A::zero(), nullptr, nullptr);
   bdf = A::store(btot);
   b = A::to_double(btot);
 }
 
-template <int PREC, bool NJ, bool NC, bool TEAM = false>
+template <int PREC, bool NJ, bool NC>
 __device__ __forceinline__ void warp_eval_any(const SysDev& S, const double* sC, const LatDev& L,
                                               const WarpMem& wm, int lane, double* ratio_out, double& b,
                                               df& bdf, double& el)
 {
   if (PREC == LRDMC_PRECISION_DF64) {
-    warp_eval_m<df, NJ, NC, TEAM>(S, sC, L, wm, lane, ratio_out, b, bdf, el);
+    warp_eval_m<df, NJ, NC>(S, sC, L, wm, lane, ratio_out, b, bdf, el);
   } else if (PREC == LRDMC_PRECISION_FP32) {
-    warp_eval_m<float, NJ, true, TEAM>(S, sC, L, wm, lane, ratio_out, b, bdf, el);
+    warp_eval_m<float, NJ, true>(S, sC, L, wm, lane, ratio_out, b, bdf, el);
   } else {
     warp_eval<NJ>(S, sC, L, wm, lane, ratio_out, b, el);
     bdf = df_make(0.0f, 0.0f);
-  }
-}
-
-// A warp whose fetch found the queue empty: attach to the open slot of its
-// block with the fewest helpers, take chunks of moves in every evaluation
-// its owner publishes, and move on when the owner releases it; return when
-// no warp of the block still runs a walker.
-template <class NT, bool NJ, bool NC>
-__device__ __noinline__ void team_help(const SysDev& S, const Layout& Lo, const LatDev& L, double* sC, int wib, int lane)
-{
-  TeamSlot* slots = g_team;
-  const BlockMem bm = block_mem(S, sC);
-  const int P = S.N * 6 * L.G;
-  for (;;) {
-    int o = -1, k = 0;
-    if (lane == 0) {
-      for (int tries = 0; tries < 64 && o < 0; ++tries) {
-        int best = -1, bc = 0x7fffffff;
-        for (int q = 0; q < kWarpsPerBlock; ++q) {
-          const int a = ld_vol(&slots[q].attach);
-          if (q == wib || a < 0) continue;  // itself, or closed (bit 31)
-          if (a < bc) { bc = a; best = q; }
-        }
-        if (best < 0) break;
-        if (atomicCAS(&slots[best].attach, bc, bc + 1) == bc) { o = best; k = bc; }
-      }
-    }
-    o = __shfl_sync(FULL_MASK, o, 0);
-    k = __shfl_sync(FULL_MASK, k, 0);
-    if (o < 0) return;
-    TeamSlot* t = &slots[o];
-    const WarpMem wm = warp_mem(Lo, S, sC + Lo.head + o * Lo.smem_warp);
-    int last = 0;
-    for (;;) {
-      int g = 0, state = 0;  // state 0: take part in generation g, 1: released, 2: timed out
-      if (lane == 0) {
-        int it = 0;
-        for (;;) {
-          const int pub = ld_vol(&t->pub);
-          if (pub == kTeamRelease) { state = 1; break; }
-          g = pub >> 4;
-          if (g > last && k < (pub & 15)) break;
-          if (++it >= kTeamSpin) { state = 2; break; }
-          __nanosleep(64);
-        }
-        if (state == 0) {
-          it = 0;
-          while (ld_vol(&t->sready) < g && ++it < kTeamSpin) __nanosleep(32);
-          if (it >= kTeamSpin) state = 2;
-        }
-        if (state == 2) atomicOr(slots[wib].err, kErrTimeout);
-        __threadfence_block();
-      }
-      state = __shfl_sync(FULL_MASK, state, 0);
-      g = __shfl_sync(FULL_MASK, g, 0);
-      __syncwarp();  // orders lane 0's observation before every lane's reads
-      if (state == 2) return;
-      if (state == 1) break;
-      chunked_candidates<NT, NJ, NC>(S, L, wm, bm, t, P, lane, nullptr);
-      if (lane == 0) atomicAdd(&t->done, 1);
-      last = g;
-    }
   }
 }
 
@@ -1973,21 +1764,8 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
   // interval
   const uint64_t k = *P.kdev;
   const bool recompute = k > 0 && P.recompute_every > 0 && k % (uint64_t)P.recompute_every == 0;
+  stage_coefficients(S, sC);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  // tail helpers (the FP32-pipe evaluations only): every slot starts closed
-  constexpr bool kTeam = PR != LRDMC_PRECISION_FP64;
-  TeamSlot* team = (kTeam && P.helpers) ? &g_team[wib] : nullptr;
-  if (kTeam && lane == 0) {
-    g_team[wib].attach = kTeamClosed;
-    g_team[wib].pub = 0;
-    g_team[wib].sready = 0;
-    g_team[wib].next = 0;
-    g_team[wib].done = 0;
-    g_team[wib].gen = 0;
-    g_team[wib].nh = 0;
-    g_team[wib].err = P.err;
-  }
-  stage_coefficients(S, sC);  // ends with __syncthreads
   WarpMem wm = warp_mem(Lo, S, sC + Lo.head + wib * Lo.smem_warp);
   const int P_moves = S.N * 6 * L.G;
   const BlockMem bm = block_mem(S, sC);
@@ -1996,7 +1774,6 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
     if (lane == 0) idx = atomicAdd(P.counter, 1);
     idx = __shfl_sync(FULL_MASK, idx, 0);
     if (idx >= P.W) break;
-    if (team) team_open(team, lane);
     const int s = P.order[idx];
     const int src = P.parent[s];
     double b, el;
@@ -2074,7 +1851,7 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
       __syncwarp();
       rotation_matrix_warp<PR>(b1, wm.R, lane, S);
       __syncwarp();
-      warp_eval_any<PR, NJ, NC, kTeam>(S, sC, L, wm, lane, nullptr, b, bdf, el);
+      warp_eval_any<PR, NJ, NC>(S, sC, L, wm, lane, nullptr, b, bdf, el);
       ++jumps;
       if (!isfinite(el) || !isfinite(b)) {
         if (lane == 0) atomicOr(P.err, kErrNonFinite);
@@ -2085,7 +1862,6 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
         break;
       }
     }
-    if (team) team_close(team, lane);
     store_record(Lo, P.rec_dst + (size_t)s * Lo.rec, wm, lane, b, el);
     if (lane == 0) {
       P.logw[s] = logw;
@@ -2094,11 +1870,6 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
       P.jumps[s] = jumps;
     }
     __syncwarp();
-  }
-  // out of walkers: help the warps of this block that still run one
-  if (kTeam && team) {
-    if (PR == LRDMC_PRECISION_DF64) team_help<df, NJ, NC>(S, Lo, L, sC, wib, lane);
-    else team_help<float, NJ, true>(S, Lo, L, sC, wib, lane);
   }
 }
 
@@ -2604,6 +2375,372 @@ cudaError_t launch_evaluate(const SysDev& S, const Layout& Lo, const LatDev& L, 
 {
   LRDMC_DISPATCH(S, Lo, return launch_evaluate_t<V>(S, Lo, L, n, x, rot, ratio, T, b, el, err, st));
   return cudaErrorInvalidValue;
+}
+
+// ----------------------------------------------------------------------------
+// Tensor-core form of the orbital contraction (tcgen05, FP32 mode).
+//
+// The literal contraction of the displaced positions' basis values with the
+// MO coefficients, phi_m(r'_c) = sum_mu chi_mu(r'_c) C[mu][m], as a GEMM on
+// the fifth-generation tensor cores: one CTA of four warps evaluates four
+// configurations in lock step; per round every lane computes the basis
+// values of one lattice move (FP32) and writes them, split into bfloat16
+// high and low parts, as one row of a 128-row A tile in shared memory;
+// thread 0 issues D = A_hi B_hi + A_hi B_lo + A_lo B_hi (B = C^T split the
+// same way; three bf16 products carry about 16 significant bits) into a
+// 128 x 32 FP32 accumulator in tensor memory; each warp reads its 32 rows
+// back (tcgen05.ld) and finishes its moves: the determinant ratio
+// sum_m phi_m Ainv[m][l_i] (FP32), the Jastrow ratio and the rate, as the
+// FP32 mode's projected form does. Shared-memory operands use the
+// canonical K-major layout without swizzle: 8 x 16-byte core matrices,
+// adjacent in K at LBO = 128 bytes, 8-row groups at SBO = 16 Kp bytes.
+// Every wait on the MMA's mbarrier is bounded; a wait that runs out sets
+// kErrTimeout, waits once more (bounded) and frees the tensor memory.
+// ----------------------------------------------------------------------------
+constexpr int kTcRows = 128;    // A tile rows: 4 warps x 32 moves
+constexpr int kTcN = 32;        // accumulator columns (orbitals, padded)
+constexpr int kTcCols = 32;     // tensor-memory columns allocated
+constexpr int kTcSpin = 1 << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t tc_desc(const void* base, uint32_t lbo, uint32_t sbo)
+{
+  uint64_t d = (uint64_t)((smem_u32(base) & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of sm_100-class tensor cores; no swizzle, base offset 0
+  return d;
+}
+
+// kind::f16 instruction descriptor: D F32, A and B BF16, both K-major, N, M.
+__host__ __device__ constexpr uint32_t tc_idesc_bf16(int M, int N)
+{
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, int accumulate)
+{
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+      :: "r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accumulate) : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* mbar)
+{
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               :: "r"(smem_u32(mbar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, int count)
+{
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(mbar)), "r"(count) : "memory");
+}
+
+// Non-blocking test of the phase with the given parity.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* mbar, uint32_t parity)
+{
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok) : "r"(smem_u32(mbar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase of the MMA barrier (kTcSpin polls, a short
+// sleep between them: well under a second); false when it ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, uint32_t parity)
+{
+  for (int it = 0; it < kTcSpin; ++it) {
+    if (mbar_test_wait(mbar, parity)) return true;
+    __nanosleep(20);
+  }
+  return false;
+}
+
+// 32 consecutive FP32 columns of this thread's tensor-memory lane.
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float* v)
+{
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// x as bfloat16 high part plus the bfloat16 of the remainder (round to
+// nearest even both times): x - hi - lo is about 2^-17 |x|.
+__device__ __forceinline__ void bf16_split(float x, uint16_t& hi, uint16_t& lo)
+{
+  const __nv_bfloat16 h = __float2bfloat16_rn(x);
+  const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+  hi = __bfloat16_as_ushort(h);
+  lo = __bfloat16_as_ushort(l);
+}
+
+// Byte offset of element (row, k) in a K-major tile without swizzle.
+__device__ __forceinline__ uint32_t tc_off(int row, int k, int Kp)
+{
+  return (uint32_t)((row >> 3) * (Kp * 16) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// Writes one row of the A tiles, value by value in K order.
+struct TcRowWriter {
+  char* hi;
+  char* lo;
+  int row, Kp, k;
+  __device__ __forceinline__ void put(float v)
+  {
+    uint16_t h, l;
+    bf16_split(v, h, l);
+    const uint32_t o = tc_off(row, k, Kp);
+    *reinterpret_cast<uint16_t*>(hi + o) = h;
+    *reinterpret_cast<uint16_t*>(lo + o) = l;
+    ++k;
+  }
+  // zeros up to Kp (the padding of K, or a whole inactive row)
+  __device__ __forceinline__ void finish()
+  {
+    while (k < Kp) put(0.0f);
+  }
+};
+
+// Basis values chi_mu(p) of every AO (FP32, in AO order) into the row
+// writer, and the electron-nucleus Jastrow terms into jen.
+template <bool NJ>
+__device__ __forceinline__ void tc_basis_row(const SysDev& S, const float p[3], const BlockMem& bm, TcRowWriter& w,
+                                             float& jen)
+{
+  typedef Ar<float> A;
+  jen = 0.0f;
+  for (int I = 0; I < S.n_nuc; ++I) {
+    const float d[3] = {p[0] - S.D.nuc[I][0].hi, p[1] - S.D.nuc[I][1].hi, p[2] - S.D.nuc[I][2].hi};
+    const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const float r = sqrtf(r2);
+    if (S.en_b1[I] != 0.0) jen -= S.D.en_b1[I].hi * r / (S.D.en_b2.hi * r + 1.0f);
+    if (NJ) jen += nj_value_m<float>(S, 2 + S.nj_species[I], r);
+    float e = 0.0f;
+    for (int q = S.nuc_shell_begin[I]; q < S.nuc_shell_begin[I + 1]; ++q) {
+      const ShellDev& sh = S.sh[q];
+      const DfShell& dsh = S.D.sh[q];
+      if (sh.kind == 0 && !sh.same_exp) e = expf(-dsh.zeta.hi * r);
+      const float Rv = radial_value_m<float>(S, sh, dsh, r, r2, e, bm);
+      float Sv[5];
+      const int nf = solid_m<float>(sh.l, d, Sv);
+      w.k = sh.ao_offset;
+      for (int f = 0; f < nf; ++f) w.put(Sv[f] * Rv);
+    }
+  }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+k_evaluate_tc(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, int n, const double* x,
+              const double* rot, double* ratio, double* T, double* b_out, double* el_out, int* err, int Kp,
+              int tile_off)
+{
+  constexpr bool NJ = (PREC & 8) != 0;
+  typedef Ar<float> A;
+  extern __shared__ double smem[];
+  __shared__ __align__(8) uint64_t s_mbar;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_bad;
+  double* sC = smem;
+  const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+  char* tiles = reinterpret_cast<char*>(smem) + tile_off;
+  const int tileA = kTcRows * Kp * 2, tileB = kTcN * Kp * 2;
+  char* Ah = tiles;
+  char* Al = Ah + tileA;
+  char* Bh = Al + tileA;
+  char* Bl = Bh + tileB;
+  stage_coefficients(S, sC);
+  const BlockMem bm = block_mem(S, sC);
+  // B = C^T (orbital m, AO k), split into bfloat16 high and low parts
+  for (int idx = tid; idx < kTcN * Kp; idx += blockDim.x) {
+    const int m = idx / Kp, k = idx - m * Kp;
+    const float v = (m < S.n_mo && k < S.n_ao) ? (float)S.C[k * S.n_mo + m] : 0.0f;
+    uint16_t h, l;
+    bf16_split(v, h, l);
+    const uint32_t o = tc_off(m, k, Kp);
+    *reinterpret_cast<uint16_t*>(Bh + o) = h;
+    *reinterpret_cast<uint16_t*>(Bl + o) = l;
+  }
+  if (wib == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&s_tmem)), "r"(kTcCols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(&s_mbar, 1);
+    s_bad = 0;
+  }
+  fence_async_shared();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  // this warp's configuration: inverses, then the local energy and the
+  // Jastrow sums of the FP32 evaluation
+  const int c = blockIdx.x * kWarpsPerBlock + wib;
+  WarpMem wm = warp_mem(Lo, S, sC + Lo.head + wib * Lo.smem_warp);
+  bool ok = c < n;
+  double b = 0.0, el = 0.0;
+  df bdf;
+  if (ok) {
+    for (int j = lane; j < 3 * Lo.N; j += 32) wm.x[j] = x[(size_t)c * 3 * Lo.N + j];
+    for (int j = lane; j < 9; j += 32) wm.R[j] = rot[(size_t)c * 9 + j];
+    __syncwarp();
+    ok = warp_inverse(S, sC, wm.x, 0, wm.A, wm.scr, lane);
+    ok = ok && warp_inverse(S, sC, wm.x, 1, wm.A + Lo.nu * Lo.nu, wm.scr, lane);
+    if (!ok && lane == 0) atomicOr(err, kErrSingular);
+    if (ok) warp_eval_m<float, NJ, true, false>(S, sC, L, wm, lane, nullptr, b, bdf, el);
+  }
+  const int N = S.N, G = L.G, per_e = 6 * G, P = N * per_e;
+  const int rounds = (P + 31) / 32;
+  df* Td = reinterpret_cast<df*>(wm.T);
+  const uint32_t idesc = tc_idesc_bf16(kTcRows, kTcN);
+  uint32_t phase = 0;
+  for (int rd = 0; rd < rounds; ++rd) {
+    const int cand = rd * 32 + lane;
+    const bool act = ok && cand < P;
+    TcRowWriter w;
+    w.hi = Ah;
+    w.lo = Al;
+    w.row = wib * 32 + lane;
+    w.Kp = Kp;
+    w.k = 0;
+    float jsum = 0.0f, pm = 1.0f;
+    int i = 0, g = 0;
+    if (act) {
+      i = cand / per_e;
+      const int rem = cand - i * per_e, k = (rem % 6) >> 1;
+      g = rem / 6;
+      float h = g ? L.ap_df.hi : L.a_df.hi;
+      if (cand & 1) h = -h;
+      const float e0 = wm.Rd[k].hi, e1 = wm.Rd[3 + k].hi, e2 = wm.Rd[6 + k].hi;
+      const float ri[3] = {wm.xd[3 * i].hi, wm.xd[3 * i + 1].hi, wm.xd[3 * i + 2].hi};
+      const float p[3] = {ri[0] + h * e0, ri[1] + h * e1, ri[2] + h * e2};
+      float jen;
+      tc_basis_row<NJ>(S, p, bm, w, jen);
+      jsum = jastrow_ee_m<float, NJ>(S, wm.xd, i, p) + jen;
+      if (G == 2) {
+        const float hh = 0.5f * h;
+        const float mid[3] = {ri[0] + hh * e0, ri[1] + hh * e1, ri[2] + hh * e2};
+        pm = p_weight_m<float>(S, L, mid, bm);
+      }
+    }
+    w.finish();
+    fence_async_shared();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      for (int kk = 0; kk < Kp / 16; ++kk) {
+        const uint32_t off = (uint32_t)kk * 256;
+        const uint64_t ah = tc_desc(Ah + off, 128, Kp * 16), al = tc_desc(Al + off, 128, Kp * 16);
+        const uint64_t bh = tc_desc(Bh + off, 128, Kp * 16), bl = tc_desc(Bl + off, 128, Kp * 16);
+        tc_mma(tmem, ah, bh, idesc, kk > 0);
+        tc_mma(tmem, ah, bl, idesc, 1);
+        tc_mma(tmem, al, bh, idesc, 1);
+      }
+      tc_commit(&s_mbar);
+    }
+    if (!mbar_wait_bounded(&s_mbar, phase)) s_bad = 1;
+    phase ^= 1u;
+    __syncthreads();
+    if (s_bad) break;
+    tc_fence_after();
+    float phi[32];
+    tc_ld32(tmem + ((uint32_t)(wib * 32) << 16), phi);
+    if (act) {
+      const int nu = S.n_up, spin = i < nu ? 0 : 1, l = i < nu ? i : i - nu, ns = spin ? S.n_dn : nu;
+      const double* Am = spin ? wm.A + nu * nu : wm.A;
+      float rdet = 0.0f;
+#pragma unroll
+      for (int m = 0; m < kTcN; ++m)
+        if (m < ns) rdet += phi[m] * (float)Am[m * ns + l];
+      const float rho = rdet * expf(jsum - wm.Sd[i].hi);
+      float wgt = 1.0f;
+      if (G == 2) wgt = g ? 1.0f - pm : pm;
+      float Tc = 0.0f;
+      if (rho > 0.0f) Tc = wgt * (g ? L.inv2ap2_df.hi : L.inv2a2_df.hi) * rho;
+      Td[cand] = A::store(Tc);
+      if (ratio) ratio[(size_t)c * P + cand] = (double)rho;
+    }
+    tc_fence_before();
+    __syncthreads();  // every lane has read the accumulator and the A tiles are free
+  }
+  if (s_bad) {
+    // the MMA barrier did not complete in time: report, wait once more for
+    // the tensor core to finish with this CTA's memory, then free it
+    if (tid == 0) {
+      atomicOr(err, kErrTimeout);
+      mbar_wait_bounded(&s_mbar, phase ^ 1u);
+    }
+    __syncthreads();
+  } else if (ok) {
+    __syncwarp();
+    const float btot = warp_scan_m<float>(Td, P, lane, 0.0f, nullptr, nullptr);
+    b = (double)btot;
+    if (T)
+      for (int j = lane; j < P; j += 32) T[(size_t)c * P + j] = (double)Td[j].hi;
+    if (lane == 0) {
+      if (b_out) b_out[c] = b;
+      if (el_out) el_out[c] = el;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (wib == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTcCols) : "memory");
+  }
+}
+
+// Shared memory of the tensor-core evaluation: the evaluation's own layout,
+// then (128-byte aligned) the A and B tiles in both parts.
+static int tc_tile_offset(const Layout& Lo) { return (Lo.smem_block_bytes + 127) & ~127; }
+static int tc_smem_bytes(const Layout& Lo, int Kp) { return tc_tile_offset(Lo) + 2 * (kTcRows + kTcN) * Kp * 2; }
+
+int evaluate_tc_smem_bytes(const SysDev& S, const Layout& Lo)
+{
+  const int Kp = (S.n_ao + 15) & ~15;
+  return tc_smem_bytes(Lo, Kp);
+}
+
+cudaError_t launch_evaluate_tc(const SysDev& S, const Layout& Lo, const LatDev& L, int n, const double* x,
+                               const double* rot, double* ratio, double* T, double* b, double* el, int* err,
+                               cudaStream_t st)
+{
+  if (n <= 0) return cudaSuccess;
+  const int Kp = (S.n_ao + 15) & ~15;
+  const int bytes = tc_smem_bytes(Lo, Kp);
+  const int blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  cudaError_t e;
+  if (S.nj_on) {
+    e = set_smem((const void*)k_evaluate_tc<LRDMC_PRECISION_FP32 | kNjBit>, bytes);
+    if (e != cudaSuccess) return e;
+    k_evaluate_tc<LRDMC_PRECISION_FP32 | kNjBit><<<blocks, kWarpsPerBlock * 32, bytes, st>>>(
+        S, Lo, L, n, x, rot, ratio, T, b, el, err, Kp, tc_tile_offset(Lo));
+  } else {
+    e = set_smem((const void*)k_evaluate_tc<LRDMC_PRECISION_FP32>, bytes);
+    if (e != cudaSuccess) return e;
+    k_evaluate_tc<LRDMC_PRECISION_FP32><<<blocks, kWarpsPerBlock * 32, bytes, st>>>(
+        S, Lo, L, n, x, rot, ratio, T, b, el, err, Kp, tc_tile_offset(Lo));
+  }
+  return cudaGetLastError();
 }
 
 

@@ -63,11 +63,12 @@ def el_scale(system, x, el_ref):
 
 # ------------------------------------------------------------------ projection
 RTOL = 1e-10
-# Double-floats share float's exponent range: an exponential whose value
-# lies below float's smallest normal number (2^-126) comes out as zero, so a
-# weight p = exp(-x) of Eq. 3 far from the nucleus carries an absolute error
-# up to 2^-126 in the double-float and FP32 modes.
-W_ABS = 2.0 ** -126
+# Double-floats share float's exponent range, and the evaluation's
+# exponential returns zero below e^-87 (about 2^-125.5, just above float's
+# smallest normal number): a weight p = exp(-x) of Eq. 3 far from the
+# nucleus carries an absolute error up to that size in the double-float and
+# FP32 modes.
+W_ABS = 2.0 ** -125
 # A decision whose uniform lies within this distance of a bin edge (relative
 # to the quantity it is compared with: tau for the waiting time, b for the
 # heat bath, the total weight for a comb tooth) may go either way between

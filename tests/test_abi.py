@@ -143,11 +143,3 @@ def test_static_eval_limit_matches_header(pkg):
     m = re.search(r"#define\s+LRDMC_STATIC_EVAL_MAX\s+(\d+)", text)
     assert m and int(m.group(1)) == pkg.STATIC_EVAL_MAX
 
-
-def test_set_tail_helpers_arguments(pkg):
-    """The tail-helper switch takes 0 or 1; anything else is LRDMC_ERR_ARG."""
-    g = pkg.LrdmcSystem(S.helium())
-    g.set_tail_helpers(False).set_tail_helpers(True)
-    with pytest.raises(pkg.LrdmcError) as e:
-        g._check(pkg.load_library().lrdmc_set_tail_helpers(g.h, 2))
-    assert e.value.status == pkg.ERR_ARG
