@@ -19,6 +19,8 @@ Usage: python -m paper_1909_01589_gb300.experiments [--systems He,Ne,Ar,Kr]
        [--steps 1000] [--out results/single_vs_double.json]
        python -m paper_1909_01589_gb300.experiments --neural --systems Ne,Ar
        [--steps 600] [--out results/neural_vs_pade.json]
+       python -m paper_1909_01589_gb300.experiments --mixed --systems Ne,Ar,Kr
+       [--out results/mixed_vs_parity.json]
        python -m paper_1909_01589_gb300.experiments --extrapolate [--neural] --systems He
        [--steps 2000] [--out results/extrapolation_he.json]
 """
@@ -263,6 +265,70 @@ def extrapolation(name="He", a_values=(0.4, 0.3, 0.2, 0.15, 0.1), W=8192, steps=
     return out
 
 
+def mixed_vs_parity(names=("Ne", "Ar", "Kr"), steps=None, equil=200, seed=7):
+    """Energy of the mixed-precision mode (FP32 evaluation, FP64 state)
+    against the FP64-parity form (double-float evaluation, whose
+    trajectories equal the FP64 mode's) on the same start population and
+    random streams, so the two projections stay correlated while their
+    decisions agree: the difference Delta E = mean_k(e32_k - e64_k) and its
+    blocked error come from the difference series itself (correlated
+    sampling), next to each mode's own energy and error. Workloads: Ne at
+    a = 0.2 with 4096 walkers (the bench workload), Ar and Kr at
+    a = 1/(3.5 Z) with 16384 walkers, this work's double grid, tau for
+    about 10 jumps per walker per interval."""
+    import torch
+
+    import lrdmc_synth as S
+
+    from . import PRECISION_FP32
+
+    work = {"Ne": (4096, 0.2, 20000), "Ar": (16384, 1.0 / 63.0, 3000), "Kr": (16384, 1.0 / 126.0, 1200),
+            "He": (4096, 0.2, 20000)}
+    rows = []
+    for name in names:
+        system = S.make_system(name)
+        W, a, n_default = work[name]
+        n = steps or n_default
+        e_trial = DEFAULTS[name][1]
+        sp = Spacing(THIS_WORK)
+        tau = 0.025 if name == "Ne" else _tau_for(system, a, sp, 10.0, seed)
+        x0 = S.initial_positions(system, W, seed)
+        res = {}
+        for label, prec in (("parity", PRECISION_DF64), ("mixed", PRECISION_FP32)):
+            g = LrdmcSystem(system).set_precision(prec)
+            g.init_walkers(torch.tensor(x0, device="cuda"), seed=seed, tau=tau, e_trial=e_trial, recompute_every=5,
+                           trace_capacity=n + equil + 4)
+            g.step(equil, a, sp)
+            g.sync()
+            torch.cuda.synchronize()
+            m0 = g.moves()
+            t0 = time.perf_counter()
+            g.step(n, a, sp)
+            g.sync()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            e, w, j = g.energy_trace()
+            e = e[equil:]
+            err, _ = stats.reblock(e)
+            res[label] = {"energy": float(np.mean(e)), "error": err, "seconds": dt,
+                          "moves_per_s": (g.moves() - m0) / dt, "efficiency": stats.efficiency(e, dt), "trace": e}
+        d = res["mixed"]["trace"] - res["parity"]["trace"]
+        derr, _ = stats.reblock(d)
+        corr = float(np.corrcoef(res["mixed"]["trace"], res["parity"]["trace"])[0, 1])
+        row = {"system": name, "walkers": W, "a": a, "tau": tau, "intervals": n, "equilibration": equil,
+               "delta_E_Ha": float(np.mean(d)), "delta_E_error_Ha": derr, "trace_correlation": corr,
+               "independent_error_Ha": float(np.hypot(res["mixed"]["error"], res["parity"]["error"])),
+               "efficiency_ratio": res["mixed"]["efficiency"] / res["parity"]["efficiency"]}
+        for label in ("parity", "mixed"):
+            row[label] = {k: v for k, v in res[label].items() if k != "trace"}
+        rows.append(row)
+        print(f"{name}: E_parity {row['parity']['energy']:.5f}({1e3 * row['parity']['error']:.2f} mHa) "
+              f"E_mixed {row['mixed']['energy']:.5f}({1e3 * row['mixed']['error']:.2f}) "
+              f"dE {1e3 * row['delta_E_Ha']:+.3f} +- {1e3 * derr:.3f} mHa (corr {corr:.3f}); "
+              f"moves/s {row['parity']['moves_per_s']:.3g} -> {row['mixed']['moves_per_s']:.3g}", flush=True)
+    return rows
+
+
 def fit_a0(a_values, E, err):
     """Weighted least-squares fit E(a) = E0 + k1 a^2 + k2 a^4 (the lattice
     error of LRDMC is even in a; the three-parameter form of the paper's
@@ -347,9 +413,17 @@ def main():
     ap.add_argument("--out", default="results/single_vs_double.json")
     ap.add_argument("--summarize", nargs="*", help="only write the markdown table of these result files")
     ap.add_argument("--neural", action="store_true", help="the neural Jastrow against Pade instead")
+    ap.add_argument("--mixed", action="store_true",
+                    help="mixed-precision (FP32 evaluation) energy against the FP64-parity form instead")
     ap.add_argument("--extrapolate", action="store_true",
                     help="E(a) and the a -> 0 fit instead (first system); with --neural, with the trained term")
     args = ap.parse_args()
+    if args.mixed:
+        rows = mixed_vs_parity(args.systems.split(","), steps=args.steps if args.steps != 1000 else None,
+                               equil=args.equil)
+        os.makedirs(os.path.dirname(args.out) or ".", exist_ok=True)
+        json.dump(rows, open(args.out, "w"), indent=1)
+        return
     if args.extrapolate:
         row = extrapolation(args.systems.split(",")[0], steps=args.steps, equil=args.equil, neural=args.neural)
         os.makedirs(os.path.dirname(args.out) or ".", exist_ok=True)
