@@ -412,6 +412,15 @@ LRDMC_API lrdmc_status lrdmc_batch_set_groups(lrdmc_batch_t batch, const int* gr
  * L1/shared split. A launch attribute of the batch's launches; lrdmc_step
  * is unaffected. Takes effect at the next batch_step. */
 LRDMC_API lrdmc_status lrdmc_batch_set_carveout(lrdmc_batch_t batch, int carveout);
+/* Pipelined schedule (on = 1; 0, the default, is the fork/join schedule
+ * above). Every system's interval kernel runs on the batch stream in group
+ * order (systems of equal group in index order), each after the first
+ * launched with programmatic stream serialization: its blocks start on the
+ * SMs that the previous system's blocks free once its walker queue is
+ * empty, so one system's end-of-interval tail overlaps the next system's
+ * start; the reconfiguration kernels follow the chain. Results do not
+ * depend on the schedule. Takes effect at the next batch_step. */
+LRDMC_API lrdmc_status lrdmc_batch_set_pipelined(lrdmc_batch_t batch, int on);
 /* The batch's own stream (a cudaStream_t), for timing with events. */
 LRDMC_API lrdmc_status lrdmc_batch_stream(lrdmc_batch_t batch, void** stream);
 LRDMC_API const char* lrdmc_batch_last_error(lrdmc_batch_t batch);

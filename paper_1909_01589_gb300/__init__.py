@@ -36,7 +36,7 @@ EXPORTED = [
     "lrdmc_destroy", "lrdmc_nj_n_params", "lrdmc_set_neural_jastrow", "lrdmc_base_terms", "lrdmc_nj_forward",
     "lrdmc_nj_backward", "lrdmc_set_interval_blocks", "lrdmc_interval_blocks", "lrdmc_batch_create",
     "lrdmc_batch_step", "lrdmc_batch_sync", "lrdmc_batch_stream", "lrdmc_batch_last_error", "lrdmc_batch_destroy",
-    "lrdmc_batch_set_groups", "lrdmc_batch_set_carveout",
+    "lrdmc_batch_set_groups", "lrdmc_batch_set_carveout", "lrdmc_batch_set_pipelined",
 ]
 NJ_MAX_CH, NJ_MAX_FEAT, NJ_HIDDEN, NJ_MAX_CELLS = 8, 12, 64, 8192
 
@@ -167,6 +167,8 @@ def load_library():
     L.lrdmc_batch_sync.argtypes = [vp]
     L.lrdmc_batch_set_carveout.restype = i
     L.lrdmc_batch_set_carveout.argtypes = [vp, i]
+    L.lrdmc_batch_set_pipelined.restype = i
+    L.lrdmc_batch_set_pipelined.argtypes = [vp, i]
     L.lrdmc_batch_set_groups.restype = i
     L.lrdmc_batch_set_groups.argtypes = [vp, vp]
     L.lrdmc_batch_stream.restype = i
@@ -553,6 +555,12 @@ class LrdmcBatch:
         self._check(load_library().lrdmc_batch_set_carveout(self.h, int(carveout)))
 
     @property
+    def set_pipelined(self, on=True):
+        """Chain the systems' interval kernels on one stream with
+        programmatic stream serialization (each starts while the previous
+        one drains its walkers); off: the fork/join groups."""
+        self._check(load_library().lrdmc_batch_set_pipelined(self.h, int(bool(on))))
+
     def stream_ptr(self):
         p = ct.c_void_p()
         self._check(load_library().lrdmc_batch_stream(self.h, ct.byref(p)))

@@ -12,7 +12,9 @@ results. ``tune`` chooses the grid sizes by measurement:
 2. candidate plans: every system concurrent with its default grid, or
    with grids proportional to w_i (so that the branches finish together)
    at several oversubscription factors; every system in turn on the whole
-   GPU; the heaviest system alone, then the rest concurrently;
+   GPU; the same order pipelined (programmatic dependent launches: each
+   system's kernel starts on the SMs the previous one frees in its tail);
+   the heaviest system alone, then the rest concurrently;
 3. each plan is timed over a few batched steps with CUDA events on the
    batch stream, and the fastest is kept.
 
@@ -57,23 +59,27 @@ def candidate_grids(defaults, work, need, factors=(1.0, 1.5, 2.0)):
 
 
 def candidate_plans(defaults, work, need):
-    """Execution plans [(name, groups, blocks, carveout)]: every system
-    concurrent (with each candidate grid, under the default and under the
-    maximal shared-memory carveout), every system in turn on the whole GPU
-    (heaviest first), and the heaviest alone followed by the rest
+    """Execution plans [(name, groups, blocks, carveout, pipelined)]: every
+    system concurrent (with each candidate grid, under the default and
+    under the maximal shared-memory carveout), every system in turn on the
+    whole GPU (heaviest first), the same order pipelined (each system's
+    interval kernel starting while the previous one drains, heaviest first
+    and lightest first), and the heaviest alone followed by the rest
     concurrently (grids proportional to the rest's work)."""
     n = len(defaults)
     cap = [max(1, min(int(d), int(m))) for d, m in zip(defaults, need)]
     grids = candidate_grids(defaults, work, need)
-    plans = [("concurrent " + name, [0] * n, b, -1) for name, b in grids]
-    plans += [("concurrent " + name + ", max shared carveout", [0] * n, b, 100) for name, b in grids]
+    plans = [("concurrent " + name, [0] * n, b, -1, 0) for name, b in grids]
+    plans += [("concurrent " + name + ", max shared carveout", [0] * n, b, 100, 0) for name, b in grids]
     if n == 1:
         return plans
     by_work = sorted(range(n), key=lambda i: -work[i])
     serial = [0] * n
     for rank, i in enumerate(by_work):
         serial[i] = rank
-    plans.append(("serial", serial, list(cap), -1))
+    plans.append(("serial", serial, list(cap), -1, 0))
+    plans.append(("pipelined, heaviest first", serial, list(cap), -1, 1))
+    plans.append(("pipelined, lightest first", [n - 1 - r for r in serial], list(cap), -1, 1))
     heavy = by_work[0]
     rest = [i for i in range(n) if i != heavy]
     rest_grids = candidate_grids([defaults[i] for i in rest], [work[i] for i in rest], [need[i] for i in rest],
@@ -83,13 +89,13 @@ def candidate_plans(defaults, work, need):
         for i, bi in zip(rest, b):
             blocks[i] = bi
         split = [0 if i == heavy else 1 for i in range(n)]
-        plans.append((f"heaviest alone, rest concurrent {name}", split, blocks, -1))
-        plans.append((f"heaviest alone, rest concurrent {name}, max shared carveout", split, blocks, 100))
+        plans.append((f"heaviest alone, rest concurrent {name}", split, blocks, -1, 0))
+        plans.append((f"heaviest alone, rest concurrent {name}, max shared carveout", split, blocks, 100, 0))
     return plans
 
 
 def choose(timings):
-    """The fastest plan; timings = [(name, groups, blocks, carveout, ms)]."""
+    """The fastest plan; timings = [(name, groups, blocks, carveout, pipelined, ms)]."""
     return min(timings, key=lambda t: t[-1])
 
 
@@ -131,24 +137,27 @@ def tune(batch, a, spacing, trial_steps=3):
         g.step(1, ai, sp)  # first evaluation outside the timing
         work.append(_time_system_steps(torch, g, trial_steps, ai, sp))
     timings = []
-    for name, groups, blocks, carve in candidate_plans(defaults, work, need):
+    for name, groups, blocks, carve, pipe in candidate_plans(defaults, work, need):
         batch.set_groups(groups)
         batch.set_carveout(carve)
+        batch.set_pipelined(pipe)
         for g, b in zip(systems, blocks):
             g.set_interval_blocks(b)
         batch.step(1)  # capture the graphs of this plan
         batch.step(1)
         batch.sync()
-        timings.append((name, groups, blocks, carve, _time_batch_steps(torch, batch, trial_steps)))
-    name, groups, blocks, carve, ms = choose(timings)
+        timings.append((name, groups, blocks, carve, pipe, _time_batch_steps(torch, batch, trial_steps)))
+    name, groups, blocks, carve, pipe, ms = choose(timings)
     batch.set_groups(groups)
     batch.set_carveout(carve)
+    batch.set_pipelined(pipe)
     for g, b in zip(systems, blocks):
         g.set_interval_blocks(b)
     return {"alone_ms_per_step": work, "sum_alone_ms": float(np.sum(work)), "defaults": defaults,
-            "candidates": [{"name": n, "groups": gr, "blocks": b, "carveout": c, "ms_per_step": t}
-                           for n, gr, b, c, t in timings],
-            "choice": {"name": name, "groups": groups, "blocks": blocks, "carveout": carve, "ms_per_step": ms}}
+            "candidates": [{"name": n, "groups": gr, "blocks": b, "carveout": c, "pipelined": pp, "ms_per_step": t}
+                           for n, gr, b, c, pp, t in timings],
+            "choice": {"name": name, "groups": groups, "blocks": blocks, "carveout": carve, "pipelined": pipe,
+                       "ms_per_step": ms}}
 
 
 def tau_for(pkg, system, a, spacing, jumps, x, rot):

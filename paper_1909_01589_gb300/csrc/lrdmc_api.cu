@@ -1067,6 +1067,7 @@ struct lrdmc_batch_s {
   std::vector<int> group;  // systems of one group run concurrently; groups run in order
   uint64_t group_version = 0;
   int carveout = -1;       // shared-memory carveout of the batched interval launches (-1: default)
+  int pipelined = 0;       // 1: interval kernels chained on one stream with programmatic serialization
   std::vector<cudaStream_t> branch;  // one per system, owned
   std::vector<cudaEvent_t> join, ready;
   cudaStream_t main = nullptr;
@@ -1113,9 +1114,37 @@ static cudaError_t capture_step(lrdmc_batch_t b, cudaGraphExec_t* out)
   cudaError_t e = cudaStreamBeginCapture(b->main, cudaStreamCaptureModeRelaxed);
   if (e != cudaSuccess) return e;
   cudaError_t first = cudaSuccess;
+  if (b->pipelined) {
+    // every system's interval kernel on the batch stream in group order (then
+    // index order), each after the first launched with programmatic stream
+    // serialization: it starts on the SMs that the previous system's blocks
+    // free as they run out of walkers. Each kernel finishes only after its
+    // predecessor (griddepcontrol.wait at its end), so the reconfiguration
+    // kernels, launched normally after the chain, see every interval done.
+    std::vector<size_t> seq(b->sys.size());
+    for (size_t i = 0; i < seq.size(); ++i) seq[i] = i;
+    std::stable_sort(seq.begin(), seq.end(), [&](size_t x, size_t y) { return b->group[x] < b->group[y]; });
+    for (size_t q = 0; q < seq.size() && first == cudaSuccess; ++q) {
+      lrdmc_system_t s = b->sys[seq[q]];
+      PopDev P = s->P;
+      P.rec_src = s->rec[s->cur];
+      P.rec_dst = s->rec[1 - s->cur];
+      first = launch_interval(s->S, s->Lo, b->lat[seq[q]], P, s->blocks, b->main, b->carveout, q > 0);
+    }
+    for (size_t q = 0; q < seq.size() && first == cudaSuccess; ++q) {
+      lrdmc_system_t s = b->sys[seq[q]];
+      PopDev P = s->P;
+      P.rec_src = s->rec[s->cur];
+      P.rec_dst = s->rec[1 - s->cur];
+      first = launch_reconfig(P, s->Lo, b->main);
+      if (first == cudaSuccess)
+        first = cudaMemcpyAsync(s->err_host, s->P.err, sizeof(int), cudaMemcpyDeviceToHost, b->main);
+    }
+  }
   std::vector<int> order(b->group);
   std::sort(order.begin(), order.end());
   order.erase(std::unique(order.begin(), order.end()), order.end());
+  if (b->pipelined) order.clear();
   for (int grp : order) {
     if (first == cudaSuccess) first = cudaEventRecord(b->fork, b->main);
     for (size_t i = 0; i < b->sys.size() && first == cudaSuccess; ++i) {
@@ -1298,6 +1327,15 @@ lrdmc_status lrdmc_batch_set_carveout(lrdmc_batch_t b, int carveout)
   if (!b) return LRDMC_ERR_ARG;
   if (carveout < -1 || carveout > 100) return bfail(b, LRDMC_ERR_ARG, "batch_set_carveout: -1 or 0..100");
   b->carveout = carveout;
+  b->group_version++;
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_batch_set_pipelined(lrdmc_batch_t b, int on)
+{
+  if (!b) return LRDMC_ERR_ARG;
+  if (on != 0 && on != 1) return bfail(b, LRDMC_ERR_ARG, "batch_set_pipelined: on must be 0 or 1");
+  b->pipelined = on;
   b->group_version++;
   return LRDMC_OK;
 }

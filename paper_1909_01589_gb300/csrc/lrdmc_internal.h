@@ -164,9 +164,10 @@ cudaError_t launch_eval_all(const SysDev& S, const Layout& Lo, const LatDev& L, 
                             cudaStream_t st);
 // carveout: preferred shared-memory share of the L1/shared storage for this
 // launch in percent (cudaLaunchAttributePreferredSharedMemoryCarveout), or
-// -1 for the default
+// -1 for the default; pdl: launch with programmatic stream serialization
+// (may start while the previous kernel in the stream drains its walkers)
 cudaError_t launch_interval(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P, int blocks,
-                            cudaStream_t st, int carveout = -1);
+                            cudaStream_t st, int carveout = -1, bool pdl = false);
 cudaError_t launch_reconfig(const PopDev& P, const Layout& Lo, cudaStream_t st);
 int interval_default_blocks(const SysDev& S, const Layout& Lo);
 cudaError_t launch_evaluate(const SysDev& S, const Layout& Lo, const LatDev& L, int n,

@@ -1773,7 +1773,13 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
     int idx = 0;
     if (lane == 0) idx = atomicAdd(P.counter, 1);
     idx = __shfl_sync(FULL_MASK, idx, 0);
-    if (idx >= P.W) break;
+    if (idx >= P.W) {
+      // out of walkers: a kernel launched after this one with programmatic
+      // stream serialization (the pipelined batch) may start on the SMs
+      // this block frees
+      asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+      break;
+    }
     const int s = P.order[idx];
     const int src = P.parent[s];
     double b, el;
@@ -1871,6 +1877,12 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
     }
     __syncwarp();
   }
+  // Launched early behind another system's interval kernel (pipelined
+  // batch): this grid does not read that kernel's results, but it finishes
+  // only after that kernel has, so that work after the chain in the stream
+  // sees every kernel of the chain complete. Without a prerequisite grid
+  // the wait returns at once.
+  if (threadIdx.x == 0) asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // Reconfiguration at the end of interval k (one block of 1024 threads):
@@ -2261,7 +2273,7 @@ int interval_default_blocks(const SysDev& S, const Layout& Lo)
 
 template <int PREC>
 static cudaError_t launch_interval_t(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P,
-                                     int blocks, int carveout, cudaStream_t st)
+                                     int blocks, int carveout, bool pdl, cudaStream_t st)
 {
   static int cached_blocks = -1, cached_smem = -1;
   cudaError_t e = set_smem((const void*)k_interval<PREC>, Lo.smem_block_bytes);
@@ -2276,30 +2288,41 @@ static cudaError_t launch_interval_t(const SysDev& S, const Layout& Lo, const La
   }
   const int need = (P.W + kWarpsPerBlock - 1) / kWarpsPerBlock;
   if (blocks > need) blocks = need;
-  if (carveout < 0) {
+  if (carveout < 0 && !pdl) {
     k_interval<PREC><<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(S, Lo, L, P);
     return cudaGetLastError();
   }
-  // the same launch with a preferred shared-memory carveout for this launch
-  // only (kernels of different systems sharing the SMs then ask for the same
-  // L1/shared split)
+  // the same launch with launch attributes: a preferred shared-memory
+  // carveout for this launch only (kernels of different systems sharing the
+  // SMs then ask for the same L1/shared split), and programmatic stream
+  // serialization (this kernel may start once every block of the previous
+  // kernel in the stream has run out of walkers)
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(blocks);
   cfg.blockDim = dim3(kWarpsPerBlock * 32);
   cfg.dynamicSmemBytes = Lo.smem_block_bytes;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributePreferredSharedMemoryCarveout;
-  attr[0].val.sharedMemCarveout = (unsigned)carveout;
+  cudaLaunchAttribute attr[2];
+  int na = 0;
+  if (carveout >= 0) {
+    attr[na].id = cudaLaunchAttributePreferredSharedMemoryCarveout;
+    attr[na].val.sharedMemCarveout = (unsigned)carveout;
+    ++na;
+  }
+  if (pdl) {
+    attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = na;
   return cudaLaunchKernelEx(&cfg, k_interval<PREC>, S, Lo, L, P);
 }
 
 cudaError_t launch_interval(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P, int blocks,
-                            cudaStream_t st, int carveout)
+                            cudaStream_t st, int carveout, bool pdl)
 {
-  LRDMC_DISPATCH(S, Lo, return launch_interval_t<V>(S, Lo, L, P, blocks, carveout, st));
+  LRDMC_DISPATCH(S, Lo, return launch_interval_t<V>(S, Lo, L, P, blocks, carveout, pdl, st));
   return cudaErrorInvalidValue;
 }
 

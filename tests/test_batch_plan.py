@@ -41,11 +41,16 @@ def test_plans_cover_concurrent_serial_and_split():
     assert sorted(serial) == [0, 1, 2] and serial[2] == 0 and serial[0] == 2  # heaviest first
     split = [p for p in plans if p[0].startswith("heaviest alone")]
     assert split and all(p[1] == [1, 1, 0] for p in split)
-    for _, groups, blocks, carve in plans:
+    for _, groups, blocks, carve, pipe in plans:
         assert len(groups) == 3 and all(1 <= b <= d for b, d in zip(blocks, defaults)) and carve in (-1, 100)
+        assert pipe in (0, 1)
     assert any(p[3] == 100 for p in plans) and any(p[3] == -1 for p in plans)
+    piped = dict((p[0], p) for p in plans if p[4] == 1)
+    assert piped["pipelined, heaviest first"][1] == serial
+    assert piped["pipelined, lightest first"][1] == [2 - r for r in serial]
 
 
 def test_choose_takes_the_fastest():
-    t = [("a", [0, 0], [608, 608], -1, 10.0), ("b", [0, 1], [100, 500], 100, 7.5), ("c", [0, 0], [304, 304], -1, 8.0)]
-    assert choose(t) == ("b", [0, 1], [100, 500], 100, 7.5)
+    t = [("a", [0, 0], [608, 608], -1, 0, 10.0), ("b", [0, 1], [100, 500], 100, 1, 7.5),
+         ("c", [0, 0], [304, 304], -1, 0, 8.0)]
+    assert choose(t) == ("b", [0, 1], [100, 500], 100, 1, 7.5)

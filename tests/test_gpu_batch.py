@@ -158,7 +158,8 @@ def test_full_size_batch_equals_single_steps(pkg):
         assert _equal(_state(g1), _state(g2))
 
 
-def test_batch_matches_oracle(pkg, oracle_mod):
+@pytest.mark.parametrize("pipelined", [False, True])
+def test_batch_matches_oracle(pkg, oracle_mod, pipelined):
     """A batch of four systems of uneven size (He, Ne, H2O, Ar: N = 2 to 18;
     single grid, this work's and the previous double grid), stepped one
     interval per CUDA graph, against each system's own oracle population
@@ -187,7 +188,11 @@ def test_batch_matches_oracle(pkg, oracle_mod):
         gs.append(g)
         systems.append((system, o))
     batch = pkg.LrdmcBatch(gs, [c[2] for c in cases], [_spacing(pkg, c[3]) for c in cases])
-    entries = [{"test": f"batch vs oracle: {c[0]} {c[3]} (W={c[1]})", "kind": "projection (batched)",
+    if pipelined:
+        batch.set_groups([3, 2, 1, 0])
+        batch.set_pipelined(True)
+    tag = "pipelined " if pipelined else ""
+    entries = [{"test": f"{tag}batch vs oracle: {c[0]} {c[3]} (W={c[1]})", "kind": "projection (batched)",
                 "walkers": c[1], "intervals_requested": 4, "intervals_compared": 0, "parted": False} for c in cases]
     live = [True] * len(cases)
     try:
@@ -217,3 +222,30 @@ def test_batch_matches_oracle(pkg, oracle_mod):
     finally:
         for e in entries:
             U.record(e)
+
+
+def test_pipelined_batch_equals_single_steps(pkg):
+    """The pipelined schedule (interval kernels chained with programmatic
+    dependent launches, each starting in the previous one's tail) gives the
+    single steps' results bit for bit, heaviest first and lightest first,
+    across a switch from and back to the fork/join schedule."""
+    a = [c[2] for c in CASES]
+    sp = [_spacing(pkg, c[3]) for c in CASES]
+    solo = _make(pkg, 400)
+    for g, ai, s in zip(solo, a, sp):
+        g.step(6, ai, s)
+        g.sync()
+    batched = _make(pkg, 400)
+    batch = pkg.LrdmcBatch(batched, a, sp)
+    batch.set_groups([3, 2, 1, 0])
+    batch.set_pipelined(True)
+    batch.step(2)
+    batch.set_groups([0, 1, 2, 3])
+    batch.step(1)
+    batch.set_pipelined(False)
+    batch.step(1)
+    batch.set_pipelined(True)
+    batch.step(2)
+    batch.sync()
+    for g1, g2 in zip(solo, batched):
+        assert _equal(_state(g1), _state(g2))
