@@ -275,7 +275,11 @@ def mixed_vs_parity(names=("Ne", "Ar", "Kr"), steps=None, equil=200, seed=7):
     sampling), next to each mode's own energy and error. Workloads: Ne at
     a = 0.2 with 4096 walkers (the bench workload), Ar and Kr at
     a = 1/(3.5 Z) with 16384 walkers, this work's double grid, tau for
-    about 10 jumps per walker per interval."""
+    about 10 jumps per walker per interval. Also the evaluation's own error
+    on the projected population: the mean shift of the local energy (the
+    quantity the mixed estimator averages) and the relative error of the
+    total rates, over the parity run's final walkers evaluated in both
+    arithmetics."""
     import torch
 
     import lrdmc_synth as S
@@ -312,12 +316,28 @@ def mixed_vs_parity(names=("Ne", "Ar", "Kr"), steps=None, equil=200, seed=7):
             err, _ = stats.reblock(e)
             res[label] = {"energy": float(np.mean(e)), "error": err, "seconds": dt,
                           "moves_per_s": (g.moves() - m0) / dt, "efficiency": stats.efficiency(e, dt), "trace": e}
+            if label == "parity":
+                x_end = g.walkers()["x"]
+        # the evaluation's own error on the projected population: local
+        # energies and total rates of the final parity-mode walkers in both
+        # arithmetics (the mixed estimator averages E_L over this population)
+        xs = torch.tensor(x_end, device="cuda")
+        rs = torch.tensor(S.random_rotations(len(x_end), seed + 3), device="cuda")
+        ev = {}
+        for label, prec in (("parity", PRECISION_DF64), ("mixed", PRECISION_FP32)):
+            ev[label] = [t.cpu().numpy() for t in LrdmcSystem(system).set_precision(prec).evaluate(xs, rs, a, sp)]
+        del_el = ev["mixed"][3] - ev["parity"][3]
+        del_b = (ev["mixed"][2] - ev["parity"][2]) / ev["parity"][2]
         d = res["mixed"]["trace"] - res["parity"]["trace"]
         derr, _ = stats.reblock(d)
         corr = float(np.corrcoef(res["mixed"]["trace"], res["parity"]["trace"])[0, 1])
         row = {"system": name, "walkers": W, "a": a, "tau": tau, "intervals": n, "equilibration": equil,
                "delta_E_Ha": float(np.mean(d)), "delta_E_error_Ha": derr, "trace_correlation": corr,
                "independent_error_Ha": float(np.hypot(res["mixed"]["error"], res["parity"]["error"])),
+               "EL_shift_on_population_Ha": float(np.mean(del_el)),
+               "EL_shift_error_Ha": float(np.std(del_el, ddof=1) / np.sqrt(len(del_el))),
+               "EL_abs_error_mean_Ha": float(np.mean(np.abs(del_el))),
+               "b_rel_error_mean": float(np.mean(del_b)), "b_rel_error_rms": float(np.sqrt(np.mean(del_b ** 2))),
                "efficiency_ratio": res["mixed"]["efficiency"] / res["parity"]["efficiency"]}
         for label in ("parity", "mixed"):
             row[label] = {k: v for k, v in res[label].items() if k != "trace"}
@@ -325,6 +345,7 @@ def mixed_vs_parity(names=("Ne", "Ar", "Kr"), steps=None, equil=200, seed=7):
         print(f"{name}: E_parity {row['parity']['energy']:.5f}({1e3 * row['parity']['error']:.2f} mHa) "
               f"E_mixed {row['mixed']['energy']:.5f}({1e3 * row['mixed']['error']:.2f}) "
               f"dE {1e3 * row['delta_E_Ha']:+.3f} +- {1e3 * derr:.3f} mHa (corr {corr:.3f}); "
+              f"E_L shift {1e3 * row['EL_shift_on_population_Ha']:+.4f} +- {1e3 * row['EL_shift_error_Ha']:.4f} mHa; "
               f"moves/s {row['parity']['moves_per_s']:.3g} -> {row['mixed']['moves_per_s']:.3g}", flush=True)
     return rows
 
