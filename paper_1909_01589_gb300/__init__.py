@@ -554,13 +554,13 @@ class LrdmcBatch:
         launches, or -1 for the default."""
         self._check(load_library().lrdmc_batch_set_carveout(self.h, int(carveout)))
 
-    @property
     def set_pipelined(self, on=True):
         """Chain the systems' interval kernels on one stream with
         programmatic stream serialization (each starts while the previous
         one drains its walkers); off: the fork/join groups."""
         self._check(load_library().lrdmc_batch_set_pipelined(self.h, int(bool(on))))
 
+    @property
     def stream_ptr(self):
         p = ct.c_void_p()
         self._check(load_library().lrdmc_batch_stream(self.h, ct.byref(p)))

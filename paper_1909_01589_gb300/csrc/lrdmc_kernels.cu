@@ -1381,14 +1381,22 @@ __device__ void warp_eval_m(const SysDev& S, const double* sC, const LatDev& L, 
   const int N = S.N, nao = S.n_ao, nu = S.n_up;
   const BlockMem bm = block_mem(S, const_cast<double*>(sC));
   // projected inverse columns (FP64, or FP32 in the mixed mode), then
-  // converted with the positions
+  // converted with the positions. The mixed mode converts the inverse
+  // blocks to float once (scratch), not once per use: each conversion from
+  // double runs on the FP64 pipe
+  const float* Af = reinterpret_cast<const float*>(wm.scr);
+  if (sizeof(NT) == sizeof(float)) {
+    for (int j = lane; j < nu * nu + S.n_dn * S.n_dn; j += 32) reinterpret_cast<float*>(wm.scr)[j] = (float)wm.A[j];
+    __syncwarp();
+  }
   for (int idx = lane; idx < N * nao; idx += 32) {
     int i = idx / nao, mu = idx % nao;
     int spin = i < nu ? 0 : 1, l = i < nu ? i : i - nu, n = spin ? S.n_dn : nu;
     const double* Am = spin ? wm.A + nu * nu : wm.A;
     if (sizeof(NT) == sizeof(float)) {
+      const float* Amf = spin ? Af + nu * nu : Af;
       float acc = 0.0f;
-      for (int m = 0; m < n; ++m) acc += bm.Cf[mu * S.n_mo + m] * (float)Am[m * n + l];
+      for (int m = 0; m < n; ++m) acc += bm.Cf[mu * S.n_mo + m] * Amf[m * n + l];
       wm.vd[idx] = df_make(acc, 0.0f);
     } else {
       double acc = 0.0;

@@ -143,3 +143,10 @@ def test_static_eval_limit_matches_header(pkg):
     m = re.search(r"#define\s+LRDMC_STATIC_EVAL_MAX\s+(\d+)", text)
     assert m and int(m.group(1)) == pkg.STATIC_EVAL_MAX
 
+
+
+def test_batch_binding_methods(pkg):
+    """The batch binding's setters are methods and its stream a property."""
+    for name in ("step", "sync", "set_groups", "set_carveout", "set_pipelined"):
+        assert callable(getattr(pkg.LrdmcBatch, name)), name
+    assert isinstance(pkg.LrdmcBatch.stream_ptr, property)
