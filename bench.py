@@ -225,7 +225,7 @@ def measure_leg(args, pkg, torch, system, precision, dev, rank, seed, x0, with_c
     _, world, local = _env_rank()
     spacing = pkg.Spacing(pkg.THIS_WORK)
     a = WORKLOAD["a"]
-    g = pkg.LrdmcSystem(system).set_precision(precision)
+    g = pkg.LrdmcSystem(system).set_precision(precision).set_tail_helpers(args.tail_helpers)
     if neural is not None:
         g.set_neural_jastrow(*neural)
     cap = args.warmup + args.steps + args.eff_steps + 8
@@ -373,7 +373,8 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": "Ne all-electron, 4096 walkers, a=0.2 bohr, smart double grid (this work), "
                                "tau=0.025", **WORKLOAD, **ARITHMETIC[args.precision],
-                   "walkers_per_gpu": W, "l2": "flushed between timed steps (512 MiB write)",
+                   "walkers_per_gpu": W, "tail_helpers": bool(args.tail_helpers),
+                   "l2": "flushed between timed steps (512 MiB write)",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_moves_all / t_e2e_all, "unit": "walker-moves/s",
                 "h2d_bytes_per_step": x0.nbytes / n_e2e, "d2h_bytes_per_step": d2h / n_e2e,
@@ -714,6 +715,8 @@ def main():
                     help="skip the A/B of the tensor-core orbital contraction")
     ap.add_argument("--no-mixed-leg", dest="mixed_leg", action="store_false",
                     help="skip the mixed-precision (FP32 evaluation) leg")
+    ap.add_argument("--tail-helpers", type=int, default=1, choices=[0, 1],
+                    help="warps out of walkers help the others of their block (results are the same bits)")
     ap.add_argument("--walkers", type=int, default=WORKLOAD["n_walkers"],
                     help="walkers per GPU (smaller cases for profiling)")
     args = ap.parse_args()

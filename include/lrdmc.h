@@ -379,6 +379,19 @@ LRDMC_API lrdmc_status lrdmc_nj_backward(lrdmc_system_t sys, const lrdmc_nj_spec
 LRDMC_API lrdmc_status lrdmc_set_interval_blocks(lrdmc_system_t sys, int blocks);
 LRDMC_API lrdmc_status lrdmc_interval_blocks(lrdmc_system_t sys, int* current, int* occupancy_default);
 
+/* Tail helpers (on = 1, the default; 0 = off). Not a step of the paper's
+ * method: a schedule of the interval kernel. Jump counts per interval are
+ * Poisson-distributed, so near the end of an interval most warps have no
+ * walker left while a few still run one. With helpers on, a warp whose
+ * fetch finds no walker takes chunks of the lattice moves of a walker that
+ * another warp of its block still runs; blocks hold up to 16 warps (one per
+ * SM), fewer for small populations. Double-float and FP32 evaluation; the
+ * FP64 mode runs every warp alone. The rates, and so every result, are bit
+ * for bit the same either way. Every wait between warps is bounded; one
+ * that runs out is reported as LRDMC_ERR_TIMEOUT. Takes effect at the next
+ * step. */
+LRDMC_API lrdmc_status lrdmc_set_tail_helpers(lrdmc_system_t sys, int on);
+
 /* A batch projects several systems (different atoms, electron counts and
  * spacings) together. Every step is one CUDA graph: per execution group
  * (lrdmc_batch_set_groups) a fork, then per system of the group on its own

@@ -34,7 +34,8 @@ EXPORTED = [
     "lrdmc_evaluate_static", "lrdmc_evaluate_tc",
     "lrdmc_save", "lrdmc_load", "lrdmc_set_precision", "lrdmc_set_profiling", "lrdmc_kernel_times", "lrdmc_last_error",
     "lrdmc_destroy", "lrdmc_nj_n_params", "lrdmc_set_neural_jastrow", "lrdmc_base_terms", "lrdmc_nj_forward",
-    "lrdmc_nj_backward", "lrdmc_set_interval_blocks", "lrdmc_interval_blocks", "lrdmc_batch_create",
+    "lrdmc_nj_backward", "lrdmc_set_interval_blocks", "lrdmc_interval_blocks", "lrdmc_set_tail_helpers",
+    "lrdmc_batch_create",
     "lrdmc_batch_step", "lrdmc_batch_sync", "lrdmc_batch_stream", "lrdmc_batch_last_error", "lrdmc_batch_destroy",
     "lrdmc_batch_set_groups", "lrdmc_batch_set_carveout", "lrdmc_batch_set_pipelined",
 ]
@@ -157,6 +158,8 @@ def load_library():
     L.lrdmc_nj_backward.argtypes = [vp, vp, vp, i, vp, vp, vp, vp, vp, vp]
     L.lrdmc_set_interval_blocks.restype = i
     L.lrdmc_set_interval_blocks.argtypes = [vp, i]
+    L.lrdmc_set_tail_helpers.restype = i
+    L.lrdmc_set_tail_helpers.argtypes = [vp, i]
     L.lrdmc_interval_blocks.restype = i
     L.lrdmc_interval_blocks.argtypes = [vp, ct.POINTER(i), ct.POINTER(i)]
     L.lrdmc_batch_create.restype = i
@@ -423,6 +426,12 @@ class LrdmcSystem:
         self._check(fn(self.h, n, _t_ptr(x), _t_ptr(rot), float(a), ct.byref(sp), _t_ptr(ratio), _t_ptr(T),
                        _t_ptr(b), _t_ptr(el), ct.c_void_p(stream.cuda_stream)))
         return ratio, T, b, el
+
+    def set_tail_helpers(self, on=True):
+        """Warps out of walkers help the warps of their block that still run
+        one (default on; results are bit for bit the same either way)."""
+        self._check(load_library().lrdmc_set_tail_helpers(self.h, int(bool(on))))
+        return self
 
     def set_interval_blocks(self, blocks):
         """Persistent grid size of the interval kernel (0 = occupancy default)."""

@@ -47,6 +47,7 @@ struct lrdmc_system_s {
   long long n_interval = 0, n_reconfig = 0;
   std::string last_error;
   int blocks = 0;  // persistent grid of the interval kernel (0 = occupancy default)
+  int helpers = 1;  // tail helpers of the interval kernel (lrdmc_set_tail_helpers)
   uint64_t version = 0;  // bumped whenever kernel arguments change (batches re-capture)
   // neural pair term (lrdmc_set_neural_jastrow)
   double* nj_tab = nullptr;
@@ -438,6 +439,7 @@ static lrdmc_status read_error_word(lrdmc_system_t s)
   if (w & kErrSingular) return fail(s, LRDMC_ERR_SINGULAR, "singular Slater matrix or zero update ratio");
   if (w & kErrNonFinite) return fail(s, LRDMC_ERR_NONFINITE, "non-finite local energy or rate");
   if (w & kErrIters) return fail(s, LRDMC_ERR_TIMEOUT, "an interval exceeded its iteration limit");
+  if (w & kErrTimeout) return fail(s, LRDMC_ERR_TIMEOUT, "a bounded wait of the interval kernel's tail helpers ran out");
   return LRDMC_OK;
 }
 
@@ -488,6 +490,7 @@ lrdmc_status lrdmc_init_walkers(lrdmc_system_t s, int W, const double* x0, uint6
   P.seed = seed;
   P.tau = tau;
   P.e_trial = e_trial;
+  P.helpers = s->helpers;
   cudaError_t e = cudaMemsetAsync(s->ws + p.moves, 0, 4 * 256, s->stream);  // moves, err, counter, kdev
   if (e != cudaSuccess) return cuda_fail(s, e, "workspace clear");
   e = cudaMemsetAsync(P.logw, 0, sizeof(double) * W, s->stream);
@@ -589,6 +592,7 @@ static lrdmc_status sync_system(lrdmc_system_t s)
   if (w & kErrSingular) return fail(s, LRDMC_ERR_SINGULAR, "singular Slater matrix or zero update ratio");
   if (w & kErrNonFinite) return fail(s, LRDMC_ERR_NONFINITE, "non-finite local energy or rate");
   if (w & kErrIters) return fail(s, LRDMC_ERR_TIMEOUT, "an interval exceeded its iteration limit");
+  if (w & kErrTimeout) return fail(s, LRDMC_ERR_TIMEOUT, "a bounded wait of the interval kernel's tail helpers ran out");
   return LRDMC_OK;
 }
 
@@ -1055,7 +1059,17 @@ lrdmc_status lrdmc_interval_blocks(lrdmc_system_t s, int* current, int* occupanc
 {
   if (!s) return fail(s, LRDMC_ERR_ARG, "");
   if (current) *current = s->blocks;
-  if (occupancy_default) *occupancy_default = interval_default_blocks(s->S, s->Lo);
+  if (occupancy_default) *occupancy_default = interval_default_blocks(s->S, s->Lo, s->W > 0 ? s->W : 1 << 30);
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_set_tail_helpers(lrdmc_system_t s, int on)
+{
+  if (!s) return fail(s, LRDMC_ERR_ARG, "");
+  if (on != 0 && on != 1) return fail(s, LRDMC_ERR_ARG, "set_tail_helpers: on must be 0 or 1");
+  s->helpers = on;
+  s->P.helpers = on;
+  s->version++;
   return LRDMC_OK;
 }
 

@@ -25,7 +25,7 @@ constexpr int kMaxItersPerInterval = 1 << 20;
 constexpr int kErrSingular = 1;
 constexpr int kErrNonFinite = 2;
 constexpr int kErrIters = 4;
-constexpr int kErrTimeout = 8;  // a bounded wait on the tensor-core MMA barrier ran out
+constexpr int kErrTimeout = 8;  // a bounded wait ran out (tail helpers of the interval kernel, tensor-core barrier)
 
 // Philox counter tags.
 constexpr uint64_t kTagTimeHB = 0;
@@ -122,8 +122,10 @@ struct Layout {
 // Shared-memory layout of a system; caches = false leaves out the
 // evaluation caches (for systems that would not fit otherwise).
 Layout make_layout(const SysDev& S, bool caches);
-// Largest dynamic shared memory of one block on sm_100-class GPUs (227 KB).
-constexpr int kMaxSmemBlock = 232448;
+// Largest dynamic shared memory of one block on sm_100-class GPUs (227 KB),
+// less 2 KB for the kernels' static shared memory (the interval kernel's
+// per-warp loop state and tail-helper slots, 1.7 KB).
+constexpr int kMaxSmemBlock = 232448 - 2048;
 
 // Populations up to this many walkers keep the comb's running sums in the
 // reconfiguration kernel's shared memory (8 bytes each).
@@ -153,6 +155,9 @@ struct PopDev {
   int trace_cap;
   uint64_t seed;
   double tau, e_trial;
+  // 1: in the FP32-pipe evaluations, warps of the interval kernel that run
+  // out of walkers help the warps of their block that still run one
+  int helpers;
 };
 
 void fill_df_constants(SysDev& S);
@@ -169,7 +174,10 @@ cudaError_t launch_eval_all(const SysDev& S, const Layout& Lo, const LatDev& L, 
 cudaError_t launch_interval(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P, int blocks,
                             cudaStream_t st, int carveout = -1, bool pdl = false);
 cudaError_t launch_reconfig(const PopDev& P, const Layout& Lo, cudaStream_t st);
-int interval_default_blocks(const SysDev& S, const Layout& Lo);
+// Occupancy-default persistent grid of the interval kernel for a population
+// of W walkers (blocks of interval_warps(S, Lo, W) warps).
+int interval_default_blocks(const SysDev& S, const Layout& Lo, int W);
+int interval_warps(const Layout& Lo, int W);
 cudaError_t launch_evaluate(const SysDev& S, const Layout& Lo, const LatDev& L, int n,
                             const double* x, const double* rot, double* ratio, double* T,
                             double* b, double* el, int* err, cudaStream_t st);

@@ -1373,9 +1373,70 @@ __device__ __forceinline__ NT el_local(const ElParts<NT>& o)
   return A::add(A::mul_f(lap, -0.5f), o.V);
 }
 
-template <class NT, bool NJ, bool NC, bool MOVES = true>
-__device__ void warp_eval_m(const SysDev& S, const double* sC, const LatDev& L, const WarpMem& wm, int lane,
-                            double* ratio_out, double& b, df& bdf, double& el)
+// One lattice move c of an evaluation (Eq. 1 lattice, fixed-node rate): the
+// determinant and Jastrow ratios at the displaced position, p at the bond
+// midpoint on the double grid, the rate T_c into Td[c]. Reads the
+// evaluation's shared-memory state (projected inverse columns, positions,
+// rotation, caches and the Jastrow sums Sd of its local-energy pass).
+template <class NT, bool NJ, bool NC>
+__device__ __forceinline__ void candidate_m(const SysDev& S, const LatDev& L, const WarpMem& wm, const BlockMem& bm,
+                                            int c, df* Td, double* ratio_out)
+{
+  typedef Ar<NT> A;
+  const int nao = S.n_ao;
+  const int G = L.G, per_e = 6 * G;
+  constexpr bool kUsePairCache = sizeof(NT) == sizeof(df) && !NC;
+  {
+    const int i = c / per_e, rem = c - i * per_e, g = rem / 6, k = (rem % 6) >> 1;
+    NT h = g ? A::c(L.ap_df) : A::c(L.a_df);
+    if (c & 1) h = A::neg(h);
+    const NT e0 = A::c(wm.Rd[k]), e1 = A::c(wm.Rd[3 + k]), e2 = A::c(wm.Rd[6 + k]);
+    NT rdet, jen, jee, pm = A::one();
+    if (kUsePairCache) {
+      // the caches pay in double-float arithmetic only (single precision
+      // recomputes a distance faster than it reads it back)
+      const NT h2 = A::sqr(h);
+      const NT he[3] = {A::mul(h, e0), A::mul(h, e1), A::mul(h, e2)};
+      NT mid2;
+      nucleus_terms_cached_m<NT, NJ>(S, &wm.vd[i * nao], &wm.enc[8 * i * S.n_nuc], k, h, he, h2, bm, rdet, jen,
+                                 mid2);
+      if (wm.n_pc) {
+        jee = jastrow_ee_cached_m<NT, NJ>(S, wm.pc, wm.pcw, i, k, h, h2);
+      } else {
+        const NT p[3] = {A::add(A::c(wm.xd[3 * i]), he[0]), A::add(A::c(wm.xd[3 * i + 1]), he[1]),
+                         A::add(A::c(wm.xd[3 * i + 2]), he[2])};
+        jee = jastrow_ee_m<NT, NJ>(S, wm.xd, i, p);
+      }
+      if (G == 2) pm = p_from_d2_m<NT>(S, L, mid2, bm);
+    } else {
+      const NT ri[3] = {A::c(wm.xd[3 * i]), A::c(wm.xd[3 * i + 1]), A::c(wm.xd[3 * i + 2])};
+      const NT p[3] = {A::add(ri[0], A::mul(h, e0)), A::add(ri[1], A::mul(h, e1)), A::add(ri[2], A::mul(h, e2))};
+      nucleus_terms_m<NT, NJ>(S, &wm.vd[i * nao], p, bm, rdet, jen);
+      jee = jastrow_ee_m<NT, NJ>(S, wm.xd, i, p);
+      if (G == 2) {
+        const NT hh = A::half(h);
+        const NT mid[3] = {A::add(ri[0], A::mul(hh, e0)), A::add(ri[1], A::mul(hh, e1)),
+                           A::add(ri[2], A::mul(hh, e2))};
+        pm = p_weight_m<NT>(S, L, mid, bm);
+      }
+    }
+    NT dJ = A::sub(A::add(jee, jen), A::c(wm.Sd[i]));
+    NT rho = A::mul(rdet, A::exp(dJ, S.D.exp.K, bm.tab));
+    NT w = A::one();
+    if (G == 2) w = g ? A::add_f(A::neg(pm), 1.0f) : pm;
+    NT T = A::zero();
+    if (A::positive(rho)) T = A::mul(A::mul(w, g ? A::c(L.inv2ap2_df) : A::c(L.inv2a2_df)), rho);
+    Td[c] = A::store(T);
+    if (ratio_out) ratio_out[c] = A::to_double(rho);
+  }
+}
+
+// The first part of an evaluation: projected inverse columns, converted
+// positions and rotation, the caches, then the local energy (into el) and
+// the Jastrow sums Sd of every electron. The moves read all of it.
+template <class NT, bool NJ, bool NC>
+__device__ __forceinline__ void eval_prelude_m(const SysDev& S, const double* sC, const LatDev& L, const WarpMem& wm,
+                                               int lane, double& el)
 {
   typedef Ar<NT> A;
   const int N = S.N, nao = S.n_ao, nu = S.n_up;
@@ -1444,6 +1505,16 @@ __device__ void warp_eval_m(const SysDev& S, const double* sC, const LatDev& L, 
   NT etot = warp_sum_m<NT>(epart);
   el = A::to_double(etot) + S.V_nn;
   __syncwarp();
+}
+
+template <class NT, bool NJ, bool NC, bool MOVES = true>
+__device__ void warp_eval_m(const SysDev& S, const double* sC, const LatDev& L, const WarpMem& wm, int lane,
+                            double* ratio_out, double& b, df& bdf, double& el)
+{
+  typedef Ar<NT> A;
+  const int N = S.N;
+  const BlockMem bm = block_mem(S, const_cast<double*>(sC));
+  eval_prelude_m<NT, NJ, NC>(S, sC, L, wm, lane, el);
   if (!MOVES) {  // local energy and Jastrow sums only (the caller forms the moves)
     b = 0.0;
     bdf = A::store(A::zero());
@@ -1452,49 +1523,7 @@ __device__ void warp_eval_m(const SysDev& S, const double* sC, const LatDev& L, 
   // the P lattice moves
   const int G = L.G, per_e = 6 * G, P = N * per_e;
   df* Td = reinterpret_cast<df*>(wm.T);  // rates stay in NT, stored as double-floats
-  for (int c = lane; c < P; c += 32) {
-    int i = c / per_e, rem = c - i * per_e, g = rem / 6, k = (rem % 6) >> 1;
-    NT h = g ? A::c(L.ap_df) : A::c(L.a_df);
-    if (c & 1) h = A::neg(h);
-    const NT e0 = A::c(wm.Rd[k]), e1 = A::c(wm.Rd[3 + k]), e2 = A::c(wm.Rd[6 + k]);
-    NT rdet, jen, jee, pm = A::one();
-    if (kUsePairCache) {
-      // the caches pay in double-float arithmetic only (single precision
-      // recomputes a distance faster than it reads it back)
-      const NT h2 = A::sqr(h);
-      const NT he[3] = {A::mul(h, e0), A::mul(h, e1), A::mul(h, e2)};
-      NT mid2;
-      nucleus_terms_cached_m<NT, NJ>(S, &wm.vd[i * nao], &wm.enc[8 * i * S.n_nuc], k, h, he, h2, bm, rdet, jen,
-                                 mid2);
-      if (wm.n_pc) {
-        jee = jastrow_ee_cached_m<NT, NJ>(S, wm.pc, wm.pcw, i, k, h, h2);
-      } else {
-        const NT p[3] = {A::add(A::c(wm.xd[3 * i]), he[0]), A::add(A::c(wm.xd[3 * i + 1]), he[1]),
-                         A::add(A::c(wm.xd[3 * i + 2]), he[2])};
-        jee = jastrow_ee_m<NT, NJ>(S, wm.xd, i, p);
-      }
-      if (G == 2) pm = p_from_d2_m<NT>(S, L, mid2, bm);
-    } else {
-      const NT ri[3] = {A::c(wm.xd[3 * i]), A::c(wm.xd[3 * i + 1]), A::c(wm.xd[3 * i + 2])};
-      const NT p[3] = {A::add(ri[0], A::mul(h, e0)), A::add(ri[1], A::mul(h, e1)), A::add(ri[2], A::mul(h, e2))};
-      nucleus_terms_m<NT, NJ>(S, &wm.vd[i * nao], p, bm, rdet, jen);
-      jee = jastrow_ee_m<NT, NJ>(S, wm.xd, i, p);
-      if (G == 2) {
-        const NT hh = A::half(h);
-        const NT mid[3] = {A::add(ri[0], A::mul(hh, e0)), A::add(ri[1], A::mul(hh, e1)),
-                           A::add(ri[2], A::mul(hh, e2))};
-        pm = p_weight_m<NT>(S, L, mid, bm);
-      }
-    }
-    NT dJ = A::sub(A::add(jee, jen), A::c(wm.Sd[i]));
-    NT rho = A::mul(rdet, A::exp(dJ, S.D.exp.K, bm.tab));
-    NT w = A::one();
-    if (G == 2) w = g ? A::add_f(A::neg(pm), 1.0f) : pm;
-    NT T = A::zero();
-    if (A::positive(rho)) T = A::mul(A::mul(w, g ? A::c(L.inv2ap2_df) : A::c(L.inv2a2_df)), rho);
-    Td[c] = A::store(T);
-    if (ratio_out) ratio_out[c] = A::to_double(rho);
-  }
+  for (int c = lane; c < P; c += 32) candidate_m<NT, NJ, NC>(S, L, wm, bm, c, Td, ratio_out);
   __syncwarp();
   NT btot = warp_scan_m<NT>(Td, P, lane, A::zero(), nullptr, nullptr);
   bdf = A::store(btot);
@@ -1751,15 +1780,395 @@ k_eval_all(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
   store_record(Lo, rec, wm, lane, b, el);
 }
 
+// ----------------------------------------------------------------------------
+// Tail helpers of the interval kernel. Walkers make Poisson-distributed
+// numbers of jumps, so at the end of an interval most warps of a block have
+// no walker left while a few still run one. A warp whose fetch finds the
+// queue empty attaches to a warp of its block that still runs a walker and,
+// in every evaluation that warp publishes (projected columns, caches, local
+// energy and Jastrow sums ready), takes chunks of 32 of its lattice moves.
+// Owner and helpers run the same inlined move code (one loop of the kernel
+// serves both roles), so a rate has the same bits whoever computes it and
+// no second copy of the move code competes for the instruction cache. Every
+// wait is bounded (kTeamSpin polls with a short sleep); one that runs out
+// sets kErrTimeout in the error word and gives up, reported to the host as
+// LRDMC_ERR_TIMEOUT, never a hang.
+// ----------------------------------------------------------------------------
+constexpr int kMaxIntervalWarps = 16;
+struct TeamSlot {
+  int attach;  // bit 31: closed to helpers; bits 0-30: helpers attached
+  int pub;     // published evaluation (generation << 4 | participants), or kTeamRelease
+  int next;    // next chunk of moves of the published evaluation
+  int done;    // helpers finished with the published evaluation
+  int gen;     // the owner's generation counter
+  int pad[3];
+};
+constexpr int kTeamClosed = (int)0x80000000;
+constexpr int kTeamRelease = -1;
+constexpr int kTeamSpin = 1 << 22;
+
+__device__ __forceinline__ int ld_vol(const int* p) { return *(const volatile int*)p; }
+
+// Owner, after the evaluation's first part: the number of helpers taking
+// part (0: alone; a helper that attaches later joins at the next one).
+__device__ __forceinline__ int team_publish(TeamSlot* t, int lane)
+{
+  int nh = 0;
+  if (lane == 0) {
+    nh = ld_vol(&t->attach);
+    nh = nh < 0 ? 0 : (nh > 15 ? 15 : nh);
+  }
+  nh = __shfl_sync(FULL_MASK, nh, 0);
+  if (nh == 0) return 0;
+  __threadfence_block();  // this lane's writes of the evaluation state
+  __syncwarp();
+  if (lane == 0) {
+    const int g = t->gen + 1;
+    t->gen = g;
+    t->next = 0;
+    t->done = 0;
+    __threadfence_block();
+    atomicExch(&t->pub, (g << 4) | nh);
+  }
+  __syncwarp();
+  return nh;
+}
+
+// The moves of an evaluation in chunks of 32: alone (t == nullptr) in
+// order, or taken in turn from t->next by the owner and its helpers.
+template <class NT, bool NJ, bool NC>
+__device__ __forceinline__ void chunked_moves(const SysDev& S, const LatDev& L, const WarpMem& wm, const BlockMem& bm,
+                                              TeamSlot* t, int P, int lane)
+{
+  df* Td = reinterpret_cast<df*>(wm.T);
+  for (int c0 = 0;; c0 += 32) {
+    if (t) {
+      int c = 0;
+      if (lane == 0) c = atomicAdd(&t->next, 32);
+      c0 = __shfl_sync(FULL_MASK, c, 0);
+    }
+    if (c0 >= P) break;
+    if (c0 + lane < P) candidate_m<NT, NJ, NC>(S, L, wm, bm, c0 + lane, Td, nullptr);
+  }
+  if (t) __threadfence_block();
+  __syncwarp();
+}
+
+// Owner: wait until the nh helpers of the published evaluation are done.
+__device__ __forceinline__ void team_wait_helpers(TeamSlot* t, int nh, int lane, int* err)
+{
+  if (lane == 0) {
+    int it = 0;
+    while (ld_vol(&t->done) < nh && ++it < kTeamSpin) __nanosleep(32);
+    if (it >= kTeamSpin) atomicOr(err, kErrTimeout);
+    __threadfence_block();
+  }
+  __syncwarp();
+}
+
+// Owner, when its walker's interval is over: close the slot and release
+// the helpers attached to it.
+__device__ __forceinline__ void team_close(TeamSlot* t, int lane)
+{
+  if (lane == 0) {
+    atomicOr(&t->attach, kTeamClosed);
+    atomicExch(&t->pub, kTeamRelease);
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ void team_open(TeamSlot* t, int lane)
+{
+  if (lane == 0) {
+    t->pub = 0;
+    __threadfence_block();
+    atomicExch(&t->attach, 0);
+  }
+  __syncwarp();
+}
+
+// Helper: attach to the open slot of the block with the fewest helpers;
+// returns the owner's warp (or -1: no warp of the block runs a walker) and
+// the helper's index among that owner's helpers.
+__device__ __forceinline__ int team_attach(TeamSlot* slots, int nw, int wib, int lane, int& kidx)
+{
+  int o = -1, kk = 0;
+  if (lane == 0) {
+    for (int tries = 0; tries < 64 && o < 0; ++tries) {
+      int best = -1, bc = 0x7fffffff;
+      for (int q = 0; q < nw; ++q) {
+        const int a = ld_vol(&slots[q].attach);
+        if (q == wib || a < 0) continue;  // itself, or closed (bit 31)
+        if (a < bc) { bc = a; best = q; }
+      }
+      if (best < 0) break;
+      if (atomicCAS(&slots[best].attach, bc, bc + 1) == bc) { o = best; kk = bc; }
+    }
+  }
+  kidx = __shfl_sync(FULL_MASK, kk, 0);
+  return __shfl_sync(FULL_MASK, o, 0);
+}
+
+// Helper: wait for an evaluation of its owner it takes part in (returns
+// its generation), a release (-1) or a timeout (-2, reported).
+__device__ __forceinline__ int team_wait_publication(TeamSlot* t, int kidx, int last, int lane, int* err)
+{
+  int g = 0;
+  if (lane == 0) {
+    int it = 0;
+    for (;;) {
+      const int pub = ld_vol(&t->pub);
+      if (pub == kTeamRelease) { g = -1; break; }
+      if ((pub >> 4) > last && kidx < (pub & 15)) { g = pub >> 4; break; }
+      if (++it >= kTeamSpin) { g = -2; atomicOr(err, kErrTimeout); break; }
+      __nanosleep(64);
+    }
+    __threadfence_block();
+  }
+  g = __shfl_sync(FULL_MASK, g, 0);
+  __syncwarp();  // orders lane 0's observation before every lane's reads
+  return g;
+}
+
+__shared__ TeamSlot g_team[kMaxIntervalWarps];
+
+// Per-warp state of the interval loop that the move code does not need: it
+// lives in shared memory (written by lane 0, read by the whole warp after a
+// __syncwarp), so that the registers of the move code are the same as in a
+// loop without helpers.
+struct WarpState {
+  double tau_left, logw, b, el;
+  unsigned long long m;
+  df bdf;
+  int s, jumps, finish;
+  int owner, kidx, last;
+};
+__shared__ WarpState g_ws[kMaxIntervalWarps];
+
+// The interval loop of the FP32-pipe evaluations (double-float and FP32):
+// each warp is an owner while it runs a walker (the same steps, draws and
+// arithmetic as the loop of the FP64 mode below), then a helper of the
+// warps of its block that still run one.
+template <class NT, int PR, bool NJ, bool NC>
+__device__ __forceinline__ void interval_team(const SysDev& S, const Layout& Lo, const LatDev& L, const PopDev& P,
+                                              double* sC, uint64_t k, bool recompute, int lane, int wib)
+{
+  typedef Ar<NT> A;
+  const int P_moves = S.N * 6 * L.G;
+  const BlockMem bm = block_mem(S, sC);
+  TeamSlot* mine = &g_team[wib];
+  WarpState& st = g_ws[wib];
+  enum { kNeed, kOwner, kSearch, kHelper, kDone };
+  int mode = kNeed;
+  for (;;) {
+    if (mode == kNeed) {
+      int idx = 0;
+      if (lane == 0) idx = atomicAdd(P.counter, 1);
+      idx = __shfl_sync(FULL_MASK, idx, 0);
+      if (idx >= P.W) {
+        // out of walkers: a kernel launched after this one with programmatic
+        // stream serialization (the pipelined batch) may start on the SMs
+        // this block frees
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+        mode = P.helpers ? kSearch : kDone;
+      } else {
+        if (P.helpers) team_open(mine, lane);
+        const int s = P.order[idx];
+        const WarpMem wm = warp_mem(Lo, S, sC + Lo.head + wib * Lo.smem_warp);
+        double b, el;
+        load_record(Lo, P.rec_src + (size_t)P.parent[s] * Lo.rec, wm, lane, b, el);
+        if (recompute) {
+          bool ok = warp_inverse(S, sC, wm.x, 0, wm.A, wm.scr, lane);
+          ok = ok && warp_inverse(S, sC, wm.x, 1, wm.A + Lo.nu * Lo.nu, wm.scr, lane);
+          if (!ok && lane == 0) atomicOr(P.err, kErrSingular);
+        }
+        if (lane == 0) {
+          st.s = s;
+          st.b = b;
+          st.el = el;
+          st.bdf = df_from_double(b);
+          st.tau_left = P.tau;
+          st.logw = 0.0;
+          st.jumps = 0;
+          st.m = 0;
+          st.finish = 0;
+        }
+        __syncwarp();
+        mode = kOwner;
+      }
+    }
+    if (mode == kDone) break;
+    int target = wib, nh = 0;
+    if (mode == kOwner) {
+      const WarpMem wm = warp_mem(Lo, S, sC + Lo.head + wib * Lo.smem_warp);
+      const double b = st.b, el = st.el, tau_left = st.tau_left;
+      const df bdf = st.bdf;
+      bool over = st.finish != 0;
+      double t = 0.0, logw = st.logw;
+      uint64_t b0[4], b1[4];
+      if (!over) {
+        // both draws of this iteration at once: even lanes compute the
+        // (waiting time, heat bath) block, odd lanes the rotation block
+        uint64_t cb[4] = {(uint64_t)st.s, k, (uint64_t)st.m, (lane & 1) ? kTagRot : kTagTimeHB};
+        philox4x64_10(cb, P.seed, 0ull);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          b0[j] = shfl_u64(cb[j], 0);
+          b1[j] = shfl_u64(cb[j], 1);
+        }
+        if (PR == LRDMC_PRECISION_DF64)
+          t = b > 0.0 ? df_to_double(df_div(df_neg(df_log(df_u01(b0[0]), S.D.exp.K, bm.tab)), bdf)) : INFINITY;
+        else
+          t = b > 0.0 ? (double)(-logf(f_u01(b0[0])) / bdf.hi) : INFINITY;
+        if (t >= tau_left) {
+          logw -= tau_left * (el - P.e_trial);
+          over = true;
+        }
+      }
+      int i = 0, pick = -1;
+      if (!over) {
+        logw -= t * (el - P.e_trial);
+        // heat bath over the cached rates
+        int lastc;
+        if (PR == LRDMC_PRECISION_DF64)
+          warp_scan_m<df>(reinterpret_cast<const df*>(wm.T), P_moves, lane, df_mul(df_u01(b0[1]), bdf), &pick,
+                          &lastc);
+        else
+          warp_scan_m<float>(reinterpret_cast<const df*>(wm.T), P_moves, lane, f_u01(b0[1]) * bdf.hi, &pick,
+                             &lastc);
+        if (pick < 0) pick = lastc;
+        if (pick < 0) {  // no allowed move: cannot happen with b > 0
+          if (lane == 0) atomicOr(P.err, kErrNonFinite);
+          over = true;
+        }
+      }
+      double pnew[3];
+      if (!over) {
+        const int per_e = 6 * L.G;
+        i = pick / per_e;
+        const int rem = pick - i * per_e, g = rem / 6, kx = (rem % 6) >> 1;
+        const double sign = (pick & 1) ? -1.0 : 1.0, h = g ? L.ap : L.a;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) pnew[d] = wm.x[3 * i + d] + sign * h * wm.R[3 * d + kx];
+        bool sm_ok;
+        if (PR != LRDMC_PRECISION_FP32) {
+          // the parity modes keep the update in IEEE double: near a node the
+          // update amplifies rounding by the condition number of the Slater
+          // matrix, and a double-float update (2^-48) parts trajectories
+          // from the FP64 reference in rare walkers
+          sm_ok = warp_sm_update<PR>(S, sC, wm, i, pnew, lane);
+        } else {
+          // the new position as a double-float (the shared-memory
+          // double-float copies of x and R belong to the last evaluation,
+          // which for the first jump of an interval may have been another
+          // walker's)
+          df pd[3] = {df_from_double(pnew[0]), df_from_double(pnew[1]), df_from_double(pnew[2])};
+          sm_ok = warp_sm_update_df(S, bm, wm, i, pd, lane);
+        }
+        if (!sm_ok) {
+          if (lane == 0) atomicOr(P.err, kErrSingular);
+          over = true;
+        }
+      }
+      if (over) {
+        if (P.helpers) team_close(mine, lane);
+        store_record(Lo, P.rec_dst + (size_t)st.s * Lo.rec, wm, lane, b, el);
+        if (lane == 0) {
+          const int s = st.s;
+          P.logw[s] = logw;
+          P.wgt[s] = exp(logw);
+          P.el_end[s] = el;
+          P.jumps[s] = st.jumps;
+        }
+        __syncwarp();
+        mode = kNeed;
+        continue;
+      }
+      if (lane == 0) {
+        st.logw = logw;
+        st.tau_left = tau_left - t;
+      }
+      if (lane < 3) wm.x[3 * i + lane] = pnew[lane];
+      __syncwarp();
+      rotation_matrix_warp<PR>(b1, wm.R, lane, S);
+      __syncwarp();
+      double eln;
+      eval_prelude_m<NT, NJ, NC>(S, sC, L, wm, lane, eln);
+      if (lane == 0) st.el = eln;
+      if (P.helpers) nh = team_publish(mine, lane);
+    } else {
+      if (mode == kSearch) {
+        int kidx;
+        const int o = team_attach(g_team, blockDim.x >> 5, wib, lane, kidx);
+        if (o < 0) {
+          mode = kDone;
+          continue;
+        }
+        if (lane == 0) {
+          st.owner = o;
+          st.kidx = kidx;
+          st.last = 0;
+        }
+        __syncwarp();
+        mode = kHelper;
+      }
+      const int gw = team_wait_publication(&g_team[st.owner], st.kidx, st.last, lane, P.err);
+      if (gw == -2) {
+        mode = kDone;
+        continue;
+      }
+      if (gw == -1) {
+        mode = kSearch;
+        continue;
+      }
+      if (lane == 0) st.last = gw;
+      target = st.owner;
+    }
+    // the moves of the target walker's evaluation: one copy of the move
+    // code for the owner alone, the owner with helpers, and the helpers
+    {
+      const WarpMem twm = warp_mem(Lo, S, sC + Lo.head + target * Lo.smem_warp);
+      chunked_moves<NT, NJ, NC>(S, L, twm, bm, (mode == kHelper || nh > 0) ? &g_team[target] : nullptr, P_moves,
+                                lane);
+    }
+    if (mode == kHelper) {
+      if (lane == 0) atomicAdd(&g_team[target].done, 1);
+      __syncwarp();
+      continue;
+    }
+    if (nh > 0) team_wait_helpers(mine, nh, lane, P.err);
+    const NT btot = warp_scan_m<NT>(reinterpret_cast<const df*>(warp_mem(Lo, S, sC + Lo.head + wib * Lo.smem_warp).T),
+                                    P_moves, lane, A::zero(), nullptr, nullptr);
+    const double b = A::to_double(btot);
+    if (lane == 0) {
+      st.bdf = A::store(btot);
+      st.b = b;
+      st.jumps = st.jumps + 1;
+      int fin = 0;
+      if (!isfinite(st.el) || !isfinite(b)) {
+        atomicOr(P.err, kErrNonFinite);
+        fin = 1;
+      }
+      if (st.m + 1 >= (unsigned long long)kMaxItersPerInterval) {
+        atomicOr(P.err, kErrIters);
+        fin = 1;
+      }
+      st.finish = fin;
+      st.m = st.m + 1;
+    }
+    __syncwarp();
+  }
+}
+
 // One interval of length tau for every walker slot (continuous-time
 // projection of the cited LRDMC method): wait for an exponential time of
 // rate b_x, decrease log w by (E_L - E_T) times the time spent, and at the
 // end of the wait jump to move c with probability T_c / b_x.
 #ifndef LRDMC_INTERVAL_MIN_BLOCKS
-#define LRDMC_INTERVAL_MIN_BLOCKS 4
+#define LRDMC_INTERVAL_MIN_BLOCKS 1
 #endif
 template <int PREC>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, LRDMC_INTERVAL_MIN_BLOCKS)
+__global__ void __launch_bounds__(kMaxIntervalWarps * 32, LRDMC_INTERVAL_MIN_BLOCKS)
 k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, const PopDev P)
 {
   constexpr int PR = PREC & 3;         // the arithmetic (LRDMC_PRECISION_*)
@@ -1772,124 +2181,137 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
   // interval
   const uint64_t k = *P.kdev;
   const bool recompute = k > 0 && P.recompute_every > 0 && k % (uint64_t)P.recompute_every == 0;
-  stage_coefficients(S, sC);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  WarpMem wm = warp_mem(Lo, S, sC + Lo.head + wib * Lo.smem_warp);
-  const int P_moves = S.N * 6 * L.G;
-  const BlockMem bm = block_mem(S, sC);
-  for (;;) {
-    int idx = 0;
-    if (lane == 0) idx = atomicAdd(P.counter, 1);
-    idx = __shfl_sync(FULL_MASK, idx, 0);
-    if (idx >= P.W) {
-      // out of walkers: a kernel launched after this one with programmatic
-      // stream serialization (the pipelined batch) may start on the SMs
-      // this block frees
-      asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-      break;
-    }
-    const int s = P.order[idx];
-    const int src = P.parent[s];
-    double b, el;
-    load_record(Lo, P.rec_src + (size_t)src * Lo.rec, wm, lane, b, el);
-    df bdf = df_from_double(b);
-    if (recompute) {
-      bool ok = warp_inverse(S, sC, wm.x, 0, wm.A, wm.scr, lane);
-      ok = ok && warp_inverse(S, sC, wm.x, 1, wm.A + Lo.nu * Lo.nu, wm.scr, lane);
-      if (!ok && lane == 0) atomicOr(P.err, kErrSingular);
-    }
-    double tau_left = P.tau, logw = 0.0;
-    int jumps = 0;
-    for (uint64_t m = 0;; ++m) {
-      // both draws of this iteration at once: even lanes compute the
-      // (waiting time, heat bath) block, odd lanes the rotation block
-      uint64_t cb[4] = {(uint64_t)s, k, m, (lane & 1) ? kTagRot : kTagTimeHB};
-      philox4x64_10(cb, P.seed, 0ull);
-      uint64_t b0[4], b1[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        b0[j] = shfl_u64(cb[j], 0);
-        b1[j] = shfl_u64(cb[j], 1);
-      }
-      double t;
-      if (PR == LRDMC_PRECISION_DF64)
-        t = b > 0.0 ? df_to_double(df_div(df_neg(df_log(df_u01(b0[0]), S.D.exp.K, bm.tab)), bdf)) : INFINITY;
-      else if (PR == LRDMC_PRECISION_FP32)
-        t = b > 0.0 ? (double)(-logf(f_u01(b0[0])) / bdf.hi) : INFINITY;
-      else
-        t = b > 0.0 ? -log(to_u01(b0[0])) / b : INFINITY;
-      if (t >= tau_left) {
-        logw -= tau_left * (el - P.e_trial);
-        break;
-      }
-      logw -= t * (el - P.e_trial);
-      tau_left -= t;
-      // heat bath over the cached rates
-      int pick, last;
-      if (PR == LRDMC_PRECISION_DF64)
-        warp_scan_m<df>(reinterpret_cast<const df*>(wm.T), P_moves, lane, df_mul(df_u01(b0[1]), bdf), &pick, &last);
-      else if (PR == LRDMC_PRECISION_FP32)
-        warp_scan_m<float>(reinterpret_cast<const df*>(wm.T), P_moves, lane, f_u01(b0[1]) * bdf.hi, &pick, &last);
-      else
-        warp_scan(wm.T, P_moves, lane, to_u01(b0[1]) * b, &pick, &last);
-      if (pick < 0) pick = last;
-      if (pick < 0) {  // no allowed move: cannot happen with b > 0
-        if (lane == 0) atomicOr(P.err, kErrNonFinite);
-        break;
-      }
-      const int per_e = 6 * L.G;
-      const int i = pick / per_e, rem = pick - i * per_e, g = rem / 6, kx = (rem % 6) >> 1;
-      const double sign = (pick & 1) ? -1.0 : 1.0, h = g ? L.ap : L.a;
-      double pnew[3];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) pnew[d] = wm.x[3 * i + d] + sign * h * wm.R[3 * d + kx];
-      bool sm_ok;
-      if (PR != LRDMC_PRECISION_FP32) {
-        // the parity modes keep the update in IEEE double: near a node the
-        // update amplifies rounding by the condition number of the Slater
-        // matrix, and a double-float update (2^-48) parts trajectories from
-        // the FP64 reference in rare walkers
-        sm_ok = warp_sm_update<PR>(S, sC, wm, i, pnew, lane);
-      } else {
-        // the new position as a double-float (the shared-memory double-float
-        // copies of x and R belong to the last evaluation, which for the
-        // first jump of an interval may have been another walker's)
-        df pd[3] = {df_from_double(pnew[0]), df_from_double(pnew[1]), df_from_double(pnew[2])};
-        sm_ok = warp_sm_update_df(S, bm, wm, i, pd, lane);
-      }
-      if (!sm_ok) {
-        if (lane == 0) atomicOr(P.err, kErrSingular);
-        break;
-      }
-      if (lane < 3) wm.x[3 * i + lane] = pnew[lane];
-      __syncwarp();
-      rotation_matrix_warp<PR>(b1, wm.R, lane, S);
-      __syncwarp();
-      warp_eval_any<PR, NJ, NC>(S, sC, L, wm, lane, nullptr, b, bdf, el);
-      ++jumps;
-      if (!isfinite(el) || !isfinite(b)) {
-        if (lane == 0) atomicOr(P.err, kErrNonFinite);
-        break;
-      }
-      if (m + 1 >= (uint64_t)kMaxItersPerInterval) {
-        if (lane == 0) atomicOr(P.err, kErrIters);
-        break;
-      }
-    }
-    store_record(Lo, P.rec_dst + (size_t)s * Lo.rec, wm, lane, b, el);
-    if (lane == 0) {
-      P.logw[s] = logw;
-      P.wgt[s] = exp(logw);
-      P.el_end[s] = el;
-      P.jumps[s] = jumps;
-    }
-    __syncwarp();
+  if (PR != LRDMC_PRECISION_FP64 && lane == 0) {
+    g_team[wib].attach = kTeamClosed;
+    g_team[wib].pub = 0;
+    g_team[wib].next = 0;
+    g_team[wib].done = 0;
+    g_team[wib].gen = 0;
   }
-  // Launched early behind another system's interval kernel (pipelined
-  // batch): this grid does not read that kernel's results, but it finishes
-  // only after that kernel has, so that work after the chain in the stream
-  // sees every kernel of the chain complete. Without a prerequisite grid
-  // the wait returns at once.
+  stage_coefficients(S, sC);  // ends with __syncthreads
+  if constexpr (PR != LRDMC_PRECISION_FP64) {
+    if (PR == LRDMC_PRECISION_DF64) interval_team<df, PR, NJ, NC>(S, Lo, L, P, sC, k, recompute, lane, wib);
+    else interval_team<float, PR, NJ, true>(S, Lo, L, P, sC, k, recompute, lane, wib);
+  } else {
+    // the FP64 mode: every warp alone
+    WarpMem wm = warp_mem(Lo, S, sC + Lo.head + wib * Lo.smem_warp);
+    const int P_moves = S.N * 6 * L.G;
+    const BlockMem bm = block_mem(S, sC);
+    for (;;) {
+      int idx = 0;
+      if (lane == 0) idx = atomicAdd(P.counter, 1);
+      idx = __shfl_sync(FULL_MASK, idx, 0);
+      if (idx >= P.W) {
+        // out of walkers: a kernel launched after this one with programmatic
+        // stream serialization (the pipelined batch) may start on the SMs
+        // this block frees
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+        break;
+      }
+      const int s = P.order[idx];
+      const int src = P.parent[s];
+      double b, el;
+      load_record(Lo, P.rec_src + (size_t)src * Lo.rec, wm, lane, b, el);
+      df bdf = df_from_double(b);
+      if (recompute) {
+        bool ok = warp_inverse(S, sC, wm.x, 0, wm.A, wm.scr, lane);
+        ok = ok && warp_inverse(S, sC, wm.x, 1, wm.A + Lo.nu * Lo.nu, wm.scr, lane);
+        if (!ok && lane == 0) atomicOr(P.err, kErrSingular);
+      }
+      double tau_left = P.tau, logw = 0.0;
+      int jumps = 0;
+      for (uint64_t m = 0;; ++m) {
+        // both draws of this iteration at once: even lanes compute the
+        // (waiting time, heat bath) block, odd lanes the rotation block
+        uint64_t cb[4] = {(uint64_t)s, k, m, (lane & 1) ? kTagRot : kTagTimeHB};
+        philox4x64_10(cb, P.seed, 0ull);
+        uint64_t b0[4], b1[4];
+  #pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          b0[j] = shfl_u64(cb[j], 0);
+          b1[j] = shfl_u64(cb[j], 1);
+        }
+        double t;
+        if (PR == LRDMC_PRECISION_DF64)
+          t = b > 0.0 ? df_to_double(df_div(df_neg(df_log(df_u01(b0[0]), S.D.exp.K, bm.tab)), bdf)) : INFINITY;
+        else if (PR == LRDMC_PRECISION_FP32)
+          t = b > 0.0 ? (double)(-logf(f_u01(b0[0])) / bdf.hi) : INFINITY;
+        else
+          t = b > 0.0 ? -log(to_u01(b0[0])) / b : INFINITY;
+        if (t >= tau_left) {
+          logw -= tau_left * (el - P.e_trial);
+          break;
+        }
+        logw -= t * (el - P.e_trial);
+        tau_left -= t;
+        // heat bath over the cached rates
+        int pick, last;
+        if (PR == LRDMC_PRECISION_DF64)
+          warp_scan_m<df>(reinterpret_cast<const df*>(wm.T), P_moves, lane, df_mul(df_u01(b0[1]), bdf), &pick, &last);
+        else if (PR == LRDMC_PRECISION_FP32)
+          warp_scan_m<float>(reinterpret_cast<const df*>(wm.T), P_moves, lane, f_u01(b0[1]) * bdf.hi, &pick, &last);
+        else
+          warp_scan(wm.T, P_moves, lane, to_u01(b0[1]) * b, &pick, &last);
+        if (pick < 0) pick = last;
+        if (pick < 0) {  // no allowed move: cannot happen with b > 0
+          if (lane == 0) atomicOr(P.err, kErrNonFinite);
+          break;
+        }
+        const int per_e = 6 * L.G;
+        const int i = pick / per_e, rem = pick - i * per_e, g = rem / 6, kx = (rem % 6) >> 1;
+        const double sign = (pick & 1) ? -1.0 : 1.0, h = g ? L.ap : L.a;
+        double pnew[3];
+  #pragma unroll
+        for (int d = 0; d < 3; ++d) pnew[d] = wm.x[3 * i + d] + sign * h * wm.R[3 * d + kx];
+        bool sm_ok;
+        if (PR != LRDMC_PRECISION_FP32) {
+          // the parity modes keep the update in IEEE double: near a node the
+          // update amplifies rounding by the condition number of the Slater
+          // matrix, and a double-float update (2^-48) parts trajectories from
+          // the FP64 reference in rare walkers
+          sm_ok = warp_sm_update<PR>(S, sC, wm, i, pnew, lane);
+        } else {
+          // the new position as a double-float (the shared-memory double-float
+          // copies of x and R belong to the last evaluation, which for the
+          // first jump of an interval may have been another walker's)
+          df pd[3] = {df_from_double(pnew[0]), df_from_double(pnew[1]), df_from_double(pnew[2])};
+          sm_ok = warp_sm_update_df(S, bm, wm, i, pd, lane);
+        }
+        if (!sm_ok) {
+          if (lane == 0) atomicOr(P.err, kErrSingular);
+          break;
+        }
+        if (lane < 3) wm.x[3 * i + lane] = pnew[lane];
+        __syncwarp();
+        rotation_matrix_warp<PR>(b1, wm.R, lane, S);
+        __syncwarp();
+        warp_eval_any<PR, NJ, NC>(S, sC, L, wm, lane, nullptr, b, bdf, el);
+        ++jumps;
+        if (!isfinite(el) || !isfinite(b)) {
+          if (lane == 0) atomicOr(P.err, kErrNonFinite);
+          break;
+        }
+        if (m + 1 >= (uint64_t)kMaxItersPerInterval) {
+          if (lane == 0) atomicOr(P.err, kErrIters);
+          break;
+        }
+      }
+      store_record(Lo, P.rec_dst + (size_t)s * Lo.rec, wm, lane, b, el);
+      if (lane == 0) {
+        P.logw[s] = logw;
+        P.wgt[s] = exp(logw);
+        P.el_end[s] = el;
+        P.jumps[s] = jumps;
+      }
+      __syncwarp();
+    }
+    // Launched early behind another system's interval kernel (pipelined
+    // batch): this grid does not read that kernel's results, but it finishes
+    // only after that kernel has, so that work after the chain in the stream
+    // sees every kernel of the chain complete. Without a prerequisite grid
+    // the wait returns at once.
+  }
   if (threadIdx.x == 0) asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
@@ -2255,27 +2677,50 @@ cudaError_t launch_eval_all(const SysDev& S, const Layout& Lo, const LatDev& L, 
   return cudaErrorInvalidValue;
 }
 
+static int sm_count_current()
+{
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+                                                cudaSuccess)
+    return 152;
+  return n;
+}
+
+// Warps per block of the interval kernel: 16 (so that the warps of an SM,
+// one block, can help one another at the end of an interval), halved while
+// the population cannot give every warp of every SM a walker or the block's
+// shared memory does not fit; at least the other kernels' four.
+int interval_warps(const Layout& Lo, int W)
+{
+  const int sms = sm_count_current();
+  int w = kMaxIntervalWarps;
+  while (w > kWarpsPerBlock &&
+         ((int)sizeof(double) * (Lo.head + w * Lo.smem_warp) > kMaxSmemBlock || W < sms * w))
+    w >>= 1;
+  return w;
+}
+
+static int interval_smem(const Layout& Lo, int w) { return (int)sizeof(double) * (Lo.head + w * Lo.smem_warp); }
+
 // Persistent grid of the interval kernel: as many blocks as fit on the GPU
 // at once (occupancy for this system's shared memory), at most one warp per
 // walker.
 template <int PREC>
-static cudaError_t interval_occupancy(const Layout& Lo, int* blocks)
+static cudaError_t interval_occupancy(const Layout& Lo, int w, int* blocks)
 {
-  int dev, sm_count = 0, per_sm = 0;
-  cudaError_t e = set_smem((const void*)k_interval<PREC>, Lo.smem_block_bytes);
-  if (e == cudaSuccess) e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
+  int per_sm = 0;
+  cudaError_t e = set_smem((const void*)k_interval<PREC>, interval_smem(Lo, w));
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interval<PREC>, kWarpsPerBlock * 32,
-                                                      Lo.smem_block_bytes);
-  *blocks = (per_sm < 1 ? 1 : per_sm) * sm_count;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interval<PREC>, w * 32, interval_smem(Lo, w));
+  *blocks = (per_sm < 1 ? 1 : per_sm) * sm_count_current();
   return e;
 }
 
-int interval_default_blocks(const SysDev& S, const Layout& Lo)
+int interval_default_blocks(const SysDev& S, const Layout& Lo, int W)
 {
   int b = 0;
-  LRDMC_DISPATCH(S, Lo, interval_occupancy<V>(Lo, &b));
+  const int w = interval_warps(Lo, W);
+  LRDMC_DISPATCH(S, Lo, interval_occupancy<V>(Lo, w, &b));
   return b;
 }
 
@@ -2284,20 +2729,22 @@ static cudaError_t launch_interval_t(const SysDev& S, const Layout& Lo, const La
                                      int blocks, int carveout, bool pdl, cudaStream_t st)
 {
   static int cached_blocks = -1, cached_smem = -1;
-  cudaError_t e = set_smem((const void*)k_interval<PREC>, Lo.smem_block_bytes);
+  const int w = interval_warps(Lo, P.W);
+  const int smem = interval_smem(Lo, w);
+  cudaError_t e = set_smem((const void*)k_interval<PREC>, smem);
   if (e != cudaSuccess) return e;
   if (blocks <= 0) {
-    if (cached_smem != Lo.smem_block_bytes) {
-      e = interval_occupancy<PREC>(Lo, &cached_blocks);
+    if (cached_smem != smem) {
+      e = interval_occupancy<PREC>(Lo, w, &cached_blocks);
       if (e != cudaSuccess) return e;
-      cached_smem = Lo.smem_block_bytes;
+      cached_smem = smem;
     }
     blocks = cached_blocks;
   }
-  const int need = (P.W + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  const int need = (P.W + w - 1) / w;
   if (blocks > need) blocks = need;
   if (carveout < 0 && !pdl) {
-    k_interval<PREC><<<blocks, kWarpsPerBlock * 32, Lo.smem_block_bytes, st>>>(S, Lo, L, P);
+    k_interval<PREC><<<blocks, w * 32, smem, st>>>(S, Lo, L, P);
     return cudaGetLastError();
   }
   // the same launch with launch attributes: a preferred shared-memory
@@ -2307,8 +2754,8 @@ static cudaError_t launch_interval_t(const SysDev& S, const Layout& Lo, const La
   // kernel in the stream has run out of walkers)
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(blocks);
-  cfg.blockDim = dim3(kWarpsPerBlock * 32);
-  cfg.dynamicSmemBytes = Lo.smem_block_bytes;
+  cfg.blockDim = dim3(w * 32);
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[2];
   int na = 0;

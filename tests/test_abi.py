@@ -150,3 +150,12 @@ def test_batch_binding_methods(pkg):
     for name in ("step", "sync", "set_groups", "set_carveout", "set_pipelined"):
         assert callable(getattr(pkg.LrdmcBatch, name)), name
     assert isinstance(pkg.LrdmcBatch.stream_ptr, property)
+
+
+def test_set_tail_helpers_arguments(pkg):
+    """The tail-helper switch takes 0 or 1; anything else is LRDMC_ERR_ARG."""
+    g = pkg.LrdmcSystem(S.helium())
+    g.set_tail_helpers(False).set_tail_helpers(True)
+    with pytest.raises(pkg.LrdmcError) as e:
+        g._check(pkg.load_library().lrdmc_set_tail_helpers(g.h, 2))
+    assert e.value.status == pkg.ERR_ARG
