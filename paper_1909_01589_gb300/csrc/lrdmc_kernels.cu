@@ -1841,14 +1841,19 @@ __device__ __forceinline__ void chunked_moves(const SysDev& S, const LatDev& L, 
                                               TeamSlot* t, int P, int lane)
 {
   df* Td = reinterpret_cast<df*>(wm.T);
+#ifdef LRDMC_TEAM_CHUNK16
+  const int cs = t ? 16 : 32;
+#else
+  const int cs = 32;
+#endif
   for (int c0 = 0;; c0 += 32) {
     if (t) {
       int c = 0;
-      if (lane == 0) c = atomicAdd(&t->next, 32);
+      if (lane == 0) c = atomicAdd(&t->next, cs);
       c0 = __shfl_sync(FULL_MASK, c, 0);
     }
     if (c0 >= P) break;
-    if (c0 + lane < P) candidate_m<NT, NJ, NC>(S, L, wm, bm, c0 + lane, Td, nullptr);
+    if (lane < cs && c0 + lane < P) candidate_m<NT, NJ, NC>(S, L, wm, bm, c0 + lane, Td, nullptr);
   }
   if (t) __threadfence_block();
   __syncwarp();
