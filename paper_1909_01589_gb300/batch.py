@@ -79,6 +79,7 @@ def candidate_plans(defaults, work, need):
         serial[i] = rank
     plans.append(("serial", serial, list(cap), -1, 0))
     plans.append(("pipelined, heaviest first", serial, list(cap), -1, 1))
+    plans.append(("pipelined, heaviest first, max shared carveout", serial, list(cap), 100, 1))
     plans.append(("pipelined, lightest first", [n - 1 - r for r in serial], list(cap), -1, 1))
     heavy = by_work[0]
     rest = [i for i in range(n) if i != heavy]
