@@ -68,3 +68,30 @@ def test_helpers_with_a_few_blocks(pkg):
     off = _run(pkg, "Ne", 40, 0.2, 0.025, -128.9, 3, pkg.PRECISION_DF64, False, blocks=2)
     on = _run(pkg, "Ne", 40, 0.2, 0.025, -128.9, 3, pkg.PRECISION_DF64, True, blocks=2)
     assert np.array_equal(off[0]["x"], on[0]["x"]) and np.array_equal(off[1], on[1])
+
+
+def test_helpers_neural_and_no_cache_variants(pkg):
+    """The kernel variants with the neural pair term (double-float) and
+    without the evaluation caches (the 48-electron cluster): helpers on and
+    off give the same bits."""
+    system = S.neon()
+    spec = S.default_neural_spec(system)
+    params = S.neural_init(spec, 3, out_scale=0.5)
+    runs = []
+    for helpers in (False, True):
+        g = pkg.LrdmcSystem(system).set_tail_helpers(helpers)
+        g.set_neural_jastrow(spec, params)
+        g.init_walkers(torch.tensor(S.initial_positions(system, 600, 71), device="cuda"), seed=72, tau=0.025,
+                       e_trial=-128.9, recompute_every=3, trace_capacity=3)
+        g.step(3, 0.2, pkg.Spacing(pkg.THIS_WORK))
+        runs.append((g.walkers()["x"], g.energy_trace()[0]))
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+    system = S.cluster(8, 24, 2)
+    runs = []
+    for helpers in (False, True):
+        g = pkg.LrdmcSystem(system).set_tail_helpers(helpers)
+        g.init_walkers(torch.tensor(S.initial_positions(system, 40, 73), device="cuda"), seed=74, tau=0.002,
+                       e_trial=40.0, recompute_every=3, trace_capacity=2)
+        g.step(2, 0.3, pkg.Spacing(pkg.THIS_WORK))
+        runs.append((g.walkers()["x"], g.energy_trace()[0]))
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
