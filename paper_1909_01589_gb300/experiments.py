@@ -208,7 +208,7 @@ def neural_vs_pade(names=("Ne", "Ar"), W=16384, steps=600, equil=150, n_train=1 
 
 
 def extrapolation(name="He", a_values=(0.4, 0.3, 0.2, 0.15, 0.1), W=8192, steps=2000, equil=200, seed=5,
-                  neural=False, n_train=1 << 18, train_steps=600, a_train=0.2):
+                  neural=False, n_train=1 << 18, train_steps=600, a_train=0.2, proj_time=None):
     """E(a) on the single grid and on this work's double grid at several
     lattice spacings, and the a -> 0 limits from the weighted least-squares
     fit E(a) = E0 + k1 a^2 + k2 a^4 (the three-parameter fit of the paper's
@@ -219,12 +219,18 @@ def extrapolation(name="He", a_values=(0.4, 0.3, 0.2, 0.15, 0.1), W=8192, steps=
     (configurations of a plain projection at a_train on this work's double
     grid) and installed in every run: the guiding function changes E(a) at
     finite a, not the fixed-node limit, so the limits must agree with the
-    plain ones."""
+    plain ones.
+
+    With ``proj_time`` every lattice spacing covers the same projection
+    time (intervals = proj_time / tau, tau for about 10 jumps per walker per
+    interval), so that the points carry comparable errors; otherwise every
+    spacing runs ``steps`` intervals."""
     import lrdmc_synth as S
 
     system = S.make_system(name)
     e_trial = DEFAULTS[name][1]
-    out = {"system": name, "a": list(a_values), "walkers": W, "steps": steps, "neural": bool(neural)}
+    out = {"system": name, "a": list(a_values), "walkers": W, "steps": steps, "neural": bool(neural),
+           "proj_time": proj_time}
     nj = None
     if neural:
         import torch
@@ -255,7 +261,8 @@ def extrapolation(name="He", a_values=(0.4, 0.3, 0.2, 0.15, 0.1), W=8192, steps=
         E, err = [], []
         for a in a_values:
             tau = _tau_for(system, a, sp, 10.0, seed)
-            r = run(system, a, sp, W, steps, equil, tau, e_trial, seed, neural=nj)
+            n_steps = steps if proj_time is None else max(200, int(round(proj_time / tau)))
+            r = run(system, a, sp, W, n_steps, equil, tau, e_trial, seed, neural=nj)
             E.append(r["energy"])
             err.append(r["error"])
         fit = fit_a0(a_values, E, err)
@@ -434,6 +441,10 @@ def main():
     ap.add_argument("--out", default="results/single_vs_double.json")
     ap.add_argument("--summarize", nargs="*", help="only write the markdown table of these result files")
     ap.add_argument("--neural", action="store_true", help="the neural Jastrow against Pade instead")
+    ap.add_argument("--proj-time", type=float, default=None,
+                    help="with --extrapolate: the projection time (1/Ha) every lattice spacing covers")
+    ap.add_argument("--a-values", default=None, help="with --extrapolate: comma-separated lattice spacings")
+    ap.add_argument("--walkers", type=int, default=None, help="with --extrapolate: walkers per run")
     ap.add_argument("--mixed", action="store_true",
                     help="mixed-precision (FP32 evaluation) energy against the FP64-parity form instead")
     ap.add_argument("--extrapolate", action="store_true",
@@ -446,7 +457,13 @@ def main():
         json.dump(rows, open(args.out, "w"), indent=1)
         return
     if args.extrapolate:
-        row = extrapolation(args.systems.split(",")[0], steps=args.steps, equil=args.equil, neural=args.neural)
+        kw = {}
+        if args.a_values:
+            kw["a_values"] = tuple(float(v) for v in args.a_values.split(","))
+        if args.walkers:
+            kw["W"] = args.walkers
+        row = extrapolation(args.systems.split(",")[0], steps=args.steps, equil=args.equil, neural=args.neural,
+                            proj_time=args.proj_time, **kw)
         os.makedirs(os.path.dirname(args.out) or ".", exist_ok=True)
         json.dump(row, open(args.out, "w"), indent=1)
         return
