@@ -181,6 +181,17 @@ LRDMC_API lrdmc_status lrdmc_sync(lrdmc_system_t sys);
 LRDMC_API lrdmc_status lrdmc_get_energy_trace(lrdmc_system_t sys, double* e, double* wbar,
                                     double* mean_jumps, int max_n, int* n_written);
 
+/* The Sherman-Morrison residual of every interval so far (not a step of
+ * the paper's method: a diagnostic of the cited LRDMC implementation's
+ * rank-one inverse updates). At the start of an interval whose inverse
+ * Slater matrices are rebuilt (k > 0, k a multiple of recompute_every), the
+ * kernel first measures, for every walker and spin block, max |sum_m
+ * A[l][m] Ainv[m][q] - delta_lq| of the inverse the updates carried, A the
+ * Slater matrix at the current positions; resid[k] is the largest over the
+ * population, and -1 at intervals without a rebuild. Same count and
+ * synchronisation as lrdmc_get_energy_trace. */
+LRDMC_API lrdmc_status lrdmc_get_residual_trace(lrdmc_system_t sys, double* resid, int max_n, int* n_written);
+
 /* Copies the population to host arrays (each nullable): positions
  * [W][N][3], E_L [W], b [W] and rates T [W][P] of the cached evaluation,
  * the pre-reconfiguration log-weights and jump counts [W] of the last

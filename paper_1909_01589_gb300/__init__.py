@@ -30,7 +30,8 @@ PRECISION_FP64, PRECISION_DF64, PRECISION_FP32 = 0, 1, 2
 
 EXPORTED = [
     "lrdmc_create_system", "lrdmc_spacing_params", "lrdmc_workspace_bytes", "lrdmc_init_walkers",
-    "lrdmc_step", "lrdmc_sync", "lrdmc_get_energy_trace", "lrdmc_get_walkers", "lrdmc_moves", "lrdmc_evaluate",
+    "lrdmc_step", "lrdmc_sync", "lrdmc_get_energy_trace", "lrdmc_get_residual_trace", "lrdmc_get_walkers",
+    "lrdmc_moves", "lrdmc_evaluate",
     "lrdmc_evaluate_static", "lrdmc_evaluate_tc",
     "lrdmc_save", "lrdmc_load", "lrdmc_set_precision", "lrdmc_set_profiling", "lrdmc_kernel_times", "lrdmc_last_error",
     "lrdmc_destroy", "lrdmc_nj_n_params", "lrdmc_set_neural_jastrow", "lrdmc_base_terms", "lrdmc_nj_forward",
@@ -121,6 +122,8 @@ def load_library():
     L.lrdmc_sync.argtypes = [vp]
     L.lrdmc_get_energy_trace.restype = i
     L.lrdmc_get_energy_trace.argtypes = [vp, vp, vp, vp, i, ct.POINTER(i)]
+    L.lrdmc_get_residual_trace.restype = i
+    L.lrdmc_get_residual_trace.argtypes = [vp, vp, i, ct.POINTER(i)]
     L.lrdmc_get_walkers.restype = i
     L.lrdmc_get_walkers.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     L.lrdmc_moves.restype = i
@@ -295,6 +298,14 @@ class LrdmcSystem:
                                                           ct.byref(n)))
         k = n.value
         return e[:k].copy(), w[:k].copy(), j[:k].copy()
+
+    def residual_trace(self, max_n=1 << 20):
+        """Largest Sherman-Morrison residual max|A Ainv - I| per interval,
+        measured at each rebuild of the inverses (-1 where none)."""
+        n = ct.c_int()
+        r = np.zeros(max_n)
+        self._check(load_library().lrdmc_get_residual_trace(self.h, _np_ptr(r), max_n, ct.byref(n)))
+        return r[:n.value].copy()
 
     def walkers(self):
         W, N = self.W, self.N

@@ -412,7 +412,7 @@ lrdmc_status lrdmc_spacing_params(lrdmc_system_t s, double a, const lrdmc_spacin
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct WsPlan {
-  size_t rec, parent, order, logw, wgt, el, jumps, cum, trace, moves, err, counter, kdev, total;
+  size_t rec, parent, order, logw, wgt, el, jumps, cum, trace, moves, err, counter, kdev, resid, total;
 };
 
 static WsPlan plan_ws(const Layout& Lo, int W, int cap)
@@ -427,11 +427,12 @@ static WsPlan plan_ws(const Layout& Lo, int W, int cap)
   p.el = o; o += align256(sizeof(double) * (size_t)W);
   p.jumps = o; o += align256(sizeof(int) * (size_t)W);
   p.cum = o; o += align256(sizeof(double) * (size_t)W);
-  p.trace = o; o += align256(sizeof(double) * 3 * (size_t)cap);
+  p.trace = o; o += align256(sizeof(double) * 4 * (size_t)cap);
   p.moves = o; o += 256;
   p.err = o; o += 256;
   p.counter = o; o += 256;
   p.kdev = o; o += 256;
+  p.resid = o; o += 256;
   p.total = o;
   return p;
 }
@@ -500,6 +501,7 @@ lrdmc_status lrdmc_init_walkers(lrdmc_system_t s, int W, const double* x0, uint6
   P.err = (int*)(s->ws + p.err);
   P.counter = (int*)(s->ws + p.counter);
   P.kdev = (unsigned long long*)(s->ws + p.kdev);
+  P.resid = (unsigned long long*)(s->ws + p.resid);
   P.recompute_every = recompute_every;
   P.W = W;
   P.trace_cap = cap;
@@ -507,7 +509,7 @@ lrdmc_status lrdmc_init_walkers(lrdmc_system_t s, int W, const double* x0, uint6
   P.tau = tau;
   P.e_trial = e_trial;
   P.helpers = s->helpers;
-  cudaError_t e = cudaMemsetAsync(s->ws + p.moves, 0, 4 * 256, s->stream);  // moves, err, counter, kdev
+  cudaError_t e = cudaMemsetAsync(s->ws + p.moves, 0, 5 * 256, s->stream);  // moves, err, counter, kdev, resid
   if (e != cudaSuccess) return cuda_fail(s, e, "workspace clear");
   e = cudaMemsetAsync(P.logw, 0, sizeof(double) * W, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(P.wgt, 0, sizeof(double) * W, s->stream);
@@ -631,6 +633,24 @@ lrdmc_status lrdmc_get_energy_trace(lrdmc_system_t s, double* e_out, double* w_o
   }
   cudaError_t e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "stream synchronize");
+  if (n_written) *n_written = n;
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_get_residual_trace(lrdmc_system_t s, double* resid, int max_n, int* n_written)
+{
+  if (!s || !resid) return fail(s, LRDMC_ERR_ARG, "residual_trace: NULL");
+  if (!s->have_pop) return fail(s, LRDMC_ERR_STATE, "residual trace before init_walkers");
+  lrdmc_status ss = sync_system(s);
+  if (ss != LRDMC_OK) return ss;
+  int n = (int)((uint64_t)max_n < s->k ? (uint64_t)max_n : s->k);
+  if (n < 0) n = 0;
+  if (n > 0) {
+    cudaError_t e = cudaMemcpyAsync(resid, s->P.trace + (size_t)3 * s->trace_cap, sizeof(double) * n,
+                                    cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "residual trace copy");
+  }
   if (n_written) *n_written = n;
   return LRDMC_OK;
 }
@@ -776,7 +796,7 @@ lrdmc_status lrdmc_evaluate_static(lrdmc_system_t s, int n, const double* x, con
 
 // Checkpoint file: magic, sizes, counters, then the current record buffer,
 // parents, trace and the moves counter.
-static const uint64_t kMagic = 0x4C52444D43303031ull;  // "LRDMC001"
+static const uint64_t kMagic = 0x4C52444D43303032ull;  // "LRDMC002" (four trace columns)
 
 lrdmc_status lrdmc_save(lrdmc_system_t s, const char* path)
 {
@@ -785,7 +805,7 @@ lrdmc_status lrdmc_save(lrdmc_system_t s, const char* path)
   lrdmc_status ss = sync_system(s);
   if (ss != LRDMC_OK) return ss;
   const int W = s->W;
-  std::vector<double> rec((size_t)W * s->Lo.rec), trace(3 * (size_t)s->trace_cap);
+  std::vector<double> rec((size_t)W * s->Lo.rec), trace(4 * (size_t)s->trace_cap);
   std::vector<int> par(W);
   unsigned long long moves = 0;
   cudaError_t e = cudaMemcpyAsync(rec.data(), s->rec[s->cur], sizeof(double) * rec.size(), cudaMemcpyDeviceToHost, s->stream);
@@ -823,7 +843,7 @@ lrdmc_status lrdmc_load(lrdmc_system_t s, const char* path)
     return fail(s, LRDMC_ERR_ARG, "load: file does not match this population");
   }
   const int W = s->W;
-  std::vector<double> rec((size_t)W * s->Lo.rec), trace(3 * (size_t)s->trace_cap);
+  std::vector<double> rec((size_t)W * s->Lo.rec), trace(4 * (size_t)s->trace_cap);
   std::vector<int> par(W);
   unsigned long long moves = 0;
   ok = fread(rec.data(), sizeof(double), rec.size(), f) == rec.size() &&

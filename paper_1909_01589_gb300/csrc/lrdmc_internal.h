@@ -141,7 +141,10 @@ struct PopDev {
   double* el_end;
   int* jumps;
   double* cum;  // running weight sums of the comb (populations above kReconfigSmemW)
-  double* trace;  // [3][cap]
+  double* trace;  // [4][cap]: e_k, mean weight, mean jumps, Sherman-Morrison residual at the recompute
+  // largest Sherman-Morrison residual of the current interval's recompute,
+  // as the bits of a non-negative double (atomicMax orders them as doubles)
+  unsigned long long* resid;
   unsigned long long* moves;
   int* err;
   int* counter;

@@ -577,8 +577,13 @@ __device__ __forceinline__ BlockMem block_mem(const SysDev& S, double* smem)
 // partial pivoting (warp-cooperative). A[l][m] = phi_m(r_l); the inverse is
 // stored as Ainv[m][l]. Returns false for a singular matrix (below).
 // ----------------------------------------------------------------------------
+// With resid (nullable), first the residual of the inverse the block holds
+// (the Sherman-Morrison-updated one): max |sum_m A[l][m] Ainv[m][q] -
+// delta_lq| over the block, where A is the Slater matrix at the current
+// positions; *resid becomes the larger of itself and that residual (the
+// same value in every lane).
 __device__ LRDMC_COLD bool warp_inverse(const SysDev& S, const double* sC, const double* sx, int spin,
-                             double* Ainv, double* scr, int lane)
+                             double* Ainv, double* scr, int lane, double* resid = nullptr)
 {
   const int n = spin == 0 ? S.n_up : S.n_dn;
   if (n == 0) return true;
@@ -596,6 +601,18 @@ __device__ LRDMC_COLD bool warp_inverse(const SysDev& S, const double* sC, const
     }
   }
   __syncwarp();
+  if (resid) {
+    double r = 0.0;
+    for (int idx = lane; idx < n * n; idx += 32) {
+      const int l = idx / n, q = idx % n;
+      double a = (l == q) ? -1.0 : 0.0;
+      for (int m = 0; m < n; ++m) a += M[l * w2 + m] * Ainv[m * n + q];
+      r = fmax(r, fabs(a));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(FULL_MASK, r, o));
+    *resid = fmax(*resid, r);
+  }
   // Singular Slater matrix: two equal-spin electrons on one point (the
   // determinant vanishes by antisymmetry; elimination would leave a residual
   // row of rounding size, not an exact zero), or a pivot that is zero or not
@@ -1984,9 +2001,11 @@ __device__ __forceinline__ void interval_team(const SysDev& S, const Layout& Lo,
         double b, el;
         load_record(Lo, P.rec_src + (size_t)P.parent[s] * Lo.rec, wm, lane, b, el);
         if (recompute) {
-          bool ok = warp_inverse(S, sC, wm.x, 0, wm.A, wm.scr, lane);
-          ok = ok && warp_inverse(S, sC, wm.x, 1, wm.A + Lo.nu * Lo.nu, wm.scr, lane);
+          double rs = 0.0;
+          bool ok = warp_inverse(S, sC, wm.x, 0, wm.A, wm.scr, lane, &rs);
+          ok = ok && warp_inverse(S, sC, wm.x, 1, wm.A + Lo.nu * Lo.nu, wm.scr, lane, &rs);
           if (!ok && lane == 0) atomicOr(P.err, kErrSingular);
+          if (lane == 0 && isfinite(rs)) atomicMax(P.resid, (unsigned long long)__double_as_longlong(rs));
         }
         if (lane == 0) {
           st.s = s;
@@ -2221,9 +2240,11 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
       load_record(Lo, P.rec_src + (size_t)src * Lo.rec, wm, lane, b, el);
       df bdf = df_from_double(b);
       if (recompute) {
-        bool ok = warp_inverse(S, sC, wm.x, 0, wm.A, wm.scr, lane);
-        ok = ok && warp_inverse(S, sC, wm.x, 1, wm.A + Lo.nu * Lo.nu, wm.scr, lane);
+        double rs = 0.0;
+        bool ok = warp_inverse(S, sC, wm.x, 0, wm.A, wm.scr, lane, &rs);
+        ok = ok && warp_inverse(S, sC, wm.x, 1, wm.A + Lo.nu * Lo.nu, wm.scr, lane, &rs);
         if (!ok && lane == 0) atomicOr(P.err, kErrSingular);
+        if (lane == 0 && isfinite(rs)) atomicMax(P.resid, (unsigned long long)__double_as_longlong(rs));
       }
       double tau_left = P.tau, logw = 0.0;
       int jumps = 0;
@@ -2410,6 +2431,11 @@ __global__ void __launch_bounds__(1024) k_reconfig(const PopDev P, const double*
     P.trace[k] = s_w[0] / total;
     P.trace[P.trace_cap + k] = total / (double)W;
     P.trace[2 * P.trace_cap + k] = s_w[1] / (double)W;
+    // the Sherman-Morrison residual measured at this interval's recompute
+    // (-1: no recompute at this interval), then cleared for the next one
+    const bool recomputed = k > 0 && P.recompute_every > 0 && k % (uint64_t)P.recompute_every == 0;
+    P.trace[3 * P.trace_cap + k] = recomputed ? __longlong_as_double((long long)*P.resid) : -1.0;
+    *P.resid = 0ull;
     *P.moves += (unsigned long long)(s_w[1] + 0.5);
     *P.counter = 0;
   }

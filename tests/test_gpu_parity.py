@@ -501,3 +501,25 @@ def test_neon_workload_lattices(pkg, oracle_mod, a, kind):
     compared, parted = _compare_runs(pkg, oracle_mod, S.neon(), kind, a, 4096, 2, tau, 29, -128.9,
                                      label=f"projection Ne workload {kind} a={a} (4096) df64")
     assert compared == 2 or parted
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64", "fp32"])
+def test_sherman_morrison_residual_trace(pkg, prec):
+    """The Sherman-Morrison diagnostic: at every rebuild of the inverse
+    Slater matrices (intervals 3 and 6 with recompute_every = 3) the largest
+    max|A Ainv - I| of the updated inverses over 512 Ne walkers is recorded;
+    it is rounding-sized (the parity modes update in IEEE double) and -1 at
+    the other intervals."""
+    system = S.neon()
+    g = pkg.LrdmcSystem(system).set_precision(_prec(pkg, prec) if prec != "fp32" else pkg.PRECISION_FP32)
+    g.init_walkers(torch.tensor(S.initial_positions(system, 512, 81), device="cuda"), seed=82, tau=0.025,
+                   e_trial=-128.9, recompute_every=3, trace_capacity=8)
+    g.step(8, 0.2, pkg.Spacing(pkg.THIS_WORK))
+    r = g.residual_trace()
+    assert len(r) == 8
+    rebuilt = [k for k in range(8) if k > 0 and k % 3 == 0]
+    for k in range(8):
+        if k in rebuilt:
+            assert 0.0 < r[k] < 1e-8, (k, r[k])
+        else:
+            assert r[k] == -1.0, (k, r[k])
