@@ -318,25 +318,42 @@ def run_ours(args):
         nj = neural_leg(args, pkg, torch, system, main_prec, dev, rank, seed, x0)
     bt = batched_leg(args, pkg, torch, main_prec, seed) if args.batch_leg else None
     tc = tc_leg(args, pkg, torch, seed) if args.tc_leg else None
-    # e2e: the public API from host memory: H2D of the start configurations,
-    # init, the same steps, each followed by a D2H read of the trace.
-    spacing = pkg.Spacing(pkg.THIS_WORK)
-    cap = args.warmup + args.steps + 8
-    x0h = torch.tensor(x0).pin_memory()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    g2 = pkg.LrdmcSystem(system).set_precision(main_prec)
-    g2.init_walkers(x0h.numpy(), seed=seed, tau=WORKLOAD["tau"], e_trial=WORKLOAD["e_trial"],
-                    recompute_every=WORKLOAD["recompute_every"], trace_capacity=cap)
-    d2h = 0
-    n_e2e = args.warmup + args.steps
-    for k in range(n_e2e):
-        g2.step(1, WORKLOAD["a"], spacing)
-        g2.energy_trace(max_n=k + 1)
-        d2h += 3 * 8 * (k + 1)
-    e2e_moves = g2.moves()
-    torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
+    # e2e: the public API from host memory: H2D of the start configurations
+    # (pinned), system creation and init, the same steps, each followed by a
+    # D2H read of its trace entry (energy, mean weight, mean jumps) into
+    # pinned host memory, enqueued behind the step, and one synchronisation
+    # at the end (a pipelined caller). The blocking variant reads the whole
+    # trace synchronously after every step instead.
+    def e2e_run(blocking):
+        spacing = pkg.Spacing(pkg.THIS_WORK)
+        cap = args.warmup + args.steps + 8
+        x0h = torch.tensor(x0).pin_memory()
+        tr = torch.zeros((3, cap), dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g2 = pkg.LrdmcSystem(system).set_precision(main_prec)
+        g2.init_walkers(x0h.numpy(), seed=seed, tau=WORKLOAD["tau"], e_trial=WORKLOAD["e_trial"],
+                        recompute_every=WORKLOAD["recompute_every"], trace_capacity=cap)
+        d2h = 0
+        n = args.warmup + args.steps
+        for k in range(n):
+            g2.step(1, WORKLOAD["a"], spacing)
+            if blocking:
+                g2.energy_trace(max_n=k + 1)
+                d2h += 3 * 8 * (k + 1)
+            else:
+                g2.energy_trace_async(k, 1, tr)
+                d2h += 3 * 8
+        g2.sync()
+        moves_ = g2.moves()
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        if not blocking and not np.all(np.isfinite(tr[:, :n].numpy())):
+            raise RuntimeError("e2e: non-finite trace entries")
+        return t, moves_, d2h, n, x0h.numel() * 8
+
+    t_e2e, e2e_moves, d2h, n_e2e, h2d = e2e_run(False)
+    t_e2e_b, e2e_moves_b, d2h_b, _, _ = e2e_run(True)
     if dist is not None:
         value, total_ms, moves_all = stats.reduce_throughput(leg["total_ms"], leg["moves"])
         e2e_all, t_e2e_all, _ = stats.reduce_throughput(t_e2e * 1e3, e2e_moves)
@@ -377,9 +394,15 @@ def run_ours(args):
                    "l2": "flushed between timed steps (512 MiB write)",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_moves_all / t_e2e_all, "unit": "walker-moves/s",
-                "h2d_bytes_per_step": x0.nbytes / n_e2e, "d2h_bytes_per_step": d2h / n_e2e,
-                "includes": "H2D of start configurations, init, warmup+timed steps, per-step trace D2H"},
-        "gpu_launches": int(leg["n_int"] + leg["n_rec"]),
+                "h2d_bytes_per_step": h2d / n_e2e, "d2h_bytes_per_step": d2h / n_e2e,
+                "includes": "H2D of start configurations (pinned), system creation, init, warmup+timed steps, "
+                            "per-step D2H of the step's trace entry into pinned memory (enqueued behind the step), "
+                            "one synchronisation at the end",
+                "blocking_per_step_read": {"value": e2e_moves_b / t_e2e_b, "d2h_bytes_per_step": d2h_b / n_e2e,
+                                           "includes": "the same, reading the whole trace synchronously after "
+                                                       "every step (rank 0)"}},
+        # per step: the interval kernel and the reconfiguration's two kernels
+        "gpu_launches": int(leg["n_int"] + 2 * leg["n_rec"]),
         "roofline": roof,
         "efficiency": eff,
         "kernel_share": {"k_interval_ms": leg["t_int_ms"], "k_reconfig_ms": leg["t_rec_ms"]},

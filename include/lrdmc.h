@@ -181,6 +181,20 @@ LRDMC_API lrdmc_status lrdmc_sync(lrdmc_system_t sys);
 LRDMC_API lrdmc_status lrdmc_get_energy_trace(lrdmc_system_t sys, double* e, double* wbar,
                                     double* mean_jumps, int max_n, int* n_written);
 
+/* Enqueues, on the system's stream and without waiting, the copy of trace
+ * entries [first, first + n) into host arrays e, wbar and mean_jumps (each
+ * nullable, length >= n; the same quantities as lrdmc_get_energy_trace).
+ * The copies run behind every step enqueued before the call, so entries
+ * first .. first + n - 1 must belong to intervals already enqueued
+ * (first + n <= the number of intervals stepped), else LRDMC_ERR_ARG. The
+ * host arrays must stay valid until the next synchronising call (lrdmc_sync
+ * or a read-back function), after which they hold the values; with pinned
+ * host memory the copies are asynchronous, with pageable memory the CUDA
+ * runtime may complete them before returning. Kernel errors are reported by
+ * that synchronising call, as for lrdmc_step. */
+LRDMC_API lrdmc_status lrdmc_get_energy_trace_async(lrdmc_system_t sys, int first, int n, double* e,
+                                                    double* wbar, double* mean_jumps);
+
 /* The Sherman-Morrison residual of every interval so far (not a step of
  * the paper's method: a diagnostic of the cited LRDMC implementation's
  * rank-one inverse updates). At the start of an interval whose inverse
@@ -243,8 +257,8 @@ LRDMC_API lrdmc_status lrdmc_evaluate_tc(lrdmc_system_t sys, int n_configs, cons
  * ints (about 1 MiB) that every GPU loading the library holds until the
  * process exits. n_configs above LRDMC_STATIC_EVAL_MAX is rejected with
  * LRDMC_ERR_ARG. The first call on a device looks up the array's device
- * address (once per device, with that device current); make that first
- * call before any stream capture. The call clears the words it uses, then
+ * address (once per device, with that device current). The call clears
+ * the words it uses, then
  * synchronises the stream to read the summary word; when it reports
  * LRDMC_ERR_SINGULAR, lrdmc_last_error names the first configuration whose
  * status word is set. All calls share the

@@ -30,7 +30,8 @@ PRECISION_FP64, PRECISION_DF64, PRECISION_FP32 = 0, 1, 2
 
 EXPORTED = [
     "lrdmc_create_system", "lrdmc_spacing_params", "lrdmc_workspace_bytes", "lrdmc_init_walkers",
-    "lrdmc_step", "lrdmc_sync", "lrdmc_get_energy_trace", "lrdmc_get_residual_trace", "lrdmc_get_walkers",
+    "lrdmc_step", "lrdmc_sync", "lrdmc_get_energy_trace", "lrdmc_get_energy_trace_async", "lrdmc_get_residual_trace",
+    "lrdmc_get_walkers",
     "lrdmc_moves", "lrdmc_evaluate",
     "lrdmc_evaluate_static", "lrdmc_evaluate_tc",
     "lrdmc_save", "lrdmc_load", "lrdmc_set_precision", "lrdmc_set_profiling", "lrdmc_kernel_times", "lrdmc_last_error",
@@ -122,6 +123,8 @@ def load_library():
     L.lrdmc_sync.argtypes = [vp]
     L.lrdmc_get_energy_trace.restype = i
     L.lrdmc_get_energy_trace.argtypes = [vp, vp, vp, vp, i, ct.POINTER(i)]
+    L.lrdmc_get_energy_trace_async.restype = i
+    L.lrdmc_get_energy_trace_async.argtypes = [vp, i, i, vp, vp, vp]
     L.lrdmc_get_residual_trace.restype = i
     L.lrdmc_get_residual_trace.argtypes = [vp, vp, i, ct.POINTER(i)]
     L.lrdmc_get_walkers.restype = i
@@ -298,6 +301,27 @@ class LrdmcSystem:
                                                           ct.byref(n)))
         k = n.value
         return e[:k].copy(), w[:k].copy(), j[:k].copy()
+
+    def energy_trace_async(self, first, n, out):
+        """Enqueues the copy of trace entries [first, first + n) into
+        out[0..2, first:first + n] (energy, mean weight, mean jumps) without
+        waiting; ``out`` is a contiguous (3, m) float64 CPU tensor or array,
+        pinned for the copies to be asynchronous, valid until ``sync()``."""
+        import torch
+
+        if isinstance(out, torch.Tensor):
+            if out.device.type != "cpu" or out.dtype != torch.float64 or not out.is_contiguous():
+                raise ValueError("energy_trace_async: out must be a contiguous float64 CPU tensor")
+            base = out.data_ptr()
+        else:
+            if not (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags.c_contiguous):
+                raise ValueError("energy_trace_async: out must be a contiguous float64 array")
+            base = out.ctypes.data
+        if out.ndim != 2 or out.shape[0] != 3 or first < 0 or n < 0 or first + n > out.shape[1]:
+            raise ValueError("energy_trace_async: out must have shape (3, m) with first + n <= m")
+        m = int(out.shape[1])
+        ptrs = [ct.c_void_p(base + 8 * (r * m + first)) for r in range(3)]
+        self._check(load_library().lrdmc_get_energy_trace_async(self.h, int(first), int(n), *ptrs))
 
     def residual_trace(self, max_n=1 << 20):
         """Largest Sherman-Morrison residual max|A Ainv - I| per interval,

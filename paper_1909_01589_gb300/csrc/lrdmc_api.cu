@@ -412,7 +412,8 @@ lrdmc_status lrdmc_spacing_params(lrdmc_system_t s, double a, const lrdmc_spacin
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct WsPlan {
-  size_t rec, parent, order, logw, wgt, el, jumps, cum, trace, moves, err, counter, kdev, resid, total;
+  size_t rec, parent, order, logw, wgt, el, jumps, cum, part, bq, trace, moves, err, counter, kdev, resid, hist,
+      ticket, total;
 };
 
 static WsPlan plan_ws(const Layout& Lo, int W, int cap)
@@ -427,12 +428,17 @@ static WsPlan plan_ws(const Layout& Lo, int W, int cap)
   p.el = o; o += align256(sizeof(double) * (size_t)W);
   p.jumps = o; o += align256(sizeof(int) * (size_t)W);
   p.cum = o; o += align256(sizeof(double) * (size_t)W);
+  p.part = o; o += align256(sizeof(CombPart) * kMaxCombBlocks);
+  p.bq = o; o += align256((size_t)W);
   p.trace = o; o += align256(sizeof(double) * 4 * (size_t)cap);
+  // seven words cleared together at initialisation
   p.moves = o; o += 256;
   p.err = o; o += 256;
   p.counter = o; o += 256;
   p.kdev = o; o += 256;
   p.resid = o; o += 256;
+  p.hist = o; o += 256;
+  p.ticket = o; o += 256;
   p.total = o;
   return p;
 }
@@ -496,6 +502,10 @@ lrdmc_status lrdmc_init_walkers(lrdmc_system_t s, int W, const double* x0, uint6
   P.el_end = (double*)(s->ws + p.el);
   P.jumps = (int*)(s->ws + p.jumps);
   P.cum = (double*)(s->ws + p.cum);
+  P.part = (CombPart*)(s->ws + p.part);
+  P.bq = (unsigned char*)(s->ws + p.bq);
+  P.hist = (int*)(s->ws + p.hist);
+  P.ticket = (int*)(s->ws + p.ticket);
   P.trace = (double*)(s->ws + p.trace);
   P.moves = (unsigned long long*)(s->ws + p.moves);
   P.err = (int*)(s->ws + p.err);
@@ -509,7 +519,8 @@ lrdmc_status lrdmc_init_walkers(lrdmc_system_t s, int W, const double* x0, uint6
   P.tau = tau;
   P.e_trial = e_trial;
   P.helpers = s->helpers;
-  cudaError_t e = cudaMemsetAsync(s->ws + p.moves, 0, 5 * 256, s->stream);  // moves, err, counter, kdev, resid
+  // moves, err, counter, kdev, resid, hist, ticket
+  cudaError_t e = cudaMemsetAsync(s->ws + p.moves, 0, 7 * 256, s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "workspace clear");
   e = cudaMemsetAsync(P.logw, 0, sizeof(double) * W, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(P.wgt, 0, sizeof(double) * W, s->stream);
@@ -576,7 +587,7 @@ lrdmc_status lrdmc_step(lrdmc_system_t s, int n_steps, double a, const lrdmc_spa
       cudaEventRecord(ev[2], s->stream);
     }
     e = launch_reconfig(P, s->Lo, s->stream);
-    if (e != cudaSuccess) return cuda_fail(s, e, "k_reconfig launch");
+    if (e != cudaSuccess) return cuda_fail(s, e, "reconfiguration launch");
     if (ev) cudaEventRecord(ev[3], s->stream);
     s->cur = 1 - s->cur;
     s->k++;
@@ -634,6 +645,23 @@ lrdmc_status lrdmc_get_energy_trace(lrdmc_system_t s, double* e_out, double* w_o
   cudaError_t e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "stream synchronize");
   if (n_written) *n_written = n;
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_get_energy_trace_async(lrdmc_system_t s, int first, int n, double* e_out, double* w_out,
+                                          double* j_out)
+{
+  if (!s) return fail(s, LRDMC_ERR_ARG, "");
+  if (!s->have_pop) return fail(s, LRDMC_ERR_STATE, "trace before init_walkers");
+  if (first < 0 || n < 0 || (uint64_t)first + (uint64_t)n > s->k)
+    return fail(s, LRDMC_ERR_ARG, "energy_trace_async: entries beyond the intervals stepped");
+  double* outs[3] = {e_out, w_out, j_out};
+  for (int r = 0; r < 3; ++r) {
+    if (!outs[r] || n == 0) continue;
+    cudaError_t e = cudaMemcpyAsync(outs[r], s->P.trace + (size_t)r * s->trace_cap + first, sizeof(double) * n,
+                                    cudaMemcpyDeviceToHost, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "trace copy");
+  }
   return LRDMC_OK;
 }
 

@@ -128,8 +128,21 @@ Layout make_layout(const SysDev& S, bool caches);
 constexpr int kMaxSmemBlock = 232448 - 2048;
 
 // Populations up to this many walkers keep the comb's running sums in the
-// reconfiguration kernel's shared memory (8 bytes each).
+// shared memory of every block of the reconfiguration (8 bytes each).
 constexpr int kReconfigSmemW = 16384;
+// Reconfiguration grid: blocks of kCombThreads threads, each owning at
+// least 64 consecutive slots, at most kMaxCombBlocks blocks.
+constexpr int kCombThreads = 256;
+constexpr int kMaxCombBlocks = 128;
+int comb_blocks(int W);
+
+// Totals of one block of the reconfiguration.
+struct CombPart {
+  double w;          // sum of the block's weights (its last running sum)
+  double swe;        // sum of w E_L
+  long long jumps;   // sum of jumps
+  float bmin, bmax;  // range of the walkers' total rates b
+};
 
 struct PopDev {
   double* rec_src;
@@ -140,7 +153,11 @@ struct PopDev {
   double* wgt;  // exp(logw) of the last interval, written with logw
   double* el_end;
   int* jumps;
-  double* cum;  // running weight sums of the comb (populations above kReconfigSmemW)
+  double* cum;  // running weight sums of the comb, relative to the start of each reconfiguration block
+  CombPart* part;       // [kMaxCombBlocks] totals of the reconfiguration blocks
+  int* hist;            // [64] slots per order bucket (zero between reconfigurations)
+  int* ticket;          // reconfiguration blocks finished (zero between reconfigurations)
+  unsigned char* bq;    // [W] order bucket of each slot
   double* trace;  // [4][cap]: e_k, mean weight, mean jumps, Sherman-Morrison residual at the recompute
   // largest Sherman-Morrison residual of the current interval's recompute,
   // as the bits of a non-negative double (atomicMax orders them as doubles)

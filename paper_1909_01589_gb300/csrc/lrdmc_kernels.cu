@@ -15,7 +15,8 @@
 //   k_eval_all  evaluate every walker (after a change of lattice)
 //   k_interval  one interval tau of continuous-time projection per walker,
 //               walkers fetched dynamically by the warps (ragged jump counts)
-//   k_reconfig  weights, trace entry and comb parents (one block)
+//   k_comb_sums, k_comb_parents  reconfiguration: running weight sums, comb
+//               parents, trace entry, order of the next interval
 //   k_evaluate  stateless evaluation of given configurations (and the
 //               variant with static scratch, k_evaluate_static)
 //   k_base_terms  gradients and local energies without the neural term
@@ -26,6 +27,7 @@
 
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "lrdmc_internal.h"
@@ -2201,7 +2203,7 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
   constexpr bool NC = (PREC & 4) != 0;  // the layout has no evaluation caches
   extern __shared__ double smem[];
   double* sC = smem;
-  // interval k from the device counter (advanced by k_reconfig); the inverse
+  // interval k from the device counter (advanced by k_comb_parents); the inverse
   // Slater matrices are recomputed at the start of every recompute_every-th
   // interval
   const uint64_t k = *P.kdev;
@@ -2342,164 +2344,294 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
   if (threadIdx.x == 0) asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
-// Reconfiguration at the end of interval k (one block of 1024 threads):
-// trace (weighted mean E_L, mean weight, mean jumps) and comb parents: slot
-// t takes the smallest s with (t + xi) C_W / W < C_s. The weights
-// w_s = exp(log w_s) come from the interval kernel (P.wgt), so their FP64
-// exponentials run on every SM, not on this block's one. Up to
-// kReconfigSmemW walkers, the running sums C_s live in dynamic shared memory
-// (the comb's binary searches then read shared memory, not L2), and the same
-// region then holds each slot's next-interval rate for the processing order,
-// read once from the records. Larger populations use P.cum and re-read the
-// records. Either way the sums, and so the parents, are the same numbers.
-__global__ void __launch_bounds__(1024) k_reconfig(const PopDev P, const double* rec_next, int rec_stride,
-                                                  int off_b)
+// Reconfiguration at the end of interval k, spread over G blocks of
+// kCombThreads threads; block g owns the R = ceil(W/G) slots from g R. Its
+// FP64 work (running sums, comb targets and comparisons) used to run on one
+// SM, whose FP64 pipe took 38 us for 4096 walkers; spread over G SMs it
+// takes a few. Two kernels:
+//   k_comb_sums     per block: running weight sums of its slots from the
+//                   block's start (P.cum) and the block's totals (weights,
+//                   w E_L, jumps, range of the walkers' b)
+//   k_comb_parents  per block: the block offsets off[g] (the same sequential
+//                   sum in every block), the comb parents of its slots and
+//                   each slot's bucket for the next interval's order; the
+//                   last block to finish writes that order and the trace
+//                   entry and clears the counters.
+// Running sums: within a block, lane i of warp 0 sums its consecutive slots
+// from zero (l_i(s)), and O_0 = 0, O_{i+1} = O_i + l_i(last slot of i)
+// sequentially; c(s) = O_i + l_i(s). Over the blocks off[0] = 0,
+// off[g+1] = off[g] + c(last slot of g), and C_s = off[g] + c(s). Each
+// boundary repeats the rounding of the sum that ends the previous part, so C
+// is non-decreasing (rounding is monotone, weights are >= 0) and slot t's
+// parent is well defined: the smallest s with (t + xi) C_{W-1} / W < C_s,
+// else W - 1.
+
+__device__ __forceinline__ int comb_slots(int W, int G) { return (W + G - 1) / G; }
+
+__global__ void __launch_bounds__(kCombThreads) k_comb_sums(const PopDev P, const double* rec_next, int rec_stride,
+                                                           int off_b)
 {
-  const uint64_t k = *P.kdev;
-  extern __shared__ double s_dyn[];
-  __shared__ double s_run[1024];
-  __shared__ double s_e[32], s_j[32], s_w[32];
-  __shared__ double s_total;
-  const int W = P.W, t = threadIdx.x, nt = blockDim.x;
-  const bool in_smem = W <= kReconfigSmemW;
-  double* cum = in_smem ? s_dyn : P.cum;
-  const int chunk = (W + nt - 1) / nt;
-  const int lo = min(W, t * chunk), hi = min(W, lo + chunk);
-  double run = 0.0, swe = 0.0, sj = 0.0;
-  for (int s = lo; s < hi; ++s) {
-    double w = P.wgt[s];
-    run += w;
-    cum[s] = run;
-    swe += w * P.el_end[s];
-    sj += (double)P.jumps[s];
+  // the parents kernel is launched behind this one with programmatic stream
+  // serialization; its blocks may take their SMs now and wait for this grid
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  constexpr int NW = kCombThreads / 32;
+  __shared__ double s_e[NW], s_tot[32];
+  __shared__ long long s_j[NW];
+  __shared__ float s_lo[NW], s_hi[NW];
+  const int W = P.W, G = gridDim.x, g = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int R = comb_slots(W, G);
+  const int b0 = min(W, g * R), b1 = min(W, b0 + R);
+  // the block's totals other than the weights: every thread
+  double swe = 0.0;
+  long long sj = 0;
+  float bmin = INFINITY, bmax = -INFINITY;
+  for (int s = b0 + t; s < b1; s += kCombThreads) {
+    swe += P.wgt[s] * P.el_end[s];
+    sj += P.jumps[s];
+    const float bs = (float)rec_next[(size_t)s * rec_stride + off_b];
+    bmin = fminf(bmin, bs);
+    bmax = fmaxf(bmax, bs);
   }
-  // block exclusive scan of the chunk totals
-  s_run[t] = run;
-  __syncthreads();
-  for (int o = 1; o < nt; o <<= 1) {
-    double y = (t >= o) ? s_run[t - o] : 0.0;
-    __syncthreads();
-    s_run[t] += y;
-    __syncthreads();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    swe += __shfl_xor_sync(FULL_MASK, swe, o);
+    sj += __shfl_xor_sync(FULL_MASK, sj, o);
+    bmin = fminf(bmin, __shfl_xor_sync(FULL_MASK, bmin, o));
+    bmax = fmaxf(bmax, __shfl_xor_sync(FULL_MASK, bmax, o));
   }
-  double offset = (t > 0) ? s_run[t - 1] : 0.0;
-  for (int s = lo; s < hi; ++s) cum[s] += offset;
-  if (t == nt - 1) s_total = s_run[nt - 1];
-  // reductions of swe and sj
-  double e = warp_sum(swe), j = warp_sum(sj);
-  if ((t & 31) == 0) { s_e[t >> 5] = e; s_j[t >> 5] = j; }
-  __syncthreads();
-  if (t < 32) {
-    double e2 = (t < (nt >> 5)) ? s_e[t] : 0.0, j2 = (t < (nt >> 5)) ? s_j[t] : 0.0;
-    e2 = warp_sum(e2);
-    j2 = warp_sum(j2);
-    if (t == 0) { s_w[0] = e2; s_w[1] = j2; }
+  if (lane == 0) { s_e[wid] = swe; s_j[wid] = sj; s_lo[wid] = bmin; s_hi[wid] = bmax; }
+  // the running sums: warp 0, each lane a run of consecutive slots
+  const int per = (b1 - b0 + 31) / 32;
+  const int lo = min(b1, b0 + lane * per), hi = min(b1, lo + per);
+  double l = 0.0;
+  if (wid == 0) {
+    for (int s = lo; s < hi; ++s) l += P.wgt[s];
+    s_tot[lane] = l;
   }
   __syncthreads();
-  const double total = s_total;
-  double u[4];
-  draw_uniforms(P.seed, kSlotGlobal, k, 0, kTagComb, u);
-  const double xi = u[0];
-  // t -> (t + xi) total / W; for W a power of two the product with 1/W is
-  // the same number as the quotient (an exact scaling), and the FP64 pipe of
-  // this one SM is spared W divisions
-  const bool w_pow2 = (W & (W - 1)) == 0;
-  const double inv_w = 1.0 / (double)W;
-  // The targets grow with t, so the parents do too: a thread searches for
-  // its first slot's parent, then steps forward from the previous one (up to
-  // 8 steps, else a search over the rest). Each parent is the smallest s
-  // with target < cum[s] (else W - 1), found with the same comparisons.
-  int a = 0;
-  for (int tt = lo; tt < hi; ++tt) {
-    const double num = ((double)tt + xi) * total;
-    const double target = w_pow2 ? num * inv_w : num / (double)W;
-    int steps = 0;
-    while (tt > lo && steps < 8 && a < W - 1 && !(target < cum[a])) {
-      ++a;
-      ++steps;
+  if (t == 0) {
+    double o = 0.0;
+    for (int i = 0; i < 32; ++i) {
+      const double ti = s_tot[i];
+      s_tot[i] = o;
+      o += ti;
     }
-    if (tt == lo || (steps == 8 && a < W - 1 && !(target < cum[a]))) {
-      int bnd = W - 1;
-      while (a < bnd) {
-        int mid = (a + bnd) >> 1;
-        if (target < cum[mid]) bnd = mid; else a = mid + 1;
+    P.part[g].w = o;  // = c(last slot of the block): the last lane with slots ends there
+    double es = 0.0;
+    long long js = 0;
+    float bl = INFINITY, bh = -INFINITY;
+    for (int q = 0; q < NW; ++q) {
+      es += s_e[q];
+      js += s_j[q];
+      bl = fminf(bl, s_lo[q]);
+      bh = fmaxf(bh, s_hi[q]);
+    }
+    P.part[g].swe = es;
+    P.part[g].jumps = js;
+    P.part[g].bmin = bl;
+    P.part[g].bmax = bh;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const double O = s_tot[lane];
+    double c = 0.0;
+    for (int s = lo; s < hi; ++s) {
+      c += P.wgt[s];
+      P.cum[s] = O + c;
+    }
+  }
+}
+
+// Running sum C_s of the comb: from shared memory when the population's sums
+// were staged there, else off[block of s] + P.cum[s] (the same number).
+__device__ __forceinline__ double comb_C(const double* s_cum, const double* s_off, const double* cum, int R, int s,
+                                        bool in_smem)
+{
+  return in_smem ? s_cum[s] : s_off[s / R] + __ldcg(cum + s);
+}
+
+// Adds one to the shared counter of bucket q for every lane of the warp
+// (lanes with q < 0 take no part) and returns this lane's old count plus
+// its rank among the lanes with the same q: one shared-memory atomic per
+// distinct bucket of the warp instead of one per lane.
+__device__ __forceinline__ int bucket_take(int* cnt, int q, int lane)
+{
+  const unsigned peers = __match_any_sync(FULL_MASK, q);
+  const int leader = __ffs(peers) - 1;
+  int base = 0;
+  if (lane == leader && q >= 0) base = atomicAdd(&cnt[q], __popc(peers));
+  base = __shfl_sync(FULL_MASK, base, leader);
+  return base + __popc(peers & ((1u << lane) - 1u));
+}
+
+__global__ void __launch_bounds__(kCombThreads) k_comb_parents(const PopDev P, const double* rec_next,
+                                                              int rec_stride, int off_b)
+{
+  extern __shared__ double s_cum[];  // the running sums C_s (W <= kReconfigSmemW)
+  __shared__ double s_off[kMaxCombBlocks + 1];
+  __shared__ CombPart s_part[kMaxCombBlocks];
+  __shared__ float s_range[2];
+  __shared__ int s_cnt[64];
+  __shared__ int s_last;
+  const int W = P.W, G = gridDim.x, g = blockIdx.x, t = threadIdx.x, lane = t & 31;
+  const int R = comb_slots(W, G);
+  const bool in_smem = W <= kReconfigSmemW;
+  // everything below reads the sums kernel's results
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const uint64_t k = *P.kdev;
+  if (t < 64) s_cnt[t] = 0;
+  for (int h = t; h < G; h += kCombThreads) {
+    s_part[h].w = __ldcg(&P.part[h].w);
+    s_part[h].swe = __ldcg(&P.part[h].swe);
+    s_part[h].jumps = __ldcg(&P.part[h].jumps);
+    s_part[h].bmin = __ldcg(&P.part[h].bmin);
+    s_part[h].bmax = __ldcg(&P.part[h].bmax);
+  }
+  __syncthreads();
+  if (t == 0) {
+    double o = 0.0;
+    float l = INFINITY, hb = -INFINITY;
+    for (int h = 0; h < G; ++h) {
+      s_off[h] = o;
+      o += s_part[h].w;
+      l = fminf(l, s_part[h].bmin);
+      hb = fmaxf(hb, s_part[h].bmax);
+    }
+    s_off[G] = o;
+    s_range[0] = l;
+    s_range[1] = hb;
+  }
+  __syncthreads();
+  if (in_smem) {
+    constexpr int U = 8;
+    for (int s0 = 0; s0 < W; s0 += U * kCombThreads) {
+      double v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int s = s0 + u * kCombThreads + t;
+        v[u] = s < W ? __ldcg(P.cum + s) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int s = s0 + u * kCombThreads + t;
+        if (s < W) s_cum[s] = s_off[s / R] + v[u];
       }
     }
-    P.parent[tt] = a;
+    __syncthreads();
+  }
+  const double total = s_off[G];
+  double uu[4];
+  draw_uniforms(P.seed, kSlotGlobal, k, 0, kTagComb, uu);
+  const double xi = uu[0];
+  // t -> (t + xi) total / W; for W a power of two the product with 1/W is
+  // the same number as the quotient (an exact scaling)
+  const bool w_pow2 = (W & (W - 1)) == 0;
+  const double inv_w = 1.0 / (double)W;
+  const float gmin = s_range[0], gmax = s_range[1];
+  const float scale = (gmax > gmin) ? 64.0f / (gmax - gmin) : 0.0f;
+  const int b0 = min(W, g * R), b1 = min(W, b0 + R);
+  const int chunk = (b1 - b0 + kCombThreads - 1) / kCombThreads;
+  const int lo = min(b1, b0 + t * chunk), hi = min(b1, lo + chunk);
+  // The targets grow with the slot, so the parents do too: a thread searches
+  // for its first slot's parent, then steps forward from the previous one
+  // (up to 8 steps, else a search over the rest), with the same comparisons.
+  // The loop runs chunk times in every thread (warp-uniform) so that the
+  // bucket counts can be taken per warp.
+  int a = 0;
+  for (int i = 0; i < chunk; ++i) {
+    const int tt = lo + i;
+    int q = -1;
+    if (tt < hi) {
+      const double num = ((double)tt + xi) * total;
+      const double target = w_pow2 ? num * inv_w : num / (double)W;
+      int steps = 0;
+      while (tt > lo && steps < 8 && a < W - 1 && !(target < comb_C(s_cum, s_off, P.cum, R, a, in_smem))) {
+        ++a;
+        ++steps;
+      }
+      if (tt == lo || (steps == 8 && a < W - 1 && !(target < comb_C(s_cum, s_off, P.cum, R, a, in_smem)))) {
+        int bnd = W - 1;
+        while (a < bnd) {
+          const int mid = (a + bnd) >> 1;
+          if (target < comb_C(s_cum, s_off, P.cum, R, mid, in_smem)) bnd = mid; else a = mid + 1;
+        }
+      }
+      P.parent[tt] = a;
+      // processing order of the next interval, longest expected first: a
+      // slot's number of jumps is about tau times the total rate b of the
+      // walker it receives, so the slots are bucketed by that b, descending
+      const float bt = (float)rec_next[(size_t)a * rec_stride + off_b];
+      q = (int)((bt - gmin) * scale);
+      q = 63 - min(63, max(0, q));
+      P.bq[tt] = (unsigned char)q;
+    }
+    bucket_take(s_cnt, q, lane);
+  }
+  __syncthreads();
+  if (t < 64 && s_cnt[t] > 0) atomicAdd(&P.hist[t], s_cnt[t]);
+  // the last block to finish writes the order and the trace entry
+  __threadfence();
+  __syncthreads();
+  if (t == 0) s_last = atomicAdd(P.ticket, 1) == G - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (t < 64) {
+    s_cnt[t] = __ldcg(&P.hist[t]);
+    P.hist[t] = 0;
+  }
+  __syncthreads();
+  if (t < 32) {  // exclusive scan of the 64 bucket counts (two per lane)
+    const int c0 = s_cnt[2 * t], c1 = s_cnt[2 * t + 1];
+    int incl = c0 + c1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(FULL_MASK, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int ex = incl - c0 - c1;
+    s_cnt[2 * t] = ex;
+    s_cnt[2 * t + 1] = ex + c0;
+  }
+  __syncthreads();
+  {
+    constexpr int U = 8;
+    for (int s0 = 0; s0 < W; s0 += U * kCombThreads) {
+      int qv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int s = s0 + u * kCombThreads + t;
+        qv[u] = s < W ? (int)__ldcg(P.bq + s) : -1;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int s = s0 + u * kCombThreads + t;
+        const int pos = bucket_take(s_cnt, qv[u], lane);
+        if (s < W) P.order[pos] = s;
+      }
+    }
   }
   if (t == 0) {
-    P.trace[k] = s_w[0] / total;
+    double swe = 0.0;
+    long long sj = 0;
+    for (int h = 0; h < G; ++h) {
+      swe += s_part[h].swe;
+      sj += s_part[h].jumps;
+    }
+    P.trace[k] = swe / total;
     P.trace[P.trace_cap + k] = total / (double)W;
-    P.trace[2 * P.trace_cap + k] = s_w[1] / (double)W;
+    P.trace[2 * P.trace_cap + k] = (double)sj / (double)W;
     // the Sherman-Morrison residual measured at this interval's recompute
     // (-1: no recompute at this interval), then cleared for the next one
     const bool recomputed = k > 0 && P.recompute_every > 0 && k % (uint64_t)P.recompute_every == 0;
     P.trace[3 * P.trace_cap + k] = recomputed ? __longlong_as_double((long long)*P.resid) : -1.0;
     *P.resid = 0ull;
-    *P.moves += (unsigned long long)(s_w[1] + 0.5);
+    *P.moves += (unsigned long long)sj;
     *P.counter = 0;
+    *P.ticket = 0;
+    // every block has read k before taking its ticket: advance it
+    *P.kdev = k + 1;
   }
-  // Processing order of the next interval, longest expected first: a slot's
-  // number of jumps is about tau times the total rate b of the walker it
-  // receives, so the slots are bucketed by that b in descending order (a
-  // counting sort over 64 buckets; the order inside a bucket is arbitrary and
-  // does not affect any result).
-  __shared__ int s_cnt[64];
-  __shared__ float s_lo[32], s_hi[32];
-  float* s_b = reinterpret_cast<float*>(s_dyn);
-  __syncthreads();  // every search has finished with the shared sums
-  float bmin = INFINITY, bmax = -INFINITY;
-  for (int tt = lo; tt < hi; ++tt) {
-    float bt = (float)rec_next[(size_t)P.parent[tt] * rec_stride + off_b];
-    if (in_smem) s_b[tt] = bt;
-    bmin = fminf(bmin, bt);
-    bmax = fmaxf(bmax, bt);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    bmin = fminf(bmin, __shfl_xor_sync(FULL_MASK, bmin, o));
-    bmax = fmaxf(bmax, __shfl_xor_sync(FULL_MASK, bmax, o));
-  }
-  if ((t & 31) == 0) { s_lo[t >> 5] = bmin; s_hi[t >> 5] = bmax; }
-  if (t < 64) s_cnt[t] = 0;
-  __syncthreads();
-  if (t < 32) {
-    float a = (t < (nt >> 5)) ? s_lo[t] : INFINITY, c = (t < (nt >> 5)) ? s_hi[t] : -INFINITY;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a = fminf(a, __shfl_xor_sync(FULL_MASK, a, o));
-      c = fmaxf(c, __shfl_xor_sync(FULL_MASK, c, o));
-    }
-    if (t == 0) { s_lo[0] = a; s_hi[0] = c; }
-  }
-  __syncthreads();
-  const float gmin = s_lo[0], gmax = s_hi[0];
-  const float scale = (gmax > gmin) ? 64.0f / (gmax - gmin) : 0.0f;
-  for (int tt = lo; tt < hi; ++tt) {
-    float bt = in_smem ? s_b[tt] : (float)rec_next[(size_t)P.parent[tt] * rec_stride + off_b];
-    int q = (int)((bt - gmin) * scale);
-    q = 63 - min(63, max(0, q));
-    atomicAdd(&s_cnt[q], 1);
-  }
-  __syncthreads();
-  if (t == 0) {
-    int run = 0;
-    for (int q = 0; q < 64; ++q) {
-      int c = s_cnt[q];
-      s_cnt[q] = run;
-      run += c;
-    }
-  }
-  __syncthreads();
-  for (int tt = lo; tt < hi; ++tt) {
-    float bt = in_smem ? s_b[tt] : (float)rec_next[(size_t)P.parent[tt] * rec_stride + off_b];
-    int q = (int)((bt - gmin) * scale);
-    q = 63 - min(63, max(0, q));
-    P.order[atomicAdd(&s_cnt[q], 1)] = tt;
-  }
-  // every thread has read k (it is used above, behind barriers): advance it
-  __syncthreads();
-  if (t == 0) *P.kdev = k + 1;
 }
 
 // Stateless evaluation of configuration c (one warp): inverses from x, then
@@ -2813,15 +2945,35 @@ cudaError_t launch_interval(const SysDev& S, const Layout& Lo, const LatDev& L, 
   return cudaErrorInvalidValue;
 }
 
+int comb_blocks(int W)
+{
+  // at least 64 slots per block, at most kMaxCombBlocks blocks
+  const int R = std::max(64, (W + kMaxCombBlocks - 1) / kMaxCombBlocks);
+  return std::max(1, (W + R - 1) / R);
+}
+
 cudaError_t launch_reconfig(const PopDev& P, const Layout& Lo, cudaStream_t st)
 {
+  const int G = comb_blocks(P.W);
   const int smem = P.W <= kReconfigSmemW ? (int)sizeof(double) * P.W : 0;
   // the attribute always takes the largest size, so systems of different
   // populations (and batches captured in one graph) never lower it
-  cudaError_t e = smem > 0 ? set_smem((const void*)k_reconfig, (int)sizeof(double) * kReconfigSmemW) : cudaSuccess;
+  cudaError_t e = set_smem((const void*)k_comb_parents, (int)sizeof(double) * kReconfigSmemW);
   if (e != cudaSuccess) return e;
-  k_reconfig<<<1, 1024, smem, st>>>(P, P.rec_dst, Lo.rec, Lo.off_b);
-  return cudaGetLastError();
+  k_comb_sums<<<G, kCombThreads, 0, st>>>(P, P.rec_dst, Lo.rec, Lo.off_b);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(G);
+  cfg.blockDim = dim3(kCombThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_comb_parents, P, (const double*)P.rec_dst, Lo.rec, Lo.off_b);
 }
 
 // Base terms of the neural objective: grad_i log|psi_G| and E_L of every

@@ -159,3 +159,19 @@ def test_set_tail_helpers_arguments(pkg):
     with pytest.raises(pkg.LrdmcError) as e:
         g._check(pkg.load_library().lrdmc_set_tail_helpers(g.h, 2))
     assert e.value.status == pkg.ERR_ARG
+
+
+def test_energy_trace_async_arguments(pkg):
+    """The asynchronous trace read: before init_walkers it is a state error;
+    the binding checks the host buffer's type and shape before the library."""
+    g = pkg.LrdmcSystem(S.helium())
+    out = np.zeros((3, 4))
+    with pytest.raises(pkg.LrdmcError) as e:
+        g.energy_trace_async(0, 1, out)
+    assert e.value.status == pkg.ERR_STATE
+    for bad in (np.zeros((3, 4), np.float32), np.zeros((2, 4)), np.zeros((4, 3)).T):
+        with pytest.raises(ValueError):
+            g.energy_trace_async(0, 1, bad)
+    with pytest.raises(ValueError):
+        g.energy_trace_async(3, 2, out)
+

@@ -49,17 +49,19 @@ def _run(pkg, name, W, a, tau, et, n, prec, helpers, blocks=0):
     return w, e, wb, j, g.moves()
 
 
-@pytest.mark.parametrize("prec", ["df64", "fp32"])
-@pytest.mark.parametrize("name,W,a,tau,et,n", CASES)
-def test_helpers_do_not_change_results(pkg, name, W, a, tau, et, n, prec):
-    p = pkg.PRECISION_DF64 if prec == "df64" else pkg.PRECISION_FP32
-    off = _run(pkg, name, W, a, tau, et, n, p, False)
-    on = _run(pkg, name, W, a, tau, et, n, p, True)
+def _same(off, on):
     for key in ("x", "EL", "b", "T", "logw_pre", "jumps_pre", "parent"):
         assert np.array_equal(off[0][key], on[0][key]), key
     for q in (1, 2, 3):
         assert np.array_equal(off[q], on[q])
     assert off[4] == on[4]
+
+
+@pytest.mark.parametrize("prec", ["df64", "fp32"])
+@pytest.mark.parametrize("name,W,a,tau,et,n", CASES)
+def test_helpers_do_not_change_results(pkg, name, W, a, tau, et, n, prec):
+    p = pkg.PRECISION_DF64 if prec == "df64" else pkg.PRECISION_FP32
+    _same(_run(pkg, name, W, a, tau, et, n, p, False), _run(pkg, name, W, a, tau, et, n, p, True))
 
 
 def test_helpers_with_a_few_blocks(pkg):

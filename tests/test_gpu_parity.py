@@ -247,6 +247,18 @@ def test_projection_full_size(pkg, oracle_mod, prec):
     assert compared >= 1
 
 
+@pytest.mark.parametrize("W", [1, 63, 65, 4097, 8193, 20000])
+def test_reconfiguration_blocks(pkg, oracle_mod, W):
+    """The reconfiguration over its grid of blocks: one walker, a block
+    boundary just before and after 64 walkers, ragged last blocks (4097,
+    8193), and a population above the 16384 whose running sums fit in shared
+    memory (20000: sums read from global memory). He, three intervals, every
+    parent, weight and trace entry against the oracle's sequential comb."""
+    compared, parted = _compare_runs(pkg, oracle_mod, S.helium(), "this_work", 0.2, W, 3, 0.05, 41, -2.9,
+                                     label=f"projection He reconfiguration blocks W={W} df64")
+    assert compared >= (1 if parted else 3)
+
+
 @pytest.mark.parametrize("name,E", [("H", -0.5), ("Be_bare", -20.0)])
 def test_zero_variance_on_gpu(pkg, name, E):
     system = S.make_system(name)
@@ -257,6 +269,28 @@ def test_zero_variance_on_gpu(pkg, name, E):
     e, w, j = g.energy_trace()
     assert np.max(np.abs(e - E)) < 1e-10 * abs(E)
     assert np.max(np.abs(w - 1.0)) < 1e-10 and np.mean(j) > 0.5
+
+
+def test_energy_trace_async_matches_sync_read(pkg):
+    """Per-step asynchronous trace reads into pinned memory hold, after
+    sync(), the same bits as the synchronous read of the whole trace; an
+    entry beyond the intervals stepped is LRDMC_ERR_ARG."""
+    system = S.neon()
+    g = pkg.LrdmcSystem(system)
+    g.init_walkers(torch.tensor(S.initial_positions(system, 512, 6), device="cuda"), seed=6, tau=0.02,
+                   e_trial=-128.9, recompute_every=3, trace_capacity=8)
+    out = torch.zeros((3, 8), dtype=torch.float64).pin_memory()
+    sp = pkg.Spacing(pkg.THIS_WORK)
+    for k in range(6):
+        g.step(1, 0.2, sp)
+        g.energy_trace_async(k, 1, out)
+    with pytest.raises(pkg.LrdmcError) as e:
+        g.energy_trace_async(5, 2, out)
+    assert e.value.status == pkg.ERR_ARG
+    g.sync()
+    e_, w_, j_ = g.energy_trace()
+    assert np.array_equal(out[0, :6].numpy(), e_) and np.array_equal(out[1, :6].numpy(), w_)
+    assert np.array_equal(out[2, :6].numpy(), j_)
 
 
 def test_checkpoint_resume_bitwise(pkg, tmp_path):
