@@ -138,13 +138,14 @@ LRDMC_API lrdmc_status lrdmc_create_system(int n_nuc, const double* nuc_xyz, con
 LRDMC_API lrdmc_status lrdmc_spacing_params(lrdmc_system_t sys, double a, const lrdmc_spacing_fn* spacing,
                                   double* aprime_over_a, double* rc);
 
-/* Device workspace bytes needed by lrdmc_init_walkers for n_walkers and a
- * trace of trace_capacity intervals. */
+/* Device workspace bytes needed by lrdmc_init_walkers for n_walkers (1 to
+ * LRDMC_MAX_WALKERS) and a trace of trace_capacity intervals. */
+#define LRDMC_MAX_WALKERS 4194304
 LRDMC_API lrdmc_status lrdmc_workspace_bytes(lrdmc_system_t sys, int n_walkers, int trace_capacity,
                                    size_t* bytes);
 
-/* Starts a population of n_walkers at configurations x0 [n_walkers][N][3]
- * (host or device memory; copied). workspace is caller-owned device memory
+/* Starts a population of n_walkers (1 to LRDMC_MAX_WALKERS) at
+ * configurations x0 [n_walkers][N][3] (host or device memory; copied). workspace is caller-owned device memory
  * of at least lrdmc_workspace_bytes(), 256-byte aligned, held by the system
  * until lrdmc_destroy or the next init. tau is the reconfiguration
  * interval, e_trial the energy shift of the log-weights, recompute_every the

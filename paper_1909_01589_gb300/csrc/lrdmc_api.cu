@@ -412,8 +412,8 @@ lrdmc_status lrdmc_spacing_params(lrdmc_system_t s, double a, const lrdmc_spacin
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct WsPlan {
-  size_t rec, parent, order, logw, wgt, el, jumps, cum, part, bq, trace, moves, err, counter, kdev, resid, hist,
-      ticket, total;
+  size_t rec, parent, order, logw, wgt, el, jumps, cum, part, trace, moves, err, counter, kdev, resid, ticket,
+      total;
 };
 
 static WsPlan plan_ws(const Layout& Lo, int W, int cap)
@@ -429,15 +429,13 @@ static WsPlan plan_ws(const Layout& Lo, int W, int cap)
   p.jumps = o; o += align256(sizeof(int) * (size_t)W);
   p.cum = o; o += align256(sizeof(double) * (size_t)W);
   p.part = o; o += align256(sizeof(CombPart) * kMaxCombBlocks);
-  p.bq = o; o += align256((size_t)W);
   p.trace = o; o += align256(sizeof(double) * 4 * (size_t)cap);
-  // seven words cleared together at initialisation
+  // six words cleared together at initialisation
   p.moves = o; o += 256;
   p.err = o; o += 256;
   p.counter = o; o += 256;
   p.kdev = o; o += 256;
   p.resid = o; o += 256;
-  p.hist = o; o += 256;
   p.ticket = o; o += 256;
   p.total = o;
   return p;
@@ -446,7 +444,8 @@ static WsPlan plan_ws(const Layout& Lo, int W, int cap)
 lrdmc_status lrdmc_workspace_bytes(lrdmc_system_t s, int n_walkers, int cap, size_t* bytes)
 {
   if (!s) return fail(s, LRDMC_ERR_ARG, "");
-  if (n_walkers < 1 || cap < 1 || !bytes) return fail(s, LRDMC_ERR_ARG, "workspace_bytes: bad sizes");
+  if (n_walkers < 1 || n_walkers > kMaxWalkers || cap < 1 || !bytes)
+    return fail(s, LRDMC_ERR_ARG, "workspace_bytes: bad sizes");
   *bytes = plan_ws(s->Lo, n_walkers, cap).total;
   return LRDMC_OK;
 }
@@ -472,6 +471,7 @@ lrdmc_status lrdmc_init_walkers(lrdmc_system_t s, int W, const double* x0, uint6
   NvtxRange nvtx("lrdmc_init_walkers");
   if (!s) return fail(s, LRDMC_ERR_ARG, "");
   if (W < 1 || cap < 1 || !x0 || !workspace) return fail(s, LRDMC_ERR_ARG, "init_walkers: bad arguments");
+  if (W > kMaxWalkers) return fail(s, LRDMC_ERR_ARG, "init_walkers: more than LRDMC_MAX_WALKERS walkers");
   if (!(tau > 0.0) || !isfinite(tau) || !isfinite(e_trial) || recompute_every < 0)
     return fail(s, LRDMC_ERR_ARG, "init_walkers: tau must be > 0, recompute_every >= 0");
   if (((uintptr_t)workspace & 255) != 0) return fail(s, LRDMC_ERR_ARG, "init_walkers: workspace not 256-byte aligned");
@@ -503,8 +503,6 @@ lrdmc_status lrdmc_init_walkers(lrdmc_system_t s, int W, const double* x0, uint6
   P.jumps = (int*)(s->ws + p.jumps);
   P.cum = (double*)(s->ws + p.cum);
   P.part = (CombPart*)(s->ws + p.part);
-  P.bq = (unsigned char*)(s->ws + p.bq);
-  P.hist = (int*)(s->ws + p.hist);
   P.ticket = (int*)(s->ws + p.ticket);
   P.trace = (double*)(s->ws + p.trace);
   P.moves = (unsigned long long*)(s->ws + p.moves);
@@ -519,8 +517,8 @@ lrdmc_status lrdmc_init_walkers(lrdmc_system_t s, int W, const double* x0, uint6
   P.tau = tau;
   P.e_trial = e_trial;
   P.helpers = s->helpers;
-  // moves, err, counter, kdev, resid, hist, ticket
-  cudaError_t e = cudaMemsetAsync(s->ws + p.moves, 0, 7 * 256, s->stream);
+  // moves, err, counter, kdev, resid, ticket
+  cudaError_t e = cudaMemsetAsync(s->ws + p.moves, 0, 6 * 256, s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "workspace clear");
   e = cudaMemsetAsync(P.logw, 0, sizeof(double) * W, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(P.wgt, 0, sizeof(double) * W, s->stream);

@@ -131,9 +131,15 @@ constexpr int kMaxSmemBlock = 232448 - 2048;
 // shared memory of every block of the reconfiguration (8 bytes each).
 constexpr int kReconfigSmemW = 16384;
 // Reconfiguration grid: blocks of kCombThreads threads, each owning at
-// least 64 consecutive slots, at most kMaxCombBlocks blocks.
+// least kCombThreads consecutive slots, at most kMaxCombBlocks blocks; the
+// largest dynamic shared memory of its second kernel (the running sums of
+// up to kReconfigSmemW walkers, or a float per slot of a block).
 constexpr int kCombThreads = 256;
 constexpr int kMaxCombBlocks = 128;
+constexpr int kCombSmemMax = 200 * 1024;
+// Largest population (the reconfiguration's per-block slots fit its shared
+// memory with room to spare).
+constexpr int kMaxWalkers = LRDMC_MAX_WALKERS;
 int comb_blocks(int W);
 
 // Totals of one block of the reconfiguration.
@@ -141,7 +147,6 @@ struct CombPart {
   double w;          // sum of the block's weights (its last running sum)
   double swe;        // sum of w E_L
   long long jumps;   // sum of jumps
-  float bmin, bmax;  // range of the walkers' total rates b
 };
 
 struct PopDev {
@@ -155,9 +160,7 @@ struct PopDev {
   int* jumps;
   double* cum;  // running weight sums of the comb, relative to the start of each reconfiguration block
   CombPart* part;       // [kMaxCombBlocks] totals of the reconfiguration blocks
-  int* hist;            // [64] slots per order bucket (zero between reconfigurations)
   int* ticket;          // reconfiguration blocks finished (zero between reconfigurations)
-  unsigned char* bq;    // [W] order bucket of each slot
   double* trace;  // [4][cap]: e_k, mean weight, mean jumps, Sherman-Morrison residual at the recompute
   // largest Sherman-Morrison residual of the current interval's recompute,
   // as the bits of a non-negative double (atomicMax orders them as doubles)

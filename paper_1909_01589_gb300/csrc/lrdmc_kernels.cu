@@ -2347,93 +2347,93 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
 // Reconfiguration at the end of interval k, spread over G blocks of
 // kCombThreads threads; block g owns the R = ceil(W/G) slots from g R. Its
 // FP64 work (running sums, comb targets and comparisons) used to run on one
-// SM, whose FP64 pipe took 38 us for 4096 walkers; spread over G SMs it
-// takes a few. Two kernels:
+// SM, whose FP64 pipe took 38 us for 4096 walkers. Two kernels:
 //   k_comb_sums     per block: running weight sums of its slots from the
 //                   block's start (P.cum) and the block's totals (weights,
-//                   w E_L, jumps, range of the walkers' b)
+//                   w E_L, jumps)
 //   k_comb_parents  per block: the block offsets off[g] (the same sequential
-//                   sum in every block), the comb parents of its slots and
-//                   each slot's bucket for the next interval's order; the
-//                   last block to finish writes that order and the trace
-//                   entry and clears the counters.
-// Running sums: within a block, lane i of warp 0 sums its consecutive slots
-// from zero (l_i(s)), and O_0 = 0, O_{i+1} = O_i + l_i(last slot of i)
-// sequentially; c(s) = O_i + l_i(s). Over the blocks off[0] = 0,
-// off[g+1] = off[g] + c(last slot of g), and C_s = off[g] + c(s). Each
-// boundary repeats the rounding of the sum that ends the previous part, so C
-// is non-decreasing (rounding is monotone, weights are >= 0) and slot t's
-// parent is well defined: the smallest s with (t + xi) C_{W-1} / W < C_s,
-// else W - 1.
+//                   sum in every block), the comb parents of its slots, and
+//                   the next interval's processing order of its slots; the
+//                   last block to finish writes the trace entry and clears
+//                   the counters.
+// Running sums: within a block, lane i of the first kCombLanes lanes sums
+// its consecutive slots from zero (l_i(s)), and O_0 = 0, O_{i+1} = O_i +
+// l_i(last slot of i) sequentially; c(s) = O_i + l_i(s). Over the blocks
+// off[0] = 0, off[g+1] = off[g] + c(last slot of g), and C_s = off[g] +
+// c(s). Each boundary repeats the rounding of the sum that ends the previous
+// part, so C is non-decreasing (rounding is monotone, weights are >= 0) and
+// slot t's parent is well defined: the smallest s with
+// (t + xi) C_{W-1} / W < C_s, else W - 1. The sequential parts are kept
+// short (FP64 additions have a long latency on this GPU): kCombLanes lanes
+// per block, a few dozen blocks.
+//
+// Processing order of the next interval, longest expected first: a slot's
+// number of jumps is about tau times the total rate b of the walker it
+// receives. Each block sorts its slots by that b (64 buckets over the
+// block's range, descending), and the blocks' sorted lists are dealt round
+// robin into P.order: the r-th slot of every block comes before the
+// (r+1)-th of any. The blocks are samples of the population, so this is
+// close to a global sort, with no pass over the whole population. The order
+// affects no result, only the tail of the next interval.
+constexpr int kCombLanes = 16;
 
 __device__ __forceinline__ int comb_slots(int W, int G) { return (W + G - 1) / G; }
 
-__global__ void __launch_bounds__(kCombThreads) k_comb_sums(const PopDev P, const double* rec_next, int rec_stride,
-                                                           int off_b)
+__global__ void __launch_bounds__(kCombThreads) k_comb_sums(const PopDev P)
 {
   // the parents kernel is launched behind this one with programmatic stream
   // serialization; its blocks may take their SMs now and wait for this grid
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   constexpr int NW = kCombThreads / 32;
-  __shared__ double s_e[NW], s_tot[32];
+  __shared__ double s_e[NW], s_tot[kCombLanes];
   __shared__ long long s_j[NW];
-  __shared__ float s_lo[NW], s_hi[NW];
   const int W = P.W, G = gridDim.x, g = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int R = comb_slots(W, G);
   const int b0 = min(W, g * R), b1 = min(W, b0 + R);
   // the block's totals other than the weights: every thread
   double swe = 0.0;
   long long sj = 0;
-  float bmin = INFINITY, bmax = -INFINITY;
   for (int s = b0 + t; s < b1; s += kCombThreads) {
     swe += P.wgt[s] * P.el_end[s];
     sj += P.jumps[s];
-    const float bs = (float)rec_next[(size_t)s * rec_stride + off_b];
-    bmin = fminf(bmin, bs);
-    bmax = fmaxf(bmax, bs);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     swe += __shfl_xor_sync(FULL_MASK, swe, o);
     sj += __shfl_xor_sync(FULL_MASK, sj, o);
-    bmin = fminf(bmin, __shfl_xor_sync(FULL_MASK, bmin, o));
-    bmax = fmaxf(bmax, __shfl_xor_sync(FULL_MASK, bmax, o));
   }
-  if (lane == 0) { s_e[wid] = swe; s_j[wid] = sj; s_lo[wid] = bmin; s_hi[wid] = bmax; }
-  // the running sums: warp 0, each lane a run of consecutive slots
-  const int per = (b1 - b0 + 31) / 32;
-  const int lo = min(b1, b0 + lane * per), hi = min(b1, lo + per);
-  double l = 0.0;
-  if (wid == 0) {
+  if (lane == 0) { s_e[wid] = swe; s_j[wid] = sj; }
+  // the running sums: the first kCombLanes lanes, each a run of slots
+  const int per = (b1 - b0 + kCombLanes - 1) / kCombLanes;
+  const int lo = min(b1, b0 + t * per), hi = min(b1, lo + per);
+  if (t < kCombLanes) {
+    double l = 0.0;
     for (int s = lo; s < hi; ++s) l += P.wgt[s];
-    s_tot[lane] = l;
+    s_tot[t] = l;
   }
   __syncthreads();
   if (t == 0) {
     double o = 0.0;
-    for (int i = 0; i < 32; ++i) {
+    for (int i = 0; i < kCombLanes; ++i) {
       const double ti = s_tot[i];
       s_tot[i] = o;
       o += ti;
     }
     P.part[g].w = o;  // = c(last slot of the block): the last lane with slots ends there
+  }
+  if (t == 32) {  // fixed-order sums of the warps' totals
     double es = 0.0;
     long long js = 0;
-    float bl = INFINITY, bh = -INFINITY;
     for (int q = 0; q < NW; ++q) {
       es += s_e[q];
       js += s_j[q];
-      bl = fminf(bl, s_lo[q]);
-      bh = fmaxf(bh, s_hi[q]);
     }
     P.part[g].swe = es;
     P.part[g].jumps = js;
-    P.part[g].bmin = bl;
-    P.part[g].bmax = bh;
   }
   __syncthreads();
-  if (wid == 0) {
-    const double O = s_tot[lane];
+  if (t < kCombLanes) {
+    const double O = s_tot[t];
     double c = 0.0;
     for (int s = lo; s < hi; ++s) {
       c += P.wgt[s];
@@ -2464,42 +2464,41 @@ __device__ __forceinline__ int bucket_take(int* cnt, int q, int lane)
   return base + __popc(peers & ((1u << lane) - 1u));
 }
 
+// Position in P.order of the r-th slot (in the block's sorted order) of
+// block g: the blocks hold R slots but for a shorter last non-empty block
+// (Rl slots) and empty ones after it (Gn non-empty blocks); the first Rl
+// ranks of all Gn blocks come first, round robin, then the further ranks of
+// the Gn - 1 full blocks. A bijection of the slots onto 0..W-1.
+__device__ __forceinline__ int comb_order_pos(int g, int r, int Gn, int Rl)
+{
+  return r < Rl ? r * Gn + g : Rl * Gn + (r - Rl) * (Gn - 1) + g;
+}
+
 __global__ void __launch_bounds__(kCombThreads) k_comb_parents(const PopDev P, const double* rec_next,
                                                               int rec_stride, int off_b)
 {
   extern __shared__ double s_cum[];  // the running sums C_s (W <= kReconfigSmemW)
   __shared__ double s_off[kMaxCombBlocks + 1];
-  __shared__ CombPart s_part[kMaxCombBlocks];
-  __shared__ float s_range[2];
+  __shared__ double s_pw[kMaxCombBlocks];
+  __shared__ float s_lo[kCombThreads / 32], s_hi[kCombThreads / 32];
   __shared__ int s_cnt[64];
   __shared__ int s_last;
-  const int W = P.W, G = gridDim.x, g = blockIdx.x, t = threadIdx.x, lane = t & 31;
+  const int W = P.W, G = gridDim.x, g = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int R = comb_slots(W, G);
   const bool in_smem = W <= kReconfigSmemW;
   // everything below reads the sums kernel's results
   asm volatile("griddepcontrol.wait;" ::: "memory");
   const uint64_t k = *P.kdev;
   if (t < 64) s_cnt[t] = 0;
-  for (int h = t; h < G; h += kCombThreads) {
-    s_part[h].w = __ldcg(&P.part[h].w);
-    s_part[h].swe = __ldcg(&P.part[h].swe);
-    s_part[h].jumps = __ldcg(&P.part[h].jumps);
-    s_part[h].bmin = __ldcg(&P.part[h].bmin);
-    s_part[h].bmax = __ldcg(&P.part[h].bmax);
-  }
+  for (int h = t; h < G; h += kCombThreads) s_pw[h] = __ldcg(&P.part[h].w);
   __syncthreads();
   if (t == 0) {
     double o = 0.0;
-    float l = INFINITY, hb = -INFINITY;
     for (int h = 0; h < G; ++h) {
       s_off[h] = o;
-      o += s_part[h].w;
-      l = fminf(l, s_part[h].bmin);
-      hb = fmaxf(hb, s_part[h].bmax);
+      o += s_pw[h];
     }
     s_off[G] = o;
-    s_range[0] = l;
-    s_range[1] = hb;
   }
   __syncthreads();
   if (in_smem) {
@@ -2527,58 +2526,62 @@ __global__ void __launch_bounds__(kCombThreads) k_comb_parents(const PopDev P, c
   // the same number as the quotient (an exact scaling)
   const bool w_pow2 = (W & (W - 1)) == 0;
   const double inv_w = 1.0 / (double)W;
-  const float gmin = s_range[0], gmax = s_range[1];
-  const float scale = (gmax > gmin) ? 64.0f / (gmax - gmin) : 0.0f;
   const int b0 = min(W, g * R), b1 = min(W, b0 + R);
   const int chunk = (b1 - b0 + kCombThreads - 1) / kCombThreads;
   const int lo = min(b1, b0 + t * chunk), hi = min(b1, lo + chunk);
   // The targets grow with the slot, so the parents do too: a thread searches
   // for its first slot's parent, then steps forward from the previous one
   // (up to 8 steps, else a search over the rest), with the same comparisons.
-  // The loop runs chunk times in every thread (warp-uniform) so that the
-  // bucket counts can be taken per warp.
+  // The rate b of each slot's parent goes to the slot's bq byte's place in
+  // shared memory (as a float, in the dynamic area after the sums).
+  float* s_b = reinterpret_cast<float*>(s_cum + (in_smem ? W : 0));
   int a = 0;
-  for (int i = 0; i < chunk; ++i) {
-    const int tt = lo + i;
+  float bmin = INFINITY, bmax = -INFINITY;
+  for (int tt = lo; tt < hi; ++tt) {
+    const double num = ((double)tt + xi) * total;
+    const double target = w_pow2 ? num * inv_w : num / (double)W;
+    int steps = 0;
+    while (tt > lo && steps < 8 && a < W - 1 && !(target < comb_C(s_cum, s_off, P.cum, R, a, in_smem))) {
+      ++a;
+      ++steps;
+    }
+    if (tt == lo || (steps == 8 && a < W - 1 && !(target < comb_C(s_cum, s_off, P.cum, R, a, in_smem)))) {
+      int bnd = W - 1;
+      while (a < bnd) {
+        const int mid = (a + bnd) >> 1;
+        if (target < comb_C(s_cum, s_off, P.cum, R, mid, in_smem)) bnd = mid; else a = mid + 1;
+      }
+    }
+    P.parent[tt] = a;
+    const float bt = (float)rec_next[(size_t)a * rec_stride + off_b];
+    s_b[tt - b0] = bt;
+    bmin = fminf(bmin, bt);
+    bmax = fmaxf(bmax, bt);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    bmin = fminf(bmin, __shfl_xor_sync(FULL_MASK, bmin, o));
+    bmax = fmaxf(bmax, __shfl_xor_sync(FULL_MASK, bmax, o));
+  }
+  if (lane == 0) { s_lo[wid] = bmin; s_hi[wid] = bmax; }
+  __syncthreads();
+  // the block's slots by bucket of b, descending: counts, bases, positions
+  float gmin = INFINITY, gmax = -INFINITY;
+  for (int q = 0; q < kCombThreads / 32; ++q) {
+    gmin = fminf(gmin, s_lo[q]);
+    gmax = fmaxf(gmax, s_hi[q]);
+  }
+  const float scale = (gmax > gmin) ? 64.0f / (gmax - gmin) : 0.0f;
+  const int n = b1 - b0;
+  const int rounds = (n + kCombThreads - 1) / kCombThreads;  // warp-uniform
+  for (int i = 0; i < rounds; ++i) {
+    const int j = i * kCombThreads + t;
     int q = -1;
-    if (tt < hi) {
-      const double num = ((double)tt + xi) * total;
-      const double target = w_pow2 ? num * inv_w : num / (double)W;
-      int steps = 0;
-      while (tt > lo && steps < 8 && a < W - 1 && !(target < comb_C(s_cum, s_off, P.cum, R, a, in_smem))) {
-        ++a;
-        ++steps;
-      }
-      if (tt == lo || (steps == 8 && a < W - 1 && !(target < comb_C(s_cum, s_off, P.cum, R, a, in_smem)))) {
-        int bnd = W - 1;
-        while (a < bnd) {
-          const int mid = (a + bnd) >> 1;
-          if (target < comb_C(s_cum, s_off, P.cum, R, mid, in_smem)) bnd = mid; else a = mid + 1;
-        }
-      }
-      P.parent[tt] = a;
-      // processing order of the next interval, longest expected first: a
-      // slot's number of jumps is about tau times the total rate b of the
-      // walker it receives, so the slots are bucketed by that b, descending
-      const float bt = (float)rec_next[(size_t)a * rec_stride + off_b];
-      q = (int)((bt - gmin) * scale);
+    if (j < n) {
+      q = (int)((s_b[j] - gmin) * scale);
       q = 63 - min(63, max(0, q));
-      P.bq[tt] = (unsigned char)q;
     }
     bucket_take(s_cnt, q, lane);
-  }
-  __syncthreads();
-  if (t < 64 && s_cnt[t] > 0) atomicAdd(&P.hist[t], s_cnt[t]);
-  // the last block to finish writes the order and the trace entry
-  __threadfence();
-  __syncthreads();
-  if (t == 0) s_last = atomicAdd(P.ticket, 1) == G - 1;
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  if (t < 64) {
-    s_cnt[t] = __ldcg(&P.hist[t]);
-    P.hist[t] = 0;
   }
   __syncthreads();
   if (t < 32) {  // exclusive scan of the 64 bucket counts (two per lane)
@@ -2594,43 +2597,52 @@ __global__ void __launch_bounds__(kCombThreads) k_comb_parents(const PopDev P, c
     s_cnt[2 * t + 1] = ex + c0;
   }
   __syncthreads();
-  {
-    constexpr int U = 8;
-    for (int s0 = 0; s0 < W; s0 += U * kCombThreads) {
-      int qv[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int s = s0 + u * kCombThreads + t;
-        qv[u] = s < W ? (int)__ldcg(P.bq + s) : -1;
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int s = s0 + u * kCombThreads + t;
-        const int pos = bucket_take(s_cnt, qv[u], lane);
-        if (s < W) P.order[pos] = s;
-      }
+  const int Gn = (W + R - 1) / R;  // blocks with slots
+  const int Rl = W - (Gn - 1) * R;  // slots of the last of them
+  for (int i = 0; i < rounds; ++i) {
+    const int j = i * kCombThreads + t;
+    int q = -1;
+    if (j < n) {
+      q = (int)((s_b[j] - gmin) * scale);
+      q = 63 - min(63, max(0, q));
     }
+    const int r = bucket_take(s_cnt, q, lane);
+    if (j < n) P.order[comb_order_pos(g, r, Gn, Rl)] = b0 + j;
   }
-  if (t == 0) {
+  // the last block to finish writes the trace entry
+  __threadfence();
+  __syncthreads();
+  if (t == 0) s_last = atomicAdd(P.ticket, 1) == G - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (t < 32) {  // fixed-order sums over the blocks' totals
     double swe = 0.0;
     long long sj = 0;
-    for (int h = 0; h < G; ++h) {
-      swe += s_part[h].swe;
-      sj += s_part[h].jumps;
+    for (int h = t; h < G; h += 32) {
+      swe += __ldcg(&P.part[h].swe);
+      sj += __ldcg(&P.part[h].jumps);
     }
-    P.trace[k] = swe / total;
-    P.trace[P.trace_cap + k] = total / (double)W;
-    P.trace[2 * P.trace_cap + k] = (double)sj / (double)W;
-    // the Sherman-Morrison residual measured at this interval's recompute
-    // (-1: no recompute at this interval), then cleared for the next one
-    const bool recomputed = k > 0 && P.recompute_every > 0 && k % (uint64_t)P.recompute_every == 0;
-    P.trace[3 * P.trace_cap + k] = recomputed ? __longlong_as_double((long long)*P.resid) : -1.0;
-    *P.resid = 0ull;
-    *P.moves += (unsigned long long)sj;
-    *P.counter = 0;
-    *P.ticket = 0;
-    // every block has read k before taking its ticket: advance it
-    *P.kdev = k + 1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      swe += __shfl_xor_sync(FULL_MASK, swe, o);
+      sj += __shfl_xor_sync(FULL_MASK, sj, o);
+    }
+    if (t == 0) {
+      P.trace[k] = swe / total;
+      P.trace[P.trace_cap + k] = total / (double)W;
+      P.trace[2 * P.trace_cap + k] = (double)sj / (double)W;
+      // the Sherman-Morrison residual measured at this interval's recompute
+      // (-1: no recompute at this interval), then cleared for the next one
+      const bool recomputed = k > 0 && P.recompute_every > 0 && k % (uint64_t)P.recompute_every == 0;
+      P.trace[3 * P.trace_cap + k] = recomputed ? __longlong_as_double((long long)*P.resid) : -1.0;
+      *P.resid = 0ull;
+      *P.moves += (unsigned long long)sj;
+      *P.counter = 0;
+      *P.ticket = 0;
+      // every block has read k before taking its ticket: advance it
+      *P.kdev = k + 1;
+    }
   }
 }
 
@@ -2947,20 +2959,25 @@ cudaError_t launch_interval(const SysDev& S, const Layout& Lo, const LatDev& L, 
 
 int comb_blocks(int W)
 {
-  // at least 64 slots per block, at most kMaxCombBlocks blocks
-  const int R = std::max(64, (W + kMaxCombBlocks - 1) / kMaxCombBlocks);
+  // at least 256 slots per block (short sequential sums over the blocks),
+  // at most kMaxCombBlocks blocks
+  const int R = std::max(kCombThreads, (W + kMaxCombBlocks - 1) / kMaxCombBlocks);
   return std::max(1, (W + R - 1) / R);
 }
 
 cudaError_t launch_reconfig(const PopDev& P, const Layout& Lo, cudaStream_t st)
 {
   const int G = comb_blocks(P.W);
-  const int smem = P.W <= kReconfigSmemW ? (int)sizeof(double) * P.W : 0;
+  const int R = (P.W + G - 1) / G;
+  // the running sums (up to kReconfigSmemW walkers), then a float per slot
+  // of the block
+  const int smem = (P.W <= kReconfigSmemW ? (int)sizeof(double) * P.W : 0) + (int)sizeof(float) * R;
   // the attribute always takes the largest size, so systems of different
   // populations (and batches captured in one graph) never lower it
-  cudaError_t e = set_smem((const void*)k_comb_parents, (int)sizeof(double) * kReconfigSmemW);
+  cudaError_t e = set_smem((const void*)k_comb_parents, kCombSmemMax);
   if (e != cudaSuccess) return e;
-  k_comb_sums<<<G, kCombThreads, 0, st>>>(P, P.rec_dst, Lo.rec, Lo.off_b);
+  if (smem > kCombSmemMax) return cudaErrorInvalidValue;
+  k_comb_sums<<<G, kCombThreads, 0, st>>>(P);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
