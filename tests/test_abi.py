@@ -110,6 +110,18 @@ def test_workspace_bytes_grow_with_walkers(pkg):
     assert b2 > 9 * b1 / 2 and b1 % 256 == 0
 
 
+def test_population_limit_matches_header(pkg):
+    """LRDMC_MAX_WALKERS walkers are accepted, one more is LRDMC_ERR_ARG;
+    the limit is read from the header."""
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "lrdmc.h")).read()
+    limit = int(re.search(r"#define LRDMC_MAX_WALKERS (\d+)", hdr).group(1))
+    g = pkg.LrdmcSystem(S.helium())
+    assert g.workspace_bytes(limit, 4) > 0
+    with pytest.raises(pkg.LrdmcError) as e:
+        g.workspace_bytes(limit + 1, 4)
+    assert e.value.status == pkg.ERR_ARG
+
+
 def test_evaluate_argument_checks_before_the_library(pkg):
     """evaluate / evaluate_static refuse tensors the kernels would overrun
     or misread - wrong shape, dtype or device, a short output - with a

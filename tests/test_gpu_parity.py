@@ -247,16 +247,52 @@ def test_projection_full_size(pkg, oracle_mod, prec):
     assert compared >= 1
 
 
-@pytest.mark.parametrize("W", [1, 63, 65, 4097, 8193, 20000])
+@pytest.mark.parametrize("W", [1, 63, 255, 256, 257, 4097, 8193, 16384, 16385, 20000])
 def test_reconfiguration_blocks(pkg, oracle_mod, W):
-    """The reconfiguration over its grid of blocks: one walker, a block
-    boundary just before and after 64 walkers, ragged last blocks (4097,
-    8193), and a population above the 16384 whose running sums fit in shared
-    memory (20000: sums read from global memory). He, three intervals, every
-    parent, weight and trace entry against the oracle's sequential comb."""
+    """The reconfiguration over its grid of blocks (at least 256 slots a
+    block): one walker, one block, the boundary from one block to two (255,
+    256, 257), ragged last blocks (4097, 8193), the last population whose
+    running sums fit in shared memory and the first that does not (16384,
+    16385) and one beyond (20000: sums read from global memory). He, three
+    intervals, every parent, weight and trace entry against the oracle's
+    sequential comb."""
     compared, parted = _compare_runs(pkg, oracle_mod, S.helium(), "this_work", 0.2, W, 3, 0.05, 41, -2.9,
                                      label=f"projection He reconfiguration blocks W={W} df64")
     assert compared >= (1 if parted else 3)
+
+
+def test_reconfiguration_at_the_largest_population(pkg, oracle_mod):
+    """LRDMC_MAX_WALKERS He walkers (128 blocks of 32768 slots, the running
+    sums in global memory, a float per slot in shared memory), two
+    intervals. Too large for the oracle's projection; instead the comb is
+    recomputed on the host from the GPU's own log-weights with a sequential
+    running sum and the comb uniform from the oracle's Philox: every parent
+    agrees except where the target lies within 1e-10 (relative) of a bin
+    edge, and the parents are non-decreasing."""
+    W = 4194304
+    system = S.helium()
+    seed = 43
+    g = pkg.LrdmcSystem(system)
+    g.init_walkers(torch.tensor(S.initial_positions(system, W, seed), device="cuda"), seed=seed, tau=0.05,
+                   e_trial=-2.9, recompute_every=3, trace_capacity=2)
+    g.step(2, 0.2, pkg.Spacing(pkg.THIS_WORK))
+    e, wbar, jumps = g.energy_trace()
+    assert np.all(np.isfinite(e)) and np.all(np.isfinite(wbar)) and np.all(jumps > 0)
+    w = g.walkers()
+    parent, logw = w["parent"].astype(np.int64), w["logw_pre"]
+    del w
+    assert np.all(np.diff(parent) >= 0) and parent[0] >= 0 and parent[-1] < W
+    wt = np.exp(logw)
+    C = np.cumsum(wt)
+    total = C[-1]
+    xi = oracle_mod.uniform(int(oracle_mod.philox4x64([2 ** 64 - 1, 1, 0, 2], [seed, 0])[0]))
+    target = (np.arange(W, dtype=np.float64) + xi) * total / W
+    ref = np.minimum(np.searchsorted(C, target, side="right"), W - 1)
+    differ = np.flatnonzero(ref != parent)
+    lo = np.where(ref > 0, C[np.maximum(ref - 1, 0)], -np.inf)
+    margin = np.minimum(np.abs(target - C[ref]), np.abs(target - lo)) / total
+    assert np.all(margin[differ] < EDGE), (len(differ), differ[:8])
+    assert abs(wbar[-1] - total / W) <= 1e-9 * wbar[-1]
 
 
 @pytest.mark.parametrize("name,E", [("H", -0.5), ("Be_bare", -20.0)])
