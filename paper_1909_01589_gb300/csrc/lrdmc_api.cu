@@ -371,6 +371,10 @@ lrdmc_status lrdmc_create_system(int n_nuc, const double* nuc_xyz, const double*
     g_static_error = "create_system: n_ao differs from the shells' 2l+1 count";
     return LRDMC_ERR_ARG;
   }
+  S.n_grp = 0;
+  for (int qs = 0; qs < n_shells; ++qs)
+    if (!(S.sh[qs].kind == 0 && S.sh[qs].same_exp)) S.grp_first[S.n_grp++] = qs;
+  S.grp_first[S.n_grp] = n_shells;
   for (int qs = 0; qs < n_shells; ++qs) {
     const int q = order[qs];
     for (int f = 0; f < 2 * shells[q].l + 1; ++f)

@@ -78,6 +78,11 @@ struct SysDev {
   double b_ee, c_par, c_anti, en_b2;
   double V_nn;
   ShellDev sh[kMaxShell];
+  // groups of consecutive shells sharing one Slater exponential (a shell
+  // with same_exp joins the group of the shell before it): group g is
+  // shells [grp_first[g], grp_first[g + 1]); lanes deal out whole groups
+  int n_grp;
+  int grp_first[kMaxShell + 1];
   double C[kMaxAO * kMaxMO];  // [n_ao][n_mo]
   int precision;  // LRDMC_PRECISION_FP64 or LRDMC_PRECISION_DF64
   // neural pair term of the Jastrow factor, tabulated: channel c, cell k

@@ -1239,14 +1239,16 @@ __device__ LRDMC_EL void el_parts_m(const SysDev& S, const WarpMem& wm, int i, i
   const NT ri[3] = {A::c(wm.xd[3 * i]), A::c(wm.xd[3 * i + 1]), A::c(wm.xd[3 * i + 2])};
   el_zero<NT>(o);
   // basis: gradient and Laplacian contracted with v. Shells sharing one
-  // Slater exponential form a group; groups are dealt to the parts.
-  int prev_c = -1, grp = -1;
+  // Slater exponential form a group; groups are dealt to the parts, and
+  // each part loops over its own groups only, so that the parts' shells run
+  // side by side on their lanes (a loop over all shells with the others'
+  // skipped would run them one after the other).
+  int prev_c = -1;
   NT d[3] = {A::zero(), A::zero(), A::zero()}, r = A::zero(), r2 = A::zero(), ir = A::zero(), e = A::zero();
-  for (int q = 0; q < S.n_shell; ++q) {
+  for (int gi = part; gi < S.n_grp; gi += L)
+  for (int q = S.grp_first[gi]; q < S.grp_first[gi + 1]; ++q) {
     const ShellDev& sh = S.sh[q];
     const DfShell& dsh = S.D.sh[q];
-    if (!(sh.kind == 0 && sh.same_exp)) ++grp;
-    if ((grp % L) != part) continue;
     if (sh.center != prev_c) {
       prev_c = sh.center;
       d[0] = A::sub_fast(ri[0], A::c(S.D.nuc[prev_c][0]));
@@ -1570,18 +1572,18 @@ __device__ __forceinline__ void warp_eval_any(const SysDev& S, const double* sC,
 // Ainv[m][n] -= Ainv[m][l] (y_n - delta_nl) / ratio.
 // ----------------------------------------------------------------------------
 // chi_mu(p) for all AOs in double-float, one lane per group of shells that
-// share an exponential, written back as doubles.
+// share an exponential (the lanes' groups side by side), written back as
+// doubles.
 __device__ void ao_values_df_lanes(const SysDev& S, const double* p, double* out, int lane, const BlockMem& bm)
 {
   typedef Ar<df> A;
   df pd[3] = {df_from_double(p[0]), df_from_double(p[1]), df_from_double(p[2])};
-  int prev_c = -1, grp = -1;
+  int prev_c = -1;
   df d[3] = {A::zero(), A::zero(), A::zero()}, r = A::zero(), r2 = A::zero(), e = A::zero();
-  for (int q = 0; q < S.n_shell; ++q) {
+  for (int gi = lane; gi < S.n_grp; gi += 32)
+  for (int q = S.grp_first[gi]; q < S.grp_first[gi + 1]; ++q) {
     const ShellDev& sh = S.sh[q];
     const DfShell& dsh = S.D.sh[q];
-    if (!(sh.kind == 0 && sh.same_exp)) ++grp;
-    if ((grp & 31) != lane) continue;
     if (sh.center != prev_c) {
       prev_c = sh.center;
       d[0] = df_sub_fast(pd[0], S.D.nuc[prev_c][0]);
@@ -1602,13 +1604,12 @@ __device__ void ao_values_df_lanes(const SysDev& S, const double* p, double* out
 __device__ void ao_values_df_out(const SysDev& S, const df* pd, df* out, int lane, const BlockMem& bm)
 {
   typedef Ar<df> A;
-  int prev_c = -1, grp = -1;
+  int prev_c = -1;
   df d[3] = {A::zero(), A::zero(), A::zero()}, r = A::zero(), r2 = A::zero(), e = A::zero();
-  for (int q = 0; q < S.n_shell; ++q) {
+  for (int gi = lane; gi < S.n_grp; gi += 32)
+  for (int q = S.grp_first[gi]; q < S.grp_first[gi + 1]; ++q) {
     const ShellDev& sh = S.sh[q];
     const DfShell& dsh = S.D.sh[q];
-    if (!(sh.kind == 0 && sh.same_exp)) ++grp;
-    if ((grp & 31) != lane) continue;
     if (sh.center != prev_c) {
       prev_c = sh.center;
       d[0] = df_sub_fast(pd[0], S.D.nuc[prev_c][0]);
