@@ -371,9 +371,12 @@ lrdmc_status lrdmc_create_system(int n_nuc, const double* nuc_xyz, const double*
     g_static_error = "create_system: n_ao differs from the shells' 2l+1 count";
     return LRDMC_ERR_ARG;
   }
+  // the local energy's parts per electron (32 / N lanes, one beyond 32
+  // electrons) deal out single shells when they outnumber the shells
+  const int el_parts = S.N <= 32 ? 32 / S.N : 1;
   S.n_grp = 0;
   for (int qs = 0; qs < n_shells; ++qs)
-    if (!(S.sh[qs].kind == 0 && S.sh[qs].same_exp)) S.grp_first[S.n_grp++] = qs;
+    if (n_shells <= el_parts || !(S.sh[qs].kind == 0 && S.sh[qs].same_exp)) S.grp_first[S.n_grp++] = qs;
   S.grp_first[S.n_grp] = n_shells;
   for (int qs = 0; qs < n_shells; ++qs) {
     const int q = order[qs];

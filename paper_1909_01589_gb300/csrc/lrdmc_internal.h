@@ -78,9 +78,11 @@ struct SysDev {
   double b_ee, c_par, c_anti, en_b2;
   double V_nn;
   ShellDev sh[kMaxShell];
-  // groups of consecutive shells sharing one Slater exponential (a shell
-  // with same_exp joins the group of the shell before it): group g is
-  // shells [grp_first[g], grp_first[g + 1]); lanes deal out whole groups
+  // units of consecutive shells that the parts of an electron's local
+  // energy deal out (unit g is shells [grp_first[g], grp_first[g + 1])):
+  // every shell alone when there are no more shells than parts (each then
+  // forms its own exponential), else groups sharing one Slater exponential
+  // (a shell with same_exp joins the group of the shell before it)
   int n_grp;
   int grp_first[kMaxShell + 1];
   double C[kMaxAO * kMaxMO];  // [n_ao][n_mo]

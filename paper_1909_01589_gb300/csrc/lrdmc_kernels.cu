@@ -1238,17 +1238,18 @@ __device__ LRDMC_EL void el_parts_m(const SysDev& S, const WarpMem& wm, int i, i
   const df* v = &wm.vd[i * nao];
   const NT ri[3] = {A::c(wm.xd[3 * i]), A::c(wm.xd[3 * i + 1]), A::c(wm.xd[3 * i + 2])};
   el_zero<NT>(o);
-  // basis: gradient and Laplacian contracted with v. Shells sharing one
-  // Slater exponential form a group; groups are dealt to the parts, and
-  // each part loops over its own groups only, so that the parts' shells run
-  // side by side on their lanes (a loop over all shells with the others'
-  // skipped would run them one after the other).
+  // basis: gradient and Laplacian contracted with v. The shells' units
+  // (single shells, or groups sharing one Slater exponential) are dealt to
+  // the parts, and each part loops over its own units only, so that the
+  // parts' shells run side by side on their lanes (a loop over all shells
+  // with the others' skipped would run them one after the other).
   int prev_c = -1;
   NT d[3] = {A::zero(), A::zero(), A::zero()}, r = A::zero(), r2 = A::zero(), ir = A::zero(), e = A::zero();
   for (int gi = part; gi < S.n_grp; gi += L)
   for (int q = S.grp_first[gi]; q < S.grp_first[gi + 1]; ++q) {
     const ShellDev& sh = S.sh[q];
     const DfShell& dsh = S.D.sh[q];
+    const bool first = q == S.grp_first[gi];
     if (sh.center != prev_c) {
       prev_c = sh.center;
       d[0] = A::sub_fast(ri[0], A::c(S.D.nuc[prev_c][0]));
@@ -1258,7 +1259,7 @@ __device__ LRDMC_EL void el_parts_m(const SysDev& S, const WarpMem& wm, int i, i
       r = A::sqrt(r2);
       ir = A::rcp(r);
     }
-    if (sh.kind == 0 && !sh.same_exp) e = A::exp(A::neg(A::mul(A::c(dsh.zeta), r)), S.D.exp.K, bm.tab);
+    if (sh.kind == 0 && (first || !sh.same_exp)) e = A::exp(A::neg(A::mul(A::c(dsh.zeta), r)), S.D.exp.K, bm.tab);
     NT Rv, R1, R2;
     if (sh.kind == 0) {
       Rv = radial_value_m<NT>(S, sh, dsh, r, r2, e, bm);
@@ -1571,28 +1572,25 @@ __device__ __forceinline__ void warp_eval_any(const SysDev& S, const double* sC,
 // y_n = sum_m phi_m(p) Ainv[m][n], ratio = y_l,
 // Ainv[m][n] -= Ainv[m][l] (y_n - delta_nl) / ratio.
 // ----------------------------------------------------------------------------
-// chi_mu(p) for all AOs in double-float, one lane per group of shells that
-// share an exponential (the lanes' groups side by side), written back as
-// doubles.
+// chi_mu(p) for all AOs in double-float, one lane per shell, written back
+// as doubles.
 __device__ void ao_values_df_lanes(const SysDev& S, const double* p, double* out, int lane, const BlockMem& bm)
 {
   typedef Ar<df> A;
   df pd[3] = {df_from_double(p[0]), df_from_double(p[1]), df_from_double(p[2])};
-  int prev_c = -1;
-  df d[3] = {A::zero(), A::zero(), A::zero()}, r = A::zero(), r2 = A::zero(), e = A::zero();
-  for (int gi = lane; gi < S.n_grp; gi += 32)
-  for (int q = S.grp_first[gi]; q < S.grp_first[gi + 1]; ++q) {
+  // one shell per lane (at most 32 shells), each with its own centre
+  // distance and exponential: all shells side by side
+  for (int q = lane; q < S.n_shell; q += 32) {
     const ShellDev& sh = S.sh[q];
     const DfShell& dsh = S.D.sh[q];
-    if (sh.center != prev_c) {
-      prev_c = sh.center;
-      d[0] = df_sub_fast(pd[0], S.D.nuc[prev_c][0]);
-      d[1] = df_sub_fast(pd[1], S.D.nuc[prev_c][1]);
-      d[2] = df_sub_fast(pd[2], S.D.nuc[prev_c][2]);
-      r2 = dot3<df>(d[0], d[1], d[2]);
-      r = df_sqrt(r2);
-    }
-    if (sh.kind == 0 && !sh.same_exp) e = df_exp(df_neg(df_mul(dsh.zeta, r)), S.D.exp.K, bm.tab);
+    df d[3];
+    d[0] = df_sub_fast(pd[0], S.D.nuc[sh.center][0]);
+    d[1] = df_sub_fast(pd[1], S.D.nuc[sh.center][1]);
+    d[2] = df_sub_fast(pd[2], S.D.nuc[sh.center][2]);
+    const df r2 = dot3<df>(d[0], d[1], d[2]);
+    const df r = df_sqrt(r2);
+    df e = A::zero();
+    if (sh.kind == 0) e = df_exp(df_neg(df_mul(dsh.zeta, r)), S.D.exp.K, bm.tab);
     df Rv = radial_value_m<df>(S, sh, dsh, r, r2, e, bm);
     df Sv[5];
     int nf = solid_m<df>(sh.l, d, Sv);
@@ -1600,25 +1598,23 @@ __device__ void ao_values_df_lanes(const SysDev& S, const double* p, double* out
   }
 }
 
-// chi_mu(p) for all AOs in double-float into out (df), lanes by exponent group.
+// chi_mu(p) for all AOs in double-float into out (df), one lane per shell.
 __device__ void ao_values_df_out(const SysDev& S, const df* pd, df* out, int lane, const BlockMem& bm)
 {
   typedef Ar<df> A;
-  int prev_c = -1;
-  df d[3] = {A::zero(), A::zero(), A::zero()}, r = A::zero(), r2 = A::zero(), e = A::zero();
-  for (int gi = lane; gi < S.n_grp; gi += 32)
-  for (int q = S.grp_first[gi]; q < S.grp_first[gi + 1]; ++q) {
+  // one shell per lane (at most 32 shells), each with its own centre
+  // distance and exponential: all shells side by side
+  for (int q = lane; q < S.n_shell; q += 32) {
     const ShellDev& sh = S.sh[q];
     const DfShell& dsh = S.D.sh[q];
-    if (sh.center != prev_c) {
-      prev_c = sh.center;
-      d[0] = df_sub_fast(pd[0], S.D.nuc[prev_c][0]);
-      d[1] = df_sub_fast(pd[1], S.D.nuc[prev_c][1]);
-      d[2] = df_sub_fast(pd[2], S.D.nuc[prev_c][2]);
-      r2 = dot3<df>(d[0], d[1], d[2]);
-      r = df_sqrt(r2);
-    }
-    if (sh.kind == 0 && !sh.same_exp) e = df_exp(df_neg(df_mul(dsh.zeta, r)), S.D.exp.K, bm.tab);
+    df d[3];
+    d[0] = df_sub_fast(pd[0], S.D.nuc[sh.center][0]);
+    d[1] = df_sub_fast(pd[1], S.D.nuc[sh.center][1]);
+    d[2] = df_sub_fast(pd[2], S.D.nuc[sh.center][2]);
+    const df r2 = dot3<df>(d[0], d[1], d[2]);
+    const df r = df_sqrt(r2);
+    df e = A::zero();
+    if (sh.kind == 0) e = df_exp(df_neg(df_mul(dsh.zeta, r)), S.D.exp.K, bm.tab);
     df Rv = radial_value_m<df>(S, sh, dsh, r, r2, e, bm);
     df Sv[5];
     int nf = solid_m<df>(sh.l, d, Sv);
