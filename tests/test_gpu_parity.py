@@ -83,7 +83,7 @@ def _w_abs(prec):
 
 class _EvalWorst:
     """Worst errors of an evaluation case: plainly relative to |value| (the
-    the benchmark spec's 1e-10, shown as measured) and against the floating-point
+    plain 1e-10 relative bar, shown as measured) and against the floating-point
     scale the assertions use; with the count of elements whose plain
     relative error exceeds 1e-10."""
 
