@@ -1214,8 +1214,9 @@ __device__ NT warp_scan_m(const df* T, int P, int lane, NT target, int* pick, in
   return carry;
 }
 
-// Partial sums of the local energy of electron i over the shells q, the
-// electrons j and the nuclei I congruent to part modulo L.
+// Partial sums of the local energy of electron i over the shell units, the
+// partners (the t-th electron other than i) and the nuclei whose index is
+// congruent to part modulo L.
 template <class NT>
 struct ElParts {
   NT gD[3], lD, gJ[3], lJ, S, V;
@@ -1303,13 +1304,14 @@ __device__ LRDMC_EL void el_parts_m(const SysDev& S, const WarpMem& wm, int i, i
       o.lD = A::add(o.lD, A::mul(cS, radlap));
     }
   }
-  // e-e pairs
+  // e-e pairs: the N - 1 partners of i (j = t, skipping i) dealt evenly
+  // to the parts
   const int si = spin_of(S, i);
   const NT b = A::c(S.D.b_ee);
   if (sizeof(NT) == sizeof(df) && (wm.pcw == 8 && wm.n_pc > 0 && NJ)) {
     // every pair's terms come from the pair cache (evaluated once per pair)
-    for (int j = part; j < S.N; j += L) {
-      if (j == i) continue;
+    for (int t = part; t < S.N - 1; t += L) {
+      const int j = t < i ? t : t + 1;
       const df* e = &wm.pc[8 * pair_index(S.N, min(i, j), max(i, j))];
       NT d0 = A::sub_fast(ri[0], A::c(wm.xd[3 * j])), d1 = A::sub_fast(ri[1], A::c(wm.xd[3 * j + 1])),
          d2 = A::sub_fast(ri[2], A::c(wm.xd[3 * j + 2]));
@@ -1322,8 +1324,8 @@ __device__ LRDMC_EL void el_parts_m(const SysDev& S, const WarpMem& wm, int i, i
       if (j > i && S.ee_on) o.V = A::add(o.V, A::c(e[7]));
     }
   } else
-  for (int j = part; j < S.N; j += L) {
-    if (j == i) continue;
+  for (int t = part; t < S.N - 1; t += L) {
+    const int j = t < i ? t : t + 1;
     NT d0 = A::sub_fast(ri[0], A::c(wm.xd[3 * j])), d1 = A::sub_fast(ri[1], A::c(wm.xd[3 * j + 1])),
        d2 = A::sub_fast(ri[2], A::c(wm.xd[3 * j + 2]));
     NT rr = A::sqrt(dot3<NT>(d0, d1, d2));
