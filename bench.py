@@ -436,6 +436,9 @@ def run_ours(args):
             "energy_minus_fp64_Ha": mx_energy - ref_energy,
             "combined_sigma_Ha": float(np.hypot(mx_err, ref_err)),
             "kernel_ms_per_launch": mx["t_int_ms"] / max(mx["n_int"], 1),
+            "efficiency_note": "from the short continuation; over 450 000 intervals this mode's rare local-energy "
+                               "spikes make its efficiency 0.59 of the double-float form's "
+                               "(results/mixed_vs_parity_ne_long.json)",
             "roofline": roofline(system, G, "fp32", mx)}
     if nj is not None:
         leg_nj, info = nj
