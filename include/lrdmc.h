@@ -286,9 +286,11 @@ LRDMC_API lrdmc_status lrdmc_load(lrdmc_system_t sys, const char* path);
  * and reconfiguration in IEEE double. Values below about 1e-30 lose
  * low-order bits in double-float (their contribution to any sum is then
  * negligible); arguments of exp below -87 give 0. LRDMC_PRECISION_FP32 is
- * the mixed-precision mode: the same evaluation, waiting time and heat bath
- * in IEEE single precision (ratios and local energies to ~1e-6 relative),
- * with FP64 kept for the inverse Slater matrices (updates and periodic
+ * the mixed-precision mode: the lattice moves (ratios and rates), waiting
+ * time and heat bath in IEEE single precision (ratios to ~1e-6 relative),
+ * the local energy in double-float (a single-precision local energy's
+ * rare large errors near the nuclei inflated the weights' variance), and
+ * FP64 kept for the inverse Slater matrices (updates and periodic
  * recomputation), weights and reconfiguration; its results are not
  * FP64-parity results but statistically equivalent ones. Takes effect at
  * the next lrdmc_step / lrdmc_evaluate call. */

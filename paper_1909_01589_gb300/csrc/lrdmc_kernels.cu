@@ -28,6 +28,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <mutex>
 
 #include "lrdmc_internal.h"
@@ -1230,7 +1231,7 @@ __device__ __forceinline__ void el_zero(ElParts<NT>& o)
   for (int k = 0; k < 3; ++k) { o.gD[k] = A::zero(); o.gJ[k] = A::zero(); }
 }
 
-template <class NT, bool NJ>
+template <class NT, bool NJ, bool PC = true>
 __device__ LRDMC_EL void el_parts_m(const SysDev& S, const WarpMem& wm, int i, int part, int L, const BlockMem& bm,
                            ElParts<NT>& o)
 {
@@ -1308,7 +1309,7 @@ __device__ LRDMC_EL void el_parts_m(const SysDev& S, const WarpMem& wm, int i, i
   // to the parts
   const int si = spin_of(S, i);
   const NT b = A::c(S.D.b_ee);
-  if (sizeof(NT) == sizeof(df) && (wm.pcw == 8 && wm.n_pc > 0 && NJ)) {
+  if (PC && sizeof(NT) == sizeof(df) && (wm.pcw == 8 && wm.n_pc > 0 && NJ)) {
     // every pair's terms come from the pair cache (evaluated once per pair)
     for (int t = part; t < S.N - 1; t += L) {
       const int j = t < i ? t : t + 1;
@@ -1458,6 +1459,11 @@ __device__ __forceinline__ void candidate_m(const SysDev& S, const LatDev& L, co
 // The first part of an evaluation: projected inverse columns, converted
 // positions and rotation, the caches, then the local energy (into el) and
 // the Jastrow sums Sd of every electron. The moves read all of it.
+// 1: the FP32 mode's local energy in double-float (the lattice moves stay in
+// single precision); 0: all of its evaluation in single precision.
+#ifndef LRDMC_FP32_EL_DF
+#define LRDMC_FP32_EL_DF 1
+#endif
 template <class NT, bool NJ, bool NC>
 __device__ __forceinline__ void eval_prelude_m(const SysDev& S, const double* sC, const LatDev& L, const WarpMem& wm,
                                                int lane, double& el)
@@ -1469,8 +1475,16 @@ __device__ __forceinline__ void eval_prelude_m(const SysDev& S, const double* sC
   // converted with the positions. The mixed mode converts the inverse
   // blocks to float once (scratch), not once per use: each conversion from
   // double runs on the FP64 pipe
+  // The FP32 mode can take its local energy in double-float (LRDMC_FP32_EL_DF,
+  // on by default): the projected columns, positions and rotation are then
+  // formed as in the double-float mode, and only the lattice moves run in
+  // single precision (they read the double-float values' leading floats).
+  constexpr bool kElDf = sizeof(NT) == sizeof(float) && LRDMC_FP32_EL_DF;
+  constexpr bool kFloatProj = sizeof(NT) == sizeof(float) && !kElDf;
+  typedef typename std::conditional<kElDf, df, NT>::type ET;
+  typedef Ar<ET> AE;
   const float* Af = reinterpret_cast<const float*>(wm.scr);
-  if (sizeof(NT) == sizeof(float)) {
+  if (kFloatProj) {
     for (int j = lane; j < nu * nu + S.n_dn * S.n_dn; j += 32) reinterpret_cast<float*>(wm.scr)[j] = (float)wm.A[j];
     __syncwarp();
   }
@@ -1478,7 +1492,7 @@ __device__ __forceinline__ void eval_prelude_m(const SysDev& S, const double* sC
     int i = idx / nao, mu = idx % nao;
     int spin = i < nu ? 0 : 1, l = i < nu ? i : i - nu, n = spin ? S.n_dn : nu;
     const double* Am = spin ? wm.A + nu * nu : wm.A;
-    if (sizeof(NT) == sizeof(float)) {
+    if (kFloatProj) {
       const float* Amf = spin ? Af + nu * nu : Af;
       float acc = 0.0f;
       for (int m = 0; m < n; ++m) acc += bm.Cf[mu * S.n_mo + m] * Amf[m * n + l];
@@ -1486,11 +1500,11 @@ __device__ __forceinline__ void eval_prelude_m(const SysDev& S, const double* sC
     } else {
       double acc = 0.0;
       for (int m = 0; m < n; ++m) acc += sC[mu * S.n_mo + m] * Am[m * n + l];
-      wm.vd[idx] = A::store(A::from_double(acc));
+      wm.vd[idx] = AE::store(AE::from_double(acc));
     }
   }
-  for (int j = lane; j < 3 * N; j += 32) wm.xd[j] = A::store(A::from_double(wm.x[j]));
-  if (lane < 9) wm.Rd[lane] = A::store(A::from_double(wm.R[lane]));
+  for (int j = lane; j < 3 * N; j += 32) wm.xd[j] = AE::store(AE::from_double(wm.x[j]));
+  if (lane < 9) wm.Rd[lane] = AE::store(AE::from_double(wm.R[lane]));
   __syncwarp();
   // the caches pay in double-float arithmetic only, and exist only when
   // the system's layout has room for them (NC is set otherwise: the
@@ -1502,32 +1516,33 @@ __device__ __forceinline__ void eval_prelude_m(const SysDev& S, const double* sC
     __syncwarp();
   }
   // local energy: Lp lanes per electron share its shells, electrons and nuclei
-  NT epart = A::zero();
+  constexpr bool kPC = sizeof(NT) == sizeof(df) && !NC;  // the pair cache holds the pairs' terms
+  ET epart = AE::zero();
   if (N <= 32) {
     const int Lp = 32 / N;
     const int i = lane % N, part = lane / N;
     const bool act = lane < N * Lp;
-    ElParts<NT> o;
-    if (act) el_parts_m<NT, NJ>(S, wm, i, part, Lp, bm, o);
-    else el_zero<NT>(o);
+    ElParts<ET> o;
+    if (act) el_parts_m<ET, NJ, kPC>(S, wm, i, part, Lp, bm, o);
+    else el_zero<ET>(o);
     for (int pp = 1; pp < Lp; ++pp) {
       int src = lane + pp * N;
-      el_combine<NT>(o, src < 32 ? src : lane, part == 0 && src < N * Lp);
+      el_combine<ET>(o, src < 32 ? src : lane, part == 0 && src < N * Lp);
     }
     if (part == 0 && act) {
-      wm.Sd[i] = A::store(o.S);
-      epart = el_local<NT>(o);
+      wm.Sd[i] = AE::store(o.S);
+      epart = el_local<ET>(o);
     }
   } else {
     for (int i = lane; i < N; i += 32) {
-      ElParts<NT> o;
-      el_parts_m<NT, NJ>(S, wm, i, 0, 1, bm, o);
-      wm.Sd[i] = A::store(o.S);
-      epart = A::add(epart, el_local<NT>(o));
+      ElParts<ET> o;
+      el_parts_m<ET, NJ, kPC>(S, wm, i, 0, 1, bm, o);
+      wm.Sd[i] = AE::store(o.S);
+      epart = AE::add(epart, el_local<ET>(o));
     }
   }
-  NT etot = warp_sum_m<NT>(epart);
-  el = A::to_double(etot) + S.V_nn;
+  ET etot = warp_sum_m<ET>(epart);
+  el = AE::to_double(etot) + S.V_nn;
   __syncwarp();
 }
 
