@@ -425,6 +425,25 @@ def test_fp32_evaluation_error(pkg, oracle_mod, name, kind, a):
     assert worst_r < FP32_RTOL and worst_e < FP32_RTOL, (worst_r, worst_e)
 
 
+@pytest.mark.parametrize("name,a", [("Ne", 0.2), ("Ar", 1 / 63), ("H2O", 0.1)])
+def test_fp32_local_energy_is_the_double_float_one(pkg, name, a):
+    """The mixed-precision mode forms the local energy in double-float: for
+    a Pade guiding function its E_L is bit for bit the double-float mode's
+    (which the parity tests hold to the FP64 oracle), while its lattice
+    moves keep single-precision ratios."""
+    system = S.make_system(name)
+    n = 32
+    x = torch.tensor(S.initial_positions(system, n, 311), device="cuda")
+    R = torch.tensor(S.random_rotations(n, 312), device="cuda")
+    sp = pkg.Spacing(pkg.THIS_WORK)
+    out = {}
+    for prec in (pkg.PRECISION_DF64, pkg.PRECISION_FP32):
+        out[prec] = [t.cpu().numpy() for t in pkg.LrdmcSystem(system).set_precision(prec).evaluate(x, R, a, sp)]
+    assert np.array_equal(out[pkg.PRECISION_DF64][3], out[pkg.PRECISION_FP32][3])
+    # the ratios are the single-precision ones (not the double-float ones)
+    assert not np.array_equal(out[pkg.PRECISION_DF64][0], out[pkg.PRECISION_FP32][0])
+
+
 def test_fp32_projection_energy_matches_fp64(pkg):
     """He, 8192 walkers, 600 intervals after 100 of equilibration: the mixed
     mode's energy agrees with the FP64 mode's within 4 combined standard
