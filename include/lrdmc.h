@@ -67,8 +67,14 @@ typedef enum {
   LRDMC_ERR_SINGULAR = 3,  /* singular Slater matrix or zero update ratio   */
   LRDMC_ERR_NONFINITE = 4, /* non-finite local energy or rate               */
   LRDMC_ERR_TIMEOUT = 5,   /* an interval exceeded its iteration limit      */
-  LRDMC_ERR_STATE = 6      /* call out of order (e.g. step before init)     */
+  LRDMC_ERR_STATE = 6,     /* call out of order (e.g. step before init)     */
+  LRDMC_ERR_BOUNDS = 7     /* a checked index was out of range (only in a
+                              build with -DLRDMC_BOUNDS, see
+                              lrdmc_build_flags)                            */
 } lrdmc_status;
+
+/* Build flags of the loaded library (lrdmc_build_flags). */
+#define LRDMC_BUILD_BOUNDS 1 /* compiled with -DLRDMC_BOUNDS                */
 
 /* Lattice spacing function, Eq. 1-7 and S-13. */
 typedef enum {
@@ -273,7 +279,12 @@ LRDMC_API lrdmc_status lrdmc_evaluate_static(lrdmc_system_t sys, int n_configs, 
                                              void* stream);
 
 /* Writes / reads the population (positions, inverses, rotations, cached
- * evaluation, parents, interval counter, trace) to / from a file. */
+ * evaluation, parents, interval counter, trace) to / from a file. load
+ * fails with LRDMC_ERR_ARG for a file of another population size or
+ * layout, a truncated file, or (default build) a parent index outside
+ * [0, W); a bounds-checked build (lrdmc_build_flags) leaves the parent
+ * indices to the kernels' checks, which report LRDMC_ERR_BOUNDS at the next
+ * lrdmc_sync. */
 LRDMC_API lrdmc_status lrdmc_save(lrdmc_system_t sys, const char* path);
 LRDMC_API lrdmc_status lrdmc_load(lrdmc_system_t sys, const char* path);
 
@@ -469,6 +480,16 @@ LRDMC_API void lrdmc_batch_destroy(lrdmc_batch_t batch);
 
 /* Last error message of the system (static string if sys is NULL). */
 LRDMC_API const char* lrdmc_last_error(lrdmc_system_t sys);
+
+/* Build flags of this library: LRDMC_BUILD_BOUNDS when it was compiled
+ * with -DLRDMC_BOUNDS. In that build every walker-level index the kernels
+ * read from device memory or derive from it (processing order, comb
+ * parents and order positions, trace slots, helper teams) is checked
+ * against its array; an index out of range sets a device error word and is
+ * replaced by 0, so the access stays in bounds, and the next
+ * synchronising call (lrdmc_sync) fails with LRDMC_ERR_BOUNDS. Results are
+ * otherwise the default build's. Needs no GPU; never fails. */
+LRDMC_API int lrdmc_build_flags(void);
 
 /* Releases the system (not the caller's workspace or stream). */
 LRDMC_API void lrdmc_destroy(lrdmc_system_t sys);

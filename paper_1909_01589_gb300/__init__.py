@@ -15,7 +15,9 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "liblrdmc.so")
+# LRDMC_LIBRARY selects another build of the library, such as the
+# bounds-checked liblrdmc_bounds.so (build.build(bounds=True))
+LIB_PATH = os.environ.get("LRDMC_LIBRARY") or os.path.join(_HERE, "liblrdmc.so")
 
 MAX_NUC = 8
 MAX_SHELL = 32
@@ -24,7 +26,8 @@ MAX_AO = 64
 MAX_SPIN = 32
 STATIC_EVAL_MAX = 262144
 
-OK, ERR_ARG, ERR_CUDA, ERR_SINGULAR, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE = range(7)
+OK, ERR_ARG, ERR_CUDA, ERR_SINGULAR, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE, ERR_BOUNDS = range(8)
+BUILD_BOUNDS = 1
 SINGLE, THIS_WORK, PREVIOUS, EXPLICIT = 0, 1, 2, 3
 PRECISION_FP64, PRECISION_DF64, PRECISION_FP32 = 0, 1, 2
 
@@ -39,7 +42,7 @@ EXPORTED = [
     "lrdmc_nj_backward", "lrdmc_set_interval_blocks", "lrdmc_interval_blocks", "lrdmc_set_tail_helpers",
     "lrdmc_batch_create",
     "lrdmc_batch_step", "lrdmc_batch_sync", "lrdmc_batch_stream", "lrdmc_batch_last_error", "lrdmc_batch_destroy",
-    "lrdmc_batch_set_groups", "lrdmc_batch_set_carveout", "lrdmc_batch_set_pipelined",
+    "lrdmc_batch_set_groups", "lrdmc_batch_set_carveout", "lrdmc_batch_set_pipelined", "lrdmc_build_flags",
 ]
 NJ_MAX_CH, NJ_MAX_FEAT, NJ_HIDDEN, NJ_MAX_CELLS = 8, 12, 64, 8192
 
@@ -150,6 +153,8 @@ def load_library():
                                      ct.POINTER(ct.c_longlong), i]
     L.lrdmc_last_error.restype = ct.c_char_p
     L.lrdmc_last_error.argtypes = [vp]
+    L.lrdmc_build_flags.restype = i
+    L.lrdmc_build_flags.argtypes = []
     L.lrdmc_destroy.restype = None
     L.lrdmc_destroy.argtypes = [vp]
     L.lrdmc_nj_n_params.restype = i
@@ -188,6 +193,12 @@ def load_library():
     L.lrdmc_batch_destroy.argtypes = [vp]
     _lib = L
     return L
+
+
+def build_flags() -> int:
+    """lrdmc_build_flags of the loaded library (BUILD_BOUNDS for the
+    bounds-checked build)."""
+    return load_library().lrdmc_build_flags()
 
 
 def _np_ptr(a):

@@ -468,6 +468,7 @@ static lrdmc_status read_error_word(lrdmc_system_t s)
   if (w & kErrNonFinite) return fail(s, LRDMC_ERR_NONFINITE, "non-finite local energy or rate");
   if (w & kErrIters) return fail(s, LRDMC_ERR_TIMEOUT, "an interval exceeded its iteration limit");
   if (w & kErrTimeout) return fail(s, LRDMC_ERR_TIMEOUT, "a bounded wait of the interval kernel's tail helpers ran out");
+  if (w & kErrBounds) return fail(s, LRDMC_ERR_BOUNDS, "a checked walker index was out of range");
   return LRDMC_OK;
 }
 
@@ -628,6 +629,7 @@ static lrdmc_status sync_system(lrdmc_system_t s)
   if (w & kErrNonFinite) return fail(s, LRDMC_ERR_NONFINITE, "non-finite local energy or rate");
   if (w & kErrIters) return fail(s, LRDMC_ERR_TIMEOUT, "an interval exceeded its iteration limit");
   if (w & kErrTimeout) return fail(s, LRDMC_ERR_TIMEOUT, "a bounded wait of the interval kernel's tail helpers ran out");
+  if (w & kErrBounds) return fail(s, LRDMC_ERR_BOUNDS, "a checked walker index was out of range");
   return LRDMC_OK;
 }
 
@@ -885,8 +887,10 @@ lrdmc_status lrdmc_load(lrdmc_system_t s, const char* path)
        fread(&moves, sizeof(moves), 1, f) == 1;
   fclose(f);
   if (!ok) return fail(s, LRDMC_ERR_ARG, "load: truncated file");
+#ifndef LRDMC_BOUNDS  // the bounds-checked build leaves them to the kernels' checks
   for (int t = 0; t < W; ++t)
     if (par[t] < 0 || par[t] >= W) return fail(s, LRDMC_ERR_ARG, "load: corrupt parent index");
+#endif
   s->cur = 0;
   cudaError_t e = cudaMemcpyAsync(s->rec[0], rec.data(), sizeof(double) * rec.size(), cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(s->P.parent, par.data(), sizeof(int) * W, cudaMemcpyHostToDevice, s->stream);
@@ -1447,6 +1451,8 @@ void lrdmc_batch_destroy(lrdmc_batch_t b)
 }
 
 const char* lrdmc_last_error(lrdmc_system_t s) { return s ? s->last_error.c_str() : g_static_error; }
+
+int lrdmc_build_flags(void) { return kBuildFlags; }
 
 void lrdmc_destroy(lrdmc_system_t s)
 {

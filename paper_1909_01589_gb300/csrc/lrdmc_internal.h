@@ -26,6 +26,34 @@ constexpr int kErrSingular = 1;
 constexpr int kErrNonFinite = 2;
 constexpr int kErrIters = 4;
 constexpr int kErrTimeout = 8;  // a bounded wait ran out (tail helpers of the interval kernel, tensor-core barrier)
+constexpr int kErrBounds = 16;  // a checked index was out of range (bounds-checked builds only)
+
+#ifdef LRDMC_BOUNDS
+constexpr int kBuildFlags = LRDMC_BUILD_BOUNDS;
+#else
+constexpr int kBuildFlags = 0;
+#endif
+
+// The walker-level indices that the kernels read from device memory or
+// derive from it (processing order, parents, comb order positions, trace
+// slots, helper teams) pass through bounded(i, n, err). In a build with
+// -DLRDMC_BOUNDS an index outside [0, n) sets kErrBounds in the error word
+// and becomes 0, so the access stays inside its array and the host reports
+// LRDMC_ERR_BOUNDS; in the default build it is the index unchanged.
+template <class I>
+__device__ __forceinline__ I bounded(I i, long long n, int* err)
+{
+#ifdef LRDMC_BOUNDS
+  if ((unsigned long long)(long long)i >= (unsigned long long)n) {
+    atomicOr(err, kErrBounds);
+    return I(0);
+  }
+#else
+  (void)n;
+  (void)err;
+#endif
+  return i;
+}
 
 // Philox counter tags.
 constexpr uint64_t kTagTimeHB = 0;

@@ -2012,10 +2012,10 @@ __device__ __forceinline__ void interval_team(const SysDev& S, const Layout& Lo,
         mode = P.helpers ? kSearch : kDone;
       } else {
         if (P.helpers) team_open(mine, lane);
-        const int s = P.order[idx];
+        const int s = bounded(P.order[idx], P.W, P.err);
         const WarpMem wm = warp_mem(Lo, S, sC + Lo.head + wib * Lo.smem_warp);
         double b, el;
-        load_record(Lo, P.rec_src + (size_t)P.parent[s] * Lo.rec, wm, lane, b, el);
+        load_record(Lo, P.rec_src + (size_t)bounded(P.parent[s], P.W, P.err) * Lo.rec, wm, lane, b, el);
         if (recompute) {
           double rs = 0.0;
           bool ok = warp_inverse(S, sC, wm.x, 0, wm.A, wm.scr, lane, &rs);
@@ -2146,7 +2146,7 @@ __device__ __forceinline__ void interval_team(const SysDev& S, const Layout& Lo,
           continue;
         }
         if (lane == 0) {
-          st.owner = o;
+          st.owner = bounded(o, blockDim.x >> 5, P.err);
           st.kidx = kidx;
           st.last = 0;
         }
@@ -2250,8 +2250,8 @@ k_interval(const __grid_constant__ SysDev S, const Layout Lo, const LatDev L, co
         asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
         break;
       }
-      const int s = P.order[idx];
-      const int src = P.parent[s];
+      const int s = bounded(P.order[idx], P.W, P.err);
+      const int src = bounded(P.parent[s], P.W, P.err);
       double b, el;
       load_record(Lo, P.rec_src + (size_t)src * Lo.rec, wm, lane, b, el);
       df bdf = df_from_double(b);
@@ -2566,9 +2566,10 @@ __global__ void __launch_bounds__(kCombThreads) k_comb_parents(const PopDev P, c
         if (target < comb_C(s_cum, s_off, P.cum, R, mid, in_smem)) bnd = mid; else a = mid + 1;
       }
     }
+    a = bounded(a, W, P.err);
     P.parent[tt] = a;
     const float bt = (float)rec_next[(size_t)a * rec_stride + off_b];
-    s_b[tt - b0] = bt;
+    s_b[bounded(tt - b0, R, P.err)] = bt;
     bmin = fminf(bmin, bt);
     bmax = fmaxf(bmax, bt);
   }
@@ -2621,7 +2622,7 @@ __global__ void __launch_bounds__(kCombThreads) k_comb_parents(const PopDev P, c
       q = 63 - min(63, max(0, q));
     }
     const int r = bucket_take(s_cnt, q, lane);
-    if (j < n) P.order[comb_order_pos(g, r, Gn, Rl)] = b0 + j;
+    if (j < n) P.order[bounded(comb_order_pos(g, r, Gn, Rl), W, P.err)] = b0 + j;
   }
   // the last block to finish writes the trace entry
   __threadfence();
@@ -2643,13 +2644,14 @@ __global__ void __launch_bounds__(kCombThreads) k_comb_parents(const PopDev P, c
       sj += __shfl_xor_sync(FULL_MASK, sj, o);
     }
     if (t == 0) {
-      P.trace[k] = swe / total;
-      P.trace[P.trace_cap + k] = total / (double)W;
-      P.trace[2 * P.trace_cap + k] = (double)sj / (double)W;
+      const uint64_t kt = bounded(k, P.trace_cap, P.err);  // the trace slot
+      P.trace[kt] = swe / total;
+      P.trace[P.trace_cap + kt] = total / (double)W;
+      P.trace[2 * P.trace_cap + kt] = (double)sj / (double)W;
       // the Sherman-Morrison residual measured at this interval's recompute
       // (-1: no recompute at this interval), then cleared for the next one
       const bool recomputed = k > 0 && P.recompute_every > 0 && k % (uint64_t)P.recompute_every == 0;
-      P.trace[3 * P.trace_cap + k] = recomputed ? __longlong_as_double((long long)*P.resid) : -1.0;
+      P.trace[3 * P.trace_cap + kt] = recomputed ? __longlong_as_double((long long)*P.resid) : -1.0;
       *P.resid = 0ull;
       *P.moves += (unsigned long long)sj;
       *P.counter = 0;

@@ -187,3 +187,28 @@ def test_energy_trace_async_arguments(pkg):
     with pytest.raises(ValueError):
         g.energy_trace_async(3, 2, out)
 
+
+
+def test_status_codes_match_header(pkg):
+    text = open(os.path.join(ROOT, "include", "lrdmc.h")).read()
+    codes = {m.group(1): int(m.group(2)) for m in re.finditer(r"LRDMC_(OK|ERR_\w+)\s*=\s*(\d+)", text)}
+    assert codes == {"OK": pkg.OK, "ERR_ARG": pkg.ERR_ARG, "ERR_CUDA": pkg.ERR_CUDA,
+                     "ERR_SINGULAR": pkg.ERR_SINGULAR, "ERR_NONFINITE": pkg.ERR_NONFINITE,
+                     "ERR_TIMEOUT": pkg.ERR_TIMEOUT, "ERR_STATE": pkg.ERR_STATE, "ERR_BOUNDS": pkg.ERR_BOUNDS}
+    assert int(re.search(r"#define LRDMC_BUILD_BOUNDS (\d+)", text).group(1)) == pkg.BUILD_BOUNDS
+
+
+def test_bounds_checked_build_exports_the_same_abi(pkg):
+    """liblrdmc_bounds.so (-DLRDMC_BOUNDS) exports every declared entry point
+    and reports LRDMC_BUILD_BOUNDS; the default library reports no flag."""
+    from paper_1909_01589_gb300 import build
+
+    path = build.build(bounds=True)
+    lib = ct.CDLL(path)
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+    lib.lrdmc_build_flags.restype = ct.c_int
+    assert lib.lrdmc_build_flags() == pkg.BUILD_BOUNDS
+    default = ct.CDLL(build.LIB)
+    default.lrdmc_build_flags.restype = ct.c_int
+    assert default.lrdmc_build_flags() == 0
