@@ -1,7 +1,6 @@
 """Pins of the oracle's counter-based generator, uniform conversion, lattice
 rotation, heat bath and comb."""
 import numpy as np
-import pytest
 
 
 def test_philox4x64_matches_numpy(oracle_mod):

@@ -6,7 +6,6 @@ import os
 import socket
 
 import numpy as np
-import pytest
 
 from paper_1909_01589_gb300 import stats
 
