@@ -71,3 +71,27 @@ def test_clock_sampler_defaults_to_a_temporary_file():
     assert clk.path.startswith(tempfile.gettempdir()) and "rank3" in clk.path
     with pytest.raises(AttributeError):
         clk.f  # nothing opened before the timed region starts
+
+
+def test_roofline_reproduces_by_hand():
+    """The bench line's roofline from the method's work: Ne on the double
+    grid counts 20 253 arithmetic operations, 1430 square roots, 1400
+    divisions and 502 exponentials per walker-move; at 8.6, 5.7 and 16.0
+    DFMA-equivalents for sqrt, division and exp that is 97 126 FP64-equivalent
+    flops. A launch of 34 058 walker-moves in 1.373 ms then achieves
+    97 126 x 34 058 / 1.373 ms = 2.409 TFLOP/s, 1.91 of the 1.259 TFLOP/s FP64
+    pipe (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)."""
+    import bench
+    import lrdmc_synth as S
+
+    ne = S.neon()
+    assert bench.method_ops_per_move(ne, 2) == {"arith": 20253, "sqrt": 1430, "div": 1400, "exp": 502}
+    flops = 2 * (20253 + 8.6 * 1430 + 5.7 * 1400 + 16.0 * 502)
+    assert abs(flops - 97126) < 0.5 and abs(2 * bench.dfma_equiv_per_move(ne, 2) - flops) < 1e-6
+    assert abs(bench.FP64_PEAK_TFLOPS - 152 * 2 * 2 * 2.07e9 / 1e12) < 1e-3
+    leg = {"t_int_ms": 10 * 1.373, "n_int": 10, "moves": 10 * 34058}
+    r = bench.roofline(ne, 2, "df64", leg)
+    assert abs(r["achieved"] - flops * 34058 / 1.373e-3 / 1e12) < 1e-9
+    assert abs(r["achieved"] - 2.409) < 1e-3 and abs(r["frac"] - 2.409 / 1.259) < 1e-3
+    assert r["bound"] == "alu" and r["peak"] == bench.FP64_PEAK_TFLOPS
+
