@@ -394,9 +394,10 @@ def initial_positions(system: System, n_walkers: int, seed: int) -> np.ndarray:
     rng = np.random.default_rng(np.random.PCG64(seed))
     N = system.N
     x = np.empty((n_walkers, N, 3))
+    orbital_shell = system.orbital_shell or [0]  # a system without the map seeds from its first shell
     for i in range(N):
         m = i if i < system.n_up else i - system.n_up
-        sh = system.shells[system.orbital_shell[m % len(system.orbital_shell)]]
+        sh = system.shells[orbital_shell[m % len(orbital_shell)]]
         r = rng.gamma(2.0 * sh.n_eff + 1.0, 1.0 / (2.0 * sh.zeta), n_walkers)
         v = rng.normal(size=(n_walkers, 3))
         v /= np.linalg.norm(v, axis=1, keepdims=True)
@@ -466,3 +467,100 @@ def neural_init(spec: NeuralSpec, seed: int, out_scale: float = 0.0) -> np.ndarr
     parts = [rng.normal(size=H * D) / np.sqrt(D), np.zeros(H), rng.normal(size=H * H) / np.sqrt(H), np.zeros(H),
              out_scale * rng.normal(size=H) / np.sqrt(H), np.zeros(1)]
     return np.concatenate(parts).astype(np.float32)
+
+
+# ---------------------------------------------------------------- JSON form of a system
+def system_to_dict(system: System) -> dict:
+    """The system as plain JSON types: nuclei, charges, spin counts, shells,
+    orbital coefficients [n_ao][n_mo] and the Pade Jastrow parameters."""
+    def shell(s):
+        d = {"center": int(s.center), "l": int(s.l), "kind": "sto" if s.kind == STO else "gto"}
+        if s.kind == STO:
+            d.update(n_eff=float(s.n_eff), zeta=float(s.zeta))
+        else:
+            d.update(alpha=[float(v) for v in s.alpha], coef=[float(v) for v in s.coef],
+                     n_eff=float(s.n_eff), zeta=float(s.zeta))
+        return d
+
+    return {
+        "name": system.name,
+        "nuclei": np.asarray(system.nuc_xyz, float).reshape(-1, 3).tolist(),
+        "Z": np.asarray(system.Z, float).tolist(),
+        "n_up": int(system.n_up), "n_dn": int(system.n_dn),
+        "shells": [shell(s) for s in system.shells],
+        "C": np.asarray(system.C, float).tolist(),
+        "jastrow": {"b_ee": float(system.b_ee), "c_par": float(system.c_par), "c_anti": float(system.c_anti),
+                    "en_b1": None if system.en_b1 is None else np.asarray(system.en_b1, float).tolist(),
+                    "en_b2": float(system.en_b2), "ee_on": bool(system.ee_on)},
+        "orbital_shell": None if system.orbital_shell is None else [int(q) for q in system.orbital_shell],
+        "exact_energy": system.exact_energy,
+    }
+
+
+def system_from_dict(d: dict) -> System:
+    """Inverse of system_to_dict; raises ValueError for a malformed system
+    (shapes, shell kinds, centres, coefficient rows against the shells)."""
+    def need(obj, key, where):
+        if key not in obj:
+            raise ValueError(f"system: missing '{key}' in {where}")
+        return obj[key]
+
+    nuc = np.asarray(need(d, "nuclei", "system"), dtype=np.float64)
+    Z = np.asarray(need(d, "Z", "system"), dtype=np.float64)
+    if nuc.ndim != 2 or nuc.shape[1] != 3 or len(Z) != len(nuc) or len(Z) == 0:
+        raise ValueError("system: 'nuclei' must be [n_nuc][3] and 'Z' [n_nuc]")
+    n_up, n_dn = int(need(d, "n_up", "system")), int(need(d, "n_dn", "system"))
+    if n_up < 1 or n_dn < 0:
+        raise ValueError("system: need n_up >= 1 and n_dn >= 0")
+    shells = []
+    for q, s in enumerate(need(d, "shells", "system")):
+        where = f"shell {q}"
+        center, l = int(need(s, "center", where)), int(need(s, "l", where))
+        if not 0 <= center < len(Z) or not 0 <= l <= 2:
+            raise ValueError(f"system: {where} has centre {center} or l = {l} out of range")
+        kind = need(s, "kind", where)
+        if kind == "sto":
+            zeta = float(need(s, "zeta", where))
+            if zeta <= 0.0:
+                raise ValueError(f"system: {where} needs zeta > 0")
+            shells.append(Shell(center, l, STO, float(need(s, "n_eff", where)), zeta))
+        elif kind == "gto":
+            alpha, coef = list(need(s, "alpha", where)), list(need(s, "coef", where))
+            if not 1 <= len(alpha) <= MAX_PRIM or len(coef) != len(alpha) or min(alpha) <= 0.0:
+                raise ValueError(f"system: {where} needs 1..{MAX_PRIM} positive exponents with one coefficient each")
+            shells.append(Shell(center, l, GTO, float(s.get("n_eff", 1.0)), float(s.get("zeta", 1.0)),
+                                [float(v) for v in alpha], [float(v) for v in coef]))
+        else:
+            raise ValueError(f"system: {where} has kind '{kind}' (sto or gto)")
+    C = np.asarray(need(d, "C", "system"), dtype=np.float64)
+    n_ao = sum(2 * s.l + 1 for s in shells)
+    if C.ndim != 2 or C.shape[0] != n_ao or C.shape[1] < max(n_up, n_dn):
+        raise ValueError(f"system: 'C' must be [{n_ao}][>= {max(n_up, n_dn)}] for these shells")
+    j = need(d, "jastrow", "system")
+    en_b1 = j.get("en_b1")
+    if en_b1 is not None and len(en_b1) != len(Z):
+        raise ValueError("system: 'en_b1' needs one value per nucleus")
+    orb = d.get("orbital_shell")
+    if orb is not None and any(not 0 <= int(q) < len(shells) for q in orb):
+        raise ValueError("system: 'orbital_shell' names a shell that does not exist")
+    return System(
+        name=str(d.get("name", "system")), nuc_xyz=nuc, Z=Z, n_up=n_up, n_dn=n_dn, shells=shells, C=C,
+        b_ee=float(j.get("b_ee", 1.0)), c_par=float(j.get("c_par", 0.25)), c_anti=float(j.get("c_anti", 0.5)),
+        en_b1=None if en_b1 is None else np.asarray(en_b1, dtype=np.float64), en_b2=float(j.get("en_b2", 1.0)),
+        ee_on=bool(j.get("ee_on", True)), orbital_shell=None if orb is None else [int(q) for q in orb],
+        exact_energy=d.get("exact_energy"),
+    )
+
+
+def save_system(system: System, path: str) -> None:
+    import json
+
+    with open(path, "w") as f:
+        json.dump(system_to_dict(system), f, indent=1)
+
+
+def load_system(path: str) -> System:
+    import json
+
+    with open(path) as f:
+        return system_from_dict(json.load(f))
