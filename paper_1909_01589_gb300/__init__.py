@@ -269,12 +269,30 @@ class LrdmcSystem:
     # ---------------------------------------------------------------- population
     def init_walkers(self, x0, seed, tau, e_trial=0.0, recompute_every=10, trace_capacity=4096,
                      stream=None, device="cuda"):
-        """x0: [W][N][3] float64, a CUDA tensor or a host array (copied)."""
+        """x0: [W][N][3] float64, a CUDA tensor on the workspace's device or a
+        host array (copied). Raises ValueError, before any device work, for
+        another shape or dtype, non-finite positions or a tensor on another
+        device."""
         import torch
 
-        W = int(x0.shape[0])
+        shape = tuple(x0.shape)
+        if len(shape) != 3 or shape[1:] != (self.N, 3) or shape[0] < 1:
+            raise ValueError(f"init_walkers: x0 must be [W][{self.N}][3] with W >= 1, got {shape}")
+        if isinstance(x0, np.ndarray):
+            if not np.issubdtype(x0.dtype, np.floating):
+                raise ValueError(f"init_walkers: x0 must be floating point, got {x0.dtype}")
+            finite = bool(np.isfinite(x0).all())
+        else:
+            if x0.dtype != torch.float64:
+                raise ValueError(f"init_walkers: x0 must be float64, got {x0.dtype}")
+            finite = bool(torch.isfinite(x0).all())
+        if not finite:
+            raise ValueError("init_walkers: start positions must be finite")
+        W = shape[0]
         nbytes = self.workspace_bytes(W, trace_capacity)
         self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        if not isinstance(x0, np.ndarray) and x0.is_cuda and x0.device != self._ws.device:
+            raise ValueError(f"init_walkers: x0 is on {x0.device}, the workspace on {self._ws.device}")
         base = self._ws.data_ptr()
         ptr = (base + 255) & ~255
         if stream is None:
@@ -285,7 +303,6 @@ class LrdmcSystem:
             xp = _np_ptr(x0)
         else:
             x0 = x0.contiguous()
-            assert x0.dtype == torch.float64
             xp = _t_ptr(x0)
         self._x0_keep = x0
         st = load_library().lrdmc_init_walkers(self.h, W, xp, int(seed), float(tau), float(e_trial),

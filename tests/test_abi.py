@@ -212,3 +212,25 @@ def test_bounds_checked_build_exports_the_same_abi(pkg):
     default = ct.CDLL(build.LIB)
     default.lrdmc_build_flags.restype = ct.c_int
     assert default.lrdmc_build_flags() == 0
+
+
+def test_init_walkers_validates_start_positions_before_device_work(pkg):
+    """Fault injection on the host: NaN start positions, a wrong shape and a
+    wrong dtype are rejected before the library or the device is touched."""
+    import torch
+
+    system = S.helium()
+    g = pkg.LrdmcSystem(system)
+    x0 = S.initial_positions(system, 8, 1)
+    bad = x0.copy()
+    bad[3, 1, 2] = np.nan
+    cases = [(bad, "finite"), (x0[:, :1], r"\[W\]\[2\]\[3\]"), (x0.reshape(8, 6), r"\[W\]\[2\]\[3\]"),
+             (x0[:0], "W >= 1"), (x0.astype(np.int64), "floating point"),
+             (torch.tensor(x0, dtype=torch.float32), "float64"), (torch.tensor(bad), "finite")]
+    inf = x0.copy()
+    inf[0, 0, 0] = np.inf
+    cases.append((inf, "finite"))
+    for x, msg in cases:
+        with pytest.raises(ValueError, match=msg):
+            g.init_walkers(x, seed=1, tau=0.02, e_trial=-2.9)
+    assert g._ws is None  # nothing was allocated
