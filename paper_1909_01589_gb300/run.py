@@ -125,7 +125,7 @@ def run(system, cfg: RunConfig, lr=None) -> dict:
     g.step(cfg.intervals, cfg.a, sp)
     g.sync()
     seconds = time.perf_counter() - t0
-    e, wbar, jumps = g.energy_trace()
+    e, wbar, jumps = g.energy_trace(max_n=cfg.intervals)
     moves = g.moves()
     q = cfg.equilibration
     energy = stats.energy_estimate(e[q:], wbar[q:], cfg.mixed_L)

@@ -98,7 +98,8 @@ class _FakeSystem:
     def sync(self):
         self.calls.append(("sync",))
 
-    def energy_trace(self):
+    def energy_trace(self, max_n=1 << 20):
+        assert max_n == 10  # the whole trace of the run, not a default length
         k = np.arange(10.0)
         return -2.9 + 0.01 * np.sin(k), 1.0 + 0.001 * np.cos(k), 3.0 + 0 * k
 
@@ -130,7 +131,7 @@ def test_runner_calls_the_binding_in_order():
     shape, kw = _FakeSystem.calls[3][1], _FakeSystem.calls[3][2]
     assert shape == (64, 2, 3)
     assert kw == {"seed": 9, "tau": 0.02, "e_trial": -2.9, "recompute_every": 3, "trace_capacity": 10}
-    e, w, _ = _FakeSystem.energy_trace(None)
+    e, w, _ = _FakeSystem.energy_trace(None, 10)
     assert out["energy_Ha"] == stats.energy_estimate(e[4:], w[4:], 2)
     assert out["error_Ha"] == stats.reblock(e[4:])[0]
     assert out["intervals_used"] == 6 and out["walker_moves"] == 4096
