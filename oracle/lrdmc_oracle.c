@@ -794,6 +794,19 @@ void orc_lattice_eval(const orc_system* s, const orc_lattice* L, const double* x
 
 /* =========================================================================
  * 5. Walkers, continuous-time projection and reconfiguration.
+ *
+ * The paper defines the lattice Hamiltonian H^a (the "Boosting the
+ * double-grid LRDMC" paragraph of the main text: Eq. 1 with p of Eq. 2 or
+ * Eq. 3, and a' of Eq. 4 or Eq. 6). It leaves the projection itself to the
+ * LRDMC literature it cites with Eq. 1 (Casula, Filippi and Sorella, 2005;
+ * Becca and Sorella, 2017). That projection is continuous-time Green's
+ * function Monte Carlo with heat-bath jumps, the fixed node with sign flip,
+ * and population control. The functions below write those steps out in
+ * their plain form, one walker at a time:
+ *  - run_interval: waiting times, weights and heat-bath jumps;
+ *  - orc_heat_bath;
+ *  - orc_sm_update: the Sherman-Morrison rank-one update;
+ *  - reconfigure and orc_comb: the comb.
  * ========================================================================= */
 
 struct orc_pop {

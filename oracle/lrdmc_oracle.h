@@ -41,12 +41,14 @@ double orc_aprime_over_a_this_work(int Z, double a, double beta, double kappa);
 double orc_aprime_over_a_previous(double Z);
 double orc_speedup(double Z, double n_core, double aprime_over_a);
 
-/* ---- counter-based generator and lattice rotation ---- */
+/* ---- counter-based generator (Philox4x64-10, Salmon et al., SC'11) and the
+ *      random lattice rotation (Shoemake's uniform quaternion) ---- */
 void   orc_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
 double orc_uniform(uint64_t bits);
 void   orc_rotation(double u1, double u2, double u3, double R[9]);
 
-/* ---- the trial function psi_G = det_up * det_dn * exp(J) ---- */
+/* ---- the trial function psi_G = det_up * det_dn * exp(J) (Slater-Jastrow,
+ *      Pade Jastrow factor); E_L = -lap psi_G / (2 psi_G) + V ---- */
 typedef struct orc_system orc_system;
 orc_system* orc_system_create(int n_nuc, const double* nuc_xyz, const double* Z,
                               int n_up, int n_dn,
@@ -94,11 +96,13 @@ void   orc_lattice_eval(const orc_system* s, const orc_lattice* L, const double*
                         const double* Ainv_up, const double* Ainv_dn, const double* R,
                         double* ratio, double* w, double* T, double* b, double* EL);
 
-/* ---- heat bath and comb ---- */
+/* ---- heat bath and comb: the jump choice and the population control of
+ *      the LRDMC projection cited with Eq. 1 ---- */
 int    orc_heat_bath(const double* T, int P, double b, double u, double* margin);
 void   orc_comb(int W, const double* wt, double xi, int* parent, double* margin, double* margin_teeth);
 
-/* ---- the walker population and the projection ---- */
+/* ---- the walker population and the continuous-time projection with H^a
+ *      (Eq. 1; the method cited with it) ---- */
 typedef struct orc_pop orc_pop;
 orc_pop* orc_pop_create(orc_system* s, int W, const double* x0, uint64_t seed,
                         double tau, double e_trial, int recompute_every);
