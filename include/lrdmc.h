@@ -129,8 +129,9 @@ typedef struct {
  * without the double-float evaluation caches is laid out without them
  * (same results, slower double-float evaluation): e.g. 48 electrons on 8
  * centres with 42 AOs. 64 electrons with 62 AOs do not fit at all; such
- * systems fail with LRDMC_ERR_ARG and a message giving the size. No GPU
- * work. */
+ * systems fail with LRDMC_ERR_ARG and a message giving the size. So do
+ * non-finite coordinates, Jastrow parameters or MO coefficients, a charge
+ * that is not positive, and two nuclei at one point. No GPU work. */
 LRDMC_API lrdmc_status lrdmc_create_system(int n_nuc, const double* nuc_xyz, const double* Z,
                                  int n_up, int n_dn, const lrdmc_shell* shells, int n_shells,
                                  const double* mo_coeff, int n_ao, int n_mo,

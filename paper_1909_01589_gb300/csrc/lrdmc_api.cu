@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -279,6 +280,26 @@ lrdmc_status lrdmc_create_system(int n_nuc, const double* nuc_xyz, const double*
     g_static_error = "create_system: sizes beyond the limits of lrdmc.h";
     return LRDMC_ERR_ARG;
   }
+  // every number the kernels read is finite, every charge positive, and no
+  // two nuclei coincide (V_nn would be infinite)
+  bool finite = std::isfinite(jas->b_ee) && std::isfinite(jas->c_par) && std::isfinite(jas->c_anti) &&
+                std::isfinite(jas->en_b2);
+  for (int I = 0; I < n_nuc; ++I) {
+    finite = finite && Z[I] > 0.0 && std::isfinite(Z[I]) && std::isfinite(jas->en_b1[I]);
+    for (int d = 0; d < 3; ++d) finite = finite && std::isfinite(nuc_xyz[3 * I + d]);
+  }
+  for (int q = 0; q < n_ao * n_mo; ++q) finite = finite && std::isfinite(mo_coeff[q]);
+  if (!finite) {
+    g_static_error = "create_system: non-finite coordinates, charges, Jastrow or MO coefficients, or a charge <= 0";
+    return LRDMC_ERR_ARG;
+  }
+  for (int I = 0; I < n_nuc; ++I)
+    for (int J = I + 1; J < n_nuc; ++J)
+      if (nuc_xyz[3 * I] == nuc_xyz[3 * J] && nuc_xyz[3 * I + 1] == nuc_xyz[3 * J + 1] &&
+          nuc_xyz[3 * I + 2] == nuc_xyz[3 * J + 2]) {
+        g_static_error = "create_system: two nuclei at one point";
+        return LRDMC_ERR_ARG;
+      }
   lrdmc_system_t s = new lrdmc_system_s();
   SysDev& S = s->S;
   memset(&S, 0, sizeof(S));

@@ -234,3 +234,38 @@ def test_init_walkers_validates_start_positions_before_device_work(pkg):
         with pytest.raises(ValueError, match=msg):
             g.init_walkers(x, seed=1, tau=0.02, e_trial=-2.9)
     assert g._ws is None  # nothing was allocated
+
+
+def test_create_system_rejects_non_finite_or_unphysical_input(pkg):
+    """Host validation before any allocation: NaN or infinite coordinates,
+    Jastrow parameters and MO coefficients, a charge <= 0 and two nuclei at
+    one point fail with LRDMC_ERR_ARG; every synthetic system still passes."""
+    def broken(change):
+        s = S.make_system("H2O")
+        s.nuc_xyz = np.array(s.nuc_xyz, float)
+        s.Z = np.array(s.Z, float)
+        s.C = np.array(s.C, float)
+        s.en_b1 = np.array(s.en_b1, float)
+        change(s)
+        return s
+
+    cases = [
+        lambda s: s.nuc_xyz.__setitem__((1, 0), np.nan),
+        lambda s: s.nuc_xyz.__setitem__((2, 2), np.inf),
+        lambda s: s.Z.__setitem__(1, 0.0),
+        lambda s: s.Z.__setitem__(0, -8.0),
+        lambda s: s.C.__setitem__((3, 1), np.nan),
+        lambda s: s.en_b1.__setitem__(2, np.inf),
+        lambda s: setattr(s, "b_ee", np.nan),
+        lambda s: setattr(s, "c_anti", np.inf),
+        lambda s: s.nuc_xyz.__setitem__(2, s.nuc_xyz[1]),
+    ]
+    for change in cases:
+        with pytest.raises(pkg.LrdmcError) as e:
+            pkg.LrdmcSystem(broken(change))
+        assert e.value.status == pkg.ERR_ARG
+    for name in S.SYSTEMS:
+        pkg.LrdmcSystem(S.make_system(name))
+    for Z in (1, 4, 18, 36, 54):
+        pkg.LrdmcSystem(S.hydrogenic_ion(Z))
+    pkg.LrdmcSystem(S.cluster(8, 24, 2))
